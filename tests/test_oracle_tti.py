@@ -1,0 +1,272 @@
+"""Pins of the FP64 TTI oracle against what the paper and mathematics fix.
+
+- plane-wave symbol of the rotated operator vs the published pseudo-acoustic
+  TTI dispersion relation (Alkhalifah 2000; the self-adjoint form of Zhang et
+  al. 2011 / Duveneck & Bakker 2011 cited in Sec. III-A), with the expected
+  convergence order in kh;
+- eps = delta = 0 collapse to the isotropic acoustic leapfrog of Sec. II-A,
+  Eq. (acou), for any tilt and azimuth;
+- point-source Green's function of the 3D wave equation;
+- exactness of the adjoint (Sec. III-A: "exactness being a mandatory
+  requirement"): dot test and assembled one-step matrices;
+- Taylor test of the zero-lag cross-correlation gradient.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+
+def homogeneous_tti(n, h, so, vp, eps, delta, theta, phi, nbl=0, nt=10, dt=1e-3):
+    m = {k: np.full((n, n, n), v, np.float32) for k, v in
+         zip(("vp", "eps", "delta", "theta", "phi"), (vp, eps, delta, theta, phi))}
+    src = np.zeros((1, 3), np.float32)
+    rec = np.zeros((1, 3), np.float32)
+    return synth.Problem(synth.TTI, n, n, n, nbl, h, so, nt, dt, m, src,
+                         np.zeros((1, nt), np.float32), rec)
+
+
+def pseudo_acoustic_v2(eps, delta, vartheta):
+    """Published pseudo-acoustic dispersion: squared phase velocities / v0^2
+    for propagation at angle vartheta from the symmetry axis."""
+    s2, c2 = math.sin(vartheta) ** 2, math.cos(vartheta) ** 2
+    a = 1 + 2 * eps * s2
+    disc = math.sqrt(max(a * a - 8 * (eps - delta) * s2 * c2, 0.0))
+    return 0.5 * (a + disc), 0.5 * (a - disc)
+
+
+def symbol(o, k, x0):
+    n = o.shape[0]
+    h = o.prob.h
+    ax = np.arange(n) * h
+    X, Y, Z = np.meshgrid(ax, ax, ax, indexing="ij")
+    phase = k[0] * (X - x0[0]) + k[1] * (Y - x0[1]) + k[2] * (Z - x0[2])
+    u = np.cos(phase)
+    z = np.zeros_like(u)
+    i0 = tuple(int(round(c / h)) for c in x0)
+    S = np.zeros((2, 2))
+    Lp, Lr = o.tti_apply_L(u, z)
+    S[0, 0], S[1, 0] = Lp[i0], Lr[i0]
+    Lp, Lr = o.tti_apply_L(z, u)
+    S[0, 1], S[1, 1] = Lp[i0], Lr[i0]
+    return S
+
+
+@pytest.mark.parametrize("theta,phi", [(0.0, 0.0), (0.5, 0.3), (0.9, 2.1), (1.3, -0.7)])
+def test_plane_wave_dispersion(theta, phi):
+    # the model is float32: evaluate the analytic relation at the same values
+    f32 = lambda v: float(np.float32(v))
+    eps, delta, theta, phi = f32(0.25), f32(0.1), f32(theta), f32(phi)
+    n, h = 25, 10.0
+    x0 = (12 * h, 12 * h, 12 * h)
+    nvec = np.array([math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi),
+                     math.cos(theta)])
+    rng = np.random.default_rng(3)
+    kdir = rng.standard_normal(3)
+    kdir /= np.linalg.norm(kdir)
+    vartheta = math.acos(abs(float(kdir @ nvec)))
+    fast, slow = pseudo_acoustic_v2(eps, delta, vartheta)
+    errs = {}
+    for so in (2, 4, 8):
+        o = oracle.Problem(homogeneous_tti(n, h, so, 2.0, eps, delta, theta, phi))
+        e = []
+        for kh in (0.2, 0.1):
+            k = kdir * kh / h
+            S = symbol(o, k, x0)
+            ev = np.sort(np.linalg.eigvals(-S).real)[::-1] / (kh / h) ** 2
+            e.append(max(abs(ev[0] - fast), abs(ev[1] - slow)))
+        errs[so] = e
+        # observed order of accuracy in kh
+        order = math.log(e[0] / e[1], 2) if e[1] > 1e-14 else so
+        assert order > so - 0.3, (so, e)
+    assert errs[8][1] < 1e-8
+
+
+def test_collapse_to_isotropic_acoustic():
+    """eps = delta = 0: for any tilt/azimuth the TTI oracle reproduces an
+    isotropic leapfrog m u_tt = sum_i D_i D_i u (written here with numpy)."""
+    n, h, so, nt = 20, 10.0, 8, 60
+    rng = np.random.default_rng(5)
+    vp = (1.5 + rng.random((n, n, n))).astype(np.float32)
+    th = rng.uniform(0, np.pi, (n, n, n)).astype(np.float32)
+    ph = rng.uniform(-np.pi, np.pi, (n, n, n)).astype(np.float32)
+    zero = np.zeros((n, n, n), np.float32)
+    dt = synth.cfl_dt(h, 2.5)
+    wav = synth.ricker(20.0, dt, nt)[None]
+    src = np.array([[100.0, 90.0, 80.0]], np.float32)        # on grid nodes
+    rec = np.array([[30.0, 50.0, 150.0], [180.0, 20.0, 10.0]], np.float32)
+    traces = []
+    for angles in ((th, ph), (zero, zero)):
+        m = {"vp": vp, "eps": zero, "delta": zero, "theta": angles[0], "phi": angles[1]}
+        p = synth.Problem(synth.TTI, n, n, n, 0, h, so, nt, dt, m, src, wav, rec)
+        traces.append(oracle.Problem(p).forward())
+
+    # independent isotropic leapfrog (no absorbing layer)
+    c = oracle.weights_centred(so)
+    M = so // 2
+
+    def D(u, ax):
+        up = np.pad(u, [(M, M) if a == ax else (0, 0) for a in range(3)])
+        out = np.zeros_like(u)
+        L = u.shape[ax]
+        for k in range(1, M + 1):
+            sp = [slice(None)] * 3
+            sm = [slice(None)] * 3
+            sp[ax] = slice(M + k, M + k + L)
+            sm[ax] = slice(M - k, M - k + L)
+            out += c[k - 1] * (up[tuple(sp)] - up[tuple(sm)])
+        return out / h
+
+    m2 = 1.0 / (vp.astype(np.float64) * 1000.0) ** 2
+    u0 = np.zeros((n, n, n))
+    u1 = np.zeros((n, n, n))
+    tr = np.zeros((2, nt))
+    si = tuple(int(v / h) for v in src[0])
+    ri = [tuple(int(v / h) for v in r) for r in rec]
+    for it in range(nt):
+        for j, r in enumerate(ri):
+            tr[j, it] = u1[r]
+        lap = sum(D(D(u1, a), a) for a in range(3))
+        u2 = 2 * u1 - u0 + dt * dt / m2 * lap
+        u2[si] += dt * dt / m2[si] * wav[0, it]
+        u0, u1 = u1, u2
+    scale = np.max(np.abs(tr))
+    assert scale > 0
+    np.testing.assert_allclose(traces[0], tr, atol=1e-10 * scale)
+    np.testing.assert_allclose(traces[1], tr, atol=1e-10 * scale)
+
+
+def test_greens_function():
+    """Homogeneous medium: u(r,t) ~ h^3 q(t - r/c) / (4 pi r) (Eq. acou with the
+    Kronecker injection s*dt**2/m of the Sec. II-A listing)."""
+    n, h, so = 72, 10.0, 8
+    c = 1500.0
+    f0 = 10.0
+    dt = float(np.float32(0.1 * h / c))
+    r_vec = np.array([120.0, 90.0, 60.0])
+    r = float(np.linalg.norm(r_vec))
+    t0 = 1.0 / f0
+    t_end = r / c + t0 + 1.2 / f0
+    nt = int(t_end / dt) + 1
+    p = homogeneous_tti(n, h, so, c / 1000.0, 0.0, 0.0, 0.3, 0.2, nbl=0, nt=nt, dt=dt)
+    s = np.array([340.0, 330.0, 320.0])
+    # The centred first derivative applied twice has a parasitic mode at the
+    # Nyquist wavenumber (u -> (-1)^i u) that a one-node source excites and
+    # that travels sum_j 2 j c_j (-1)^(j+1) times faster (2.66x at so 8).
+    # A 4x4x4 binomial source ([1,3,3,1]/8 per axis) has a triple zero at
+    # Nyquist; the analytic field is the superposition of its 64 point
+    # sources.
+    bw = np.array([1.0, 3.0, 3.0, 1.0]) / 8.0
+    offs, wts = [], []
+    for a in range(4):
+        for b in range(4):
+            for d in range(4):
+                offs.append([a * h, b * h, d * h])
+                wts.append(bw[a] * bw[b] * bw[d])
+    offs = np.array(offs)
+    p.src = (s[None] + offs).astype(np.float32)
+    rec = s + 1.5 * h + r_vec
+    p.rec = rec[None].astype(np.float32)
+    q0 = synth.ricker(f0, dt, nt)
+    p.wavelet = (np.array(wts)[:, None] * q0[None]).astype(np.float32)
+    tr = oracle.Problem(p).forward()[0]
+    t = np.arange(nt) * dt
+    ana = np.zeros(nt)
+    for o_, w_ in zip(offs, wts):
+        rr = float(np.linalg.norm(rec - s - o_))
+        tau = t - rr / c - t0
+        q = (1 - 2 * (math.pi * f0 * tau) ** 2) * np.exp(-(math.pi * f0 * tau) ** 2)
+        ana += w_ * h ** 3 * q / (4 * math.pi * rr)
+    # Reflections from the grid faces arrive after t_end.  The remaining
+    # misfit (3% at h = 10 m) is the numerical dispersion of the wavelet's
+    # high-frequency tail (kh > 1.5) and shrinks with h, not with the order.
+    err = np.linalg.norm(tr - ana) / np.linalg.norm(ana)
+    assert err < 0.05, err
+
+
+def _small_problem(so=4, nt=40, nbl=4, n=12):
+    p = synth.tti_two_layer(n=n, nbl=nbl, so=so, nt=nt)
+    p.src = np.array([[55.3, 57.1, 31.7], [20.0, 80.4, 60.2]], np.float32)
+    p.wavelet = np.vstack([p.wavelet[0], 0.5 * np.roll(p.wavelet[0], 5)]).astype(np.float32)
+    p.rec = synth.line_receivers(3.1, 9.7, 10, 52.2, 22.9)
+    return p
+
+
+@pytest.mark.parametrize("so", [4, 8])
+def test_dot_product(so):
+    p = _small_problem(so=so)
+    o = oracle.Problem(p)
+    rng = np.random.default_rng(11)
+    q = rng.standard_normal((2, p.nt)).astype(np.float32)
+    d = rng.standard_normal((p.rec.shape[0], p.nt))
+    a = np.sum(o.forward(wavelet=q) * d)
+    b = np.sum(q.astype(np.float64) * o.adjoint(d))
+    assert abs(a - b) <= 1e-12 * abs(a), (a, b)
+
+
+def test_one_step_matrices_transpose():
+    """Brute force on a 6^3 grid: assemble the forward step blocks
+    u^{n+1} = S1 u^n + S2 u^{n-1} and the adjoint step blocks
+    lam^k = T1 lam^{k+1} + T2 lam^{k+2}; lam = A^{-1} mu implies
+    T_j = A^{-1} S_j^T A."""
+    p = synth.tti_two_layer(n=4, nbl=1, so=4, nt=5, h=10.0)
+    p.model["theta"][:] = 0.4
+    p.model["phi"][:] = 1.1
+    p.model["eps"][:] = 0.3
+    p.model["delta"][:] = 0.1
+    o = oracle.Problem(p)
+    N = o.N
+    z = np.zeros(N, np.float32)
+
+    def blocks(adj):
+        S1 = np.zeros((2 * N, 2 * N))
+        S2 = np.zeros((2 * N, 2 * N))
+        for j in range(2 * N):
+            e = np.zeros(2 * N, np.float32)
+            e[j] = 1.0
+            ep, er = e[:N], e[N:]
+            p2, r2 = o.tti_step(z, ep, z, er, adjoint=adj)       # from u^n / lam^{k+1}
+            S1[:, j] = np.concatenate([p2.ravel(), r2.ravel()])
+            p2, r2 = o.tti_step(ep, z, er, z, adjoint=adj)       # from u^{n-1} / lam^{k+2}
+            S2[:, j] = np.concatenate([p2.ravel(), r2.ravel()])
+        return S1, S2
+
+    S1, S2 = blocks(False)
+    T1, T2 = blocks(True)
+    m = o.param(0).ravel()
+    sig = o.param(5).ravel()
+    A = np.tile(m * (1 + 0.5 * sig * p.dt), 2)
+    for S, T in ((S1, T1), (S2, T2)):
+        ref = (S.T * A[None, :]) / A[:, None]
+        np.testing.assert_allclose(T, ref, atol=1e-13 * np.abs(ref).max())
+
+
+def test_taylor_gradient():
+    p = _small_problem(so=4, nt=60)
+    p.vdamp = 2500.0 * math.sqrt(1.4)       # damping held fixed under perturbation
+    keys = ("vp", "eps", "delta", "theta", "phi")
+    dobs = oracle.Problem(p).forward()
+    vp0 = (p.model["vp"].astype(np.float64) * 0.97)
+
+    def J_and(vp):
+        mm = dict(p.model)
+        mm["vp"] = vp.astype(np.float32)
+        o = oracle.Problem(p, model=[mm[k] for k in keys])
+        return 0.5 * np.sum((o.forward() - dobs) ** 2), o, mm
+
+    J0, o0, mm0 = J_and(vp0)
+    vp0 = mm0["vp"].astype(np.float64)
+    g, J = o0.gradient(dobs)
+    assert abs(J - J0) <= 1e-12 * J0
+    m = 1.0 / (vp0 * 1000.0) ** 2
+    dm = synth.perturbation(vp0.shape, 2, 7).astype(np.float64) * m * 0.05
+    lin = float(np.sum(g * dm))
+    e2 = []
+    for hh in (1.0, 0.5, 0.25, 0.125, 0.0625):
+        Jh, _, _ = J_and(1.0 / np.sqrt(m + hh * dm) / 1000.0)
+        e2.append(abs(Jh - J0 - hh * lin))
+    slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
+    assert all(abs(s - 2.0) < 0.1 for s in slopes), slopes
