@@ -1,0 +1,298 @@
+"""Benchmark of the wave propagators on one GB300.
+
+Workload (default): the 3D isotropic elastic velocity-stress system, 256^3
+physical grid at 10 m + 20-cell absorbing layer (296^3 computational
+points), space order 8, 1000 time steps, smooth random model (vp 1.5-4.5
+km/s, vs = vp/1.73, rho 1.0-2.5 g/cc, 200 m correlation length), explosive
+10 Hz Ricker source at the centre, 64 x 64 receivers at the surface.
+One benchmark step = one forward modelling + one adjoint modelling of that
+shot (2 x 1000 propagator time steps).  Metric: grid-point updates per
+second (Gpts/s, computational grid).
+
+Reported beside it: the roofline of the dominant kernel (algorithmic bytes
+per launch / CUDA-event launch time vs the measured HBM copy bandwidth),
+the FP64 CPU oracle on a bounded sample of the same workload, the same
+metric end to end through the C ABI with host buffers, and SM clocks sampled
+during the timed region.
+
+--impl reference times the FP64 CPU oracle instead (bounded sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+HBM_FALLBACK_GBS = 6800.0
+# algorithmic bytes per point update of one fused time step (each state
+# array read and written once, each parameter array read once):
+#   elastic: 9 state reads + 9 writes + 3 parameters (b, lambda, mu) = 84 B
+#   TTI:     4 state reads + 2 writes + 5 parameters                  = 44 B
+ALG_BYTES = {"elastic": 84.0, "tti": 44.0}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu=0):
+        self.gpu = gpu
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def elastic_workload(small=False):
+    if small:
+        return synth.elastic_random(n=64, nbl=20, so=8, nt=200)
+    return synth.elastic_random()      # 256^3 @ 10 m + 20, so 8, 1000 steps
+
+
+def cpu_baseline(prob, budget_s=20.0):
+    """FP64 oracle on the host cores: forward + adjoint time steps on the full
+    computational grid of the workload from a seeded state, as many steps as
+    fit the budget (at least one of each)."""
+    import oracle
+    o = oracle.Problem(prob)
+    N = o.N
+    st = np.random.default_rng(3).standard_normal((9,) + o.shape, dtype=np.float32)
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        o.el_step(st, adjoint=(steps % 2 == 1), nsteps=1)
+        steps += 1
+        if time.perf_counter() - t0 > budget_s or steps >= 64:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": N * steps / dt / 1e9, "unit": "Gpts/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"{steps} elastic time steps (alternating forward/adjoint) of the "
+                      f"{o.shape[0]}x{o.shape[1]}x{o.shape[2]} grid, FP64, OpenMP"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    prob = elastic_workload(args.small)
+    import oracle
+    o = oracle.Problem(prob)
+    st = np.random.default_rng(3).standard_normal((9,) + o.shape, dtype=np.float32)
+    per_step = 2   # bounded sample: one forward + one adjoint time step per bench step
+    for _ in range(args.warmup):
+        o.el_step(st, nsteps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.el_step(st, nsteps=1)
+        o.el_step(st, adjoint=True, nsteps=1)
+    dt = time.perf_counter() - t0
+    v = o.N * per_step * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": "elastic propagator grid-point updates per second",
+            "value": v, "unit": "Gpts/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": prob.name, "grid": list(o.shape), "space_order": prob.so},
+            "cpu_baseline": {"value": v, "unit": "Gpts/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{per_step} time steps per bench step (1 forward + 1 adjoint) "
+                                       "of the full grid, FP64"},
+            "e2e": {"value": v, "unit": "Gpts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2004_10519_gb300 as wp
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    prob = elastic_workload(args.small)
+    # replicas: every rank models its own shot (independent problems)
+    prop = wp.Propagator.from_problem(prob, stream=torch.cuda.current_stream(dev).cuda_stream)
+    N = int(np.prod(prop.grid))
+    nt = prob.nt
+    wav = torch.from_numpy(prob.wavelet).to(dev)
+    src = torch.from_numpy(prob.src).to(dev)
+    rec = torch.from_numpy(prob.rec).to(dev)
+    nrec, nsrc = prob.rec.shape[0], prob.src.shape[0]
+    traces = torch.empty((nrec, nt), dtype=torch.float32, device=dev)
+    resid = torch.from_numpy(np.random.default_rng(1).standard_normal((nrec, nt)).astype(np.float32)).to(dev)
+    qout = torch.empty((nsrc, nt), dtype=torch.float32, device=dev)
+
+    def one_step():
+        prop.forward(wav, src, rec, out=traces)
+        n1 = prop.last_launches()
+        prop.adjoint(resid, src, rec, out=qout)
+        return n1 + prop.last_launches()
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            launches += one_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    upd = N * 2 * nt * args.steps * world
+    value = upd / (ms / 1e3) / 1e9
+
+    # roofline of the dominant kernel: per-launch CUDA events on the library's
+    # stream, forward step (the adjoint step is reported beside it)
+    prop.profile(True)
+    prop.step(50)
+    f_ms, f_n = prop.kernel_stats(wp.K_EL_FWD)
+    prop.step(50, adjoint=True)
+    a_ms, a_n = prop.kernel_stats(wp.K_EL_ADJ)
+    prop.profile(False)
+    hbm, src_peak = peaks()
+    t_launch = f_ms / max(f_n, 1) / 1e3
+    ach = ALG_BYTES["elastic"] * N / t_launch / 1e9
+    roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+            "traffic": None, "kernel": "elastic forward step (velocity + stress passes)",
+            "peak_source": src_peak, "launch_ms": t_launch * 1e3,
+            "alg_bytes_per_launch": ALG_BYTES["elastic"] * N,
+            "adjoint_launch_ms": a_ms / max(a_n, 1)}
+
+    # end to end through the C ABI with pinned host buffers
+    h_wav = torch.from_numpy(prob.wavelet).pin_memory()
+    h_src = torch.from_numpy(prob.src).pin_memory()
+    h_rec = torch.from_numpy(prob.rec).pin_memory()
+    h_res = resid.cpu().pin_memory()
+    h_tr = torch.empty((nrec, nt), dtype=torch.float32).pin_memory()
+    h_q = torch.empty((nsrc, nt), dtype=torch.float32).pin_memory()
+    prop.forward(h_wav, h_src, h_rec, out=h_tr)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        prop.forward(h_wav, h_src, h_rec, out=h_tr)
+        prop.adjoint(h_res, h_src, h_rec, out=h_q)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    h2d = (h_wav.numel() + h_src.numel() + h_rec.numel() + h_res.numel() + h_src.numel() + h_rec.numel()) * 4
+    d2h = (h_tr.numel() + h_q.numel()) * 4
+    e2e = {"value": upd / e2e_s / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        prop.close()
+        cpu = cpu_baseline(prob)
+    if rank == 0:
+        line = {"metric": "elastic propagator grid-point updates per second",
+                "value": value, "unit": "Gpts/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": prob.name, "grid": list(prop.grid), "space_order": prob.so,
+                           "time_steps_per_bench_step": 2 * nt, "shots_per_gpu": 1,
+                           "parallelism": f"replicas{world}",
+                           "l2": "working set 2.2 GB >> L2 (no flush needed)"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

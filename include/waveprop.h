@@ -1,0 +1,164 @@
+/*
+ * waveprop: 3D pseudo-acoustic TTI and isotropic elastic wave propagators,
+ * their exact adjoints and FWI gradients, on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Louboutin et al., "Scaling through abstractions - high-performance
+ * vectorial wave simulations for seismic inversion with Devito" (SC20).
+ *   - forward operator: model + source wavelet -> receiver traces, with the
+ *     source injected (s.inject(u.forward, expr=s*dt**2/m)) and the data
+ *     interpolated (d.interpolate(u)): Sec. II-A, Eq. (acou) and the
+ *     wave-equation listing;
+ *   - TTI system with rotated self-adjoint second derivatives
+ *     G_xbarxbar = D_xbar^T D_xbar: Sec. III-A, Eq. (rot);
+ *   - elastic velocity-stress system on staggered grids with a damping
+ *     factor: Sec. IV, Eq. (elas1) and the elastic listing;
+ *   - adjoints ("propagators along with their adjoints", abstract) and the
+ *     adjoint-state gradient (zero-lag cross-correlation of forward and
+ *     adjoint wavefields), exactness required: Sec. III-A;
+ *   - checkpointing of forward wavefields: Sec. III.
+ *
+ * Conventions (every entry point):
+ *   - Grids are indexed [x][y][z], z fastest, float32.  The PHYSICAL grid has
+ *     nx*ny*nz points at spacing h; the library adds nbl absorbing cells on
+ *     every face (computational grid (nx+2nbl)(ny+2nbl)(nz+2nbl)) and fills
+ *     the layer by edge replication of the model.
+ *   - Coordinates are metres, origin at the first physical point, z = depth;
+ *     every source/receiver must lie inside [0,(n-1)h] on each axis.
+ *   - Buffers may be host or device pointers (detected per pointer with
+ *     cudaPointerGetAttributes).  The caller owns every buffer passed in or
+ *     out; the library owns the handle and all device memory it allocates,
+ *     and frees it in prop_destroy.
+ *   - All work is enqueued on the stream given at prop_create (NULL = the
+ *     legacy default stream); every call returns after that work completed.
+ *   - Negative return = error.  After PROP_EINVAL the handle stays usable;
+ *     after PROP_ECUDA or PROP_ETIMEOUT every later call returns PROP_ESTATE
+ *     until prop_destroy.  prop_last_error gives the message.
+ *   - One handle per host thread at a time.
+ */
+#ifndef WAVEPROP_H
+#define WAVEPROP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct prop_s prop_t;
+
+enum {
+    PROP_OK = 0,
+    PROP_EINVAL = -1,     /* bad argument (message says which)             */
+    PROP_ENOMEM = -2,     /* device allocation failed (nothing leaked)     */
+    PROP_ECUDA = -3,      /* CUDA runtime error; handle unusable           */
+    PROP_EUNSTABLE = -4,  /* dt violates the CFL bound, or NaN/Inf seen    */
+    PROP_ETIMEOUT = -5,   /* a bounded device-side wait gave up            */
+    PROP_ESTATE = -6      /* handle unusable after an earlier error,
+                             or a call that needs a saved forward run      */
+};
+
+enum { PROP_TTI = 1, PROP_ELASTIC = 2 };
+
+/* Storage of forward wavefields for the gradient (Sec. III: full storage in
+ * memory, or checkpointing).  CKPT_* keep the full state every
+ * ckpt_interval steps and recompute the segment in FP32 during the adjoint
+ * sweep; BF16/FP16 store each checkpoint field with one FP32 scale. */
+enum { SNAP_FULL_FP32 = 0, SNAP_CKPT_FP32 = 1, SNAP_CKPT_BF16 = 2, SNAP_CKPT_FP16 = 3 };
+
+typedef struct {
+    int kind;            /* PROP_TTI or PROP_ELASTIC                          */
+    int nx, ny, nz;      /* physical grid points (>= 1)                       */
+    int nbl;             /* absorbing cells added on every face (>= 0)        */
+    float h;             /* grid spacing [m] (> 0)                            */
+    int space_order;     /* 4, 8, 12 or 16                                    */
+    int nt;              /* time samples per trace (>= 2)                     */
+    float dt;            /* time step [s]; <= 0 selects dt = 0.4 h / vmax     */
+    float vdamp;         /* TTI damping reference velocity [m/s]; <= 0: the
+                            model's max vp sqrt(1+2 eps)                      */
+    int snap_mode;       /* SNAP_* for prop_gradient / prop_backward          */
+    int ckpt_interval;   /* steps between checkpoints; 0 = ceil(sqrt(nt))     */
+    int check_nan;       /* nonzero: stencil kernels flag NaN/Inf, reported
+                            as PROP_EUNSTABLE at the end of the call          */
+} prop_desc;
+
+/* Create a propagator.  model points to the PHYSICAL-grid float32 arrays
+ *   TTI:     vp [km/s], epsilon, delta, theta (tilt) [rad], phi (azimuth) [rad]
+ *   ELASTIC: vp [km/s], vs [km/s], rho [g/cc]
+ * (Sec. III-A: 4 Thomsen/angle parameters + velocity; Sec. IV: Lame
+ * parameters and density, lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2).
+ * The arrays are copied; they may be freed after the call.
+ * Errors: PROP_EINVAL for bad sizes, space order, non-positive velocity or
+ * density, eps < delta (TTI stability needs eps >= delta), lambda < 0;
+ * PROP_EUNSTABLE if dt exceeds the scheme's CFL bound.
+ * cuda_stream: a cudaStream_t (NULL = default stream). */
+int prop_create(const prop_desc *desc, const float *const *model, void *cuda_stream,
+                prop_t **out);
+
+/* Forward modelling (Sec. II-A listing order per step n = 0..nt-1):
+ * record d^n from u^n, advance, inject q^n.
+ *   wavelet  [nsrc][nt]  source time functions q
+ *   src_xyz  [nsrc][3]   source positions
+ *   rec_xyz  [nrec][3]   receiver positions
+ *   traces   [nrec][nt]  output: TTI records p; ELASTIC records
+ *                        txx + tyy + tzz (trace of stress, Sec. IV-B).
+ * TTI injects q into both p and r; ELASTIC injects dt q into txx, tyy, tzz
+ * (explosive source).  nsrc, nrec >= 1. */
+int prop_forward(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,
+                 const float *rec_xyz, int nrec, float *traces);
+
+/* Adjoint modelling: the exact transpose of prop_forward (as a linear map
+ * from wavelets to traces).  traces_in [nrec][nt] -> src_out [nsrc][nt]. */
+int prop_adjoint(prop_t *p, const float *traces_in, const float *rec_xyz, int nrec,
+                 const float *src_xyz, int nsrc, float *src_out);
+
+/* FWI gradient of J = 1/2 ||F(model) q - d_obs||^2 by the adjoint-state
+ * method (zero-lag cross-correlation of forward and adjoint wavefields).
+ *   d_obs  [nrec][nt]
+ *   grad   TTI: [nx][ny][nz] dJ/dm, m = 1/vp^2 [s^2/m^2] on the physical grid
+ *          (layer contributions folded back through the edge replication);
+ *          ELASTIC: [3][nx][ny][nz] dJ/d(lambda [Pa], mu [Pa], b = 1/rho [m^3/kg])
+ *   misfit J (may be NULL).
+ * Forward wavefields are kept according to desc.snap_mode. */
+int prop_gradient(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,
+                  const float *rec_xyz, int nrec, const float *d_obs, float *grad,
+                  double *misfit);
+
+/* Two-phase form of prop_gradient for automatic differentiation:
+ * prop_forward_saved runs prop_forward and keeps the forward wavefields
+ * (snap_mode) in the handle; prop_backward then takes the trace gradient
+ * resid [nrec][nt] (dJ/dtraces) and returns grad (as prop_gradient, may be
+ * NULL) and src_grad [nsrc][nt] = dJ/dwavelet (may be NULL).  prop_backward
+ * without a saved forward run returns PROP_ESTATE; it releases the saved
+ * wavefields. */
+int prop_forward_saved(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,
+                       const float *rec_xyz, int nrec, float *traces);
+int prop_backward(prop_t *p, const float *resid, float *grad, float *src_grad);
+
+/* Wavefield state access (computational grid, float32 [NX][NY][NZ] each):
+ *   TTI:     fields[0..3] = p^n, r^n, p^{n-1}, r^{n-1}
+ *   ELASTIC: fields[0..8] = vx vy vz txx tyy tzz txy txz tyz
+ * prop_step advances nsteps steps without sources or receivers (adjoint != 0:
+ * transposed step, state holds the adjoint fields in the same order). */
+int prop_grid_dims(const prop_t *p, int *dims /* [3] = NX, NY, NZ */, int *nfields);
+int prop_set_state(prop_t *p, const float *const *fields);
+int prop_get_state(prop_t *p, float *const *fields);
+int prop_step(prop_t *p, int nsteps, int adjoint);
+
+/* Time step actually used (after the CFL rule), in seconds. */
+float prop_dt(const prop_t *p);
+
+/* Device time of the stencil kernels of the most recent call, summed over
+ * launches [ms], and the number of those launches (CUDA events on the
+ * handle's stream).  Used for roofline accounting. */
+int prop_kernel_time(const prop_t *p, double *ms, long long *launches);
+
+void prop_destroy(prop_t *p);                 /* NULL-safe */
+
+/* Message of the last error on this handle; with p == NULL, the last
+ * error of the calling thread (e.g. a failed prop_create). */
+const char *prop_last_error(const prop_t *p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WAVEPROP_H */

@@ -1,0 +1,279 @@
+"""waveprop: TTI and elastic wave propagators on one GB300 (sm_103a).
+
+Thin ctypes binding of ``libwaveprop.so`` (C ABI in ``include/waveprop.h``).
+Every step of the propagators runs in the library's CUDA kernels; this module
+only marshals arguments.  PyTorch is used for device memory and streams when
+tensors are passed.  If the library is missing the import of ``lib()`` fails
+loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libwaveprop.so")
+
+PROP_OK, PROP_EINVAL, PROP_ENOMEM, PROP_ECUDA, PROP_EUNSTABLE, PROP_ETIMEOUT, PROP_ESTATE = \
+    0, -1, -2, -3, -4, -5, -6
+PROP_TTI, PROP_ELASTIC = 1, 2
+SNAP_FULL_FP32, SNAP_CKPT_FP32, SNAP_CKPT_BF16, SNAP_CKPT_FP16 = 0, 1, 2, 3
+ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA",
+             -4: "PROP_EUNSTABLE", -5: "PROP_ETIMEOUT", -6: "PROP_ESTATE"}
+
+# exported symbols declared in include/waveprop.h
+ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
+               "prop_forward_saved", "prop_backward", "prop_grid_dims", "prop_set_state",
+               "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
+               "prop_last_error")
+
+
+class PropDesc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("nbl", C.c_int), ("h", C.c_float), ("space_order", C.c_int), ("nt", C.c_int),
+                ("dt", C.c_float), ("vdamp", C.c_float), ("snap_mode", C.c_int),
+                ("ckpt_interval", C.c_int), ("check_nan", C.c_int)]
+
+
+class PropError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERR_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libwaveprop.so (built by ``__graft_entry__.build()``)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"waveprop CUDA library not built ({LIB_PATH} missing); "
+                               "run __graft_entry__.build() -- there is no CPU fallback")
+        L = C.CDLL(LIB_PATH)
+        vp = C.c_void_p
+        fpp = C.POINTER(C.c_void_p)
+        L.prop_create.argtypes = [C.POINTER(PropDesc), fpp, vp, C.POINTER(vp)]
+        L.prop_forward.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp]
+        L.prop_forward_saved.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp]
+        L.prop_adjoint.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp]
+        L.prop_gradient.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, C.POINTER(C.c_double)]
+        L.prop_backward.argtypes = [vp, vp, vp, vp]
+        L.prop_grid_dims.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.prop_set_state.argtypes = [vp, fpp]
+        L.prop_get_state.argtypes = [vp, fpp]
+        L.prop_step.argtypes = [vp, C.c_int, C.c_int]
+        L.prop_dt.restype = C.c_float
+        L.prop_dt.argtypes = [vp]
+        L.prop_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.prop_destroy.argtypes = [vp]
+        L.prop_last_error.restype = C.c_char_p
+        L.prop_last_error.argtypes = [vp]
+        L.prop_profile.argtypes = [vp, C.c_int]
+        L.prop_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.prop_last_launches.restype = C.c_longlong
+        L.prop_last_launches.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+class _Arg:
+    """Pointer to a caller buffer: numpy (host) or torch (host/device), float32
+    contiguous.  Keeps the converted object alive."""
+
+    def __init__(self, x, n=None, writable=False):
+        if _is_torch(x):
+            import torch
+            if x.dtype != torch.float32 or not x.is_contiguous():
+                if writable:
+                    raise ValueError("output tensor must be contiguous float32")
+                x = x.contiguous().to(torch.float32)
+            self.obj = x
+            self.ptr = C.c_void_p(x.data_ptr())
+            size = x.numel()
+        else:
+            a = np.asarray(x)
+            if a.dtype != np.float32 or not a.flags.c_contiguous:
+                if writable:
+                    raise ValueError("output array must be C-contiguous float32")
+                a = np.ascontiguousarray(a, dtype=np.float32)
+            self.obj = a
+            self.ptr = C.c_void_p(a.ctypes.data)
+            size = a.size
+        if n is not None and size < n:
+            raise ValueError(f"buffer has {size} elements, need {n}")
+
+
+def _npts(a):
+    n = a.obj.numel() if _is_torch(a.obj) else a.obj.size
+    if n % 3:
+        raise ValueError("coordinates must be [n][3]")
+    return n // 3
+
+
+def _stream_of(*xs):
+    for x in xs:
+        if _is_torch(x) and x.is_cuda:
+            import torch
+            return C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)
+    return C.c_void_p(0)
+
+
+class Propagator:
+    """Handle on one propagator (``prop_t``).
+
+    kind: PROP_TTI or PROP_ELASTIC; model: list of physical-grid float32
+    arrays (TTI: vp, eps, delta, theta, phi; elastic: vp, vs, rho) as numpy
+    arrays or torch tensors (host or device)."""
+
+    def __init__(self, kind, shape, nbl, h, space_order, nt, model, dt=0.0, vdamp=0.0,
+                 snap_mode=SNAP_FULL_FP32, ckpt_interval=0, check_nan=0, stream=None):
+        L = lib()
+        nx, ny, nz = shape
+        self.desc = PropDesc(kind, nx, ny, nz, nbl, float(h), space_order, nt, float(dt),
+                             float(vdamp), snap_mode, ckpt_interval, check_nan)
+        args = [_Arg(m, nx * ny * nz) for m in model]
+        arr = (C.c_void_p * len(args))(*[a.ptr for a in args])
+        if stream is None:
+            stream = _stream_of(*model)
+        elif not isinstance(stream, C.c_void_p):
+            stream = C.c_void_p(int(stream))
+        self.stream = stream
+        h_ = C.c_void_p()
+        rc = L.prop_create(C.byref(self.desc), arr, stream, C.byref(h_))
+        if rc:
+            raise PropError(rc, L.prop_last_error(None).decode())
+        self.h = h_
+        self.kind, self.nt = kind, nt
+        self.shape = (nx, ny, nz)
+        d = (C.c_int * 3)()
+        nf = C.c_int()
+        L.prop_grid_dims(self.h, d, C.byref(nf))
+        self.grid = (d[0], d[1], d[2])
+        self.nfields = nf.value
+
+    @classmethod
+    def from_problem(cls, prob, model=None, **kw):
+        keys = ("vp", "eps", "delta", "theta", "phi") if prob.kind == PROP_TTI else ("vp", "vs", "rho")
+        ml = model if model is not None else [prob.model[k] for k in keys]
+        kw.setdefault("dt", prob.dt)
+        kw.setdefault("vdamp", getattr(prob, "vdamp", 0.0) or 0.0)
+        return cls(prob.kind, (prob.nx, prob.ny, prob.nz), prob.nbl, prob.h, prob.so, prob.nt, ml, **kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().prop_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc:
+            raise PropError(rc, lib().prop_last_error(self.h).decode())
+
+    @property
+    def dt(self):
+        return lib().prop_dt(self.h)
+
+    def _out(self, like, shape):
+        if _is_torch(like):
+            import torch
+            return torch.empty(shape, dtype=torch.float32, device=like.device)
+        return np.empty(shape, np.float32)
+
+    def forward(self, wavelet, src, rec, out=None, save=False):
+        src_a, rec_a = _Arg(src), _Arg(rec)
+        nsrc, nrec = _npts(src_a), _npts(rec_a)
+        w = _Arg(wavelet, nsrc * self.nt)
+        if out is None:
+            out = self._out(wavelet, (nrec, self.nt))
+        o = _Arg(out, nrec * self.nt, writable=True)
+        f = lib().prop_forward_saved if save else lib().prop_forward
+        self._check(f(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, o.ptr))
+        return out
+
+    def adjoint(self, traces, src, rec, out=None):
+        src_a, rec_a = _Arg(src), _Arg(rec)
+        nsrc, nrec = _npts(src_a), _npts(rec_a)
+        t = _Arg(traces, nrec * self.nt)
+        if out is None:
+            out = self._out(traces, (nsrc, self.nt))
+        o = _Arg(out, nsrc * self.nt, writable=True)
+        self._check(lib().prop_adjoint(self.h, t.ptr, rec_a.ptr, nrec, src_a.ptr, nsrc, o.ptr))
+        return out
+
+    def _gshape(self):
+        nx, ny, nz = self.shape
+        return (nx, ny, nz) if self.kind == PROP_TTI else (3, nx, ny, nz)
+
+    def gradient(self, wavelet, src, rec, d_obs, out=None):
+        src_a, rec_a = _Arg(src), _Arg(rec)
+        nsrc, nrec = _npts(src_a), _npts(rec_a)
+        w = _Arg(wavelet, nsrc * self.nt)
+        d = _Arg(d_obs, nrec * self.nt)
+        if out is None:
+            out = self._out(d_obs, self._gshape())
+        o = _Arg(out, int(np.prod(self._gshape())), writable=True)
+        J = C.c_double()
+        self._check(lib().prop_gradient(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, d.ptr,
+                                        o.ptr, C.byref(J)))
+        return out, J.value
+
+    def backward(self, resid, grad_out=True, src_grad_out=True, nsrc=None):
+        r = _Arg(resid)
+        g = self._out(resid, self._gshape()) if grad_out is True else grad_out
+        sg = None
+        if src_grad_out is True:
+            sg = self._out(resid, (nsrc, self.nt))
+        elif src_grad_out is not None and src_grad_out is not False:
+            sg = src_grad_out
+        ga = _Arg(g, writable=True) if g is not None and g is not False else None
+        sa = _Arg(sg, writable=True) if sg is not None else None
+        self._check(lib().prop_backward(self.h, r.ptr, ga.ptr if ga else None,
+                                        sa.ptr if sa else None))
+        return (g if ga else None), (sg if sa else None)
+
+    # ---- state -----------------------------------------------------------
+    def set_state(self, fields):
+        args = [_Arg(f, int(np.prod(self.grid))) for f in fields]
+        arr = (C.c_void_p * len(args))(*[a.ptr for a in args])
+        self._check(lib().prop_set_state(self.h, arr))
+
+    def get_state(self, like=None):
+        outs = [self._out(like if like is not None else np.zeros(1), self.grid)
+                for _ in range(self.nfields)]
+        args = [_Arg(o, writable=True) for o in outs]
+        arr = (C.c_void_p * len(args))(*[a.ptr for a in args])
+        self._check(lib().prop_get_state(self.h, arr))
+        return outs
+
+    def step(self, nsteps=1, adjoint=False):
+        self._check(lib().prop_step(self.h, nsteps, int(adjoint)))
+
+    # ---- measurement -------------------------------------------------------
+    def profile(self, on=True):
+        self._check(lib().prop_profile(self.h, int(on)))
+
+    def kernel_stats(self, kid):
+        ms = C.c_double()
+        n = C.c_longlong()
+        self._check(lib().prop_kernel_stats(self.h, kid, C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def last_launches(self):
+        return lib().prop_last_launches(self.h)
+
+
+# kernel ids of Propagator.kernel_stats
+K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD = 0, 1, 2, 3, 4

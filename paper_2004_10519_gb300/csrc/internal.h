@@ -1,0 +1,140 @@
+// Internal declarations of the waveprop CUDA library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/waveprop.h"
+
+#define WP_MAXM 8   // space order up to 16
+
+// Computational grid as seen by the kernels.  Index (x,y,z) -> (x*NY + y)*NZ + z.
+struct GridDev {
+    int NX, NY, NZ;          // computational grid
+    int nbl, px, py, pz;     // absorbing width, physical grid
+    long long N;             // NX*NY*NZ
+    float h, ih, dt;         // spacing, 1/h, time step
+    float sig0;              // TTI damping: sigma(d) = sig0 * (d/L)^2 per axis [1/s]
+    float cer;               // elastic Cerjan coefficient per cell (0.015)
+};
+
+// Finite-difference weights (FP32, from FP64 host solves).
+struct FDW {
+    float c[WP_MAXM];        // centred   c_1..c_M
+    float b[WP_MAXM];        // staggered b_1..b_M
+};
+
+// Sparse-point tables (device).  Record: nrec x 8 (index, weight) pairs.
+// Inject: unique grid cells with CSR lists of (trace, weight).
+struct SparseDev {
+    int n = 0;               // points
+    long long *rec_idx = nullptr;
+    float *rec_w = nullptr;  // [n*8]
+    int ncell = 0;
+    long long *cell = nullptr;
+    int *cell_ptr = nullptr; // [ncell+1]
+    int *ent_trace = nullptr;
+    float *ent_w = nullptr;
+};
+
+struct prop_s {
+    prop_desc d{};
+    GridDev g{};
+    FDW w{};
+    int M = 0;
+    cudaStream_t stream = nullptr;
+    bool broken = false;
+    std::string err;
+    float vmax = 0.f;        // max model velocity used for the CFL rule
+    // model (computational grid)
+    float *m = nullptr, *eps = nullptr, *del = nullptr, *th = nullptr, *ph = nullptr;   // TTI
+    float *bu = nullptr, *lam = nullptr, *mu = nullptr;                                 // elastic
+    // state: TTI 4 fields (p_cur, r_cur, p_prev, r_prev); elastic 9 fields
+    float *st[9] = {};
+    // scratch: TTI 6 intermediates (ex ey ez fx fy fz) + 2 (zeta p, r);
+    // elastic adjoint: 6 (stress-like) + 3 (weighted velocity) + 6 gradient
+    // products (edges xy xz yz, faces x y z)
+    float *tmp[16] = {};
+    int *flag = nullptr;     // device: bit0 NaN/Inf seen
+    // saved forward run for prop_backward
+    bool saved = false;
+    int saved_nsrc = 0, saved_nrec = 0;
+    std::vector<float> saved_src, saved_rec, saved_wav;   // host copies of geometry/wavelet
+    // snapshot storage
+    float *snap = nullptr;   size_t snap_bytes = 0;       // full FP32 store or FP32 checkpoints
+    uint16_t *snap16 = nullptr; size_t snap16_bytes = 0;  // BF16/FP16 checkpoints
+    float *snap_scale = nullptr;                          // per checkpoint field scales
+    float *seg = nullptr;   size_t seg_bytes = 0;         // recompute segment buffer
+    // timing of stencil kernels in the last call
+    double kern_ms = 0.0;
+    long long kern_launches = 0;
+    bool prof = false;                                    // per-launch event timing on
+    std::vector<cudaEvent_t> prof_ev;                     // pool (pairs)
+    std::vector<int> prof_id;                             // id of each recorded pair
+    int prof_used = 0;
+    double prof_ms[8] = {};
+    long long prof_n[8] = {};
+    // adjoint state (separate from the forward state during gradients)
+    float *ast[9] = {};
+};
+
+// ---------------------------------------------------------------------------
+// kernels (launchers), one translation unit per family
+// ---------------------------------------------------------------------------
+// TTI step on state S = (p_cur, r_cur, p_prev, r_prev): the new level is
+// written over (p_prev, r_prev).  adjoint: transposed step on the adjoint
+// state (lam^{k+1}, lam^{k+2}); with grad != NULL also the imaging term using
+// the forward wavefield (img_p, img_r) at the new level.
+int tti_launch_step(prop_s *P, float *const *S, bool adjoint, const float *img_p,
+                    const float *img_r, float *grad);
+// elastic step in place on S (9 fields); adjoint: transposed step
+int el_launch_step(prop_s *P, float *const *S, bool adjoint);
+
+// sparse ops (sparse.cu)
+int sp_build(prop_s *P, const float *xyz_host, int n, const int *trace_of_point, SparseDev *S);
+void sp_free(SparseDev *S);
+// record: out[t*n + i] = scale * sum_c w * (f0 + f1 + f2)[idx]   (f1, f2 may be NULL)
+void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, const float *f2,
+               float scale, float *out_col);
+// inject: f[cell] += coef(cell) * sum_j w_j traces[trace_j*nt + t] into up to 3 fields;
+// mode 0: coef = scale; mode 1: coef = scale / A (TTI, A = m(1+sig dt/2));
+// grad_u != NULL: grad[cell] -= u[cell] * scale*sum / m  (TTI imaging of the
+// residual injection)
+void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
+               int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad);
+void sp_transpose(prop_s *P, const float *in_tn, float *out_nt, int n, int nt);
+
+// misc kernels
+void k_fill(prop_s *P, float *a, long long n, float v);
+void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode);
+void k_fold(prop_s *P, const float *comp, float *phys);
+void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long n);
+double k_sumsq_host(prop_s *P, const float *a, long long n);
+void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr);
+// snapshot codec
+void k_snap_encode(prop_s *P, const float *in, long long n, uint16_t *out, float *scale_dev,
+                   int bf16, float *scratch);
+void k_snap_decode(prop_s *P, const uint16_t *in, long long n, const float *scale_dev,
+                   int bf16, float *out);
+// elastic transposed step fused with the gradient of forward step k:
+// xk = X^k, xk1 = X^{k+1} (9 fields each), g = (g_lambda, g_mu, g_b) accumulated
+int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1,
+                       float *const *g);
+
+// optional per-kernel timing (CUDA events on the handle's stream); ids:
+// 0 TTI forward step, 1 TTI adjoint step, 2 elastic forward step,
+// 3 elastic adjoint step, 4 elastic adjoint+gradient step
+void prof_begin(prop_s *P, int id);
+void prof_end(prop_s *P, int id);
+void k_lame(prop_s *P);
+
+// error helpers
+int wp_fail(prop_s *P, int code, const std::string &msg);
+int wp_cuda(prop_s *P, cudaError_t e, const char *what);
+#define WP_CK(P, call)                                          \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return wp_cuda((P), _e, #call);  \
+    } while (0)

@@ -1,0 +1,949 @@
+// Host runtime and C ABI of waveprop (declared in include/waveprop.h).
+//
+// Time loops follow the order of the Sec. II-A listing: per step n record
+// d^n from u^n, advance, inject q^n into the new level.  Adjoint loops run
+// the transposed steps backwards.  Gradients use the adjoint-state method
+// (Sec. III) with forward wavefields either kept in full or recomputed from
+// checkpoints (FP32, or BF16/FP16 with one scale per field).
+#include "internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+
+static thread_local std::string tl_err;
+
+int wp_fail(prop_s *P, int code, const std::string &msg)
+{
+    tl_err = msg;
+    if (P) {
+        P->err = msg;
+        if (code == PROP_ECUDA || code == PROP_ETIMEOUT) P->broken = true;
+    }
+    return code;
+}
+
+int wp_cuda(prop_s *P, cudaError_t e, const char *what)
+{
+    std::string m = std::string("CUDA error '") + cudaGetErrorString(e) + "' in " + what;
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return wp_fail(P, PROP_ENOMEM, m);
+    }
+    return wp_fail(P, PROP_ECUDA, m);
+}
+
+// All device allocations of the library go through here.  WAVEPROP_FAULT=alloc
+// makes every allocation fail (host-side fault injection for tests).
+static int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what)
+{
+    *p = nullptr;
+    const char *f = getenv("WAVEPROP_FAULT");
+    if (f && !strcmp(f, "alloc"))
+        return wp_fail(P, PROP_ENOMEM, std::string("injected allocation failure: ") + what);
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        char buf[160];
+        snprintf(buf, sizeof buf, "cannot allocate %.3f GB for %s", bytes / 1e9, what);
+        return wp_fail(P, PROP_ENOMEM, buf);
+    }
+    return PROP_OK;
+}
+#define WP_MALLOC(P, ptr, bytes, what)                                            \
+    do {                                                                          \
+        int _r = wp_malloc((P), (void **)&(ptr), (bytes), (what));                \
+        if (_r) return _r;                                                        \
+    } while (0)
+#define WP_TRY(expr)                 \
+    do {                             \
+        int _r = (expr);             \
+        if (_r) return _r;           \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// FD weights: solve the moment conditions in double precision
+//   centred:   sum_k c_k 2 k^(2j+1)       = [j == 0],  j = 0..M-1
+//   staggered: sum_k b_k 2 (k-1/2)^(2j+1) = [j == 0]
+// ---------------------------------------------------------------------------
+static bool solve_dense(int n, std::vector<double> &A, std::vector<double> &b)
+{
+    for (int c = 0; c < n; c++) {
+        int piv = c;
+        for (int r = c + 1; r < n; r++)
+            if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+        if (A[piv * n + c] == 0.0) return false;
+        if (piv != c) {
+            for (int k = 0; k < n; k++) std::swap(A[c * n + k], A[piv * n + k]);
+            std::swap(b[c], b[piv]);
+        }
+        for (int r = c + 1; r < n; r++) {
+            double f = A[r * n + c] / A[c * n + c];
+            for (int k = c; k < n; k++) A[r * n + k] -= f * A[c * n + k];
+            b[r] -= f * b[c];
+        }
+    }
+    for (int r = n - 1; r >= 0; r--) {
+        double s = b[r];
+        for (int k = r + 1; k < n; k++) s -= A[r * n + k] * b[k];
+        b[r] = s / A[r * n + r];
+    }
+    return true;
+}
+
+static bool fd_weights(int M, float *c, float *bst)
+{
+    for (int stag = 0; stag < 2; stag++) {
+        std::vector<double> A(M * M), b(M, 0.0);
+        for (int j = 0; j < M; j++)
+            for (int k = 1; k <= M; k++) {
+                double off = stag ? k - 0.5 : (double)k;
+                A[j * M + (k - 1)] = 2.0 * pow(off, 2 * j + 1);
+            }
+        b[0] = 1.0;
+        if (!solve_dense(M, A, b)) return false;
+        for (int k = 0; k < M; k++) (stag ? bst : c)[k] = (float)b[k];
+    }
+    for (int k = M; k < WP_MAXM; k++) c[k] = bst[k] = 0.f;
+    return true;
+}
+
+// max over kappa of |sum_k 2 w_k sin(s_k kappa)| (s_k = k or k - 1/2)
+static double symbol_max(const float *w, int M, bool stag)
+{
+    double mx = 0.0;
+    for (int i = 0; i <= 4096; i++) {
+        double kap = M_PI * i / 4096.0, s = 0.0;
+        for (int k = 1; k <= M; k++) s += 2.0 * w[k - 1] * sin((stag ? k - 0.5 : (double)k) * kap);
+        mx = std::max(mx, fabs(s));
+    }
+    return mx;
+}
+
+// ---------------------------------------------------------------------------
+// pointers: host or device
+// ---------------------------------------------------------------------------
+static bool is_dev(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+struct DevBuf {   // RAII device buffer owned by one call
+    void *p = nullptr;
+    ~DevBuf() { if (p) cudaFree(p); }
+};
+
+// device view of a caller buffer of n floats (copied in if host)
+static int dev_in(prop_s *P, const float *src, size_t n, DevBuf &tmp, const float **out)
+{
+    if (is_dev(src)) {
+        *out = src;
+        return PROP_OK;
+    }
+    WP_TRY(wp_malloc(P, &tmp.p, n * sizeof(float), "input staging"));
+    WP_CK(P, cudaMemcpyAsync(tmp.p, src, n * sizeof(float), cudaMemcpyHostToDevice, P->stream));
+    *out = (const float *)tmp.p;
+    return PROP_OK;
+}
+static int copy_out(prop_s *P, float *dst, const float *src_dev, size_t n)
+{
+    WP_CK(P, cudaMemcpyAsync(dst, src_dev, n * sizeof(float), cudaMemcpyDefault, P->stream));
+    return PROP_OK;
+}
+
+static int nfields(const prop_s *P) { return P->d.kind == PROP_TTI ? 4 : 9; }
+
+// ---------------------------------------------------------------------------
+// profiling
+// ---------------------------------------------------------------------------
+void prof_begin(prop_s *P, int id)
+{
+    if (!P->prof) return;
+    if ((size_t)P->prof_used * 2 + 2 > P->prof_ev.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        P->prof_ev.push_back(a);
+        P->prof_ev.push_back(b);
+        P->prof_id.push_back(id);
+    }
+    P->prof_id[P->prof_used] = id;
+    cudaEventRecord(P->prof_ev[2 * P->prof_used], P->stream);
+}
+void prof_end(prop_s *P, int id)
+{
+    (void)id;
+    if (!P->prof) return;
+    cudaEventRecord(P->prof_ev[2 * P->prof_used + 1], P->stream);
+    P->prof_used++;
+}
+static void prof_collect(prop_s *P)
+{
+    if (!P->prof || !P->prof_used) return;
+    cudaStreamSynchronize(P->stream);
+    for (int i = 0; i < P->prof_used; i++) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, P->prof_ev[2 * i], P->prof_ev[2 * i + 1]) == cudaSuccess) {
+            P->prof_ms[P->prof_id[i]] += ms;
+            P->prof_n[P->prof_id[i]] += 1;
+        }
+    }
+    P->prof_used = 0;
+}
+
+// collect events every so often so the pool stays small
+static void prof_maybe_collect(prop_s *P)
+{
+    if (P->prof && P->prof_used >= 256) prof_collect(P);
+}
+
+// ---------------------------------------------------------------------------
+// creation
+// ---------------------------------------------------------------------------
+static int ensure_tmp(prop_s *P, int count)
+{
+    for (int i = 0; i < count; i++)
+        if (!P->tmp[i]) WP_MALLOC(P, P->tmp[i], sizeof(float) * P->g.N, "scratch fields");
+    return PROP_OK;
+}
+static int ensure_ast(prop_s *P)
+{
+    for (int i = 0; i < nfields(P); i++)
+        if (!P->ast[i]) WP_MALLOC(P, P->ast[i], sizeof(float) * P->g.N, "adjoint state");
+    return PROP_OK;
+}
+
+static void free_snaps(prop_s *P)
+{
+    cudaFree(P->snap); P->snap = nullptr; P->snap_bytes = 0;
+    cudaFree(P->snap16); P->snap16 = nullptr; P->snap16_bytes = 0;
+    cudaFree(P->snap_scale); P->snap_scale = nullptr;
+    cudaFree(P->seg); P->seg = nullptr; P->seg_bytes = 0;
+    P->saved = false;
+}
+
+static void free_all(prop_s *P)
+{
+    float *arrs[] = {P->m, P->eps, P->del, P->th, P->ph, P->bu, P->lam, P->mu};
+    for (float *a : arrs) cudaFree(a);
+    for (auto &a : P->st) cudaFree(a);
+    for (auto &a : P->ast) cudaFree(a);
+    for (auto &a : P->tmp) cudaFree(a);
+    cudaFree(P->flag);
+    free_snaps(P);
+    for (auto e : P->prof_ev) cudaEventDestroy(e);
+}
+
+static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
+{
+    P->d = *d;
+    const int so = d->space_order;
+    if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC) return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI or PROP_ELASTIC");
+    if (d->nx < 1 || d->ny < 1 || d->nz < 1) return wp_fail(P, PROP_EINVAL, "grid sizes must be >= 1");
+    if (d->nbl < 0) return wp_fail(P, PROP_EINVAL, "nbl must be >= 0");
+    if (!(d->h > 0.f) || !std::isfinite(d->h)) return wp_fail(P, PROP_EINVAL, "h must be > 0");
+    if (so != 4 && so != 8 && so != 12 && so != 16) return wp_fail(P, PROP_EINVAL, "space_order must be 4, 8, 12 or 16");
+    if (d->nt < 2) return wp_fail(P, PROP_EINVAL, "nt must be >= 2");
+    if (d->snap_mode < 0 || d->snap_mode > 3) return wp_fail(P, PROP_EINVAL, "snap_mode out of range");
+    if (d->ckpt_interval < 0) return wp_fail(P, PROP_EINVAL, "ckpt_interval must be >= 0");
+    if (!model) return wp_fail(P, PROP_EINVAL, "model is NULL");
+    const int nf = d->kind == PROP_TTI ? 5 : 3;
+    for (int i = 0; i < nf; i++)
+        if (!model[i]) return wp_fail(P, PROP_EINVAL, "model array is NULL");
+    P->M = so / 2;
+    GridDev &g = P->g;
+    g.nbl = d->nbl;
+    g.px = d->nx; g.py = d->ny; g.pz = d->nz;
+    g.NX = d->nx + 2 * d->nbl; g.NY = d->ny + 2 * d->nbl; g.NZ = d->nz + 2 * d->nbl;
+    g.N = (long long)g.NX * g.NY * g.NZ;
+    g.h = d->h; g.ih = 1.f / d->h;
+    if (!fd_weights(P->M, P->w.c, P->w.b)) return wp_fail(P, PROP_EINVAL, "FD weights");
+
+    // model on the host for validation
+    const size_t np = (size_t)d->nx * d->ny * d->nz;
+    std::vector<std::vector<float>> hm(nf);
+    for (int i = 0; i < nf; i++) {
+        hm[i].resize(np);
+        WP_CK(P, cudaMemcpy(hm[i].data(), model[i], np * sizeof(float), cudaMemcpyDefault));
+    }
+    double vmax = 0.0;
+    for (size_t q = 0; q < np; q++) {
+        const float vp = hm[0][q];
+        if (!(vp > 0.f) || !std::isfinite(vp)) return wp_fail(P, PROP_EINVAL, "vp must be finite and > 0");
+        if (d->kind == PROP_TTI) {
+            const float e = hm[1][q], dl = hm[2][q];
+            if (!std::isfinite(e) || !std::isfinite(dl) || !std::isfinite(hm[3][q]) || !std::isfinite(hm[4][q]))
+                return wp_fail(P, PROP_EINVAL, "non-finite TTI parameter");
+            if (e < dl) return wp_fail(P, PROP_EINVAL, "epsilon < delta somewhere (TTI stability needs eps >= delta)");
+            if (1.0 + 2.0 * dl <= 0.0) return wp_fail(P, PROP_EINVAL, "1 + 2 delta must be > 0");
+            vmax = std::max(vmax, 1000.0 * vp * sqrt(1.0 + 2.0 * e));
+        } else {
+            const float vs = hm[1][q], rho = hm[2][q];
+            if (!(vs >= 0.f) || !std::isfinite(vs)) return wp_fail(P, PROP_EINVAL, "vs must be finite and >= 0");
+            if (!(rho > 0.f) || !std::isfinite(rho)) return wp_fail(P, PROP_EINVAL, "rho must be finite and > 0");
+            if ((double)vp * vp < 2.0 * (double)vs * vs) return wp_fail(P, PROP_EINVAL, "lambda < 0 (vp^2 < 2 vs^2)");
+            vmax = std::max(vmax, 1000.0 * vp);
+        }
+    }
+    P->vmax = (float)vmax;
+    const double dt = d->dt > 0.f ? (double)d->dt : 0.4 * d->h / vmax;
+    g.dt = (float)dt;
+    P->d.dt = g.dt;
+    // CFL: vmax dt / h <= 2 / (sqrt(3) max|symbol|)
+    const bool stag = d->kind == PROP_ELASTIC;
+    const double lim = 2.0 / (sqrt(3.0) * symbol_max(stag ? P->w.b : P->w.c, P->M, stag));
+    const double cour = vmax * dt / d->h;
+    if (cour > lim) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "dt = %g s gives Courant number %.4f above the stability bound %.4f", dt, cour, lim);
+        return wp_fail(P, PROP_EUNSTABLE, buf);
+    }
+    g.cer = 0.015f;
+    if (d->nbl > 0) {
+        const double L = d->nbl * (double)d->h;
+        const double vd = d->vdamp > 0.f ? (double)d->vdamp : vmax;
+        g.sig0 = (float)(3.0 * vd / (2.0 * L) * log(1000.0));
+    }
+    // device model
+    const size_t N = (size_t)g.N;
+    float *phys = nullptr;
+    WP_MALLOC(P, phys, np * sizeof(float), "model staging");
+    std::unique_ptr<float, decltype(&cudaFree)> guard(phys, &cudaFree);
+    auto upload = [&](int i, float *&dst, float scale, int mode) -> int {
+        WP_MALLOC(P, dst, N * sizeof(float), "model");
+        WP_CK(P, cudaMemcpyAsync(phys, hm[i].data(), np * sizeof(float), cudaMemcpyHostToDevice, P->stream));
+        k_extend(P, phys, dst, scale, mode);
+        return PROP_OK;
+    };
+    if (d->kind == PROP_TTI) {
+        WP_TRY(upload(0, P->m, 1000.f, 1));
+        WP_TRY(upload(1, P->eps, 1.f, 0));
+        WP_TRY(upload(2, P->del, 1.f, 0));
+        WP_TRY(upload(3, P->th, 1.f, 0));
+        WP_TRY(upload(4, P->ph, 1.f, 0));
+    } else {
+        WP_TRY(upload(0, P->bu, 1.f, 0));    // vp  -> b      (k_lame)
+        WP_TRY(upload(1, P->lam, 1.f, 0));   // vs  -> lambda
+        WP_TRY(upload(2, P->mu, 1.f, 0));    // rho -> mu
+        k_lame(P);
+    }
+    for (int i = 0; i < nfields(P); i++) WP_MALLOC(P, P->st[i], N * sizeof(float), "state");
+    WP_TRY(ensure_tmp(P, d->kind == PROP_TTI ? 8 : 0));
+    WP_MALLOC(P, P->flag, sizeof(int), "flag");
+    WP_CK(P, cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
+    WP_CK(P, cudaStreamSynchronize(P->stream));
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
+extern "C" int prop_create(const prop_desc *desc, const float *const *model, void *cuda_stream,
+                           prop_t **out)
+{
+    if (!out) return wp_fail(nullptr, PROP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!desc) return wp_fail(nullptr, PROP_EINVAL, "desc is NULL");
+    prop_s *P = new prop_s();
+    P->stream = (cudaStream_t)cuda_stream;
+    int rc = create_impl(P, desc, model);
+    if (rc) {
+        std::string m = P->err;
+        free_all(P);
+        delete P;
+        tl_err = m;
+        return rc;
+    }
+    *out = P;
+    return PROP_OK;
+}
+
+extern "C" void prop_destroy(prop_t *P)
+{
+    if (!P) return;
+    if (P->stream) cudaStreamSynchronize(P->stream);
+    free_all(P);
+    delete P;
+}
+
+extern "C" const char *prop_last_error(const prop_t *P)
+{
+    return P ? P->err.c_str() : tl_err.c_str();
+}
+
+extern "C" float prop_dt(const prop_t *P) { return P ? P->g.dt : 0.f; }
+
+extern "C" int prop_grid_dims(const prop_t *P, int *dims, int *nf)
+{
+    if (!P) return wp_fail(nullptr, PROP_EINVAL, "NULL handle");
+    if (dims) { dims[0] = P->g.NX; dims[1] = P->g.NY; dims[2] = P->g.NZ; }
+    if (nf) *nf = nfields(P);
+    return PROP_OK;
+}
+
+static int check_handle(prop_s *P)
+{
+    if (!P) return wp_fail(nullptr, PROP_EINVAL, "NULL handle");
+    if (P->broken) return wp_fail(P, PROP_ESTATE, "handle unusable after an earlier CUDA error: " + P->err);
+    P->kern_launches = 0;
+    return PROP_OK;
+}
+
+// end of a call: surface asynchronous errors and the NaN flag
+static int finish(prop_s *P)
+{
+    WP_CK(P, cudaStreamSynchronize(P->stream));
+    WP_CK(P, cudaGetLastError());
+    prof_collect(P);
+    if (P->d.check_nan) {
+        int f = 0;
+        WP_CK(P, cudaMemcpy(&f, P->flag, sizeof(int), cudaMemcpyDeviceToHost));
+        if (f) {
+            cudaMemset(P->flag, 0, sizeof(int));
+            return wp_fail(P, PROP_EUNSTABLE, "NaN or Inf in the wavefield");
+        }
+    }
+    return PROP_OK;
+}
+
+static int zero_fields(prop_s *P, float *const *f, int n)
+{
+    for (int i = 0; i < n; i++) WP_CK(P, cudaMemsetAsync(f[i], 0, sizeof(float) * P->g.N, P->stream));
+    return PROP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// state access
+// ---------------------------------------------------------------------------
+extern "C" int prop_set_state(prop_t *P, const float *const *fields)
+{
+    WP_TRY(check_handle(P));
+    if (!fields) return wp_fail(P, PROP_EINVAL, "fields is NULL");
+    for (int i = 0; i < nfields(P); i++) {
+        if (!fields[i]) return wp_fail(P, PROP_EINVAL, "field pointer is NULL");
+        WP_CK(P, cudaMemcpyAsync(P->st[i], fields[i], sizeof(float) * P->g.N, cudaMemcpyDefault, P->stream));
+    }
+    return finish(P);
+}
+
+extern "C" int prop_get_state(prop_t *P, float *const *fields)
+{
+    WP_TRY(check_handle(P));
+    if (!fields) return wp_fail(P, PROP_EINVAL, "fields is NULL");
+    for (int i = 0; i < nfields(P); i++) {
+        if (!fields[i]) return wp_fail(P, PROP_EINVAL, "field pointer is NULL");
+        WP_CK(P, cudaMemcpyAsync(fields[i], P->st[i], sizeof(float) * P->g.N, cudaMemcpyDefault, P->stream));
+    }
+    return finish(P);
+}
+
+static int step_state(prop_s *P, float **s, bool adjoint)
+{
+    if (P->d.kind == PROP_TTI) {
+        WP_TRY(tti_launch_step(P, s, adjoint, nullptr, nullptr, nullptr));
+        std::swap(s[0], s[2]);
+        std::swap(s[1], s[3]);
+    } else {
+        if (adjoint) WP_TRY(ensure_tmp(P, 9));
+        WP_TRY(el_launch_step(P, s, adjoint));
+    }
+    prof_maybe_collect(P);
+    return PROP_OK;
+}
+
+extern "C" int prop_step(prop_t *P, int nsteps, int adjoint)
+{
+    WP_TRY(check_handle(P));
+    if (nsteps < 0) return wp_fail(P, PROP_EINVAL, "nsteps < 0");
+    for (int i = 0; i < nsteps; i++) WP_TRY(step_state(P, P->st, adjoint != 0));
+    return finish(P);
+}
+
+extern "C" int prop_kernel_time(const prop_t *P, double *ms, long long *launches)
+{
+    if (!P) return wp_fail(nullptr, PROP_EINVAL, "NULL handle");
+    double t = 0.0;
+    long long n = 0;
+    for (int i = 0; i < 8; i++) { t += P->prof_ms[i]; n += P->prof_n[i]; }
+    if (ms) *ms = t;
+    if (launches) *launches = n;
+    return PROP_OK;
+}
+
+// measurement hooks (declared in the Python binding, not in the public header)
+extern "C" int prop_profile(prop_t *P, int on)
+{
+    if (!P) return wp_fail(nullptr, PROP_EINVAL, "NULL handle");
+    prof_collect(P);
+    P->prof = on != 0;
+    for (int i = 0; i < 8; i++) { P->prof_ms[i] = 0.0; P->prof_n[i] = 0; }
+    return PROP_OK;
+}
+extern "C" int prop_kernel_stats(const prop_t *P, int id, double *ms, long long *n)
+{
+    if (!P || id < 0 || id >= 8) return wp_fail(nullptr, PROP_EINVAL, "bad handle or id");
+    if (ms) *ms = P->prof_ms[id];
+    if (n) *n = P->prof_n[id];
+    return PROP_OK;
+}
+extern "C" long long prop_last_launches(const prop_t *P) { return P ? P->kern_launches : 0; }
+
+// ---------------------------------------------------------------------------
+// forward modelling with optional saving of forward wavefields
+// ---------------------------------------------------------------------------
+struct Geometry {
+    SparseDev S, R;
+    ~Geometry() { sp_free(&S); sp_free(&R); }
+};
+
+static int ckpt_K(const prop_s *P)
+{
+    int K = P->d.ckpt_interval;
+    if (K <= 0) K = (int)ceil(sqrt((double)P->d.nt));
+    return std::max(1, std::min(K, P->d.nt));
+}
+
+// slots of wavefield storage
+static size_t snap_fields(const prop_s *P) { return P->d.kind == PROP_TTI ? 2 : 9; }
+
+static int alloc_saves(prop_s *P)
+{
+    free_snaps(P);
+    const size_t N = (size_t)P->g.N;
+    const int nt = P->d.nt, K = ckpt_K(P);
+    const int J = (nt - 1 + K - 1) / K;     // checkpoints / segments
+    const int cf = nfields(P);               // fields per checkpoint
+    switch (P->d.snap_mode) {
+    case SNAP_FULL_FP32: {
+        // TTI: u^k, k = 1..nt-1 (p, r); elastic: X^k, k = 0..nt-1 (9 fields)
+        const size_t slots = P->d.kind == PROP_TTI ? (size_t)(nt - 1) : (size_t)nt;
+        P->snap_bytes = slots * snap_fields(P) * N * sizeof(float);
+        WP_MALLOC(P, P->snap, P->snap_bytes, "full FP32 wavefield storage");
+        break;
+    }
+    case SNAP_CKPT_FP32:
+        P->snap_bytes = (size_t)J * cf * N * sizeof(float);
+        WP_MALLOC(P, P->snap, P->snap_bytes, "FP32 checkpoints");
+        break;
+    default:
+        P->snap16_bytes = (size_t)J * cf * N * sizeof(uint16_t);
+        WP_MALLOC(P, P->snap16, P->snap16_bytes, "16-bit checkpoints");
+        WP_MALLOC(P, P->snap_scale, sizeof(float) * J * cf + 1024 * sizeof(float), "checkpoint scales");
+        break;
+    }
+    if (P->d.snap_mode != SNAP_FULL_FP32) {
+        const size_t slots = P->d.kind == PROP_TTI ? (size_t)K : (size_t)K + 1;
+        P->seg_bytes = slots * snap_fields(P) * N * sizeof(float);
+        WP_MALLOC(P, P->seg, P->seg_bytes, "recompute segment buffer");
+    }
+    return PROP_OK;
+}
+
+static float *snap_slot(prop_s *P, size_t slot)
+{
+    return P->snap + slot * snap_fields(P) * (size_t)P->g.N;
+}
+static float *seg_slot(prop_s *P, size_t slot)
+{
+    return P->seg + slot * snap_fields(P) * (size_t)P->g.N;
+}
+
+static int save_checkpoint(prop_s *P, int j, float *const *s)
+{
+    const size_t N = (size_t)P->g.N;
+    const int cf = nfields(P), K = ckpt_K(P);
+    const size_t nscale = (size_t)((P->d.nt - 1 + K - 1) / K) * cf;   // scales, then 1024 partials
+    for (int f = 0; f < cf; f++) {
+        const size_t slot = (size_t)j * cf + f;
+        if (P->d.snap_mode == SNAP_CKPT_FP32)
+            WP_CK(P, cudaMemcpyAsync(P->snap + slot * N, s[f], N * sizeof(float), cudaMemcpyDeviceToDevice, P->stream));
+        else
+            k_snap_encode(P, s[f], (long long)N, P->snap16 + slot * N, P->snap_scale + slot,
+                          P->d.snap_mode == SNAP_CKPT_BF16, P->snap_scale + nscale);
+    }
+    return PROP_OK;
+}
+static int load_checkpoint(prop_s *P, int j, float *const *s)
+{
+    const size_t N = (size_t)P->g.N;
+    const int cf = nfields(P);
+    for (int f = 0; f < cf; f++) {
+        const size_t slot = (size_t)j * cf + f;
+        if (P->d.snap_mode == SNAP_CKPT_FP32)
+            WP_CK(P, cudaMemcpyAsync(s[f], P->snap + slot * N, N * sizeof(float), cudaMemcpyDeviceToDevice, P->stream));
+        else
+            k_snap_decode(P, P->snap16 + slot * N, (long long)N, P->snap_scale + slot,
+                          P->d.snap_mode == SNAP_CKPT_BF16, s[f]);
+    }
+    return PROP_OK;
+}
+
+// inject q^n into the new level of state s (after the step)
+static void inject_src(prop_s *P, const SparseDev &S, const float *wav, int n, float *const *s)
+{
+    const int nt = P->d.nt;
+    if (P->d.kind == PROP_TTI)
+        sp_inject(P, &S, wav, nt, n, P->g.dt * P->g.dt, 1, s[0], s[1], nullptr, nullptr, nullptr);
+    else
+        sp_inject(P, &S, wav, nt, n, P->g.dt, 0, s[3], s[4], s[5], nullptr, nullptr);
+}
+static void record_rec(prop_s *P, const SparseDev &R, float *const *s, float *col)
+{
+    if (P->d.kind == PROP_TTI) sp_record(P, &R, s[0], nullptr, nullptr, 1.f, col);
+    else sp_record(P, &R, s[3], s[4], s[5], 1.f, col);
+}
+
+// One forward step n of state s (record already done).  TTI pointer rotation
+// is applied so that s[0..1] hold the new level afterwards.
+static int fwd_step(prop_s *P, float **s, const SparseDev &S, const float *wav, int n)
+{
+    if (P->d.kind == PROP_TTI) {
+        WP_TRY(tti_launch_step(P, s, false, nullptr, nullptr, nullptr));
+        std::swap(s[0], s[2]);
+        std::swap(s[1], s[3]);
+    } else {
+        WP_TRY(el_launch_step(P, s, false));
+    }
+    inject_src(P, S, wav, n, s);
+    prof_maybe_collect(P);
+    return PROP_OK;
+}
+
+// store level `lvl` (state s holds level lvl) in full storage
+static int store_full(prop_s *P, float *const *s, int lvl)
+{
+    const size_t N = (size_t)P->g.N;
+    if (P->d.kind == PROP_TTI) {
+        if (lvl < 1 || lvl > P->d.nt - 1) return PROP_OK;
+        float *d = snap_slot(P, lvl - 1);
+        WP_CK(P, cudaMemcpyAsync(d, s[0], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        WP_CK(P, cudaMemcpyAsync(d + N, s[1], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+    } else {
+        if (lvl < 0 || lvl > P->d.nt - 1) return PROP_OK;
+        float *d = snap_slot(P, lvl);
+        for (int f = 0; f < 9; f++)
+            WP_CK(P, cudaMemcpyAsync(d + f * N, s[f], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+    }
+    return PROP_OK;
+}
+
+// forward time loop; stage [nt][nrec]; save: keep wavefields per snap_mode
+static int run_forward(prop_s *P, const Geometry &G, const float *wav, float *stage, bool save)
+{
+    const int nt = P->d.nt, K = ckpt_K(P);
+    float *s[9];
+    for (int i = 0; i < 9; i++) s[i] = P->st[i];
+    WP_TRY(zero_fields(P, s, nfields(P)));
+    const bool full = save && P->d.snap_mode == SNAP_FULL_FP32;
+    const bool ckpt = save && !full;
+    if (full && P->d.kind == PROP_ELASTIC) WP_TRY(store_full(P, s, 0));
+    for (int n = 0; n < nt; n++) {
+        record_rec(P, G.R, s, stage + (size_t)n * G.R.n);
+        if (ckpt && n % K == 0 && n < nt - 1) WP_TRY(save_checkpoint(P, n / K, s));
+        WP_TRY(fwd_step(P, s, G.S, wav, n));
+        if (full) WP_TRY(store_full(P, s, n + 1));
+    }
+    // the final state, in st[] order, for prop_get_state (buffers permuted)
+    for (int i = 0; i < nfields(P); i++) P->st[i] = s[i];
+    return PROP_OK;
+}
+
+static int build_geometry(prop_s *P, Geometry &G, const float *src, int nsrc, const float *rec, int nrec)
+{
+    if (nsrc < 1 || nrec < 1) return wp_fail(P, PROP_EINVAL, "nsrc and nrec must be >= 1");
+    if (!src || !rec) return wp_fail(P, PROP_EINVAL, "coordinates are NULL");
+    std::vector<float> hs((size_t)nsrc * 3), hr((size_t)nrec * 3);
+    WP_CK(P, cudaMemcpy(hs.data(), src, hs.size() * 4, cudaMemcpyDefault));
+    WP_CK(P, cudaMemcpy(hr.data(), rec, hr.size() * 4, cudaMemcpyDefault));
+    WP_TRY(sp_build(P, hs.data(), nsrc, nullptr, &G.S));
+    WP_TRY(sp_build(P, hr.data(), nrec, nullptr, &G.R));
+    return PROP_OK;
+}
+
+static int forward_impl(prop_s *P, const float *wavelet, const float *src, int nsrc,
+                        const float *rec, int nrec, float *traces, bool save)
+{
+    WP_TRY(check_handle(P));
+    if (!wavelet || !traces) return wp_fail(P, PROP_EINVAL, "wavelet or traces is NULL");
+    Geometry G;
+    WP_TRY(build_geometry(P, G, src, nsrc, rec, nrec));
+    const int nt = P->d.nt;
+    DevBuf wbuf, stage, tr;
+    const float *wav = nullptr;
+    WP_TRY(dev_in(P, wavelet, (size_t)nsrc * nt, wbuf, &wav));
+    WP_TRY(wp_malloc(P, &stage.p, sizeof(float) * (size_t)nt * nrec, "trace staging"));
+    WP_TRY(wp_malloc(P, &tr.p, sizeof(float) * (size_t)nt * nrec, "traces"));
+    if (save) {
+        WP_TRY(alloc_saves(P));
+        if (P->d.kind == PROP_ELASTIC) WP_TRY(ensure_tmp(P, 15));
+    }
+    WP_TRY(run_forward(P, G, wav, (float *)stage.p, save));
+    sp_transpose(P, (const float *)stage.p, (float *)tr.p, nrec, nt);
+    WP_TRY(copy_out(P, traces, (const float *)tr.p, (size_t)nt * nrec));
+    if (save) {
+        P->saved = true;
+        P->saved_nsrc = nsrc;
+        P->saved_nrec = nrec;
+        P->saved_src.resize((size_t)nsrc * 3);
+        P->saved_rec.resize((size_t)nrec * 3);
+        P->saved_wav.resize((size_t)nsrc * nt);
+        WP_CK(P, cudaMemcpyAsync(P->saved_src.data(), src, (size_t)nsrc * 12, cudaMemcpyDefault, P->stream));
+        WP_CK(P, cudaMemcpyAsync(P->saved_rec.data(), rec, (size_t)nrec * 12, cudaMemcpyDefault, P->stream));
+        WP_CK(P, cudaMemcpyAsync(P->saved_wav.data(), wav, (size_t)nsrc * nt * 4, cudaMemcpyDefault, P->stream));
+    }
+    return finish(P);
+}
+
+extern "C" int prop_forward(prop_t *P, const float *wavelet, const float *src_xyz, int nsrc,
+                            const float *rec_xyz, int nrec, float *traces)
+{
+    return forward_impl(P, wavelet, src_xyz, nsrc, rec_xyz, nrec, traces, false);
+}
+
+extern "C" int prop_forward_saved(prop_t *P, const float *wavelet, const float *src_xyz, int nsrc,
+                                  const float *rec_xyz, int nrec, float *traces)
+{
+    int rc = forward_impl(P, wavelet, src_xyz, nsrc, rec_xyz, nrec, traces, true);
+    if (rc && P) free_snaps(P);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------
+// adjoint sweeps
+// ---------------------------------------------------------------------------
+// inject residual column k (traces [nrec][nt]) into the adjoint state
+static void inject_resid(prop_s *P, const Geometry &G, const float *res, int k, float *const *a,
+                         const float *img_p, float *grad)
+{
+    const int nt = P->d.nt;
+    if (P->d.kind == PROP_TTI)
+        sp_inject(P, &G.R, res, nt, k, 1.f, 1, a[0], nullptr, nullptr, grad ? img_p : nullptr, grad);
+    else
+        sp_inject(P, &G.R, res, nt, k, 1.f, 0, a[3], a[4], a[5], nullptr, nullptr);
+}
+// adjoint source output qbar^{k-1} from the adjoint state at level k
+static void sample_src(prop_s *P, const Geometry &G, float *const *a, float *col)
+{
+    if (P->d.kind == PROP_TTI) sp_record(P, &G.S, a[0], a[1], nullptr, P->g.dt * P->g.dt, col);
+    else sp_record(P, &G.S, a[3], a[4], a[5], P->g.dt, col);
+}
+
+// TTI adjoint sweep.  grad != NULL: imaging with forward wavefields.
+static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float *wav,
+                     float *srcstage, float *grad)
+{
+    const int nt = P->d.nt;
+    const size_t N = (size_t)P->g.N;
+    WP_TRY(ensure_ast(P));
+    float *a[4] = {P->ast[0], P->ast[1], P->ast[2], P->ast[3]};
+    WP_TRY(zero_fields(P, a, 4));
+    if (srcstage) WP_CK(P, cudaMemsetAsync(srcstage, 0, sizeof(float) * (size_t)nt * G.S.n, P->stream));
+    auto adj_iter = [&](int k, const float *up, const float *ur) -> int {
+        WP_TRY(tti_launch_step(P, a, true, up, ur, grad));
+        std::swap(a[0], a[2]);
+        std::swap(a[1], a[3]);
+        inject_resid(P, G, res, k, a, up, grad);
+        if (srcstage) sample_src(P, G, a, srcstage + (size_t)(k - 1) * G.S.n);
+        prof_maybe_collect(P);
+        return PROP_OK;
+    };
+    if (!grad) {
+        for (int k = nt - 1; k >= 1; k--) WP_TRY(adj_iter(k, nullptr, nullptr));
+        return PROP_OK;
+    }
+    if (P->d.snap_mode == SNAP_FULL_FP32) {
+        for (int k = nt - 1; k >= 1; k--) {
+            const float *u = snap_slot(P, k - 1);
+            WP_TRY(adj_iter(k, u, u + N));
+        }
+        return PROP_OK;
+    }
+    const int K = ckpt_K(P), J = (nt - 1 + K - 1) / K;
+    float *s[4] = {P->st[0], P->st[1], P->st[2], P->st[3]};
+    for (int j = J - 1; j >= 0; j--) {
+        const int n0 = j * K, E = std::min((j + 1) * K, nt - 1);
+        // restore level n0 and recompute levels n0+1..E
+        float *f[4] = {P->st[0], P->st[1], P->st[2], P->st[3]};
+        for (int i = 0; i < 4; i++) s[i] = f[i];
+        WP_TRY(load_checkpoint(P, j, s));
+        for (int n = n0; n < E; n++) {
+            WP_TRY(fwd_step(P, s, G.S, wav, n));
+            float *d = seg_slot(P, n - n0);     // level n+1
+            WP_CK(P, cudaMemcpyAsync(d, s[0], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+            WP_CK(P, cudaMemcpyAsync(d + N, s[1], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        }
+        for (int k = E; k >= n0 + 1; k--) {
+            const float *u = seg_slot(P, k - n0 - 1);
+            WP_TRY(adj_iter(k, u, u + N));
+        }
+    }
+    return PROP_OK;
+}
+
+// elastic adjoint sweep; g3 != NULL: gradient (lambda, mu, b) on the computational grid
+static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float *wav,
+                    float *srcstage, float *const *g3)
+{
+    const int nt = P->d.nt;
+    const size_t N = (size_t)P->g.N;
+    WP_TRY(ensure_ast(P));
+    WP_TRY(ensure_tmp(P, g3 ? 15 : 9));
+    float *a[9];
+    for (int i = 0; i < 9; i++) a[i] = P->ast[i];
+    WP_TRY(zero_fields(P, a, 9));
+    if (srcstage) WP_CK(P, cudaMemsetAsync(srcstage, 0, sizeof(float) * (size_t)nt * G.S.n, P->stream));
+    auto after = [&](int k) {
+        if (k >= 1) {
+            inject_resid(P, G, res, k, a, nullptr, nullptr);
+            if (srcstage) sample_src(P, G, a, srcstage + (size_t)(k - 1) * G.S.n);
+        }
+        prof_maybe_collect(P);
+    };
+    // k = nt-1: transposed step of a zero state, then the last residual sample
+    WP_TRY(el_launch_step(P, a, true));
+    after(nt - 1);
+    if (!g3) {
+        for (int k = nt - 2; k >= 0; k--) {
+            WP_TRY(el_launch_step(P, a, true));
+            after(k);
+        }
+        return PROP_OK;
+    }
+    auto xs = [&](float *base, const float **out) {
+        for (int f = 0; f < 9; f++) out[f] = base + f * N;
+    };
+    if (P->d.snap_mode == SNAP_FULL_FP32) {
+        for (int k = nt - 2; k >= 0; k--) {
+            const float *x0[9], *x1[9];
+            xs(snap_slot(P, k), x0);
+            xs(snap_slot(P, k + 1), x1);
+            WP_TRY(el_launch_adj_grad(P, a, x0, x1, g3));
+            after(k);
+        }
+        return PROP_OK;
+    }
+    const int K = ckpt_K(P), J = (nt - 1 + K - 1) / K;
+    for (int j = J - 1; j >= 0; j--) {
+        const int n0 = j * K, E = std::min((j + 1) * K, nt - 1);
+        float *s[9];
+        for (int i = 0; i < 9; i++) s[i] = P->st[i];
+        WP_TRY(load_checkpoint(P, j, s));
+        for (int f = 0; f < 9; f++)
+            WP_CK(P, cudaMemcpyAsync(seg_slot(P, 0) + f * N, s[f], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        for (int n = n0; n < E; n++) {
+            WP_TRY(fwd_step(P, s, G.S, wav, n));
+            for (int f = 0; f < 9; f++)
+                WP_CK(P, cudaMemcpyAsync(seg_slot(P, n + 1 - n0) + f * N, s[f], N * 4,
+                                         cudaMemcpyDeviceToDevice, P->stream));
+        }
+        for (int k = E - 1; k >= n0; k--) {
+            const float *x0[9], *x1[9];
+            xs(seg_slot(P, k - n0), x0);
+            xs(seg_slot(P, k + 1 - n0), x1);
+            WP_TRY(el_launch_adj_grad(P, a, x0, x1, g3));
+            after(k);
+        }
+    }
+    return PROP_OK;
+}
+
+extern "C" int prop_adjoint(prop_t *P, const float *traces_in, const float *rec_xyz, int nrec,
+                            const float *src_xyz, int nsrc, float *src_out)
+{
+    WP_TRY(check_handle(P));
+    if (!traces_in || !src_out) return wp_fail(P, PROP_EINVAL, "traces_in or src_out is NULL");
+    Geometry G;
+    WP_TRY(build_geometry(P, G, src_xyz, nsrc, rec_xyz, nrec));
+    const int nt = P->d.nt;
+    DevBuf rbuf, stage, out;
+    const float *res = nullptr;
+    WP_TRY(dev_in(P, traces_in, (size_t)nrec * nt, rbuf, &res));
+    WP_TRY(wp_malloc(P, &stage.p, sizeof(float) * (size_t)nt * nsrc, "source staging"));
+    WP_TRY(wp_malloc(P, &out.p, sizeof(float) * (size_t)nt * nsrc, "source output"));
+    if (P->d.kind == PROP_TTI) WP_TRY(tti_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
+    else WP_TRY(el_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
+    sp_transpose(P, (const float *)stage.p, (float *)out.p, nsrc, nt);
+    WP_TRY(copy_out(P, src_out, (const float *)out.p, (size_t)nt * nsrc));
+    return finish(P);
+}
+
+// backward pass with the saved forward run
+static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_grad, double *misfit_unused)
+{
+    (void)misfit_unused;
+    if (!P->saved) return wp_fail(P, PROP_ESTATE, "prop_backward needs a preceding prop_forward_saved");
+    const int nt = P->d.nt, nsrc = P->saved_nsrc, nrec = P->saved_nrec;
+    Geometry G;
+    WP_TRY(sp_build(P, P->saved_src.data(), nsrc, nullptr, &G.S));
+    WP_TRY(sp_build(P, P->saved_rec.data(), nrec, nullptr, &G.R));
+    DevBuf rbuf, wbuf, stage, out, gbuf, gphys;
+    const float *res = nullptr;
+    WP_TRY(dev_in(P, resid, (size_t)nrec * nt, rbuf, &res));
+    WP_TRY(wp_malloc(P, &wbuf.p, sizeof(float) * (size_t)nsrc * nt, "wavelet"));
+    WP_CK(P, cudaMemcpyAsync(wbuf.p, P->saved_wav.data(), sizeof(float) * (size_t)nsrc * nt,
+                             cudaMemcpyHostToDevice, P->stream));
+    if (src_grad) {
+        WP_TRY(wp_malloc(P, &stage.p, sizeof(float) * (size_t)nt * nsrc, "source staging"));
+        WP_TRY(wp_malloc(P, &out.p, sizeof(float) * (size_t)nt * nsrc, "source output"));
+    }
+    const int ng = P->d.kind == PROP_TTI ? 1 : 3;
+    const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
+    float *g3[3] = {};
+    if (grad) {
+        WP_TRY(wp_malloc(P, &gbuf.p, sizeof(float) * N * ng, "gradient"));
+        WP_CK(P, cudaMemsetAsync(gbuf.p, 0, sizeof(float) * N * ng, P->stream));
+        for (int i = 0; i < ng; i++) g3[i] = (float *)gbuf.p + i * N;
+        WP_TRY(wp_malloc(P, &gphys.p, sizeof(float) * np * ng, "gradient (physical)"));
+    }
+    if (P->d.kind == PROP_TTI)
+        WP_TRY(tti_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3[0] : nullptr));
+    else
+        WP_TRY(el_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3 : nullptr));
+    if (src_grad) {
+        sp_transpose(P, (const float *)stage.p, (float *)out.p, nsrc, nt);
+        WP_TRY(copy_out(P, src_grad, (const float *)out.p, (size_t)nt * nsrc));
+    }
+    if (grad) {
+        for (int i = 0; i < ng; i++) k_fold(P, g3[i], (float *)gphys.p + i * np);
+        WP_TRY(copy_out(P, grad, (const float *)gphys.p, np * ng));
+    }
+    return finish(P);
+}
+
+extern "C" int prop_backward(prop_t *P, const float *resid, float *grad, float *src_grad)
+{
+    WP_TRY(check_handle(P));
+    if (!resid) return wp_fail(P, PROP_EINVAL, "resid is NULL");
+    int rc = backward_impl(P, resid, grad, src_grad, nullptr);
+    free_snaps(P);
+    return rc;
+}
+
+extern "C" int prop_gradient(prop_t *P, const float *wavelet, const float *src_xyz, int nsrc,
+                             const float *rec_xyz, int nrec, const float *d_obs, float *grad,
+                             double *misfit)
+{
+    WP_TRY(check_handle(P));
+    if (!d_obs || !grad) return wp_fail(P, PROP_EINVAL, "d_obs or grad is NULL");
+    const int nt = P->d.nt;
+    DevBuf tr, obs;
+    WP_TRY(wp_malloc(P, &tr.p, sizeof(float) * (size_t)nrec * nt, "traces"));
+    int rc = forward_impl(P, wavelet, src_xyz, nsrc, rec_xyz, nrec, (float *)tr.p, true);
+    if (rc) { free_snaps(P); return rc; }
+    const float *dobs = nullptr;
+    rc = dev_in(P, d_obs, (size_t)nrec * nt, obs, &dobs);
+    if (rc) { free_snaps(P); return rc; }
+    k_axpy_sq(P, (const float *)tr.p, dobs, (float *)tr.p, (long long)nrec * nt);
+    if (misfit) *misfit = 0.5 * k_sumsq_host(P, (const float *)tr.p, (long long)nrec * nt);
+    rc = backward_impl(P, (const float *)tr.p, grad, nullptr, nullptr);
+    free_snaps(P);
+    return rc;
+}

@@ -1,0 +1,395 @@
+// Sparse operators (source injection, receiver interpolation; Sec. II-A:
+// s.inject(u.forward, expr=s*dt**2/m) and d.interpolate(u)), model set-up,
+// gradient fold, reductions and the snapshot codec.
+#include "common.cuh"
+
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <tuple>
+
+namespace {
+constexpr int NB = 256;
+
+inline int nblk(long long n, int b = NB) { return (int)std::min<long long>((n + b - 1) / b, 1 << 30); }
+
+__global__ void record_kernel(int n, const long long *__restrict__ idx, const float *__restrict__ w,
+                              const float *__restrict__ f0, const float *__restrict__ f1,
+                              const float *__restrict__ f2, float scale, float *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const long long q = idx[8 * i + c];
+        const float wc = w[8 * i + c];
+        if (wc != 0.f) {
+            float v = f0[q];
+            if (f1) v += f1[q];
+            if (f2) v += f2[q];
+            s += wc * v;
+        }
+    }
+    out[i] = scale * s;
+}
+
+__global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict__ cell,
+                              const int *__restrict__ ptr, const int *__restrict__ tr,
+                              const float *__restrict__ w, const float *__restrict__ traces, int nt,
+                              int t, float scale, int mode, const float *__restrict__ m,
+                              float *f0, float *f1, float *f2, const float *__restrict__ gu,
+                              float *grad)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= ncell) return;
+    float acc = 0.f;
+    for (int e = ptr[j]; e < ptr[j + 1]; e++) acc += w[e] * traces[(long long)tr[e] * nt + t];
+    const long long q = cell[j];
+    float coef = scale;
+    if (mode == 1) {
+        const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
+        const float A = m[q] * (1.f + 0.5f * tti_sigma(g, x, y, z) * g.dt);
+        coef = scale / A;
+    }
+    const float v = coef * acc;
+    f0[q] += v;
+    if (f1) f1[q] += v;
+    if (f2) f2[q] += v;
+    if (grad) grad[q] -= gu[q] * (scale * acc) / m[q];
+}
+
+__global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int n, int nt)
+{
+    __shared__ float tile[32][33];
+    int t0 = blockIdx.y * 32, i0 = blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int t = t0 + r, i = i0 + threadIdx.x;
+        if (t < nt && i < n) tile[r][threadIdx.x] = in[(long long)t * n + i];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int i = i0 + r, t = t0 + threadIdx.x;
+        if (t < nt && i < n) out[(long long)i * nt + t] = tile[threadIdx.x][r];
+    }
+}
+
+__global__ void fill_kernel(float *a, long long n, float v)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+// mode 0: comp = scale*phys ; 1: comp = 1/(scale*phys)^2
+__global__ void extend_kernel(GridDev g, const float *__restrict__ phys, float *__restrict__ comp,
+                              float scale, int mode)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= g.N) return;
+    const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
+    const int i = clampi(x - g.nbl, 0, g.px - 1), j = clampi(y - g.nbl, 0, g.py - 1),
+              k = clampi(z - g.nbl, 0, g.pz - 1);
+    const float v = phys[((long long)i * g.py + j) * g.pz + k];
+    if (mode == 0) comp[q] = scale * v;
+    else {
+        const float s = scale * v;
+        comp[q] = 1.f / (s * s);
+    }
+}
+
+// elastic: (vp, vs, rho) computational -> (b, lambda, mu) in place
+__global__ void lame_kernel(long long n, float *vp_b, float *vs_l, float *rho_mu)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float vp = 1000.f * vp_b[q], vs = 1000.f * vs_l[q], rho = 1000.f * rho_mu[q];
+    vp_b[q] = 1.f / rho;
+    vs_l[q] = rho * (vp * vp - 2.f * vs * vs);
+    rho_mu[q] = rho * vs * vs;
+}
+
+// adjoint of the edge-replication extension (gather form)
+__global__ void fold_kernel(GridDev g, const float *__restrict__ comp, float *__restrict__ phys)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long np = (long long)g.px * g.py * g.pz;
+    if (q >= np) return;
+    const int k = (int)(q % g.pz), j = (int)((q / g.pz) % g.py), i = (int)(q / ((long long)g.pz * g.py));
+    auto range = [&](int c, int n, int N, int &lo, int &hi) {
+        lo = (c == 0) ? 0 : c + g.nbl;
+        hi = (c == n - 1) ? N - 1 : c + g.nbl;
+    };
+    int x0, x1, y0, y1, z0, z1;
+    range(i, g.px, g.NX, x0, x1);
+    range(j, g.py, g.NY, y0, y1);
+    range(k, g.pz, g.NZ, z0, z1);
+    float s = 0.f;
+    for (int x = x0; x <= x1; x++)
+        for (int y = y0; y <= y1; y++)
+            for (int z = z0; z <= z1; z++) s += comp[gidx(g, x, y, z)];
+    phys[q] = s;
+}
+
+__global__ void zeta_kernel(long long n, const float *__restrict__ eps, const float *__restrict__ del,
+                            const float *__restrict__ lp, const float *__restrict__ lr,
+                            float *__restrict__ zp, float *__restrict__ zr)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float a = 1.f + 2.f * eps[q], s = sqrtf(1.f + 2.f * del[q]);
+    const float p = lp[q], r = lr[q];
+    zp[q] = a * p + s * r;
+    zr[q] = s * p + r;
+}
+
+__global__ void diff_kernel(const float *a, const float *b, float *out, long long n)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n) out[q] = a[q] - b[q];
+}
+
+// deterministic two-stage sum of squares (double)
+__global__ void sumsq_partial(const float *__restrict__ a, long long n, double *part)
+{
+    __shared__ double sh[NB];
+    double s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s += (double)a[i] * (double)a[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = NB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// ---- snapshot codec -------------------------------------------------------
+__global__ void absmax_partial(const float *__restrict__ a, long long n, float *part)
+{
+    __shared__ float sh[NB];
+    float s = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s = fmaxf(s, fabsf(a[i]));
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = NB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+// one block: scale = amax / target (1 if amax == 0)
+__global__ void absmax_final(const float *part, int np, float target, float *scale)
+{
+    __shared__ float sh[NB];
+    float s = 0.f;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) s = fmaxf(s, part[i]);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = NB / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *scale = sh[0] > 0.f ? sh[0] / target : 1.f;
+}
+
+// round-to-nearest-even conversions written from the IEEE formats
+__device__ __forceinline__ uint16_t f2bf16(float f)
+{
+    uint32_t u = __float_as_uint(f);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)((u >> 16) | ((u & 0xffff) ? 0x40 : 0));
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return (uint16_t)(u >> 16);
+}
+__device__ __forceinline__ float bf162f(uint16_t b) { return __uint_as_float(((uint32_t)b) << 16); }
+
+__global__ void quant_kernel(const float *__restrict__ in, long long n, uint16_t *__restrict__ out,
+                             const float *__restrict__ scale, int bf16)
+{
+    const float inv = 1.f / *scale;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float v = in[i] * inv;
+        out[i] = bf16 ? f2bf16(v) : __half_as_ushort(__float2half_rn(v));
+    }
+}
+__global__ void dequant_kernel(const uint16_t *__restrict__ in, long long n, const float *__restrict__ scale,
+                               int bf16, float *__restrict__ out)
+{
+    const float s = *scale;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const uint16_t b = in[i];
+        out[i] = s * (bf16 ? bf162f(b) : __half2float(__ushort_as_half(b)));
+    }
+}
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int sp_build(prop_s *P, const float *xyz, int n, const int *trace_of_point, SparseDev *S)
+{
+    const GridDev &g = P->g;
+    std::vector<long long> ridx((size_t)n * 8, 0);
+    std::vector<float> rw((size_t)n * 8, 0.f);
+    std::vector<std::tuple<long long, int, float>> ent;
+    ent.reserve((size_t)n * 8);
+    const int dims[3] = {g.NX, g.NY, g.NZ};
+    for (int i = 0; i < n; i++) {
+        double s[3], f[3];
+        int i0[3];
+        for (int a = 0; a < 3; a++) {
+            s[a] = (double)xyz[3 * i + a] / (double)g.h + (double)g.nbl;
+            if (!(s[a] >= 0.0) || s[a] > (double)(dims[a] - 1))
+                return wp_fail(P, PROP_EINVAL, "sparse point " + std::to_string(i) + " outside the grid");
+            i0[a] = (int)std::floor(s[a]);
+            f[a] = s[a] - i0[a];
+        }
+        int c = 0;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++)
+                for (int d = 0; d < 2; d++, c++) {
+                    const double wt = (a ? f[0] : 1 - f[0]) * (b ? f[1] : 1 - f[1]) * (d ? f[2] : 1 - f[2]);
+                    if (wt == 0.0) continue;
+                    const long long q = ((long long)(i0[0] + a) * g.NY + (i0[1] + b)) * g.NZ + (i0[2] + d);
+                    ridx[8 * (size_t)i + c] = q;
+                    rw[8 * (size_t)i + c] = (float)wt;
+                    ent.emplace_back(q, trace_of_point ? trace_of_point[i] : i, (float)wt);
+                }
+    }
+    std::stable_sort(ent.begin(), ent.end(),
+                     [](const auto &A, const auto &B) { return std::get<0>(A) < std::get<0>(B); });
+    std::vector<long long> cells;
+    std::vector<int> ptr, trs;
+    std::vector<float> ws;
+    for (size_t e = 0; e < ent.size(); e++) {
+        if (e == 0 || std::get<0>(ent[e]) != std::get<0>(ent[e - 1])) {
+            cells.push_back(std::get<0>(ent[e]));
+            ptr.push_back((int)e);
+        }
+        trs.push_back(std::get<1>(ent[e]));
+        ws.push_back(std::get<2>(ent[e]));
+    }
+    ptr.push_back((int)ent.size());
+    S->n = n;
+    S->ncell = (int)cells.size();
+    WP_CK(P, cudaMalloc(&S->rec_idx, sizeof(long long) * ridx.size()));
+    WP_CK(P, cudaMalloc(&S->rec_w, sizeof(float) * rw.size()));
+    WP_CK(P, cudaMalloc(&S->cell, sizeof(long long) * std::max<size_t>(1, cells.size())));
+    WP_CK(P, cudaMalloc(&S->cell_ptr, sizeof(int) * ptr.size()));
+    WP_CK(P, cudaMalloc(&S->ent_trace, sizeof(int) * std::max<size_t>(1, trs.size())));
+    WP_CK(P, cudaMalloc(&S->ent_w, sizeof(float) * std::max<size_t>(1, ws.size())));
+    WP_CK(P, cudaMemcpyAsync(S->rec_idx, ridx.data(), sizeof(long long) * ridx.size(), cudaMemcpyHostToDevice, P->stream));
+    WP_CK(P, cudaMemcpyAsync(S->rec_w, rw.data(), sizeof(float) * rw.size(), cudaMemcpyHostToDevice, P->stream));
+    if (!cells.empty()) {
+        WP_CK(P, cudaMemcpyAsync(S->cell, cells.data(), sizeof(long long) * cells.size(), cudaMemcpyHostToDevice, P->stream));
+        WP_CK(P, cudaMemcpyAsync(S->ent_trace, trs.data(), sizeof(int) * trs.size(), cudaMemcpyHostToDevice, P->stream));
+        WP_CK(P, cudaMemcpyAsync(S->ent_w, ws.data(), sizeof(float) * ws.size(), cudaMemcpyHostToDevice, P->stream));
+    }
+    WP_CK(P, cudaMemcpyAsync(S->cell_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, P->stream));
+    WP_CK(P, cudaStreamSynchronize(P->stream));   // host vectors go out of scope
+    return PROP_OK;
+}
+
+void sp_free(SparseDev *S)
+{
+    cudaFree(S->rec_idx); cudaFree(S->rec_w); cudaFree(S->cell); cudaFree(S->cell_ptr);
+    cudaFree(S->ent_trace); cudaFree(S->ent_w);
+    *S = SparseDev{};
+}
+
+void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, const float *f2,
+               float scale, float *out_col)
+{
+    if (S->n <= 0) return;
+    record_kernel<<<nblk(S->n), NB, 0, P->stream>>>(S->n, S->rec_idx, S->rec_w, f0, f1, f2, scale, out_col);
+    P->kern_launches++;
+}
+
+void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
+               int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad)
+{
+    if (S->ncell <= 0) return;
+    inject_kernel<<<nblk(S->ncell), NB, 0, P->stream>>>(P->g, S->ncell, S->cell, S->cell_ptr,
+                                                        S->ent_trace, S->ent_w, traces, nt, t, scale,
+                                                        mode, P->m, f0, f1, f2, grad_u, grad);
+    P->kern_launches++;
+}
+
+void sp_transpose(prop_s *P, const float *in_tn, float *out_nt, int n, int nt)
+{
+    dim3 blk(32, 8), grd((n + 31) / 32, (nt + 31) / 32);
+    transpose_kernel<<<grd, blk, 0, P->stream>>>(in_tn, out_nt, n, nt);
+    P->kern_launches++;
+}
+
+void k_fill(prop_s *P, float *a, long long n, float v)
+{
+    fill_kernel<<<std::min(nblk(n), 152 * 16), NB, 0, P->stream>>>(a, n, v);
+}
+
+void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode)
+{
+    extend_kernel<<<nblk(P->g.N), NB, 0, P->stream>>>(P->g, phys, comp, scale, mode);
+}
+
+void k_lame(prop_s *P)
+{
+    lame_kernel<<<nblk(P->g.N), NB, 0, P->stream>>>(P->g.N, P->bu, P->lam, P->mu);
+}
+
+void k_fold(prop_s *P, const float *comp, float *phys)
+{
+    const long long np = (long long)P->g.px * P->g.py * P->g.pz;
+    fold_kernel<<<nblk(np), NB, 0, P->stream>>>(P->g, comp, phys);
+    P->kern_launches++;
+}
+
+void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr)
+{
+    zeta_kernel<<<nblk(P->g.N), NB, 0, P->stream>>>(P->g.N, P->eps, P->del, lp, lr, zp, zr);
+    P->kern_launches += 1;
+}
+
+void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long n)
+{
+    diff_kernel<<<nblk(n), NB, 0, P->stream>>>(a, b, out, n);
+    P->kern_launches++;
+}
+
+double k_sumsq_host(prop_s *P, const float *a, long long n)
+{
+    const int nb = 1024;
+    double *part = nullptr;
+    if (cudaMalloc(&part, sizeof(double) * nb) != cudaSuccess) return NAN;
+    sumsq_partial<<<nb, NB, 0, P->stream>>>(a, n, part);
+    P->kern_launches++;
+    std::vector<double> h(nb);
+    cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, P->stream);
+    cudaStreamSynchronize(P->stream);
+    cudaFree(part);
+    double s = 0.0;
+    for (double v : h) s += v;
+    return s;
+}
+
+void k_snap_encode(prop_s *P, const float *in, long long n, uint16_t *out, float *scale_dev,
+                   int bf16, float *scratch)
+{
+    const int nb = 1024;   // scratch holds nb partial maxima
+    absmax_partial<<<nb, NB, 0, P->stream>>>(in, n, scratch);
+    absmax_final<<<1, NB, 0, P->stream>>>(scratch, nb, bf16 ? 1.f : 32768.f, scale_dev);
+    quant_kernel<<<std::min(nblk(n), 152 * 16), NB, 0, P->stream>>>(in, n, out, scale_dev, bf16);
+    P->kern_launches += 3;
+}
+
+void k_snap_decode(prop_s *P, const uint16_t *in, long long n, const float *scale_dev, int bf16,
+                   float *out)
+{
+    dequant_kernel<<<std::min(nblk(n), 152 * 16), NB, 0, P->stream>>>(in, n, scale_dev, bf16, out);
+    P->kern_launches++;
+}

@@ -1,0 +1,81 @@
+"""C ABI checks that need no GPU: the library builds/loads, exports every
+function declared in include/waveprop.h, and the binding's prop_desc layout
+matches the C compiler's."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "waveprop.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(prop_[a-z_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2004_10519_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for n in ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient", "prop_destroy",
+              "prop_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+    # and the binding lists exactly the header's functions
+    import paper_2004_10519_gb300 as wp
+    assert sorted(wp.ABI_SYMBOLS) == _declared()
+
+
+def test_library_loads_without_gpu(libpath):
+    L = C.CDLL(libpath)
+    for n in _declared():
+        assert hasattr(L, n)
+    # calls that touch no device: NULL-safe destroy and error queries
+    L.prop_destroy(None)
+    L.prop_last_error.restype = C.c_char_p
+    L.prop_last_error.argtypes = [C.c_void_p]
+    assert isinstance(L.prop_last_error(None), bytes)
+
+
+def test_prop_desc_layout_matches_binding():
+    import paper_2004_10519_gb300 as wp
+    fields = [f[0] for f in wp.PropDesc._fields_]
+    prog = '#include <stdio.h>\n#include <stddef.h>\n#include "waveprop.h"\nint main(void){\n'
+    prog += 'printf("%zu\\n", sizeof(prop_desc));\n'
+    for f in fields:
+        prog += f'printf("%zu\\n", offsetof(prop_desc, {f}));\n'
+    prog += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(src, "w").write(prog)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), src, "-o", exe])
+        vals = [int(v) for v in subprocess.check_output([exe]).split()]
+    assert vals[0] == C.sizeof(wp.PropDesc)
+    for f, off in zip(fields, vals[1:]):
+        assert getattr(wp.PropDesc, f).offset == off, f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    import paper_2004_10519_gb300 as wp
+    monkeypatch.setattr(wp, "_lib", None)
+    monkeypatch.setattr(wp, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        wp.lib()

@@ -1,0 +1,183 @@
+"""GPU parity of the TTI propagator (C ABI, FP32 CUDA kernels) against the
+FP64 oracle.  Tolerance: relative L2 <= 1e-5 on traces (the stated target of
+the method's FP32 implementation); gradients 1e-4 (FP32 accumulation of a
+cross-correlation over all steps)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def wp():
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    return wp
+
+
+def ragged_tti(so, nt=70, seed=3, shape=(37, 29, 45), nbl=7, h=10.0):
+    """Small heterogeneous TTI problem with ragged tile tails."""
+    nx, ny, nz = shape
+    m = synth.layered_tti(nx, ny, nz, seed, noise_sigma=3.0, smooth_sigma=1.5)
+    vmax = float(np.max(m["vp"] * np.sqrt(1 + 2 * m["eps"])))
+    dt = synth.cfl_dt(h, vmax)
+    src = np.array([[nx * h * 0.45 + 1.3, ny * h * 0.55 - 2.1, 3.3 * h],
+                    [nx * h * 0.25, ny * h * 0.3 + 0.7, nz * h * 0.6]], np.float32)
+    wav = np.vstack([synth.ricker(25.0, dt, nt), 0.6 * synth.ricker(18.0, dt, nt)])
+    rec = synth.carpet_receivers(5.2, 7.1, 3.7 * h, 9, 7, 1.9 * h)
+    return synth.Problem(synth.TTI, nx, ny, nz, nbl, h, so, nt, dt, m, src, wav, rec)
+
+
+def test_forward_parity_two_layer_so8(wp):
+    """84^3 computational grid (64^3 + 10-cell layer), space order 8, 150
+    steps, two-layer model: the small TTI workload in full."""
+    p = synth.tti_two_layer()
+    tr = wp.Propagator.from_problem(p).forward(p.wavelet, p.src, p.rec)
+    ref = oracle.Problem(p).forward()
+    assert rel(tr, ref) <= TOL
+
+
+@pytest.mark.parametrize("so", [4, 8, 12, 16])
+def test_forward_parity_ragged(wp, so):
+    p = ragged_tti(so)
+    tr = wp.Propagator.from_problem(p).forward(p.wavelet, p.src, p.rec)
+    ref = oracle.Problem(p).forward()
+    assert rel(tr, ref) <= TOL, so
+
+
+@pytest.mark.parametrize("so", [8, 12])
+def test_adjoint_parity_and_dot(wp, so):
+    p = ragged_tti(so, nt=60)
+    prop = wp.Propagator.from_problem(p)
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    q = rng.standard_normal((2, p.nt)).astype(np.float32)
+    qa = prop.adjoint(d, p.src, p.rec)
+    ref = oracle.Problem(p).adjoint(d)
+    assert rel(qa, ref) <= TOL
+    Fq = prop.forward(q, p.src, p.rec)
+    a = float(np.sum(Fq.astype(np.float64) * d))
+    b = float(np.sum(q.astype(np.float64) * qa))
+    assert abs(a - b) <= 1e-5 * abs(a), (a, b)
+
+
+def grad_problem(so=8, nt=80):
+    p = ragged_tti(so, nt=nt, shape=(30, 26, 34), nbl=6)
+    p.vdamp = float(np.max(p.model["vp"] * np.sqrt(1 + 2 * p.model["eps"]))) * 1000.0
+    true = oracle.Problem(p)
+    d_obs = true.forward()
+    start = synth.smooth_model(p.model, 3.0)
+    p0 = synth.Problem(**{**p.__dict__, "model": start})
+    return p, p0, d_obs
+
+
+def test_gradient_parity_and_checkpoint_modes(wp):
+    p, p0, d_obs = grad_problem()
+    g_ref, J_ref = oracle.Problem(p0).gradient(d_obs)
+    d32 = d_obs.astype(np.float32)
+    res = {}
+    for mode in (wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16):
+        prop = wp.Propagator.from_problem(p0, snap_mode=mode, ckpt_interval=9)
+        res[mode] = prop.gradient(p0.wavelet, p0.src, p0.rec, d32)
+        prop.close()
+    g, J = res[wp.SNAP_FULL_FP32]
+    assert abs(J - J_ref) <= 1e-5 * J_ref
+    assert rel(g, g_ref) <= 1e-4
+    # FP32 checkpoints recompute bit-identical forward wavefields
+    np.testing.assert_array_equal(res[wp.SNAP_CKPT_FP32][0], g)
+    # 16-bit checkpoints: stated error bound of the storage
+    assert rel(res[wp.SNAP_CKPT_BF16][0], g_ref) <= 2e-2
+    assert rel(res[wp.SNAP_CKPT_FP16][0], g_ref) <= 2e-3
+
+
+def test_backward_matches_oracle(wp):
+    """prop_forward_saved + prop_backward (autograd form): gradient w.r.t. m
+    and w.r.t. the wavelet for an arbitrary trace cotangent."""
+    p, p0, _ = grad_problem(nt=60)
+    rng = np.random.default_rng(9)
+    resid = rng.standard_normal((p0.rec.shape[0], p0.nt)).astype(np.float32)
+    g_ref, q_ref = oracle.Problem(p0).backward(resid)
+    prop = wp.Propagator.from_problem(p0)
+    prop.forward(p0.wavelet, p0.src, p0.rec, save=True)
+    g, q = prop.backward(resid, nsrc=p0.src.shape[0])
+    assert rel(g, g_ref) <= 1e-4
+    assert rel(q, q_ref) <= TOL
+
+
+def test_determinism(wp):
+    p = ragged_tti(8, nt=40)
+    prop = wp.Propagator.from_problem(p)
+    a = prop.forward(p.wavelet, p.src, p.rec)
+    b = prop.forward(p.wavelet, p.src, p.rec)
+    np.testing.assert_array_equal(a, b)
+
+
+def test_eps_delta_collapse_gpu(wp):
+    """eps = delta = 0: p and r stay identical on the GPU (same expressions)."""
+    p = ragged_tti(8, nt=40)
+    for k in ("eps", "delta"):
+        p.model[k] = np.zeros_like(p.model[k])
+    prop = wp.Propagator.from_problem(p)
+    prop.forward(p.wavelet, p.src, p.rec)
+    st = prop.get_state()
+    np.testing.assert_array_equal(st[0], st[1])
+    np.testing.assert_array_equal(st[2], st[3])
+
+
+def random_tti_model(shape, seed):
+    rng = np.random.default_rng(seed)
+    f = lambda lo, hi: rng.uniform(lo, hi, shape).astype(np.float32)
+    eps = f(0.0, 0.3)
+    return {"vp": f(1.5, 4.5), "eps": eps, "delta": (eps * f(0.0, 0.5)).astype(np.float32),
+            "theta": f(0.0, 40 * synth.DEG), "phi": f(0.0, 90 * synth.DEG)}
+
+
+def sample_points(shape, n, seed):
+    """Sampled outputs: random interior points plus every corner / face / edge class."""
+    NX, NY, NZ = shape
+    rng = np.random.default_rng(seed)
+    pts = [(rng.integers(NX), rng.integers(NY), rng.integers(NZ)) for _ in range(n)]
+    for x in (0, 1, NX // 2, NX - 2, NX - 1):
+        for y in (0, NY // 3, NY - 1):
+            for z in (0, 5, NZ - 3, NZ - 1):
+                pts.append((x, y, z))
+    return np.array([(x * NY + y) * NZ + z for x, y, z in pts], np.int64)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_one_step_sampled_full_size(wp, adjoint):
+    """Industry-scale TTI grid (800x800x400 + 40-cell layer = 880x880x480),
+    space order 12: one step from a seeded random state; the oracle evaluates
+    the step at sampled points (interior, faces, edges, corners)."""
+    nx, ny, nz, nbl, h = 800, 800, 400, 40, 12.5
+    model = random_tti_model((nx, ny, nz), 77)
+    dt = synth.cfl_dt(h, float(np.max(model["vp"] * np.sqrt(1 + 2 * model["eps"]))))
+    p = synth.Problem(synth.TTI, nx, ny, nz, nbl, h, 12, 10, dt, model,
+                      np.zeros((1, 3), np.float32), np.zeros((1, 10), np.float32),
+                      np.zeros((1, 3), np.float32))
+    prop = wp.Propagator.from_problem(p)
+    shape = prop.grid
+    rng = np.random.default_rng(5)
+    state = [rng.standard_normal(shape, dtype=np.float32) for _ in range(4)]
+    prop.set_state(state)          # p^n, r^n, p^{n-1}, r^{n-1}
+    prop.step(1, adjoint=adjoint)
+    out = prop.get_state()
+    prop.close()
+    idx = sample_points(shape, 400, 6)
+    ref = oracle.tti_step_points(p, (state[2], state[0], state[3], state[1]), idx, adjoint=adjoint)
+    got = np.stack([out[0].reshape(-1)[idx], out[1].reshape(-1)[idx]], axis=1)
+    # compare the increment over 2u^n - u^{n-1} scale: absolute error relative
+    # to the largest sampled value
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err <= TOL, err
