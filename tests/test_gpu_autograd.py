@@ -1,0 +1,90 @@
+"""torch.autograd path: TTI modelling with checkpointed adjoint-state
+gradients; Taylor test through autograd and agreement with the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import paper_2004_10519_gb300 as wp
+    from paper_2004_10519_gb300 import autograd as ag
+    wp.lib()
+    return torch, wp, ag
+
+
+def problem(nt=90):
+    nx, ny, nz, h, nbl = 28, 24, 30, 10.0, 6
+    m = synth.layered_tti(nx, ny, nz, 31, noise_sigma=3.0, smooth_sigma=1.5)
+    vmax = float(np.max(m["vp"] * np.sqrt(1 + 2 * m["eps"])))
+    dt = synth.cfl_dt(h, vmax)
+    src = np.array([[nx * h / 2 + 0.4, ny * h / 2 - 0.3, 2.2 * h]], np.float32)
+    wav = synth.ricker(20.0, dt, nt)[None]
+    rec = synth.carpet_receivers(5.0, 5.0, 3 * h, 9, 8, 1.5 * h)
+    p = synth.Problem(synth.TTI, nx, ny, nz, nbl, h, 8, nt, dt, m, src, wav, rec)
+    p.vdamp = vmax * 1000.0
+    return p
+
+
+@pytest.mark.parametrize("snap", ["full", "ckpt32", "bf16"])
+def test_taylor_through_autograd(env, snap):
+    torch, wp, ag = env
+    dev = torch.device("cuda", 0)
+    p = problem()
+    mode = {"full": wp.SNAP_FULL_FP32, "ckpt32": wp.SNAP_CKPT_FP32, "bf16": wp.SNAP_CKPT_BF16}[snap]
+    spec = ag.tti_spec_from_problem(p, dev, snap_mode=mode, ckpt_interval=10)
+    d_obs = torch.from_numpy(oracle.Problem(p).forward().astype(np.float32)).to(dev)
+    vp0 = torch.from_numpy(synth.smooth_model(p.model, 2.0)["vp"]).to(dev)
+    m0 = (1.0 / (vp0.double() * 1000) ** 2).float().requires_grad_(True)
+    wav = torch.from_numpy(p.wavelet).to(dev)
+
+    def J(m):
+        tr = ag.TTIModelling.apply(m, wav, spec)
+        return 0.5 * torch.sum((tr.double() - d_obs.double()) ** 2)
+
+    J0 = J(m0)
+    J0.backward()
+    g = m0.grad.double()
+    dm = torch.from_numpy(synth.perturbation(tuple(m0.shape), 2, 5)).to(dev).double() * m0.detach().double() * 0.03
+    lin = float(torch.sum(g * dm))
+    e1, e2 = [], []
+    with torch.no_grad():
+        for hh in (1.0, 0.5, 0.25, 0.125):
+            Jh = float(J((m0.double() + hh * dm).float()))
+            e1.append(abs(Jh - float(J0)))
+            e2.append(abs(Jh - float(J0) - hh * lin))
+    s1 = [math.log(e1[i] / e1[i + 1], 2) for i in range(3)]
+    s2 = [math.log(e2[i] / e2[i + 1], 2) for i in range(3)]
+    assert all(abs(s - 1.0) < 0.15 for s in s1), s1
+    if snap != "bf16":
+        # exact gradient of the FP32 forward (up to FP32 rounding): second order
+        assert all(s > 1.8 for s in s2[:2]), (s2, e2)
+    else:
+        # BF16 checkpoints: first-order term still dominated by the gradient
+        assert e2[-1] < 0.1 * e1[-1], (e1, e2)
+
+
+def test_autograd_gradient_matches_oracle(env):
+    torch, wp, ag = env
+    dev = torch.device("cuda", 0)
+    p = problem(nt=70)
+    rng = np.random.default_rng(2)
+    gtr = rng.standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    g_ref, q_ref = oracle.Problem(p).backward(gtr)
+    spec = ag.tti_spec_from_problem(p, dev)
+    m = torch.from_numpy((1.0 / (p.model["vp"].astype(np.float64) * 1000) ** 2).astype(np.float32)).to(dev)
+    m.requires_grad_(True)
+    wav = torch.from_numpy(p.wavelet).to(dev).requires_grad_(True)
+    tr = ag.TTIModelling.apply(m, wav, spec)
+    tr.backward(torch.from_numpy(gtr).to(dev))
+    gm = m.grad.cpu().numpy().astype(np.float64)
+    gw = wav.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gm - g_ref) / np.linalg.norm(g_ref) <= 1e-4
+    assert np.linalg.norm(gw - q_ref) / np.linalg.norm(q_ref) <= 1e-5
