@@ -152,6 +152,27 @@ float prop_dt(const prop_t *p);
  * handle's stream).  Used for roofline accounting. */
 int prop_kernel_time(const prop_t *p, double *ms, long long *launches);
 
+/* Forward modelling that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc, e.g. an
+ * application whose own allocator has already reserved the GPU's memory, or
+ * a latency-bound service that forbids device allocation after start-up
+ * (cudaMalloc/cudaFree can synchronize the device).  It computes exactly what
+ * prop_create(desc, model, cuda_stream) + prop_forward(...) + prop_destroy
+ * would, with the same arguments, conventions and error codes, but every
+ * device buffer it needs lives in one static device array of 48 MiB that the
+ * library keeps on each GPU where it is used, from the first call there until
+ * the process exits.  Problems that do not fit (TTI needs about 60 bytes per
+ * computational grid point, elastic about 48, plus the wavelet, traces and
+ * point tables) are rejected with PROP_EINVAL and a message giving the size.
+ * The first call on a device looks up the array's address; make that first
+ * call before starting any stream capture on that device.  All calls share
+ * the array (contents are cleared as needed on each call): calls that overlap
+ * on the GPU -- concurrent streams or host threads -- race and must be
+ * serialised by the caller.  Errors are reported through prop_last_error(NULL). */
+int prop_forward_noalloc(const prop_desc *desc, const float *const *model, const float *wavelet,
+                         const float *src_xyz, int nsrc, const float *rec_xyz, int nrec,
+                         float *traces, void *cuda_stream);
+
 void prop_destroy(prop_t *p);                 /* NULL-safe */
 
 /* Message of the last error on this handle; with p == NULL, the last

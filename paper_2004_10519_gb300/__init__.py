@@ -27,7 +27,7 @@ ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA
 ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_forward_saved", "prop_backward", "prop_grid_dims", "prop_set_state",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
-               "prop_last_error")
+               "prop_last_error", "prop_forward_noalloc")
 
 
 class PropDesc(C.Structure):

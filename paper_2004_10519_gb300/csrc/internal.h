@@ -130,6 +130,11 @@ void prof_begin(prop_s *P, int id);
 void prof_end(prop_s *P, int id);
 void k_lame(prop_s *P);
 
+// FD weights from the moment conditions (FP64 solve, FP32 result) and the
+// maximum of the discrete derivative symbol (CFL bound)
+bool fd_weights(int M, float *c, float *bst);
+double symbol_max(const float *w, int M, bool stag);
+
 // error helpers
 int wp_fail(prop_s *P, int code, const std::string &msg);
 int wp_cuda(prop_s *P, cudaError_t e, const char *what);

@@ -95,7 +95,7 @@ static bool solve_dense(int n, std::vector<double> &A, std::vector<double> &b)
     return true;
 }
 
-static bool fd_weights(int M, float *c, float *bst)
+bool fd_weights(int M, float *c, float *bst)
 {
     for (int stag = 0; stag < 2; stag++) {
         std::vector<double> A(M * M), b(M, 0.0);
@@ -113,7 +113,7 @@ static bool fd_weights(int M, float *c, float *bst)
 }
 
 // max over kappa of |sum_k 2 w_k sin(s_k kappa)| (s_k = k or k - 1/2)
-static double symbol_max(const float *w, int M, bool stag)
+double symbol_max(const float *w, int M, bool stag)
 {
     double mx = 0.0;
     for (int i = 0; i <= 4096; i++) {
