@@ -111,7 +111,9 @@ class Clocks:
 
 def elastic_workload(small=False):
     if small:
-        return synth.elastic_random(n=64, nbl=20, so=8, nt=200)
+        # profiling case: 160^3 + 20-cell layer = 200^3 points, 32 MB per field
+        # (working set ~0.7 GB > L2), 100 steps
+        return synth.elastic_random(n=160, nbl=20, so=8, nt=100)
     return synth.elastic_random()      # 256^3 @ 10 m + 20, so 8, 1000 steps
 
 
@@ -167,6 +169,100 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def aggregate(ms, units_per_rank, dist=None, device=None):
+    """Whole-job throughput of independent replicas: every rank processes
+    its own units (shots); time = max over ranks; value = all units / time.
+    Returns (max_ms, units_per_second)."""
+    world = 1
+    if dist is not None and dist.is_initialized():
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, units_per_rank * world / (ms / 1e3)
+
+
+def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
+    """TTI so-12 forward and adjoint step rates on the industry-scale grid
+    (880 x 880 x 480 computational points) from a seeded random state; the
+    model is uniform random within the workload's ranges (content does not
+    change the work)."""
+    rng = np.random.default_rng(7)
+    f = lambda lo, hi: rng.uniform(lo, hi, (nx, ny, nz)).astype(np.float32)
+    eps = f(0.0, 0.3)
+    model = [f(1.5, 4.5), eps, (eps * f(0.0, 0.5)).astype(np.float32), f(0.0, 0.7), f(0.0, 1.57)]
+    vmax = 4.5 * np.sqrt(1.6)
+    dt = synth.cfl_dt(h, vmax)
+    prop = wp.Propagator(wp.PROP_TTI, (nx, ny, nz), nbl, h, so, 10, model, dt=dt,
+                         stream=torch.cuda.current_stream(dev).cuda_stream)
+    del model
+    N = int(np.prod(prop.grid))
+    st = [torch.randn(prop.grid, device=dev) for _ in range(4)]
+    prop.set_state(st)
+    del st
+    out = {}
+    for adj, key, kid in ((False, "tti_forward", wp.K_TTI_FWD), (True, "tti_adjoint", wp.K_TTI_ADJ)):
+        prop.step(5, adjoint=adj)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        prop.step(steps, adjoint=adj)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prop.profile(True)
+        prop.step(10, adjoint=adj)
+        kms, kn = prop.kernel_stats(kid)
+        prop.profile(False)
+        out[key] = {"gpts_per_s": N / (ms / 1e3) / 1e9, "ms_per_step": ms,
+                    "kernel_ms_per_step": kms / max(kn, 1),
+                    "alg_gbs": ALG_BYTES["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e9}
+    prop.close()
+    out["grid"] = list(prop.grid)
+    out["space_order"] = so
+    return out
+
+
+def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
+    """TTI FWI gradient (so 12) shots/hour on the 400x400x300 + 40 workload
+    for several wavefield-storage modes at equal nt."""
+    if small:
+        true, p0 = synth.tti_gradient_problem(nx=120, ny=120, nz=100, nt=nt)
+    else:
+        true, p0 = synth.tti_gradient_problem(nt=nt)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    ptrue = wp.Propagator.from_problem(true, stream=stream)
+    d_obs = ptrue.forward(torch.from_numpy(true.wavelet).to(dev), torch.from_numpy(true.src).to(dev),
+                          torch.from_numpy(true.rec).to(dev))
+    ptrue.close()
+    wav = torch.from_numpy(p0.wavelet).to(dev)
+    src = torch.from_numpy(p0.src).to(dev)
+    rec = torch.from_numpy(p0.rec).to(dev)
+    res = {}
+    ref = None
+    for mode in modes:
+        prop = wp.Propagator.from_problem(p0, snap_mode=mode, stream=stream)
+        try:
+            g, J = prop.gradient(wav, src, rec, d_obs)          # warm-up + result
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g, J = prop.gradient(wav, src, rec, d_obs)
+            torch.cuda.synchronize()
+            s = time.perf_counter() - t0
+            gd = g.double()
+            if ref is None:
+                ref = gd
+            err = float(torch.linalg.norm(gd - ref) / torch.linalg.norm(ref))
+            res[str(mode)] = {"seconds": s, "shots_per_hour": 3600.0 / s, "misfit": J,
+                              "rel_l2_vs_first_mode": err}
+        except wp.PropError as e:
+            res[str(mode)] = {"error": str(e)}
+        prop.close()
+    return {"nt": nt, "grid": [p0.nx + 2 * p0.nbl, p0.ny + 2 * p0.nbl, p0.nz + 2 * p0.nbl],
+            "modes": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -175,12 +271,28 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--extra", default="", help="comma list: tti, grad (secondary measurements)")
+    ap.add_argument("--grad-nt", type=int, default=600)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
 
     import torch
     import paper_2004_10519_gb300 as wp
+    extras = [e for e in args.extra.split(",") if e]
+    if extras:
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        out = {}
+        if "tti" in extras:
+            out["tti"] = tti_throughput(wp, torch, dev)
+        if "grad" in extras:
+            out["grad"] = gradient_shots_per_hour(
+                wp, torch, dev, args.grad_nt,
+                [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
+                small=args.small)
+        print(json.dumps(out), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -229,12 +341,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     upd = N * 2 * nt * args.steps * world
-    value = upd / (ms / 1e3) / 1e9
+    ms, rate = aggregate(ms, N * 2 * nt * args.steps, dist, dev)
+    value = rate / 1e9
 
     # roofline of the dominant kernel: per-launch CUDA events on the library's
     # stream, forward step (the adjoint step is reported beside it)

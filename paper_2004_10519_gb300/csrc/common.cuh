@@ -17,25 +17,21 @@ WP_DEV float layer_depth(float s, int nbl, int n)
     return s < lo ? lo - s : (s > hi ? s - hi : 0.f);
 }
 
-// TTI damping rate at a node: sum over axes of sig0 * (d/L)^2, L = nbl*h.
+// TTI damping rate at a node: sum over axes of sig0 * (d/L)^2, L = nbl*h
+// (per-axis table).
 WP_DEV float tti_sigma(const GridDev &g, int x, int y, int z)
 {
-    if (g.nbl <= 0) return 0.f;
-    float inv = 1.f / (float)g.nbl;
-    float dx = layer_depth((float)x, g.nbl, g.px) * inv;
-    float dy = layer_depth((float)y, g.nbl, g.py) * inv;
-    float dz = layer_depth((float)z, g.nbl, g.pz) * inv;
-    return g.sig0 * (dx * dx + dy * dy + dz * dz);
+    return __ldg(g.tab + x) + __ldg(g.tab + g.NX + y) + __ldg(g.tab + g.NX + g.NY + z);
 }
 
-// Cerjan taper exp(-(a d)^2) per axis at continuous position (sx, sy, sz).
+// Cerjan taper: product over axes of exp(-(0.015 d)^2) at the position
+// (sx, sy, sz), each coordinate a node i or a half point i + 1/2 (table).
 WP_DEV float cerjan(const GridDev &g, float sx, float sy, float sz)
 {
-    if (g.nbl <= 0) return 1.f;
-    float dx = g.cer * layer_depth(sx, g.nbl, g.px);
-    float dy = g.cer * layer_depth(sy, g.nbl, g.py);
-    float dz = g.cer * layer_depth(sz, g.nbl, g.pz);
-    return expf(-(dx * dx + dy * dy + dz * dz));
+    const int ix = (int)sx, iy = (int)sy, iz = (int)sz;
+    const int hx = (sx - ix) > 0.25f, hy = (sy - iy) > 0.25f, hz = (sz - iz) > 0.25f;
+    return __ldg(g.tab + 2 * ix + hx) * __ldg(g.tab + 2 * g.NX + 2 * iy + hy) *
+           __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * iz + hz);
 }
 
 // load with zero extension outside the computational grid

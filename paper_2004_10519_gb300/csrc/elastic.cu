@@ -106,55 +106,6 @@ struct Fields9 {
     float *f[9];
 };
 
-template <int M>
-__global__ void __launch_bounds__(TZ *TY)
-el_v_kernel(GridDev g, FDW w, Fields9 s, const float *__restrict__ bu, int *flag, int check)
-{
-    EL_IDX
-    float d[3];
-    div_tau<M>(g, w, s.f[3], s.f[4], s.f[5], s.f[6], s.f[7], s.f[8], x, y, z, d);
-    const float c = g.dt * g.ih;
-    const float fx = (float)x, fy = (float)y, fz = (float)z;
-    const float gx = cerjan(g, fx + 0.5f, fy, fz), gy = cerjan(g, fx, fy + 0.5f, fz),
-                gz = cerjan(g, fx, fy, fz + 0.5f);
-    const float vx = gx * (s.f[0][q] + c * bavg(bu, g, 0, x, y, z) * d[0]);
-    const float vy = gy * (s.f[1][q] + c * bavg(bu, g, 1, x, y, z) * d[1]);
-    const float vz = gz * (s.f[2][q] + c * bavg(bu, g, 2, x, y, z) * d[2]);
-    s.f[0][q] = vx;
-    s.f[1][q] = vy;
-    s.f[2][q] = vz;
-    if (check && !(isfinite(vx) && isfinite(vy) && isfinite(vz))) atomicOr(flag, 1);
-}
-
-template <int M>
-__global__ void __launch_bounds__(TZ *TY)
-el_t_kernel(GridDev g, FDW w, Fields9 s, const float *__restrict__ lam,
-            const float *__restrict__ mu, int *flag, int check)
-{
-    EL_IDX
-    float e[6];
-    strain<M>(g, w, s.f[0], s.f[1], s.f[2], x, y, z, e);
-    const float c = g.dt * g.ih;
-    const float l = __ldg(lam + q), m2 = 2.f * __ldg(mu + q);
-    const float tr = e[0] + e[1] + e[2];
-    const float fx = (float)x, fy = (float)y, fz = (float)z;
-    const float gn = cerjan(g, fx, fy, fz);
-    float out[6];
-    out[0] = gn * (s.f[3][q] + c * (l * tr + m2 * e[0]));
-    out[1] = gn * (s.f[4][q] + c * (l * tr + m2 * e[1]));
-    out[2] = gn * (s.f[5][q] + c * (l * tr + m2 * e[2]));
-    out[3] = cerjan(g, fx + 0.5f, fy + 0.5f, fz) * (s.f[6][q] + c * muavg(mu, g, 0, 1, x, y, z) * e[3]);
-    out[4] = cerjan(g, fx + 0.5f, fy, fz + 0.5f) * (s.f[7][q] + c * muavg(mu, g, 0, 2, x, y, z) * e[4]);
-    out[5] = cerjan(g, fx, fy + 0.5f, fz + 0.5f) * (s.f[8][q] + c * muavg(mu, g, 1, 2, x, y, z) * e[5]);
-    bool ok = true;
-#pragma unroll
-    for (int i = 0; i < 6; i++) {
-        s.f[3 + i][q] = out[i];
-        ok = ok && isfinite(out[i]);
-    }
-    if (check && !ok) atomicOr(flag, 1);
-}
-
 // adjoint pass 1 (pointwise): t = g tbar (in place), sigma = C t -> sg[0..5]
 __global__ void __launch_bounds__(TZ *TY)
 el_adj_pre_kernel(GridDev g, Fields9 s, Fields9 sg, const float *__restrict__ lam,
@@ -300,6 +251,411 @@ el_grad_gather_kernel(GridDev g, const float *__restrict__ ep0, const float *__r
     gb[q] += 0.5f * s;
 }
 
+// ---------------------------------------------------------------------------
+// Tiled forward passes.  A CTA owns an FZ x FY tile of (y, z) columns and
+// streams along x over a chunk of planes.  x-derivatives come from
+// per-thread register queues (2M values), y/z-derivatives from shared-memory
+// planes with an M-point halo; values outside the grid read as 0.
+// ---------------------------------------------------------------------------
+constexpr int FZ = 32, FY = 16, FT = FZ * FY;
+
+WP_DEV float lz(const float *__restrict__ f, const GridDev &g, int x, int y, int z)
+{
+    return (x >= 0 && x < g.NX && y >= 0 && y < g.NY && z >= 0 && z < g.NZ)
+               ? __ldg(f + gidx(g, x, y, z)) : 0.f;
+}
+// taper of one staggered position from the per-axis tables
+WP_DEV float tp(const GridDev &g, int x, int hx, int y, int hy, int z, int hz)
+{
+    return __ldg(g.tab + 2 * x + hx) * __ldg(g.tab + 2 * g.NX + 2 * y + hy) *
+           __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * z + hz);
+}
+
+// velocity pass: v <- g (v + dt b_avg div tau)
+template <int M>
+__global__ void __launch_bounds__(FT, 2)
+el_v_tiled(GridDev g, FDW w, Fields9 s, const float *__restrict__ bu, int *flag, int check, int xc)
+{
+    constexpr int HY = FY + 2 * M, HZ = FZ + 2 * M, Q = 2 * M;
+    __shared__ float s_xy[HY][FZ], s_yy[HY][FZ], s_yz[HY][HZ], s_xz[FY][HZ], s_zz[FY][HZ];
+    const int tz = threadIdx.x, ty = threadIdx.y;
+    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z = z0 + tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const float *txx = s.f[3], *tyy = s.f[4], *tzz = s.f[5], *txy = s.f[6], *txz = s.f[7], *tyz = s.f[8];
+    // queues: qxx[j] = txx[x-M+1+j] (D+x), qxy[j] = txy[x-M+j], qxz[j] = txz[x-M+j] (D-x)
+    float qxx[Q], qxy[Q], qxz[Q];
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        qxx[j] = lz(txx, g, xa - M + 1 + j, y, z);
+        qxy[j] = lz(txy, g, xa - M + j, y, z);
+        qxz[j] = lz(txz, g, xa - M + j, y, z);
+    }
+    const bool act = y < g.NY && z < g.NZ;
+    const float c = g.dt * g.ih;
+    const long long sx = (long long)g.NY * g.NZ;
+    const int y1 = min(y + 1, g.NY - 1), z1 = min(z + 1, g.NZ - 1);
+    for (int x = xa; x < xb; x++) {
+        qxx[Q - 1] = lz(txx, g, x + M, y, z);
+        qxy[Q - 1] = lz(txy, g, x + M - 1, y, z);
+        qxz[Q - 1] = lz(txz, g, x + M - 1, y, z);
+        __syncthreads();
+        s_xy[ty + M][tz] = qxy[M];
+        s_xz[ty][tz + M] = qxz[M];
+        s_yy[ty + M][tz] = lz(tyy, g, x, y, z);
+        s_zz[ty][tz + M] = lz(tzz, g, x, y, z);
+        s_yz[ty + M][tz + M] = lz(tyz, g, x, y, z);
+        if (ty < M) {
+            const int ya = y0 - M + ty, yb = y0 + FY + ty;
+            s_xy[ty][tz] = lz(txy, g, x, ya, z);
+            s_yy[ty][tz] = lz(tyy, g, x, ya, z);
+            s_yz[ty][tz + M] = lz(tyz, g, x, ya, z);
+            s_xy[ty + FY + M][tz] = lz(txy, g, x, yb, z);
+            s_yy[ty + FY + M][tz] = lz(tyy, g, x, yb, z);
+            s_yz[ty + FY + M][tz + M] = lz(tyz, g, x, yb, z);
+        }
+        if (tz < M) {
+            const int za = z0 - M + tz, zb = z0 + FZ + tz;
+            s_xz[ty][tz] = lz(txz, g, x, y, za);
+            s_zz[ty][tz] = lz(tzz, g, x, y, za);
+            s_yz[ty + M][tz] = lz(tyz, g, x, y, za);
+            s_xz[ty][tz + FZ + M] = lz(txz, g, x, y, zb);
+            s_zz[ty][tz + FZ + M] = lz(tzz, g, x, y, zb);
+            s_yz[ty + M][tz + FZ + M] = lz(tyz, g, x, y, zb);
+        }
+        __syncthreads();
+        if (act) {
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+            for (int k = 1; k <= M; k++) {
+                const float b = w.b[k - 1];
+                d0 += b * ((qxx[M - 1 + k] - qxx[M - k]) +
+                           (s_xy[ty + M + k - 1][tz] - s_xy[ty + M - k][tz]) +
+                           (s_xz[ty][tz + M + k - 1] - s_xz[ty][tz + M - k]));
+                d1 += b * ((qxy[M + k - 1] - qxy[M - k]) +
+                           (s_yy[ty + M + k][tz] - s_yy[ty + M - k + 1][tz]) +
+                           (s_yz[ty + M][tz + M + k - 1] - s_yz[ty + M][tz + M - k]));
+                d2 += b * ((qxz[M + k - 1] - qxz[M - k]) +
+                           (s_yz[ty + M + k - 1][tz + M] - s_yz[ty + M - k][tz + M]) +
+                           (s_zz[ty][tz + M + k] - s_zz[ty][tz + M - k + 1]));
+            }
+            const long long q = gidx(g, x, y, z);
+            const float b0 = __ldg(bu + q);
+            const float bx = 0.5f * (b0 + __ldg(bu + (x + 1 < g.NX ? q + sx : q)));
+            const float by = 0.5f * (b0 + __ldg(bu + q + (long long)(y1 - y) * g.NZ));
+            const float bz = 0.5f * (b0 + __ldg(bu + q + (z1 - z)));
+            const float vx = tp(g, x, 1, y, 0, z, 0) * (s.f[0][q] + c * bx * d0);
+            const float vy = tp(g, x, 0, y, 1, z, 0) * (s.f[1][q] + c * by * d1);
+            const float vz = tp(g, x, 0, y, 0, z, 1) * (s.f[2][q] + c * bz * d2);
+            s.f[0][q] = vx;
+            s.f[1][q] = vy;
+            s.f[2][q] = vz;
+            if (check && !(isfinite(vx) && isfinite(vy) && isfinite(vz))) atomicOr(flag, 1);
+        }
+#pragma unroll
+        for (int j = 0; j < Q - 1; j++) {
+            qxx[j] = qxx[j + 1];
+            qxy[j] = qxy[j + 1];
+            qxz[j] = qxz[j + 1];
+        }
+    }
+}
+
+// stress pass: tau <- g (tau + dt (lambda tr(e) I + mu (grad v + grad v^T)))
+template <int M>
+__global__ void __launch_bounds__(FT, 2)
+el_t_tiled(GridDev g, FDW w, Fields9 s, const float *__restrict__ lam, const float *__restrict__ mu,
+           int *flag, int check, int xc)
+{
+    constexpr int HY = FY + 2 * M, HZ = FZ + 2 * M, Q = 2 * M;
+    __shared__ float s_vx[HY][HZ], s_vy[HY][HZ], s_vz[HY][HZ];
+    const int tz = threadIdx.x, ty = threadIdx.y;
+    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z = z0 + tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
+    // qvx[j] = vx[x-M+j] (D-x), qvy[j] = vy[x-M+1+j], qvz[j] = vz[x-M+1+j] (D+x)
+    float qvx[Q], qvy[Q], qvz[Q];
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        qvx[j] = lz(vxp, g, xa - M + j, y, z);
+        qvy[j] = lz(vyp, g, xa - M + 1 + j, y, z);
+        qvz[j] = lz(vzp, g, xa - M + 1 + j, y, z);
+    }
+    const bool act = y < g.NY && z < g.NZ;
+    const float c = g.dt * g.ih;
+    const long long sx = (long long)g.NY * g.NZ;
+    const long long dy1 = (long long)(min(y + 1, g.NY - 1) - y) * g.NZ;
+    const long long dz1 = min(z + 1, g.NZ - 1) - z;
+    for (int x = xa; x < xb; x++) {
+        qvx[Q - 1] = lz(vxp, g, x + M - 1, y, z);
+        qvy[Q - 1] = lz(vyp, g, x + M, y, z);
+        qvz[Q - 1] = lz(vzp, g, x + M, y, z);
+        __syncthreads();
+        s_vx[ty + M][tz + M] = qvx[M];
+        s_vy[ty + M][tz + M] = qvy[M - 1];
+        s_vz[ty + M][tz + M] = qvz[M - 1];
+        if (ty < M) {
+            const int ya = y0 - M + ty, yb = y0 + FY + ty;
+            s_vx[ty][tz + M] = lz(vxp, g, x, ya, z);
+            s_vy[ty][tz + M] = lz(vyp, g, x, ya, z);
+            s_vz[ty][tz + M] = lz(vzp, g, x, ya, z);
+            s_vx[ty + FY + M][tz + M] = lz(vxp, g, x, yb, z);
+            s_vy[ty + FY + M][tz + M] = lz(vyp, g, x, yb, z);
+            s_vz[ty + FY + M][tz + M] = lz(vzp, g, x, yb, z);
+        }
+        if (tz < M) {
+            const int za = z0 - M + tz, zb = z0 + FZ + tz;
+            s_vx[ty + M][tz] = lz(vxp, g, x, y, za);
+            s_vy[ty + M][tz] = lz(vyp, g, x, y, za);
+            s_vz[ty + M][tz] = lz(vzp, g, x, y, za);
+            s_vx[ty + M][tz + FZ + M] = lz(vxp, g, x, y, zb);
+            s_vy[ty + M][tz + FZ + M] = lz(vyp, g, x, y, zb);
+            s_vz[ty + M][tz + FZ + M] = lz(vzp, g, x, y, zb);
+        }
+        __syncthreads();
+        if (act) {
+            float exx = 0.f, eyy = 0.f, ezz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+            const int cy = ty + M, cz = tz + M;
+#pragma unroll
+            for (int k = 1; k <= M; k++) {
+                const float b = w.b[k - 1];
+                exx += b * (qvx[M + k - 1] - qvx[M - k]);
+                eyy += b * (s_vy[cy + k - 1][cz] - s_vy[cy - k][cz]);
+                ezz += b * (s_vz[cy][cz + k - 1] - s_vz[cy][cz - k]);
+                gxy += b * ((s_vx[cy + k][cz] - s_vx[cy - k + 1][cz]) + (qvy[M - 1 + k] - qvy[M - k]));
+                gxz += b * ((s_vx[cy][cz + k] - s_vx[cy][cz - k + 1]) + (qvz[M - 1 + k] - qvz[M - k]));
+                gyz += b * ((s_vy[cy][cz + k] - s_vy[cy][cz - k + 1]) + (s_vz[cy + k][cz] - s_vz[cy - k + 1][cz]));
+            }
+            const long long q = gidx(g, x, y, z);
+            const long long dx1 = x + 1 < g.NX ? sx : 0;
+            const float l = __ldg(lam + q), m0 = __ldg(mu + q);
+            const float mx = __ldg(mu + q + dx1), my = __ldg(mu + q + dy1), mz = __ldg(mu + q + dz1);
+            const float mxy = 0.25f * (m0 + mx + my + __ldg(mu + q + dx1 + dy1));
+            const float mxz = 0.25f * (m0 + mx + mz + __ldg(mu + q + dx1 + dz1));
+            const float myz = 0.25f * (m0 + my + mz + __ldg(mu + q + dy1 + dz1));
+            const float tr = exx + eyy + ezz, m2 = 2.f * m0;
+            const float gn = tp(g, x, 0, y, 0, z, 0);
+            const float o0 = gn * (s.f[3][q] + c * (l * tr + m2 * exx));
+            const float o1 = gn * (s.f[4][q] + c * (l * tr + m2 * eyy));
+            const float o2 = gn * (s.f[5][q] + c * (l * tr + m2 * ezz));
+            const float o3 = tp(g, x, 1, y, 1, z, 0) * (s.f[6][q] + c * mxy * gxy);
+            const float o4 = tp(g, x, 1, y, 0, z, 1) * (s.f[7][q] + c * mxz * gxz);
+            const float o5 = tp(g, x, 0, y, 1, z, 1) * (s.f[8][q] + c * myz * gyz);
+            s.f[3][q] = o0; s.f[4][q] = o1; s.f[5][q] = o2;
+            s.f[6][q] = o3; s.f[7][q] = o4; s.f[8][q] = o5;
+            if (check && !(isfinite(o0) && isfinite(o1) && isfinite(o2) && isfinite(o3) &&
+                           isfinite(o4) && isfinite(o5)))
+                atomicOr(flag, 1);
+        }
+#pragma unroll
+        for (int j = 0; j < Q - 1; j++) {
+            qvx[j] = qvx[j + 1];
+            qvy[j] = qvy[j + 1];
+            qvz[j] = qvz[j + 1];
+        }
+    }
+}
+
+// ---- tiled adjoint passes -------------------------------------------------
+// C (g tbar) at a node, diagonal component c (0..2); 0 outside the grid
+WP_DEV float adj_sdiag(const GridDev &g, const Fields9 &s, const float *__restrict__ lam,
+                       const float *__restrict__ mu, int c, int x, int y, int z)
+{
+    if (!(x >= 0 && x < g.NX && y >= 0 && y < g.NY && z >= 0 && z < g.NZ)) return 0.f;
+    const long long q = gidx(g, x, y, z);
+    const float gn = tp(g, x, 0, y, 0, z, 0);
+    const float t0 = gn * s.f[3][q], t1 = gn * s.f[4][q], t2 = gn * s.f[5][q];
+    const float tc = c == 0 ? t0 : (c == 1 ? t1 : t2);
+    return __ldg(lam + q) * (t0 + t1 + t2) + 2.f * __ldg(mu + q) * tc;
+}
+// C (g tbar) on an edge: mu averaged over the 4 nodes of the (A1, A2) plane
+template <int A1, int A2>
+WP_DEV float adj_sedge(const GridDev &g, const float *tc, const float *__restrict__ mu, int x,
+                       int y, int z)
+{
+    if (!(x >= 0 && x < g.NX && y >= 0 && y < g.NY && z >= 0 && z < g.NZ)) return 0.f;
+    const long long q = gidx(g, x, y, z);
+    const long long d1 = A1 == 0 ? (x + 1 < g.NX ? (long long)g.NY * g.NZ : 0)
+                                 : (y + 1 < g.NY ? (long long)g.NZ : 0);
+    const long long d2 = A2 == 1 ? (y + 1 < g.NY ? (long long)g.NZ : 0) : (z + 1 < g.NZ ? 1 : 0);
+    const float mavg = 0.25f * (__ldg(mu + q) + __ldg(mu + q + d1) + __ldg(mu + q + d2) +
+                                __ldg(mu + q + d1 + d2));
+    const float gt = tp(g, x, A1 == 0, y, (A1 == 1) || (A2 == 1), z, A2 == 2);
+    return mavg * gt * tc[q];
+}
+// b_avg * vbar at a velocity point of component c; 0 outside the grid
+WP_DEV float adj_bv(const GridDev &g, const float *__restrict__ v, const float *__restrict__ bu, int c,
+                    int x, int y, int z)
+{
+    if (!(x >= 0 && x < g.NX && y >= 0 && y < g.NY && z >= 0 && z < g.NZ)) return 0.f;
+    const long long q = gidx(g, x, y, z);
+    long long d = 0;
+    if (c == 0) d = x + 1 < g.NX ? (long long)g.NY * g.NZ : 0;
+    else if (c == 1) d = y + 1 < g.NY ? (long long)g.NZ : 0;
+    else d = z + 1 < g.NZ ? 1 : 0;
+    return 0.5f * (__ldg(bu + q) + __ldg(bu + q + d)) * v[q];
+}
+
+// adjoint velocity pass: vbar <- g (vbar - dt Dtau(C g tbar))
+template <int M>
+__global__ void __launch_bounds__(FT, 2)
+el_adj_v_tiled(GridDev g, FDW w, Fields9 s, const float *__restrict__ lam,
+               const float *__restrict__ mu, int xc)
+{
+    constexpr int HY = FY + 2 * M, HZ = FZ + 2 * M, Q = 2 * M;
+    __shared__ float s_xy[HY][FZ], s_yy[HY][FZ], s_yz[HY][HZ], s_xz[FY][HZ], s_zz[FY][HZ];
+    const int tz = threadIdx.x, ty = threadIdx.y;
+    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z = z0 + tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const float *txy = s.f[6], *txz = s.f[7], *tyz = s.f[8];
+    float qxx[Q], qxy[Q], qxz[Q];
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        qxx[j] = adj_sdiag(g, s, lam, mu, 0, xa - M + 1 + j, y, z);
+        qxy[j] = adj_sedge<0, 1>(g, txy, mu, xa - M + j, y, z);
+        qxz[j] = adj_sedge<0, 2>(g, txz, mu, xa - M + j, y, z);
+    }
+    const bool act = y < g.NY && z < g.NZ;
+    const float c = g.dt * g.ih;
+    for (int x = xa; x < xb; x++) {
+        qxx[Q - 1] = adj_sdiag(g, s, lam, mu, 0, x + M, y, z);
+        qxy[Q - 1] = adj_sedge<0, 1>(g, txy, mu, x + M - 1, y, z);
+        qxz[Q - 1] = adj_sedge<0, 2>(g, txz, mu, x + M - 1, y, z);
+        __syncthreads();
+        s_xy[ty + M][tz] = qxy[M];
+        s_xz[ty][tz + M] = qxz[M];
+        s_yy[ty + M][tz] = adj_sdiag(g, s, lam, mu, 1, x, y, z);
+        s_zz[ty][tz + M] = adj_sdiag(g, s, lam, mu, 2, x, y, z);
+        s_yz[ty + M][tz + M] = adj_sedge<1, 2>(g, tyz, mu, x, y, z);
+        if (ty < M) {
+            const int ya = y0 - M + ty, yb = y0 + FY + ty;
+            s_xy[ty][tz] = adj_sedge<0, 1>(g, txy, mu, x, ya, z);
+            s_yy[ty][tz] = adj_sdiag(g, s, lam, mu, 1, x, ya, z);
+            s_yz[ty][tz + M] = adj_sedge<1, 2>(g, tyz, mu, x, ya, z);
+            s_xy[ty + FY + M][tz] = adj_sedge<0, 1>(g, txy, mu, x, yb, z);
+            s_yy[ty + FY + M][tz] = adj_sdiag(g, s, lam, mu, 1, x, yb, z);
+            s_yz[ty + FY + M][tz + M] = adj_sedge<1, 2>(g, tyz, mu, x, yb, z);
+        }
+        if (tz < M) {
+            const int za = z0 - M + tz, zb = z0 + FZ + tz;
+            s_xz[ty][tz] = adj_sedge<0, 2>(g, txz, mu, x, y, za);
+            s_zz[ty][tz] = adj_sdiag(g, s, lam, mu, 2, x, y, za);
+            s_yz[ty + M][tz] = adj_sedge<1, 2>(g, tyz, mu, x, y, za);
+            s_xz[ty][tz + FZ + M] = adj_sedge<0, 2>(g, txz, mu, x, y, zb);
+            s_zz[ty][tz + FZ + M] = adj_sdiag(g, s, lam, mu, 2, x, y, zb);
+            s_yz[ty + M][tz + FZ + M] = adj_sedge<1, 2>(g, tyz, mu, x, y, zb);
+        }
+        __syncthreads();
+        if (act) {
+            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+            for (int k = 1; k <= M; k++) {
+                const float b = w.b[k - 1];
+                d0 += b * ((qxx[M - 1 + k] - qxx[M - k]) +
+                           (s_xy[ty + M + k - 1][tz] - s_xy[ty + M - k][tz]) +
+                           (s_xz[ty][tz + M + k - 1] - s_xz[ty][tz + M - k]));
+                d1 += b * ((qxy[M + k - 1] - qxy[M - k]) +
+                           (s_yy[ty + M + k][tz] - s_yy[ty + M - k + 1][tz]) +
+                           (s_yz[ty + M][tz + M + k - 1] - s_yz[ty + M][tz + M - k]));
+                d2 += b * ((qxz[M + k - 1] - qxz[M - k]) +
+                           (s_yz[ty + M + k - 1][tz + M] - s_yz[ty + M - k][tz + M]) +
+                           (s_zz[ty][tz + M + k] - s_zz[ty][tz + M - k + 1]));
+            }
+            const long long q = gidx(g, x, y, z);
+            s.f[0][q] = tp(g, x, 1, y, 0, z, 0) * (s.f[0][q] - c * d0);
+            s.f[1][q] = tp(g, x, 0, y, 1, z, 0) * (s.f[1][q] - c * d1);
+            s.f[2][q] = tp(g, x, 0, y, 0, z, 1) * (s.f[2][q] - c * d2);
+        }
+#pragma unroll
+        for (int j = 0; j < Q - 1; j++) {
+            qxx[j] = qxx[j + 1];
+            qxy[j] = qxy[j + 1];
+            qxz[j] = qxz[j + 1];
+        }
+    }
+}
+
+// adjoint stress pass: tbar <- g tbar - dt S(b_avg vbar)
+template <int M>
+__global__ void __launch_bounds__(FT, 2)
+el_adj_t_tiled(GridDev g, FDW w, Fields9 s, const float *__restrict__ bu, int xc)
+{
+    constexpr int HY = FY + 2 * M, HZ = FZ + 2 * M, Q = 2 * M;
+    __shared__ float s_vx[HY][HZ], s_vy[HY][HZ], s_vz[HY][HZ];
+    const int tz = threadIdx.x, ty = threadIdx.y;
+    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z = z0 + tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
+    float qvx[Q], qvy[Q], qvz[Q];
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        qvx[j] = adj_bv(g, vxp, bu, 0, xa - M + j, y, z);
+        qvy[j] = adj_bv(g, vyp, bu, 1, xa - M + 1 + j, y, z);
+        qvz[j] = adj_bv(g, vzp, bu, 2, xa - M + 1 + j, y, z);
+    }
+    const bool act = y < g.NY && z < g.NZ;
+    const float c = g.dt * g.ih;
+    for (int x = xa; x < xb; x++) {
+        qvx[Q - 1] = adj_bv(g, vxp, bu, 0, x + M - 1, y, z);
+        qvy[Q - 1] = adj_bv(g, vyp, bu, 1, x + M, y, z);
+        qvz[Q - 1] = adj_bv(g, vzp, bu, 2, x + M, y, z);
+        __syncthreads();
+        s_vx[ty + M][tz + M] = qvx[M];
+        s_vy[ty + M][tz + M] = qvy[M - 1];
+        s_vz[ty + M][tz + M] = qvz[M - 1];
+        if (ty < M) {
+            const int ya = y0 - M + ty, yb = y0 + FY + ty;
+            s_vx[ty][tz + M] = adj_bv(g, vxp, bu, 0, x, ya, z);
+            s_vy[ty][tz + M] = adj_bv(g, vyp, bu, 1, x, ya, z);
+            s_vz[ty][tz + M] = adj_bv(g, vzp, bu, 2, x, ya, z);
+            s_vx[ty + FY + M][tz + M] = adj_bv(g, vxp, bu, 0, x, yb, z);
+            s_vy[ty + FY + M][tz + M] = adj_bv(g, vyp, bu, 1, x, yb, z);
+            s_vz[ty + FY + M][tz + M] = adj_bv(g, vzp, bu, 2, x, yb, z);
+        }
+        if (tz < M) {
+            const int za = z0 - M + tz, zb = z0 + FZ + tz;
+            s_vx[ty + M][tz] = adj_bv(g, vxp, bu, 0, x, y, za);
+            s_vy[ty + M][tz] = adj_bv(g, vyp, bu, 1, x, y, za);
+            s_vz[ty + M][tz] = adj_bv(g, vzp, bu, 2, x, y, za);
+            s_vx[ty + M][tz + FZ + M] = adj_bv(g, vxp, bu, 0, x, y, zb);
+            s_vy[ty + M][tz + FZ + M] = adj_bv(g, vyp, bu, 1, x, y, zb);
+            s_vz[ty + M][tz + FZ + M] = adj_bv(g, vzp, bu, 2, x, y, zb);
+        }
+        __syncthreads();
+        if (act) {
+            float exx = 0.f, eyy = 0.f, ezz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+            const int cy = ty + M, cz = tz + M;
+#pragma unroll
+            for (int k = 1; k <= M; k++) {
+                const float b = w.b[k - 1];
+                exx += b * (qvx[M + k - 1] - qvx[M - k]);
+                eyy += b * (s_vy[cy + k - 1][cz] - s_vy[cy - k][cz]);
+                ezz += b * (s_vz[cy][cz + k - 1] - s_vz[cy][cz - k]);
+                gxy += b * ((s_vx[cy + k][cz] - s_vx[cy - k + 1][cz]) + (qvy[M - 1 + k] - qvy[M - k]));
+                gxz += b * ((s_vx[cy][cz + k] - s_vx[cy][cz - k + 1]) + (qvz[M - 1 + k] - qvz[M - k]));
+                gyz += b * ((s_vy[cy][cz + k] - s_vy[cy][cz - k + 1]) + (s_vz[cy + k][cz] - s_vz[cy - k + 1][cz]));
+            }
+            const long long q = gidx(g, x, y, z);
+            const float gn = tp(g, x, 0, y, 0, z, 0);
+            s.f[3][q] = gn * s.f[3][q] - c * exx;
+            s.f[4][q] = gn * s.f[4][q] - c * eyy;
+            s.f[5][q] = gn * s.f[5][q] - c * ezz;
+            s.f[6][q] = tp(g, x, 1, y, 1, z, 0) * s.f[6][q] - c * gxy;
+            s.f[7][q] = tp(g, x, 1, y, 0, z, 1) * s.f[7][q] - c * gxz;
+            s.f[8][q] = tp(g, x, 0, y, 1, z, 1) * s.f[8][q] - c * gyz;
+        }
+#pragma unroll
+        for (int j = 0; j < Q - 1; j++) {
+            qvx[j] = qvx[j + 1];
+            qvy[j] = qvy[j + 1];
+            qvz[j] = qvz[j + 1];
+        }
+    }
+}
+
 template <int M>
 int launch_step(prop_s *P, float *const *S, bool adjoint)
 {
@@ -309,17 +665,18 @@ int launch_step(prop_s *P, float *const *S, bool adjoint)
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
     prof_begin(P, adjoint ? 3 : 2);
     if (!adjoint) {
-        el_v_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, P->bu, P->flag, P->d.check_nan);
-        el_t_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, P->lam, P->mu, P->flag,
-                                                   P->d.check_nan);
+        const int xc = P->xchunk;
+        dim3 fb(FZ, FY, 1), fg((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+        el_v_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->bu, P->flag, P->d.check_nan, xc);
+        el_t_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->lam, P->mu, P->flag,
+                                                P->d.check_nan, xc);
         P->kern_launches += 2;
     } else {
-        Fields9 sg;
-        for (int i = 0; i < 9; i++) sg.f[i] = P->tmp[i];
-        el_adj_pre_kernel<<<grd, blk, 0, P->stream>>>(g, s, sg, P->lam, P->mu);
-        el_adj_v_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, sg, P->bu);
-        el_adj_t_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, sg);
-        P->kern_launches += 3;
+        const int xc = P->xchunk;
+        dim3 fb(FZ, FY, 1), fg((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+        el_adj_v_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->lam, P->mu, xc);
+        el_adj_t_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->bu, xc);
+        P->kern_launches += 2;
     }
     prof_end(P, adjoint ? 3 : 2);
     WP_CK(P, cudaGetLastError());

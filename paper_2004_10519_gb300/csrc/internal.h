@@ -18,6 +18,11 @@ struct GridDev {
     float h, ih, dt;         // spacing, 1/h, time step
     float sig0;              // TTI damping: sigma(d) = sig0 * (d/L)^2 per axis [1/s]
     float cer;               // elastic Cerjan coefficient per cell (0.015)
+    // per-axis absorbing-layer tables (device):
+    //   TTI:     sigma_x[NX], sigma_y[NY], sigma_z[NZ]  (sigma = sum of the three)
+    //   elastic: taper_x[2 NX], taper_y[2 NY], taper_z[2 NZ]; entry 2i is the
+    //            node i, 2i+1 the half point i+1/2 (taper = product of three)
+    const float *tab;
 };
 
 // Finite-difference weights (FP32, from FP64 host solves).
@@ -58,6 +63,8 @@ struct prop_s {
     // products (edges xy xz yz, faces x y z)
     float *tmp[16] = {};
     int *flag = nullptr;     // device: bit0 NaN/Inf seen
+    float *tab = nullptr;    // per-axis absorbing-layer tables (GridDev::tab)
+    int xchunk = 8;          // planes per CTA of the x-streaming stencil kernels
     // saved forward run for prop_backward
     bool saved = false;
     int saved_nsrc = 0, saved_nrec = 0;
@@ -134,6 +141,10 @@ void k_lame(prop_s *P);
 // maximum of the discrete derivative symbol (CFL bound)
 bool fd_weights(int M, float *c, float *bst);
 double symbol_max(const float *w, int M, bool stag);
+// host: per-axis absorbing-layer tables (layout of GridDev::tab)
+std::vector<float> layer_tables(const GridDev &g, int kind);
+// planes per CTA for the x-streaming stencil kernels
+int stencil_xchunk(const GridDev &g, int sms);
 
 // error helpers
 int wp_fail(prop_s *P, int code, const std::string &msg);

@@ -175,8 +175,9 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     if (int rc = host_tables(P, hs.data(), nsrc, TS)) return rc;
     if (int rc = host_tables(P, hr.data(), nrec, TR)) return rc;
     SparseDev S, R;
-    float *phys, *wav, *stage, *out, *fields[20] = {};
+    float *phys, *wav, *stage, *out, *tabd, *fields[20] = {};
     int *flag;
+    const size_t ntab = (size_t)(g.NX + g.NY + g.NZ) * (tti ? 1 : 2);
     const int nmodel = tti ? 5 : 3, nstate = tti ? 4 : 9, ntmp = tti ? 6 : 0;
     auto layout = [&](Carver &C) -> int {
         for (int i = 0; i < nmodel + nstate + ntmp; i++) fields[i] = C.take<float>(N);
@@ -185,6 +186,7 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
         stage = C.take<float>((size_t)nrec * nt);
         out = C.take<float>((size_t)nrec * nt);
         flag = C.take<int>(1);
+        tabd = C.take<float>(ntab);
         if (int rc = place_tables(P, C, TS, nsrc, S)) return rc;
         return place_tables(P, C, TR, nrec, R);
     };
@@ -249,6 +251,16 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     for (int i = 0; i < nstate; i++) P->st[i] = fields[k++];
     for (int i = 0; i < ntmp; i++) P->tmp[i] = fields[k++];
     P->flag = flag;
+    const std::vector<float> tabh = layer_tables(g, d->kind);     // after sig0 is known
+    WP_CK(P, cudaMemcpyAsync(tabd, tabh.data(), tabh.size() * sizeof(float), cudaMemcpyHostToDevice,
+                             P->stream));
+    g.tab = tabd;
+    {
+        int dev = 0, sms = 152;
+        WP_CK(P, cudaGetDevice(&dev));
+        WP_CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        P->xchunk = stencil_xchunk(g, sms);
+    }
     float *mdst[5] = {tti ? P->m : P->bu, tti ? P->eps : P->lam, tti ? P->del : P->mu, P->th, P->ph};
     for (int i = 0; i < nf; i++) {
         WP_CK(P, cudaMemcpyAsync(phys, hm[i].data(), np * sizeof(float), cudaMemcpyHostToDevice, P->stream));

@@ -124,6 +124,33 @@ double symbol_max(const float *w, int M, bool stag)
     return mx;
 }
 
+// Absorbing-layer factors are separable per axis: the TTI damping rate is a
+// sum sig0 (d/L)^2 over axes, the elastic Cerjan taper a product
+// exp(-(0.015 d)^2) over axes (d = depth into the layer in cells, at the
+// node or at the half point of a staggered component).
+std::vector<float> layer_tables(const GridDev &g, int kind)
+{
+    auto depth = [&](double s, int n) {
+        const double lo = g.nbl, hi = g.nbl + n - 1;
+        return s < lo ? lo - s : (s > hi ? s - hi : 0.0);
+    };
+    const int NN[3] = {g.NX, g.NY, g.NZ}, PN[3] = {g.px, g.py, g.pz};
+    std::vector<float> t;
+    for (int a = 0; a < 3; a++)
+        for (int i = 0; i < NN[a]; i++) {
+            if (kind == PROP_TTI) {
+                const double d = g.nbl > 0 ? depth(i, PN[a]) / g.nbl : 0.0;
+                t.push_back((float)((double)g.sig0 * d * d));
+            } else {
+                for (int hf = 0; hf < 2; hf++) {
+                    const double d = g.nbl > 0 ? (double)g.cer * depth(i + 0.5 * hf, PN[a]) : 0.0;
+                    t.push_back((float)exp(-d * d));
+                }
+            }
+        }
+    return t;
+}
+
 // ---------------------------------------------------------------------------
 // pointers: host or device
 // ---------------------------------------------------------------------------
@@ -240,6 +267,7 @@ static void free_all(prop_s *P)
     for (auto &a : P->ast) cudaFree(a);
     for (auto &a : P->tmp) cudaFree(a);
     cudaFree(P->flag);
+    cudaFree(P->tab);
     free_snaps(P);
     for (auto e : P->prof_ev) cudaEventDestroy(e);
 }
@@ -336,6 +364,16 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
         WP_TRY(upload(1, P->lam, 1.f, 0));   // vs  -> lambda
         WP_TRY(upload(2, P->mu, 1.f, 0));    // rho -> mu
         k_lame(P);
+    }
+    {
+        const std::vector<float> tab = layer_tables(g, d->kind);
+        WP_MALLOC(P, P->tab, tab.size() * sizeof(float), "layer tables");
+        WP_CK(P, cudaMemcpy(P->tab, tab.data(), tab.size() * sizeof(float), cudaMemcpyHostToDevice));
+        g.tab = P->tab;
+        int dev = 0, sms = 152;
+        WP_CK(P, cudaGetDevice(&dev));
+        WP_CK(P, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        P->xchunk = stencil_xchunk(g, sms);
     }
     for (int i = 0; i < nfields(P); i++) WP_MALLOC(P, P->st[i], N * sizeof(float), "state");
     WP_TRY(ensure_tmp(P, d->kind == PROP_TTI ? 8 : 0));
