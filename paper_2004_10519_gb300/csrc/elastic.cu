@@ -663,15 +663,9 @@ int launch_step(prop_s *P, float *const *S, bool adjoint)
     dim3 blk(TZ, TY, 1), grd((g.NZ + TZ - 1) / TZ, (g.NY + TY - 1) / TY, g.NX);
     Fields9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
-    prof_begin(P, adjoint ? 3 : 2);
-    if (!adjoint) {
-        const int xc = P->xchunk;
-        dim3 fb(FZ, FY, 1), fg((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
-        el_v_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->bu, P->flag, P->d.check_nan, xc);
-        el_t_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->lam, P->mu, P->flag,
-                                                P->d.check_nan, xc);
-        P->kern_launches += 2;
-    } else {
+    if (!adjoint) return el_launch_fast(P, S, false);
+    prof_begin(P, 3);
+    {
         const int xc = P->xchunk;
         dim3 fb(FZ, FY, 1), fg((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
         el_adj_v_tiled<M><<<fg, fb, 0, P->stream>>>(g, P->w, s, P->lam, P->mu, xc);

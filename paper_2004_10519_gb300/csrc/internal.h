@@ -96,8 +96,14 @@ struct prop_s {
 // the forward wavefield (img_p, img_r) at the new level.
 int tti_launch_step(prop_s *P, float *const *S, bool adjoint, const float *img_p,
                     const float *img_r, float *grad);
-// elastic step in place on S (9 fields); adjoint: transposed step
+int tti_launch_fast(prop_s *P, float *const *S, bool adjoint, const float *img_p,
+                    const float *img_r, float *grad);
+int tti_launch_tiled(prop_s *P, float *const *S, bool adjoint, const float *img_p,
+                     const float *img_r, float *grad);
+// elastic step in place on S (9 fields); adjoint: transposed step (tbar form)
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
+// pipelined elastic step: forward, or transposed step in s = C tbar variables
+int el_launch_fast(prop_s *P, float *const *S, bool adjoint_s);
 
 // sparse ops (sparse.cu)
 int sp_build(prop_s *P, const float *xyz_host, int n, const int *trace_of_point, SparseDev *S);
@@ -107,10 +113,15 @@ void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, 
                float scale, float *out_col);
 // inject: f[cell] += coef(cell) * sum_j w_j traces[trace_j*nt + t] into up to 3 fields;
 // mode 0: coef = scale; mode 1: coef = scale / A (TTI, A = m(1+sig dt/2));
+// mode 2: coef = scale (3 lambda + 2 mu) (elastic adjoint in s = C tbar);
 // grad_u != NULL: grad[cell] -= u[cell] * scale*sum / m  (TTI imaging of the
 // residual injection)
 void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
                int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad);
+// as sp_record but each field sum is divided by (3 lambda + 2 mu) at the cell
+// (trace of tbar from s = C tbar)
+void sp_record_trace_s(prop_s *P, const SparseDev *S, const float *f0, const float *f1,
+                       const float *f2, float scale, float *out_col);
 void sp_transpose(prop_s *P, const float *in_tn, float *out_nt, int n, int nt);
 
 // misc kernels

@@ -845,16 +845,21 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
         }
         prof_maybe_collect(P);
     };
-    // k = nt-1: transposed step of a zero state, then the last residual sample
-    WP_TRY(el_launch_step(P, a, true));
-    after(nt - 1);
     if (!g3) {
-        for (int k = nt - 2; k >= 0; k--) {
-            WP_TRY(el_launch_step(P, a, true));
-            after(k);
+        // adjoint modelling in s = C tbar: residuals enter as (3 lambda + 2 mu) w r,
+        // the source side reads dt P tr(s) / (3 lambda + 2 mu)
+        for (int k = nt - 1; k >= 1; k--) {
+            WP_TRY(el_launch_fast(P, a, true));
+            sp_inject(P, &G.R, res, nt, k, 1.f, 2, a[3], a[4], a[5], nullptr, nullptr);
+            if (srcstage)
+                sp_record_trace_s(P, &G.S, a[3], a[4], a[5], P->g.dt, srcstage + (size_t)(k - 1) * G.S.n);
+            prof_maybe_collect(P);
         }
         return PROP_OK;
     }
+    // k = nt-1: transposed step of a zero state, then the last residual sample
+    WP_TRY(el_launch_step(P, a, true));
+    after(nt - 1);
     auto xs = [&](float *base, const float **out) {
         for (int f = 0; f < 9; f++) out[f] = base + f * N;
     };

@@ -39,6 +39,7 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
                               const int *__restrict__ ptr, const int *__restrict__ tr,
                               const float *__restrict__ w, const float *__restrict__ traces, int nt,
                               int t, float scale, int mode, const float *__restrict__ m,
+                              const float *__restrict__ lam, const float *__restrict__ mu,
                               float *f0, float *f1, float *f2, const float *__restrict__ gu,
                               float *grad)
 {
@@ -52,12 +53,31 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
         const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
         const float A = m[q] * (1.f + 0.5f * tti_sigma(g, x, y, z) * g.dt);
         coef = scale / A;
+    } else if (mode == 2) {
+        coef = scale * (3.f * lam[q] + 2.f * mu[q]);
     }
     const float v = coef * acc;
     f0[q] += v;
     if (f1) f1[q] += v;
     if (f2) f2[q] += v;
     if (grad) grad[q] -= gu[q] * (scale * acc) / m[q];
+}
+
+__global__ void record_s_kernel(int n, const long long *__restrict__ idx, const float *__restrict__ w,
+                                const float *__restrict__ f0, const float *__restrict__ f1,
+                                const float *__restrict__ f2, const float *__restrict__ lam,
+                                const float *__restrict__ mu, float scale, float *__restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float s = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const long long q = idx[8 * i + c];
+        const float wc = w[8 * i + c];
+        if (wc != 0.f) s += wc * (f0[q] + f1[q] + f2[q]) / (3.f * lam[q] + 2.f * mu[q]);
+    }
+    out[i] = scale * s;
 }
 
 __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict__ out, int n, int nt)
@@ -316,7 +336,17 @@ void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t
     if (S->ncell <= 0) return;
     inject_kernel<<<nblk(S->ncell), NB, 0, P->stream>>>(P->g, S->ncell, S->cell, S->cell_ptr,
                                                         S->ent_trace, S->ent_w, traces, nt, t, scale,
-                                                        mode, P->m, f0, f1, f2, grad_u, grad);
+                                                        mode, P->m, P->lam, P->mu, f0, f1, f2,
+                                                        grad_u, grad);
+    P->kern_launches++;
+}
+
+void sp_record_trace_s(prop_s *P, const SparseDev *S, const float *f0, const float *f1,
+                       const float *f2, float scale, float *out_col)
+{
+    if (S->n <= 0) return;
+    record_s_kernel<<<nblk(S->n), NB, 0, P->stream>>>(S->n, S->rec_idx, S->rec_w, f0, f1, f2, P->lam,
+                                                      P->mu, scale, out_col);
     P->kern_launches++;
 }
 

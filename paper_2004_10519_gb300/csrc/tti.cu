@@ -245,6 +245,14 @@ int launch(prop_s *P, float *const *S, bool adjoint, const float *up, const floa
 int tti_launch_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
                     float *grad)
 {
+    return tti_launch_fast(P, S, adjoint, img_p, img_r, grad);
+}
+
+// first tiled form (loads of plane x issued after the previous barrier);
+// kept as the comparison point of the pipelined passes in tti_fast.cu
+int tti_launch_tiled(prop_s *P, float *const *S, bool adjoint, const float *img_p,
+                     const float *img_r, float *grad)
+{
     switch (P->M) {
     case 2: return launch<2>(P, S, adjoint, img_p, img_r, grad);
     case 4: return launch<4>(P, S, adjoint, img_p, img_r, grad);
