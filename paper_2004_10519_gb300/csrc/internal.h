@@ -104,6 +104,14 @@ int tti_launch_tiled(prop_s *P, float *const *S, bool adjoint, const float *img_
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 // pipelined elastic step: forward, or transposed step in s = C tbar variables
 int el_launch_fast(prop_s *P, float *const *S, bool adjoint_s);
+// TMA-fed passes (stencil_tma.cu): usable when NZ % 4 == 0
+bool tma_usable(const prop_s *P);
+int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
+int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
+                   const float *img_r, float *grad);
+// transposed elastic step in the variables (b_avg vbar, g C tbar): the
+// forward step with dt -> -dt
+int el_step_adjoint_u(prop_s *P, float *const *S);
 
 // sparse ops (sparse.cu)
 int sp_build(prop_s *P, const float *xyz_host, int n, const int *trace_of_point, SparseDev *S);

@@ -441,14 +441,11 @@ static int finish(prop_s *P)
     WP_CK(P, cudaStreamSynchronize(P->stream));
     WP_CK(P, cudaGetLastError());
     prof_collect(P);
-    if (P->d.check_nan) {
-        int f = 0;
-        WP_CK(P, cudaMemcpy(&f, P->flag, sizeof(int), cudaMemcpyDeviceToHost));
-        if (f) {
-            cudaMemset(P->flag, 0, sizeof(int));
-            return wp_fail(P, PROP_EUNSTABLE, "NaN or Inf in the wavefield");
-        }
-    }
+    int f = 0;
+    WP_CK(P, cudaMemcpy(&f, P->flag, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f) WP_CK(P, cudaMemset(P->flag, 0, sizeof(int)));
+    if (f & 2) return wp_fail(P, PROP_ETIMEOUT, "a bounded device-side wait expired (TMA pipeline)");
+    if (P->d.check_nan && (f & 1)) return wp_fail(P, PROP_EUNSTABLE, "NaN or Inf in the wavefield");
     return PROP_OK;
 }
 
@@ -849,7 +846,7 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
         // adjoint modelling in s = C tbar: residuals enter as (3 lambda + 2 mu) w r,
         // the source side reads dt P tr(s) / (3 lambda + 2 mu)
         for (int k = nt - 1; k >= 1; k--) {
-            WP_TRY(el_launch_fast(P, a, true));
+            WP_TRY(el_step_adjoint_u(P, a));
             sp_inject(P, &G.R, res, nt, k, 1.f, 2, a[3], a[4], a[5], nullptr, nullptr);
             if (srcstage)
                 sp_record_trace_s(P, &G.S, a[3], a[4], a[5], P->g.dt, srcstage + (size_t)(k - 1) * G.S.n);

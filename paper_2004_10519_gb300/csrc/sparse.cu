@@ -54,7 +54,10 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
         const float A = m[q] * (1.f + 0.5f * tti_sigma(g, x, y, z) * g.dt);
         coef = scale / A;
     } else if (mode == 2) {
-        coef = scale * (3.f * lam[q] + 2.f * mu[q]);
+        // residual into u = g C tbar: g (3 lambda + 2 mu) on each diagonal component
+        const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
+        const float gn = g.tab[2 * x] * g.tab[2 * g.NX + 2 * y] * g.tab[2 * (g.NX + g.NY) + 2 * z];
+        coef = scale * (3.f * lam[q] + 2.f * mu[q]) * gn;
     }
     const float v = coef * acc;
     f0[q] += v;
@@ -63,7 +66,7 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
     if (grad) grad[q] -= gu[q] * (scale * acc) / m[q];
 }
 
-__global__ void record_s_kernel(int n, const long long *__restrict__ idx, const float *__restrict__ w,
+__global__ void record_s_kernel(GridDev g, int n, const long long *__restrict__ idx, const float *__restrict__ w,
                                 const float *__restrict__ f0, const float *__restrict__ f1,
                                 const float *__restrict__ f2, const float *__restrict__ lam,
                                 const float *__restrict__ mu, float scale, float *__restrict__ out)
@@ -75,7 +78,13 @@ __global__ void record_s_kernel(int n, const long long *__restrict__ idx, const 
     for (int c = 0; c < 8; c++) {
         const long long q = idx[8 * i + c];
         const float wc = w[8 * i + c];
-        if (wc != 0.f) s += wc * (f0[q] + f1[q] + f2[q]) / (3.f * lam[q] + 2.f * mu[q]);
+        if (wc != 0.f) {
+            // tr(tbar) = tr(u) / (g (3 lambda + 2 mu)) at a node
+            const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY),
+                      x = (int)(q / ((long long)g.NZ * g.NY));
+            const float gn = g.tab[2 * x] * g.tab[2 * g.NX + 2 * y] * g.tab[2 * (g.NX + g.NY) + 2 * z];
+            s += wc * (f0[q] + f1[q] + f2[q]) / ((3.f * lam[q] + 2.f * mu[q]) * gn);
+        }
     }
     out[i] = scale * s;
 }
@@ -345,7 +354,7 @@ void sp_record_trace_s(prop_s *P, const SparseDev *S, const float *f0, const flo
                        const float *f2, float scale, float *out_col)
 {
     if (S->n <= 0) return;
-    record_s_kernel<<<nblk(S->n), NB, 0, P->stream>>>(S->n, S->rec_idx, S->rec_w, f0, f1, f2, P->lam,
+    record_s_kernel<<<nblk(S->n), NB, 0, P->stream>>>(P->g, S->n, S->rec_idx, S->rec_w, f0, f1, f2, P->lam,
                                                       P->mu, scale, out_col);
     P->kern_launches++;
 }

@@ -245,7 +245,8 @@ int launch(prop_s *P, float *const *S, bool adjoint, const float *up, const floa
 int tti_launch_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
                     float *grad)
 {
-    return tti_launch_fast(P, S, adjoint, img_p, img_r, grad);
+    return tma_usable(P) ? tti_launch_tma(P, S, adjoint, img_p, img_r, grad)
+                         : tti_launch_fast(P, S, adjoint, img_p, img_r, grad);
 }
 
 // first tiled form (loads of plane x issued after the previous barrier);

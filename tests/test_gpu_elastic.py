@@ -43,17 +43,23 @@ def test_forward_parity_reduced_random_model(wp):
     assert rel(tr, ref) <= TOL
 
 
+# computational NZ % 4 != 0 runs the pipelined kernels, NZ % 4 == 0 the TMA-fed ones
+SHAPES = [(31, 27, 37), (31, 27, 40)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("so", [4, 8, 12, 16])
-def test_forward_parity_ragged(wp, so):
-    p = ragged_el(so)
+def test_forward_parity_ragged(wp, so, shape):
+    p = ragged_el(so, shape=shape)
     tr = wp.Propagator.from_problem(p).forward(p.wavelet, p.src, p.rec)
     ref = oracle.Problem(p).forward()
     assert rel(tr, ref) <= TOL, so
 
 
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("so", [8, 12])
-def test_adjoint_parity_and_dot(wp, so):
-    p = ragged_el(so, nt=60)
+def test_adjoint_parity_and_dot(wp, so, shape):
+    p = ragged_el(so, nt=60, shape=shape)
     prop = wp.Propagator.from_problem(p)
     rng = np.random.default_rng(4)
     d = rng.standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)

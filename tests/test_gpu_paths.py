@@ -1,0 +1,51 @@
+"""The TMA-fed stencil passes (used when the computational NZ is a multiple
+of 4) and the pipelined passes (any NZ; forced with WAVEPROP_NO_TMA=1) compute
+the same discrete operators: their traces agree to FP32 rounding."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def tti_problem(shape=(36, 30, 44), nbl=6, so=12, nt=60, h=10.0):
+    nx, ny, nz = shape
+    m = synth.layered_tti(nx, ny, nz, 5, noise_sigma=3.0, smooth_sigma=1.5)
+    dt = synth.cfl_dt(h, float(np.max(m["vp"] * np.sqrt(1 + 2 * m["eps"]))))
+    src = np.array([[nx * h / 2 + 0.3, ny * h / 2 - 0.8, 3.1 * h]], np.float32)
+    rec = synth.carpet_receivers(5.0, 6.0, 3.3 * h, 9, 8, 2.2 * h)
+    return synth.Problem(synth.TTI, nx, ny, nz, nbl, h, so, nt, dt, m, src,
+                         synth.ricker(22.0, dt, nt)[None], rec)
+
+
+def el_problem(shape=(34, 30, 44), nbl=6, so=8, nt=60, h=10.0):
+    nx, ny, nz = shape
+    m = synth.random_elastic(nx, ny, nz, 8, 4.0)
+    dt = synth.cfl_dt(h, float(m["vp"].max()))
+    src = np.array([[nx * h / 2 + 0.3, ny * h / 2 - 0.8, nz * h / 2]], np.float32)
+    rec = synth.carpet_receivers(5.0, 6.0, 3.3 * h, 9, 8, 0.0)
+    return synth.Problem(synth.ELASTIC, nx, ny, nz, nbl, h, so, nt, dt, m, src,
+                         synth.ricker(20.0, dt, nt)[None], rec)
+
+
+@pytest.mark.parametrize("kind", ["tti", "elastic"])
+def test_tma_and_pipelined_paths_agree(kind, monkeypatch):
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    p = tti_problem() if kind == "tti" else el_problem()
+    assert (p.nz + 2 * p.nbl) % 4 == 0
+    d = np.random.default_rng(3).standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    out = {}
+    for tag, env in (("tma", None), ("pipelined", "1")):
+        if env:
+            monkeypatch.setenv("WAVEPROP_NO_TMA", env)
+        else:
+            monkeypatch.delenv("WAVEPROP_NO_TMA", raising=False)
+        prop = wp.Propagator.from_problem(p)
+        out[tag] = (prop.forward(p.wavelet, p.src, p.rec).astype(np.float64),
+                    prop.adjoint(d, p.src, p.rec).astype(np.float64))
+        prop.close()
+    for i in range(2):
+        a, b = out["tma"][i], out["pipelined"][i]
+        assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b), (kind, i)

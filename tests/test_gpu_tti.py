@@ -48,17 +48,23 @@ def test_forward_parity_two_layer_so8(wp):
     assert rel(tr, ref) <= TOL
 
 
+# computational NZ % 4 != 0 runs the pipelined kernels, NZ % 4 == 0 the TMA-fed ones
+SHAPES = [(37, 29, 45), (37, 29, 42)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("so", [4, 8, 12, 16])
-def test_forward_parity_ragged(wp, so):
-    p = ragged_tti(so)
+def test_forward_parity_ragged(wp, so, shape):
+    p = ragged_tti(so, shape=shape)
     tr = wp.Propagator.from_problem(p).forward(p.wavelet, p.src, p.rec)
     ref = oracle.Problem(p).forward()
     assert rel(tr, ref) <= TOL, so
 
 
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("so", [8, 12])
-def test_adjoint_parity_and_dot(wp, so):
-    p = ragged_tti(so, nt=60)
+def test_adjoint_parity_and_dot(wp, so, shape):
+    p = ragged_tti(so, nt=60, shape=shape)
     prop = wp.Propagator.from_problem(p)
     rng = np.random.default_rng(4)
     d = rng.standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
@@ -72,8 +78,8 @@ def test_adjoint_parity_and_dot(wp, so):
     assert abs(a - b) <= 1e-5 * abs(a), (a, b)
 
 
-def grad_problem(so=8, nt=80):
-    p = ragged_tti(so, nt=nt, shape=(30, 26, 34), nbl=6)
+def grad_problem(so=8, nt=80, shape=(30, 26, 34)):
+    p = ragged_tti(so, nt=nt, shape=shape, nbl=6)
     p.vdamp = float(np.max(p.model["vp"] * np.sqrt(1 + 2 * p.model["eps"]))) * 1000.0
     true = oracle.Problem(p)
     d_obs = true.forward()
@@ -82,8 +88,9 @@ def grad_problem(so=8, nt=80):
     return p, p0, d_obs
 
 
-def test_gradient_parity_and_checkpoint_modes(wp):
-    p, p0, d_obs = grad_problem()
+@pytest.mark.parametrize("shape", [(30, 26, 34), (30, 26, 36)])
+def test_gradient_parity_and_checkpoint_modes(wp, shape):
+    p, p0, d_obs = grad_problem(shape=shape)
     g_ref, J_ref = oracle.Problem(p0).gradient(d_obs)
     d32 = d_obs.astype(np.float32)
     res = {}
