@@ -285,7 +285,10 @@ def main():
         torch.cuda.set_device(dev)
         out = {}
         if "tti" in extras:
-            out["tti"] = tti_throughput(wp, torch, dev)
+            if args.small:      # profiling case: 240x240x200 + 40 (320x320x280 points)
+                out["tti"] = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
+            else:
+                out["tti"] = tti_throughput(wp, torch, dev)
         if "grad" in extras:
             out["grad"] = gradient_shots_per_hour(
                 wp, torch, dev, args.grad_nt,
