@@ -41,6 +41,11 @@ HBM_FALLBACK_GBS = 6800.0
 #   elastic: 9 state reads + 9 writes + 3 parameters (b, lambda, mu) = 84 B
 #   TTI:     4 state reads + 2 writes + 5 parameters                  = 44 B
 ALG_BYTES = {"elastic": 84.0, "tti": 44.0}
+# DRAM bytes per point of one elastic step (velocity + stress pass) measured
+# by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 200^3 case of
+# the same kernels (profiles/elastic_tma_passes_200cube_so8.md), scaled to a
+# full launch by the number of points
+TRAFFIC_B_PER_PT = {"elastic": 111.9}
 
 
 def peaks():
@@ -263,6 +268,50 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
             "modes": res}
 
 
+def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
+    """Batched TTI gradients (so 12, BF16 checkpoints): shots on windows of
+    one large model with nx, ny ~ U[200, 600], nz = 300 (+ 40-cell layer);
+    shots/hour of one prop_gradient call after another against one
+    prop_gradient_batch call over the same shots (results compared bitwise)."""
+    kw = dict(size_range=(60, 120), nz=80) if small else {}
+    shots = synth.tti_batch_shots(nshots, nt, **kw)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    to = lambda a: torch.from_numpy(a).to(dev)
+    props, wav, src, rec, obs = [], [], [], [], []
+    npts = 0
+    for true, p0 in shots:
+        pt = wp.Propagator.from_problem(true, stream=stream)
+        w, s_, r = to(true.wavelet), to(true.src), to(true.rec)
+        obs.append(pt.forward(w, s_, r))
+        pt.close()
+        props.append(wp.Propagator.from_problem(p0, snap_mode=wp.SNAP_CKPT_BF16, stream=stream))
+        wav.append(w); src.append(s_); rec.append(r)
+        npts += int(np.prod(props[-1].grid))
+    torch.cuda.synchronize()
+    # warm-up (tensor maps, autotuned tiles, allocator) on the first shot
+    props[0].gradient(wav[0], src[0], rec[0], obs[0])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    seq = [p.gradient(wav[i], src[i], rec[i], obs[i]) for i, p in enumerate(props)]
+    torch.cuda.synchronize()
+    t_seq = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    grads, J = wp.gradient_batch(props, wav, src, rec, obs)
+    torch.cuda.synchronize()
+    t_bat = time.perf_counter() - t0
+    same = all(bool(torch.equal(g, s[0])) for g, s in zip(grads, seq))
+    waves = wp.plan_waves([p.gradient_bytes(r.shape[0]) for p, r in zip(props, rec)],
+                          int(torch.cuda.mem_get_info(dev)[0] * 0.9))[1]
+    for p in props:
+        p.close()
+    return {"shots": nshots, "nt": nt, "storage": "bf16 checkpoints",
+            "windows": [s[1].name for s in shots], "points_total": npts,
+            "sequential": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq},
+            "batched": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
+                        "waves": waves},
+            "bitwise_equal": same}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -271,8 +320,10 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--extra", default="", help="comma list: tti, grad (secondary measurements)")
+    ap.add_argument("--extra", default="", help="comma list: tti, grad, batch (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
+    ap.add_argument("--batch-shots", type=int, default=8)
+    ap.add_argument("--batch-nt", type=int, default=150)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -294,6 +345,9 @@ def main():
                 wp, torch, dev, args.grad_nt,
                 [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
                 small=args.small)
+        if "batch" in extras:
+            out["batch"] = batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
+                                                small=args.small)
         print(json.dumps(out), flush=True)
         return
 
@@ -353,14 +407,15 @@ def main():
     prop.profile(True)
     prop.step(50)
     f_ms, f_n = prop.kernel_stats(wp.K_EL_FWD)
-    prop.step(50, adjoint=True)
-    a_ms, a_n = prop.kernel_stats(wp.K_EL_ADJ)
+    prop.adjoint(resid, src, rec, out=qout)
+    a_ms, a_n = prop.kernel_stats(wp.K_EL_ADJ_U)
     prop.profile(False)
     hbm, src_peak = peaks()
     t_launch = f_ms / max(f_n, 1) / 1e3
     ach = ALG_BYTES["elastic"] * N / t_launch / 1e9
     roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-            "traffic": None, "kernel": "elastic forward step (velocity + stress passes)",
+            "traffic": TRAFFIC_B_PER_PT["elastic"] * N,
+            "kernel": "elastic forward step (velocity + stress passes)",
             "peak_source": src_peak, "launch_ms": t_launch * 1e3,
             "alg_bytes_per_launch": ALG_BYTES["elastic"] * N,
             "adjoint_launch_ms": a_ms / max(a_n, 1)}

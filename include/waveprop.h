@@ -134,6 +134,35 @@ int prop_forward_saved(prop_t *p, const float *wavelet, const float *src_xyz, in
                        const float *rec_xyz, int nrec, float *traces);
 int prop_backward(prop_t *p, const float *resid, float *grad, float *src_grad);
 
+/* Gradients of many independent shots (the paper's embarrassingly parallel
+ * loop over sources, Sec. III-B: each shot its own model window, geometry
+ * and handle).  Shot i computes exactly prop_gradient(shots[i], wavelet[i],
+ * src_xyz[i], nsrc[i], rec_xyz[i], nrec[i], d_obs[i], grad[i], &misfit[i])
+ * -- bitwise the same result.  Shots are grouped, in order, into waves
+ * whose prop_gradient_bytes sum to at most budget_bytes (0: 90 % of the
+ * free device memory at the call); the shots of a wave run concurrently,
+ * each from its own host thread on a private stream that is ordered after
+ * the handle's stream, which in turn waits for the shot.  All handles must
+ * be distinct and live on the calling thread's current device; the caller
+ * must not use them from another thread during the call.  misfit [nshots]
+ * may be NULL.  Returns PROP_OK, or the error of the first failing shot
+ * (its message, prefixed "shot i: ", from prop_last_error(NULL); each
+ * handle keeps its own message); the other shots still run. */
+int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
+                        const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
+                        const int *nrec, const float *const *d_obs, float *const *grad,
+                        double *misfit, size_t budget_bytes);
+
+/* Device bytes a prop_gradient call with nrec receivers would allocate on
+ * top of what the handle holds (0 for p == NULL). */
+size_t prop_gradient_bytes(const prop_t *p, int nrec);
+
+/* The wave plan of prop_gradient_batch: shot i (of n, needing bytes[i]) goes
+ * to wave wave_of[i]; waves are filled first-fit in shot order up to budget,
+ * a shot above the budget alone.  Returns the number of waves, or PROP_EINVAL
+ * for n < 0 or NULL arrays with n > 0.  Host only. */
+int prop_plan_waves(const size_t *bytes, int n, size_t budget, int *wave_of);
+
 /* Wavefield state access (computational grid, float32 [NX][NY][NZ] each):
  *   TTI:     fields[0..3] = p^n, r^n, p^{n-1}, r^{n-1}
  *   ELASTIC: fields[0..8] = vx vy vz txx tyy tzz txy txz tyz
@@ -151,6 +180,15 @@ float prop_dt(const prop_t *p);
  * launches [ms], and the number of those launches (CUDA events on the
  * handle's stream).  Used for roofline accounting. */
 int prop_kernel_time(const prop_t *p, double *ms, long long *launches);
+
+/* Planes along x that one CTA of the x-streaming stencil kernels updates.
+ * prop_create picks it by timing a few steps of the zero state for a set of
+ * candidates (the choice is cached per kind, space order, grid and kernel
+ * variant for the process; environment WAVEPROP_AUTOTUNE_CACHE=<file> keeps
+ * the cache across processes, WAVEPROP_AUTOTUNE=0 skips the timing and keeps
+ * an occupancy heuristic).  Results are bitwise independent of the choice.
+ * Returns 0 for p == NULL. */
+int prop_tile_planes(const prop_t *p);
 
 /* Forward modelling that allocates no device memory.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc, e.g. an

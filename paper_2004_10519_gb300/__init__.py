@@ -27,7 +27,8 @@ ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA
 ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_forward_saved", "prop_backward", "prop_grid_dims", "prop_set_state",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
-               "prop_last_error", "prop_forward_noalloc")
+               "prop_last_error", "prop_forward_noalloc", "prop_tile_planes",
+               "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves")
 
 
 class PropDesc(C.Structure):
@@ -69,6 +70,13 @@ def lib():
         L.prop_dt.restype = C.c_float
         L.prop_dt.argtypes = [vp]
         L.prop_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.prop_tile_planes.argtypes = [vp]
+        L.prop_gradient_batch.argtypes = [fpp, C.c_int, fpp, fpp, C.POINTER(C.c_int), fpp,
+                                          C.POINTER(C.c_int), fpp, fpp, C.POINTER(C.c_double),
+                                          C.c_size_t]
+        L.prop_gradient_bytes.restype = C.c_size_t
+        L.prop_gradient_bytes.argtypes = [vp, C.c_int]
+        L.prop_plan_waves.argtypes = [C.POINTER(C.c_size_t), C.c_int, C.c_size_t, C.POINTER(C.c_int)]
         L.prop_destroy.argtypes = [vp]
         L.prop_last_error.restype = C.c_char_p
         L.prop_last_error.argtypes = [vp]
@@ -186,6 +194,11 @@ class Propagator:
     def dt(self):
         return lib().prop_dt(self.h)
 
+    @property
+    def tile_planes(self):
+        """x-planes per CTA chosen by the autotuner at creation."""
+        return lib().prop_tile_planes(self.h)
+
     def _out(self, like, shape):
         if _is_torch(like):
             import torch
@@ -274,6 +287,47 @@ class Propagator:
     def last_launches(self):
         return lib().prop_last_launches(self.h)
 
+    def gradient_bytes(self, nrec):
+        """Device bytes a gradient call with nrec receivers would allocate."""
+        return lib().prop_gradient_bytes(self.h, int(nrec))
+
 
 # kernel ids of Propagator.kernel_stats
-K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD = 0, 1, 2, 3, 4
+K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD, K_EL_ADJ_U = 0, 1, 2, 3, 4, 5
+
+
+def plan_waves(nbytes, budget):
+    """Wave index of each shot under ``prop_plan_waves`` (first fit in order)."""
+    n = len(nbytes)
+    b = (C.c_size_t * max(n, 1))(*[int(x) for x in nbytes])
+    w = (C.c_int * max(n, 1))()
+    rc = lib().prop_plan_waves(b, n, int(budget), w)
+    if rc < 0:
+        raise PropError(rc, "prop_plan_waves")
+    return [w[i] for i in range(n)], rc
+
+
+def gradient_batch(props, wavelets, srcs, recs, d_obs, outs=None, budget_bytes=0):
+    """Gradients of independent shots (``prop_gradient_batch``); shot i uses
+    ``props[i]`` and the i-th entry of every list.  Returns (grads, misfits)."""
+    n = len(props)
+    keep, W, S, R, D, G = [], [], [], [], [], []
+    ns, nr = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))()
+    grads = []
+    for i, p in enumerate(props):
+        sa, ra = _Arg(srcs[i]), _Arg(recs[i])
+        ns[i], nr[i] = _npts(sa), _npts(ra)
+        w = _Arg(wavelets[i], ns[i] * p.nt)
+        d = _Arg(d_obs[i], nr[i] * p.nt)
+        out = outs[i] if outs is not None else p._out(d_obs[i], p._gshape())
+        o = _Arg(out, int(np.prod(p._gshape())), writable=True)
+        grads.append(out)
+        keep += [sa, ra, w, d, o]
+        W.append(w.ptr); S.append(sa.ptr); R.append(ra.ptr); D.append(d.ptr); G.append(o.ptr)
+    arr = lambda xs: (C.c_void_p * max(n, 1))(*xs)
+    J = (C.c_double * max(n, 1))()
+    rc = lib().prop_gradient_batch(arr([p.h for p in props]), n, arr(W), arr(S), ns, arr(R), nr,
+                                   arr(D), arr(G), J, int(budget_bytes))
+    if rc:
+        raise PropError(rc, lib().prop_last_error(None).decode())
+    return grads, [J[i] for i in range(n)]

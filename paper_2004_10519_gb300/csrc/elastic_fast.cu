@@ -466,12 +466,9 @@ int launch(prop_s *P, float *const *S)
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
     const size_t smv = 2 * VP<M, ADJ>::BUF * sizeof(float);
     const size_t smt = (2 * TP_<M>::BUF + 3 * TP_<M>::MU) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(el_vpass<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv);
-        cudaFuncSetAttribute(el_tpass<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt);
-        attr = true;
-    }
+    static const bool attr = (cudaFuncSetAttribute(el_vpass<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv),
+                              cudaFuncSetAttribute(el_tpass<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt), true);
+    (void)attr;
     prof_begin(P, ADJ ? 5 : 2);
     el_vpass<M, ADJ><<<grd, blk, smv, P->stream>>>(g, P->w, s, P->bu, xc);
     el_tpass<M, ADJ><<<grd, blk, smt, P->stream>>>(g, P->w, s, P->lam, P->mu, P->bu, xc);

@@ -272,6 +272,101 @@ static void free_all(prop_s *P)
     for (auto e : P->prof_ev) cudaEventDestroy(e);
 }
 
+static int step_state(prop_s *P, float **s, bool adjoint);
+static int zero_fields(prop_s *P, float *const *f, int n);
+
+// ---------------------------------------------------------------------------
+// autotuner: x-extent of the stencil tiles (planes per CTA).  It sets the
+// number of CTAs (waves on the SMs) against the queue warm-up cost per chunk.
+// Candidates are timed on a few forward steps of the zero state; the choice
+// is cached per (kind, space order, grid, TMA path) for the process and, if
+// WAVEPROP_AUTOTUNE_CACHE names a file, across processes.  WAVEPROP_AUTOTUNE=0
+// keeps the occupancy heuristic.  Results do not depend on the choice.
+// ---------------------------------------------------------------------------
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <fstream>
+
+static std::mutex g_tune_mtx;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static std::string tune_key(const prop_s *P)
+{
+    std::ostringstream k;
+    k << P->d.kind << ':' << P->M << ':' << P->g.NX << 'x' << P->g.NY << 'x' << P->g.NZ << ':'
+      << (tma_usable(P) ? "tma" : "pipe");
+    return k.str();
+}
+
+static int autotune_xchunk(prop_s *P)
+{
+    const char *on = getenv("WAVEPROP_AUTOTUNE");
+    if (on && !strcmp(on, "0")) return PROP_OK;
+    const char *path = getenv("WAVEPROP_AUTOTUNE_CACHE");
+    const std::string key = tune_key(P);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mtx);
+        if (!g_tune_loaded && path) {
+            std::ifstream f(path);
+            std::string k;
+            int v;
+            while (f >> k >> v) g_tune[k] = v;
+        }
+        g_tune_loaded = true;
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            P->xchunk = it->second;
+            return PROP_OK;
+        }
+    }
+    const int NX = P->g.NX;
+    std::vector<int> cand;
+    for (int c : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48}) {
+        const int xc = std::max(8, (NX + c - 1) / c);
+        if (std::find(cand.begin(), cand.end(), xc) == cand.end()) cand.push_back(xc);
+    }
+    const int heuristic = P->xchunk;
+    if (std::find(cand.begin(), cand.end(), heuristic) == cand.end()) cand.push_back(heuristic);
+    float *s[9];
+    for (int i = 0; i < 9; i++) s[i] = P->st[i];
+    WP_TRY(zero_fields(P, s, P->d.kind == PROP_TTI ? 4 : 9));
+    cudaEvent_t e0, e1;
+    WP_CK(P, cudaEventCreate(&e0));
+    WP_CK(P, cudaEventCreate(&e1));
+    int best = heuristic;
+    float best_ms = 1e30f;
+    for (int xc : cand) {
+        P->xchunk = xc;
+        WP_TRY(step_state(P, s, false));                   // warm-up (first launch of a variant)
+        WP_CK(P, cudaEventRecord(e0, P->stream));
+        for (int i = 0; i < 3; i++) WP_TRY(step_state(P, s, false));
+        WP_CK(P, cudaEventRecord(e1, P->stream));
+        WP_CK(P, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        WP_CK(P, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = xc;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < 9; i++) P->st[i] = s[i];
+    WP_TRY(zero_fields(P, s, P->d.kind == PROP_TTI ? 4 : 9));
+    P->xchunk = best;
+    std::lock_guard<std::mutex> lk(g_tune_mtx);
+    g_tune[key] = best;
+    if (path) {
+        std::ofstream f(path, std::ios::app);
+        f << key << ' ' << best << '\n';
+    }
+    return PROP_OK;
+}
+
+extern "C" int prop_tile_planes(const prop_t *P) { return P ? P->xchunk : 0; }
+
 static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
 {
     P->d = *d;
@@ -378,6 +473,8 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     for (int i = 0; i < nfields(P); i++) WP_MALLOC(P, P->st[i], N * sizeof(float), "state");
     WP_TRY(ensure_tmp(P, d->kind == PROP_TTI ? 8 : 0));
     WP_MALLOC(P, P->flag, sizeof(int), "flag");
+    WP_CK(P, cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
+    WP_TRY(autotune_xchunk(P));
     WP_CK(P, cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
     WP_CK(P, cudaStreamSynchronize(P->stream));
     WP_CK(P, cudaGetLastError());
@@ -967,6 +1064,57 @@ extern "C" int prop_backward(prop_t *P, const float *resid, float *grad, float *
     return rc;
 }
 
+// device bytes one prop_gradient call allocates on top of what the handle
+// already holds (wavefield storage or checkpoints + recompute segment,
+// adjoint state, scratch fields, gradient buffers, traces)
+static size_t gradient_bytes(const prop_s *P, int nrec)
+{
+    const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
+    const int nt = P->d.nt, K = ckpt_K(P), J = (nt - 1 + K - 1) / K, cf = nfields(P);
+    size_t b = 0;
+    switch (P->d.snap_mode) {
+    case SNAP_FULL_FP32:
+        b += (P->d.kind == PROP_TTI ? (size_t)(nt - 1) : (size_t)nt) * snap_fields(P) * N * 4;
+        break;
+    case SNAP_CKPT_FP32: b += (size_t)J * cf * N * 4; break;
+    default: b += (size_t)J * cf * N * 2 + 4 * ((size_t)J * cf + 1024); break;
+    }
+    if (P->d.snap_mode != SNAP_FULL_FP32)
+        b += (P->d.kind == PROP_TTI ? (size_t)K : (size_t)K + 1) * snap_fields(P) * N * 4;
+    for (int i = 0; i < cf; i++)
+        if (!P->ast[i]) b += N * 4;
+    const int ntmp = P->d.kind == PROP_TTI ? 8 : 15;
+    for (int i = 0; i < ntmp; i++)
+        if (!P->tmp[i]) b += N * 4;
+    const int ng = P->d.kind == PROP_TTI ? 1 : 3;
+    b += (N + np) * ng * 4;
+    b += (size_t)4 * 4 * nrec * nt;    // traces, staging, observed data, residual
+    return b + ((size_t)64 << 20);     // point tables, wavelet, allocator granularity
+}
+
+extern "C" size_t prop_gradient_bytes(const prop_t *P, int nrec)
+{
+    return P ? gradient_bytes(P, std::max(nrec, 0)) : 0;
+}
+
+// greedy first-fit of shots, in order, into waves whose bytes sum to at most
+// budget; a shot larger than the budget gets a wave of its own
+extern "C" int prop_plan_waves(const size_t *bytes, int n, size_t budget, int *wave_of)
+{
+    if (n < 0 || (n > 0 && (!bytes || !wave_of))) return PROP_EINVAL;
+    int w = 0;
+    size_t used = 0;
+    for (int i = 0; i < n; i++) {
+        if (used > 0 && used + bytes[i] > budget) {
+            w++;
+            used = 0;
+        }
+        wave_of[i] = w;
+        used += bytes[i];
+    }
+    return n > 0 ? w + 1 : 0;
+}
+
 extern "C" int prop_gradient(prop_t *P, const float *wavelet, const float *src_xyz, int nsrc,
                              const float *rec_xyz, int nrec, const float *d_obs, float *grad,
                              double *misfit)
@@ -986,4 +1134,88 @@ extern "C" int prop_gradient(prop_t *P, const float *wavelet, const float *src_x
     rc = backward_impl(P, (const float *)tr.p, grad, nullptr, nullptr);
     free_snaps(P);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// batched gradients: shots of one wave run concurrently, one host thread and
+// one private stream per shot; waves are sized to the free device memory
+// ---------------------------------------------------------------------------
+#include <thread>
+
+extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
+                                   const float *const *src_xyz, const int *nsrc,
+                                   const float *const *rec_xyz, const int *nrec,
+                                   const float *const *d_obs, float *const *grad, double *misfit,
+                                   size_t budget_bytes)
+{
+    if (nshots < 0) return wp_fail(nullptr, PROP_EINVAL, "nshots < 0");
+    if (nshots == 0) return PROP_OK;
+    if (!shots || !wavelet || !src_xyz || !nsrc || !rec_xyz || !nrec || !d_obs || !grad)
+        return wp_fail(nullptr, PROP_EINVAL, "NULL array argument");
+    for (int i = 0; i < nshots; i++) {
+        if (!shots[i]) return wp_fail(nullptr, PROP_EINVAL, "shot handle " + std::to_string(i) + " is NULL");
+        for (int j = 0; j < i; j++)
+            if (shots[j] == shots[i])
+                return wp_fail(nullptr, PROP_EINVAL, "shot handle " + std::to_string(i) + " repeats an earlier one");
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return wp_fail(nullptr, PROP_ECUDA, "cudaGetDevice failed");
+    if (budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return wp_fail(nullptr, PROP_ECUDA, "cudaMemGetInfo failed");
+        budget_bytes = fr / 10 * 9;
+    }
+    std::vector<size_t> need(nshots);
+    for (int i = 0; i < nshots; i++) need[i] = gradient_bytes(shots[i], nrec[i]);
+    std::vector<int> wave(nshots);
+    const int nw = prop_plan_waves(need.data(), nshots, budget_bytes, wave.data());
+    std::vector<int> rc(nshots, PROP_OK);
+    std::vector<double> mis(nshots, 0.0);
+    for (int w = 0; w < nw; w++) {
+        std::vector<std::thread> th;
+        for (int i = 0; i < nshots; i++) {
+            if (wave[i] != w) continue;
+            th.emplace_back([&, i] {
+                prop_s *P = shots[i];
+                if (cudaSetDevice(dev) != cudaSuccess) {
+                    rc[i] = wp_fail(P, PROP_ECUDA, "cudaSetDevice failed");
+                    return;
+                }
+                // private stream, ordered after the caller's stream and
+                // before anything the caller enqueues later
+                cudaStream_t own = P->stream, s = nullptr;
+                cudaEvent_t e0 = nullptr, e1 = nullptr;
+                if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+                    if (s) cudaStreamDestroy(s);
+                    if (e0) cudaEventDestroy(e0);
+                    rc[i] = wp_fail(P, PROP_ECUDA, "stream/event creation failed");
+                    return;
+                }
+                cudaEventRecord(e0, own);
+                cudaStreamWaitEvent(s, e0, 0);
+                P->stream = s;
+                rc[i] = prop_gradient(P, wavelet[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i], d_obs[i],
+                                      grad[i], &mis[i]);
+                cudaEventRecord(e1, s);
+                cudaStreamWaitEvent(own, e1, 0);
+                P->stream = own;
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+            });
+        }
+        for (auto &t : th) t.join();
+    }
+    int first = PROP_OK;
+    for (int i = 0; i < nshots; i++) {
+        if (misfit) misfit[i] = mis[i];
+        if (rc[i] && !first) {
+            first = rc[i];
+            tl_err = "shot " + std::to_string(i) + ": " + prop_last_error(shots[i]);
+        }
+    }
+    return first;
 }

@@ -694,12 +694,8 @@ int el_launch(prop_s *P, float *const *S, float dt)
               make_map(&mvz, S[2], g, B::RC, B::RR) && make_map(&mmu, P->mu, g, B::PC, B::PR);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = NSTAGE * VL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * TL<M>::SZ * sizeof(float) + 64;
-    static bool attr = false;
-    if (!attr) {
-        set_smem(el_vpass_tma<M>, s1);
-        set_smem(el_tpass_tma<M>, s2);
-        attr = true;
-    }
+    static const bool attr = (set_smem(el_vpass_tma<M>, s1), set_smem(el_tpass_tma<M>, s2), true);
+    (void)attr;
     el_vpass_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, s, P->bu, mxy, myy, mxz, mzz, myz, mb, xc, P->flag);
     el_tpass_tma<M><<<grd, blk, s2, P->stream>>>(g, P->w, s, P->lam, mvx, mvy, mvz, mmu, xc, P->flag);
     P->kern_launches += 2;
@@ -723,12 +719,8 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = NSTAGE * RL<M, ADJ>::SZ * sizeof(float) + 64,
                  s2 = NSTAGE * UL<M>::SZ * sizeof(float) + 64;
-    static bool attr = false;
-    if (!attr) {
-        set_smem(tti_rot_tma<M, ADJ>, s1);
-        set_smem(tti_upd_tma<M, ADJ>, s2);
-        attr = true;
-    }
+    static const bool attr = (set_smem(tti_rot_tma<M, ADJ>, s1), set_smem(tti_upd_tma<M, ADJ>, s2), true);
+    (void)attr;
     tti_rot_tma<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->th, P->ph, mp, mr,
                                                     me, md, t[0], t[1], t[2], t[3], t[4], t[5], xc, P->flag);
     tti_upd_tma<M, ADJ><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], mey, mfy, mez, mfz, P->m, P->eps,

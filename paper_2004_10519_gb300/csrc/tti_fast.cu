@@ -246,12 +246,9 @@ int launch(prop_s *P, float *const *S, const float *up, const float *ur, float *
     float *const *t = P->tmp;
     const size_t s1 = 2 * 2 * PG<M>::size(2) * sizeof(float);
     const size_t s2 = 2 * (2 * PG<M>::size(0) + 2 * PG<M>::size(1)) * sizeof(float);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tti_rot_p<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1);
-        cudaFuncSetAttribute(tti_upd_p<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2);
-        attr = true;
-    }
+    static const bool attr = (cudaFuncSetAttribute(tti_rot_p<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1),
+                              cudaFuncSetAttribute(tti_upd_p<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2), true);
+    (void)attr;
     prof_begin(P, ADJ ? 1 : 0);
     tti_rot_p<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->th, P->ph,
                                                    t[0], t[1], t[2], t[3], t[4], t[5], xc);

@@ -281,3 +281,98 @@ def random_state(n_fields, shape, seed, sigma_cells=1.5):
         u = smooth_noise(shape, sigma_cells, seed + i) * 2.0 - 1.0
         out.append(np.ascontiguousarray(u, dtype=np.float32))
     return out
+
+
+# --------------------------------------------------------------------------
+# batched shots on windows of one large model
+# --------------------------------------------------------------------------
+class UndulatingTTI:
+    """A large layered TTI model given in closed form, so that any window of
+    it can be drawn without building the whole volume.
+
+    Layers of constant vp (``nlayers`` from vmin to vmax with depth) are
+    bounded by interfaces that all follow one smooth seeded undulation
+    U(x, y) (a sum of a few random 2D cosine modes with wavelengths of
+    1.5-6 km and ``amp`` metres of total relief): a point (x, y, z) lies in
+    layer floor((z - U(x, y)) / thickness).  Anisotropy follows the velocity
+    (eps = eps_max (vp - vmin)/(vmax - vmin), delta = eps/2), the tilt is the
+    dip of the interfaces (tan theta = |grad U|) and the azimuth that of
+    grad U, folded to [0, 90 deg] -- the structure of the industry-scale
+    TTI recipe, without its small-scale noise."""
+
+    def __init__(self, seed, extent=(12500.0, 12500.0, 6250.0), nlayers=10, vmin=1.5,
+                 vmax=4.5, amp=400.0, nmodes=6, eps_max=0.3):
+        rng = np.random.default_rng(seed)
+        self.extent, self.nlayers, self.vmin, self.vmax = extent, nlayers, vmin, vmax
+        self.eps_max = eps_max
+        lam = rng.uniform(1500.0, 6000.0, nmodes)
+        ang = rng.uniform(0.0, 2 * math.pi, nmodes)
+        self.k = np.stack([np.cos(ang), np.sin(ang)], 1) * (2 * math.pi / lam)[:, None]
+        self.ph = rng.uniform(0.0, 2 * math.pi, nmodes)
+        self.a = rng.uniform(0.5, 1.0, nmodes)
+        self.a *= 0.5 * amp / self.a.sum()
+
+    def window(self, ox, oy, nx, ny, nz, h) -> dict:
+        """Model on the window whose first point is (ox, oy, 0) cells."""
+        x = (ox + np.arange(nx)) * h
+        y = (oy + np.arange(ny)) * h
+        X, Y = np.meshgrid(x, y, indexing="ij")
+        U = np.zeros((nx, ny))
+        Ux = np.zeros((nx, ny))
+        Uy = np.zeros((nx, ny))
+        for (kx, ky), ph, a in zip(self.k, self.ph, self.a):
+            arg = kx * X + ky * Y + ph
+            U += a * np.cos(arg)
+            s = -a * np.sin(arg)
+            Ux += s * kx
+            Uy += s * ky
+        thick = self.extent[2] / self.nlayers
+        vl = (self.vmin + (self.vmax - self.vmin) * np.arange(self.nlayers)
+              / max(self.nlayers - 1, 1)).astype(np.float32)
+        z = (np.arange(nz) * h).astype(np.float32)
+        zeta = z[None, None, :] - U.astype(np.float32)[:, :, None] + np.float32(0.5 * thick)
+        layer = np.clip(np.floor(zeta / np.float32(thick)), 0, self.nlayers - 1).astype(np.int8)
+        vp = vl[layer]
+        del zeta, layer
+        eps = (np.float32(self.eps_max / (self.vmax - self.vmin)) * (vp - np.float32(self.vmin)))
+        theta = np.arctan(np.hypot(Ux, Uy)).astype(np.float32)
+        phi = np.arctan2(np.abs(Uy), np.abs(Ux)).astype(np.float32)
+        full = lambda a2: np.ascontiguousarray(np.broadcast_to(a2[:, :, None], (nx, ny, nz)))
+        return {"vp": vp, "eps": eps, "delta": np.ascontiguousarray(0.5 * eps, dtype=np.float32),
+                "theta": full(theta), "phi": full(phi)}
+
+
+def tti_batch_shots(nshots=8, nt=150, seed=20045, size_range=(200, 600), nz=300, h=12.5,
+                    nbl=40, so=12, f0=12.0, global_cells=(1000, 1000, 500)):
+    """Batched-gradient workload: ``nshots`` TTI shots on windows with
+    nx, ny ~ U[size_range], nz fixed, at random offsets in a large
+    undulating-layer model of ``global_cells`` cells at h; source at the
+    window centre, 25 m deep; receivers every 4 cells at depth h.  Each shot
+    is (true problem, starting problem): the starting model replaces vp by a
+    linear increase with depth over the velocity range (other parameters
+    true).  One dt (CFL of the global velocity range) for all shots."""
+    rng = np.random.default_rng(seed)
+    gx, gy, gz = global_cells
+    model = UndulatingTTI(seed, extent=(gx * h, gy * h, gz * h))
+    vmax = model.vmax * math.sqrt(1 + 2 * model.eps_max)
+    dt = cfl_dt(h, vmax)
+    shots = []
+    for s in range(nshots):
+        nx, ny = (int(v) for v in rng.integers(size_range[0], size_range[1] + 1, 2))
+        ox = int(rng.integers(0, gx - nx + 1))
+        oy = int(rng.integers(0, gy - ny + 1))
+        m = model.window(ox, oy, nx, ny, nz, h)
+        src = np.array([[(nx // 2) * h, (ny // 2) * h, 25.0]], np.float32)
+        rec = carpet_receivers(0.0, 0.0, 4 * h, (nx - 1) // 4 + 1, (ny - 1) // 4 + 1, h)
+        wav = ricker(f0, dt, nt)[None, :]
+        name = f"tti-window-{nx}x{ny}x{nz}-at-{ox},{oy}-so{so}-nt{nt}"
+        true = Problem(TTI, nx, ny, nz, nbl, h, so, nt, dt, m, src, wav, rec, name=name)
+        z = (np.arange(nz) / max(nz - 1, 1)).astype(np.float32)
+        v0 = model.vmin + (model.vmax - model.vmin) * z
+        start = dict(m)
+        start["vp"] = np.ascontiguousarray(np.broadcast_to(v0[None, None, :], (nx, ny, nz)),
+                                           dtype=np.float32)
+        p0 = Problem(TTI, nx, ny, nz, nbl, h, so, nt, dt, start, src, wav, rec,
+                     name=name.replace("window", "window-start"))
+        shots.append((true, p0))
+    return shots

@@ -79,3 +79,39 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(wp, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         wp.lib()
+
+
+def test_wave_plan_first_fit_in_order(libpath):
+    """Host-side wave planner of the batched gradients: shots keep their
+    order, a wave never exceeds the budget unless one shot alone does."""
+    import paper_2004_10519_gb300 as wp
+    assert wp.plan_waves([5, 3, 4, 10, 1, 1], 8) == ([0, 0, 1, 2, 3, 3], 4)
+    assert wp.plan_waves([], 8) == ([], 0)
+    assert wp.plan_waves([9], 8) == ([0], 1)
+    assert wp.plan_waves([1] * 5, 100) == ([0] * 5, 1)
+    rng = __import__("numpy").random.default_rng(1)
+    b = [int(x) for x in rng.integers(1, 50, 40)]
+    waves, n = wp.plan_waves(b, 60)
+    assert waves == sorted(waves) and n == waves[-1] + 1
+    for w in range(n):
+        tot = sum(x for x, k in zip(b, waves) if k == w)
+        assert tot <= 60
+    L = wp.lib()
+    assert L.prop_plan_waves(None, -1, 10, None) == wp.PROP_EINVAL
+    assert L.prop_gradient_bytes(None, 10) == 0
+    assert L.prop_tile_planes(None) == 0
+
+
+def test_batch_argument_checks_need_no_gpu(libpath):
+    import paper_2004_10519_gb300 as wp
+    L = wp.lib()
+    n = None
+    assert L.prop_gradient_batch(n, 0, n, n, n, n, n, n, n, n, 0) == wp.PROP_OK
+    assert L.prop_gradient_batch(n, -1, n, n, n, n, n, n, n, n, 0) == wp.PROP_EINVAL
+    assert L.prop_gradient_batch(n, 2, n, n, n, n, n, n, n, n, 0) == wp.PROP_EINVAL
+    handles = (C.c_void_p * 2)(None, None)
+    arr = (C.c_void_p * 2)()
+    ints = (C.c_int * 2)(1, 1)
+    rc = L.prop_gradient_batch(handles, 2, arr, arr, ints, arr, ints, arr, arr, None, 0)
+    assert rc == wp.PROP_EINVAL
+    assert b"shot handle 0 is NULL" in L.prop_last_error(None)

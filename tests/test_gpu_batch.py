@@ -1,0 +1,111 @@
+"""Batched gradients (prop_gradient_batch): shots on model windows of
+different sizes, run concurrently in waves, give bitwise the gradients and
+misfits of one prop_gradient call per shot; two shots are checked against
+the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def wp():
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    return wp
+
+
+def window_shots(nt=60, h=10.0, nbl=6):
+    """TTI shots on windows (random offsets, different nx, ny) cut from one
+    layered model, source at the window centre near the surface."""
+    big = synth.layered_tti(52, 46, 36, 17, noise_sigma=3.0, smooth_sigma=1.5)
+    vmax = float(np.max(big["vp"] * np.sqrt(1 + 2 * big["eps"])))
+    dt = synth.cfl_dt(h, vmax)
+    shots = []
+    for (ox, oy, nx, ny) in [(0, 0, 30, 26), (14, 9, 36, 30), (20, 4, 28, 34)]:
+        m = {k: np.ascontiguousarray(v[ox:ox + nx, oy:oy + ny]) for k, v in big.items()}
+        src = np.array([[nx * h / 2 + 0.7, ny * h / 2 - 1.3, 3.2 * h]], np.float32)
+        rec = synth.carpet_receivers(4.1, 5.3, 3.0 * h, 8, 6, 1.7 * h)
+        p = synth.Problem(synth.TTI, nx, ny, 36, nbl, h, 8, nt, dt, m, src,
+                          synth.ricker(22.0, dt, nt)[None], rec)
+        p.vdamp = vmax * 1000.0
+        d_obs = oracle.Problem(p).forward()
+        p0 = synth.Problem(**{**p.__dict__, "model": synth.smooth_model(p.model, 3.0)})
+        shots.append((p0, d_obs.astype(np.float32)))
+    return shots
+
+
+def elastic_shot(nt=50):
+    nx, ny, nz, h = 22, 20, 24, 10.0
+    m = synth.random_elastic(nx, ny, nz, 8, 3.0)
+    dt = synth.cfl_dt(h, float(m["vp"].max()))
+    src = np.array([[nx * h / 2 + 0.4, ny * h / 2, nz * h / 2 - 0.6]], np.float32)
+    rec = synth.carpet_receivers(3.3, 4.4, 3.3 * h, 6, 5, 0.0)
+    p = synth.Problem(synth.ELASTIC, nx, ny, nz, 4, h, 8, nt, dt, m, src,
+                      synth.ricker(20.0, dt, nt)[None], rec)
+    d_obs = oracle.Problem(p).forward()
+    start = synth.random_elastic(nx, ny, nz, 5, 3.0)
+    start = {k: (0.5 * (start[k] + m[k])).astype(np.float32) for k in start}
+    return synth.Problem(**{**p.__dict__, "model": start}), d_obs.astype(np.float32)
+
+
+@pytest.fixture(scope="module")
+def shots():
+    return window_shots() + [elastic_shot()]
+
+
+@pytest.mark.parametrize("budget", [0, 1])
+def test_batch_equals_one_call_per_shot(wp, shots, budget):
+    """budget 0: one wave of four concurrent shots; budget 1: every shot its
+    own wave."""
+    ref = []
+    for p, d in shots:
+        prop = wp.Propagator.from_problem(p)
+        ref.append(prop.gradient(p.wavelet, p.src, p.rec, d))
+        prop.close()
+    props = [wp.Propagator.from_problem(p) for p, _ in shots]
+    grads, J = wp.gradient_batch(props, [p.wavelet for p, _ in shots], [p.src for p, _ in shots],
+                                 [p.rec for p, _ in shots], [d for _, d in shots],
+                                 budget_bytes=budget)
+    for i, (g, j) in enumerate(zip(grads, J)):
+        np.testing.assert_array_equal(g, ref[i][0], err_msg=f"shot {i}")
+        assert j == ref[i][1], i
+    # the handles stay usable after the batch
+    p, d = shots[0]
+    again = props[0].gradient(p.wavelet, p.src, p.rec, d)
+    np.testing.assert_array_equal(again[0], ref[0][0])
+    for pr in props:
+        pr.close()
+
+
+def test_batch_two_shots_against_oracle(wp, shots):
+    sel = [shots[0], shots[2]]
+    props = [wp.Propagator.from_problem(p) for p, _ in sel]
+    grads, J = wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                                 [p.rec for p, _ in sel], [d for _, d in sel])
+    for (p, d), g, j in zip(sel, grads, J):
+        g_ref, J_ref = oracle.Problem(p).gradient(d.astype(np.float64))
+        assert abs(j - J_ref) <= 1e-5 * J_ref
+        assert rel(g, g_ref) <= 1e-4
+
+
+def test_batch_reports_failing_shot(wp, shots):
+    """A shot whose observed data has the wrong receiver count is rejected
+    by the argument check of its own call; the error names the shot and the
+    other shots still produce their gradients."""
+    (p, d), (p2, d2) = shots[0], shots[1]
+    props = [wp.Propagator.from_problem(p), wp.Propagator.from_problem(p2)]
+    import paper_2004_10519_gb300 as m
+    with pytest.raises(m.PropError) as e:
+        m.gradient_batch(props, [p.wavelet, p2.wavelet], [p.src, p2.src], [p.rec, p2.rec[:0]],
+                         [d, d2])
+    assert "shot 1" in str(e.value)
+    for pr in props:
+        pr.close()

@@ -49,3 +49,24 @@ def test_tma_and_pipelined_paths_agree(kind, monkeypatch):
     for i in range(2):
         a, b = out["tma"][i], out["pipelined"][i]
         assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b), (kind, i)
+
+
+@pytest.mark.parametrize("kind", ["tti", "elastic"])
+def test_tile_planes_do_not_change_results(kind, monkeypatch):
+    """The autotuned x-extent of the stencil tiles only moves CTA boundaries:
+    traces are bitwise identical to the occupancy heuristic's."""
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    p = tti_problem(nt=40) if kind == "tti" else el_problem(nt=40)
+    out, planes = {}, {}
+    for tag, env in (("tuned", None), ("heuristic", "0")):
+        if env:
+            monkeypatch.setenv("WAVEPROP_AUTOTUNE", env)
+        else:
+            monkeypatch.delenv("WAVEPROP_AUTOTUNE", raising=False)
+        prop = wp.Propagator.from_problem(p)
+        planes[tag] = prop.tile_planes
+        out[tag] = prop.forward(p.wavelet, p.src, p.rec)
+        prop.close()
+    assert planes["tuned"] >= 8 and planes["heuristic"] >= 8
+    np.testing.assert_array_equal(out["tuned"], out["heuristic"])
