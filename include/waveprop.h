@@ -199,7 +199,7 @@ int prop_tile_planes(const prop_t *p);
  * would, with the same arguments, conventions and error codes, but every
  * device buffer it needs lives in one static device array of 48 MiB that the
  * library keeps on each GPU where it is used, from the first call there until
- * the process exits.  Problems that do not fit (TTI needs about 60 bytes per
+ * the process exits.  Problems that do not fit (TTI needs about 68 bytes per
  * computational grid point, elastic about 48, plus the wavelet, traces and
  * point tables) are rejected with PROP_EINVAL and a message giving the size.
  * The first call on a device looks up the array's address; make that first

@@ -252,209 +252,19 @@ el_grad_gather_kernel(GridDev g, const float *__restrict__ ep0, const float *__r
 }
 
 // ---------------------------------------------------------------------------
-// Tiled forward passes.  A CTA owns an FZ x FY tile of (y, z) columns and
-// streams along x over a chunk of planes.  x-derivatives come from
-// per-thread register queues (2M values), y/z-derivatives from shared-memory
-// planes with an M-point halo; values outside the grid read as 0.
+// Tiled transposed passes (tbar form, used by prop_step's adjoint).  A CTA
+// owns an FZ x FY tile of (y, z) columns and streams along x over a chunk of
+// planes.  x-derivatives come from per-thread register queues (2M values),
+// y/z-derivatives from shared-memory planes with an M-point halo; values
+// outside the grid read as 0.
 // ---------------------------------------------------------------------------
 constexpr int FZ = 32, FY = 16, FT = FZ * FY;
 
-WP_DEV float lz(const float *__restrict__ f, const GridDev &g, int x, int y, int z)
-{
-    return (x >= 0 && x < g.NX && y >= 0 && y < g.NY && z >= 0 && z < g.NZ)
-               ? __ldg(f + gidx(g, x, y, z)) : 0.f;
-}
 // taper of one staggered position from the per-axis tables
 WP_DEV float tp(const GridDev &g, int x, int hx, int y, int hy, int z, int hz)
 {
     return __ldg(g.tab + 2 * x + hx) * __ldg(g.tab + 2 * g.NX + 2 * y + hy) *
            __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * z + hz);
-}
-
-// velocity pass: v <- g (v + dt b_avg div tau)
-template <int M>
-__global__ void __launch_bounds__(FT, 2)
-el_v_tiled(GridDev g, FDW w, Fields9 s, const float *__restrict__ bu, int *flag, int check, int xc)
-{
-    constexpr int HY = FY + 2 * M, HZ = FZ + 2 * M, Q = 2 * M;
-    __shared__ float s_xy[HY][FZ], s_yy[HY][FZ], s_yz[HY][HZ], s_xz[FY][HZ], s_zz[FY][HZ];
-    const int tz = threadIdx.x, ty = threadIdx.y;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
-    const float *txx = s.f[3], *tyy = s.f[4], *tzz = s.f[5], *txy = s.f[6], *txz = s.f[7], *tyz = s.f[8];
-    // queues: qxx[j] = txx[x-M+1+j] (D+x), qxy[j] = txy[x-M+j], qxz[j] = txz[x-M+j] (D-x)
-    float qxx[Q], qxy[Q], qxz[Q];
-#pragma unroll
-    for (int j = 0; j < Q - 1; j++) {
-        qxx[j] = lz(txx, g, xa - M + 1 + j, y, z);
-        qxy[j] = lz(txy, g, xa - M + j, y, z);
-        qxz[j] = lz(txz, g, xa - M + j, y, z);
-    }
-    const bool act = y < g.NY && z < g.NZ;
-    const float c = g.dt * g.ih;
-    const long long sx = (long long)g.NY * g.NZ;
-    const int y1 = min(y + 1, g.NY - 1), z1 = min(z + 1, g.NZ - 1);
-    for (int x = xa; x < xb; x++) {
-        qxx[Q - 1] = lz(txx, g, x + M, y, z);
-        qxy[Q - 1] = lz(txy, g, x + M - 1, y, z);
-        qxz[Q - 1] = lz(txz, g, x + M - 1, y, z);
-        __syncthreads();
-        s_xy[ty + M][tz] = qxy[M];
-        s_xz[ty][tz + M] = qxz[M];
-        s_yy[ty + M][tz] = lz(tyy, g, x, y, z);
-        s_zz[ty][tz + M] = lz(tzz, g, x, y, z);
-        s_yz[ty + M][tz + M] = lz(tyz, g, x, y, z);
-        if (ty < M) {
-            const int ya = y0 - M + ty, yb = y0 + FY + ty;
-            s_xy[ty][tz] = lz(txy, g, x, ya, z);
-            s_yy[ty][tz] = lz(tyy, g, x, ya, z);
-            s_yz[ty][tz + M] = lz(tyz, g, x, ya, z);
-            s_xy[ty + FY + M][tz] = lz(txy, g, x, yb, z);
-            s_yy[ty + FY + M][tz] = lz(tyy, g, x, yb, z);
-            s_yz[ty + FY + M][tz + M] = lz(tyz, g, x, yb, z);
-        }
-        if (tz < M) {
-            const int za = z0 - M + tz, zb = z0 + FZ + tz;
-            s_xz[ty][tz] = lz(txz, g, x, y, za);
-            s_zz[ty][tz] = lz(tzz, g, x, y, za);
-            s_yz[ty + M][tz] = lz(tyz, g, x, y, za);
-            s_xz[ty][tz + FZ + M] = lz(txz, g, x, y, zb);
-            s_zz[ty][tz + FZ + M] = lz(tzz, g, x, y, zb);
-            s_yz[ty + M][tz + FZ + M] = lz(tyz, g, x, y, zb);
-        }
-        __syncthreads();
-        if (act) {
-            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
-#pragma unroll
-            for (int k = 1; k <= M; k++) {
-                const float b = w.b[k - 1];
-                d0 += b * ((qxx[M - 1 + k] - qxx[M - k]) +
-                           (s_xy[ty + M + k - 1][tz] - s_xy[ty + M - k][tz]) +
-                           (s_xz[ty][tz + M + k - 1] - s_xz[ty][tz + M - k]));
-                d1 += b * ((qxy[M + k - 1] - qxy[M - k]) +
-                           (s_yy[ty + M + k][tz] - s_yy[ty + M - k + 1][tz]) +
-                           (s_yz[ty + M][tz + M + k - 1] - s_yz[ty + M][tz + M - k]));
-                d2 += b * ((qxz[M + k - 1] - qxz[M - k]) +
-                           (s_yz[ty + M + k - 1][tz + M] - s_yz[ty + M - k][tz + M]) +
-                           (s_zz[ty][tz + M + k] - s_zz[ty][tz + M - k + 1]));
-            }
-            const long long q = gidx(g, x, y, z);
-            const float b0 = __ldg(bu + q);
-            const float bx = 0.5f * (b0 + __ldg(bu + (x + 1 < g.NX ? q + sx : q)));
-            const float by = 0.5f * (b0 + __ldg(bu + q + (long long)(y1 - y) * g.NZ));
-            const float bz = 0.5f * (b0 + __ldg(bu + q + (z1 - z)));
-            const float vx = tp(g, x, 1, y, 0, z, 0) * (s.f[0][q] + c * bx * d0);
-            const float vy = tp(g, x, 0, y, 1, z, 0) * (s.f[1][q] + c * by * d1);
-            const float vz = tp(g, x, 0, y, 0, z, 1) * (s.f[2][q] + c * bz * d2);
-            s.f[0][q] = vx;
-            s.f[1][q] = vy;
-            s.f[2][q] = vz;
-            if (check && !(isfinite(vx) && isfinite(vy) && isfinite(vz))) atomicOr(flag, 1);
-        }
-#pragma unroll
-        for (int j = 0; j < Q - 1; j++) {
-            qxx[j] = qxx[j + 1];
-            qxy[j] = qxy[j + 1];
-            qxz[j] = qxz[j + 1];
-        }
-    }
-}
-
-// stress pass: tau <- g (tau + dt (lambda tr(e) I + mu (grad v + grad v^T)))
-template <int M>
-__global__ void __launch_bounds__(FT, 2)
-el_t_tiled(GridDev g, FDW w, Fields9 s, const float *__restrict__ lam, const float *__restrict__ mu,
-           int *flag, int check, int xc)
-{
-    constexpr int HY = FY + 2 * M, HZ = FZ + 2 * M, Q = 2 * M;
-    __shared__ float s_vx[HY][HZ], s_vy[HY][HZ], s_vz[HY][HZ];
-    const int tz = threadIdx.x, ty = threadIdx.y;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
-    const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
-    // qvx[j] = vx[x-M+j] (D-x), qvy[j] = vy[x-M+1+j], qvz[j] = vz[x-M+1+j] (D+x)
-    float qvx[Q], qvy[Q], qvz[Q];
-#pragma unroll
-    for (int j = 0; j < Q - 1; j++) {
-        qvx[j] = lz(vxp, g, xa - M + j, y, z);
-        qvy[j] = lz(vyp, g, xa - M + 1 + j, y, z);
-        qvz[j] = lz(vzp, g, xa - M + 1 + j, y, z);
-    }
-    const bool act = y < g.NY && z < g.NZ;
-    const float c = g.dt * g.ih;
-    const long long sx = (long long)g.NY * g.NZ;
-    const long long dy1 = (long long)(min(y + 1, g.NY - 1) - y) * g.NZ;
-    const long long dz1 = min(z + 1, g.NZ - 1) - z;
-    for (int x = xa; x < xb; x++) {
-        qvx[Q - 1] = lz(vxp, g, x + M - 1, y, z);
-        qvy[Q - 1] = lz(vyp, g, x + M, y, z);
-        qvz[Q - 1] = lz(vzp, g, x + M, y, z);
-        __syncthreads();
-        s_vx[ty + M][tz + M] = qvx[M];
-        s_vy[ty + M][tz + M] = qvy[M - 1];
-        s_vz[ty + M][tz + M] = qvz[M - 1];
-        if (ty < M) {
-            const int ya = y0 - M + ty, yb = y0 + FY + ty;
-            s_vx[ty][tz + M] = lz(vxp, g, x, ya, z);
-            s_vy[ty][tz + M] = lz(vyp, g, x, ya, z);
-            s_vz[ty][tz + M] = lz(vzp, g, x, ya, z);
-            s_vx[ty + FY + M][tz + M] = lz(vxp, g, x, yb, z);
-            s_vy[ty + FY + M][tz + M] = lz(vyp, g, x, yb, z);
-            s_vz[ty + FY + M][tz + M] = lz(vzp, g, x, yb, z);
-        }
-        if (tz < M) {
-            const int za = z0 - M + tz, zb = z0 + FZ + tz;
-            s_vx[ty + M][tz] = lz(vxp, g, x, y, za);
-            s_vy[ty + M][tz] = lz(vyp, g, x, y, za);
-            s_vz[ty + M][tz] = lz(vzp, g, x, y, za);
-            s_vx[ty + M][tz + FZ + M] = lz(vxp, g, x, y, zb);
-            s_vy[ty + M][tz + FZ + M] = lz(vyp, g, x, y, zb);
-            s_vz[ty + M][tz + FZ + M] = lz(vzp, g, x, y, zb);
-        }
-        __syncthreads();
-        if (act) {
-            float exx = 0.f, eyy = 0.f, ezz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
-            const int cy = ty + M, cz = tz + M;
-#pragma unroll
-            for (int k = 1; k <= M; k++) {
-                const float b = w.b[k - 1];
-                exx += b * (qvx[M + k - 1] - qvx[M - k]);
-                eyy += b * (s_vy[cy + k - 1][cz] - s_vy[cy - k][cz]);
-                ezz += b * (s_vz[cy][cz + k - 1] - s_vz[cy][cz - k]);
-                gxy += b * ((s_vx[cy + k][cz] - s_vx[cy - k + 1][cz]) + (qvy[M - 1 + k] - qvy[M - k]));
-                gxz += b * ((s_vx[cy][cz + k] - s_vx[cy][cz - k + 1]) + (qvz[M - 1 + k] - qvz[M - k]));
-                gyz += b * ((s_vy[cy][cz + k] - s_vy[cy][cz - k + 1]) + (s_vz[cy + k][cz] - s_vz[cy - k + 1][cz]));
-            }
-            const long long q = gidx(g, x, y, z);
-            const long long dx1 = x + 1 < g.NX ? sx : 0;
-            const float l = __ldg(lam + q), m0 = __ldg(mu + q);
-            const float mx = __ldg(mu + q + dx1), my = __ldg(mu + q + dy1), mz = __ldg(mu + q + dz1);
-            const float mxy = 0.25f * (m0 + mx + my + __ldg(mu + q + dx1 + dy1));
-            const float mxz = 0.25f * (m0 + mx + mz + __ldg(mu + q + dx1 + dz1));
-            const float myz = 0.25f * (m0 + my + mz + __ldg(mu + q + dy1 + dz1));
-            const float tr = exx + eyy + ezz, m2 = 2.f * m0;
-            const float gn = tp(g, x, 0, y, 0, z, 0);
-            const float o0 = gn * (s.f[3][q] + c * (l * tr + m2 * exx));
-            const float o1 = gn * (s.f[4][q] + c * (l * tr + m2 * eyy));
-            const float o2 = gn * (s.f[5][q] + c * (l * tr + m2 * ezz));
-            const float o3 = tp(g, x, 1, y, 1, z, 0) * (s.f[6][q] + c * mxy * gxy);
-            const float o4 = tp(g, x, 1, y, 0, z, 1) * (s.f[7][q] + c * mxz * gxz);
-            const float o5 = tp(g, x, 0, y, 1, z, 1) * (s.f[8][q] + c * myz * gyz);
-            s.f[3][q] = o0; s.f[4][q] = o1; s.f[5][q] = o2;
-            s.f[6][q] = o3; s.f[7][q] = o4; s.f[8][q] = o5;
-            if (check && !(isfinite(o0) && isfinite(o1) && isfinite(o2) && isfinite(o3) &&
-                           isfinite(o4) && isfinite(o5)))
-                atomicOr(flag, 1);
-        }
-#pragma unroll
-        for (int j = 0; j < Q - 1; j++) {
-            qvx[j] = qvx[j + 1];
-            qvy[j] = qvy[j + 1];
-            qvz[j] = qvz[j + 1];
-        }
-    }
 }
 
 // ---- tiled adjoint passes -------------------------------------------------

@@ -55,6 +55,7 @@ struct prop_s {
     float vmax = 0.f;        // max model velocity used for the CFL rule
     // model (computational grid)
     float *m = nullptr, *eps = nullptr, *del = nullptr, *th = nullptr, *ph = nullptr;   // TTI
+    float *nrm[2] = {};      // TTI symmetry axis n_x, n_y (sign chosen so that n_z >= 0)
     float *bu = nullptr, *lam = nullptr, *mu = nullptr;                                 // elastic
     // state: TTI 4 fields (p_cur, r_cur, p_prev, r_prev); elastic 9 fields
     float *st[9] = {};
@@ -98,8 +99,6 @@ int tti_launch_step(prop_s *P, float *const *S, bool adjoint, const float *img_p
                     const float *img_r, float *grad);
 int tti_launch_fast(prop_s *P, float *const *S, bool adjoint, const float *img_p,
                     const float *img_r, float *grad);
-int tti_launch_tiled(prop_s *P, float *const *S, bool adjoint, const float *img_p,
-                     const float *img_r, float *grad);
 // elastic step in place on S (9 fields); adjoint: transposed step (tbar form)
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 // pipelined elastic step: forward, or transposed step in s = C tbar variables
@@ -155,6 +154,7 @@ int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const
 void prof_begin(prop_s *P, int id);
 void prof_end(prop_s *P, int id);
 void k_lame(prop_s *P);
+void k_normals(prop_s *P);
 
 // FD weights from the moment conditions (FP64 solve, FP32 result) and the
 // maximum of the discrete derivative symbol (CFL bound)

@@ -178,7 +178,7 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     float *phys, *wav, *stage, *out, *tabd, *fields[20] = {};
     int *flag;
     const size_t ntab = (size_t)(g.NX + g.NY + g.NZ) * (tti ? 1 : 2);
-    const int nmodel = tti ? 5 : 3, nstate = tti ? 4 : 9, ntmp = tti ? 6 : 0;
+    const int nmodel = tti ? 7 : 3, nstate = tti ? 4 : 9, ntmp = tti ? 6 : 0;
     auto layout = [&](Carver &C) -> int {
         for (int i = 0; i < nmodel + nstate + ntmp; i++) fields[i] = C.take<float>(N);
         phys = C.take<float>(np);
@@ -245,6 +245,7 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     int k = 0;
     if (tti) {
         P->m = fields[k++]; P->eps = fields[k++]; P->del = fields[k++]; P->th = fields[k++]; P->ph = fields[k++];
+        P->nrm[0] = fields[k++]; P->nrm[1] = fields[k++];
     } else {
         P->bu = fields[k++]; P->lam = fields[k++]; P->mu = fields[k++];
     }
@@ -267,6 +268,7 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
         k_extend(P, phys, mdst[i], (tti && i == 0) ? 1000.f : 1.f, (tti && i == 0) ? 1 : 0);
     }
     if (!tti) k_lame(P);
+    else k_normals(P);
     WP_CK(P, cudaMemcpyAsync(wav, wavelet, (size_t)nsrc * nt * sizeof(float), cudaMemcpyDefault, P->stream));
     for (int i = 0; i < nstate; i++) WP_CK(P, cudaMemsetAsync(P->st[i], 0, N * sizeof(float), P->stream));
     WP_CK(P, cudaMemsetAsync(flag, 0, sizeof(int), P->stream));

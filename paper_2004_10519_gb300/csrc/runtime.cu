@@ -261,7 +261,7 @@ static void free_snaps(prop_s *P)
 
 static void free_all(prop_s *P)
 {
-    float *arrs[] = {P->m, P->eps, P->del, P->th, P->ph, P->bu, P->lam, P->mu};
+    float *arrs[] = {P->m, P->eps, P->del, P->th, P->ph, P->nrm[0], P->nrm[1], P->bu, P->lam, P->mu};
     for (float *a : arrs) cudaFree(a);
     for (auto &a : P->st) cudaFree(a);
     for (auto &a : P->ast) cudaFree(a);
@@ -389,6 +389,7 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     g.px = d->nx; g.py = d->ny; g.pz = d->nz;
     g.NX = d->nx + 2 * d->nbl; g.NY = d->ny + 2 * d->nbl; g.NZ = d->nz + 2 * d->nbl;
     g.N = (long long)g.NX * g.NY * g.NZ;
+    if (g.N >= (1LL << 32)) return wp_fail(P, PROP_EINVAL, "computational grid above 2^32 - 1 points");
     g.h = d->h; g.ih = 1.f / d->h;
     if (!fd_weights(P->M, P->w.c, P->w.b)) return wp_fail(P, PROP_EINVAL, "FD weights");
 
@@ -454,6 +455,9 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
         WP_TRY(upload(2, P->del, 1.f, 0));
         WP_TRY(upload(3, P->th, 1.f, 0));
         WP_TRY(upload(4, P->ph, 1.f, 0));
+        WP_MALLOC(P, P->nrm[0], N * sizeof(float), "symmetry axis");
+        WP_MALLOC(P, P->nrm[1], N * sizeof(float), "symmetry axis");
+        k_normals(P);
     } else {
         WP_TRY(upload(0, P->bu, 1.f, 0));    // vp  -> b      (k_lame)
         WP_TRY(upload(1, P->lam, 1.f, 0));   // vs  -> lambda

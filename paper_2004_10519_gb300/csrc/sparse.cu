@@ -139,6 +139,21 @@ __global__ void lame_kernel(long long n, float *vp_b, float *vs_l, float *rho_mu
     rho_mu[q] = rho * vs * vs;
 }
 
+// TTI symmetry axis n = (sin th cos ph, sin th sin ph, cos th) (Sec. III-A),
+// stored as (n_x, n_y) with the sign flipped where cos th < 0 so that
+// n_z = sqrt(1 - n_x^2 - n_y^2); evaluated in double once per model
+__global__ void normals_kernel(long long n, const float *th, const float *ph, float *nx, float *ny)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double st, ct, sp, cp;
+    sincos((double)th[q], &st, &ct);
+    sincos((double)ph[q], &sp, &cp);
+    const double sg = ct < 0.0 ? -1.0 : 1.0;
+    nx[q] = (float)(sg * st * cp);
+    ny[q] = (float)(sg * st * sp);
+}
+
 // adjoint of the edge-replication extension (gather form)
 __global__ void fold_kernel(GridDev g, const float *__restrict__ comp, float *__restrict__ phys)
 {
@@ -379,6 +394,11 @@ void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode)
 void k_lame(prop_s *P)
 {
     lame_kernel<<<nblk(P->g.N), NB, 0, P->stream>>>(P->g.N, P->bu, P->lam, P->mu);
+}
+
+void k_normals(prop_s *P)
+{
+    normals_kernel<<<nblk(P->g.N), NB, 0, P->stream>>>(P->g.N, P->th, P->ph, P->nrm[0], P->nrm[1]);
 }
 
 void k_fold(prop_s *P, const float *comp, float *phys)

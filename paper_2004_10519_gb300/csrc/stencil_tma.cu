@@ -1,14 +1,18 @@
 // Stencil passes fed by the Tensor Memory Accelerator (sm_103a).
 //
-// Each CTA owns a 32(z) x 16(y) tile of columns and streams along x.  For
-// every plane the y/z-halo boxes of the differentiated fields are fetched by
-// one thread with cp.async.bulk.tensor into a 3-stage shared-memory ring
-// (mbarrier completion); out-of-grid elements arrive as zeros, which is the
-// zero extension of the finite-difference operators.  Threads only do
-// arithmetic on shared memory; x-derivatives use per-thread register queues
-// fed by plain coalesced loads, pointwise fields are plain loads issued one
-// plane ahead.  Every mbarrier wait is bounded in time: on expiry the CTA
-// sets bit 2 of the error word and leaves (no hang).
+// Each CTA owns a 32(z) x 16(y) tile of columns and streams along x; each of
+// its 256 threads updates two adjacent z points, so shared-memory taps and
+// global accesses are 8-byte (float2) and every y-tap row serves two
+// outputs.  For every plane the y/z-halo boxes of the differentiated fields
+// are fetched by one thread with cp.async.bulk.tensor into a 3-stage
+// shared-memory ring (mbarrier completion); out-of-grid elements arrive as
+// zeros, which is the zero extension of the finite-difference operators.
+// z-derivatives read a window of M+1 float2 per field; x-derivatives use
+// per-thread float2 register queues fed by coalesced loads one plane ahead.
+// Offsets are 32-bit (the runtime keeps N below 2^32).  Every mbarrier wait
+// is bounded in time: on expiry the thread sets bit 2 of the error word and
+// a shared abort flag; at the next plane barrier the whole CTA leaves, after
+// its lead thread has waited (again bounded) for the copies still in flight.
 //
 // Elastic (Sec. IV, Eq. elas1, elastic listing):
 //   velocity pass  v <- g (v + dt b_avg Dtau(tau))
@@ -16,8 +20,10 @@
 // The transposed step is the same two passes with dt -> -dt in the variables
 // (b_avg vbar, g C tbar) (the taper, C and the averages are pointwise and
 // commute), so adjoint modelling uses these kernels too.
-// TTI (Sec. III-A): rotation pass (D of p, r or of zeta = C lam) and update
-// pass (divergence, coupling, damped leapfrog, fused imaging).
+// TTI (Sec. III-A): rotation pass (D of p, r or of zeta = C lam, projected on
+// the symmetry axis n) and update pass (divergence, coupling, damped
+// leapfrog, fused imaging).  n is read from two precomputed arrays (n_x, n_y
+// with n_z >= 0; the operators are quadratic in n, so n and -n agree).
 #include "tile.cuh"
 
 #include <cuda.h>
@@ -26,8 +32,11 @@
 
 namespace {
 
-using namespace tile;
+using tile::FY;
+using tile::FZ;
 
+constexpr int TZ2 = FZ / 2;        // threads along z, two points each
+constexpr int NT2 = TZ2 * FY;      // threads per CTA
 constexpr int NSTAGE = 3;
 
 struct F9 {
@@ -85,6 +94,19 @@ WP_DEV bool mbar_wait(uint64_t *bar, uint32_t parity)
         if (gtimer() - t0 > 2000000000ull) return false;
     return true;
 }
+// lead thread after an abort: wait (bounded) for the stages of iterations
+// [a, b] that may still be in flight, so no copy lands after the CTA exits
+WP_DEV void drain(uint64_t *bars, int a, int b)
+{
+    for (int j = a < 0 ? 0 : a; j <= b; j++) mbar_wait(&bars[j % NSTAGE], (uint32_t)((j / NSTAGE) & 1));
+}
+
+// 8-byte accesses (z even, NZ even: always aligned)
+WP_DEV float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+WP_DEV float2 ldg2(const float *__restrict__ p, unsigned o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); }
+WP_DEV float2 ld2(const float *p, unsigned o) { return *reinterpret_cast<const float2 *>(p + o); }
+WP_DEV void st2(float *p, unsigned o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); }
+WP_DEV float2 dif2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 constexpr int al32(int n) { return (n + 31) & ~31; }   // 128-byte aligned float offsets
 
@@ -99,19 +121,32 @@ struct BX {
     static constexpr int YS = al32(YR * YC), ZS = al32(ZR * ZC), RS = al32(RR * RC), PS = al32(PR * PC);
 };
 
-// one bounded wait of the whole CTA for stage `st` of iteration `it`;
-// returns false (uniformly) if any thread gave up
-WP_DEV bool stage_wait(uint64_t *bars, int it, int *err)
+// z window of 2M+2 values starting M before the thread's first point:
+// w[M + d] = f(z + d), d = -M .. M+1
+template <int M>
+WP_DEV void zwin(const float *row, int cz, float (&w)[2 * M + 2])
 {
-    const int st = it % NSTAGE;
-    const bool ok = mbar_wait(&bars[st], (uint32_t)((it / NSTAGE) & 1));
-    const int bad = __syncthreads_or(!ok);
-    if (bad) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) atomicOr(err, 2);
-        return false;
+#pragma unroll
+    for (int j = 0; j <= M; j++) {
+        const float2 a = lds2(row + cz - M + 2 * j);
+        w[2 * j] = a.x;
+        w[2 * j + 1] = a.y;
     }
-    return true;
 }
+
+// plane ring bookkeeping shared by the kernels
+struct Ring {
+    int st = 0;
+    uint32_t ph = 0;
+    WP_DEV int refill() const { return st == 0 ? NSTAGE - 1 : st - 1; }   // stage of iteration it+NSTAGE-1
+    WP_DEV void next()
+    {
+        if (++st == NSTAGE) {
+            st = 0;
+            ph ^= 1u;
+        }
+    }
+};
 
 // ---------------------------------------------------------------------------
 // elastic velocity pass
@@ -127,7 +162,7 @@ struct VL {
 };
 
 template <int M>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT2, 2)
 el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
              const __grid_constant__ CUtensorMap mxy, const __grid_constant__ CUtensorMap myy,
              const __grid_constant__ CUtensorMap mxz, const __grid_constant__ CUtensorMap mzz,
@@ -138,12 +173,13 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
     using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
+    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y;
     const bool lead = tz == 0 && ty == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const int z = z0 + 2 * tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     const float *txx = s.f[3], *txy = s.f[6], *txz = s.f[7];
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
@@ -158,77 +194,100 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
         fence_init();
+        s_abort = 0;
     }
     __syncthreads();
     if (lead)
-        for (int i = 0; i < NSTAGE - 1 && xa + i < xb; i++) issue(xa + i, i);
+        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
     const bool act = y < g.NY && z < g.NZ;
-    const long long pl = (long long)g.NY * g.NZ;
-    const long long q0 = act ? (long long)y * g.NZ + z : 0;
-    float qxx[Q], qxy[Q], qxz[Q];
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    float2 qxx[Q], qxy[Q], qxz[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
         const int xq = xa - M + 1 + j, xr = xa - M + j;
-        qxx[j] = act && xq >= 0 && xq < g.NX ? __ldg(txx + xq * pl + q0) : 0.f;
-        qxy[j] = act && xr >= 0 && xr < g.NX ? __ldg(txy + xr * pl + q0) : 0.f;
-        qxz[j] = act && xr >= 0 && xr < g.NX ? __ldg(txz + xr * pl + q0) : 0.f;
+        qxx[j] = act && xq >= 0 && xq < g.NX ? ldg2(txx, xq * pl + q0) : Z2;
+        qxy[j] = act && xr >= 0 && xr < g.NX ? ldg2(txy, xr * pl + q0) : Z2;
+        qxz[j] = act && xr >= 0 && xr < g.NX ? ldg2(txz, xr * pl + q0) : Z2;
     }
-    float nxx = 0.f, nxy = 0.f, nxz = 0.f, nbx = 0.f, nv0 = 0.f, nv1 = 0.f, nv2 = 0.f;
+    float2 nxx = Z2, nxy = Z2, nxz = Z2, nbx = Z2, nv0 = Z2, nv1 = Z2, nv2 = Z2;
     auto fetch = [&](int x) {
         if (!act) return;
-        nxx = x + M < g.NX ? __ldg(txx + (x + M) * pl + q0) : 0.f;
-        nxy = x + M - 1 < g.NX ? __ldg(txy + (x + M - 1) * pl + q0) : 0.f;
-        nxz = x + M - 1 < g.NX ? __ldg(txz + (x + M - 1) * pl + q0) : 0.f;
-        nbx = __ldg(bu + min(x + 1, g.NX - 1) * pl + q0);
-        nv0 = s.f[0][x * pl + q0];
-        nv1 = s.f[1][x * pl + q0];
-        nv2 = s.f[2][x * pl + q0];
+        const unsigned o = x * pl + q0;
+        nxx = x + M < g.NX ? ldg2(txx, o + M * pl) : Z2;
+        nxy = x + M - 1 < g.NX ? ldg2(txy, o + (M - 1) * pl) : Z2;
+        nxz = x + M - 1 < g.NX ? ldg2(txz, o + (M - 1) * pl) : Z2;
+        nbx = ldg2(bu, x + 1 < g.NX ? o + pl : o);
+        nv0 = ld2(s.f[0], o);
+        nv1 = ld2(s.f[1], o);
+        nv2 = ld2(s.f[2], o);
     };
     fetch(xa);
     const float c = g.dt * g.ih;
-    const float gzn = __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * min(z, g.NZ - 1));
-    const float gzh = __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * min(z, g.NZ - 1) + 1);
-    const float gyn = __ldg(g.tab + 2 * g.NX + 2 * min(y, g.NY - 1));
-    const float gyh = __ldg(g.tab + 2 * g.NX + 2 * min(y, g.NY - 1) + 1);
-    const int cy = ty + M, cz = tz + B::MZ;
+    const float *tabz = g.tab + 2 * (g.NX + g.NY);
+    const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
+    const float gzn0 = __ldg(tabz + 2 * zc0), gzh0 = __ldg(tabz + 2 * zc0 + 1);
+    const float gzn1 = __ldg(tabz + 2 * zc1), gzh1 = __ldg(tabz + 2 * zc1 + 1);
+    const float gyn = __ldg(g.tab + 2 * g.NX + 2 * yc), gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
+    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz;
+    const int yb1 = y + 1 < g.NY ? ty + 1 : ty;           // +1 box row of b(y+1), clamped
+    const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;       // +1 box column of b(z+2), clamped
+    Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
         qxx[Q - 1] = nxx;
         qxy[Q - 1] = nxy;
         qxz[Q - 1] = nxz;
-        const float v0 = nv0, v1 = nv1, v2 = nv2, bxn = nbx;
+        const float2 v0 = nv0, v1 = nv1, v2 = nv2, bxn = nbx;
         // all threads are past iteration it-1: its stage may be refilled
         __syncthreads();
-        if (lead && x + NSTAGE - 1 < xb) issue(x + NSTAGE - 1, (it + NSTAGE - 1) % NSTAGE);
+        if (s_abort) {
+            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+            return;
+        }
+        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
         if (x + 1 < xb) fetch(x + 1);
-        if (!stage_wait(bars, it, err)) return;
-        const float *S = sm + (it % NSTAGE) * L::SZ;
-        if (act) {
-            const float *sxy = S + L::OXY, *syy = S + L::OYY, *sxz = S + L::OXZ, *szz = S + L::OZZ,
-                        *syz = S + L::OYZ, *sb = S + L::OB;
-            float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+        const bool ok = mbar_wait(&bars[R.st], R.ph);
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(err, 2);
+        }
+        if (ok && act) {
+            const float *S = sm + R.st * L::SZ;
+            const float *sxy = S + L::OXY, *syy = S + L::OYY, *syz = S + L::OYZ, *sb = S + L::OB;
+            float wxz[2 * M + 2], wyz[2 * M + 2], wzz[2 * M + 2];
+            zwin<M>(S + L::OXZ + ty * B::ZC, cz, wxz);
+            zwin<M>(syz + cy * B::RC, cz, wyz);
+            zwin<M>(S + L::OZZ + ty * B::ZC, cz, wzz);
+            float d0a = 0.f, d0b = 0.f, d1a = 0.f, d1b = 0.f, d2a = 0.f, d2b = 0.f;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
                 const float b = w.b[k - 1];
-                d0 += b * ((qxx[M - 1 + k] - qxx[M - k]) +
-                           (sxy[(cy + k - 1) * B::YC + tz] - sxy[(cy - k) * B::YC + tz]) +
-                           (sxz[ty * B::ZC + cz + k - 1] - sxz[ty * B::ZC + cz - k]));
-                d1 += b * ((qxy[M + k - 1] - qxy[M - k]) +
-                           (syy[(cy + k) * B::YC + tz] - syy[(cy - k + 1) * B::YC + tz]) +
-                           (syz[cy * B::RC + cz + k - 1] - syz[cy * B::RC + cz - k]));
-                d2 += b * ((qxz[M + k - 1] - qxz[M - k]) +
-                           (syz[(cy + k - 1) * B::RC + cz] - syz[(cy - k) * B::RC + cz]) +
-                           (szz[ty * B::ZC + cz + k] - szz[ty * B::ZC + cz - k + 1]));
+                const float2 ax = dif2(qxx[M - 1 + k], qxx[M - k]);
+                const float2 ay = dif2(lds2(sxy + (cy + k - 1) * B::YC + c2), lds2(sxy + (cy - k) * B::YC + c2));
+                d0a += b * (ax.x + ay.x + (wxz[M + k - 1] - wxz[M - k]));
+                d0b += b * (ax.y + ay.y + (wxz[M + k] - wxz[M - k + 1]));
+                const float2 bx_ = dif2(qxy[M + k - 1], qxy[M - k]);
+                const float2 by_ = dif2(lds2(syy + (cy + k) * B::YC + c2), lds2(syy + (cy - k + 1) * B::YC + c2));
+                d1a += b * (bx_.x + by_.x + (wyz[M + k - 1] - wyz[M - k]));
+                d1b += b * (bx_.y + by_.y + (wyz[M + k] - wyz[M - k + 1]));
+                const float2 cx_ = dif2(qxz[M + k - 1], qxz[M - k]);
+                const float2 cy_ = dif2(lds2(syz + (cy + k - 1) * B::RC + cz), lds2(syz + (cy - k) * B::RC + cz));
+                d2a += b * (cx_.x + cy_.x + (wzz[M + k] - wzz[M - k + 1]));
+                d2b += b * (cx_.y + cy_.y + (wzz[M + k + 1] - wzz[M - k + 2]));
             }
-            const float b0 = sb[ty * B::PC + tz];
-            const float bx = 0.5f * (b0 + bxn);
-            const float by = 0.5f * (b0 + sb[(y + 1 < g.NY ? ty + 1 : ty) * B::PC + tz]);
-            const float bz = 0.5f * (b0 + sb[ty * B::PC + (z + 1 < g.NZ ? tz + 1 : tz)]);
+            const float2 b0 = lds2(sb + ty * B::PC + c2);
+            const float2 bY = lds2(sb + yb1 * B::PC + c2);
+            const float bz2 = sb[ty * B::PC + zb2];
             const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
-            const long long q = x * pl + q0;
-            s.f[0][q] = gxh * gyn * gzn * (v0 + c * bx * d0);
-            s.f[1][q] = gxn * gyh * gzn * (v1 + c * by * d1);
-            s.f[2][q] = gxn * gyn * gzh * (v2 + c * bz * d2);
+            const unsigned q = x * pl + q0;
+            st2(s.f[0], q, gxh * gyn * gzn0 * (v0.x + c * (0.5f * (b0.x + bxn.x)) * d0a),
+                gxh * gyn * gzn1 * (v0.y + c * (0.5f * (b0.y + bxn.y)) * d0b));
+            st2(s.f[1], q, gxn * gyh * gzn0 * (v1.x + c * (0.5f * (b0.x + bY.x)) * d1a),
+                gxn * gyh * gzn1 * (v1.y + c * (0.5f * (b0.y + bY.y)) * d1b));
+            st2(s.f[2], q, gxn * gyn * gzh0 * (v2.x + c * (0.5f * (b0.x + b0.y)) * d2a),
+                gxn * gyn * gzh1 * (v2.y + c * (0.5f * (b0.y + bz2)) * d2b));
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -236,7 +295,10 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
             qxy[j] = qxy[j + 1];
             qxz[j] = qxz[j + 1];
         }
+        R.next();
     }
+    __syncthreads();
+    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -252,7 +314,7 @@ struct TL {
 };
 
 template <int M>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT2, 2)
 el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
              const __grid_constant__ CUtensorMap mvx, const __grid_constant__ CUtensorMap mvy,
              const __grid_constant__ CUtensorMap mvz, const __grid_constant__ CUtensorMap mmu, int xc,
@@ -262,12 +324,13 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
     using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
+    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y;
     const bool lead = tz == 0 && ty == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const int z = z0 + 2 * tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
@@ -281,85 +344,119 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
         fence_init();
+        s_abort = 0;
     }
     __syncthreads();
     if (lead)
-        for (int i = 0; i < NSTAGE - 1 && xa + i < xb; i++) issue(xa + i, i);
+        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
     const bool act = y < g.NY && z < g.NZ;
-    const long long pl = (long long)g.NY * g.NZ;
-    const long long q0 = act ? (long long)y * g.NZ + z : 0;
-    float qvx[Q], qvy[Q], qvz[Q];
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    float2 qvx[Q], qvy[Q], qvz[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
         const int xr = xa - M + j, xq = xa - M + 1 + j;
-        qvx[j] = act && xr >= 0 && xr < g.NX ? __ldg(vxp + xr * pl + q0) : 0.f;
-        qvy[j] = act && xq >= 0 && xq < g.NX ? __ldg(vyp + xq * pl + q0) : 0.f;
-        qvz[j] = act && xq >= 0 && xq < g.NX ? __ldg(vzp + xq * pl + q0) : 0.f;
+        qvx[j] = act && xr >= 0 && xr < g.NX ? ldg2(vxp, xr * pl + q0) : Z2;
+        qvy[j] = act && xq >= 0 && xq < g.NX ? ldg2(vyp, xq * pl + q0) : Z2;
+        qvz[j] = act && xq >= 0 && xq < g.NX ? ldg2(vzp, xq * pl + q0) : Z2;
     }
-    float nvx = 0.f, nvy = 0.f, nvz = 0.f;
+    float2 nvx = Z2, nvy = Z2, nvz = Z2;
     auto fetch = [&](int x) {
         if (!act) return;
-        nvx = x + M - 1 < g.NX ? __ldg(vxp + (x + M - 1) * pl + q0) : 0.f;
-        nvy = x + M < g.NX ? __ldg(vyp + (x + M) * pl + q0) : 0.f;
-        nvz = x + M < g.NX ? __ldg(vzp + (x + M) * pl + q0) : 0.f;
+        const unsigned o = x * pl + q0;
+        nvx = x + M - 1 < g.NX ? ldg2(vxp, o + (M - 1) * pl) : Z2;
+        nvy = x + M < g.NX ? ldg2(vyp, o + M * pl) : Z2;
+        nvz = x + M < g.NX ? ldg2(vzp, o + M * pl) : Z2;
     };
     fetch(xa);
     const float c = g.dt * g.ih;
-    const int zc = min(z, g.NZ - 1), yc = min(y, g.NY - 1);
-    const float gzn = __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * zc),
-                gzh = __ldg(g.tab + 2 * (g.NX + g.NY) + 2 * zc + 1);
+    const float *tabz = g.tab + 2 * (g.NX + g.NY);
+    const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
+    const float gzn0 = __ldg(tabz + 2 * zc0), gzh0 = __ldg(tabz + 2 * zc0 + 1);
+    const float gzn1 = __ldg(tabz + 2 * zc1), gzh1 = __ldg(tabz + 2 * zc1 + 1);
     const float gyn = __ldg(g.tab + 2 * g.NX + 2 * yc), gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
-    const int cy = ty + M, cz = tz + B::MZ;
-    const int y1 = y + 1 < g.NY ? ty + 1 : ty, z1 = z + 1 < g.NZ ? tz + 1 : tz;
+    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz;
+    const int yb1 = y + 1 < g.NY ? ty + 1 : ty;
+    const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;
+    Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
         qvx[Q - 1] = nvx;
         qvy[Q - 1] = nvy;
         qvz[Q - 1] = nvz;
         __syncthreads();
-        if (lead && x + NSTAGE - 1 < xb) issue(x + NSTAGE - 1, (it + NSTAGE - 1) % NSTAGE);
-        const long long q = x * pl + q0;
-        float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f, t4 = 0.f, t5 = 0.f, l = 0.f;
+        if (s_abort) {
+            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+            return;
+        }
+        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
+        const unsigned q = x * pl + q0;
+        float2 t0 = Z2, t1 = Z2, t2 = Z2, t3 = Z2, t4 = Z2, t5 = Z2, l = Z2;
         if (act) {
-            t0 = s.f[3][q]; t1 = s.f[4][q]; t2 = s.f[5][q];
-            t3 = s.f[6][q]; t4 = s.f[7][q]; t5 = s.f[8][q];
-            l = __ldg(lam + q);
+            t0 = ld2(s.f[3], q); t1 = ld2(s.f[4], q); t2 = ld2(s.f[5], q);
+            t3 = ld2(s.f[6], q); t4 = ld2(s.f[7], q); t5 = ld2(s.f[8], q);
+            l = ldg2(lam, q);
         }
         if (x + 1 < xb) fetch(x + 1);
-        if (!stage_wait(bars, it, err)) return;
-        const float *S = sm + (it % NSTAGE) * L::SZ;
-        if (act) {
+        const bool ok = mbar_wait(&bars[R.st], R.ph);
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(err, 2);
+        }
+        if (ok && act) {
+            const float *S = sm + R.st * L::SZ;
             const float *svx = S + L::OVX, *svy = S + L::OVY, *svz = S + L::OVZ;
-            float exx = 0.f, eyy = 0.f, ezz = 0.f, gxy = 0.f, gxz = 0.f, gyz = 0.f;
+            float wvx[2 * M + 2], wvy[2 * M + 2], wvz[2 * M + 2];
+            zwin<M>(svx + cy * B::RC, cz, wvx);
+            zwin<M>(svy + cy * B::RC, cz, wvy);
+            zwin<M>(svz + cy * B::RC, cz, wvz);
+            float exa = 0.f, exb = 0.f, eya = 0.f, eyb = 0.f, eza = 0.f, ezb = 0.f;
+            float gxya = 0.f, gxyb = 0.f, gxza = 0.f, gxzb = 0.f, gyza = 0.f, gyzb = 0.f;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
                 const float b = w.b[k - 1];
-                exx += b * (qvx[M + k - 1] - qvx[M - k]);
-                eyy += b * (svy[(cy + k - 1) * B::RC + cz] - svy[(cy - k) * B::RC + cz]);
-                ezz += b * (svz[cy * B::RC + cz + k - 1] - svz[cy * B::RC + cz - k]);
-                gxy += b * ((svx[(cy + k) * B::RC + cz] - svx[(cy - k + 1) * B::RC + cz]) +
-                            (qvy[M - 1 + k] - qvy[M - k]));
-                gxz += b * ((svx[cy * B::RC + cz + k] - svx[cy * B::RC + cz - k + 1]) +
-                            (qvz[M - 1 + k] - qvz[M - k]));
-                gyz += b * ((svy[cy * B::RC + cz + k] - svy[cy * B::RC + cz - k + 1]) +
-                            (svz[(cy + k) * B::RC + cz] - svz[(cy - k + 1) * B::RC + cz]));
+                const float2 dx = dif2(qvx[M + k - 1], qvx[M - k]);
+                exa += b * dx.x;
+                exb += b * dx.y;
+                const float2 dy = dif2(lds2(svy + (cy + k - 1) * B::RC + cz), lds2(svy + (cy - k) * B::RC + cz));
+                eya += b * dy.x;
+                eyb += b * dy.y;
+                eza += b * (wvz[M + k - 1] - wvz[M - k]);
+                ezb += b * (wvz[M + k] - wvz[M - k + 1]);
+                const float2 xy = dif2(lds2(svx + (cy + k) * B::RC + cz), lds2(svx + (cy - k + 1) * B::RC + cz));
+                const float2 yx = dif2(qvy[M - 1 + k], qvy[M - k]);
+                gxya += b * (xy.x + yx.x);
+                gxyb += b * (xy.y + yx.y);
+                const float2 zx = dif2(qvz[M - 1 + k], qvz[M - k]);
+                gxza += b * ((wvx[M + k] - wvx[M - k + 1]) + zx.x);
+                gxzb += b * ((wvx[M + k + 1] - wvx[M - k + 2]) + zx.y);
+                const float2 zy = dif2(lds2(svz + (cy + k) * B::RC + cz), lds2(svz + (cy - k + 1) * B::RC + cz));
+                gyza += b * ((wvy[M + k] - wvy[M - k + 1]) + zy.x);
+                gyzb += b * ((wvy[M + k + 1] - wvy[M - k + 2]) + zy.y);
             }
             const float *R0 = S + L::OM0, *R1 = S + L::OM1;
-            const float m0 = R0[ty * B::PC + tz], my = R0[y1 * B::PC + tz], mz = R0[ty * B::PC + z1];
-            const float mx = R1[ty * B::PC + tz], mxy_ = R1[y1 * B::PC + tz], mxz_ = R1[ty * B::PC + z1];
-            const float myz_ = R0[y1 * B::PC + z1];
-            const float mxy = 0.25f * (m0 + mx + my + mxy_);
-            const float mxz = 0.25f * (m0 + mx + mz + mxz_);
-            const float myz = 0.25f * (m0 + my + mz + myz_);
-            const float tr = exx + eyy + ezz, m2 = 2.f * m0;
+            const float2 m0 = lds2(R0 + ty * B::PC + c2), my = lds2(R0 + yb1 * B::PC + c2);
+            const float2 mx = lds2(R1 + ty * B::PC + c2), mxy_ = lds2(R1 + yb1 * B::PC + c2);
+            const float m0z = R0[ty * B::PC + zb2], myz = R0[yb1 * B::PC + zb2], mxz = R1[ty * B::PC + zb2];
             const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
-            const float gn = gxn * gyn * gzn;
-            s.f[3][q] = gn * (t0 + c * (l * tr + m2 * exx));
-            s.f[4][q] = gn * (t1 + c * (l * tr + m2 * eyy));
-            s.f[5][q] = gn * (t2 + c * (l * tr + m2 * ezz));
-            s.f[6][q] = gxh * gyh * gzn * (t3 + c * mxy * gxy);
-            s.f[7][q] = gxh * gyn * gzh * (t4 + c * mxz * gxz);
-            s.f[8][q] = gxn * gyh * gzh * (t5 + c * myz * gyz);
+            const float gn0 = gxn * gyn * gzn0, gn1 = gxn * gyn * gzn1;
+            // averages of mu over the 4 nodes around each edge (the pair's
+            // second lane is the first point's z+1 neighbour)
+            const float mxya = 0.25f * (m0.x + mx.x + my.x + mxy_.x);
+            const float mxza = 0.25f * (m0.x + mx.x + m0.y + mx.y);
+            const float myza = 0.25f * (m0.x + my.x + m0.y + my.y);
+            const float mxyb = 0.25f * (m0.y + mx.y + my.y + mxy_.y);
+            const float mxzb = 0.25f * (m0.y + mx.y + m0z + mxz);
+            const float myzb = 0.25f * (m0.y + my.y + m0z + myz);
+            const float tra = exa + eya + eza, trb = exb + eyb + ezb;
+            const float m2a = 2.f * m0.x, m2b = 2.f * m0.y;
+            st2(s.f[3], q, gn0 * (t0.x + c * (l.x * tra + m2a * exa)), gn1 * (t0.y + c * (l.y * trb + m2b * exb)));
+            st2(s.f[4], q, gn0 * (t1.x + c * (l.x * tra + m2a * eya)), gn1 * (t1.y + c * (l.y * trb + m2b * eyb)));
+            st2(s.f[5], q, gn0 * (t2.x + c * (l.x * tra + m2a * eza)), gn1 * (t2.y + c * (l.y * trb + m2b * ezb)));
+            st2(s.f[6], q, gxh * gyh * gzn0 * (t3.x + c * mxya * gxya), gxh * gyh * gzn1 * (t3.y + c * mxyb * gxyb));
+            st2(s.f[7], q, gxh * gyn * gzh0 * (t4.x + c * mxza * gxza), gxh * gyn * gzh1 * (t4.y + c * mxzb * gxzb));
+            st2(s.f[8], q, gxn * gyh * gzh0 * (t5.x + c * myza * gyza), gxn * gyh * gzh1 * (t5.y + c * myzb * gyzb));
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -367,7 +464,10 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
             qvy[j] = qvy[j + 1];
             qvz[j] = qvz[j + 1];
         }
+        R.next();
     }
+    __syncthreads();
+    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -382,10 +482,10 @@ struct RL {
 };
 
 template <int M, int ADJ>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT2, 2)
 tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
             const float *__restrict__ eps, const float *__restrict__ del,
-            const float *__restrict__ th, const float *__restrict__ ph,
+            const float *__restrict__ nxa, const float *__restrict__ nya,
             const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mr,
             const __grid_constant__ CUtensorMap me, const __grid_constant__ CUtensorMap md,
             float *__restrict__ ex, float *__restrict__ ey, float *__restrict__ ez,
@@ -395,12 +495,13 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
+    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * FZ + tz;
+    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * TZ2 + tz;
     const bool lead = tid == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const int z = z0 + 2 * tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
         mbar_expect(&bars[st], L::BYTES);
@@ -414,95 +515,140 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
         fence_init();
+        s_abort = 0;
     }
     __syncthreads();
     if (lead)
-        for (int i = 0; i < NSTAGE - 1 && xa + i < xb; i++) issue(xa + i, i);
+        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
     const bool act = y < g.NY && z < g.NZ;
-    const long long pl = (long long)g.NY * g.NZ;
-    const long long q0 = act ? (long long)y * g.NZ + z : 0;
-    // (p, r) or zeta = C (lam_p, lam_r) at own column, plane x
-    auto own = [&](int x, float &a, float &b) {
-        a = b = 0.f;
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    // (p, r) or zeta = C (lam_p, lam_r) at the thread's pair, plane x
+    auto own = [&](int x, float2 &a, float2 &b) {
+        a = b = Z2;
         if (!act || x < 0 || x >= g.NX) return;
-        const long long q = x * pl + q0;
-        const float u = __ldg(p + q), v = __ldg(r + q);
-        if (!ADJ) { a = u; b = v; return; }
-        const float c1 = 1.f + 2.f * __ldg(eps + q), c2 = sqrtf(1.f + 2.f * __ldg(del + q));
-        a = c1 * u + c2 * v;
-        b = c2 * u + v;
+        const unsigned q = x * pl + q0;
+        const float2 u = ldg2(p, q), v = ldg2(r, q);
+        if (!ADJ) {
+            a = u;
+            b = v;
+            return;
+        }
+        const float2 e = ldg2(eps, q), d = ldg2(del, q);
+        const float c1a = 1.f + 2.f * e.x, c2a = sqrtf(1.f + 2.f * d.x);
+        const float c1b = 1.f + 2.f * e.y, c2b = sqrtf(1.f + 2.f * d.y);
+        a = make_float2(c1a * u.x + c2a * v.x, c1b * u.y + c2b * v.y);
+        b = make_float2(c2a * u.x + v.x, c2b * u.y + v.y);
     };
-    float qp[Q], qr[Q];
+    float2 qp[Q], qr[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) own(xa - M + j, qp[j], qr[j]);
-    float np_ = 0.f, nr_ = 0.f, nth = 0.f, nph = 0.f;
+    float2 np_ = Z2, nr_ = Z2, nnx = Z2, nny = Z2;
     auto fetch = [&](int x) {
         own(x + M, np_, nr_);
         if (act) {
-            nth = __ldg(th + x * pl + q0);
-            nph = __ldg(ph + x * pl + q0);
+            nnx = ldg2(nxa, x * pl + q0);
+            nny = ldg2(nya, x * pl + q0);
         }
     };
     fetch(xa);
-    const int cy = ty + M, cz = tz + B::MZ;
+    const int cy = ty + M, cz = B::MZ + 2 * tz;
     const int ci = cy * B::RC + cz;
+    Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
         qp[Q - 1] = np_;
         qr[Q - 1] = nr_;
-        const float th_ = nth, ph_ = nph;
+        const float2 n0 = nnx, n1 = nny;
         __syncthreads();
-        if (lead && x + NSTAGE - 1 < xb) issue(x + NSTAGE - 1, (it + NSTAGE - 1) % NSTAGE);
+        if (s_abort) {
+            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+            return;
+        }
+        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
         if (x + 1 < xb) fetch(x + 1);
-        if (!stage_wait(bars, it, err)) return;
-        float *S = sm + (it % NSTAGE) * L::SZ;
+        const bool ok = mbar_wait(&bars[R.st], R.ph);
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(err, 2);
+        }
+        float *S = sm + R.st * L::SZ;
         if (ADJ) {
             // zeta = C lam over the whole rectangle, in place (each thread a share)
-            float *sp = S + L::OP, *sr = S + L::OR;
-            const float *se = S + L::OE, *sd = S + L::OD;
-            for (int i = tid; i < B::RR * B::RC; i += NT) {
-                const float c1 = 1.f + 2.f * se[i], c2 = sqrtf(1.f + 2.f * sd[i]);
-                const float u = sp[i], v = sr[i];
-                sp[i] = c1 * u + c2 * v;
-                sr[i] = c2 * u + v;
+            if (ok) {
+                float *sp = S + L::OP, *sr = S + L::OR;
+                const float *se = S + L::OE, *sd = S + L::OD;
+                for (int i = tid; i < B::RR * B::RC; i += NT2) {
+                    const float c1 = 1.f + 2.f * se[i], c2 = sqrtf(1.f + 2.f * sd[i]);
+                    const float u = sp[i], v = sr[i];
+                    sp[i] = c1 * u + c2 * v;
+                    sr[i] = c2 * u + v;
+                }
             }
             __syncthreads();
         }
-        if (act) {
+        if (ok && act) {
             const float *sp = S + L::OP, *sr = S + L::OR;
-            float gp0 = 0.f, gp1 = 0.f, gp2 = 0.f, gr0 = 0.f, gr1 = 0.f, gr2 = 0.f;
+            float wp[2 * M + 2], wr[2 * M + 2];
+            zwin<M>(sp + cy * B::RC, cz, wp);
+            zwin<M>(sr + cy * B::RC, cz, wr);
+            float gp0a = 0.f, gp0b = 0.f, gp1a = 0.f, gp1b = 0.f, gp2a = 0.f, gp2b = 0.f;
+            float gr0a = 0.f, gr0b = 0.f, gr1a = 0.f, gr1b = 0.f, gr2a = 0.f, gr2b = 0.f;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
                 const float c = w.c[k - 1];
-                gp0 += c * (qp[M + k] - qp[M - k]);
-                gr0 += c * (qr[M + k] - qr[M - k]);
-                gp1 += c * (sp[ci + k * B::RC] - sp[ci - k * B::RC]);
-                gr1 += c * (sr[ci + k * B::RC] - sr[ci - k * B::RC]);
-                gp2 += c * (sp[ci + k] - sp[ci - k]);
-                gr2 += c * (sr[ci + k] - sr[ci - k]);
+                const float2 px_ = dif2(qp[M + k], qp[M - k]), rx_ = dif2(qr[M + k], qr[M - k]);
+                gp0a += c * px_.x;
+                gp0b += c * px_.y;
+                gr0a += c * rx_.x;
+                gr0b += c * rx_.y;
+                const float2 py_ = dif2(lds2(sp + ci + k * B::RC), lds2(sp + ci - k * B::RC));
+                const float2 ry_ = dif2(lds2(sr + ci + k * B::RC), lds2(sr + ci - k * B::RC));
+                gp1a += c * py_.x;
+                gp1b += c * py_.y;
+                gr1a += c * ry_.x;
+                gr1b += c * ry_.y;
+                gp2a += c * (wp[M + k] - wp[M - k]);
+                gp2b += c * (wp[M + k + 1] - wp[M - k + 1]);
+                gr2a += c * (wr[M + k] - wr[M - k]);
+                gr2b += c * (wr[M + k + 1] - wr[M - k + 1]);
             }
-            float st, ct, sph, cph;
-            sincosf(th_, &st, &ct);
-            sincosf(ph_, &sph, &cph);
-            const float n0 = st * cph, n1 = st * sph, n2 = ct;
-            gp0 *= g.ih; gp1 *= g.ih; gp2 *= g.ih;
-            gr0 *= g.ih; gr1 *= g.ih; gr2 *= g.ih;
-            const float wp = n0 * gp0 + n1 * gp1 + n2 * gp2;
-            const float wr = n0 * gr0 + n1 * gr1 + n2 * gr2;
-            const long long q = x * pl + q0;
-            ex[q] = gp0 - n0 * wp;
-            ey[q] = gp1 - n1 * wp;
-            ez[q] = gp2 - n2 * wp;
-            fx[q] = n0 * wr;
-            fy[q] = n1 * wr;
-            fz[q] = n2 * wr;
+            const float ih = g.ih;
+            const unsigned q = x * pl + q0;
+            const float gp[2][3] = {{gp0a * ih, gp1a * ih, gp2a * ih}, {gp0b * ih, gp1b * ih, gp2b * ih}};
+            const float gr[2][3] = {{gr0a * ih, gr1a * ih, gr2a * ih}, {gr0b * ih, gr1b * ih, gr2b * ih}};
+            const float nx2[2] = {n0.x, n0.y}, ny2[2] = {n1.x, n1.y};
+            float o[2][6];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const float a0 = nx2[i], a1 = ny2[i];
+                const float a2 = sqrtf(fmaxf(0.f, 1.f - a0 * a0 - a1 * a1));
+                const float wpn = a0 * gp[i][0] + a1 * gp[i][1] + a2 * gp[i][2];
+                const float wrn = a0 * gr[i][0] + a1 * gr[i][1] + a2 * gr[i][2];
+                o[i][0] = gp[i][0] - a0 * wpn;
+                o[i][1] = gp[i][1] - a1 * wpn;
+                o[i][2] = gp[i][2] - a2 * wpn;
+                o[i][3] = a0 * wrn;
+                o[i][4] = a1 * wrn;
+                o[i][5] = a2 * wrn;
+            }
+            st2(ex, q, o[0][0], o[1][0]);
+            st2(ey, q, o[0][1], o[1][1]);
+            st2(ez, q, o[0][2], o[1][2]);
+            st2(fx, q, o[0][3], o[1][3]);
+            st2(fy, q, o[0][4], o[1][4]);
+            st2(fz, q, o[0][5], o[1][5]);
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
             qp[j] = qp[j + 1];
             qr[j] = qr[j + 1];
         }
+        R.next();
     }
+    __syncthreads();
+    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -516,7 +662,7 @@ struct UL {
 };
 
 template <int M, int ADJ>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT2, 2)
 tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
             const __grid_constant__ CUtensorMap mey, const __grid_constant__ CUtensorMap mfy,
             const __grid_constant__ CUtensorMap mez, const __grid_constant__ CUtensorMap mfz,
@@ -529,12 +675,13 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
+    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y;
     const bool lead = tz == 0 && ty == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX);
+    const int z = z0 + 2 * tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
         mbar_expect(&bars[st], L::BYTES);
@@ -546,91 +693,124 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
         fence_init();
+        s_abort = 0;
     }
     __syncthreads();
     if (lead)
-        for (int i = 0; i < NSTAGE - 1 && xa + i < xb; i++) issue(xa + i, i);
+        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
     const bool act = y < g.NY && z < g.NZ;
-    const long long pl = (long long)g.NY * g.NZ;
-    const long long q0 = act ? (long long)y * g.NZ + z : 0;
-    float qe[Q], qf[Q];
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    float2 qe[Q], qf[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
         const int xq = xa - M + j;
         const bool in = act && xq >= 0 && xq < g.NX;
-        qe[j] = in ? __ldg(ex + xq * pl + q0) : 0.f;
-        qf[j] = in ? __ldg(fx + xq * pl + q0) : 0.f;
+        qe[j] = in ? ldg2(ex, xq * pl + q0) : Z2;
+        qf[j] = in ? ldg2(fx, xq * pl + q0) : Z2;
     }
-    float ne = 0.f, nf = 0.f;
+    float2 ne = Z2, nf = Z2;
     auto fetch = [&](int x) {
         const bool in = act && x + M < g.NX;
-        ne = in ? __ldg(ex + (x + M) * pl + q0) : 0.f;
-        nf = in ? __ldg(fx + (x + M) * pl + q0) : 0.f;
+        ne = in ? ldg2(ex, (x + M) * pl + q0) : Z2;
+        nf = in ? ldg2(fx, (x + M) * pl + q0) : Z2;
     };
     fetch(xa);
     const float *sx = g.tab, *sy = g.tab + g.NX, *sz = g.tab + g.NX + g.NY;
     const float dt2 = g.dt * g.dt, hdt = 0.5f * g.dt;
-    const float syz = act ? __ldg(sy + y) + __ldg(sz + z) : 0.f;
-    const int iy = (ty + M) * B::YC + tz, iz = ty * B::ZC + tz + B::MZ;
+    const float syv = act ? __ldg(sy + y) : 0.f;
+    const float syz0 = act ? syv + __ldg(sz + z) : 0.f, syz1 = act ? syv + __ldg(sz + z + 1) : 0.f;
+    const int c2 = 2 * tz;
+    const int iy = (ty + M) * B::YC + c2, izr = ty * B::ZC, cz = B::MZ + c2;
+    Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
         qe[Q - 1] = ne;
         qf[Q - 1] = nf;
         __syncthreads();
-        if (lead && x + NSTAGE - 1 < xb) issue(x + NSTAGE - 1, (it + NSTAGE - 1) % NSTAGE);
-        const long long q = x * pl + q0;
-        float mm = 1.f, e_ = 0.f, d_ = 0.f, p1 = 0.f, r1 = 0.f, p0 = 0.f, r0 = 0.f;
+        if (s_abort) {
+            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+            return;
+        }
+        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
+        const unsigned q = x * pl + q0;
+        float2 mm = make_float2(1.f, 1.f), e_ = Z2, d_ = Z2, p1 = Z2, r1 = Z2, p0 = Z2, r0 = Z2;
         if (act) {
-            mm = __ldg(m + q);
+            mm = ldg2(m, q);
             if (!ADJ) {
-                e_ = __ldg(eps + q);
-                d_ = __ldg(del + q);
+                e_ = ldg2(eps, q);
+                d_ = ldg2(del, q);
             }
-            p1 = __ldg(pc + q);
-            r1 = __ldg(rc + q);
-            p0 = pp[q];
-            r0 = rp[q];
+            p1 = ldg2(pc, q);
+            r1 = ldg2(rc, q);
+            p0 = ld2(pp, q);
+            r0 = ld2(rp, q);
         }
         if (x + 1 < xb) fetch(x + 1);
-        if (!stage_wait(bars, it, err)) return;
-        const float *S = sm + (it % NSTAGE) * L::SZ;
-        if (act) {
-            const float *sey = S + L::OEY, *sfy = S + L::OFY, *sez = S + L::OEZ, *sfz = S + L::OFZ;
-            float h0 = 0.f, hz = 0.f;
+        const bool ok = mbar_wait(&bars[R.st], R.ph);
+        if (!ok) {
+            s_abort = 1;
+            atomicOr(err, 2);
+        }
+        if (ok && act) {
+            const float *S = sm + R.st * L::SZ;
+            const float *sey = S + L::OEY, *sfy = S + L::OFY;
+            float we[2 * M + 2], wf[2 * M + 2];
+            zwin<M>(S + L::OEZ + izr, cz, we);
+            zwin<M>(S + L::OFZ + izr, cz, wf);
+            float h0a = 0.f, h0b = 0.f, hza = 0.f, hzb = 0.f;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
                 const float c = w.c[k - 1];
-                h0 += c * ((qe[M + k] - qe[M - k]) + (sey[iy + k * B::YC] - sey[iy - k * B::YC]) +
-                           (sez[iz + k] - sez[iz - k]));
-                hz += c * ((qf[M + k] - qf[M - k]) + (sfy[iy + k * B::YC] - sfy[iy - k * B::YC]) +
-                           (sfz[iz + k] - sfz[iz - k]));
+                const float2 ex_ = dif2(qe[M + k], qe[M - k]), fx_ = dif2(qf[M + k], qf[M - k]);
+                const float2 ey_ = dif2(lds2(sey + iy + k * B::YC), lds2(sey + iy - k * B::YC));
+                const float2 fy_ = dif2(lds2(sfy + iy + k * B::YC), lds2(sfy + iy - k * B::YC));
+                h0a += c * (ex_.x + ey_.x + (we[M + k] - we[M - k]));
+                h0b += c * (ex_.y + ey_.y + (we[M + k + 1] - we[M - k + 1]));
+                hza += c * (fx_.x + fy_.x + (wf[M + k] - wf[M - k]));
+                hzb += c * (fx_.y + fy_.y + (wf[M + k + 1] - wf[M - k + 1]));
             }
-            h0 *= g.ih;
-            hz *= g.ih;
-            float Lp, Lr;
-            if (!ADJ) {
-                const float a = 1.f + 2.f * e_, s2 = sqrtf(1.f + 2.f * d_);
-                Lp = a * h0 + s2 * hz;
-                Lr = s2 * h0 + hz;
-            } else {
-                Lp = h0;
-                Lr = hz;
+            const float sxv = __ldg(sx + x);
+            const float h0[2] = {h0a * g.ih, h0b * g.ih}, hz[2] = {hza * g.ih, hzb * g.ih};
+            const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
+            const float P1[2] = {p1.x, p1.y}, R1[2] = {r1.x, r1.y}, P0[2] = {p0.x, p0.y}, R0[2] = {r0.x, r0.y};
+            const float SYZ[2] = {syz0, syz1};
+            float pn[2], rn[2], Lp[2], Lr[2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                if (!ADJ) {
+                    const float a = 1.f + 2.f * E2[i], s2 = sqrtf(1.f + 2.f * D2[i]);
+                    Lp[i] = a * h0[i] + s2 * hz[i];
+                    Lr[i] = s2 * h0[i] + hz[i];
+                } else {
+                    Lp[i] = h0[i];
+                    Lr[i] = hz[i];
+                }
+                const float sd = hdt * (sxv + SYZ[i]);
+                const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
+                pn[i] = (dt2 * Lp[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
+                rn[i] = (dt2 * Lr[i] + 2.f * M2[i] * R1[i] - Bc * R0[i]) / A;
             }
-            const float sd = hdt * (__ldg(sx + x) + syz);
-            const float A = mm * (1.f + sd), Bc = mm * (1.f - sd);
-            const float pn = (dt2 * Lp + 2.f * mm * p1 - Bc * p0) / A;
-            const float rn = (dt2 * Lr + 2.f * mm * r1 - Bc * r0) / A;
-            pp[q] = pn;
-            rp[q] = rn;
-            if (ADJ && grad) grad[q] -= dt2 * (__ldg(up + q) * Lp + __ldg(ur + q) * Lr) / mm;
-            if (check && !(isfinite(pn) && isfinite(rn))) atomicOr(flag, 1);
+            st2(pp, q, pn[0], pn[1]);
+            st2(rp, q, rn[0], rn[1]);
+            if (ADJ && grad) {
+                const float2 u = ldg2(up, q), v = ldg2(ur, q), gg = ld2(grad, q);
+                st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
+                    gg.y - dt2 * (u.y * Lp[1] + v.y * Lr[1]) / M2[1]);
+            }
+            if (check && !(isfinite(pn[0]) && isfinite(rn[0]) && isfinite(pn[1]) && isfinite(rn[1])))
+                atomicOr(flag, 1);
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
             qe[j] = qe[j + 1];
             qf[j] = qf[j + 1];
         }
+        R.next();
     }
+    __syncthreads();
+    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -671,9 +851,9 @@ bool make_map(CUtensorMap *m, const float *base, const GridDev &g, int bz, int b
 }
 
 template <class K>
-void set_smem(K kernel, size_t bytes)
+bool set_smem(K kernel, size_t bytes)
 {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
 template <int M>
@@ -683,7 +863,7 @@ int el_launch(prop_s *P, float *const *S, float dt)
     GridDev g = P->g;
     g.dt = dt;
     const int xc = P->xchunk;
-    dim3 blk(FZ, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    dim3 blk(TZ2, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     F9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
     CUtensorMap mxy, myy, mxz, mzz, myz, mb, mvx, mvy, mvz, mmu;
@@ -694,7 +874,7 @@ int el_launch(prop_s *P, float *const *S, float dt)
               make_map(&mvz, S[2], g, B::RC, B::RR) && make_map(&mmu, P->mu, g, B::PC, B::PR);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = NSTAGE * VL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * TL<M>::SZ * sizeof(float) + 64;
-    static const bool attr = (set_smem(el_vpass_tma<M>, s1), set_smem(el_tpass_tma<M>, s2), true);
+    static const bool attr = set_smem(el_vpass_tma<M>, s1) && set_smem(el_tpass_tma<M>, s2);
     (void)attr;
     el_vpass_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, s, P->bu, mxy, myy, mxz, mzz, myz, mb, xc, P->flag);
     el_tpass_tma<M><<<grd, blk, s2, P->stream>>>(g, P->w, s, P->lam, mvx, mvy, mvz, mmu, xc, P->flag);
@@ -709,7 +889,7 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     using B = BX<M>;
     const GridDev &g = P->g;
     const int xc = P->xchunk;
-    dim3 blk(FZ, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    dim3 blk(TZ2, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     float *const *t = P->tmp;
     CUtensorMap mp, mr, me, md, mey, mfy, mez, mfz;
     bool ok = make_map(&mp, S[0], g, B::RC, B::RR) && make_map(&mr, S[1], g, B::RC, B::RR) &&
@@ -719,10 +899,11 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = NSTAGE * RL<M, ADJ>::SZ * sizeof(float) + 64,
                  s2 = NSTAGE * UL<M>::SZ * sizeof(float) + 64;
-    static const bool attr = (set_smem(tti_rot_tma<M, ADJ>, s1), set_smem(tti_upd_tma<M, ADJ>, s2), true);
+    static const bool attr = set_smem(tti_rot_tma<M, ADJ>, s1) && set_smem(tti_upd_tma<M, ADJ>, s2);
     (void)attr;
-    tti_rot_tma<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->th, P->ph, mp, mr,
-                                                    me, md, t[0], t[1], t[2], t[3], t[4], t[5], xc, P->flag);
+    tti_rot_tma<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->nrm[0],
+                                                    P->nrm[1], mp, mr, me, md, t[0], t[1], t[2], t[3],
+                                                    t[4], t[5], xc, P->flag);
     tti_upd_tma<M, ADJ><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], mey, mfy, mez, mfz, P->m, P->eps,
                                                     P->del, S[0], S[1], S[2], S[3], up, ur, grad, P->flag,
                                                     P->d.check_nan, xc, P->flag);
@@ -733,11 +914,12 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
 
 }  // namespace
 
-// TMA-fed passes need 16-byte row strides (NZ a multiple of 4) and the
-// driver's tensor-map encoder
+// TMA-fed passes need 16-byte row strides (NZ a multiple of 4), the
+// driver's tensor-map encoder and (TTI) the symmetry-axis arrays
 bool tma_usable(const prop_s *P)
 {
-    return P->g.NZ % 4 == 0 && encode_fn() != nullptr && getenv("WAVEPROP_NO_TMA") == nullptr;
+    return P->g.NZ % 4 == 0 && encode_fn() != nullptr && getenv("WAVEPROP_NO_TMA") == nullptr &&
+           (P->d.kind != PROP_TTI || (P->nrm[0] && P->nrm[1]));
 }
 
 // elastic step with time step dt_sign * dt (forward: +1; adjoint modelling

@@ -38,8 +38,8 @@ WP_DEV void src_pair(const GridDev &g, const float *__restrict__ p, const float 
 template <int M, int ADJ>
 __global__ void __launch_bounds__(NT, 2)
 tti_rot_p(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
-          const float *__restrict__ eps, const float *__restrict__ del, const float *__restrict__ th,
-          const float *__restrict__ ph, float *__restrict__ ex, float *__restrict__ ey,
+          const float *__restrict__ eps, const float *__restrict__ del, const float *__restrict__ nxa,
+          const float *__restrict__ nya, float *__restrict__ ex, float *__restrict__ ey,
           float *__restrict__ ez, float *__restrict__ fx, float *__restrict__ fy,
           float *__restrict__ fz, int xc)
 {
@@ -81,11 +81,11 @@ tti_rot_p(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict
                 sr[hs.off[k]] = hr[k];
             }
         __syncthreads();
-        float th_ = 0.f, ph_ = 0.f;
+        float n0 = 0.f, n1 = 0.f;
         const long long q = act ? gidx(g, x, y, z) : 0;
         if (act) {
-            th_ = __ldg(th + q);
-            ph_ = __ldg(ph + q);
+            n0 = __ldg(nxa + q);
+            n1 = __ldg(nya + q);
         }
         if (x + 1 < xb) fetch(x + 1);
         if (act) {
@@ -100,10 +100,8 @@ tti_rot_p(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict
                 gp2 += c * (sp[ci + k] - sp[ci - k]);
                 gr2 += c * (sr[ci + k] - sr[ci - k]);
             }
-            float st, ct, sph, cph;
-            sincosf(th_, &st, &ct);
-            sincosf(ph_, &sph, &cph);
-            const float n0 = st * cph, n1 = st * sph, n2 = ct;
+            // symmetry axis from the precomputed (n_x, n_y), n_z >= 0
+            const float n2 = sqrtf(fmaxf(0.f, 1.f - n0 * n0 - n1 * n1));
             gp0 *= g.ih; gp1 *= g.ih; gp2 *= g.ih;
             gr0 *= g.ih; gr1 *= g.ih; gr2 *= g.ih;
             const float wp = n0 * gp0 + n1 * gp1 + n2 * gp2;
@@ -250,7 +248,7 @@ int launch(prop_s *P, float *const *S, const float *up, const float *ur, float *
                               cudaFuncSetAttribute(tti_upd_p<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2), true);
     (void)attr;
     prof_begin(P, ADJ ? 1 : 0);
-    tti_rot_p<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->th, P->ph,
+    tti_rot_p<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->nrm[0], P->nrm[1],
                                                    t[0], t[1], t[2], t[3], t[4], t[5], xc);
     tti_upd_p<M, ADJ><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[1], t[2], t[3], t[4], t[5], P->m,
                                                    P->eps, P->del, S[0], S[1], S[2], S[3], up, ur,

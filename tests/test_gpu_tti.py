@@ -62,6 +62,20 @@ def test_forward_parity_ragged(wp, so, shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
+def test_any_tilt_and_azimuth(wp, shape):
+    """Tilts beyond 90 degrees and azimuths of any sign: the kernels store the
+    symmetry axis with n_z >= 0 (n and -n give the same operator, which is
+    quadratic in n); the oracle uses theta and phi as given."""
+    p = ragged_tti(8, nt=60, shape=shape)
+    rng = np.random.default_rng(9)
+    p.model["theta"] = rng.uniform(0.0, np.pi, p.model["theta"].shape).astype(np.float32)
+    p.model["phi"] = rng.uniform(-np.pi, np.pi, p.model["phi"].shape).astype(np.float32)
+    tr = wp.Propagator.from_problem(p).forward(p.wavelet, p.src, p.rec)
+    ref = oracle.Problem(p).forward()
+    assert rel(tr, ref) <= TOL
+
+
+@pytest.mark.parametrize("shape", SHAPES)
 @pytest.mark.parametrize("so", [8, 12])
 def test_adjoint_parity_and_dot(wp, so, shape):
     p = ragged_tti(so, nt=60, shape=shape)
