@@ -473,7 +473,7 @@ int launch_step(prop_s *P, float *const *S, bool adjoint)
     dim3 blk(TZ, TY, 1), grd((g.NZ + TZ - 1) / TZ, (g.NY + TY - 1) / TY, g.NX);
     Fields9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
-    if (!adjoint) return tma_usable(P) ? el_launch_tma(P, S, 1.f) : el_launch_fast(P, S, false);
+    if (!adjoint) return tma_usable(P) ? el_launch_tma(P, S, 1.f) : el_launch_fast(P, S, 1.f);
     prof_begin(P, 3);
     {
         const int xc = P->xchunk;
@@ -531,11 +531,7 @@ int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const
 
 int el_step_adjoint_u(prop_s *P, float *const *S)
 {
-    if (tma_usable(P)) return el_launch_tma(P, S, -1.f);
-    P->g.dt = -P->g.dt;                    // kernels take the grid by value at launch
-    const int rc = el_launch_fast(P, S, false);
-    P->g.dt = -P->g.dt;
-    return rc;
+    return tma_usable(P) ? el_launch_tma(P, S, -1.f) : el_launch_fast(P, S, -1.f);
 }
 
 int el_launch_step(prop_s *P, float *const *S, bool adjoint)

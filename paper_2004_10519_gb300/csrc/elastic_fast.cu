@@ -3,12 +3,10 @@
 // Two passes per step, each streaming along x over a 32(z) x 16(y) tile:
 //   velocity pass  v <- g (v + dt b_avg Dtau(tau))
 //   stress pass    tau <- g (tau + dt C S(v))
-// and, for adjoint modelling, the same passes in the variable s = C tbar
-// (exact transpose of the step; C and the taper g commute):
-//   velocity pass  vbar <- g (vbar - dt Dtau(g s))
-//   stress pass    s <- g s - dt C S(b_avg vbar)
-// Residuals enter s as C R^T r = (3 lambda + 2 mu) w r on the diagonal and the
-// source-side output reads tr(tbar) = tr(s) / (3 lambda + 2 mu).
+// The transposed step (adjoint modelling) is the same two passes with
+// dt -> -dt in the variables (b_avg vbar, g C tbar).  These kernels serve
+// grids whose computational NZ is not a multiple of 4 (the TMA-fed passes
+// need 16-byte rows).
 //
 // Pipelining: while plane x is computed from shared memory, the loads of
 // plane x+1 (x-queue heads, own interior values, an even share of the halo
@@ -136,21 +134,21 @@ struct HaloShare {
 // ---------------------------------------------------------------------------
 // velocity pass
 // fields: 0 f_xy (y halo), 1 f_yy (y), 2 f_yz (cross), 3 f_xz (z), 4 f_zz (z),
-//         5 buoyancy (+1 plane, forward only)
+//         5 buoyancy (+1 plane)
 // ---------------------------------------------------------------------------
-template <int M, int ADJ>
+template <int M>
 struct VP {
-    static constexpr int NF = ADJ ? 5 : 6;
+    static constexpr int NF = 6;
     static constexpr int B0 = 0, B1 = PG<M>::size(0), B2 = 2 * PG<M>::size(0),
                          B3 = B2 + PG<M>::size(2), B4 = B3 + PG<M>::size(1),
-                         B5 = B4 + PG<M>::size(1), BUF = B5 + (ADJ ? 0 : PG<M>::size(3));
+                         B5 = B4 + PG<M>::size(1), BUF = B5 + PG<M>::size(3);
     static constexpr int HTOT = 2 * PG<M>::nhalo(0) + PG<M>::nhalo(2) + 2 * PG<M>::nhalo(1) +
-                                (ADJ ? 0 : PG<M>::nhalo(3));
+                                PG<M>::nhalo(3);
     static constexpr int S = (HTOT + NT - 1) / NT;
 };
 
-// value of component c of the differentiated stress at (x, y, z):
-// forward tau_c; adjoint g_c s_c.  Components: 0 xx 1 yy 2 zz 3 xy 4 xz 5 yz
+// stress component c at (x, y, z), 0 outside the grid.
+// Components: 0 xx 1 yy 2 zz 3 xy 4 xz 5 yz
 WP_DEV const float *pick(const F9 &s, int i)
 {
     switch (i) {
@@ -161,21 +159,16 @@ WP_DEV const float *pick(const F9 &s, int i)
     return s.f[8];
 }
 
-template <int ADJ>
 WP_DEV float vp_val(const GridDev &g, const F9 &s, int c, int x, int y, int z)
 {
-    if (!inside(g, x, y, z)) return 0.f;
-    const float v = __ldg(pick(s, 3 + c) + gidx(g, x, y, z));
-    if (!ADJ) return v;
-    const int hx = c == 3 || c == 4, hy = c == 3 || c == 5, hz = c == 4 || c == 5;
-    return tp(g, x, hx, y, hy, z, hz) * v;
+    return inside(g, x, y, z) ? __ldg(pick(s, 3 + c) + gidx(g, x, y, z)) : 0.f;
 }
 
-template <int M, int ADJ>
+template <int M>
 __global__ void __launch_bounds__(NT, 2)
 el_vpass(GridDev g, FDW w, F9 s, const float *__restrict__ bu, int xc)
 {
-    using L = VP<M, ADJ>;
+    using L = VP<M>;
     constexpr int Q = 2 * M, NF = L::NF, S = L::S;
     extern __shared__ float sm[];
     const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * FZ + tz;
@@ -195,30 +188,28 @@ el_vpass(GridDev g, FDW w, F9 s, const float *__restrict__ bu, int xc)
     float qxx[Q], qxy[Q], qxz[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
-        qxx[j] = vp_val<ADJ>(g, s, 0, xa - M + 1 + j, y, z);
-        qxy[j] = vp_val<ADJ>(g, s, 3, xa - M + j, y, z);
-        qxz[j] = vp_val<ADJ>(g, s, 4, xa - M + j, y, z);
+        qxx[j] = vp_val(g, s, 0, xa - M + 1 + j, y, z);
+        qxy[j] = vp_val(g, s, 3, xa - M + j, y, z);
+        qxz[j] = vp_val(g, s, 4, xa - M + j, y, z);
     }
     // prefetched values of the next plane
     float nxx, nxy, nxz, nyy, nzz, nyz, nb = 0.f, nbx = 0.f, hv[S];
     auto fetch = [&](int x) {
-        nxx = vp_val<ADJ>(g, s, 0, x + M, y, z);
-        nxy = vp_val<ADJ>(g, s, 3, x + M - 1, y, z);
-        nxz = vp_val<ADJ>(g, s, 4, x + M - 1, y, z);
-        nyy = vp_val<ADJ>(g, s, 1, x, y, z);
-        nzz = vp_val<ADJ>(g, s, 2, x, y, z);
-        nyz = vp_val<ADJ>(g, s, 5, x, y, z);
-        if (!ADJ) {
-            nb = lc(bu, g, x, y, z);
-            nbx = lc(bu, g, x + 1, y, z);
-        }
+        nxx = vp_val(g, s, 0, x + M, y, z);
+        nxy = vp_val(g, s, 3, x + M - 1, y, z);
+        nxz = vp_val(g, s, 4, x + M - 1, y, z);
+        nyy = vp_val(g, s, 1, x, y, z);
+        nzz = vp_val(g, s, 2, x, y, z);
+        nyz = vp_val(g, s, 5, x, y, z);
+        nb = lc(bu, g, x, y, z);
+        nbx = lc(bu, g, x + 1, y, z);
 #pragma unroll
         for (int k = 0; k < S; k++) {
             const int f = hs.fld(k);
             float v = 0.f;
             if (f >= 0) {
                 const int yy = y0 + hs.dy(k), zz = z0 + hs.dz(k);
-                v = f == 5 ? lc(bu, g, x, yy, zz) : vp_val<ADJ>(g, s, comp(f), x, yy, zz);
+                v = f == 5 ? lc(bu, g, x, yy, zz) : vp_val(g, s, comp(f), x, yy, zz);
             }
             hv[k] = v;
         }
@@ -236,7 +227,7 @@ el_vpass(GridDev g, FDW w, F9 s, const float *__restrict__ bu, int xc)
         B[L::B2 + PG<M>::inner(2, ty, tz)] = nyz;
         B[L::B3 + PG<M>::inner(1, ty, tz)] = qxz[M];
         B[L::B4 + PG<M>::inner(1, ty, tz)] = nzz;
-        if (!ADJ) B[L::B5 + PG<M>::inner(3, ty, tz)] = nb;
+        B[L::B5 + PG<M>::inner(3, ty, tz)] = nb;
 #pragma unroll
         for (int k = 0; k < S; k++)
             if (hs.fld(k) >= 0) B[hs.off[k]] = hv[k];
@@ -270,21 +261,15 @@ el_vpass(GridDev g, FDW w, F9 s, const float *__restrict__ bu, int xc)
                            (szz[ty * C1 + cz + k] - szz[ty * C1 + cz - k + 1]));
             }
             const long long q = gidx(g, x, y, z);
-            if (!ADJ) {
-                constexpr int C3 = PG<M>::cols(3);
-                const float *sb = B + L::B5;
-                const float b0 = sb[ty * C3 + tz];
-                const float bx = 0.5f * (b0 + bxn);
-                const float by = 0.5f * (b0 + sb[(y + 1 < g.NY ? ty + 1 : ty) * C3 + tz]);
-                const float bz = 0.5f * (b0 + sb[ty * C3 + (z + 1 < g.NZ ? tz + 1 : tz)]);
-                s.f[0][q] = tp(g, x, 1, y, 0, z, 0) * (v0 + c * bx * d0);
-                s.f[1][q] = tp(g, x, 0, y, 1, z, 0) * (v1 + c * by * d1);
-                s.f[2][q] = tp(g, x, 0, y, 0, z, 1) * (v2 + c * bz * d2);
-            } else {
-                s.f[0][q] = tp(g, x, 1, y, 0, z, 0) * (v0 - c * d0);
-                s.f[1][q] = tp(g, x, 0, y, 1, z, 0) * (v1 - c * d1);
-                s.f[2][q] = tp(g, x, 0, y, 0, z, 1) * (v2 - c * d2);
-            }
+            constexpr int C3 = PG<M>::cols(3);
+            const float *sb = B + L::B5;
+            const float b0 = sb[ty * C3 + tz];
+            const float bx = 0.5f * (b0 + bxn);
+            const float by = 0.5f * (b0 + sb[(y + 1 < g.NY ? ty + 1 : ty) * C3 + tz]);
+            const float bz = 0.5f * (b0 + sb[ty * C3 + (z + 1 < g.NZ ? tz + 1 : tz)]);
+            s.f[0][q] = tp(g, x, 1, y, 0, z, 0) * (v0 + c * bx * d0);
+            s.f[1][q] = tp(g, x, 0, y, 1, z, 0) * (v1 + c * by * d1);
+            s.f[2][q] = tp(g, x, 0, y, 0, z, 1) * (v2 + c * bz * d2);
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -309,26 +294,15 @@ struct TP_ {
     static constexpr int SMU = (PG<M>::nhalo(3) + NT - 1) / NT;
 };
 
-// value of velocity component c at (x,y,z): forward v_c; adjoint b_avg v_c
-template <int ADJ>
-WP_DEV float tp_val(const GridDev &g, const F9 &s, const float *__restrict__ bu, int c, int x, int y,
-                    int z)
+// velocity component c at (x, y, z), 0 outside the grid
+WP_DEV float tp_val(const GridDev &g, const F9 &s, int c, int x, int y, int z)
 {
-    if (!inside(g, x, y, z)) return 0.f;
-    const long long q = gidx(g, x, y, z);
-    const float v = __ldg(pick(s, c) + q);
-    if (!ADJ) return v;
-    long long d = 0;
-    if (c == 0) d = x + 1 < g.NX ? (long long)g.NY * g.NZ : 0;
-    else if (c == 1) d = y + 1 < g.NY ? (long long)g.NZ : 0;
-    else d = z + 1 < g.NZ ? 1 : 0;
-    return 0.5f * (__ldg(bu + q) + __ldg(bu + q + d)) * v;
+    return inside(g, x, y, z) ? __ldg(pick(s, c) + gidx(g, x, y, z)) : 0.f;
 }
 
-template <int M, int ADJ>
+template <int M>
 __global__ void __launch_bounds__(NT, 2)
-el_tpass(GridDev g, FDW w, F9 s, const float *__restrict__ lam, const float *__restrict__ mu,
-         const float *__restrict__ bu, int xc)
+el_tpass(GridDev g, FDW w, F9 s, const float *__restrict__ lam, const float *__restrict__ mu, int xc)
 {
     using L = TP_<M>;
     constexpr int Q = 2 * M, S = L::S;
@@ -348,19 +322,19 @@ el_tpass(GridDev g, FDW w, F9 s, const float *__restrict__ lam, const float *__r
     float qvx[Q], qvy[Q], qvz[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
-        qvx[j] = tp_val<ADJ>(g, s, bu, 0, xa - M + j, y, z);
-        qvy[j] = tp_val<ADJ>(g, s, bu, 1, xa - M + 1 + j, y, z);
-        qvz[j] = tp_val<ADJ>(g, s, bu, 2, xa - M + 1 + j, y, z);
+        qvx[j] = tp_val(g, s, 0, xa - M + j, y, z);
+        qvy[j] = tp_val(g, s, 1, xa - M + 1 + j, y, z);
+        qvz[j] = tp_val(g, s, 2, xa - M + 1 + j, y, z);
     }
     float nvx, nvy, nvz, hv[S], nmu, nmuh;
     auto fetch = [&](int x) {
-        nvx = tp_val<ADJ>(g, s, bu, 0, x + M - 1, y, z);
-        nvy = tp_val<ADJ>(g, s, bu, 1, x + M, y, z);
-        nvz = tp_val<ADJ>(g, s, bu, 2, x + M, y, z);
+        nvx = tp_val(g, s, 0, x + M - 1, y, z);
+        nvy = tp_val(g, s, 1, x + M, y, z);
+        nvz = tp_val(g, s, 2, x + M, y, z);
 #pragma unroll
         for (int k = 0; k < S; k++) {
             const int f = hs.fld(k);
-            hv[k] = f >= 0 ? tp_val<ADJ>(g, s, bu, f, x, y0 + hs.dy(k), z0 + hs.dz(k)) : 0.f;
+            hv[k] = f >= 0 ? tp_val(g, s, f, x, y0 + hs.dy(k), z0 + hs.dz(k)) : 0.f;
         }
         // mu plane x+1 (clamped) for the edge averages
         nmu = lc(mu, g, x + 1, y, z);
@@ -431,21 +405,12 @@ el_tpass(GridDev g, FDW w, F9 s, const float *__restrict__ lam, const float *__r
             const float gn = tp(g, x, 0, y, 0, z, 0);
             const float gxy_ = tp(g, x, 1, y, 1, z, 0), gxz_ = tp(g, x, 1, y, 0, z, 1),
                         gyz_ = tp(g, x, 0, y, 1, z, 1);
-            if (!ADJ) {
-                s.f[3][q] = gn * (t0 + c * (l * tr + m2 * exx));
-                s.f[4][q] = gn * (t1 + c * (l * tr + m2 * eyy));
-                s.f[5][q] = gn * (t2 + c * (l * tr + m2 * ezz));
-                s.f[6][q] = gxy_ * (t3 + c * mxy * gxy);
-                s.f[7][q] = gxz_ * (t4 + c * mxz * gxz);
-                s.f[8][q] = gyz_ * (t5 + c * myz * gyz);
-            } else {
-                s.f[3][q] = gn * t0 - c * (l * tr + m2 * exx);
-                s.f[4][q] = gn * t1 - c * (l * tr + m2 * eyy);
-                s.f[5][q] = gn * t2 - c * (l * tr + m2 * ezz);
-                s.f[6][q] = gxy_ * t3 - c * mxy * gxy;
-                s.f[7][q] = gxz_ * t4 - c * mxz * gxz;
-                s.f[8][q] = gyz_ * t5 - c * myz * gyz;
-            }
+            s.f[3][q] = gn * (t0 + c * (l * tr + m2 * exx));
+            s.f[4][q] = gn * (t1 + c * (l * tr + m2 * eyy));
+            s.f[5][q] = gn * (t2 + c * (l * tr + m2 * ezz));
+            s.f[6][q] = gxy_ * (t3 + c * mxy * gxy);
+            s.f[7][q] = gxz_ * (t4 + c * mxz * gxz);
+            s.f[8][q] = gyz_ * (t5 + c * myz * gyz);
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -456,23 +421,24 @@ el_tpass(GridDev g, FDW w, F9 s, const float *__restrict__ lam, const float *__r
     }
 }
 
-template <int M, int ADJ>
-int launch(prop_s *P, float *const *S)
+template <int M>
+int launch(prop_s *P, float *const *S, float dt_sign)
 {
-    const GridDev &g = P->g;
+    GridDev g = P->g;
+    g.dt = dt_sign * g.dt;
     const int xc = P->xchunk;
     dim3 blk(FZ, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     F9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
-    const size_t smv = 2 * VP<M, ADJ>::BUF * sizeof(float);
+    const size_t smv = 2 * VP<M>::BUF * sizeof(float);
     const size_t smt = (2 * TP_<M>::BUF + 3 * TP_<M>::MU) * sizeof(float);
-    static const bool attr = (cudaFuncSetAttribute(el_vpass<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv),
-                              cudaFuncSetAttribute(el_tpass<M, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt), true);
+    static const bool attr = (cudaFuncSetAttribute(el_vpass<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smv),
+                              cudaFuncSetAttribute(el_tpass<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smt), true);
     (void)attr;
-    prof_begin(P, ADJ ? 5 : 2);
-    el_vpass<M, ADJ><<<grd, blk, smv, P->stream>>>(g, P->w, s, P->bu, xc);
-    el_tpass<M, ADJ><<<grd, blk, smt, P->stream>>>(g, P->w, s, P->lam, P->mu, P->bu, xc);
-    prof_end(P, ADJ ? 5 : 2);
+    prof_begin(P, dt_sign > 0 ? 2 : 5);
+    el_vpass<M><<<grd, blk, smv, P->stream>>>(g, P->w, s, P->bu, xc);
+    el_tpass<M><<<grd, blk, smt, P->stream>>>(g, P->w, s, P->lam, P->mu, xc);
+    prof_end(P, dt_sign > 0 ? 2 : 5);
     P->kern_launches += 2;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
@@ -480,15 +446,15 @@ int launch(prop_s *P, float *const *S)
 
 }  // namespace
 
-// forward step (adjoint_s = false) or transposed step in the s = C tbar
-// variables (adjoint_s = true), in place on S (9 fields)
-int el_launch_fast(prop_s *P, float *const *S, bool adjoint_s)
+// elastic step with time step dt_sign * dt, in place on S (9 fields):
+// forward (+1), or the transposed step in (b_avg vbar, g C tbar) (-1)
+int el_launch_fast(prop_s *P, float *const *S, float dt_sign)
 {
     switch (P->M) {
-    case 2: return adjoint_s ? launch<2, 1>(P, S) : launch<2, 0>(P, S);
-    case 4: return adjoint_s ? launch<4, 1>(P, S) : launch<4, 0>(P, S);
-    case 6: return adjoint_s ? launch<6, 1>(P, S) : launch<6, 0>(P, S);
-    case 8: return adjoint_s ? launch<8, 1>(P, S) : launch<8, 0>(P, S);
+    case 2: return launch<2>(P, S, dt_sign);
+    case 4: return launch<4>(P, S, dt_sign);
+    case 6: return launch<6>(P, S, dt_sign);
+    case 8: return launch<8>(P, S, dt_sign);
     }
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }

@@ -1,9 +1,12 @@
 // Internal declarations of the waveprop CUDA library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstdint>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/waveprop.h"
@@ -86,6 +89,9 @@ struct prop_s {
     long long prof_n[8] = {};
     // adjoint state (separate from the forward state during gradients)
     float *ast[9] = {};
+    // TMA descriptors of the stencil passes, keyed by (array, box width, box
+    // height) (stencil_tma.cu)
+    std::map<std::tuple<const void *, int, int>, CUtensorMap> tmaps;
 };
 
 // ---------------------------------------------------------------------------
@@ -101,8 +107,9 @@ int tti_launch_fast(prop_s *P, float *const *S, bool adjoint, const float *img_p
                     const float *img_r, float *grad);
 // elastic step in place on S (9 fields); adjoint: transposed step (tbar form)
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
-// pipelined elastic step: forward, or transposed step in s = C tbar variables
-int el_launch_fast(prop_s *P, float *const *S, bool adjoint_s);
+// pipelined elastic step with time step dt_sign * dt (any NZ): forward (+1)
+// or the transposed step in (b_avg vbar, g C tbar) variables (-1)
+int el_launch_fast(prop_s *P, float *const *S, float dt_sign);
 // TMA-fed passes (stencil_tma.cu): usable when NZ % 4 == 0
 bool tma_usable(const prop_s *P);
 int el_launch_tma(prop_s *P, float *const *S, float dt_sign);

@@ -257,6 +257,7 @@ static void free_snaps(prop_s *P)
     cudaFree(P->snap_scale); P->snap_scale = nullptr;
     cudaFree(P->seg); P->seg = nullptr; P->seg_bytes = 0;
     P->saved = false;
+    P->tmaps.clear();        // descriptors may name the freed buffers
 }
 
 static void free_all(prop_s *P)

@@ -7,8 +7,11 @@
 // are fetched by one thread with cp.async.bulk.tensor into a 3-stage
 // shared-memory ring (mbarrier completion); out-of-grid elements arrive as
 // zeros, which is the zero extension of the finite-difference operators.
+// Every other per-plane input (the thread's own values, parameters, the new
+// head of each x-derivative queue M planes ahead) comes through the same
+// ring as an interior box, so all loads are issued two planes ahead.
 // z-derivatives read a window of M+1 float2 per field; x-derivatives use
-// per-thread float2 register queues fed by coalesced loads one plane ahead.
+// per-thread float2 register queues.
 // Offsets are 32-bit (the runtime keeps N below 2^32).  Every mbarrier wait
 // is bounded in time: on expiry the thread sets bit 2 of the error word and
 // a shared abort flag; at the next plane barrier the whole CTA leaves, after
@@ -109,6 +112,7 @@ WP_DEV void st2(float *p, unsigned o, float a, float b) { *reinterpret_cast<floa
 WP_DEV float2 dif2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
 constexpr int al32(int n) { return (n + 31) & ~31; }   // 128-byte aligned float offsets
+constexpr int IS = FZ * FY;                             // interior box (tile of one plane)
 
 // box geometries (floats): rows x cols
 template <int M>
@@ -150,24 +154,27 @@ struct Ring {
 
 // ---------------------------------------------------------------------------
 // elastic velocity pass
-// stage: [xy (y box)] [yy (y box)] [xz (z box)] [zz (z box)] [yz (rect)] [b (+1 box)]
+// stage: [xy (y box)] [yy (y box)] [xz (z box)] [zz (z box)] [yz (rect)]
+//        [b (+1 box)] [v_x v_y v_z (plane x)] [queue heads: xx (x+M),
+//        xy (x+M-1), xz (x+M-1)] [b (plane x+1, clamped)]
 // ---------------------------------------------------------------------------
 template <int M>
 struct VL {
     using B = BX<M>;
     static constexpr int OXY = 0, OYY = B::YS, OXZ = 2 * B::YS, OZZ = OXZ + B::ZS, OYZ = OZZ + B::ZS,
-                         OB = OYZ + B::RS, SZ = OB + B::PS;
+                         OB = OYZ + B::RS, OV = OB + B::PS, OQ = OV + 3 * IS, OBX = OQ + 3 * IS,
+                         SZ = OBX + IS;
     static constexpr uint32_t BYTES = 4u * (2 * B::YR * B::YC + 2 * B::ZR * B::ZC + B::RR * B::RC +
-                                            B::PR * B::PC);
+                                            B::PR * B::PC + 7 * IS);
+};
+
+struct VMaps {
+    CUtensorMap xy, yy, xz, zz, yz, b, v[3], qxx, qxy, qxz, bi;
 };
 
 template <int M>
 __global__ void __launch_bounds__(NT2, 2)
-el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
-             const __grid_constant__ CUtensorMap mxy, const __grid_constant__ CUtensorMap myy,
-             const __grid_constant__ CUtensorMap mxz, const __grid_constant__ CUtensorMap mzz,
-             const __grid_constant__ CUtensorMap myz, const __grid_constant__ CUtensorMap mb, int xc,
-             int *err)
+el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, int *err)
 {
     using L = VL<M>;
     using B = BX<M>;
@@ -180,16 +187,21 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
-    const float *txx = s.f[3], *txy = s.f[6], *txz = s.f[7];
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
-        mbar_expect(&bars[st], L::BYTES);
-        tma3(S + L::OXY, &mxy, z0, y0 - M, x, &bars[st]);
-        tma3(S + L::OYY, &myy, z0, y0 - M, x, &bars[st]);
-        tma3(S + L::OXZ, &mxz, z0 - B::MZ, y0, x, &bars[st]);
-        tma3(S + L::OZZ, &mzz, z0 - B::MZ, y0, x, &bars[st]);
-        tma3(S + L::OYZ, &myz, z0 - B::MZ, y0 - M, x, &bars[st]);
-        tma3(S + L::OB, &mb, z0, y0, x, &bars[st]);
+        uint64_t *bar = &bars[st];
+        mbar_expect(bar, L::BYTES);
+        tma3(S + L::OXY, &mp.xy, z0, y0 - M, x, bar);
+        tma3(S + L::OYY, &mp.yy, z0, y0 - M, x, bar);
+        tma3(S + L::OXZ, &mp.xz, z0 - B::MZ, y0, x, bar);
+        tma3(S + L::OZZ, &mp.zz, z0 - B::MZ, y0, x, bar);
+        tma3(S + L::OYZ, &mp.yz, z0 - B::MZ, y0 - M, x, bar);
+        tma3(S + L::OB, &mp.b, z0, y0, x, bar);
+        for (int i = 0; i < 3; i++) tma3(S + L::OV + i * IS, &mp.v[i], z0, y0, x, bar);
+        tma3(S + L::OQ, &mp.qxx, z0, y0, x + M, bar);                  // beyond NX: zeros
+        tma3(S + L::OQ + IS, &mp.qxy, z0, y0, x + M - 1, bar);
+        tma3(S + L::OQ + 2 * IS, &mp.qxz, z0, y0, x + M - 1, bar);
+        tma3(S + L::OBX, &mp.bi, z0, y0, min(x + 1, g.NX - 1), bar);
     };
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
@@ -203,6 +215,7 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
     const float2 Z2 = make_float2(0.f, 0.f);
+    const float *txx = s.f[3], *txy = s.f[6], *txz = s.f[7];
     float2 qxx[Q], qxy[Q], qxz[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
@@ -211,35 +224,18 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
         qxy[j] = act && xr >= 0 && xr < g.NX ? ldg2(txy, xr * pl + q0) : Z2;
         qxz[j] = act && xr >= 0 && xr < g.NX ? ldg2(txz, xr * pl + q0) : Z2;
     }
-    float2 nxx = Z2, nxy = Z2, nxz = Z2, nbx = Z2, nv0 = Z2, nv1 = Z2, nv2 = Z2;
-    auto fetch = [&](int x) {
-        if (!act) return;
-        const unsigned o = x * pl + q0;
-        nxx = x + M < g.NX ? ldg2(txx, o + M * pl) : Z2;
-        nxy = x + M - 1 < g.NX ? ldg2(txy, o + (M - 1) * pl) : Z2;
-        nxz = x + M - 1 < g.NX ? ldg2(txz, o + (M - 1) * pl) : Z2;
-        nbx = ldg2(bu, x + 1 < g.NX ? o + pl : o);
-        nv0 = ld2(s.f[0], o);
-        nv1 = ld2(s.f[1], o);
-        nv2 = ld2(s.f[2], o);
-    };
-    fetch(xa);
     const float c = g.dt * g.ih;
     const float *tabz = g.tab + 2 * (g.NX + g.NY);
     const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
     const float gzn0 = __ldg(tabz + 2 * zc0), gzh0 = __ldg(tabz + 2 * zc0 + 1);
     const float gzn1 = __ldg(tabz + 2 * zc1), gzh1 = __ldg(tabz + 2 * zc1 + 1);
     const float gyn = __ldg(g.tab + 2 * g.NX + 2 * yc), gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
-    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz;
+    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz, ii = ty * FZ + c2;
     const int yb1 = y + 1 < g.NY ? ty + 1 : ty;           // +1 box row of b(y+1), clamped
     const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;       // +1 box column of b(z+2), clamped
     Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
-        qxx[Q - 1] = nxx;
-        qxy[Q - 1] = nxy;
-        qxz[Q - 1] = nxz;
-        const float2 v0 = nv0, v1 = nv1, v2 = nv2, bxn = nbx;
         // all threads are past iteration it-1: its stage may be refilled
         __syncthreads();
         if (s_abort) {
@@ -247,14 +243,18 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
             return;
         }
         if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        if (x + 1 < xb) fetch(x + 1);
         const bool ok = mbar_wait(&bars[R.st], R.ph);
         if (!ok) {
             s_abort = 1;
             atomicOr(err, 2);
         }
+        const float *S = sm + R.st * L::SZ;
+        if (ok) {
+            qxx[Q - 1] = lds2(S + L::OQ + ii);
+            qxy[Q - 1] = lds2(S + L::OQ + IS + ii);
+            qxz[Q - 1] = lds2(S + L::OQ + 2 * IS + ii);
+        }
         if (ok && act) {
-            const float *S = sm + R.st * L::SZ;
             const float *sxy = S + L::OXY, *syy = S + L::OYY, *syz = S + L::OYZ, *sb = S + L::OB;
             float wxz[2 * M + 2], wyz[2 * M + 2], wzz[2 * M + 2];
             zwin<M>(S + L::OXZ + ty * B::ZC, cz, wxz);
@@ -277,6 +277,8 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
                 d2a += b * (cx_.x + cy_.x + (wzz[M + k] - wzz[M - k + 1]));
                 d2b += b * (cx_.y + cy_.y + (wzz[M + k + 1] - wzz[M - k + 2]));
             }
+            const float2 v0 = lds2(S + L::OV + ii), v1 = lds2(S + L::OV + IS + ii), v2 = lds2(S + L::OV + 2 * IS + ii);
+            const float2 bxn = lds2(S + L::OBX + ii);
             const float2 b0 = lds2(sb + ty * B::PC + c2);
             const float2 bY = lds2(sb + yb1 * B::PC + c2);
             const float bz2 = sb[ty * B::PC + zb2];
@@ -303,22 +305,25 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ bu,
 
 // ---------------------------------------------------------------------------
 // elastic stress pass
-// stage: [vx rect] [vy rect] [vz rect] [mu +1 box, plane x] [mu +1 box, plane x+1]
+// stage: [vx rect] [vy rect] [vz rect] [mu +1 box, plane x] [mu +1 box,
+//        plane x+1] [t_xx .. t_yz, lambda (plane x)] [queue heads: vx
+//        (x+M-1), vy (x+M), vz (x+M)]
 // ---------------------------------------------------------------------------
 template <int M>
 struct TL {
     using B = BX<M>;
     static constexpr int OVX = 0, OVY = B::RS, OVZ = 2 * B::RS, OM0 = 3 * B::RS, OM1 = OM0 + B::PS,
-                         SZ = OM1 + B::PS;
-    static constexpr uint32_t BYTES = 4u * (3 * B::RR * B::RC + 2 * B::PR * B::PC);
+                         OT = OM1 + B::PS, OL = OT + 6 * IS, OQ = OL + IS, SZ = OQ + 3 * IS;
+    static constexpr uint32_t BYTES = 4u * (3 * B::RR * B::RC + 2 * B::PR * B::PC + 10 * IS);
+};
+
+struct TMaps {
+    CUtensorMap vx, vy, vz, mu, t[6], lam, qvx, qvy, qvz;
 };
 
 template <int M>
 __global__ void __launch_bounds__(NT2, 2)
-el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
-             const __grid_constant__ CUtensorMap mvx, const __grid_constant__ CUtensorMap mvy,
-             const __grid_constant__ CUtensorMap mvz, const __grid_constant__ CUtensorMap mmu, int xc,
-             int *err)
+el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, int *err)
 {
     using L = TL<M>;
     using B = BX<M>;
@@ -331,15 +336,20 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
-    const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
-        mbar_expect(&bars[st], L::BYTES);
-        tma3(S + L::OVX, &mvx, z0 - B::MZ, y0 - M, x, &bars[st]);
-        tma3(S + L::OVY, &mvy, z0 - B::MZ, y0 - M, x, &bars[st]);
-        tma3(S + L::OVZ, &mvz, z0 - B::MZ, y0 - M, x, &bars[st]);
-        tma3(S + L::OM0, &mmu, z0, y0, x, &bars[st]);
-        tma3(S + L::OM1, &mmu, z0, y0, min(x + 1, g.NX - 1), &bars[st]);
+        uint64_t *bar = &bars[st];
+        mbar_expect(bar, L::BYTES);
+        tma3(S + L::OVX, &mp.vx, z0 - B::MZ, y0 - M, x, bar);
+        tma3(S + L::OVY, &mp.vy, z0 - B::MZ, y0 - M, x, bar);
+        tma3(S + L::OVZ, &mp.vz, z0 - B::MZ, y0 - M, x, bar);
+        tma3(S + L::OM0, &mp.mu, z0, y0, x, bar);
+        tma3(S + L::OM1, &mp.mu, z0, y0, min(x + 1, g.NX - 1), bar);
+        for (int i = 0; i < 6; i++) tma3(S + L::OT + i * IS, &mp.t[i], z0, y0, x, bar);
+        tma3(S + L::OL, &mp.lam, z0, y0, x, bar);
+        tma3(S + L::OQ, &mp.qvx, z0, y0, x + M - 1, bar);              // beyond NX: zeros
+        tma3(S + L::OQ + IS, &mp.qvy, z0, y0, x + M, bar);
+        tma3(S + L::OQ + 2 * IS, &mp.qvz, z0, y0, x + M, bar);
     };
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
@@ -353,6 +363,7 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
     const float2 Z2 = make_float2(0.f, 0.f);
+    const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
     float2 qvx[Q], qvy[Q], qvz[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
@@ -361,51 +372,36 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
         qvy[j] = act && xq >= 0 && xq < g.NX ? ldg2(vyp, xq * pl + q0) : Z2;
         qvz[j] = act && xq >= 0 && xq < g.NX ? ldg2(vzp, xq * pl + q0) : Z2;
     }
-    float2 nvx = Z2, nvy = Z2, nvz = Z2;
-    auto fetch = [&](int x) {
-        if (!act) return;
-        const unsigned o = x * pl + q0;
-        nvx = x + M - 1 < g.NX ? ldg2(vxp, o + (M - 1) * pl) : Z2;
-        nvy = x + M < g.NX ? ldg2(vyp, o + M * pl) : Z2;
-        nvz = x + M < g.NX ? ldg2(vzp, o + M * pl) : Z2;
-    };
-    fetch(xa);
     const float c = g.dt * g.ih;
     const float *tabz = g.tab + 2 * (g.NX + g.NY);
     const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
     const float gzn0 = __ldg(tabz + 2 * zc0), gzh0 = __ldg(tabz + 2 * zc0 + 1);
     const float gzn1 = __ldg(tabz + 2 * zc1), gzh1 = __ldg(tabz + 2 * zc1 + 1);
     const float gyn = __ldg(g.tab + 2 * g.NX + 2 * yc), gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
-    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz;
+    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz, ii = ty * FZ + c2;
     const int yb1 = y + 1 < g.NY ? ty + 1 : ty;
     const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;
     Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
-        qvx[Q - 1] = nvx;
-        qvy[Q - 1] = nvy;
-        qvz[Q - 1] = nvz;
         __syncthreads();
         if (s_abort) {
             if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
             return;
         }
         if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        const unsigned q = x * pl + q0;
-        float2 t0 = Z2, t1 = Z2, t2 = Z2, t3 = Z2, t4 = Z2, t5 = Z2, l = Z2;
-        if (act) {
-            t0 = ld2(s.f[3], q); t1 = ld2(s.f[4], q); t2 = ld2(s.f[5], q);
-            t3 = ld2(s.f[6], q); t4 = ld2(s.f[7], q); t5 = ld2(s.f[8], q);
-            l = ldg2(lam, q);
-        }
-        if (x + 1 < xb) fetch(x + 1);
         const bool ok = mbar_wait(&bars[R.st], R.ph);
         if (!ok) {
             s_abort = 1;
             atomicOr(err, 2);
         }
+        const float *S = sm + R.st * L::SZ;
+        if (ok) {
+            qvx[Q - 1] = lds2(S + L::OQ + ii);
+            qvy[Q - 1] = lds2(S + L::OQ + IS + ii);
+            qvz[Q - 1] = lds2(S + L::OQ + 2 * IS + ii);
+        }
         if (ok && act) {
-            const float *S = sm + R.st * L::SZ;
             const float *svx = S + L::OVX, *svy = S + L::OVY, *svz = S + L::OVZ;
             float wvx[2 * M + 2], wvy[2 * M + 2], wvz[2 * M + 2];
             zwin<M>(svx + cy * B::RC, cz, wvx);
@@ -435,12 +431,16 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
                 gyza += b * ((wvy[M + k] - wvy[M - k + 1]) + zy.x);
                 gyzb += b * ((wvy[M + k + 1] - wvy[M - k + 2]) + zy.y);
             }
-            const float *R0 = S + L::OM0, *R1 = S + L::OM1;
+            const float *R0 = S + L::OM0, *R1 = S + L::OM1, *T = S + L::OT + ii;
             const float2 m0 = lds2(R0 + ty * B::PC + c2), my = lds2(R0 + yb1 * B::PC + c2);
             const float2 mx = lds2(R1 + ty * B::PC + c2), mxy_ = lds2(R1 + yb1 * B::PC + c2);
             const float m0z = R0[ty * B::PC + zb2], myz = R0[yb1 * B::PC + zb2], mxz = R1[ty * B::PC + zb2];
+            const float2 t0 = lds2(T), t1 = lds2(T + IS), t2 = lds2(T + 2 * IS);
+            const float2 t3 = lds2(T + 3 * IS), t4 = lds2(T + 4 * IS), t5 = lds2(T + 5 * IS);
+            const float2 l = lds2(S + L::OL + ii);
             const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
             const float gn0 = gxn * gyn * gzn0, gn1 = gxn * gyn * gzn1;
+            const unsigned q = x * pl + q0;
             // averages of mu over the 4 nodes around each edge (the pair's
             // second lane is the first point's z+1 neighbour)
             const float mxya = 0.25f * (m0.x + mx.x + my.x + mxy_.x);
@@ -471,23 +471,27 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const float *__restrict__ lam,
 }
 
 // ---------------------------------------------------------------------------
-// TTI rotation pass.  stage: [p rect] [r rect] (+ [eps rect] [del rect] ADJ)
+// TTI rotation pass.
+// stage: [p rect] [r rect] (+ [eps rect] [del rect] ADJ) [queue heads p, r
+//        (x+M)] (+ [eps, del (x+M)] ADJ) [n_x, n_y (plane x)]
 // ---------------------------------------------------------------------------
 template <int M, int ADJ>
 struct RL {
     using B = BX<M>;
-    static constexpr int OP = 0, OR = B::RS, OE = 2 * B::RS, OD = 3 * B::RS,
-                         SZ = (ADJ ? 4 : 2) * B::RS;
-    static constexpr uint32_t BYTES = 4u * (ADJ ? 4 : 2) * B::RR * B::RC;
+    static constexpr int NR = ADJ ? 4 : 2, NQ = ADJ ? 4 : 2;
+    static constexpr int OP = 0, OR = B::RS, OE = 2 * B::RS, OD = 3 * B::RS, OQ = NR * B::RS,
+                         ON = OQ + NQ * IS, SZ = ON + 2 * IS;
+    static constexpr uint32_t BYTES = 4u * (NR * B::RR * B::RC + (NQ + 2) * IS);
+};
+
+struct RMaps {
+    CUtensorMap p, r, e, d, qp, qr, qe, qd, nx, ny;
 };
 
 template <int M, int ADJ>
 __global__ void __launch_bounds__(NT2, 2)
 tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
-            const float *__restrict__ eps, const float *__restrict__ del,
-            const float *__restrict__ nxa, const float *__restrict__ nya,
-            const __grid_constant__ CUtensorMap mp, const __grid_constant__ CUtensorMap mr,
-            const __grid_constant__ CUtensorMap me, const __grid_constant__ CUtensorMap md,
+            const float *__restrict__ eps, const float *__restrict__ del, const __grid_constant__ RMaps mp,
             float *__restrict__ ex, float *__restrict__ ey, float *__restrict__ ez,
             float *__restrict__ fx, float *__restrict__ fy, float *__restrict__ fz, int xc, int *err)
 {
@@ -504,13 +508,22 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
-        mbar_expect(&bars[st], L::BYTES);
-        tma3(S + L::OP, &mp, z0 - B::MZ, y0 - M, x, &bars[st]);
-        tma3(S + L::OR, &mr, z0 - B::MZ, y0 - M, x, &bars[st]);
+        uint64_t *bar = &bars[st];
+        mbar_expect(bar, L::BYTES);
+        tma3(S + L::OP, &mp.p, z0 - B::MZ, y0 - M, x, bar);
+        tma3(S + L::OR, &mp.r, z0 - B::MZ, y0 - M, x, bar);
         if (ADJ) {
-            tma3(S + L::OE, &me, z0 - B::MZ, y0 - M, x, &bars[st]);
-            tma3(S + L::OD, &md, z0 - B::MZ, y0 - M, x, &bars[st]);
+            tma3(S + L::OE, &mp.e, z0 - B::MZ, y0 - M, x, bar);
+            tma3(S + L::OD, &mp.d, z0 - B::MZ, y0 - M, x, bar);
         }
+        tma3(S + L::OQ, &mp.qp, z0, y0, x + M, bar);                  // beyond NX: zeros
+        tma3(S + L::OQ + IS, &mp.qr, z0, y0, x + M, bar);
+        if (ADJ) {
+            tma3(S + L::OQ + 2 * IS, &mp.qe, z0, y0, x + M, bar);
+            tma3(S + L::OQ + 3 * IS, &mp.qd, z0, y0, x + M, bar);
+        }
+        tma3(S + L::ON, &mp.nx, z0, y0, x, bar);
+        tma3(S + L::ON + IS, &mp.ny, z0, y0, x, bar);
     };
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
@@ -524,18 +537,8 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
     const float2 Z2 = make_float2(0.f, 0.f);
-    // (p, r) or zeta = C (lam_p, lam_r) at the thread's pair, plane x
-    auto own = [&](int x, float2 &a, float2 &b) {
-        a = b = Z2;
-        if (!act || x < 0 || x >= g.NX) return;
-        const unsigned q = x * pl + q0;
-        const float2 u = ldg2(p, q), v = ldg2(r, q);
-        if (!ADJ) {
-            a = u;
-            b = v;
-            return;
-        }
-        const float2 e = ldg2(eps, q), d = ldg2(del, q);
+    // zeta = C (lam_p, lam_r) of a pair (ADJ)
+    auto cmul = [](float2 u, float2 v, float2 e, float2 d, float2 &a, float2 &b) {
         const float c1a = 1.f + 2.f * e.x, c2a = sqrtf(1.f + 2.f * d.x);
         const float c1b = 1.f + 2.f * e.y, c2b = sqrtf(1.f + 2.f * d.y);
         a = make_float2(c1a * u.x + c2a * v.x, c1b * u.y + c2b * v.y);
@@ -543,37 +546,38 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     };
     float2 qp[Q], qr[Q];
 #pragma unroll
-    for (int j = 0; j < Q - 1; j++) own(xa - M + j, qp[j], qr[j]);
-    float2 np_ = Z2, nr_ = Z2, nnx = Z2, nny = Z2;
-    auto fetch = [&](int x) {
-        own(x + M, np_, nr_);
-        if (act) {
-            nnx = ldg2(nxa, x * pl + q0);
-            nny = ldg2(nya, x * pl + q0);
+    for (int j = 0; j < Q - 1; j++) {
+        const int xq = xa - M + j;
+        qp[j] = qr[j] = Z2;
+        if (act && xq >= 0 && xq < g.NX) {
+            const unsigned q = xq * pl + q0;
+            const float2 u = ldg2(p, q), v = ldg2(r, q);
+            if (ADJ) cmul(u, v, ldg2(eps, q), ldg2(del, q), qp[j], qr[j]);
+            else { qp[j] = u; qr[j] = v; }
         }
-    };
-    fetch(xa);
-    const int cy = ty + M, cz = B::MZ + 2 * tz;
+    }
+    const int cy = ty + M, cz = B::MZ + 2 * tz, ii = ty * FZ + 2 * tz;
     const int ci = cy * B::RC + cz;
     Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
-        qp[Q - 1] = np_;
-        qr[Q - 1] = nr_;
-        const float2 n0 = nnx, n1 = nny;
         __syncthreads();
         if (s_abort) {
             if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
             return;
         }
         if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        if (x + 1 < xb) fetch(x + 1);
         const bool ok = mbar_wait(&bars[R.st], R.ph);
         if (!ok) {
             s_abort = 1;
             atomicOr(err, 2);
         }
         float *S = sm + R.st * L::SZ;
+        if (ok) {
+            const float2 u = lds2(S + L::OQ + ii), v = lds2(S + L::OQ + IS + ii);
+            if (ADJ) cmul(u, v, lds2(S + L::OQ + 2 * IS + ii), lds2(S + L::OQ + 3 * IS + ii), qp[Q - 1], qr[Q - 1]);
+            else { qp[Q - 1] = u; qr[Q - 1] = v; }
+        }
         if (ADJ) {
             // zeta = C lam over the whole rectangle, in place (each thread a share)
             if (ok) {
@@ -614,6 +618,7 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
                 gr2a += c * (wr[M + k] - wr[M - k]);
                 gr2b += c * (wr[M + k + 1] - wr[M - k + 1]);
             }
+            const float2 n0 = lds2(S + L::ON + ii), n1 = lds2(S + L::ON + IS + ii);
             const float ih = g.ih;
             const unsigned q = x * pl + q0;
             const float gp[2][3] = {{gp0a * ih, gp1a * ih, gp2a * ih}, {gp0b * ih, gp1b * ih, gp2b * ih}};
@@ -652,26 +657,34 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
 }
 
 // ---------------------------------------------------------------------------
-// TTI update pass.  stage: [e_y y box] [f_y y box] [e_z z box] [f_z z box]
+// TTI update pass.
+// stage: [e_y y box] [f_y y box] [e_z z box] [f_z z box] [queue heads e_x,
+//        f_x (x+M)] [m, p^n, r^n, p^{n-1}, r^{n-1} (plane x)] (+ [eps, del]
+//        forward) (+ [u_p, u_r, g] imaging)
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, int ADJ, int GRAD>
 struct UL {
     using B = BX<M>;
-    static constexpr int OEY = 0, OFY = B::YS, OEZ = 2 * B::YS, OFZ = OEZ + B::ZS, SZ = OFZ + B::ZS;
-    static constexpr uint32_t BYTES = 4u * (2 * B::YR * B::YC + 2 * B::ZR * B::ZC);
+    static constexpr int NI = 7 + (ADJ ? 0 : 2) + (GRAD ? 3 : 0);
+    static constexpr int OEY = 0, OFY = B::YS, OEZ = 2 * B::YS, OFZ = OEZ + B::ZS, OI = OFZ + B::ZS,
+                         SZ = OI + NI * IS;
+    // interior slots
+    static constexpr int QE = 0, QF = 1, MM = 2, PC = 3, RC = 4, PP = 5, RP = 6, EP = 7, DE = 8,
+                         UP = ADJ ? 7 : 9, UR = UP + 1, GG = UP + 2;
+    static constexpr uint32_t BYTES = 4u * (2 * B::YR * B::YC + 2 * B::ZR * B::ZC + NI * IS);
 };
 
-template <int M, int ADJ>
+struct UMaps {
+    CUtensorMap ey, fy, ez, fz, qe, qf, m, pc, rc, pp, rp, e, d, up, ur, g;
+};
+
+template <int M, int ADJ, int GRAD>
 __global__ void __launch_bounds__(NT2, 2)
 tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
-            const __grid_constant__ CUtensorMap mey, const __grid_constant__ CUtensorMap mfy,
-            const __grid_constant__ CUtensorMap mez, const __grid_constant__ CUtensorMap mfz,
-            const float *__restrict__ m, const float *__restrict__ eps, const float *__restrict__ del,
-            const float *__restrict__ pc, const float *__restrict__ rc, float *__restrict__ pp,
-            float *__restrict__ rp, const float *__restrict__ up, const float *__restrict__ ur,
+            const __grid_constant__ UMaps mp, float *__restrict__ pp, float *__restrict__ rp,
             float *__restrict__ grad, int *flag, int check, int xc, int *err)
 {
-    using L = UL<M>;
+    using L = UL<M, ADJ, GRAD>;
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
@@ -684,11 +697,29 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
-        mbar_expect(&bars[st], L::BYTES);
-        tma3(S + L::OEY, &mey, z0, y0 - M, x, &bars[st]);
-        tma3(S + L::OFY, &mfy, z0, y0 - M, x, &bars[st]);
-        tma3(S + L::OEZ, &mez, z0 - B::MZ, y0, x, &bars[st]);
-        tma3(S + L::OFZ, &mfz, z0 - B::MZ, y0, x, &bars[st]);
+        float *I = S + L::OI;
+        uint64_t *bar = &bars[st];
+        mbar_expect(bar, L::BYTES);
+        tma3(S + L::OEY, &mp.ey, z0, y0 - M, x, bar);
+        tma3(S + L::OFY, &mp.fy, z0, y0 - M, x, bar);
+        tma3(S + L::OEZ, &mp.ez, z0 - B::MZ, y0, x, bar);
+        tma3(S + L::OFZ, &mp.fz, z0 - B::MZ, y0, x, bar);
+        tma3(I + L::QE * IS, &mp.qe, z0, y0, x + M, bar);             // beyond NX: zeros
+        tma3(I + L::QF * IS, &mp.qf, z0, y0, x + M, bar);
+        tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
+        tma3(I + L::PC * IS, &mp.pc, z0, y0, x, bar);
+        tma3(I + L::RC * IS, &mp.rc, z0, y0, x, bar);
+        tma3(I + L::PP * IS, &mp.pp, z0, y0, x, bar);
+        tma3(I + L::RP * IS, &mp.rp, z0, y0, x, bar);
+        if (!ADJ) {
+            tma3(I + L::EP * IS, &mp.e, z0, y0, x, bar);
+            tma3(I + L::DE * IS, &mp.d, z0, y0, x, bar);
+        }
+        if (GRAD) {
+            tma3(I + L::UP * IS, &mp.up, z0, y0, x, bar);
+            tma3(I + L::UR * IS, &mp.ur, z0, y0, x, bar);
+            tma3(I + L::GG * IS, &mp.g, z0, y0, x, bar);
+        }
     };
     if (lead) {
         for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
@@ -710,51 +741,33 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
         qe[j] = in ? ldg2(ex, xq * pl + q0) : Z2;
         qf[j] = in ? ldg2(fx, xq * pl + q0) : Z2;
     }
-    float2 ne = Z2, nf = Z2;
-    auto fetch = [&](int x) {
-        const bool in = act && x + M < g.NX;
-        ne = in ? ldg2(ex, (x + M) * pl + q0) : Z2;
-        nf = in ? ldg2(fx, (x + M) * pl + q0) : Z2;
-    };
-    fetch(xa);
     const float *sx = g.tab, *sy = g.tab + g.NX, *sz = g.tab + g.NX + g.NY;
     const float dt2 = g.dt * g.dt, hdt = 0.5f * g.dt;
     const float syv = act ? __ldg(sy + y) : 0.f;
     const float syz0 = act ? syv + __ldg(sz + z) : 0.f, syz1 = act ? syv + __ldg(sz + z + 1) : 0.f;
-    const int c2 = 2 * tz;
+    const int c2 = 2 * tz, ii = ty * FZ + c2;
     const int iy = (ty + M) * B::YC + c2, izr = ty * B::ZC, cz = B::MZ + c2;
     Ring R;
     for (int x = xa; x < xb; x++) {
         const int it = x - xa;
-        qe[Q - 1] = ne;
-        qf[Q - 1] = nf;
         __syncthreads();
         if (s_abort) {
             if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
             return;
         }
         if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        const unsigned q = x * pl + q0;
-        float2 mm = make_float2(1.f, 1.f), e_ = Z2, d_ = Z2, p1 = Z2, r1 = Z2, p0 = Z2, r0 = Z2;
-        if (act) {
-            mm = ldg2(m, q);
-            if (!ADJ) {
-                e_ = ldg2(eps, q);
-                d_ = ldg2(del, q);
-            }
-            p1 = ldg2(pc, q);
-            r1 = ldg2(rc, q);
-            p0 = ld2(pp, q);
-            r0 = ld2(rp, q);
-        }
-        if (x + 1 < xb) fetch(x + 1);
         const bool ok = mbar_wait(&bars[R.st], R.ph);
         if (!ok) {
             s_abort = 1;
             atomicOr(err, 2);
         }
+        const float *S = sm + R.st * L::SZ;
+        const float *I = S + L::OI + ii;
+        if (ok) {
+            qe[Q - 1] = lds2(I + L::QE * IS);
+            qf[Q - 1] = lds2(I + L::QF * IS);
+        }
         if (ok && act) {
-            const float *S = sm + R.st * L::SZ;
             const float *sey = S + L::OEY, *sfy = S + L::OFY;
             float we[2 * M + 2], wf[2 * M + 2];
             zwin<M>(S + L::OEZ + izr, cz, we);
@@ -771,6 +784,9 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
                 hza += c * (fx_.x + fy_.x + (wf[M + k] - wf[M - k]));
                 hzb += c * (fx_.y + fy_.y + (wf[M + k + 1] - wf[M - k + 1]));
             }
+            const float2 mm = lds2(I + L::MM * IS), p1 = lds2(I + L::PC * IS), r1 = lds2(I + L::RC * IS);
+            const float2 p0 = lds2(I + L::PP * IS), r0 = lds2(I + L::RP * IS);
+            const float2 e_ = ADJ ? Z2 : lds2(I + L::EP * IS), d_ = ADJ ? Z2 : lds2(I + L::DE * IS);
             const float sxv = __ldg(sx + x);
             const float h0[2] = {h0a * g.ih, h0b * g.ih}, hz[2] = {hza * g.ih, hzb * g.ih};
             const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
@@ -792,10 +808,11 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
                 pn[i] = (dt2 * Lp[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
                 rn[i] = (dt2 * Lr[i] + 2.f * M2[i] * R1[i] - Bc * R0[i]) / A;
             }
+            const unsigned q = x * pl + q0;
             st2(pp, q, pn[0], pn[1]);
             st2(rp, q, rn[0], rn[1]);
-            if (ADJ && grad) {
-                const float2 u = ldg2(up, q), v = ldg2(ur, q), gg = ld2(grad, q);
+            if (GRAD) {
+                const float2 u = lds2(I + L::UP * IS), v = lds2(I + L::UR * IS), gg = lds2(I + L::GG * IS);
                 st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
                     gg.y - dt2 * (u.y * Lp[1] + v.y * Lr[1]) / M2[1]);
             }
@@ -850,6 +867,20 @@ bool make_map(CUtensorMap *m, const float *base, const GridDev &g, int bz, int b
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// descriptor of (array, box) from the handle's cache; false if encoding failed
+bool map_of(prop_s *P, const float *base, int bz, int by, CUtensorMap *out)
+{
+    const auto key = std::make_tuple((const void *)base, bz, by);
+    auto it = P->tmaps.find(key);
+    if (it == P->tmaps.end()) {
+        CUtensorMap m;
+        if (!make_map(&m, base, P->g, bz, by)) return false;
+        it = P->tmaps.emplace(key, m).first;
+    }
+    *out = it->second;
+    return true;
+}
+
 template <class K>
 bool set_smem(K kernel, size_t bytes)
 {
@@ -866,24 +897,31 @@ int el_launch(prop_s *P, float *const *S, float dt)
     dim3 blk(TZ2, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     F9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
-    CUtensorMap mxy, myy, mxz, mzz, myz, mb, mvx, mvy, mvz, mmu;
-    bool ok = make_map(&mxy, S[6], g, B::YC, B::YR) && make_map(&myy, S[4], g, B::YC, B::YR) &&
-              make_map(&mxz, S[7], g, B::ZC, B::ZR) && make_map(&mzz, S[5], g, B::ZC, B::ZR) &&
-              make_map(&myz, S[8], g, B::RC, B::RR) && make_map(&mb, P->bu, g, B::PC, B::PR) &&
-              make_map(&mvx, S[0], g, B::RC, B::RR) && make_map(&mvy, S[1], g, B::RC, B::RR) &&
-              make_map(&mvz, S[2], g, B::RC, B::RR) && make_map(&mmu, P->mu, g, B::PC, B::PR);
+    VMaps vm;
+    TMaps tm;
+    bool ok = map_of(P, S[6], B::YC, B::YR, &vm.xy) && map_of(P, S[4], B::YC, B::YR, &vm.yy) &&
+              map_of(P, S[7], B::ZC, B::ZR, &vm.xz) && map_of(P, S[5], B::ZC, B::ZR, &vm.zz) &&
+              map_of(P, S[8], B::RC, B::RR, &vm.yz) && map_of(P, P->bu, B::PC, B::PR, &vm.b) &&
+              map_of(P, S[3], FZ, FY, &vm.qxx) && map_of(P, S[6], FZ, FY, &vm.qxy) &&
+              map_of(P, S[7], FZ, FY, &vm.qxz) && map_of(P, P->bu, FZ, FY, &vm.bi) &&
+              map_of(P, S[0], B::RC, B::RR, &tm.vx) && map_of(P, S[1], B::RC, B::RR, &tm.vy) &&
+              map_of(P, S[2], B::RC, B::RR, &tm.vz) && map_of(P, P->mu, B::PC, B::PR, &tm.mu) &&
+              map_of(P, P->lam, FZ, FY, &tm.lam) && map_of(P, S[0], FZ, FY, &tm.qvx) &&
+              map_of(P, S[1], FZ, FY, &tm.qvy) && map_of(P, S[2], FZ, FY, &tm.qvz);
+    for (int i = 0; i < 3; i++) ok = ok && map_of(P, S[i], FZ, FY, &vm.v[i]);
+    for (int i = 0; i < 6; i++) ok = ok && map_of(P, S[3 + i], FZ, FY, &tm.t[i]);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = NSTAGE * VL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * TL<M>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(el_vpass_tma<M>, s1) && set_smem(el_tpass_tma<M>, s2);
     (void)attr;
-    el_vpass_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, s, P->bu, mxy, myy, mxz, mzz, myz, mb, xc, P->flag);
-    el_tpass_tma<M><<<grd, blk, s2, P->stream>>>(g, P->w, s, P->lam, mvx, mvy, mvz, mmu, xc, P->flag);
+    el_vpass_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, s, vm, xc, P->flag);
+    el_tpass_tma<M><<<grd, blk, s2, P->stream>>>(g, P->w, s, tm, xc, P->flag);
     P->kern_launches += 2;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
 }
 
-template <int M, int ADJ>
+template <int M, int ADJ, int GRAD>
 int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, float *grad)
 {
     using B = BX<M>;
@@ -891,25 +929,44 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     const int xc = P->xchunk;
     dim3 blk(TZ2, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     float *const *t = P->tmp;
-    CUtensorMap mp, mr, me, md, mey, mfy, mez, mfz;
-    bool ok = make_map(&mp, S[0], g, B::RC, B::RR) && make_map(&mr, S[1], g, B::RC, B::RR) &&
-              make_map(&me, P->eps, g, B::RC, B::RR) && make_map(&md, P->del, g, B::RC, B::RR) &&
-              make_map(&mey, t[1], g, B::YC, B::YR) && make_map(&mfy, t[4], g, B::YC, B::YR) &&
-              make_map(&mez, t[2], g, B::ZC, B::ZR) && make_map(&mfz, t[5], g, B::ZC, B::ZR);
+    RMaps rm;
+    UMaps um;
+    bool ok = map_of(P, S[0], B::RC, B::RR, &rm.p) && map_of(P, S[1], B::RC, B::RR, &rm.r) &&
+              map_of(P, S[0], FZ, FY, &rm.qp) && map_of(P, S[1], FZ, FY, &rm.qr) &&
+              map_of(P, P->nrm[0], FZ, FY, &rm.nx) && map_of(P, P->nrm[1], FZ, FY, &rm.ny) &&
+              map_of(P, t[1], B::YC, B::YR, &um.ey) && map_of(P, t[4], B::YC, B::YR, &um.fy) &&
+              map_of(P, t[2], B::ZC, B::ZR, &um.ez) && map_of(P, t[5], B::ZC, B::ZR, &um.fz) &&
+              map_of(P, t[0], FZ, FY, &um.qe) && map_of(P, t[3], FZ, FY, &um.qf) &&
+              map_of(P, P->m, FZ, FY, &um.m) && map_of(P, S[0], FZ, FY, &um.pc) &&
+              map_of(P, S[1], FZ, FY, &um.rc) && map_of(P, S[2], FZ, FY, &um.pp) &&
+              map_of(P, S[3], FZ, FY, &um.rp);
+    if (ADJ)
+        ok = ok && map_of(P, P->eps, B::RC, B::RR, &rm.e) && map_of(P, P->del, B::RC, B::RR, &rm.d) &&
+             map_of(P, P->eps, FZ, FY, &rm.qe) && map_of(P, P->del, FZ, FY, &rm.qd);
+    else
+        ok = ok && map_of(P, P->eps, FZ, FY, &um.e) && map_of(P, P->del, FZ, FY, &um.d);
+    if (GRAD)
+        ok = ok && map_of(P, up, FZ, FY, &um.up) && map_of(P, ur, FZ, FY, &um.ur) &&
+             map_of(P, grad, FZ, FY, &um.g);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = NSTAGE * RL<M, ADJ>::SZ * sizeof(float) + 64,
-                 s2 = NSTAGE * UL<M>::SZ * sizeof(float) + 64;
-    static const bool attr = set_smem(tti_rot_tma<M, ADJ>, s1) && set_smem(tti_upd_tma<M, ADJ>, s2);
+                 s2 = NSTAGE * UL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_rot_tma<M, ADJ>, s1) && set_smem(tti_upd_tma<M, ADJ, GRAD>, s2);
     (void)attr;
-    tti_rot_tma<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, P->nrm[0],
-                                                    P->nrm[1], mp, mr, me, md, t[0], t[1], t[2], t[3],
-                                                    t[4], t[5], xc, P->flag);
-    tti_upd_tma<M, ADJ><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], mey, mfy, mez, mfz, P->m, P->eps,
-                                                    P->del, S[0], S[1], S[2], S[3], up, ur, grad, P->flag,
-                                                    P->d.check_nan, xc, P->flag);
+    tti_rot_tma<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, rm, t[0], t[1],
+                                                    t[2], t[3], t[4], t[5], xc, P->flag);
+    tti_upd_tma<M, ADJ, GRAD><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, S[2], S[3], grad,
+                                                          P->flag, P->d.check_nan, xc, P->flag);
     P->kern_launches += 2;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
+}
+
+template <int M>
+int tti_launch_any(prop_s *P, float *const *S, bool adjoint, const float *up, const float *ur, float *grad)
+{
+    if (!adjoint) return tti_launch<M, 0, 0>(P, S, up, ur, grad);
+    return grad ? tti_launch<M, 1, 1>(P, S, up, ur, grad) : tti_launch<M, 1, 0>(P, S, up, ur, grad);
 }
 
 }  // namespace
@@ -945,10 +1002,10 @@ int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
     prof_begin(P, adjoint ? 1 : 0);
     int rc;
     switch (P->M) {
-    case 2: rc = adjoint ? tti_launch<2, 1>(P, S, img_p, img_r, grad) : tti_launch<2, 0>(P, S, img_p, img_r, grad); break;
-    case 4: rc = adjoint ? tti_launch<4, 1>(P, S, img_p, img_r, grad) : tti_launch<4, 0>(P, S, img_p, img_r, grad); break;
-    case 6: rc = adjoint ? tti_launch<6, 1>(P, S, img_p, img_r, grad) : tti_launch<6, 0>(P, S, img_p, img_r, grad); break;
-    case 8: rc = adjoint ? tti_launch<8, 1>(P, S, img_p, img_r, grad) : tti_launch<8, 0>(P, S, img_p, img_r, grad); break;
+    case 2: rc = tti_launch_any<2>(P, S, adjoint, img_p, img_r, grad); break;
+    case 4: rc = tti_launch_any<4>(P, S, adjoint, img_p, img_r, grad); break;
+    case 6: rc = tti_launch_any<6>(P, S, adjoint, img_p, img_r, grad); break;
+    case 8: rc = tti_launch_any<8>(P, S, adjoint, img_p, img_r, grad); break;
     default: return wp_fail(P, PROP_EINVAL, "unsupported space order");
     }
     prof_end(P, adjoint ? 1 : 0);
