@@ -45,7 +45,11 @@ ALG_BYTES = {"elastic": 84.0, "tti": 44.0}
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 200^3 case of
 # the same kernels (profiles/elastic_tma_passes_200cube_so8.md), scaled to a
 # full launch by the number of points
-TRAFFIC_B_PER_PT = {"elastic": 111.9}
+TRAFFIC_B_PER_PT = {"elastic": 114.4}
+# algorithmic FP32 operations per point update, counted from the kernels'
+# arithmetic (FMA = 2): elastic so 8 (velocity + stress pass), TTI so 12
+# (rotation + update pass)
+FLOP_PER_PT = {"elastic": 263.0, "tti": 250.0}
 
 
 def peaks():
@@ -222,10 +226,13 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
         prop.profile(False)
         out[key] = {"gpts_per_s": N / (ms / 1e3) / 1e9, "ms_per_step": ms,
                     "kernel_ms_per_step": kms / max(kn, 1),
-                    "alg_gbs": ALG_BYTES["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e9}
+                    "alg_gbs": ALG_BYTES["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e9,
+                    "alg_tflops": FLOP_PER_PT["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e12}
     prop.close()
     out["grid"] = list(prop.grid)
     out["space_order"] = so
+    out["hbm_peak_gbs"] = peaks()[0]
+    out["fp32_peak_tflops"] = wp.fp32_peak()
     return out
 
 
@@ -418,7 +425,10 @@ def main():
             "kernel": "elastic forward step (velocity + stress passes)",
             "peak_source": src_peak, "launch_ms": t_launch * 1e3,
             "alg_bytes_per_launch": ALG_BYTES["elastic"] * N,
-            "adjoint_launch_ms": a_ms / max(a_n, 1)}
+            "adjoint_launch_ms": a_ms / max(a_n, 1),
+            "fp32": {"alg_flop_per_pt": FLOP_PER_PT["elastic"],
+                     "achieved_tflops": FLOP_PER_PT["elastic"] * N / t_launch / 1e12,
+                     "peak_tflops": wp.fp32_peak(), "peak_source": "measured (FMA loop)"}}
 
     # end to end through the C ABI with pinned host buffers
     h_wav = torch.from_numpy(prob.wavelet).pin_memory()

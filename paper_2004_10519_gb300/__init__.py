@@ -82,6 +82,7 @@ def lib():
         L.prop_last_error.argtypes = [vp]
         L.prop_profile.argtypes = [vp, C.c_int]
         L.prop_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+        L.prop_fp32_peak.argtypes = [C.POINTER(C.c_double)]
         L.prop_last_launches.restype = C.c_longlong
         L.prop_last_launches.argtypes = [vp]
         _lib = L
@@ -294,6 +295,15 @@ class Propagator:
 
 # kernel ids of Propagator.kernel_stats
 K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD, K_EL_ADJ_U = 0, 1, 2, 3, 4, 5
+
+
+def fp32_peak():
+    """Measured FP32 FMA throughput of the current device [TFLOP/s]."""
+    t = C.c_double()
+    rc = lib().prop_fp32_peak(C.byref(t))
+    if rc:
+        raise PropError(rc, "prop_fp32_peak")
+    return t.value
 
 
 def plan_waves(nbytes, budget):

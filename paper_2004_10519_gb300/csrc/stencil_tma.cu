@@ -4,18 +4,20 @@
 // its 256 threads updates two adjacent z points, so shared-memory taps and
 // global accesses are 8-byte (float2) and every y-tap row serves two
 // outputs.  For every plane the y/z-halo boxes of the differentiated fields
-// are fetched by one thread with cp.async.bulk.tensor into a 3-stage
-// shared-memory ring (mbarrier completion); out-of-grid elements arrive as
-// zeros, which is the zero extension of the finite-difference operators.
-// Every other per-plane input (the thread's own values, parameters, the new
-// head of each x-derivative queue M planes ahead) comes through the same
-// ring as an interior box, so all loads are issued two planes ahead.
+// are fetched with cp.async.bulk.tensor into a 3-stage shared-memory ring;
+// out-of-grid elements arrive as zeros, which is the zero extension of the
+// finite-difference operators.  Every other per-plane input (the thread's
+// own values, parameters, the new head of each x-derivative queue M planes
+// ahead) comes through the same ring as an interior box, so all loads are
+// issued two planes ahead.  The ring is a producer/consumer pipeline on
+// mbarriers (see Ring): lane 0 of warp 0 refills a stage once every warp has
+// released it, and no CTA-wide barrier is taken per plane.
 // z-derivatives read a window of M+1 float2 per field; x-derivatives use
 // per-thread float2 register queues.
 // Offsets are 32-bit (the runtime keeps N below 2^32).  Every mbarrier wait
-// is bounded in time: on expiry the thread sets bit 2 of the error word and
-// a shared abort flag; at the next plane barrier the whole CTA leaves, after
-// its lead thread has waited (again bounded) for the copies still in flight.
+// is bounded in time: on expiry the warp sets bit 2 of the error word and
+// leaves, the producer first waiting (again bounded) for its copies in
+// flight.
 //
 // Elastic (Sec. IV, Eq. elas1, elastic listing):
 //   velocity pass  v <- g (v + dt b_avg Dtau(tau))
@@ -39,7 +41,8 @@ using tile::FY;
 using tile::FZ;
 
 constexpr int TZ2 = FZ / 2;        // threads along z, two points each
-constexpr int NT2 = TZ2 * FY;      // threads per CTA
+constexpr int NT2 = TZ2 * FY;      // consumer threads per CTA (8 warps)
+constexpr int NTP = NT2 + 32;      // + one producer warp
 constexpr int NSTAGE = 3;
 
 struct F9 {
@@ -97,17 +100,20 @@ WP_DEV bool mbar_wait(uint64_t *bar, uint32_t parity)
         if (gtimer() - t0 > 2000000000ull) return false;
     return true;
 }
-// lead thread after an abort: wait (bounded) for the stages of iterations
-// [a, b] that may still be in flight, so no copy lands after the CTA exits
-WP_DEV void drain(uint64_t *bars, int a, int b)
+WP_DEV void mbar_arrive(uint64_t *bar)
 {
-    for (int j = a < 0 ? 0 : a; j <= b; j++) mbar_wait(&bars[j % NSTAGE], (uint32_t)((j / NSTAGE) & 1));
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(saddr(bar)) : "memory");
+}
+// producer after an abort: wait (bounded) for the stages of iterations
+// [a, b] that may still be in flight, so no copy lands after the CTA exits
+WP_DEV void drain(uint64_t *full, int a, int b)
+{
+    for (int j = a < 0 ? 0 : a; j <= b; j++) mbar_wait(&full[j % NSTAGE], (uint32_t)((j / NSTAGE) & 1));
 }
 
 // 8-byte accesses (z even, NZ even: always aligned)
 WP_DEV float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
 WP_DEV float2 ldg2(const float *__restrict__ p, unsigned o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); }
-WP_DEV float2 ld2(const float *p, unsigned o) { return *reinterpret_cast<const float2 *>(p + o); }
 WP_DEV void st2(float *p, unsigned o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); }
 WP_DEV float2 dif2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 
@@ -138,19 +144,67 @@ WP_DEV void zwin(const float *row, int cz, float (&w)[2 * M + 2])
     }
 }
 
-// plane ring bookkeeping shared by the kernels
+// Producer/consumer plane ring.  full[s] completes when the copies of a
+// stage have landed (one arrive with the byte count + the TMA bytes);
+// empty[s] when every consumer warp has finished reading it (one arrive per
+// warp).  A dedicated producer warp (its lane 0) keeps NSTAGE planes in
+// flight: it refills a stage as soon as it is released, so consumers never
+// wait for each other.  All waits are bounded; a warp that gives up reports
+// bit 2 and leaves, and the producer drains its copies in flight first.
+constexpr int NWARP = NT2 / 32;
+
 struct Ring {
+    uint64_t *full, *empty;
     int st = 0;
     uint32_t ph = 0;
-    WP_DEV int refill() const { return st == 0 ? NSTAGE - 1 : st - 1; }   // stage of iteration it+NSTAGE-1
-    WP_DEV void next()
+    WP_DEV explicit Ring(uint64_t *bars) : full(bars), empty(bars + NSTAGE) {}
+    WP_DEV void init()
     {
+        for (int i = 0; i < NSTAGE; i++) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], NWARP);
+        }
+        fence_init();
+    }
+    // producer (lane 0 of the producer warp): plane xa + it into stage it % NSTAGE
+    template <class F>
+    WP_DEV void produce(int xa, int nit, F issue, int *err)
+    {
+        for (int it = 0; it < nit; it++) {
+            const int s = it % NSTAGE;
+            if (it >= NSTAGE && !mbar_wait(&empty[s], (uint32_t)(((it / NSTAGE) - 1) & 1))) {
+                atomicOr(err, 2);
+                drain(full, it - NSTAGE, it - 1);
+                return;
+            }
+            issue(xa + it, s);
+        }
+    }
+    WP_DEV bool wait_full() { return mbar_wait(&full[st], ph); }
+    // end of iteration: this warp is done with the stage
+    WP_DEV void release(int lane)
+    {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
         if (++st == NSTAGE) {
             st = 0;
             ph ^= 1u;
         }
     }
 };
+
+// barrier / OR-reduction over the consumer warps only (named barrier 1)
+WP_DEV void csync() { asm volatile("bar.sync 1, %0;" ::"n"(NT2) : "memory"); }
+WP_DEV bool csync_or(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(NT2)
+        : "memory");
+    return r != 0;
+}
 
 // ---------------------------------------------------------------------------
 // elastic velocity pass
@@ -173,17 +227,16 @@ struct VMaps {
 };
 
 template <int M>
-__global__ void __launch_bounds__(NT2, 2)
+__global__ void __launch_bounds__(NTP, 2)
 el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, int *err)
 {
     using L = VL<M>;
     using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
-    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y;
-    const bool lead = tz == 0 && ty == 0;
+    const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
+    const bool lead = warp == 0 && lane == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
@@ -203,14 +256,13 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, i
         tma3(S + L::OQ + 2 * IS, &mp.qxz, z0, y0, x + M - 1, bar);
         tma3(S + L::OBX, &mp.bi, z0, y0, min(x + 1, g.NX - 1), bar);
     };
-    if (lead) {
-        for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
-        fence_init();
-        s_abort = 0;
-    }
+    Ring R(bars);
+    if (lead) R.init();
     __syncthreads();
-    if (lead)
-        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
+    if (ty >= FY) {                                       // producer warp
+        if (lane == 0) R.produce(xa, nit, issue, err);
+        return;
+    }
     const bool act = y < g.NY && z < g.NZ;
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
@@ -233,28 +285,19 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, i
     const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz, ii = ty * FZ + c2;
     const int yb1 = y + 1 < g.NY ? ty + 1 : ty;           // +1 box row of b(y+1), clamped
     const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;       // +1 box column of b(z+2), clamped
-    Ring R;
     for (int x = xa; x < xb; x++) {
-        const int it = x - xa;
         // all threads are past iteration it-1: its stage may be refilled
-        __syncthreads();
-        if (s_abort) {
-            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+        if (!__all_sync(0xffffffffu, R.wait_full())) {
+            if (lane == 0) atomicOr(err, 2);
             return;
         }
-        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        const bool ok = mbar_wait(&bars[R.st], R.ph);
-        if (!ok) {
-            s_abort = 1;
-            atomicOr(err, 2);
-        }
         const float *S = sm + R.st * L::SZ;
-        if (ok) {
+        {
             qxx[Q - 1] = lds2(S + L::OQ + ii);
             qxy[Q - 1] = lds2(S + L::OQ + IS + ii);
             qxz[Q - 1] = lds2(S + L::OQ + 2 * IS + ii);
         }
-        if (ok && act) {
+        if (act) {
             const float *sxy = S + L::OXY, *syy = S + L::OYY, *syz = S + L::OYZ, *sb = S + L::OB;
             float wxz[2 * M + 2], wyz[2 * M + 2], wzz[2 * M + 2];
             zwin<M>(S + L::OXZ + ty * B::ZC, cz, wxz);
@@ -297,10 +340,8 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, i
             qxy[j] = qxy[j + 1];
             qxz[j] = qxz[j + 1];
         }
-        R.next();
+        R.release(lane);
     }
-    __syncthreads();
-    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -322,17 +363,16 @@ struct TMaps {
 };
 
 template <int M>
-__global__ void __launch_bounds__(NT2, 2)
+__global__ void __launch_bounds__(NTP, 2)
 el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, int *err)
 {
     using L = TL<M>;
     using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
-    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y;
-    const bool lead = tz == 0 && ty == 0;
+    const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
+    const bool lead = warp == 0 && lane == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
@@ -351,14 +391,13 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, i
         tma3(S + L::OQ + IS, &mp.qvy, z0, y0, x + M, bar);
         tma3(S + L::OQ + 2 * IS, &mp.qvz, z0, y0, x + M, bar);
     };
-    if (lead) {
-        for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
-        fence_init();
-        s_abort = 0;
-    }
+    Ring R(bars);
+    if (lead) R.init();
     __syncthreads();
-    if (lead)
-        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
+    if (ty >= FY) {                                       // producer warp
+        if (lane == 0) R.produce(xa, nit, issue, err);
+        return;
+    }
     const bool act = y < g.NY && z < g.NZ;
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
@@ -381,27 +420,18 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, i
     const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz, ii = ty * FZ + c2;
     const int yb1 = y + 1 < g.NY ? ty + 1 : ty;
     const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;
-    Ring R;
     for (int x = xa; x < xb; x++) {
-        const int it = x - xa;
-        __syncthreads();
-        if (s_abort) {
-            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+        if (!__all_sync(0xffffffffu, R.wait_full())) {
+            if (lane == 0) atomicOr(err, 2);
             return;
         }
-        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        const bool ok = mbar_wait(&bars[R.st], R.ph);
-        if (!ok) {
-            s_abort = 1;
-            atomicOr(err, 2);
-        }
         const float *S = sm + R.st * L::SZ;
-        if (ok) {
+        {
             qvx[Q - 1] = lds2(S + L::OQ + ii);
             qvy[Q - 1] = lds2(S + L::OQ + IS + ii);
             qvz[Q - 1] = lds2(S + L::OQ + 2 * IS + ii);
         }
-        if (ok && act) {
+        if (act) {
             const float *svx = S + L::OVX, *svy = S + L::OVY, *svz = S + L::OVZ;
             float wvx[2 * M + 2], wvy[2 * M + 2], wvz[2 * M + 2];
             zwin<M>(svx + cy * B::RC, cz, wvx);
@@ -464,10 +494,8 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, i
             qvy[j] = qvy[j + 1];
             qvz[j] = qvz[j + 1];
         }
-        R.next();
+        R.release(lane);
     }
-    __syncthreads();
-    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,7 +517,7 @@ struct RMaps {
 };
 
 template <int M, int ADJ>
-__global__ void __launch_bounds__(NT2, 2)
+__global__ void __launch_bounds__(NTP, 2)
 tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
             const float *__restrict__ eps, const float *__restrict__ del, const __grid_constant__ RMaps mp,
             float *__restrict__ ex, float *__restrict__ ey, float *__restrict__ ez,
@@ -499,9 +527,8 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
-    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * TZ2 + tz;
+    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * TZ2 + tz, warp = tid >> 5, lane = tid & 31;
     const bool lead = tid == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
@@ -525,14 +552,13 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
         tma3(S + L::ON, &mp.nx, z0, y0, x, bar);
         tma3(S + L::ON + IS, &mp.ny, z0, y0, x, bar);
     };
-    if (lead) {
-        for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
-        fence_init();
-        s_abort = 0;
-    }
+    Ring R(bars);
+    if (lead) R.init();
     __syncthreads();
-    if (lead)
-        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
+    if (ty >= FY) {                                       // producer warp
+        if (lane == 0) R.produce(xa, nit, issue, err);
+        return;
+    }
     const bool act = y < g.NY && z < g.NZ;
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
@@ -558,41 +584,40 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     }
     const int cy = ty + M, cz = B::MZ + 2 * tz, ii = ty * FZ + 2 * tz;
     const int ci = cy * B::RC + cz;
-    Ring R;
     for (int x = xa; x < xb; x++) {
-        const int it = x - xa;
-        __syncthreads();
-        if (s_abort) {
-            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+        if (ADJ) {
+            // the in-place transform below needs every consumer warp: decide
+            // for all of them together
+            if (csync_or(!R.wait_full())) {
+                if (lead) atomicOr(err, 2);
+                return;
+            }
+        } else if (!__all_sync(0xffffffffu, R.wait_full())) {
+            if (lane == 0) atomicOr(err, 2);
             return;
         }
-        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        const bool ok = mbar_wait(&bars[R.st], R.ph);
-        if (!ok) {
-            s_abort = 1;
-            atomicOr(err, 2);
-        }
         float *S = sm + R.st * L::SZ;
-        if (ok) {
+        {
             const float2 u = lds2(S + L::OQ + ii), v = lds2(S + L::OQ + IS + ii);
             if (ADJ) cmul(u, v, lds2(S + L::OQ + 2 * IS + ii), lds2(S + L::OQ + 3 * IS + ii), qp[Q - 1], qr[Q - 1]);
             else { qp[Q - 1] = u; qr[Q - 1] = v; }
         }
         if (ADJ) {
-            // zeta = C lam over the whole rectangle, in place (each thread a share)
-            if (ok) {
-                float *sp = S + L::OP, *sr = S + L::OR;
-                const float *se = S + L::OE, *sd = S + L::OD;
-                for (int i = tid; i < B::RR * B::RC; i += NT2) {
-                    const float c1 = 1.f + 2.f * se[i], c2 = sqrtf(1.f + 2.f * sd[i]);
-                    const float u = sp[i], v = sr[i];
-                    sp[i] = c1 * u + c2 * v;
-                    sr[i] = c2 * u + v;
-                }
+            // zeta = C lam over the whole rectangle, in place (each thread a
+            // share); the proxy fence orders these writes before the copies
+            // that later refill the stage
+            float *sp = S + L::OP, *sr = S + L::OR;
+            const float *se = S + L::OE, *sd = S + L::OD;
+            for (int i = tid; i < B::RR * B::RC; i += NT2) {
+                const float c1 = 1.f + 2.f * se[i], c2 = sqrtf(1.f + 2.f * sd[i]);
+                const float u = sp[i], v = sr[i];
+                sp[i] = c1 * u + c2 * v;
+                sr[i] = c2 * u + v;
             }
-            __syncthreads();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            csync();
         }
-        if (ok && act) {
+        if (act) {
             const float *sp = S + L::OP, *sr = S + L::OR;
             float wp[2 * M + 2], wr[2 * M + 2];
             zwin<M>(sp + cy * B::RC, cz, wp);
@@ -650,10 +675,8 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
             qp[j] = qp[j + 1];
             qr[j] = qr[j + 1];
         }
-        R.next();
+        R.release(lane);
     }
-    __syncthreads();
-    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -679,7 +702,7 @@ struct UMaps {
 };
 
 template <int M, int ADJ, int GRAD>
-__global__ void __launch_bounds__(NT2, 2)
+__global__ void __launch_bounds__(NTP, 2)
 tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
             const __grid_constant__ UMaps mp, float *__restrict__ pp, float *__restrict__ rp,
             float *__restrict__ grad, int *flag, int check, int xc, int *err)
@@ -688,10 +711,9 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
-    __shared__ int s_abort;
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y;
-    const bool lead = tz == 0 && ty == 0;
+    const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
+    const bool lead = warp == 0 && lane == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
@@ -721,14 +743,13 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
             tma3(I + L::GG * IS, &mp.g, z0, y0, x, bar);
         }
     };
-    if (lead) {
-        for (int i = 0; i < NSTAGE; i++) mbar_init(&bars[i], 1);
-        fence_init();
-        s_abort = 0;
-    }
+    Ring R(bars);
+    if (lead) R.init();
     __syncthreads();
-    if (lead)
-        for (int i = 0; i < NSTAGE - 1 && i < nit; i++) issue(xa + i, i);
+    if (ty >= FY) {                                       // producer warp
+        if (lane == 0) R.produce(xa, nit, issue, err);
+        return;
+    }
     const bool act = y < g.NY && z < g.NZ;
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
@@ -747,27 +768,18 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
     const float syz0 = act ? syv + __ldg(sz + z) : 0.f, syz1 = act ? syv + __ldg(sz + z + 1) : 0.f;
     const int c2 = 2 * tz, ii = ty * FZ + c2;
     const int iy = (ty + M) * B::YC + c2, izr = ty * B::ZC, cz = B::MZ + c2;
-    Ring R;
     for (int x = xa; x < xb; x++) {
-        const int it = x - xa;
-        __syncthreads();
-        if (s_abort) {
-            if (lead) drain(bars, it - 1, min(it + NSTAGE - 2, nit - 1));
+        if (!__all_sync(0xffffffffu, R.wait_full())) {
+            if (lane == 0) atomicOr(err, 2);
             return;
-        }
-        if (lead && it + NSTAGE - 1 < nit) issue(x + NSTAGE - 1, R.refill());
-        const bool ok = mbar_wait(&bars[R.st], R.ph);
-        if (!ok) {
-            s_abort = 1;
-            atomicOr(err, 2);
         }
         const float *S = sm + R.st * L::SZ;
         const float *I = S + L::OI + ii;
-        if (ok) {
+        {
             qe[Q - 1] = lds2(I + L::QE * IS);
             qf[Q - 1] = lds2(I + L::QF * IS);
         }
-        if (ok && act) {
+        if (act) {
             const float *sey = S + L::OEY, *sfy = S + L::OFY;
             float we[2 * M + 2], wf[2 * M + 2];
             zwin<M>(S + L::OEZ + izr, cz, we);
@@ -824,10 +836,8 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
             qe[j] = qe[j + 1];
             qf[j] = qf[j + 1];
         }
-        R.next();
+        R.release(lane);
     }
-    __syncthreads();
-    if (s_abort && lead) drain(bars, nit - 1, nit - 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -894,7 +904,7 @@ int el_launch(prop_s *P, float *const *S, float dt)
     GridDev g = P->g;
     g.dt = dt;
     const int xc = P->xchunk;
-    dim3 blk(TZ2, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     F9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
     VMaps vm;
@@ -927,7 +937,7 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     using B = BX<M>;
     const GridDev &g = P->g;
     const int xc = P->xchunk;
-    dim3 blk(TZ2, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     float *const *t = P->tmp;
     RMaps rm;
     UMaps um;

@@ -118,3 +118,26 @@ def test_antisymmetry_and_literal_transposes(so):
     np.testing.assert_allclose(DpT, Dp.T, atol=1e-15)
     np.testing.assert_allclose(DmT, Dm.T, atol=1e-15)
     np.testing.assert_allclose(Dp.T, -Dm, atol=1e-15)        # (D+)^T = -D-
+
+
+def _golden_weights():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "fd_weights.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            kind, so, *w = line.split()
+            rows.append((kind, int(so), [Fraction(v) for v in w]))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_weights(), ids=lambda r: f"{r[0]}{r[1]}")
+def test_golden_weights(row):
+    """The oracle's weights equal the published rational values
+    (tests/golden/fd_weights.txt, sources cited there) to FP64 rounding."""
+    kind, so, w = row
+    got = oracle.weights_centred(so) if kind == "centred" else oracle.weights_staggered(so)
+    assert len(got) == len(w)
+    for a, b in zip(got, w):
+        assert abs(a - float(b)) <= 2e-16 * max(1.0, abs(float(b))) * 8, (kind, so, a, b)
