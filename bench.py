@@ -45,7 +45,7 @@ ALG_BYTES = {"elastic": 84.0, "tti": 44.0}
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 200^3 case of
 # the same kernels (profiles/elastic_tma_passes_200cube_so8.md), scaled to a
 # full launch by the number of points
-TRAFFIC_B_PER_PT = {"elastic": 114.4}
+TRAFFIC_B_PER_PT = {"elastic": 113.9}
 # algorithmic FP32 operations per point update, counted from the kernels'
 # arithmetic (FMA = 2): elastic so 8 (velocity + stress pass), TTI so 12
 # (rotation + update pass)
@@ -275,6 +275,43 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
             "modes": res}
 
 
+def elastic_gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
+    """Elastic FWI gradient (so 8, dJ/d(lambda, mu, b)) shots/hour on the
+    benchmark grid (256^3 + 20-cell layer) for several storage modes at equal
+    nt; starting model: true model with a smoothed vp (vs = vp/1.73 kept)."""
+    n = 96 if small else 256
+    true = synth.elastic_random(n=n, nt=nt)
+    true.src[:, 2] = 5 * true.h        # shallow source: signal at the receivers within nt
+    start = synth.smooth_model(true.model, 100.0 / true.h, keys=("vp", "vs"))
+    p0 = synth.Problem(**{**true.__dict__, "model": start})
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    to = lambda a: torch.from_numpy(a).to(dev)
+    ptrue = wp.Propagator.from_problem(true, stream=stream)
+    d_obs = ptrue.forward(to(true.wavelet), to(true.src), to(true.rec))
+    ptrue.close()
+    wav, src, rec = to(p0.wavelet), to(p0.src), to(p0.rec)
+    res, ref = {}, None
+    for mode in modes:
+        prop = wp.Propagator.from_problem(p0, snap_mode=mode, stream=stream)
+        try:
+            g, J = prop.gradient(wav, src, rec, d_obs)          # warm-up + result
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g, J = prop.gradient(wav, src, rec, d_obs)
+            torch.cuda.synchronize()
+            sec = time.perf_counter() - t0
+            gd = g.double()
+            if ref is None:
+                ref = gd
+            err = [float(torch.linalg.norm(gd[c] - ref[c]) / torch.linalg.norm(ref[c])) for c in range(3)]
+            res[str(mode)] = {"seconds": sec, "shots_per_hour": 3600.0 / sec, "misfit": J,
+                              "rel_l2_vs_first_mode": err}
+        except wp.PropError as e:
+            res[str(mode)] = {"error": str(e)}
+        prop.close()
+    return {"nt": nt, "grid": [n + 2 * p0.nbl] * 3, "modes": res}
+
+
 def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
     """Batched TTI gradients (so 12, BF16 checkpoints): shots on windows of
     one large model with nx, ny ~ U[200, 600], nz = 300 (+ 40-cell layer);
@@ -327,7 +364,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--extra", default="", help="comma list: tti, grad, batch (secondary measurements)")
+    ap.add_argument("--extra", default="", help="comma list: tti, grad, elgrad, batch (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--batch-shots", type=int, default=8)
     ap.add_argument("--batch-nt", type=int, default=150)
@@ -349,6 +386,11 @@ def main():
                 out["tti"] = tti_throughput(wp, torch, dev)
         if "grad" in extras:
             out["grad"] = gradient_shots_per_hour(
+                wp, torch, dev, args.grad_nt,
+                [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
+                small=args.small)
+        if "elgrad" in extras:
+            out["elgrad"] = elastic_gradient_shots_per_hour(
                 wp, torch, dev, args.grad_nt,
                 [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
                 small=args.small)

@@ -199,6 +199,22 @@ el_grad_b_kernel(GridDev g, FDW w, Fields9 s, Fields9 xf0, float *__restrict__ f
     f2[q] = c * s.f[2][q] * d[2];
 }
 
+// Face products without a stencil: the forward velocity update
+// v^{k+1} = g (v^k + (dt/h) b_avg Dtau(tau^k)) gives
+// (dt/h) Dtau(tau^k) = (v^{k+1}/g - v^k) / b_avg at each velocity point, so
+// fp_c = vbar_c (v^{k+1}_c / g_c - v^k_c) / b_avg,c equals the product of
+// el_grad_b_kernel (used with the TMA-fed passes)
+__global__ void __launch_bounds__(TZ *TY)
+el_grad_face_kernel(GridDev g, Fields9 s, Fields9 xf0, Fields9 xf1, const float *__restrict__ bu,
+                    float *__restrict__ f0, float *__restrict__ f1, float *__restrict__ f2)
+{
+    EL_IDX
+    const float fx = (float)x, fy = (float)y, fz = (float)z;
+    f0[q] = s.f[0][q] * (xf1.f[0][q] / cerjan(g, fx + 0.5f, fy, fz) - xf0.f[0][q]) / bavg(bu, g, 0, x, y, z);
+    f1[q] = s.f[1][q] * (xf1.f[1][q] / cerjan(g, fx, fy + 0.5f, fz) - xf0.f[1][q]) / bavg(bu, g, 1, x, y, z);
+    f2[q] = s.f[2][q] * (xf1.f[2][q] / cerjan(g, fx, fy, fz + 0.5f) - xf0.f[2][q]) / bavg(bu, g, 2, x, y, z);
+}
+
 // gather of the scattered products: a node receives 1/4 of each of the 4
 // edges around it in each plane (clamped averaging transposed) and 1/2 of
 // the 2 faces along each axis.
@@ -515,11 +531,40 @@ int launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const fl
     return PROP_OK;
 }
 
+// the same transposed step with imaging on the TMA-fed passes: pointwise
+// tapering and stiffness, three streaming passes (velocity, imaging, stress;
+// stencil_tma.cu), pointwise face products, gather
+int launch_adj_grad_tma(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1,
+                        float *const *gr)
+{
+    const GridDev &g = P->g;
+    dim3 blk(TZ, TY, 1), grd((g.NZ + TZ - 1) / TZ, (g.NY + TY - 1) / TY, g.NX);
+    Fields9 s, sg, f0, f1;
+    for (int i = 0; i < 9; i++) {
+        s.f[i] = S[i];
+        sg.f[i] = P->tmp[i];
+        f0.f[i] = const_cast<float *>(xk[i]);
+        f1.f[i] = const_cast<float *>(xk1[i]);
+    }
+    float *const *pr = P->tmp + 9;   // edge products pr[0..2], face products pr[3..5]
+    prof_begin(P, 4);
+    el_adj_pre_kernel<<<grd, blk, 0, P->stream>>>(g, s, sg, P->lam, P->mu);
+    WP_TRY(el_adj_grad_tma(P, S, P->tmp, P->tmp + 6, xk1, gr, P->tmp + 9));
+    el_grad_face_kernel<<<grd, blk, 0, P->stream>>>(g, s, f0, f1, P->bu, pr[3], pr[4], pr[5]);
+    el_grad_gather_kernel<<<grd, blk, 0, P->stream>>>(g, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5],
+                                                      gr[1], gr[2]);
+    prof_end(P, 4);
+    P->kern_launches += 3;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 }  // namespace
 
 int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1,
                        float *const *g)
 {
+    if (tma_usable(P)) return launch_adj_grad_tma(P, S, xk, xk1, g);
     switch (P->M) {
     case 2: return launch_adj_grad<2>(P, S, xk, xk1, g);
     case 4: return launch_adj_grad<4>(P, S, xk, xk1, g);

@@ -113,6 +113,13 @@ int el_launch_fast(prop_s *P, float *const *S, float dt_sign);
 // TMA-fed passes (stencil_tma.cu): usable when NZ % 4 == 0
 bool tma_usable(const prop_s *P);
 int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
+// TMA passes of a transposed elastic step with imaging: on entry S[3..8] hold
+// t = g tbar and sig[0..5] = C t; updates vbar (S[0..2]), writes b_avg vbar to
+// w[0..2], accumulates g_lambda, g_mu (gr[0], gr[1]) and the edge products
+// ep[0..2] with the strain of v1 (forward velocities at k+1), then
+// tbar = t - dt S(w) into S[3..8]
+int el_adj_grad_tma(prop_s *P, float *const *S, float *const *sig, float *const *w, const float *const *v1,
+                    float *const *gr, float *const *ep);
 int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
                    const float *img_r, float *grad);
 // transposed elastic step in the variables (b_avg vbar, g C tbar): the
@@ -179,4 +186,9 @@ int wp_cuda(prop_s *P, cudaError_t e, const char *what);
     do {                                                        \
         cudaError_t _e = (call);                                \
         if (_e != cudaSuccess) return wp_cuda((P), _e, #call);  \
+    } while (0)
+#define WP_TRY(expr)                 \
+    do {                             \
+        int _r = (expr);             \
+        if (_r) return _r;           \
     } while (0)

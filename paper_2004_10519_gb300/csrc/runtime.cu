@@ -59,11 +59,6 @@ static int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what)
         int _r = wp_malloc((P), (void **)&(ptr), (bytes), (what));                \
         if (_r) return _r;                                                        \
     } while (0)
-#define WP_TRY(expr)                 \
-    do {                             \
-        int _r = (expr);             \
-        if (_r) return _r;           \
-    } while (0)
 
 // ---------------------------------------------------------------------------
 // FD weights: solve the moment conditions in double precision

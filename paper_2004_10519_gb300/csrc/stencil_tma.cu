@@ -43,10 +43,15 @@ using tile::FZ;
 constexpr int TZ2 = FZ / 2;        // threads along z, two points each
 constexpr int NT2 = TZ2 * FY;      // consumer threads per CTA (8 warps)
 constexpr int NTP = NT2 + 32;      // + one producer warp
+// Elastic passes above space order 8 need more than 96 registers per thread
+// and more shared memory than two CTAs per SM allow: they run one CTA per SM.
 constexpr int NSTAGE = 3;
 
 struct F9 {
     float *f[9];
+};
+struct F5 {
+    float *f[5];
 };
 
 // ---------------------------------------------------------------------------
@@ -179,6 +184,9 @@ struct Ring {
             }
             issue(xa + it, s);
         }
+        // stay until the last copies have landed (bounded), so none can
+        // arrive after the CTA has exited even if the consumers gave up
+        drain(full, nit - NSTAGE, nit - 1);
     }
     WP_DEV bool wait_full() { return mbar_wait(&full[st], ph); }
     // end of iteration: this warp is done with the stage
@@ -207,7 +215,9 @@ WP_DEV bool csync_or(bool v)
 }
 
 // ---------------------------------------------------------------------------
-// elastic velocity pass
+// elastic velocity pass.  ADJ = 1: the velocity half of the transposed step
+// in the tbar form, vbar <- g (vbar - dt Dtau(sigma)) with sigma = C g tbar
+// in s.f[3..8], and w = b_avg vbar written to o.f[0..2].
 // stage: [xy (y box)] [yy (y box)] [xz (z box)] [zz (z box)] [yz (rect)]
 //        [b (+1 box)] [v_x v_y v_z (plane x)] [queue heads: xx (x+M),
 //        xy (x+M-1), xz (x+M-1)] [b (plane x+1, clamped)]
@@ -226,9 +236,9 @@ struct VMaps {
     CUtensorMap xy, yy, xz, zz, yz, b, v[3], qxx, qxy, qxz, bi;
 };
 
-template <int M>
-__global__ void __launch_bounds__(NTP, 2)
-el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, int *err)
+template <int M, int ADJ>
+__global__ void __launch_bounds__(NTP, M <= 4 ? 2 : 1)
+el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int xc, int *err)
 {
     using L = VL<M>;
     using B = BX<M>;
@@ -327,12 +337,28 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, i
             const float bz2 = sb[ty * B::PC + zb2];
             const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
             const unsigned q = x * pl + q0;
-            st2(s.f[0], q, gxh * gyn * gzn0 * (v0.x + c * (0.5f * (b0.x + bxn.x)) * d0a),
-                gxh * gyn * gzn1 * (v0.y + c * (0.5f * (b0.y + bxn.y)) * d0b));
-            st2(s.f[1], q, gxn * gyh * gzn0 * (v1.x + c * (0.5f * (b0.x + bY.x)) * d1a),
-                gxn * gyh * gzn1 * (v1.y + c * (0.5f * (b0.y + bY.y)) * d1b));
-            st2(s.f[2], q, gxn * gyn * gzh0 * (v2.x + c * (0.5f * (b0.x + b0.y)) * d2a),
-                gxn * gyn * gzh1 * (v2.y + c * (0.5f * (b0.y + bz2)) * d2b));
+            // face averages of buoyancy and tapers at the three velocity points
+            const float bxa = 0.5f * (b0.x + bxn.x), bxb = 0.5f * (b0.y + bxn.y);
+            const float bya = 0.5f * (b0.x + bY.x), byb = 0.5f * (b0.y + bY.y);
+            const float bza = 0.5f * (b0.x + b0.y), bzb = 0.5f * (b0.y + bz2);
+            const float gx0 = gxh * gyn * gzn0, gx1 = gxh * gyn * gzn1;
+            const float gy0 = gxn * gyh * gzn0, gy1 = gxn * gyh * gzn1;
+            const float gz0 = gxn * gyn * gzh0, gz1 = gxn * gyn * gzh1;
+            if (!ADJ) {
+                st2(s.f[0], q, gx0 * (v0.x + c * bxa * d0a), gx1 * (v0.y + c * bxb * d0b));
+                st2(s.f[1], q, gy0 * (v1.x + c * bya * d1a), gy1 * (v1.y + c * byb * d1b));
+                st2(s.f[2], q, gz0 * (v2.x + c * bza * d2a), gz1 * (v2.y + c * bzb * d2b));
+            } else {
+                const float u0a = gx0 * (v0.x - c * d0a), u0b = gx1 * (v0.y - c * d0b);
+                const float u1a = gy0 * (v1.x - c * d1a), u1b = gy1 * (v1.y - c * d1b);
+                const float u2a = gz0 * (v2.x - c * d2a), u2b = gz1 * (v2.y - c * d2b);
+                st2(s.f[0], q, u0a, u0b);
+                st2(s.f[1], q, u1a, u1b);
+                st2(s.f[2], q, u2a, u2b);
+                st2(o.f[0], q, bxa * u0a, bxb * u0b);
+                st2(o.f[1], q, bya * u1a, byb * u1b);
+                st2(o.f[2], q, bza * u2a, bzb * u2b);
+            }
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -345,28 +371,38 @@ el_vpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ VMaps mp, int xc, i
 }
 
 // ---------------------------------------------------------------------------
-// elastic stress pass
-// stage: [vx rect] [vy rect] [vz rect] [mu +1 box, plane x] [mu +1 box,
-//        plane x+1] [t_xx .. t_yz, lambda (plane x)] [queue heads: vx
-//        (x+M-1), vy (x+M), vz (x+M)]
+// elastic stress pass: the strain S(v) of a velocity triple (s.f[0..2]) and
+//   MODE 0  tau <- g (tau + dt C S(v))                     (forward step)
+//   MODE 1  tbar <- t - dt S(w), t = g tbar, w = b_avg vbar  (stress half of
+//           the transposed step in the tbar form; t read, tbar written in
+//           s.f[3..8])
+//   MODE 2  imaging with the forward v^{k+1}: g_lambda += dt tr(t) tr(S v),
+//           g_mu += 2 dt sum_i t_ii S_ii, edge products dt t_c S_c
+//           (o.f = g_lambda, g_mu, xy, xz, yz products)
+// stage: [vx rect] [vy rect] [vz rect] (+ [mu +1 box, planes x, x+1] MODE 0)
+//        [t_xx .. t_yz (plane x)] (+ [lambda] MODE 0) (+ [g_lambda, g_mu]
+//        MODE 2) [queue heads: vx (x+M-1), vy (x+M), vz (x+M)]
 // ---------------------------------------------------------------------------
-template <int M>
+template <int M, int MODE>
 struct TL {
     using B = BX<M>;
+    static constexpr int NP = MODE == 0 ? 2 : 0;           // +1 boxes
+    static constexpr int NI = 6 + (MODE == 0 ? 1 : 0) + (MODE == 2 ? 2 : 0) + 3;
     static constexpr int OVX = 0, OVY = B::RS, OVZ = 2 * B::RS, OM0 = 3 * B::RS, OM1 = OM0 + B::PS,
-                         OT = OM1 + B::PS, OL = OT + 6 * IS, OQ = OL + IS, SZ = OQ + 3 * IS;
-    static constexpr uint32_t BYTES = 4u * (3 * B::RR * B::RC + 2 * B::PR * B::PC + 10 * IS);
+                         OT = 3 * B::RS + NP * B::PS, OL = OT + 6 * IS, OG = OL + (MODE == 0 ? IS : 0),
+                         OQ = OG + (MODE == 2 ? 2 * IS : 0), SZ = OQ + 3 * IS;
+    static constexpr uint32_t BYTES = 4u * (3 * B::RR * B::RC + NP * B::PR * B::PC + NI * IS);
 };
 
 struct TMaps {
-    CUtensorMap vx, vy, vz, mu, t[6], lam, qvx, qvy, qvz;
+    CUtensorMap vx, vy, vz, mu, t[6], lam, qvx, qvy, qvz, gl, gm;
 };
 
-template <int M>
-__global__ void __launch_bounds__(NTP, 2)
-el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, int *err)
+template <int M, int MODE>
+__global__ void __launch_bounds__(NTP, M <= 4 ? 2 : 1)
+el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int xc, int *err)
 {
-    using L = TL<M>;
+    using L = TL<M, MODE>;
     using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
@@ -383,10 +419,16 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, i
         tma3(S + L::OVX, &mp.vx, z0 - B::MZ, y0 - M, x, bar);
         tma3(S + L::OVY, &mp.vy, z0 - B::MZ, y0 - M, x, bar);
         tma3(S + L::OVZ, &mp.vz, z0 - B::MZ, y0 - M, x, bar);
-        tma3(S + L::OM0, &mp.mu, z0, y0, x, bar);
-        tma3(S + L::OM1, &mp.mu, z0, y0, min(x + 1, g.NX - 1), bar);
+        if (MODE == 0) {
+            tma3(S + L::OM0, &mp.mu, z0, y0, x, bar);
+            tma3(S + L::OM1, &mp.mu, z0, y0, min(x + 1, g.NX - 1), bar);
+            tma3(S + L::OL, &mp.lam, z0, y0, x, bar);
+        }
         for (int i = 0; i < 6; i++) tma3(S + L::OT + i * IS, &mp.t[i], z0, y0, x, bar);
-        tma3(S + L::OL, &mp.lam, z0, y0, x, bar);
+        if (MODE == 2) {
+            tma3(S + L::OG, &mp.gl, z0, y0, x, bar);
+            tma3(S + L::OG + IS, &mp.gm, z0, y0, x, bar);
+        }
         tma3(S + L::OQ, &mp.qvx, z0, y0, x + M - 1, bar);              // beyond NX: zeros
         tma3(S + L::OQ + IS, &mp.qvy, z0, y0, x + M, bar);
         tma3(S + L::OQ + 2 * IS, &mp.qvz, z0, y0, x + M, bar);
@@ -461,32 +503,51 @@ el_tpass_tma(GridDev g, FDW w, F9 s, const __grid_constant__ TMaps mp, int xc, i
                 gyza += b * ((wvy[M + k] - wvy[M - k + 1]) + zy.x);
                 gyzb += b * ((wvy[M + k + 1] - wvy[M - k + 2]) + zy.y);
             }
-            const float *R0 = S + L::OM0, *R1 = S + L::OM1, *T = S + L::OT + ii;
-            const float2 m0 = lds2(R0 + ty * B::PC + c2), my = lds2(R0 + yb1 * B::PC + c2);
-            const float2 mx = lds2(R1 + ty * B::PC + c2), mxy_ = lds2(R1 + yb1 * B::PC + c2);
-            const float m0z = R0[ty * B::PC + zb2], myz = R0[yb1 * B::PC + zb2], mxz = R1[ty * B::PC + zb2];
+            const float *T = S + L::OT + ii;
             const float2 t0 = lds2(T), t1 = lds2(T + IS), t2 = lds2(T + 2 * IS);
             const float2 t3 = lds2(T + 3 * IS), t4 = lds2(T + 4 * IS), t5 = lds2(T + 5 * IS);
-            const float2 l = lds2(S + L::OL + ii);
-            const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
-            const float gn0 = gxn * gyn * gzn0, gn1 = gxn * gyn * gzn1;
             const unsigned q = x * pl + q0;
-            // averages of mu over the 4 nodes around each edge (the pair's
-            // second lane is the first point's z+1 neighbour)
-            const float mxya = 0.25f * (m0.x + mx.x + my.x + mxy_.x);
-            const float mxza = 0.25f * (m0.x + mx.x + m0.y + mx.y);
-            const float myza = 0.25f * (m0.x + my.x + m0.y + my.y);
-            const float mxyb = 0.25f * (m0.y + mx.y + my.y + mxy_.y);
-            const float mxzb = 0.25f * (m0.y + mx.y + m0z + mxz);
-            const float myzb = 0.25f * (m0.y + my.y + m0z + myz);
-            const float tra = exa + eya + eza, trb = exb + eyb + ezb;
-            const float m2a = 2.f * m0.x, m2b = 2.f * m0.y;
-            st2(s.f[3], q, gn0 * (t0.x + c * (l.x * tra + m2a * exa)), gn1 * (t0.y + c * (l.y * trb + m2b * exb)));
-            st2(s.f[4], q, gn0 * (t1.x + c * (l.x * tra + m2a * eya)), gn1 * (t1.y + c * (l.y * trb + m2b * eyb)));
-            st2(s.f[5], q, gn0 * (t2.x + c * (l.x * tra + m2a * eza)), gn1 * (t2.y + c * (l.y * trb + m2b * ezb)));
-            st2(s.f[6], q, gxh * gyh * gzn0 * (t3.x + c * mxya * gxya), gxh * gyh * gzn1 * (t3.y + c * mxyb * gxyb));
-            st2(s.f[7], q, gxh * gyn * gzh0 * (t4.x + c * mxza * gxza), gxh * gyn * gzh1 * (t4.y + c * mxzb * gxzb));
-            st2(s.f[8], q, gxn * gyh * gzh0 * (t5.x + c * myza * gyza), gxn * gyh * gzh1 * (t5.y + c * myzb * gyzb));
+            if (MODE == 0) {
+                const float *R0 = S + L::OM0, *R1 = S + L::OM1;
+                const float2 m0 = lds2(R0 + ty * B::PC + c2), my = lds2(R0 + yb1 * B::PC + c2);
+                const float2 mx = lds2(R1 + ty * B::PC + c2), mxy_ = lds2(R1 + yb1 * B::PC + c2);
+                const float m0z = R0[ty * B::PC + zb2], myz = R0[yb1 * B::PC + zb2], mxz = R1[ty * B::PC + zb2];
+                const float2 l = lds2(S + L::OL + ii);
+                const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
+                const float gn0 = gxn * gyn * gzn0, gn1 = gxn * gyn * gzn1;
+                // averages of mu over the 4 nodes around each edge (the pair's
+                // second lane is the first point's z+1 neighbour)
+                const float mxya = 0.25f * (m0.x + mx.x + my.x + mxy_.x);
+                const float mxza = 0.25f * (m0.x + mx.x + m0.y + mx.y);
+                const float myza = 0.25f * (m0.x + my.x + m0.y + my.y);
+                const float mxyb = 0.25f * (m0.y + mx.y + my.y + mxy_.y);
+                const float mxzb = 0.25f * (m0.y + mx.y + m0z + mxz);
+                const float myzb = 0.25f * (m0.y + my.y + m0z + myz);
+                const float tra = exa + eya + eza, trb = exb + eyb + ezb;
+                const float m2a = 2.f * m0.x, m2b = 2.f * m0.y;
+                st2(s.f[3], q, gn0 * (t0.x + c * (l.x * tra + m2a * exa)), gn1 * (t0.y + c * (l.y * trb + m2b * exb)));
+                st2(s.f[4], q, gn0 * (t1.x + c * (l.x * tra + m2a * eya)), gn1 * (t1.y + c * (l.y * trb + m2b * eyb)));
+                st2(s.f[5], q, gn0 * (t2.x + c * (l.x * tra + m2a * eza)), gn1 * (t2.y + c * (l.y * trb + m2b * ezb)));
+                st2(s.f[6], q, gxh * gyh * gzn0 * (t3.x + c * mxya * gxya), gxh * gyh * gzn1 * (t3.y + c * mxyb * gxyb));
+                st2(s.f[7], q, gxh * gyn * gzh0 * (t4.x + c * mxza * gxza), gxh * gyn * gzh1 * (t4.y + c * mxzb * gxzb));
+                st2(s.f[8], q, gxn * gyh * gzh0 * (t5.x + c * myza * gyza), gxn * gyh * gzh1 * (t5.y + c * myzb * gyzb));
+            } else if (MODE == 1) {
+                st2(s.f[3], q, t0.x - c * exa, t0.y - c * exb);
+                st2(s.f[4], q, t1.x - c * eya, t1.y - c * eyb);
+                st2(s.f[5], q, t2.x - c * eza, t2.y - c * ezb);
+                st2(s.f[6], q, t3.x - c * gxya, t3.y - c * gxyb);
+                st2(s.f[7], q, t4.x - c * gxza, t4.y - c * gxzb);
+                st2(s.f[8], q, t5.x - c * gyza, t5.y - c * gyzb);
+            } else {
+                const float2 gl = lds2(S + L::OG + ii), gm = lds2(S + L::OG + IS + ii);
+                st2(o.f[0], q, gl.x + c * (t0.x + t1.x + t2.x) * (exa + eya + eza),
+                    gl.y + c * (t0.y + t1.y + t2.y) * (exb + eyb + ezb));
+                st2(o.f[1], q, gm.x + 2.f * c * (t0.x * exa + t1.x * eya + t2.x * eza),
+                    gm.y + 2.f * c * (t0.y * exb + t1.y * eyb + t2.y * ezb));
+                st2(o.f[2], q, c * t3.x * gxya, c * t3.y * gxyb);
+                st2(o.f[3], q, c * t4.x * gxza, c * t4.y * gxzb);
+                st2(o.f[4], q, c * t5.x * gyza, c * t5.y * gyzb);
+            }
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -528,7 +589,7 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * TZ2 + tz, warp = tid >> 5, lane = tid & 31;
+    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * TZ2 + tz, lane = tid & 31;
     const bool lead = tid == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
@@ -897,38 +958,111 @@ bool set_smem(K kernel, size_t bytes)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) == cudaSuccess;
 }
 
+// descriptors of the velocity pass: velocities v[3], stress-like fields
+// sig[6] (xx yy zz xy xz yz)
+template <int M>
+bool vmaps(prop_s *P, float *const *v, float *const *sig, VMaps *m)
+{
+    using B = BX<M>;
+    bool ok = map_of(P, sig[3], B::YC, B::YR, &m->xy) && map_of(P, sig[1], B::YC, B::YR, &m->yy) &&
+              map_of(P, sig[4], B::ZC, B::ZR, &m->xz) && map_of(P, sig[2], B::ZC, B::ZR, &m->zz) &&
+              map_of(P, sig[5], B::RC, B::RR, &m->yz) && map_of(P, P->bu, B::PC, B::PR, &m->b) &&
+              map_of(P, sig[0], FZ, FY, &m->qxx) && map_of(P, sig[3], FZ, FY, &m->qxy) &&
+              map_of(P, sig[4], FZ, FY, &m->qxz) && map_of(P, P->bu, FZ, FY, &m->bi);
+    for (int i = 0; i < 3; i++) ok = ok && map_of(P, v[i], FZ, FY, &m->v[i]);
+    return ok;
+}
+// descriptors of the stress pass: velocities vel[3], stress-like interiors t[6]
+template <int M>
+bool tmaps(prop_s *P, const float *const *vel, const float *const *t, TMaps *m)
+{
+    using B = BX<M>;
+    bool ok = map_of(P, vel[0], B::RC, B::RR, &m->vx) && map_of(P, vel[1], B::RC, B::RR, &m->vy) &&
+              map_of(P, vel[2], B::RC, B::RR, &m->vz) && map_of(P, P->mu, B::PC, B::PR, &m->mu) &&
+              map_of(P, P->lam, FZ, FY, &m->lam) && map_of(P, vel[0], FZ, FY, &m->qvx) &&
+              map_of(P, vel[1], FZ, FY, &m->qvy) && map_of(P, vel[2], FZ, FY, &m->qvz);
+    for (int i = 0; i < 6; i++) ok = ok && map_of(P, t[i], FZ, FY, &m->t[i]);
+    return ok;
+}
+
+dim3 el_grid(const prop_s *P)
+{
+    const GridDev &g = P->g;
+    const int xc = P->xchunk;
+    return dim3((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+}
+
+template <int M, int ADJ>
+int launch_v(prop_s *P, const GridDev &g, const F9 &s, const F5 &o, const VMaps &vm)
+{
+    const size_t sm = NSTAGE * VL<M>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(el_vpass_tma<M, ADJ>, sm);
+    (void)attr;
+    el_vpass_tma<M, ADJ><<<el_grid(P), dim3(TZ2, FY + 2, 1), sm, P->stream>>>(g, P->w, s, o, vm, P->xchunk,
+                                                                                P->flag);
+    P->kern_launches++;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+template <int M, int MODE>
+int launch_t(prop_s *P, const GridDev &g, const F9 &s, const F5 &o, const TMaps &tm)
+{
+    const size_t sm = NSTAGE * TL<M, MODE>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(el_tpass_tma<M, MODE>, sm);
+    (void)attr;
+    el_tpass_tma<M, MODE><<<el_grid(P), dim3(TZ2, FY + 2, 1), sm, P->stream>>>(g, P->w, s, o, tm, P->xchunk,
+                                                                                 P->flag);
+    P->kern_launches++;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 template <int M>
 int el_launch(prop_s *P, float *const *S, float dt)
 {
-    using B = BX<M>;
     GridDev g = P->g;
     g.dt = dt;
-    const int xc = P->xchunk;
-    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     F9 s;
     for (int i = 0; i < 9; i++) s.f[i] = S[i];
+    const F5 o{};
     VMaps vm;
     TMaps tm;
-    bool ok = map_of(P, S[6], B::YC, B::YR, &vm.xy) && map_of(P, S[4], B::YC, B::YR, &vm.yy) &&
-              map_of(P, S[7], B::ZC, B::ZR, &vm.xz) && map_of(P, S[5], B::ZC, B::ZR, &vm.zz) &&
-              map_of(P, S[8], B::RC, B::RR, &vm.yz) && map_of(P, P->bu, B::PC, B::PR, &vm.b) &&
-              map_of(P, S[3], FZ, FY, &vm.qxx) && map_of(P, S[6], FZ, FY, &vm.qxy) &&
-              map_of(P, S[7], FZ, FY, &vm.qxz) && map_of(P, P->bu, FZ, FY, &vm.bi) &&
-              map_of(P, S[0], B::RC, B::RR, &tm.vx) && map_of(P, S[1], B::RC, B::RR, &tm.vy) &&
-              map_of(P, S[2], B::RC, B::RR, &tm.vz) && map_of(P, P->mu, B::PC, B::PR, &tm.mu) &&
-              map_of(P, P->lam, FZ, FY, &tm.lam) && map_of(P, S[0], FZ, FY, &tm.qvx) &&
-              map_of(P, S[1], FZ, FY, &tm.qvy) && map_of(P, S[2], FZ, FY, &tm.qvz);
-    for (int i = 0; i < 3; i++) ok = ok && map_of(P, S[i], FZ, FY, &vm.v[i]);
-    for (int i = 0; i < 6; i++) ok = ok && map_of(P, S[3 + i], FZ, FY, &tm.t[i]);
-    if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-    const size_t s1 = NSTAGE * VL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * TL<M>::SZ * sizeof(float) + 64;
-    static const bool attr = set_smem(el_vpass_tma<M>, s1) && set_smem(el_tpass_tma<M>, s2);
-    (void)attr;
-    el_vpass_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, s, vm, xc, P->flag);
-    el_tpass_tma<M><<<grd, blk, s2, P->stream>>>(g, P->w, s, tm, xc, P->flag);
-    P->kern_launches += 2;
-    WP_CK(P, cudaGetLastError());
-    return PROP_OK;
+    if (!vmaps<M>(P, S, S + 3, &vm) || !tmaps<M>(P, S, S + 3, &tm))
+        return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+    WP_TRY((launch_v<M, 0>(P, g, s, o, vm)));
+    return launch_t<M, 0>(P, g, s, o, tm);
+}
+
+// transposed step in the tbar form with imaging (one forward step k -> k+1):
+// on entry S[3..8] = t = g tbar and sig[0..5] = C t; S[0..2] = vbar.
+//   vbar <- g (vbar - dt Dtau(sig)),  w = b_avg vbar   (w[0..2])
+//   g_lambda, g_mu, edge products from t and S(v^{k+1})
+//   tbar <- t - dt S(w)
+template <int M>
+int el_adj_grad(prop_s *P, float *const *S, float *const *sig, float *const *w, const float *const *v1,
+                float *const *gr, float *const *ep)
+{
+    const GridDev &g = P->g;
+    VMaps vm;
+    TMaps tg, tt;
+    if (!vmaps<M>(P, S, sig, &vm) || !tmaps<M>(P, v1, S + 3, &tg) || !tmaps<M>(P, w, S + 3, &tt) ||
+        !map_of(P, gr[0], FZ, FY, &tg.gl) || !map_of(P, gr[1], FZ, FY, &tg.gm))
+        return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+    F9 sv, sg, st;
+    for (int i = 0; i < 3; i++) {
+        sv.f[i] = S[i];
+        sg.f[i] = const_cast<float *>(v1[i]);
+        st.f[i] = w[i];
+    }
+    for (int i = 0; i < 6; i++) {
+        sv.f[3 + i] = sig[i];
+        sg.f[3 + i] = S[3 + i];
+        st.f[3 + i] = S[3 + i];
+    }
+    const F5 ow{{w[0], w[1], w[2], nullptr, nullptr}}, og{{gr[0], gr[1], ep[0], ep[1], ep[2]}}, none{};
+    WP_TRY((launch_v<M, 1>(P, g, sv, ow, vm)));
+    WP_TRY((launch_t<M, 2>(P, g, sg, og, tg)));
+    return launch_t<M, 1>(P, g, st, none, tt);
 }
 
 template <int M, int ADJ, int GRAD>
@@ -1004,6 +1138,19 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
     }
     prof_end(P, dt_sign > 0 ? 2 : 5);
     return rc;
+}
+
+// the TMA passes of one transposed elastic step with imaging (see el_adj_grad)
+int el_adj_grad_tma(prop_s *P, float *const *S, float *const *sig, float *const *w, const float *const *v1,
+                    float *const *gr, float *const *ep)
+{
+    switch (P->M) {
+    case 2: return el_adj_grad<2>(P, S, sig, w, v1, gr, ep);
+    case 4: return el_adj_grad<4>(P, S, sig, w, v1, gr, ep);
+    case 6: return el_adj_grad<6>(P, S, sig, w, v1, gr, ep);
+    case 8: return el_adj_grad<8>(P, S, sig, w, v1, gr, ep);
+    }
+    return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
 
 int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,

@@ -73,8 +73,11 @@ def test_adjoint_parity_and_dot(wp, so, shape):
     assert abs(a - b) <= 1e-5 * abs(a), (a, b)
 
 
-def test_gradient_parity_and_checkpoint_modes(wp):
-    p = ragged_el(8, nt=60, shape=(22, 20, 24), nbl=4)
+# computational NZ 32: TMA-fed passes with pointwise face products;
+# NZ 33: the direct-load transposed step
+@pytest.mark.parametrize("shape", [(22, 20, 24), (22, 20, 25)])
+def test_gradient_parity_and_checkpoint_modes(wp, shape):
+    p = ragged_el(8, nt=60, shape=shape, nbl=4)
     d_obs = oracle.Problem(p).forward()
     start = synth.random_elastic(p.nx, p.ny, p.nz, 5, 3.0)
     start = {k: (0.5 * (start[k] + p.model[k])).astype(np.float32) for k in start}
