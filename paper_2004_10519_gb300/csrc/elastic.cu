@@ -199,20 +199,38 @@ el_grad_b_kernel(GridDev g, FDW w, Fields9 s, Fields9 xf0, float *__restrict__ f
     f2[q] = c * s.f[2][q] * d[2];
 }
 
-// Face products without a stencil: the forward velocity update
-// v^{k+1} = g (v^k + (dt/h) b_avg Dtau(tau^k)) gives
+// Face products of the b-gradient without a stencil.  The forward velocity
+// update v^{k+1} = g (v^k + (dt/h) b_avg Dtau(tau^k)) gives
 // (dt/h) Dtau(tau^k) = (v^{k+1}/g - v^k) / b_avg at each velocity point, so
 // fp_c = vbar_c (v^{k+1}_c / g_c - v^k_c) / b_avg,c equals the product of
-// el_grad_b_kernel (used with the TMA-fed passes)
-__global__ void __launch_bounds__(TZ *TY)
-el_grad_face_kernel(GridDev g, Fields9 s, Fields9 xf0, Fields9 xf1, const float *__restrict__ bu,
-                    float *__restrict__ f0, float *__restrict__ f1, float *__restrict__ f2)
+// el_grad_b_kernel.  Two z points per thread, 8-byte accesses (NZ even, as
+// on the TMA path that uses it); tapers and averages as in the TMA passes.
+__global__ void __launch_bounds__(256)
+el_face2_kernel(GridDev g, Fields9 s, Fields9 xf0, Fields9 xf1, const float *__restrict__ bu,
+                float *__restrict__ f0, float *__restrict__ f1, float *__restrict__ f2)
 {
-    EL_IDX
-    const float fx = (float)x, fy = (float)y, fz = (float)z;
-    f0[q] = s.f[0][q] * (xf1.f[0][q] / cerjan(g, fx + 0.5f, fy, fz) - xf0.f[0][q]) / bavg(bu, g, 0, x, y, z);
-    f1[q] = s.f[1][q] * (xf1.f[1][q] / cerjan(g, fx, fy + 0.5f, fz) - xf0.f[1][q]) / bavg(bu, g, 1, x, y, z);
-    f2[q] = s.f[2][q] * (xf1.f[2][q] / cerjan(g, fx, fy, fz + 0.5f) - xf0.f[2][q]) / bavg(bu, g, 2, x, y, z);
+    const int x = blockIdx.z, y = blockIdx.y * 8 + threadIdx.y, z = 2 * (blockIdx.x * 32 + threadIdx.x);
+    if (y >= g.NY || z >= g.NZ) return;
+    const long long pl = (long long)g.NY * g.NZ, q = ((long long)x * g.NY + y) * g.NZ + z;
+    auto ld = [](const float *p, long long o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
+    auto st = [](float *p, long long o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); };
+    const float2 b0 = ld(bu, q);
+    const float2 bX = x + 1 < g.NX ? ld(bu, q + pl) : b0, bY = y + 1 < g.NY ? ld(bu, q + g.NZ) : b0;
+    const float bz2 = z + 2 < g.NZ ? __ldg(bu + q + 2) : b0.y;
+    const float *tz = g.tab + 2 * (g.NX + g.NY);
+    const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
+    const float gyn = __ldg(g.tab + 2 * g.NX + 2 * y), gyh = __ldg(g.tab + 2 * g.NX + 2 * y + 1);
+    const float gzn0 = __ldg(tz + 2 * z), gzh0 = __ldg(tz + 2 * z + 1);
+    const float gzn1 = __ldg(tz + 2 * z + 2), gzh1 = __ldg(tz + 2 * z + 3);
+    const float2 u0 = ld(s.f[0], q), u1 = ld(s.f[1], q), u2 = ld(s.f[2], q);
+    const float2 a0 = ld(xf0.f[0], q), a1 = ld(xf0.f[1], q), a2 = ld(xf0.f[2], q);
+    const float2 c0 = ld(xf1.f[0], q), c1 = ld(xf1.f[1], q), c2 = ld(xf1.f[2], q);
+    st(f0, q, u0.x * (c0.x / (gxh * gyn * gzn0) - a0.x) / (0.5f * (b0.x + bX.x)),
+       u0.y * (c0.y / (gxh * gyn * gzn1) - a0.y) / (0.5f * (b0.y + bX.y)));
+    st(f1, q, u1.x * (c1.x / (gxn * gyh * gzn0) - a1.x) / (0.5f * (b0.x + bY.x)),
+       u1.y * (c1.y / (gxn * gyh * gzn1) - a1.y) / (0.5f * (b0.y + bY.y)));
+    st(f2, q, u2.x * (c2.x / (gxn * gyn * gzh0) - a2.x) / (0.5f * (b0.x + b0.y)),
+       u2.y * (c2.y / (gxn * gyn * gzh1) - a2.y) / (0.5f * (b0.y + bz2)));
 }
 
 // gather of the scattered products: a node receives 1/4 of each of the 4
@@ -549,8 +567,9 @@ int launch_adj_grad_tma(prop_s *P, float *const *S, const float *const *xk, cons
     float *const *pr = P->tmp + 9;   // edge products pr[0..2], face products pr[3..5]
     prof_begin(P, 4);
     el_adj_pre_kernel<<<grd, blk, 0, P->stream>>>(g, s, sg, P->lam, P->mu);
-    WP_TRY(el_adj_grad_tma(P, S, P->tmp, P->tmp + 6, xk1, gr, P->tmp + 9));
-    el_grad_face_kernel<<<grd, blk, 0, P->stream>>>(g, s, f0, f1, P->bu, pr[3], pr[4], pr[5]);
+    WP_TRY(el_adj_grad_tma(P, S, P->tmp, P->tmp + 6, xk1, gr, pr));
+    el_face2_kernel<<<dim3((g.NZ + 63) / 64, (g.NY + 7) / 8, g.NX), dim3(32, 8, 1), 0, P->stream>>>(
+        g, s, f0, f1, P->bu, pr[3], pr[4], pr[5]);
     el_grad_gather_kernel<<<grd, blk, 0, P->stream>>>(g, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5],
                                                       gr[1], gr[2]);
     prof_end(P, 4);

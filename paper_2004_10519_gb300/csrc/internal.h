@@ -135,6 +135,8 @@ void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, 
 // inject: f[cell] += coef(cell) * sum_j w_j traces[trace_j*nt + t] into up to 3 fields;
 // mode 0: coef = scale; mode 1: coef = scale / A (TTI, A = m(1+sig dt/2));
 // mode 2: coef = scale (3 lambda + 2 mu) (elastic adjoint in s = C tbar);
+// mode 3: as mode 1 into f0 = lam_p, and (1 + 2 eps), sqrt(1 + 2 delta) times
+// that into f1 = zeta_p, f2 = zeta_r (TTI transposed step, zeta = C lam);
 // grad_u != NULL: grad[cell] -= u[cell] * scale*sum / m  (TTI imaging of the
 // residual injection)
 void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
@@ -148,7 +150,9 @@ void sp_transpose(prop_s *P, const float *in_tn, float *out_nt, int n, int nt);
 // misc kernels
 void k_fill(prop_s *P, float *a, long long n, float v);
 void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode);
-void k_fold(prop_s *P, const float *comp, float *phys);
+// fold a computational-grid array onto the physical grid (transpose of the
+// edge-replication extension); s1, s2: scratch of N floats each
+void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2);
 void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long n);
 double k_sumsq_host(prop_s *P, const float *a, long long n);
 void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr);

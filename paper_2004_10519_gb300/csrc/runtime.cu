@@ -594,6 +594,9 @@ static int step_state(prop_s *P, float **s, bool adjoint)
 extern "C" int prop_step(prop_t *P, int nsteps, int adjoint)
 {
     WP_TRY(check_handle(P));
+    // TTI transposed steps differentiate zeta = C lam, which each step then
+    // keeps up to date: form it once from the state
+    if (adjoint && P->d.kind == PROP_TTI && nsteps > 0) k_tti_zeta(P, P->st[0], P->st[1], P->tmp[6], P->tmp[7]);
     if (nsteps < 0) return wp_fail(P, PROP_EINVAL, "nsteps < 0");
     for (int i = 0; i < nsteps; i++) WP_TRY(step_state(P, P->st, adjoint != 0));
     return finish(P);
@@ -856,8 +859,8 @@ static void inject_resid(prop_s *P, const Geometry &G, const float *res, int k, 
                          const float *img_p, float *grad)
 {
     const int nt = P->d.nt;
-    if (P->d.kind == PROP_TTI)
-        sp_inject(P, &G.R, res, nt, k, 1.f, 1, a[0], nullptr, nullptr, grad ? img_p : nullptr, grad);
+    if (P->d.kind == PROP_TTI)   // also keeps zeta = C lam (tmp[6], tmp[7]) in step
+        sp_inject(P, &G.R, res, nt, k, 1.f, 3, a[0], P->tmp[6], P->tmp[7], grad ? img_p : nullptr, grad);
     else
         sp_inject(P, &G.R, res, nt, k, 1.f, 0, a[3], a[4], a[5], nullptr, nullptr);
 }
@@ -877,6 +880,7 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
     WP_TRY(ensure_ast(P));
     float *a[4] = {P->ast[0], P->ast[1], P->ast[2], P->ast[3]};
     WP_TRY(zero_fields(P, a, 4));
+    WP_TRY(zero_fields(P, P->tmp + 6, 2));   // zeta = C lam of the zero state
     if (srcstage) WP_CK(P, cudaMemsetAsync(srcstage, 0, sizeof(float) * (size_t)nt * G.S.n, P->stream));
     auto adj_iter = [&](int k, const float *up, const float *ur) -> int {
         WP_TRY(tti_launch_step(P, a, true, up, ur, grad));
@@ -1049,7 +1053,8 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
         WP_TRY(copy_out(P, src_grad, (const float *)out.p, (size_t)nt * nsrc));
     }
     if (grad) {
-        for (int i = 0; i < ng; i++) k_fold(P, g3[i], (float *)gphys.p + i * np);
+        WP_TRY(ensure_tmp(P, 2));        // fold scratch (free after the sweep)
+        for (int i = 0; i < ng; i++) k_fold(P, g3[i], (float *)gphys.p + i * np, P->tmp[0], P->tmp[1]);
         WP_TRY(copy_out(P, grad, (const float *)gphys.p, np * ng));
     }
     return finish(P);

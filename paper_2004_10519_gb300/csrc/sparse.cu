@@ -43,13 +43,14 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
                               float *f0, float *f1, float *f2, const float *__restrict__ gu,
                               float *grad)
 {
+    // lam, mu: the elastic Lame parameters; for TTI (mode 3) epsilon, delta
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ncell) return;
     float acc = 0.f;
     for (int e = ptr[j]; e < ptr[j + 1]; e++) acc += w[e] * traces[(long long)tr[e] * nt + t];
     const long long q = cell[j];
     float coef = scale;
-    if (mode == 1) {
+    if (mode == 1 || mode == 3) {
         const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
         const float A = m[q] * (1.f + 0.5f * tti_sigma(g, x, y, z) * g.dt);
         coef = scale / A;
@@ -61,8 +62,15 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
     }
     const float v = coef * acc;
     f0[q] += v;
-    if (f1) f1[q] += v;
-    if (f2) f2[q] += v;
+    if (mode == 3) {
+        // TTI transposed step: the residual enters lam_p; keep zeta = C lam
+        // (f1, f2) consistent: zeta_p += (1 + 2 eps) v, zeta_r += sqrt(1 + 2 delta) v
+        f1[q] += (1.f + 2.f * lam[q]) * v;
+        f2[q] += sqrtf(1.f + 2.f * mu[q]) * v;
+    } else {
+        if (f1) f1[q] += v;
+        if (f2) f2[q] += v;
+    }
     if (grad) grad[q] -= gu[q] * (scale * acc) / m[q];
 }
 
@@ -155,25 +163,25 @@ __global__ void normals_kernel(long long n, const float *th, const float *ph, fl
 }
 
 // adjoint of the edge-replication extension (gather form)
-__global__ void fold_kernel(GridDev g, const float *__restrict__ comp, float *__restrict__ phys)
+// adjoint of the edge-replication extension along one axis of a [d0][d1][d2]
+// array: physical index c of that axis (n points) receives the
+// computational cells c + nbl, plus the whole layer in front of c = 0 and
+// behind c = n - 1.  Folding the three axes in turn is the transpose of the
+// three-axis extension, with at most nbl + 1 terms per output.
+__global__ void fold_axis_kernel(const float *__restrict__ in, float *__restrict__ out, int d0, int d1,
+                                 int d2, int axis, int n, int nbl)
 {
-    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long np = (long long)g.px * g.py * g.pz;
-    if (q >= np) return;
-    const int k = (int)(q % g.pz), j = (int)((q / g.pz) % g.py), i = (int)(q / ((long long)g.pz * g.py));
-    auto range = [&](int c, int n, int N, int &lo, int &hi) {
-        lo = (c == 0) ? 0 : c + g.nbl;
-        hi = (c == n - 1) ? N - 1 : c + g.nbl;
-    };
-    int x0, x1, y0, y1, z0, z1;
-    range(i, g.px, g.NX, x0, x1);
-    range(j, g.py, g.NY, y0, y1);
-    range(k, g.pz, g.NZ, z0, z1);
+    const int o0 = axis == 0 ? n : d0, o1 = axis == 1 ? n : d1, o2 = axis == 2 ? n : d2;
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= (long long)o0 * o1 * o2) return;
+    const int k = (int)(q % o2), j = (int)((q / o2) % o1), i = (int)(q / ((long long)o2 * o1));
+    const int c = axis == 0 ? i : (axis == 1 ? j : k), N = axis == 0 ? d0 : (axis == 1 ? d1 : d2);
+    const int lo = c == 0 ? 0 : c + nbl, hi = c == n - 1 ? N - 1 : c + nbl;
+    const long long st = axis == 0 ? (long long)d1 * d2 : (axis == 1 ? (long long)d2 : 1LL);
+    const long long base = ((long long)(axis == 0 ? 0 : i) * d1 + (axis == 1 ? 0 : j)) * d2 + (axis == 2 ? 0 : k);
     float s = 0.f;
-    for (int x = x0; x <= x1; x++)
-        for (int y = y0; y <= y1; y++)
-            for (int z = z0; z <= z1; z++) s += comp[gidx(g, x, y, z)];
-    phys[q] = s;
+    for (int t = lo; t <= hi; t++) s += in[base + t * st];
+    out[q] = s;
 }
 
 __global__ void zeta_kernel(long long n, const float *__restrict__ eps, const float *__restrict__ del,
@@ -360,7 +368,8 @@ void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t
     if (S->ncell <= 0) return;
     inject_kernel<<<nblk(S->ncell), NB, 0, P->stream>>>(P->g, S->ncell, S->cell, S->cell_ptr,
                                                         S->ent_trace, S->ent_w, traces, nt, t, scale,
-                                                        mode, P->m, P->lam, P->mu, f0, f1, f2,
+                                                        mode, P->m, mode == 3 ? P->eps : P->lam,
+                                                        mode == 3 ? P->del : P->mu, f0, f1, f2,
                                                         grad_u, grad);
     P->kern_launches++;
 }
@@ -401,11 +410,15 @@ void k_normals(prop_s *P)
     normals_kernel<<<nblk(P->g.N), NB, 0, P->stream>>>(P->g.N, P->th, P->ph, P->nrm[0], P->nrm[1]);
 }
 
-void k_fold(prop_s *P, const float *comp, float *phys)
+void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2)
 {
-    const long long np = (long long)P->g.px * P->g.py * P->g.pz;
-    fold_kernel<<<nblk(np), NB, 0, P->stream>>>(P->g, comp, phys);
-    P->kern_launches++;
+    const GridDev &g = P->g;
+    const long long n1 = (long long)g.NX * g.NY * g.pz, n2 = (long long)g.NX * g.py * g.pz,
+                    n3 = (long long)g.px * g.py * g.pz;
+    fold_axis_kernel<<<nblk(n1), NB, 0, P->stream>>>(comp, s1, g.NX, g.NY, g.NZ, 2, g.pz, g.nbl);
+    fold_axis_kernel<<<nblk(n2), NB, 0, P->stream>>>(s1, s2, g.NX, g.NY, g.pz, 1, g.py, g.nbl);
+    fold_axis_kernel<<<nblk(n3), NB, 0, P->stream>>>(s2, phys, g.NX, g.py, g.pz, 0, g.px, g.nbl);
+    P->kern_launches += 3;
 }
 
 void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr)

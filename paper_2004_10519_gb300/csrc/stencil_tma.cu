@@ -54,6 +54,7 @@ struct F5 {
     float *f[5];
 };
 
+
 // ---------------------------------------------------------------------------
 // device: mbarrier / TMA helpers (inline PTX)
 // ---------------------------------------------------------------------------
@@ -201,18 +202,6 @@ struct Ring {
     }
 };
 
-// barrier / OR-reduction over the consumer warps only (named barrier 1)
-WP_DEV void csync() { asm volatile("bar.sync 1, %0;" ::"n"(NT2) : "memory"); }
-WP_DEV bool csync_or(bool v)
-{
-    uint32_t r;
-    asm volatile(
-        "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}"
-        : "=r"(r)
-        : "r"((uint32_t)v), "n"(NT2)
-        : "memory");
-    return r != 0;
-}
 
 // ---------------------------------------------------------------------------
 // elastic velocity pass.  ADJ = 1: the velocity half of the transposed step
@@ -296,7 +285,6 @@ el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int
     const int yb1 = y + 1 < g.NY ? ty + 1 : ty;           // +1 box row of b(y+1), clamped
     const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;       // +1 box column of b(z+2), clamped
     for (int x = xa; x < xb; x++) {
-        // all threads are past iteration it-1: its stage may be refilled
         if (!__all_sync(0xffffffffu, R.wait_full())) {
             if (lane == 0) atomicOr(err, 2);
             return;
@@ -560,37 +548,35 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
 }
 
 // ---------------------------------------------------------------------------
-// TTI rotation pass.
-// stage: [p rect] [r rect] (+ [eps rect] [del rect] ADJ) [queue heads p, r
-//        (x+M)] (+ [eps, del (x+M)] ADJ) [n_x, n_y (plane x)]
+// TTI rotation pass on (p, r), or on zeta = C lam in the transposed step
+// (the update pass of the previous adjoint step writes zeta).
+// stage: [p rect] [r rect] [queue heads p, r (x+M)] [n_x, n_y (plane x)]
 // ---------------------------------------------------------------------------
-template <int M, int ADJ>
+template <int M>
 struct RL {
     using B = BX<M>;
-    static constexpr int NR = ADJ ? 4 : 2, NQ = ADJ ? 4 : 2;
-    static constexpr int OP = 0, OR = B::RS, OE = 2 * B::RS, OD = 3 * B::RS, OQ = NR * B::RS,
-                         ON = OQ + NQ * IS, SZ = ON + 2 * IS;
-    static constexpr uint32_t BYTES = 4u * (NR * B::RR * B::RC + (NQ + 2) * IS);
+    static constexpr int OP = 0, OR = B::RS, OQ = 2 * B::RS, ON = OQ + 2 * IS, SZ = ON + 2 * IS;
+    static constexpr uint32_t BYTES = 4u * (2 * B::RR * B::RC + 4 * IS);
 };
 
 struct RMaps {
-    CUtensorMap p, r, e, d, qp, qr, qe, qd, nx, ny;
+    CUtensorMap p, r, qp, qr, nx, ny;
 };
 
-template <int M, int ADJ>
+template <int M>
 __global__ void __launch_bounds__(NTP, 2)
 tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
-            const float *__restrict__ eps, const float *__restrict__ del, const __grid_constant__ RMaps mp,
-            float *__restrict__ ex, float *__restrict__ ey, float *__restrict__ ez,
-            float *__restrict__ fx, float *__restrict__ fy, float *__restrict__ fz, int xc, int *err)
+            const __grid_constant__ RMaps mp, float *__restrict__ ex, float *__restrict__ ey,
+            float *__restrict__ ez, float *__restrict__ fx, float *__restrict__ fy, float *__restrict__ fz,
+            int xc, int *err)
 {
-    using L = RL<M, ADJ>;
+    using L = RL<M>;
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
-    const int tz = threadIdx.x, ty = threadIdx.y, tid = ty * TZ2 + tz, lane = tid & 31;
-    const bool lead = tid == 0;
+    const int tz = threadIdx.x, ty = threadIdx.y, lane = (ty * TZ2 + tz) & 31;
+    const bool lead = ty == 0 && tz == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
@@ -600,16 +586,8 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
         mbar_expect(bar, L::BYTES);
         tma3(S + L::OP, &mp.p, z0 - B::MZ, y0 - M, x, bar);
         tma3(S + L::OR, &mp.r, z0 - B::MZ, y0 - M, x, bar);
-        if (ADJ) {
-            tma3(S + L::OE, &mp.e, z0 - B::MZ, y0 - M, x, bar);
-            tma3(S + L::OD, &mp.d, z0 - B::MZ, y0 - M, x, bar);
-        }
         tma3(S + L::OQ, &mp.qp, z0, y0, x + M, bar);                  // beyond NX: zeros
         tma3(S + L::OQ + IS, &mp.qr, z0, y0, x + M, bar);
-        if (ADJ) {
-            tma3(S + L::OQ + 2 * IS, &mp.qe, z0, y0, x + M, bar);
-            tma3(S + L::OQ + 3 * IS, &mp.qd, z0, y0, x + M, bar);
-        }
         tma3(S + L::ON, &mp.nx, z0, y0, x, bar);
         tma3(S + L::ON + IS, &mp.ny, z0, y0, x, bar);
     };
@@ -624,60 +602,24 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
     const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
     const float2 Z2 = make_float2(0.f, 0.f);
-    // zeta = C (lam_p, lam_r) of a pair (ADJ)
-    auto cmul = [](float2 u, float2 v, float2 e, float2 d, float2 &a, float2 &b) {
-        const float c1a = 1.f + 2.f * e.x, c2a = sqrtf(1.f + 2.f * d.x);
-        const float c1b = 1.f + 2.f * e.y, c2b = sqrtf(1.f + 2.f * d.y);
-        a = make_float2(c1a * u.x + c2a * v.x, c1b * u.y + c2b * v.y);
-        b = make_float2(c2a * u.x + v.x, c2b * u.y + v.y);
-    };
     float2 qp[Q], qr[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
         const int xq = xa - M + j;
-        qp[j] = qr[j] = Z2;
-        if (act && xq >= 0 && xq < g.NX) {
-            const unsigned q = xq * pl + q0;
-            const float2 u = ldg2(p, q), v = ldg2(r, q);
-            if (ADJ) cmul(u, v, ldg2(eps, q), ldg2(del, q), qp[j], qr[j]);
-            else { qp[j] = u; qr[j] = v; }
-        }
+        const bool in = act && xq >= 0 && xq < g.NX;
+        qp[j] = in ? ldg2(p, xq * pl + q0) : Z2;
+        qr[j] = in ? ldg2(r, xq * pl + q0) : Z2;
     }
     const int cy = ty + M, cz = B::MZ + 2 * tz, ii = ty * FZ + 2 * tz;
     const int ci = cy * B::RC + cz;
     for (int x = xa; x < xb; x++) {
-        if (ADJ) {
-            // the in-place transform below needs every consumer warp: decide
-            // for all of them together
-            if (csync_or(!R.wait_full())) {
-                if (lead) atomicOr(err, 2);
-                return;
-            }
-        } else if (!__all_sync(0xffffffffu, R.wait_full())) {
+        if (!__all_sync(0xffffffffu, R.wait_full())) {
             if (lane == 0) atomicOr(err, 2);
             return;
         }
-        float *S = sm + R.st * L::SZ;
-        {
-            const float2 u = lds2(S + L::OQ + ii), v = lds2(S + L::OQ + IS + ii);
-            if (ADJ) cmul(u, v, lds2(S + L::OQ + 2 * IS + ii), lds2(S + L::OQ + 3 * IS + ii), qp[Q - 1], qr[Q - 1]);
-            else { qp[Q - 1] = u; qr[Q - 1] = v; }
-        }
-        if (ADJ) {
-            // zeta = C lam over the whole rectangle, in place (each thread a
-            // share); the proxy fence orders these writes before the copies
-            // that later refill the stage
-            float *sp = S + L::OP, *sr = S + L::OR;
-            const float *se = S + L::OE, *sd = S + L::OD;
-            for (int i = tid; i < B::RR * B::RC; i += NT2) {
-                const float c1 = 1.f + 2.f * se[i], c2 = sqrtf(1.f + 2.f * sd[i]);
-                const float u = sp[i], v = sr[i];
-                sp[i] = c1 * u + c2 * v;
-                sr[i] = c2 * u + v;
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            csync();
-        }
+        const float *S = sm + R.st * L::SZ;
+        qp[Q - 1] = lds2(S + L::OQ + ii);
+        qr[Q - 1] = lds2(S + L::OQ + IS + ii);
         if (act) {
             const float *sp = S + L::OP, *sr = S + L::OR;
             float wp[2 * M + 2], wr[2 * M + 2];
@@ -741,20 +683,21 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
 }
 
 // ---------------------------------------------------------------------------
-// TTI update pass.
+// TTI update pass.  ADJ: the transposed step, which also writes
+// zeta = C lam of the new level (zp, zr) for the next rotation pass.
 // stage: [e_y y box] [f_y y box] [e_z z box] [f_z z box] [queue heads e_x,
-//        f_x (x+M)] [m, p^n, r^n, p^{n-1}, r^{n-1} (plane x)] (+ [eps, del]
-//        forward) (+ [u_p, u_r, g] imaging)
+//        f_x (x+M)] [m, p^n, r^n, p^{n-1}, r^{n-1}, eps, del (plane x)]
+//        (+ [u_p, u_r, g] imaging)
 // ---------------------------------------------------------------------------
 template <int M, int ADJ, int GRAD>
 struct UL {
     using B = BX<M>;
-    static constexpr int NI = 7 + (ADJ ? 0 : 2) + (GRAD ? 3 : 0);
+    static constexpr int NI = 9 + (GRAD ? 3 : 0);
     static constexpr int OEY = 0, OFY = B::YS, OEZ = 2 * B::YS, OFZ = OEZ + B::ZS, OI = OFZ + B::ZS,
                          SZ = OI + NI * IS;
     // interior slots
     static constexpr int QE = 0, QF = 1, MM = 2, PC = 3, RC = 4, PP = 5, RP = 6, EP = 7, DE = 8,
-                         UP = ADJ ? 7 : 9, UR = UP + 1, GG = UP + 2;
+                         UP = 9, UR = UP + 1, GG = UP + 2;
     static constexpr uint32_t BYTES = 4u * (2 * B::YR * B::YC + 2 * B::ZR * B::ZC + NI * IS);
 };
 
@@ -766,7 +709,8 @@ template <int M, int ADJ, int GRAD>
 __global__ void __launch_bounds__(NTP, 2)
 tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
             const __grid_constant__ UMaps mp, float *__restrict__ pp, float *__restrict__ rp,
-            float *__restrict__ grad, int *flag, int check, int xc, int *err)
+            float *__restrict__ grad, float *__restrict__ zp, float *__restrict__ zr, int *flag, int check,
+            int xc, int *err)
 {
     using L = UL<M, ADJ, GRAD>;
     using B = BX<M>;
@@ -794,10 +738,8 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
         tma3(I + L::RC * IS, &mp.rc, z0, y0, x, bar);
         tma3(I + L::PP * IS, &mp.pp, z0, y0, x, bar);
         tma3(I + L::RP * IS, &mp.rp, z0, y0, x, bar);
-        if (!ADJ) {
-            tma3(I + L::EP * IS, &mp.e, z0, y0, x, bar);
-            tma3(I + L::DE * IS, &mp.d, z0, y0, x, bar);
-        }
+        tma3(I + L::EP * IS, &mp.e, z0, y0, x, bar);
+        tma3(I + L::DE * IS, &mp.d, z0, y0, x, bar);
         if (GRAD) {
             tma3(I + L::UP * IS, &mp.up, z0, y0, x, bar);
             tma3(I + L::UR * IS, &mp.ur, z0, y0, x, bar);
@@ -859,19 +801,20 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
             }
             const float2 mm = lds2(I + L::MM * IS), p1 = lds2(I + L::PC * IS), r1 = lds2(I + L::RC * IS);
             const float2 p0 = lds2(I + L::PP * IS), r0 = lds2(I + L::RP * IS);
-            const float2 e_ = ADJ ? Z2 : lds2(I + L::EP * IS), d_ = ADJ ? Z2 : lds2(I + L::DE * IS);
+            const float2 e_ = lds2(I + L::EP * IS), d_ = lds2(I + L::DE * IS);
             const float sxv = __ldg(sx + x);
             const float h0[2] = {h0a * g.ih, h0b * g.ih}, hz[2] = {hza * g.ih, hzb * g.ih};
             const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
             const float P1[2] = {p1.x, p1.y}, R1[2] = {r1.x, r1.y}, P0[2] = {p0.x, p0.y}, R0[2] = {r0.x, r0.y};
             const float SYZ[2] = {syz0, syz1};
-            float pn[2], rn[2], Lp[2], Lr[2];
+            float pn[2], rn[2], Lp[2], Lr[2], c1[2], c2[2];
 #pragma unroll
             for (int i = 0; i < 2; i++) {
+                c1[i] = 1.f + 2.f * E2[i];
+                c2[i] = sqrtf(1.f + 2.f * D2[i]);
                 if (!ADJ) {
-                    const float a = 1.f + 2.f * E2[i], s2 = sqrtf(1.f + 2.f * D2[i]);
-                    Lp[i] = a * h0[i] + s2 * hz[i];
-                    Lr[i] = s2 * h0[i] + hz[i];
+                    Lp[i] = c1[i] * h0[i] + c2[i] * hz[i];
+                    Lr[i] = c2[i] * h0[i] + hz[i];
                 } else {
                     Lp[i] = h0[i];
                     Lr[i] = hz[i];
@@ -884,6 +827,10 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
             const unsigned q = x * pl + q0;
             st2(pp, q, pn[0], pn[1]);
             st2(rp, q, rn[0], rn[1]);
+            if (ADJ) {
+                st2(zp, q, c1[0] * pn[0] + c2[0] * rn[0], c1[1] * pn[1] + c2[1] * rn[1]);
+                st2(zr, q, c2[0] * pn[0] + rn[0], c2[1] * pn[1] + rn[1]);
+            }
             if (GRAD) {
                 const float2 u = lds2(I + L::UP * IS), v = lds2(I + L::UR * IS), gg = lds2(I + L::GG * IS);
                 st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
@@ -1073,33 +1020,32 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     const int xc = P->xchunk;
     dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
     float *const *t = P->tmp;
+    // the rotation pass differentiates (p, r), or zeta = C lam (tmp[6], tmp[7])
+    // in the transposed step
+    const float *rp_ = ADJ ? t[6] : S[0], *rr_ = ADJ ? t[7] : S[1];
     RMaps rm;
     UMaps um;
-    bool ok = map_of(P, S[0], B::RC, B::RR, &rm.p) && map_of(P, S[1], B::RC, B::RR, &rm.r) &&
-              map_of(P, S[0], FZ, FY, &rm.qp) && map_of(P, S[1], FZ, FY, &rm.qr) &&
+    bool ok = map_of(P, rp_, B::RC, B::RR, &rm.p) && map_of(P, rr_, B::RC, B::RR, &rm.r) &&
+              map_of(P, rp_, FZ, FY, &rm.qp) && map_of(P, rr_, FZ, FY, &rm.qr) &&
               map_of(P, P->nrm[0], FZ, FY, &rm.nx) && map_of(P, P->nrm[1], FZ, FY, &rm.ny) &&
               map_of(P, t[1], B::YC, B::YR, &um.ey) && map_of(P, t[4], B::YC, B::YR, &um.fy) &&
               map_of(P, t[2], B::ZC, B::ZR, &um.ez) && map_of(P, t[5], B::ZC, B::ZR, &um.fz) &&
               map_of(P, t[0], FZ, FY, &um.qe) && map_of(P, t[3], FZ, FY, &um.qf) &&
               map_of(P, P->m, FZ, FY, &um.m) && map_of(P, S[0], FZ, FY, &um.pc) &&
               map_of(P, S[1], FZ, FY, &um.rc) && map_of(P, S[2], FZ, FY, &um.pp) &&
-              map_of(P, S[3], FZ, FY, &um.rp);
-    if (ADJ)
-        ok = ok && map_of(P, P->eps, B::RC, B::RR, &rm.e) && map_of(P, P->del, B::RC, B::RR, &rm.d) &&
-             map_of(P, P->eps, FZ, FY, &rm.qe) && map_of(P, P->del, FZ, FY, &rm.qd);
-    else
-        ok = ok && map_of(P, P->eps, FZ, FY, &um.e) && map_of(P, P->del, FZ, FY, &um.d);
+              map_of(P, S[3], FZ, FY, &um.rp) && map_of(P, P->eps, FZ, FY, &um.e) &&
+              map_of(P, P->del, FZ, FY, &um.d);
     if (GRAD)
         ok = ok && map_of(P, up, FZ, FY, &um.up) && map_of(P, ur, FZ, FY, &um.ur) &&
              map_of(P, grad, FZ, FY, &um.g);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-    const size_t s1 = NSTAGE * RL<M, ADJ>::SZ * sizeof(float) + 64,
+    const size_t s1 = NSTAGE * RL<M>::SZ * sizeof(float) + 64,
                  s2 = NSTAGE * UL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
-    static const bool attr = set_smem(tti_rot_tma<M, ADJ>, s1) && set_smem(tti_upd_tma<M, ADJ, GRAD>, s2);
+    static const bool attr = set_smem(tti_rot_tma<M>, s1) && set_smem(tti_upd_tma<M, ADJ, GRAD>, s2);
     (void)attr;
-    tti_rot_tma<M, ADJ><<<grd, blk, s1, P->stream>>>(g, P->w, S[0], S[1], P->eps, P->del, rm, t[0], t[1],
-                                                    t[2], t[3], t[4], t[5], xc, P->flag);
-    tti_upd_tma<M, ADJ, GRAD><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, S[2], S[3], grad,
+    tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, rp_, rr_, rm, t[0], t[1], t[2], t[3], t[4], t[5], xc,
+                                               P->flag);
+    tti_upd_tma<M, ADJ, GRAD><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, S[2], S[3], grad, t[6], t[7],
                                                           P->flag, P->d.check_nan, xc, P->flag);
     P->kern_launches += 2;
     WP_CK(P, cudaGetLastError());
