@@ -312,6 +312,30 @@ def elastic_gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
     return {"nt": nt, "grid": [n + 2 * p0.nbl] * 3, "modes": res}
 
 
+def gradient_small(wp, torch, dev):
+    """Profiling case of the gradient paths: one elastic gradient (so 8,
+    160^3 + 20-cell layer = 200^3, 60 steps, full storage, shallow source)
+    and one TTI gradient (so 12, 240x240x200 + 40-cell layer = 320x320x280,
+    40 steps, full storage), observed data 1.1 x the predicted traces."""
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    out = {}
+    for key, p in (("elastic", synth.elastic_random(n=160, nt=60)),
+                   ("tti", synth.tti_layered(nx=240, ny=240, nz=200, nt=40))):
+        if key == "elastic":
+            p.src[:, 2] = 5 * p.h
+        prop = wp.Propagator.from_problem(p, stream=stream)
+        w, s_, r = to(p.wavelet), to(p.src), to(p.rec)
+        d = prop.forward(w, s_, r) * 1.1
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, J = prop.gradient(w, s_, r, d)
+        torch.cuda.synchronize()
+        out[key] = {"grid": list(prop.grid), "nt": p.nt, "seconds": time.perf_counter() - t0, "misfit": J}
+        prop.close()
+    return out
+
+
 def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
     """Batched TTI gradients (so 12, BF16 checkpoints): shots on windows of
     one large model with nx, ny ~ U[200, 600], nz = 300 (+ 40-cell layer);
@@ -364,7 +388,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--extra", default="", help="comma list: tti, grad, elgrad, batch (secondary measurements)")
+    ap.add_argument("--extra", default="", help="comma list: tti, grad, elgrad, gradsmall, batch (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--batch-shots", type=int, default=8)
     ap.add_argument("--batch-nt", type=int, default=150)
@@ -394,6 +418,8 @@ def main():
                 wp, torch, dev, args.grad_nt,
                 [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
                 small=args.small)
+        if "gradsmall" in extras:
+            out["gradsmall"] = gradient_small(wp, torch, dev)
         if "batch" in extras:
             out["batch"] = batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
                                                 small=args.small)
