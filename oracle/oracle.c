@@ -668,7 +668,8 @@ int or_tti_forward(or_prob *P, int nsrc, const float *src, const float *wav,
  *   a = 1 + sig dt/2, b = 1 - sig dt/2  (d/dm of A u^{n+1} - 2m u^n + B u^{n-1})
  * is added using the stored forward wavefields. */
 static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double *res,
-                            int nsrc, const float *src, double *qbar, double *grad)
+                            int nsrc, const float *src, double *qbar, double *grad,
+                            double *grad_e, double *grad_d)
 {
     int e1, e2;
     pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
@@ -705,6 +706,23 @@ static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double
                 grad[q] -= l0[q] * dp + s0[q] * dr;
             }
         }
+        if (grad_e && k >= 2) {
+            /* anisotropy: the step n = k-1 depends on eps, delta only through
+             * C in dt^2 C [H0 p^n; Hz r^n], with dC/deps = [[2, 0], [0, 0]] and
+             * dC/ddelta = [[0, s'], [s', 0]], s' = 1 / sqrt(1 + 2 delta), so
+             *   g_eps   += 2 dt^2 lam_p H0 p^n,
+             *   g_delta += dt^2 s' (lam_p Hz r^n + lam_r H0 p^n)
+             * (p^0 = r^0 = 0: no term for k = 1) */
+            const double *up1 = P->store + (long)(k - 1) * 2 * N, *ur1 = up1 + N;
+            double *H0 = dalloc(N), *Hz = dalloc(N);
+            tti_apply_H(P, up1, ur1, H0, Hz);
+#pragma omp parallel for
+            for (long q = 0; q < N; q++) {
+                grad_e[q] += 2.0 * dt * dt * l0[q] * H0[q];
+                grad_d[q] += dt * dt / sqrt(1.0 + 2.0 * P->del[q]) * (l0[q] * Hz[q] + s0[q] * H0[q]);
+            }
+            free(H0); free(Hz);
+        }
         double *t;
         t = l2; l2 = l1; l1 = l0; l0 = t;
         t = s2; s2 = s1; s1 = s0; s0 = t;
@@ -717,7 +735,7 @@ int or_tti_adjoint(or_prob *P, int nrec, const float *rec, const double *traces,
                    int nsrc, const float *src, double *qbar)
 {
     if (P->d.kind != 1) return OR_EINVAL;
-    return tti_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL);
+    return tti_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL, NULL, NULL);
 }
 
 /* FWI gradient w.r.t. m = 1/vp^2 on the PHYSICAL grid (fold of the
@@ -739,10 +757,38 @@ int or_tti_gradient(or_prob *P, int nsrc, const float *src, const float *wav,
     }
     if (misfit) *misfit = J;
     double *g = dalloc(P->N);
-    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g);
+    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, NULL, NULL);
     if (!rc) {
         if (grad_comp) memcpy(grad_comp, g, sizeof(double) * P->N);
         if (grad_phys) fold(g, grad_phys, P);
+    }
+    free(g); free(tr);
+    free(P->store); P->store = NULL; P->stored = 0;
+    return rc;
+}
+
+/* Gradient w.r.t. (m, epsilon, delta) on the physical grid:
+ * grad_phys [3][nx][ny][nz] (each folded through the edge replication). */
+int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *wav,
+                          int nrec, const float *rec, const double *d_obs,
+                          double *grad_phys, double *misfit)
+{
+    if (P->d.kind != 1) return OR_EINVAL;
+    int nt = P->d.nt;
+    double *tr = dalloc((long)nrec * nt);
+    int rc = or_tti_forward(P, nsrc, src, wav, nrec, rec, tr, 1);
+    if (rc) { free(tr); return rc; }
+    double J = 0.0;
+    for (long i = 0; i < (long)nrec * nt; i++) {
+        tr[i] -= d_obs[i];
+        J += 0.5 * tr[i] * tr[i];
+    }
+    if (misfit) *misfit = J;
+    double *g = dalloc(3 * P->N);
+    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, g + P->N, g + 2 * P->N);
+    if (!rc && grad_phys) {
+        const long np = (long)P->d.nx * P->d.ny * P->d.nz;
+        for (int c = 0; c < 3; c++) fold(g + c * P->N, grad_phys + c * np, P);
     }
     free(g); free(tr);
     free(P->store); P->store = NULL; P->stored = 0;
@@ -762,7 +808,7 @@ int or_tti_backward(or_prob *P, int nsrc, const float *src, const float *wav,
     free(tr);
     if (rc) return rc;
     double *g = dalloc(P->N);
-    rc = tti_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g);
+    rc = tti_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g, NULL, NULL);
     if (!rc && grad_phys) fold(g, grad_phys, P);
     free(g);
     free(P->store); P->store = NULL; P->stored = 0;

@@ -270,3 +270,42 @@ def test_taylor_gradient():
         e2.append(abs(Jh - J0 - hh * lin))
     slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
     assert all(abs(s - 2.0) < 0.1 for s in slopes), slopes
+
+
+@pytest.mark.parametrize("which", ["eps", "delta"])
+def test_taylor_gradient_anisotropy(which):
+    """Gradient w.r.t. epsilon and delta: the step depends on them only
+    through the coupling C of Sec. III-A (dC/deps = [[2, 0], [0, 0]],
+    dC/ddelta = [[0, s'], [s', 0]], s' = 1/sqrt(1 + 2 delta)).  Pinned by the
+    Taylor test (second-order remainder) along a smooth direction that keeps
+    eps >= delta; its m component equals the m-only gradient."""
+    p = _small_problem(so=4, nt=60)
+    p.vdamp = 2500.0 * math.sqrt(1.4)       # damping held fixed under perturbation
+    keys = ("vp", "eps", "delta", "theta", "phi")
+    dobs = oracle.Problem(p).forward()
+    base = dict(p.model)
+    base["eps"] = (base["eps"].astype(np.float64) + 0.02).astype(np.float32)   # off the data model
+    idx = {"eps": 1, "delta": 2}[which]
+    sign = 1.0 if which == "eps" else -1.0    # raise eps / lower delta: eps >= delta holds
+
+    def J_of(field):
+        mm = dict(base)
+        mm[which] = field.astype(np.float32)
+        o = oracle.Problem(p, model=[mm[k] for k in keys])
+        return 0.5 * np.sum((o.forward() - dobs) ** 2), o, mm
+
+    J0, o0, mm0 = J_of(base[which].astype(np.float64))
+    f0 = mm0[which].astype(np.float64)
+    g3, J = o0.gradient_aniso(dobs)
+    assert abs(J - J0) <= 1e-12 * J0
+    g_m, _ = oracle.Problem(p, model=[mm0[k] for k in keys]).gradient(dobs)
+    np.testing.assert_array_equal(g3[0], g_m)
+    d = sign * 0.05 * np.abs(synth.perturbation(f0.shape, 2, 9).astype(np.float64))
+    lin = float(np.sum(g3[idx] * d))
+    assert abs(lin) > 0
+    e2 = []
+    for hh in (1.0, 0.5, 0.25, 0.125, 0.0625):
+        Jh, _, _ = J_of(f0 + hh * d)
+        e2.append(abs(Jh - J0 - hh * lin))
+    slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
+    assert all(abs(s - 2.0) < 0.15 for s in slopes), slopes
