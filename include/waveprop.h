@@ -123,6 +123,22 @@ int prop_gradient(prop_t *p, const float *wavelet, const float *src_xyz, int nsr
                   const float *rec_xyz, int nrec, const float *d_obs, float *grad,
                   double *misfit);
 
+/* TTI only: the same gradient also with respect to the anisotropy
+ * parameters, from the same forward and adjoint sweeps.  The step depends on
+ * epsilon and delta only through the coupling matrix C of Sec. III-A, so
+ * with h^n = [H0 p^n; Hz r^n] of the forward field and lam^{n+1} the adjoint
+ * field of the same step:
+ *   dJ/deps   = sum_n 2 dt^2 lam_p^{n+1} H0 p^n,
+ *   dJ/ddelta = sum_n dt^2 (lam_p^{n+1} Hz r^n + lam_r^{n+1} H0 p^n) / sqrt(1 + 2 delta)
+ * (each folded onto the physical grid like dJ/dm).
+ *   grad  [3][nx][ny][nz]: dJ/dm, dJ/deps, dJ/ddelta.
+ * Costs one more application of H to the stored forward field per step.
+ * PROP_EINVAL for an elastic handle or a computational nz (nz + 2 nbl) that
+ * is not a multiple of 4 (the TMA-fed kernels it uses need 16-byte rows). */
+int prop_gradient_aniso(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,
+                        const float *rec_xyz, int nrec, const float *d_obs, float *grad,
+                        double *misfit);
+
 /* Two-phase form of prop_gradient for automatic differentiation:
  * prop_forward_saved runs prop_forward and keeps the forward wavefields
  * (snap_mode) in the handle; prop_backward then takes the trace gradient

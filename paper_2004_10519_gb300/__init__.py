@@ -28,7 +28,8 @@ ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_forward_saved", "prop_backward", "prop_grid_dims", "prop_set_state",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
                "prop_last_error", "prop_forward_noalloc", "prop_tile_planes",
-               "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves")
+               "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves",
+               "prop_gradient_aniso")
 
 
 class PropDesc(C.Structure):
@@ -63,6 +64,7 @@ def lib():
         L.prop_adjoint.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp]
         L.prop_gradient.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, C.POINTER(C.c_double)]
         L.prop_backward.argtypes = [vp, vp, vp, vp]
+        L.prop_gradient_aniso.argtypes = [vp, vp, vp, C.c_int, vp, C.c_int, vp, vp, C.POINTER(C.c_double)]
         L.prop_grid_dims.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.prop_set_state.argtypes = [vp, fpp]
         L.prop_get_state.argtypes = [vp, fpp]
@@ -242,6 +244,22 @@ class Propagator:
         J = C.c_double()
         self._check(lib().prop_gradient(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, d.ptr,
                                         o.ptr, C.byref(J)))
+        return out, J.value
+
+    def gradient_aniso(self, wavelet, src, rec, d_obs, out=None):
+        """TTI: gradient w.r.t. (m, epsilon, delta), shape [3][nx][ny][nz], and
+        the misfit (``prop_gradient_aniso``)."""
+        src_a, rec_a = _Arg(src), _Arg(rec)
+        nsrc, nrec = _npts(src_a), _npts(rec_a)
+        w = _Arg(wavelet, nsrc * self.nt)
+        d = _Arg(d_obs, nrec * self.nt)
+        shape = (3,) + self.shape
+        if out is None:
+            out = self._out(d_obs, shape)
+        o = _Arg(out, int(np.prod(shape)), writable=True)
+        J = C.c_double()
+        self._check(lib().prop_gradient_aniso(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, d.ptr,
+                                              o.ptr, C.byref(J)))
         return out, J.value
 
     def backward(self, resid, grad_out=True, src_grad_out=True, nsrc=None):

@@ -71,6 +71,7 @@ struct prop_s {
     int xchunk = 8;          // planes per CTA of the x-streaming stencil kernels
     // saved forward run for prop_backward
     bool saved = false;
+    bool aniso = false;      // TTI gradient also w.r.t. eps, delta (prop_gradient_aniso)
     int saved_nsrc = 0, saved_nrec = 0;
     std::vector<float> saved_src, saved_rec, saved_wav;   // host copies of geometry/wavelet
     // snapshot storage
@@ -113,6 +114,11 @@ int el_launch_fast(prop_s *P, float *const *S, float dt_sign);
 // TMA-fed passes (stencil_tma.cu): usable when NZ % 4 == 0
 bool tma_usable(const prop_s *P);
 int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
+// TTI imaging of the coupling matrix (TMA passes): with the forward field
+// (up, ur) at level n and the adjoint field (lp, lr) at level n+1,
+// ge += 2 dt^2 lam_p H0 p^n, gd += dt^2 (lam_p Hz r^n + lam_r H0 p^n) / sqrt(1+2 delta)
+int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
+                        float *ge, float *gd);
 // TMA passes of a transposed elastic step with imaging: on entry S[3..8] hold
 // t = g tbar and sig[0..5] = C t; updates vbar (S[0..2]), writes b_avg vbar to
 // w[0..2], accumulates g_lambda, g_mu (gr[0], gr[1]) and the edge products

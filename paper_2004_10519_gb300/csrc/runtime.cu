@@ -675,7 +675,9 @@ static int alloc_saves(prop_s *P)
         break;
     }
     if (P->d.snap_mode != SNAP_FULL_FP32) {
-        const size_t slots = P->d.kind == PROP_TTI ? (size_t)K : (size_t)K + 1;
+        // TTI: levels n0+1 .. n0+K of a segment and (slot K) the checkpoint
+        // level n0 itself (eps/delta imaging); elastic: levels n0 .. n0+K
+        const size_t slots = (size_t)K + 1;
         P->seg_bytes = slots * snap_fields(P) * N * sizeof(float);
         WP_MALLOC(P, P->seg, P->seg_bytes, "recompute segment buffer");
     }
@@ -873,8 +875,11 @@ static void sample_src(prop_s *P, const Geometry &G, float *const *a, float *col
 
 // TTI adjoint sweep.  grad != NULL: imaging with forward wavefields.
 static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float *wav,
-                     float *srcstage, float *grad)
+                     float *srcstage, float *const *g3)
 {
+    // g3: NULL (adjoint modelling), {dJ/dm} or, with P->aniso, {dJ/dm, dJ/deps, dJ/ddelta}
+    float *grad = g3 ? g3[0] : nullptr;
+    const bool aniso = g3 && P->aniso;
     const int nt = P->d.nt;
     const size_t N = (size_t)P->g.N;
     WP_TRY(ensure_ast(P));
@@ -891,6 +896,12 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
         prof_maybe_collect(P);
         return PROP_OK;
     };
+    // eps/delta imaging: lam^k (a[0], a[1] after the step and the residual)
+    // with the forward level k-1 (level 0 is zero: no term for k = 1)
+    auto aniso_iter = [&](int k, const float *u1) -> int {
+        if (!aniso || k < 2) return PROP_OK;
+        return tti_image_aniso_tma(P, u1, u1 + N, a[0], a[1], g3[1], g3[2]);
+    };
     if (!grad) {
         for (int k = nt - 1; k >= 1; k--) WP_TRY(adj_iter(k, nullptr, nullptr));
         return PROP_OK;
@@ -899,6 +910,7 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
         for (int k = nt - 1; k >= 1; k--) {
             const float *u = snap_slot(P, k - 1);
             WP_TRY(adj_iter(k, u, u + N));
+            if (k >= 2) WP_TRY(aniso_iter(k, snap_slot(P, k - 2)));
         }
         return PROP_OK;
     }
@@ -910,6 +922,10 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
         float *f[4] = {P->st[0], P->st[1], P->st[2], P->st[3]};
         for (int i = 0; i < 4; i++) s[i] = f[i];
         WP_TRY(load_checkpoint(P, j, s));
+        if (aniso) {                            // level n0 into the extra slot K
+            WP_CK(P, cudaMemcpyAsync(seg_slot(P, K), s[0], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+            WP_CK(P, cudaMemcpyAsync(seg_slot(P, K) + N, s[1], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        }
         for (int n = n0; n < E; n++) {
             WP_TRY(fwd_step(P, s, G.S, wav, n));
             float *d = seg_slot(P, n - n0);     // level n+1
@@ -919,6 +935,7 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
         for (int k = E; k >= n0 + 1; k--) {
             const float *u = seg_slot(P, k - n0 - 1);
             WP_TRY(adj_iter(k, u, u + N));
+            WP_TRY(aniso_iter(k, k - 1 > n0 ? seg_slot(P, k - n0 - 2) : seg_slot(P, K)));
         }
     }
     return PROP_OK;
@@ -1035,7 +1052,7 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
         WP_TRY(wp_malloc(P, &stage.p, sizeof(float) * (size_t)nt * nsrc, "source staging"));
         WP_TRY(wp_malloc(P, &out.p, sizeof(float) * (size_t)nt * nsrc, "source output"));
     }
-    const int ng = P->d.kind == PROP_TTI ? 1 : 3;
+    const int ng = P->d.kind == PROP_TTI ? (P->aniso ? 3 : 1) : 3;
     const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
     float *g3[3] = {};
     if (grad) {
@@ -1045,7 +1062,7 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
         WP_TRY(wp_malloc(P, &gphys.p, sizeof(float) * np * ng, "gradient (physical)"));
     }
     if (P->d.kind == PROP_TTI)
-        WP_TRY(tti_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3[0] : nullptr));
+        WP_TRY(tti_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3 : nullptr));
     else
         WP_TRY(el_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3 : nullptr));
     if (src_grad) {
@@ -1069,6 +1086,20 @@ extern "C" int prop_backward(prop_t *P, const float *resid, float *grad, float *
     return rc;
 }
 
+extern "C" int prop_gradient_aniso(prop_t *P, const float *wavelet, const float *src_xyz, int nsrc,
+                                   const float *rec_xyz, int nrec, const float *d_obs, float *grad,
+                                   double *misfit)
+{
+    WP_TRY(check_handle(P));
+    if (P->d.kind != PROP_TTI) return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso is for TTI propagators");
+    if (!tma_usable(P))
+        return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso needs a computational nz that is a multiple of 4");
+    P->aniso = true;
+    const int rc = prop_gradient(P, wavelet, src_xyz, nsrc, rec_xyz, nrec, d_obs, grad, misfit);
+    P->aniso = false;
+    return rc;
+}
+
 // device bytes one prop_gradient call allocates on top of what the handle
 // already holds (wavefield storage or checkpoints + recompute segment,
 // adjoint state, scratch fields, gradient buffers, traces)
@@ -1085,7 +1116,7 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
     default: b += (size_t)J * cf * N * 2 + 4 * ((size_t)J * cf + 1024); break;
     }
     if (P->d.snap_mode != SNAP_FULL_FP32)
-        b += (P->d.kind == PROP_TTI ? (size_t)K : (size_t)K + 1) * snap_fields(P) * N * 4;
+        b += ((size_t)K + 1) * snap_fields(P) * N * 4;
     for (int i = 0; i < cf; i++)
         if (!P->ast[i]) b += N * 4;
     const int ntmp = P->d.kind == PROP_TTI ? 8 : 15;

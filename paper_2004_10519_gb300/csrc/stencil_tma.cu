@@ -683,8 +683,13 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
 }
 
 // ---------------------------------------------------------------------------
-// TTI update pass.  ADJ: the transposed step, which also writes
+// TTI update pass.  ADJ = 1: the transposed step, which also writes
 // zeta = C lam of the new level (zp, zr) for the next rotation pass.
+// ADJ = 2: no step; imaging of the coupling C with the forward field whose
+// rotated intermediates were just formed: with h = [H0 p^n; Hz r^n] and
+// lam = lam^{n+1} (pc, rc), g_eps (grad) += 2 dt^2 lam_p H0 p^n and
+// g_delta (zp) += dt^2 (lam_p Hz r^n + lam_r H0 p^n) / sqrt(1 + 2 delta)
+// (dC/deps = [[2, 0], [0, 0]], dC/ddelta = [[0, s'], [s', 0]]).
 // stage: [e_y y box] [f_y y box] [e_z z box] [f_z z box] [queue heads e_x,
 //        f_x (x+M)] [m, p^n, r^n, p^{n-1}, r^{n-1}, eps, del (plane x)]
 //        (+ [u_p, u_r, g] imaging)
@@ -692,12 +697,13 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
 template <int M, int ADJ, int GRAD>
 struct UL {
     using B = BX<M>;
-    static constexpr int NI = 9 + (GRAD ? 3 : 0);
+    static constexpr bool IMG = ADJ == 2;
+    static constexpr int NI = IMG ? 7 : 9 + (GRAD ? 3 : 0);
     static constexpr int OEY = 0, OFY = B::YS, OEZ = 2 * B::YS, OFZ = OEZ + B::ZS, OI = OFZ + B::ZS,
                          SZ = OI + NI * IS;
-    // interior slots
-    static constexpr int QE = 0, QF = 1, MM = 2, PC = 3, RC = 4, PP = 5, RP = 6, EP = 7, DE = 8,
-                         UP = 9, UR = UP + 1, GG = UP + 2;
+    // interior slots (ADJ = 2: lam_p, lam_r in PC, RC; g_eps, g_delta in UP, UR)
+    static constexpr int QE = 0, QF = 1, MM = 2, PC = IMG ? 2 : 3, RC = PC + 1, PP = 5, RP = 6, EP = 7,
+                         DE = IMG ? 4 : 8, UP = IMG ? 5 : 9, UR = UP + 1, GG = UP + 2;
     static constexpr uint32_t BYTES = 4u * (2 * B::YR * B::YC + 2 * B::ZR * B::ZC + NI * IS);
 };
 
@@ -733,17 +739,22 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
         tma3(S + L::OFZ, &mp.fz, z0 - B::MZ, y0, x, bar);
         tma3(I + L::QE * IS, &mp.qe, z0, y0, x + M, bar);             // beyond NX: zeros
         tma3(I + L::QF * IS, &mp.qf, z0, y0, x + M, bar);
-        tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
         tma3(I + L::PC * IS, &mp.pc, z0, y0, x, bar);
         tma3(I + L::RC * IS, &mp.rc, z0, y0, x, bar);
-        tma3(I + L::PP * IS, &mp.pp, z0, y0, x, bar);
-        tma3(I + L::RP * IS, &mp.rp, z0, y0, x, bar);
-        tma3(I + L::EP * IS, &mp.e, z0, y0, x, bar);
         tma3(I + L::DE * IS, &mp.d, z0, y0, x, bar);
-        if (GRAD) {
+        if (L::IMG) {
             tma3(I + L::UP * IS, &mp.up, z0, y0, x, bar);
             tma3(I + L::UR * IS, &mp.ur, z0, y0, x, bar);
-            tma3(I + L::GG * IS, &mp.g, z0, y0, x, bar);
+        } else {
+            tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
+            tma3(I + L::PP * IS, &mp.pp, z0, y0, x, bar);
+            tma3(I + L::RP * IS, &mp.rp, z0, y0, x, bar);
+            tma3(I + L::EP * IS, &mp.e, z0, y0, x, bar);
+            if (GRAD) {
+                tma3(I + L::UP * IS, &mp.up, z0, y0, x, bar);
+                tma3(I + L::UR * IS, &mp.ur, z0, y0, x, bar);
+                tma3(I + L::GG * IS, &mp.g, z0, y0, x, bar);
+            }
         }
     };
     Ring R(bars);
@@ -799,45 +810,54 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
                 hza += c * (fx_.x + fy_.x + (wf[M + k] - wf[M - k]));
                 hzb += c * (fx_.y + fy_.y + (wf[M + k + 1] - wf[M - k + 1]));
             }
-            const float2 mm = lds2(I + L::MM * IS), p1 = lds2(I + L::PC * IS), r1 = lds2(I + L::RC * IS);
-            const float2 p0 = lds2(I + L::PP * IS), r0 = lds2(I + L::RP * IS);
-            const float2 e_ = lds2(I + L::EP * IS), d_ = lds2(I + L::DE * IS);
-            const float sxv = __ldg(sx + x);
-            const float h0[2] = {h0a * g.ih, h0b * g.ih}, hz[2] = {hza * g.ih, hzb * g.ih};
-            const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
-            const float P1[2] = {p1.x, p1.y}, R1[2] = {r1.x, r1.y}, P0[2] = {p0.x, p0.y}, R0[2] = {r0.x, r0.y};
-            const float SYZ[2] = {syz0, syz1};
-            float pn[2], rn[2], Lp[2], Lr[2], c1[2], c2[2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                c1[i] = 1.f + 2.f * E2[i];
-                c2[i] = sqrtf(1.f + 2.f * D2[i]);
-                if (!ADJ) {
-                    Lp[i] = c1[i] * h0[i] + c2[i] * hz[i];
-                    Lr[i] = c2[i] * h0[i] + hz[i];
-                } else {
-                    Lp[i] = h0[i];
-                    Lr[i] = hz[i];
-                }
-                const float sd = hdt * (sxv + SYZ[i]);
-                const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
-                pn[i] = (dt2 * Lp[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
-                rn[i] = (dt2 * Lr[i] + 2.f * M2[i] * R1[i] - Bc * R0[i]) / A;
-            }
             const unsigned q = x * pl + q0;
-            st2(pp, q, pn[0], pn[1]);
-            st2(rp, q, rn[0], rn[1]);
-            if (ADJ) {
-                st2(zp, q, c1[0] * pn[0] + c2[0] * rn[0], c1[1] * pn[1] + c2[1] * rn[1]);
-                st2(zr, q, c2[0] * pn[0] + rn[0], c2[1] * pn[1] + rn[1]);
+            if (L::IMG) {
+                const float2 lp = lds2(I + L::PC * IS), lr = lds2(I + L::RC * IS), d_ = lds2(I + L::DE * IS);
+                const float2 ge = lds2(I + L::UP * IS), gd = lds2(I + L::UR * IS);
+                const float h0a_ = h0a * g.ih, h0b_ = h0b * g.ih, hza_ = hza * g.ih, hzb_ = hzb * g.ih;
+                st2(grad, q, ge.x + 2.f * dt2 * lp.x * h0a_, ge.y + 2.f * dt2 * lp.y * h0b_);
+                st2(zp, q, gd.x + dt2 * (lp.x * hza_ + lr.x * h0a_) / sqrtf(1.f + 2.f * d_.x),
+                    gd.y + dt2 * (lp.y * hzb_ + lr.y * h0b_) / sqrtf(1.f + 2.f * d_.y));
+            } else {
+                const float2 mm = lds2(I + L::MM * IS), p1 = lds2(I + L::PC * IS), r1 = lds2(I + L::RC * IS);
+                const float2 p0 = lds2(I + L::PP * IS), r0 = lds2(I + L::RP * IS);
+                const float2 e_ = lds2(I + L::EP * IS), d_ = lds2(I + L::DE * IS);
+                const float sxv = __ldg(sx + x);
+                const float h0[2] = {h0a * g.ih, h0b * g.ih}, hz[2] = {hza * g.ih, hzb * g.ih};
+                const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
+                const float P1[2] = {p1.x, p1.y}, R1[2] = {r1.x, r1.y}, P0[2] = {p0.x, p0.y}, R0[2] = {r0.x, r0.y};
+                const float SYZ[2] = {syz0, syz1};
+                float pn[2], rn[2], Lp[2], Lr[2], c1[2], c2[2];
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    c1[i] = 1.f + 2.f * E2[i];
+                    c2[i] = sqrtf(1.f + 2.f * D2[i]);
+                    if (!ADJ) {
+                        Lp[i] = c1[i] * h0[i] + c2[i] * hz[i];
+                        Lr[i] = c2[i] * h0[i] + hz[i];
+                    } else {
+                        Lp[i] = h0[i];
+                        Lr[i] = hz[i];
+                    }
+                    const float sd = hdt * (sxv + SYZ[i]);
+                    const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
+                    pn[i] = (dt2 * Lp[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
+                    rn[i] = (dt2 * Lr[i] + 2.f * M2[i] * R1[i] - Bc * R0[i]) / A;
+                }
+                st2(pp, q, pn[0], pn[1]);
+                st2(rp, q, rn[0], rn[1]);
+                if (ADJ) {
+                    st2(zp, q, c1[0] * pn[0] + c2[0] * rn[0], c1[1] * pn[1] + c2[1] * rn[1]);
+                    st2(zr, q, c2[0] * pn[0] + rn[0], c2[1] * pn[1] + rn[1]);
+                }
+                if (GRAD) {
+                    const float2 u = lds2(I + L::UP * IS), v = lds2(I + L::UR * IS), gg = lds2(I + L::GG * IS);
+                    st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
+                        gg.y - dt2 * (u.y * Lp[1] + v.y * Lr[1]) / M2[1]);
+                }
+                if (check && !(isfinite(pn[0]) && isfinite(rn[0]) && isfinite(pn[1]) && isfinite(rn[1])))
+                    atomicOr(flag, 1);
             }
-            if (GRAD) {
-                const float2 u = lds2(I + L::UP * IS), v = lds2(I + L::UR * IS), gg = lds2(I + L::GG * IS);
-                st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
-                    gg.y - dt2 * (u.y * Lp[1] + v.y * Lr[1]) / M2[1]);
-            }
-            if (check && !(isfinite(pn[0]) && isfinite(rn[0]) && isfinite(pn[1]) && isfinite(rn[1])))
-                atomicOr(flag, 1);
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -1052,6 +1072,41 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     return PROP_OK;
 }
 
+// imaging of the coupling matrix (eps, delta gradients) with the forward
+// field (up, ur) at level n and the adjoint field (lp, lr) at level n+1:
+// rotation pass on the forward field, then the update pass in mode 2
+template <int M>
+int tti_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr, float *ge,
+                    float *gd)
+{
+    using B = BX<M>;
+    const GridDev &g = P->g;
+    const int xc = P->xchunk;
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    float *const *t = P->tmp;
+    RMaps rm;
+    UMaps um;
+    bool ok = map_of(P, up, B::RC, B::RR, &rm.p) && map_of(P, ur, B::RC, B::RR, &rm.r) &&
+              map_of(P, up, FZ, FY, &rm.qp) && map_of(P, ur, FZ, FY, &rm.qr) &&
+              map_of(P, P->nrm[0], FZ, FY, &rm.nx) && map_of(P, P->nrm[1], FZ, FY, &rm.ny) &&
+              map_of(P, t[1], B::YC, B::YR, &um.ey) && map_of(P, t[4], B::YC, B::YR, &um.fy) &&
+              map_of(P, t[2], B::ZC, B::ZR, &um.ez) && map_of(P, t[5], B::ZC, B::ZR, &um.fz) &&
+              map_of(P, t[0], FZ, FY, &um.qe) && map_of(P, t[3], FZ, FY, &um.qf) &&
+              map_of(P, lp, FZ, FY, &um.pc) && map_of(P, lr, FZ, FY, &um.rc) &&
+              map_of(P, P->del, FZ, FY, &um.d) && map_of(P, ge, FZ, FY, &um.up) && map_of(P, gd, FZ, FY, &um.ur);
+    if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+    const size_t s1 = NSTAGE * RL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * UL<M, 2, 0>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_rot_tma<M>, s1) && set_smem(tti_upd_tma<M, 2, 0>, s2);
+    (void)attr;
+    tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[0], t[1], t[2], t[3], t[4], t[5], xc,
+                                               P->flag);
+    tti_upd_tma<M, 2, 0><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, nullptr, nullptr, ge, gd, nullptr,
+                                                     P->flag, 0, xc, P->flag);
+    P->kern_launches += 2;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 template <int M>
 int tti_launch_any(prop_s *P, float *const *S, bool adjoint, const float *up, const float *ur, float *grad)
 {
@@ -1084,6 +1139,19 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
     }
     prof_end(P, dt_sign > 0 ? 2 : 5);
     return rc;
+}
+
+// eps, delta imaging of one transposed TTI step (see tti_image_aniso)
+int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
+                        float *ge, float *gd)
+{
+    switch (P->M) {
+    case 2: return tti_image_aniso<2>(P, up, ur, lp, lr, ge, gd);
+    case 4: return tti_image_aniso<4>(P, up, ur, lp, lr, ge, gd);
+    case 6: return tti_image_aniso<6>(P, up, ur, lp, lr, ge, gd);
+    case 8: return tti_image_aniso<8>(P, up, ur, lp, lr, ge, gd);
+    }
+    return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
 
 // the TMA passes of one transposed elastic step with imaging (see el_adj_grad)

@@ -122,6 +122,34 @@ def test_gradient_parity_and_checkpoint_modes(wp, shape):
     assert rel(res[wp.SNAP_CKPT_FP16][0], g_ref) <= 2e-3
 
 
+def test_gradient_aniso_parity(wp):
+    """dJ/d(m, eps, delta) (prop_gradient_aniso) against the oracle, full
+    storage and FP32 checkpoints (bitwise equal to each other); the m
+    component equals prop_gradient's."""
+    p, p0, d_obs = grad_problem(shape=(30, 26, 36))
+    g_ref, J_ref = oracle.Problem(p0).gradient_aniso(d_obs)
+    d32 = d_obs.astype(np.float32)
+    res = {}
+    for mode in (wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32):
+        prop = wp.Propagator.from_problem(p0, snap_mode=mode, ckpt_interval=9)
+        res[mode] = prop.gradient_aniso(p0.wavelet, p0.src, p0.rec, d32)
+        g_m, _ = prop.gradient(p0.wavelet, p0.src, p0.rec, d32)
+        np.testing.assert_array_equal(res[mode][0][0], g_m)
+        prop.close()
+    g, J = res[wp.SNAP_FULL_FP32]
+    assert abs(J - J_ref) <= 1e-5 * J_ref
+    for c in range(3):
+        assert rel(g[c], g_ref[c]) <= 1e-4, c
+    np.testing.assert_array_equal(res[wp.SNAP_CKPT_FP32][0], g)
+    # computational nz not a multiple of 4: rejected, handle stays usable
+    q, q0, d2 = grad_problem(shape=(30, 26, 34))
+    prop = wp.Propagator.from_problem(q0)
+    with pytest.raises(wp.PropError) as e:
+        prop.gradient_aniso(q0.wavelet, q0.src, q0.rec, d2.astype(np.float32))
+    assert e.value.code == wp.PROP_EINVAL
+    prop.gradient(q0.wavelet, q0.src, q0.rec, d2.astype(np.float32))
+
+
 def test_backward_matches_oracle(wp):
     """prop_forward_saved + prop_backward (autograd form): gradient w.r.t. m
     and w.r.t. the wavelet for an arbitrary trace cotangent."""
