@@ -234,11 +234,11 @@ class Problem:
         return g, J.value
 
     def gradient_aniso(self, d_obs, wavelet=None, src=None, rec=None):
-        """TTI only: gradient w.r.t. (m, epsilon, delta) on the physical grid,
-        shape [3][nx][ny][nz], and the misfit."""
+        """TTI only: gradient w.r.t. (m, epsilon, delta, theta, phi) on the
+        physical grid, shape [5][nx][ny][nz], and the misfit."""
         src, rec, wav = self._geom(src, rec, wavelet)
         p = self.prob
-        g = np.zeros((3, p.nx, p.ny, p.nz))
+        g = np.zeros((5, p.nx, p.ny, p.nz))
         J = C.c_double(0.0)
         rc = lib().or_tti_gradient_aniso(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0],
                                          _fp(rec), _dp(_d(d_obs)), _dp(g), C.byref(J))

@@ -549,6 +549,60 @@ static void tti_apply_H(const or_prob *P, const double *p, const double *r,
     }
 }
 
+/* Derivatives of the frame of Eq. (rot) with respect to theta and phi. */
+static void frame_dth(double th, double ph, double *xb, double *yb, double *zb)
+{
+    xb[0] = -sin(th) * cos(ph); xb[1] = -sin(th) * sin(ph); xb[2] = -cos(th);
+    yb[0] = 0.0;                yb[1] = 0.0;                yb[2] = 0.0;
+    zb[0] = cos(th) * cos(ph);  zb[1] = cos(th) * sin(ph);  zb[2] = -sin(th);
+}
+static void frame_dph(double th, double ph, double *xb, double *yb, double *zb)
+{
+    xb[0] = -cos(th) * sin(ph); xb[1] = cos(th) * cos(ph);  xb[2] = 0.0;
+    yb[0] = -cos(ph);           yb[1] = -sin(ph);           yb[2] = 0.0;
+    zb[0] = -sin(th) * sin(ph); zb[1] = sin(th) * cos(ph);  zb[2] = 0.0;
+}
+static inline double dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
+
+/* Tilt/azimuth imaging of one step: with the bilinear forms
+ *   <zp, H0 p> = -sum_{a = xb, yb} <D_a zp, D_a p>,  <zr, Hz r> = -<D_zb zr, D_zb r>
+ * (D_a u = sum_i a_i D_i u at each point), the derivative with respect to the
+ * angle t at point q is
+ *   -sum_{a = xb, yb} [(a_t . D zp)(a . D p) + (a . D zp)(a_t . D p)]
+ *   - [(zb_t . D zr)(zb . D r) + (zb . D zr)(zb_t . D r)],
+ * all at q; scaled by `scale` and added to gt (t = theta) and gf (t = phi). */
+static void tti_frame_image(const or_prob *P, const double *zp, const double *zr, const double *p,
+                            const double *r, double scale, double *gt, double *gf)
+{
+    long N = P->N;
+    double *Gz[3], *Gr[3], *gp[3], *gr[3];
+    for (int i = 0; i < 3; i++) {
+        Gz[i] = dalloc(N); Gr[i] = dalloc(N); gp[i] = dalloc(N); gr[i] = dalloc(N);
+        apply_axis(line_D, zp, Gz[i], i, P);
+        apply_axis(line_D, zr, Gr[i], i, P);
+        apply_axis(line_D, p, gp[i], i, P);
+        apply_axis(line_D, r, gr[i], i, P);
+    }
+#pragma omp parallel for
+    for (long q = 0; q < N; q++) {
+        double xb[3], yb[3], zb[3], A[3], B[3], C3[3], U[3], V[3], W[3];
+        double a[3] = {Gz[0][q], Gz[1][q], Gz[2][q]}, b[3] = {gp[0][q], gp[1][q], gp[2][q]};
+        double c[3] = {Gr[0][q], Gr[1][q], Gr[2][q]}, d[3] = {gr[0][q], gr[1][q], gr[2][q]};
+        frame(P->th[q], P->ph[q], xb, yb, zb);
+        frame_dth(P->th[q], P->ph[q], A, B, C3);
+        frame_dph(P->th[q], P->ph[q], U, V, W);
+        double t = -(dot3(A, a) * dot3(xb, b) + dot3(xb, a) * dot3(A, b))
+                   - (dot3(B, a) * dot3(yb, b) + dot3(yb, a) * dot3(B, b))
+                   - (dot3(C3, c) * dot3(zb, d) + dot3(zb, c) * dot3(C3, d));
+        double f = -(dot3(U, a) * dot3(xb, b) + dot3(xb, a) * dot3(U, b))
+                   - (dot3(V, a) * dot3(yb, b) + dot3(yb, a) * dot3(V, b))
+                   - (dot3(W, c) * dot3(zb, d) + dot3(zb, c) * dot3(W, d));
+        gt[q] += scale * t;
+        gf[q] += scale * f;
+    }
+    for (int i = 0; i < 3; i++) { free(Gz[i]); free(Gr[i]); free(gp[i]); free(gr[i]); }
+}
+
 /* exported for the plane-wave dispersion pin: L u = C [H0 p; Hz r] */
 void or_tti_apply_L(const or_prob *P, const double *p, const double *r, double *Lp, double *Lr)
 {
@@ -669,7 +723,7 @@ int or_tti_forward(or_prob *P, int nsrc, const float *src, const float *wav,
  * is added using the stored forward wavefields. */
 static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double *res,
                             int nsrc, const float *src, double *qbar, double *grad,
-                            double *grad_e, double *grad_d)
+                            double *grad_e, double *grad_d, double *grad_t, double *grad_f)
 {
     int e1, e2;
     pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
@@ -723,6 +777,20 @@ static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double
             }
             free(H0); free(Hz);
         }
+        if (grad_t && k >= 2) {
+            /* tilt and azimuth: the step n = k-1 depends on theta, phi only
+             * through H in dt^2 C H u^n, so the term is dt^2 (C lam)^T dH/dt u^n */
+            const double *up1 = P->store + (long)(k - 1) * 2 * N, *ur1 = up1 + N;
+            double *zp = dalloc(N), *zr = dalloc(N);
+#pragma omp parallel for
+            for (long q = 0; q < N; q++) {
+                double a = 1.0 + 2.0 * P->eps[q], s = sqrt(1.0 + 2.0 * P->del[q]);
+                zp[q] = a * l0[q] + s * s0[q];
+                zr[q] = s * l0[q] + s0[q];
+            }
+            tti_frame_image(P, zp, zr, up1, ur1, dt * dt, grad_t, grad_f);
+            free(zp); free(zr);
+        }
         double *t;
         t = l2; l2 = l1; l1 = l0; l0 = t;
         t = s2; s2 = s1; s1 = s0; s0 = t;
@@ -735,7 +803,7 @@ int or_tti_adjoint(or_prob *P, int nrec, const float *rec, const double *traces,
                    int nsrc, const float *src, double *qbar)
 {
     if (P->d.kind != 1) return OR_EINVAL;
-    return tti_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL, NULL, NULL);
+    return tti_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* FWI gradient w.r.t. m = 1/vp^2 on the PHYSICAL grid (fold of the
@@ -757,7 +825,7 @@ int or_tti_gradient(or_prob *P, int nsrc, const float *src, const float *wav,
     }
     if (misfit) *misfit = J;
     double *g = dalloc(P->N);
-    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, NULL, NULL);
+    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, NULL, NULL, NULL, NULL);
     if (!rc) {
         if (grad_comp) memcpy(grad_comp, g, sizeof(double) * P->N);
         if (grad_phys) fold(g, grad_phys, P);
@@ -767,8 +835,8 @@ int or_tti_gradient(or_prob *P, int nsrc, const float *src, const float *wav,
     return rc;
 }
 
-/* Gradient w.r.t. (m, epsilon, delta) on the physical grid:
- * grad_phys [3][nx][ny][nz] (each folded through the edge replication). */
+/* Gradient w.r.t. (m, epsilon, delta, theta, phi) on the physical grid:
+ * grad_phys [5][nx][ny][nz] (each folded through the edge replication). */
 int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *wav,
                           int nrec, const float *rec, const double *d_obs,
                           double *grad_phys, double *misfit)
@@ -784,11 +852,12 @@ int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *w
         J += 0.5 * tr[i] * tr[i];
     }
     if (misfit) *misfit = J;
-    double *g = dalloc(3 * P->N);
-    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, g + P->N, g + 2 * P->N);
+    double *g = dalloc(5 * P->N);
+    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, g + P->N, g + 2 * P->N, g + 3 * P->N,
+                          g + 4 * P->N);
     if (!rc && grad_phys) {
         const long np = (long)P->d.nx * P->d.ny * P->d.nz;
-        for (int c = 0; c < 3; c++) fold(g + c * P->N, grad_phys + c * np, P);
+        for (int c = 0; c < 5; c++) fold(g + c * P->N, grad_phys + c * np, P);
     }
     free(g); free(tr);
     free(P->store); P->store = NULL; P->stored = 0;
@@ -808,7 +877,7 @@ int or_tti_backward(or_prob *P, int nsrc, const float *src, const float *wav,
     free(tr);
     if (rc) return rc;
     double *g = dalloc(P->N);
-    rc = tti_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g, NULL, NULL);
+    rc = tti_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g, NULL, NULL, NULL, NULL);
     if (!rc && grad_phys) fold(g, grad_phys, P);
     free(g);
     free(P->store); P->store = NULL; P->stored = 0;

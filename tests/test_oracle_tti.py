@@ -309,3 +309,58 @@ def test_taylor_gradient_anisotropy(which):
         e2.append(abs(Jh - J0 - hh * lin))
     slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
     assert all(abs(s - 2.0) < 0.15 for s in slopes), slopes
+
+
+@pytest.mark.parametrize("which", ["theta", "phi"])
+def test_taylor_gradient_tilt_azimuth(which):
+    """Gradient w.r.t. the tilt and azimuth of the symmetry axis (Eq. rot):
+    the step depends on them only through the frame inside H0 and Hz.
+    Pinned by the Taylor test (second-order remainder) along a smooth
+    direction; the other components equal those of the (m, eps, delta)
+    gradient computed without them."""
+    p = _small_problem(so=4, nt=60)
+    p.vdamp = 2500.0 * math.sqrt(1.4)
+    keys = ("vp", "eps", "delta", "theta", "phi")
+    dobs = oracle.Problem(p).forward()
+    base = dict(p.model)
+    base["theta"] = (base["theta"].astype(np.float64) + 0.15).astype(np.float32)   # off the data model
+    idx = {"theta": 3, "phi": 4}[which]
+
+    def J_of(field):
+        mm = dict(base)
+        mm[which] = field.astype(np.float32)
+        o = oracle.Problem(p, model=[mm[k] for k in keys])
+        return 0.5 * np.sum((o.forward() - dobs) ** 2), o, mm
+
+    J0, o0, mm0 = J_of(base[which].astype(np.float64))
+    f0 = mm0[which].astype(np.float64)
+    g5, J = o0.gradient_aniso(dobs)
+    assert abs(J - J0) <= 1e-12 * J0
+    g_m, _ = oracle.Problem(p, model=[mm0[k] for k in keys]).gradient(dobs)
+    np.testing.assert_array_equal(g5[0], g_m)
+    d = 0.2 * synth.perturbation(f0.shape, 2, 13).astype(np.float64)
+    lin = float(np.sum(g5[idx] * d))
+    assert abs(lin) > 0
+    e2 = []
+    for hh in (1.0, 0.5, 0.25, 0.125, 0.0625):
+        Jh, _, _ = J_of(f0 + hh * d)
+        e2.append(abs(Jh - J0 - hh * lin))
+    slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
+    assert all(abs(s - 2.0) < 0.15 for s in slopes), slopes
+
+
+def test_gradient_azimuth_vanishes_for_vertical_axis():
+    """With theta = 0 everywhere the symmetry axis is vertical whatever phi
+    is (the frame only spins about it, x-bar x-bar^T + y-bar y-bar^T is
+    unchanged), so dJ/dphi is zero while dJ/dtheta is not."""
+    p = _small_problem(so=4, nt=50)
+    keys = ("vp", "eps", "delta", "theta", "phi")
+    dobs = oracle.Problem(p).forward()
+    mm = dict(p.model)
+    mm["theta"] = np.zeros_like(mm["theta"])
+    mm["phi"] = (2.0 * synth.perturbation(mm["phi"].shape, 2, 5)).astype(np.float32)
+    g5, J = oracle.Problem(p, model=[mm[k] for k in keys]).gradient_aniso(dobs)
+    assert J > 0
+    gt, gf = np.abs(g5[3]).max(), np.abs(g5[4]).max()
+    assert gt > 0
+    assert gf <= 1e-12 * gt, (gf, gt)
