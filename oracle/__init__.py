@@ -69,7 +69,7 @@ def lib():
             for f in ("or_tti_gradient", "or_el_gradient"):
                 getattr(L, f).argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp, dp]
             L.or_tti_backward.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp]
-            L.or_tti_gradient_aniso.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp]
+            L.or_tti_gradient_aniso.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp, dp]
             L.or_tti_apply_L.argtypes = [P, dp, dp, dp, dp]
             L.or_tti_step_state.argtypes = [P, fp, fp, fp, fp, dp, dp, C.c_int]
             L.or_tti_step_state_d.argtypes = [P, dp, dp, dp, dp, C.c_int]
@@ -233,18 +233,22 @@ class Problem:
             return g, J.value, (gc[0] if nf == 1 else gc)
         return g, J.value
 
-    def gradient_aniso(self, d_obs, wavelet=None, src=None, rec=None):
+    def gradient_aniso(self, d_obs, wavelet=None, src=None, rec=None, magnitudes=False):
         """TTI only: gradient w.r.t. (m, epsilon, delta, theta, phi) on the
-        physical grid, shape [5][nx][ny][nz], and the misfit."""
+        physical grid, shape [5][nx][ny][nz], and the misfit; with
+        ``magnitudes`` also the theta and phi sums over the magnitudes of
+        their terms, shape [2][nx][ny][nz]."""
         src, rec, wav = self._geom(src, rec, wavelet)
         p = self.prob
         g = np.zeros((5, p.nx, p.ny, p.nz))
+        a = np.zeros((2, p.nx, p.ny, p.nz)) if magnitudes else None
         J = C.c_double(0.0)
         rc = lib().or_tti_gradient_aniso(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0],
-                                         _fp(rec), _dp(_d(d_obs)), _dp(g), C.byref(J))
+                                         _fp(rec), _dp(_d(d_obs)), _dp(g), C.byref(J),
+                                         _dp(a) if magnitudes else None)
         if rc:
             raise ValueError(f"oracle gradient rc={rc}")
-        return g, J.value
+        return (g, J.value, a) if magnitudes else (g, J.value)
 
     def backward(self, resid, wavelet=None, src=None, rec=None):
         """TTI only: (dJ/dm physical, dJ/dwavelet) for a given trace residual."""

@@ -572,7 +572,7 @@ static inline double dot3(const double *a, const double *b) { return a[0] * b[0]
  *   - [(zb_t . D zr)(zb . D r) + (zb . D zr)(zb_t . D r)],
  * all at q; scaled by `scale` and added to gt (t = theta) and gf (t = phi). */
 static void tti_frame_image(const or_prob *P, const double *zp, const double *zr, const double *p,
-                            const double *r, double scale, double *gt, double *gf)
+                            const double *r, double scale, double *gt, double *gf, double *at, double *af)
 {
     long N = P->N;
     double *Gz[3], *Gr[3], *gp[3], *gr[3];
@@ -599,6 +599,17 @@ static void tti_frame_image(const or_prob *P, const double *zp, const double *zr
                    - (dot3(W, c) * dot3(zb, d) + dot3(zb, c) * dot3(W, d));
         gt[q] += scale * t;
         gf[q] += scale * f;
+        if (at) {
+            /* magnitude of the summed terms (for rounding-error bounds of the sum) */
+            double u = fabs(dot3(A, a) * dot3(xb, b)) + fabs(dot3(xb, a) * dot3(A, b)) +
+                       fabs(dot3(B, a) * dot3(yb, b)) + fabs(dot3(yb, a) * dot3(B, b)) +
+                       fabs(dot3(C3, c) * dot3(zb, d)) + fabs(dot3(zb, c) * dot3(C3, d));
+            double v = fabs(dot3(U, a) * dot3(xb, b)) + fabs(dot3(xb, a) * dot3(U, b)) +
+                       fabs(dot3(V, a) * dot3(yb, b)) + fabs(dot3(yb, a) * dot3(V, b)) +
+                       fabs(dot3(W, c) * dot3(zb, d)) + fabs(dot3(zb, c) * dot3(W, d));
+            at[q] += fabs(scale) * u;
+            af[q] += fabs(scale) * v;
+        }
     }
     for (int i = 0; i < 3; i++) { free(Gz[i]); free(Gr[i]); free(gp[i]); free(gr[i]); }
 }
@@ -723,7 +734,8 @@ int or_tti_forward(or_prob *P, int nsrc, const float *src, const float *wav,
  * is added using the stored forward wavefields. */
 static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double *res,
                             int nsrc, const float *src, double *qbar, double *grad,
-                            double *grad_e, double *grad_d, double *grad_t, double *grad_f)
+                            double *grad_e, double *grad_d, double *grad_t, double *grad_f,
+                            double *abs_tf)
 {
     int e1, e2;
     pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
@@ -788,7 +800,7 @@ static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double
                 zp[q] = a * l0[q] + s * s0[q];
                 zr[q] = s * l0[q] + s0[q];
             }
-            tti_frame_image(P, zp, zr, up1, ur1, dt * dt, grad_t, grad_f);
+            tti_frame_image(P, zp, zr, up1, ur1, dt * dt, grad_t, grad_f, abs_tf, abs_tf ? abs_tf + N : NULL);
             free(zp); free(zr);
         }
         double *t;
@@ -803,7 +815,7 @@ int or_tti_adjoint(or_prob *P, int nrec, const float *rec, const double *traces,
                    int nsrc, const float *src, double *qbar)
 {
     if (P->d.kind != 1) return OR_EINVAL;
-    return tti_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL, NULL, NULL, NULL, NULL);
+    return tti_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL, NULL, NULL, NULL, NULL, NULL);
 }
 
 /* FWI gradient w.r.t. m = 1/vp^2 on the PHYSICAL grid (fold of the
@@ -825,7 +837,7 @@ int or_tti_gradient(or_prob *P, int nsrc, const float *src, const float *wav,
     }
     if (misfit) *misfit = J;
     double *g = dalloc(P->N);
-    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, NULL, NULL, NULL, NULL);
+    rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, NULL, NULL, NULL, NULL, NULL);
     if (!rc) {
         if (grad_comp) memcpy(grad_comp, g, sizeof(double) * P->N);
         if (grad_phys) fold(g, grad_phys, P);
@@ -836,10 +848,12 @@ int or_tti_gradient(or_prob *P, int nsrc, const float *src, const float *wav,
 }
 
 /* Gradient w.r.t. (m, epsilon, delta, theta, phi) on the physical grid:
- * grad_phys [5][nx][ny][nz] (each folded through the edge replication). */
+ * grad_phys [5][nx][ny][nz] (each folded through the edge replication).
+ * abs_phys (may be NULL) [2][nx][ny][nz]: the theta and phi sums taken over
+ * the magnitudes of their terms (the scale of their rounding errors). */
 int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *wav,
                           int nrec, const float *rec, const double *d_obs,
-                          double *grad_phys, double *misfit)
+                          double *grad_phys, double *misfit, double *abs_phys)
 {
     if (P->d.kind != 1) return OR_EINVAL;
     int nt = P->d.nt;
@@ -852,13 +866,14 @@ int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *w
         J += 0.5 * tr[i] * tr[i];
     }
     if (misfit) *misfit = J;
-    double *g = dalloc(5 * P->N);
+    double *g = dalloc(7 * P->N);
     rc = tti_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g, g + P->N, g + 2 * P->N, g + 3 * P->N,
-                          g + 4 * P->N);
-    if (!rc && grad_phys) {
-        const long np = (long)P->d.nx * P->d.ny * P->d.nz;
+                          g + 4 * P->N, g + 5 * P->N);
+    const long np = (long)P->d.nx * P->d.ny * P->d.nz;
+    if (!rc && grad_phys)
         for (int c = 0; c < 5; c++) fold(g + c * P->N, grad_phys + c * np, P);
-    }
+    if (!rc && abs_phys)
+        for (int c = 0; c < 2; c++) fold(g + (5 + c) * P->N, abs_phys + c * np, P);
     free(g); free(tr);
     free(P->store); P->store = NULL; P->stored = 0;
     return rc;
@@ -877,7 +892,7 @@ int or_tti_backward(or_prob *P, int nsrc, const float *src, const float *wav,
     free(tr);
     if (rc) return rc;
     double *g = dalloc(P->N);
-    rc = tti_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g, NULL, NULL, NULL, NULL);
+    rc = tti_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g, NULL, NULL, NULL, NULL, NULL);
     if (!rc && grad_phys) fold(g, grad_phys, P);
     free(g);
     free(P->store); P->store = NULL; P->stored = 0;

@@ -334,10 +334,12 @@ def test_taylor_gradient_tilt_azimuth(which):
 
     J0, o0, mm0 = J_of(base[which].astype(np.float64))
     f0 = mm0[which].astype(np.float64)
-    g5, J = o0.gradient_aniso(dobs)
+    g5, J, mag = o0.gradient_aniso(dobs, magnitudes=True)
     assert abs(J - J0) <= 1e-12 * J0
     g_m, _ = oracle.Problem(p, model=[mm0[k] for k in keys]).gradient(dobs)
     np.testing.assert_array_equal(g5[0], g_m)
+    # the sum of the term magnitudes bounds the sum (triangle inequality)
+    assert np.all(mag[idx - 3] >= np.abs(g5[idx]) * (1 - 1e-12))
     d = 0.2 * synth.perturbation(f0.shape, 2, 13).astype(np.float64)
     lin = float(np.sum(g5[idx] * d))
     assert abs(lin) > 0
