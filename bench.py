@@ -271,8 +271,21 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
         except wp.PropError as e:
             res[str(mode)] = {"error": str(e)}
         prop.close()
+    # gradient w.r.t. (m, eps, delta, theta, phi), full FP32 storage
+    prop = wp.Propagator.from_problem(p0, snap_mode=modes[0], stream=stream)
+    try:
+        prop.gradient_aniso(wav, src, rec, d_obs)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, J = prop.gradient_aniso(wav, src, rec, d_obs)
+        torch.cuda.synchronize()
+        s = time.perf_counter() - t0
+        aniso = {"mode": str(modes[0]), "seconds": s, "shots_per_hour": 3600.0 / s, "misfit": J}
+    except wp.PropError as e:
+        aniso = {"error": str(e)}
+    prop.close()
     return {"nt": nt, "grid": [p0.nx + 2 * p0.nbl, p0.ny + 2 * p0.nbl, p0.nz + 2 * p0.nbl],
-            "modes": res}
+            "modes": res, "aniso_m_eps_delta_theta_phi": aniso}
 
 
 def elastic_gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):

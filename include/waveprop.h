@@ -129,10 +129,17 @@ int prop_gradient(prop_t *p, const float *wavelet, const float *src_xyz, int nsr
  * with h^n = [H0 p^n; Hz r^n] of the forward field and lam^{n+1} the adjoint
  * field of the same step:
  *   dJ/deps   = sum_n 2 dt^2 lam_p^{n+1} H0 p^n,
- *   dJ/ddelta = sum_n dt^2 (lam_p^{n+1} Hz r^n + lam_r^{n+1} H0 p^n) / sqrt(1 + 2 delta)
+ *   dJ/ddelta = sum_n dt^2 (lam_p^{n+1} Hz r^n + lam_r^{n+1} H0 p^n) / sqrt(1 + 2 delta).
+ * It depends on the tilt theta and azimuth phi only through the symmetry
+ * axis n of Eq. (rot) inside H0 and Hz; with zeta = C lam^{n+1}, g = D p^n,
+ * h = D r^n (centred first derivatives at the point) and
+ *   V = D zeta_p (n.g) + (n.D zeta_p) g - D zeta_r (n.h) - (n.D zeta_r) h,
+ *   dJ/dtheta = sum_n dt^2 dn/dtheta . V,   dJ/dphi = sum_n dt^2 dn/dphi . V
  * (each folded onto the physical grid like dJ/dm).
- *   grad  [3][nx][ny][nz]: dJ/dm, dJ/deps, dJ/ddelta.
- * Costs one more application of H to the stored forward field per step.
+ *   grad  [5][nx][ny][nz]: dJ/dm, dJ/deps, dJ/ddelta, dJ/dtheta, dJ/dphi.
+ * Costs per step one more application of H to the stored forward field and
+ * the first derivatives of zeta and of the forward field; needs 6 more
+ * scratch fields than prop_gradient.
  * PROP_EINVAL for an elastic handle or a computational nz (nz + 2 nbl) that
  * is not a multiple of 4 (the TMA-fed kernels it uses need 16-byte rows). */
 int prop_gradient_aniso(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,

@@ -247,13 +247,13 @@ class Propagator:
         return out, J.value
 
     def gradient_aniso(self, wavelet, src, rec, d_obs, out=None):
-        """TTI: gradient w.r.t. (m, epsilon, delta), shape [3][nx][ny][nz], and
-        the misfit (``prop_gradient_aniso``)."""
+        """TTI: gradient w.r.t. (m, epsilon, delta, theta, phi), shape
+        [5][nx][ny][nz], and the misfit (``prop_gradient_aniso``)."""
         src_a, rec_a = _Arg(src), _Arg(rec)
         nsrc, nrec = _npts(src_a), _npts(rec_a)
         w = _Arg(wavelet, nsrc * self.nt)
         d = _Arg(d_obs, nrec * self.nt)
-        shape = (3,) + self.shape
+        shape = (5,) + self.shape
         if out is None:
             out = self._out(d_obs, shape)
         o = _Arg(out, int(np.prod(shape)), writable=True)

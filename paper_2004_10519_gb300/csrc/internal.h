@@ -117,8 +117,12 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
 // TTI imaging of the coupling matrix (TMA passes): with the forward field
 // (up, ur) at level n and the adjoint field (lp, lr) at level n+1,
 // ge += 2 dt^2 lam_p H0 p^n, gd += dt^2 (lam_p Hz r^n + lam_r H0 p^n) / sqrt(1+2 delta)
+// gax != NULL (3 fields): also gax += dt^2 V, V the dJ/dn term of the step
+// (tilt/azimuth imaging; zeta = C lam must be in tmp[6], tmp[7]; uses tmp[0..13])
 int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
-                        float *ge, float *gd);
+                        float *ge, float *gd, float *const *gax);
+// dJ/dn accumulators a[0..2] -> dJ/dtheta in a[0], dJ/dphi in a[1] (pointwise)
+void tti_axis_to_angles(prop_s *P, float *const *a);
 // TMA passes of a transposed elastic step with imaging: on entry S[3..8] hold
 // t = g tbar and sig[0..5] = C t; updates vbar (S[0..2]), writes b_avg vbar to
 // w[0..2], accumulates g_lambda, g_mu (gr[0], gr[1]) and the edge products

@@ -877,12 +877,14 @@ static void sample_src(prop_s *P, const Geometry &G, float *const *a, float *col
 static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float *wav,
                      float *srcstage, float *const *g3)
 {
-    // g3: NULL (adjoint modelling), {dJ/dm} or, with P->aniso, {dJ/dm, dJ/deps, dJ/ddelta}
+    // g3: NULL (adjoint modelling), {dJ/dm} or, with P->aniso,
+    // {dJ/dm, dJ/deps, dJ/ddelta, dJ/dn (3 components)}
     float *grad = g3 ? g3[0] : nullptr;
     const bool aniso = g3 && P->aniso;
     const int nt = P->d.nt;
     const size_t N = (size_t)P->g.N;
     WP_TRY(ensure_ast(P));
+    if (aniso) WP_TRY(ensure_tmp(P, 14));
     float *a[4] = {P->ast[0], P->ast[1], P->ast[2], P->ast[3]};
     WP_TRY(zero_fields(P, a, 4));
     WP_TRY(zero_fields(P, P->tmp + 6, 2));   // zeta = C lam of the zero state
@@ -896,11 +898,12 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
         prof_maybe_collect(P);
         return PROP_OK;
     };
-    // eps/delta imaging: lam^k (a[0], a[1] after the step and the residual)
-    // with the forward level k-1 (level 0 is zero: no term for k = 1)
+    // eps/delta/axis imaging: lam^k (a[0], a[1] after the step and the
+    // residual; zeta = C lam^k in tmp[6], tmp[7]) with the forward level k-1
+    // (level 0 is zero: no term for k = 1)
     auto aniso_iter = [&](int k, const float *u1) -> int {
         if (!aniso || k < 2) return PROP_OK;
-        return tti_image_aniso_tma(P, u1, u1 + N, a[0], a[1], g3[1], g3[2]);
+        return tti_image_aniso_tma(P, u1, u1 + N, a[0], a[1], g3[1], g3[2], g3 + 3);
     };
     if (!grad) {
         for (int k = nt - 1; k >= 1; k--) WP_TRY(adj_iter(k, nullptr, nullptr));
@@ -1052,14 +1055,18 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
         WP_TRY(wp_malloc(P, &stage.p, sizeof(float) * (size_t)nt * nsrc, "source staging"));
         WP_TRY(wp_malloc(P, &out.p, sizeof(float) * (size_t)nt * nsrc, "source output"));
     }
-    const int ng = P->d.kind == PROP_TTI ? (P->aniso ? 3 : 1) : 3;
+    // computational-grid accumulators and physical outputs: TTI m (+ eps,
+    // delta and the three dJ/dn components that become theta, phi); elastic
+    // lambda, mu, b
+    const bool aniso = P->d.kind == PROP_TTI && P->aniso;
+    const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : 3, nout = aniso ? 5 : ng;
     const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
-    float *g3[3] = {};
+    float *g3[6] = {};
     if (grad) {
         WP_TRY(wp_malloc(P, &gbuf.p, sizeof(float) * N * ng, "gradient"));
         WP_CK(P, cudaMemsetAsync(gbuf.p, 0, sizeof(float) * N * ng, P->stream));
         for (int i = 0; i < ng; i++) g3[i] = (float *)gbuf.p + i * N;
-        WP_TRY(wp_malloc(P, &gphys.p, sizeof(float) * np * ng, "gradient (physical)"));
+        WP_TRY(wp_malloc(P, &gphys.p, sizeof(float) * np * nout, "gradient (physical)"));
     }
     if (P->d.kind == PROP_TTI)
         WP_TRY(tti_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3 : nullptr));
@@ -1071,8 +1078,9 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
     }
     if (grad) {
         WP_TRY(ensure_tmp(P, 2));        // fold scratch (free after the sweep)
-        for (int i = 0; i < ng; i++) k_fold(P, g3[i], (float *)gphys.p + i * np, P->tmp[0], P->tmp[1]);
-        WP_TRY(copy_out(P, grad, (const float *)gphys.p, np * ng));
+        if (aniso) tti_axis_to_angles(P, g3 + 3);
+        for (int i = 0; i < nout; i++) k_fold(P, g3[i], (float *)gphys.p + i * np, P->tmp[0], P->tmp[1]);
+        WP_TRY(copy_out(P, grad, (const float *)gphys.p, np * nout));
     }
     return finish(P);
 }
@@ -1119,11 +1127,12 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
         b += ((size_t)K + 1) * snap_fields(P) * N * 4;
     for (int i = 0; i < cf; i++)
         if (!P->ast[i]) b += N * 4;
-    const int ntmp = P->d.kind == PROP_TTI ? 8 : 15;
+    const bool aniso = P->d.kind == PROP_TTI && P->aniso;
+    const int ntmp = P->d.kind == PROP_TTI ? (aniso ? 14 : 8) : 15;
     for (int i = 0; i < ntmp; i++)
         if (!P->tmp[i]) b += N * 4;
-    const int ng = P->d.kind == PROP_TTI ? 1 : 3;
-    b += (N + np) * ng * 4;
+    const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : 3, nout = aniso ? 5 : ng;
+    b += (N * ng + np * nout) * 4;
     b += (size_t)4 * 4 * nrec * nt;    // traces, staging, observed data, residual
     return b + ((size_t)64 << 20);     // point tables, wavelet, allocator granularity
 }

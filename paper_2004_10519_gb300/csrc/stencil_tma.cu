@@ -549,7 +549,8 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
 
 // ---------------------------------------------------------------------------
 // TTI rotation pass on (p, r), or on zeta = C lam in the transposed step
-// (the update pass of the previous adjoint step writes zeta).
+// (the update pass of the previous adjoint step writes zeta).  RAW: write
+// the unprojected first derivatives D p, D r (tilt/azimuth imaging).
 // stage: [p rect] [r rect] [queue heads p, r (x+M)] [n_x, n_y (plane x)]
 // ---------------------------------------------------------------------------
 template <int M>
@@ -563,7 +564,7 @@ struct RMaps {
     CUtensorMap p, r, qp, qr, nx, ny;
 };
 
-template <int M>
+template <int M, bool RAW = false>
 __global__ void __launch_bounds__(NTP, 2)
 tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
             const __grid_constant__ RMaps mp, float *__restrict__ ex, float *__restrict__ ey,
@@ -655,6 +656,14 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
             float o[2][6];
 #pragma unroll
             for (int i = 0; i < 2; i++) {
+                if constexpr (RAW) {
+#pragma unroll
+                    for (int c = 0; c < 3; c++) {
+                        o[i][c] = gp[i][c];
+                        o[i][3 + c] = gr[i][c];
+                    }
+                    continue;
+                }
                 const float a0 = nx2[i], a1 = ny2[i];
                 const float a2 = sqrtf(fmaxf(0.f, 1.f - a0 * a0 - a1 * a1));
                 const float wpn = a0 * gp[i][0] + a1 * gp[i][1] + a2 * gp[i][2];
@@ -1072,12 +1081,69 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
     return PROP_OK;
 }
 
+// Tilt/azimuth imaging of one step.  With zeta = C lam (dz: D zeta_p, D zeta_r)
+// and the forward field's g = D p, h = D r (du), the step's term of dJ/dn is
+//   V = D zeta_p (n.g) + (n.D zeta_p) g - D zeta_r (n.h) - (n.D zeta_r) h
+// (the derivative of -zeta_p^T (I - n n^T) g - (n.D zeta_r)(n.h), the
+// bilinear forms of H0 and Hz, with respect to n at the point);
+// acc += s V, s = dt^2.  n is the stored axis (n_z >= 0).
+struct AxisIn {
+    const float *dz[6], *du[6], *nx, *ny;
+    float *acc[3];
+};
+__global__ void tti_axis_image(long long n, float s, AxisIn a)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const float n0 = a.nx[q], n1 = a.ny[q];
+    const float nv[3] = {n0, n1, sqrtf(fmaxf(0.f, 1.f - n0 * n0 - n1 * n1))};
+    float zp[3], zr[3], gp[3], gr[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        zp[c] = a.dz[c][q];
+        zr[c] = a.dz[3 + c][q];
+        gp[c] = a.du[c][q];
+        gr[c] = a.du[3 + c][q];
+    }
+    float ng = 0.f, nzp = 0.f, nh = 0.f, nzr = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        ng += nv[c] * gp[c];
+        nzp += nv[c] * zp[c];
+        nh += nv[c] * gr[c];
+        nzr += nv[c] * zr[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++)
+        a.acc[c][q] += s * (zp[c] * ng + nzp * gp[c] - zr[c] * nh - nzr * gr[c]);
+}
+
+// dJ/dn (stored axis) -> dJ/dtheta into a0, dJ/dphi into a1: with the sign sg
+// that makes n_z >= 0, the stored axis is sg n(theta, phi), so
+// dJ/dt = sg dn/dt . acc  (t = theta, phi)
+__global__ void tti_axis_finalize(long long n, const float *th, const float *ph, float *a0, float *a1,
+                                  const float *a2)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    double st, ct, sp, cp;
+    sincos((double)th[q], &st, &ct);
+    sincos((double)ph[q], &sp, &cp);
+    const double sg = ct < 0.0 ? -1.0 : 1.0;
+    const double v0 = a0[q], v1 = a1[q], v2 = a2[q];
+    a0[q] = (float)(sg * (ct * cp * v0 + ct * sp * v1 - st * v2));
+    a1[q] = (float)(sg * (-st * sp * v0 + st * cp * v1));
+}
+
 // imaging of the coupling matrix (eps, delta gradients) with the forward
 // field (up, ur) at level n and the adjoint field (lp, lr) at level n+1:
-// rotation pass on the forward field, then the update pass in mode 2
+// rotation pass on the forward field, then the update pass in mode 2.
+// gax != NULL: also the tilt/azimuth term, from zeta = C lam in tmp[6], tmp[7]
+// (raw rotation passes on zeta into tmp[0..5] and on the forward field into
+// tmp[8..13], then tti_axis_image into gax[0..2])
 template <int M>
 int tti_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr, float *ge,
-                    float *gd)
+                    float *gd, float *const *gax)
 {
     using B = BX<M>;
     const GridDev &g = P->g;
@@ -1103,6 +1169,30 @@ int tti_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp
     tti_upd_tma<M, 2, 0><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, nullptr, nullptr, ge, gd, nullptr,
                                                      P->flag, 0, xc, P->flag);
     P->kern_launches += 2;
+    if (gax) {
+        RMaps rz;
+        ok = map_of(P, t[6], B::RC, B::RR, &rz.p) && map_of(P, t[7], B::RC, B::RR, &rz.r) &&
+             map_of(P, t[6], FZ, FY, &rz.qp) && map_of(P, t[7], FZ, FY, &rz.qr) && (rz.nx = rm.nx, true) &&
+             (rz.ny = rm.ny, true);
+        if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+        static const bool attr_raw = set_smem(tti_rot_tma<M, true>, s1);
+        (void)attr_raw;
+        tti_rot_tma<M, true><<<grd, blk, s1, P->stream>>>(g, P->w, t[6], t[7], rz, t[0], t[1], t[2], t[3], t[4],
+                                                          t[5], xc, P->flag);
+        tti_rot_tma<M, true><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[8], t[9], t[10], t[11], t[12],
+                                                          t[13], xc, P->flag);
+        AxisIn ai;
+        for (int c = 0; c < 6; c++) {
+            ai.dz[c] = t[c];
+            ai.du[c] = t[8 + c];
+        }
+        ai.nx = P->nrm[0];
+        ai.ny = P->nrm[1];
+        for (int c = 0; c < 3; c++) ai.acc[c] = gax[c];
+        const long long n = (long long)g.N;
+        tti_axis_image<<<(unsigned)((n + 255) / 256), 256, 0, P->stream>>>(n, P->g.dt * P->g.dt, ai);
+        P->kern_launches += 3;
+    }
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
 }
@@ -1141,17 +1231,25 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
     return rc;
 }
 
-// eps, delta imaging of one transposed TTI step (see tti_image_aniso)
+// eps, delta (and theta, phi) imaging of one transposed TTI step (see tti_image_aniso)
 int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
-                        float *ge, float *gd)
+                        float *ge, float *gd, float *const *gax)
 {
     switch (P->M) {
-    case 2: return tti_image_aniso<2>(P, up, ur, lp, lr, ge, gd);
-    case 4: return tti_image_aniso<4>(P, up, ur, lp, lr, ge, gd);
-    case 6: return tti_image_aniso<6>(P, up, ur, lp, lr, ge, gd);
-    case 8: return tti_image_aniso<8>(P, up, ur, lp, lr, ge, gd);
+    case 2: return tti_image_aniso<2>(P, up, ur, lp, lr, ge, gd, gax);
+    case 4: return tti_image_aniso<4>(P, up, ur, lp, lr, ge, gd, gax);
+    case 6: return tti_image_aniso<6>(P, up, ur, lp, lr, ge, gd, gax);
+    case 8: return tti_image_aniso<8>(P, up, ur, lp, lr, ge, gd, gax);
     }
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
+}
+
+// dJ/dn accumulators (computational grid) -> dJ/dtheta in a[0], dJ/dphi in a[1]
+void tti_axis_to_angles(prop_s *P, float *const *a)
+{
+    const long long n = (long long)P->g.N;
+    tti_axis_finalize<<<(unsigned)((n + 255) / 256), 256, 0, P->stream>>>(n, P->th, P->ph, a[0], a[1], a[2]);
+    P->kern_launches += 1;
 }
 
 // the TMA passes of one transposed elastic step with imaging (see el_adj_grad)

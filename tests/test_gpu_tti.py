@@ -123,11 +123,15 @@ def test_gradient_parity_and_checkpoint_modes(wp, shape):
 
 
 def test_gradient_aniso_parity(wp):
-    """dJ/d(m, eps, delta) (prop_gradient_aniso) against the oracle, full
-    storage and FP32 checkpoints (bitwise equal to each other); the m
-    component equals prop_gradient's."""
+    """dJ/d(m, eps, delta, theta, phi) (prop_gradient_aniso) against the
+    oracle, full storage and FP32 checkpoints (bitwise equal to each other);
+    the m component equals prop_gradient's.  The theta and phi sums cancel
+    strongly (the p and r terms of their imaging nearly balance, and the
+    cross-correlation oscillates): their error is bounded relative to the
+    oracle's sum of the term magnitudes, 1e-5 of it (FP32 wavefields carry
+    relative errors of about 1e-6), instead of relative to the result."""
     p, p0, d_obs = grad_problem(shape=(30, 26, 36))
-    g_ref, J_ref = oracle.Problem(p0).gradient_aniso(d_obs)
+    g_ref, J_ref, mag = oracle.Problem(p0).gradient_aniso(d_obs, magnitudes=True)
     d32 = d_obs.astype(np.float32)
     res = {}
     for mode in (wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32):
@@ -138,8 +142,13 @@ def test_gradient_aniso_parity(wp):
         prop.close()
     g, J = res[wp.SNAP_FULL_FP32]
     assert abs(J - J_ref) <= 1e-5 * J_ref
+    assert g.shape == g_ref.shape == (5, p0.nx, p0.ny, p0.nz)
     for c in range(3):
-        assert rel(g[c], g_ref[c]) <= 1e-4, c
+        assert rel(g[c], g_ref[c]) <= 1e-4, (c, rel(g[c], g_ref[c]))
+    for c in (3, 4):
+        err = float(np.linalg.norm(g[c].astype(np.float64) - g_ref[c]))
+        assert err <= 1e-5 * float(np.linalg.norm(mag[c - 3])), (c, err, rel(g[c], g_ref[c]))
+        assert rel(g[c], g_ref[c]) <= 1e-3, c
     np.testing.assert_array_equal(res[wp.SNAP_CKPT_FP32][0], g)
     # computational nz not a multiple of 4: rejected, handle stays usable
     q, q0, d2 = grad_problem(shape=(30, 26, 34))
