@@ -62,13 +62,17 @@ def lib():
             L.or_dims.argtypes = [P, C.POINTER(C.c_int)]
             L.or_param.restype = dp
             L.or_param.argtypes = [P, C.c_int]
-            for f in ("or_tti_forward", "or_el_forward"):
+            for f in ("or_tti_forward", "or_el_forward", "or_ac_forward"):
                 getattr(L, f).argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, C.c_int]
-            for f in ("or_tti_adjoint", "or_el_adjoint"):
+            for f in ("or_tti_adjoint", "or_el_adjoint", "or_ac_adjoint"):
                 getattr(L, f).argtypes = [P, C.c_int, fp, dp, C.c_int, fp, dp]
-            for f in ("or_tti_gradient", "or_el_gradient"):
+            for f in ("or_tti_gradient", "or_el_gradient", "or_ac_gradient"):
                 getattr(L, f).argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp, dp]
             L.or_tti_backward.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp]
+            L.or_ac_backward.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp]
+            L.or_ac_step_state_d.argtypes = [P, dp, dp, C.c_int]
+            L.or_ac_step_points.argtypes = [C.POINTER(_Desc), fp, fp, fp, C.c_int, lp, dp]
+            L.or_weights_d2.argtypes = [C.c_int, dp]
             L.or_tti_gradient_aniso.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp, dp]
             L.or_tti_apply_L.argtypes = [P, dp, dp, dp, dp]
             L.or_tti_step_state.argtypes = [P, fp, fp, fp, fp, dp, dp, C.c_int]
@@ -199,7 +203,7 @@ class Problem:
     def forward(self, wavelet=None, src=None, rec=None, store=False):
         src, rec, wav = self._geom(src, rec, wavelet)
         tr = np.zeros((rec.shape[0], self.nt))
-        f = lib().or_tti_forward if self.prob.kind == 1 else lib().or_el_forward
+        f = {1: lib().or_tti_forward, 2: lib().or_el_forward, 3: lib().or_ac_forward}[self.prob.kind]
         rc = f(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0], _fp(rec), _dp(tr), int(store))
         if rc:
             raise ValueError(f"oracle forward rc={rc}")
@@ -209,7 +213,7 @@ class Problem:
         src, rec, _ = self._geom(src, rec, None)
         traces = _d(traces)
         q = np.zeros((src.shape[0], self.nt))
-        f = lib().or_tti_adjoint if self.prob.kind == 1 else lib().or_el_adjoint
+        f = {1: lib().or_tti_adjoint, 2: lib().or_el_adjoint, 3: lib().or_ac_adjoint}[self.prob.kind]
         rc = f(self.h, rec.shape[0], _fp(rec), _dp(traces), src.shape[0], _fp(src), _dp(q))
         if rc:
             raise ValueError(f"oracle adjoint rc={rc}")
@@ -219,11 +223,11 @@ class Problem:
         src, rec, wav = self._geom(src, rec, wavelet)
         d_obs = _d(d_obs)
         p = self.prob
-        nf = 1 if p.kind == 1 else 3
+        nf = 3 if p.kind == 2 else 1
         g = np.zeros((nf, p.nx, p.ny, p.nz))
         gc = np.zeros((nf,) + self.shape) if comp else None
         J = C.c_double(0.0)
-        f = lib().or_tti_gradient if p.kind == 1 else lib().or_el_gradient
+        f = {1: lib().or_tti_gradient, 2: lib().or_el_gradient, 3: lib().or_ac_gradient}[p.kind]
         rc = f(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0], _fp(rec), _dp(d_obs),
                _dp(g), C.byref(J), _dp(gc) if comp else None)
         if rc:
@@ -251,13 +255,15 @@ class Problem:
         return (g, J.value, a) if magnitudes else (g, J.value)
 
     def backward(self, resid, wavelet=None, src=None, rec=None):
-        """TTI only: (dJ/dm physical, dJ/dwavelet) for a given trace residual."""
+        """TTI and acoustic: (dJ/dm physical, dJ/dwavelet) for a given trace
+        residual."""
         src, rec, wav = self._geom(src, rec, wavelet)
         p = self.prob
         g = np.zeros((p.nx, p.ny, p.nz))
         q = np.zeros((src.shape[0], self.nt))
-        rc = lib().or_tti_backward(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0],
-                                   _fp(rec), _dp(_d(resid)), _dp(g), _dp(q))
+        f = lib().or_ac_backward if p.kind == 3 else lib().or_tti_backward
+        rc = f(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0],
+               _fp(rec), _dp(_d(resid)), _dp(g), _dp(q))
         if rc:
             raise ValueError(rc)
         return g, q
@@ -273,6 +279,13 @@ class Problem:
     def tti_run_d(self, p0, p1, r0, r1, nsteps):
         a = [_d(x).reshape(-1).copy() for x in (p0, p1, r0, r1)]
         lib().or_tti_step_state_d(self.h, *[_dp(x) for x in a], nsteps)
+        return [x.reshape(self.shape) for x in a]
+
+    def ac_run_d(self, u0, u1, nsteps):
+        """Acoustic: nsteps source-free steps of (u^{n-1}, u^n); returns the
+        last two levels (older first)."""
+        a = [_d(x).reshape(-1).copy() for x in (u0, u1)]
+        lib().or_ac_step_state_d(self.h, _dp(a[0]), _dp(a[1]), nsteps)
         return [x.reshape(self.shape) for x in a]
 
     def el_step(self, state, adjoint=False, nsteps=1):
@@ -320,6 +333,28 @@ def tti_step_points(prob, state, idx, adjoint=False):
     out = np.zeros((idx.size, 2))
     rc = lib().or_tti_step_points(C.byref(d), arr, *[_fp(s) for s in st], idx.size, _lp(idx),
                                   _dp(out), int(adjoint))
+    if rc:
+        raise ValueError(rc)
+    return out
+
+
+def weights_d2(so):
+    w = np.zeros(so // 2 + 1)
+    if lib().or_weights_d2(so, _dp(w)):
+        raise ValueError(so)
+    return w
+
+
+def ac_step_points(prob, state, idx):
+    """One acoustic step evaluated only at ``idx``; state = (u0, u1) float32
+    computational-grid arrays."""
+    d = desc_of(prob)
+    vp = _f(prob.model["vp"])
+    st = [_f(s).reshape(-1) for s in state]
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    out = np.zeros(idx.size)
+    rc = lib().or_ac_step_points(C.byref(d), _fp(vp), _fp(st[0]), _fp(st[1]), idx.size, _lp(idx),
+                                 _dp(out))
     if rc:
         raise ValueError(rc)
     return out

@@ -1,5 +1,5 @@
 /*
- * FP64 CPU oracle for the TTI and elastic propagators.
+ * FP64 CPU oracle for the TTI, elastic and isotropic acoustic propagators.
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
  * bench.py's cpu_baseline leg load this library.  It shares no code with the
@@ -20,7 +20,9 @@
  *   - zero-lag cross-correlation imaging (adjoint-state gradient): Sec. III;
  *   - elastic velocity-stress system, Eq. (elas1), staggered grids with
  *     half-node averaging and the damp factor: Sec. IV-A, elastic listing;
- *   - Cerjan absorbing layer: Sec. V.
+ *   - Cerjan absorbing layer: Sec. V;
+ *   - isotropic acoustic propagator: Eq. (acou) with u.laplace as the sum of
+ *     centred second derivatives of the space order, damped like TTI.
  * Readings where the paper is silent (the TTI system of Zhang et al. /
  * Duveneck et al. cited in Sec. III-A, FD weights, damping profiles,
  * staggering, averaging, trilinear interpolation) are listed in the design
@@ -31,7 +33,10 @@
  * dispersion of the TTI operator against the pseudo-acoustic dispersion
  * relation, eps=delta=0 collapse to an isotropic leapfrog, the point-source
  * Green's function, elastic energy conservation, mu=0 invariants, dot tests,
- * assembled-matrix transposes and Taylor tests of both gradients).
+ * assembled-matrix transposes and Taylor tests of the gradients; for the
+ * acoustic propagator the second-derivative moment conditions, Green's
+ * function convergence, undamped leapfrog energy conservation, the dot test,
+ * the assembled step's symmetry and a Taylor test).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -48,7 +53,7 @@
 /* descriptor (own definition; the CUDA library has its own)           */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    int kind;            /* 1 = TTI, 2 = elastic */
+    int kind;            /* 1 = TTI, 2 = elastic, 3 = isotropic acoustic */
     int nx, ny, nz;      /* PHYSICAL grid points */
     int nbl;             /* absorbing cells added on every face */
     int so;              /* space order (even) */
@@ -66,12 +71,14 @@ typedef struct {
     int M;
     double c[MAXM + 1];  /* centred weights c_1..c_M */
     double b[MAXM + 1];  /* staggered weights b_1..b_M */
+    double c2[MAXM + 1]; /* second-derivative weights c2_0..c2_M (acoustic) */
     /* TTI */
     double *m, *eps, *del, *th, *ph, *sig;   /* sig: damping rate [1/s] */
     /* elastic */
     double *lam, *mu, *bu;                   /* Lame [Pa], buoyancy [m^3/kg] */
     /* forward wavefield store for gradients */
-    double *store;       /* TTI: [nt+1][2][N] (p^n, r^n) ; elastic: [nt+1][9][N] */
+    double *store;       /* TTI: [nt+1][2][N] (p^n, r^n) ; elastic: [nt+1][9][N] ;
+                            acoustic: [nt+1][N] */
     int stored;
 } or_prob;
 
@@ -146,6 +153,22 @@ int or_weights_staggered(int so, double *b)
     return OR_OK;
 }
 
+/* Centred second derivative of order so (the u.laplace of the Sec. II-A
+ * listing, one axis): Fornberg weights for d^2/dx^2 at 0 on the nodes
+ * -M..M; w[k] (k = 0..M) is the weight of the nodes +-k, so that
+ *   (D2 u)_i = (1/h^2) (w_0 u_i + sum_k w_k (u_{i+k} + u_{i-k})). */
+int or_weights_d2(int so, double *w)
+{
+    if (so < 2 || so % 2 || so / 2 > MAXM) return OR_EINVAL;
+    int M = so / 2;
+    double x[2 * MAXM + 1], f[2 * MAXM + 1];
+    for (int i = 0; i <= 2 * M; i++) x[i] = i - M;
+    int rc = or_fornberg(2, 0.0, x, 2 * M + 1, f);
+    if (rc) return rc;
+    for (int k = 0; k <= M; k++) w[k] = f[M + k];
+    return OR_OK;
+}
+
 /* ------------------------------------------------------------------ */
 /* 1D line operators (zero extension outside [0, n))                    */
 /* ------------------------------------------------------------------ */
@@ -173,6 +196,16 @@ static void line_DT_add(const double *w, double *o, long s, int n, const or_prob
             if (i + k < n) o[(long)(i + k) * s] += P->c[k] * wi;
             if (i - k >= 0) o[(long)(i - k) * s] -= P->c[k] * wi;
         }
+    }
+}
+/* second derivative: out_i = (1/h^2) (c2_0 f_i + sum_k c2_k (f_{i+k} + f_{i-k})) */
+static void line_D2(const double *f, double *o, long s, int n, const or_prob *P)
+{
+    for (int i = 0; i < n; i++) {
+        double acc = P->c2[0] * at(f, s, n, i);
+        for (int k = 1; k <= P->M; k++)
+            acc += P->c2[k] * (at(f, s, n, i + k) + at(f, s, n, i - k));
+        o[(long)i * s] = acc / (P->d.h * P->d.h);
     }
 }
 /* node -> half:  out_{i+1/2} (stored at i) = (1/h) sum_k b_k (f_{i+k} - f_{i-k+1}) */
@@ -369,14 +402,15 @@ void or_destroy(or_prob *P)
 }
 
 /* model (physical grid, float32):
- *   TTI:     vp [km/s], eps, delta, theta [rad], phi [rad]
- *   elastic: vp [km/s], vs [km/s], rho [g/cc] */
+ *   TTI:      vp [km/s], eps, delta, theta [rad], phi [rad]
+ *   elastic:  vp [km/s], vs [km/s], rho [g/cc]
+ *   acoustic: vp [km/s]  (damping as for TTI, vmax = max vp) */
 or_prob *or_create(const or_desc *d, const float *const *model)
 {
     if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nbl < 0 || d->so < 2 ||
         d->so % 2 || d->so / 2 > MAXM || d->nt < 1 || !(d->h > 0) || !(d->dt > 0))
         return NULL;
-    if (d->kind != 1 && d->kind != 2) return NULL;
+    if (d->kind != 1 && d->kind != 2 && d->kind != 3) return NULL;
     or_prob *P = (or_prob *)calloc(1, sizeof(or_prob));
     P->d = *d;
     P->NX = d->nx + 2 * d->nbl;
@@ -389,6 +423,7 @@ or_prob *or_create(const or_desc *d, const float *const *model)
     for (int k = 1; k <= P->M; k++) P->c[k] = tmp[k - 1];
     or_weights_staggered(d->so, tmp);
     for (int k = 1; k <= P->M; k++) P->b[k] = tmp[k - 1];
+    or_weights_d2(d->so, P->c2);
     long N = P->N;
     if (d->kind == 1) {
         double *vp = dalloc(N);
@@ -407,6 +442,22 @@ or_prob *or_create(const or_desc *d, const float *const *model)
             P->m[i] = 1.0 / (vp[i] * vp[i]);      /* squared slowness [s^2/m^2] */
             double v = vp[i] * sqrt(1.0 + 2.0 * P->eps[i]);
             if (v > vmax) vmax = v;
+        }
+        if (d->vdamp > 0) vmax = d->vdamp;
+        free(vp);
+        for (int x = 0; x < P->NX; x++)
+            for (int y = 0; y < P->NY; y++)
+                for (int z = 0; z < P->NZ; z++)
+                    P->sig[IDX(P, x, y, z)] = tti_sigma(P, x, y, z, vmax);
+    } else if (d->kind == 3) {
+        double *vp = dalloc(N);
+        P->m = dalloc(N); P->sig = dalloc(N);
+        if (!vp || !P->m || !P->sig) { free(vp); or_destroy(P); return NULL; }
+        extend(model[0], vp, P, 1000.0);
+        double vmax = 0.0;
+        for (long i = 0; i < N; i++) {
+            P->m[i] = 1.0 / (vp[i] * vp[i]);
+            if (vp[i] > vmax) vmax = vp[i];
         }
         if (d->vdamp > 0) vmax = d->vdamp;
         free(vp);
@@ -917,6 +968,229 @@ int or_tti_step_state(or_prob *P, const float *p0f, const float *p1f, const floa
         }
     }
     free(p0); free(p1); free(r0); free(r1);
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------ */
+/* Isotropic acoustic propagator (Sec. II-A, Eq. (acou) and the          */
+/* wave-equation listing: m u_tt - laplace(u) + damp u_t = q), with the  */
+/* damped leapfrog, injection and interpolation of the TTI path on one   */
+/* wavefield.  L = sum over axes of the second derivative D2.            */
+/* ------------------------------------------------------------------ */
+static void ac_apply_L(const or_prob *P, const double *u, double *Lu)
+{
+    long N = P->N;
+    double *t = dalloc(N);
+    memset(Lu, 0, sizeof(double) * N);
+    for (int a = 0; a < 3; a++) {
+        apply_axis(line_D2, u, t, a, P);
+        for (long q = 0; q < N; q++) Lu[q] += t[q];
+    }
+    free(t);
+}
+
+/* A u2 = dt^2 L u1 + 2 m u1 - B u0,  A = m (1 + sig dt/2), B = m (1 - sig dt/2).
+ * L is symmetric, so the same map advances the adjoint state. */
+static void ac_step(const or_prob *P, const double *u0, const double *u1, double *u2)
+{
+    long N = P->N;
+    double dt = P->d.dt;
+    double *Lu = dalloc(N);
+    ac_apply_L(P, u1, Lu);
+#pragma omp parallel for
+    for (long q = 0; q < N; q++) {
+        double A = P->m[q] * (1.0 + 0.5 * P->sig[q] * dt);
+        double B = P->m[q] * (1.0 - 0.5 * P->sig[q] * dt);
+        u2[q] = (dt * dt * Lu[q] + 2.0 * P->m[q] * u1[q] - B * u0[q]) / A;
+    }
+    free(Lu);
+}
+
+/* Forward modelling, per time step n = 0..nt-1: d^n = R u^n; u^{n+1} from
+ * the leapfrog step; q^n injected into u^{n+1} with factor dt^2 / A.
+ * traces [nrec][nt]; store != 0 keeps u^n, n = 0..nt. */
+int or_ac_forward(or_prob *P, int nsrc, const float *src, const float *wav,
+                  int nrec, const float *rec, double *traces, int store)
+{
+    if (P->d.kind != 3) return OR_EINVAL;
+    int e1, e2;
+    pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
+    if (e1 || e2) { free(S); free(R); return OR_EINVAL; }
+    long N = P->N; int nt = P->d.nt; double dt = P->d.dt;
+    double *u0 = dalloc(N), *u1 = dalloc(N), *u2 = dalloc(N);
+    if (store) {
+        free(P->store);
+        P->store = dalloc((long)(nt + 1) * N);
+        if (!P->store) { free(u0); free(u1); free(u2); free(S); free(R); return OR_ENOMEM; }
+        P->stored = 1;
+    }
+    for (int n = 0; n < nt; n++) {
+        for (int i = 0; i < nrec; i++) traces[(long)i * nt + n] = sample(&R[i], u1);
+        ac_step(P, u0, u1, u2);
+        for (int s = 0; s < nsrc; s++)
+            for (int c = 0; c < S[s].n; c++) {
+                long q = S[s].idx[c];
+                double A = P->m[q] * (1.0 + 0.5 * P->sig[q] * dt);
+                u2[q] += dt * dt / A * S[s].w[c] * (double)wav[(long)s * nt + n];
+            }
+        if (store) memcpy(P->store + (long)(n + 1) * N, u2, sizeof(double) * N);
+        double *t = u0; u0 = u1; u1 = u2; u2 = t;
+    }
+    free(u0); free(u1); free(u2); free(S); free(R);
+    return OR_OK;
+}
+
+/* Adjoint of or_ac_forward, k = nt-1 .. 1 (lam^{nt} = lam^{nt+1} = 0):
+ *   A lam^k = dt^2 L lam^{k+1} + 2 m lam^{k+1} - B lam^{k+2} + R^T r^k,
+ *   qbar^{k-1} = dt^2 (S lam^k);
+ * grad != NULL: g -= lam^k (a u^k - 2 u^{k-1} + b u^{k-2}) with the stored
+ * forward field (d/dm of the step's A u^{n+1} - 2 m u^n + B u^{n-1}). */
+static int ac_adjoint_core(or_prob *P, int nrec, const float *rec, const double *res,
+                           int nsrc, const float *src, double *qbar, double *grad)
+{
+    int e1, e2;
+    pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
+    if (e1 || e2) { free(S); free(R); return OR_EINVAL; }
+    long N = P->N; int nt = P->d.nt; double dt = P->d.dt;
+    double *l2 = dalloc(N), *l1 = dalloc(N), *l0 = dalloc(N), *Ll = dalloc(N);
+    if (qbar) memset(qbar, 0, sizeof(double) * (size_t)nsrc * nt);
+    for (int k = nt - 1; k >= 1; k--) {
+        ac_apply_L(P, l1, Ll);
+#pragma omp parallel for
+        for (long q = 0; q < N; q++) {
+            double B = P->m[q] * (1.0 - 0.5 * P->sig[q] * dt);
+            l0[q] = dt * dt * Ll[q] + 2.0 * P->m[q] * l1[q] - B * l2[q];
+        }
+        for (int i = 0; i < nrec; i++)
+            for (int c = 0; c < R[i].n; c++)
+                l0[R[i].idx[c]] += R[i].w[c] * res[(long)i * nt + k];
+#pragma omp parallel for
+        for (long q = 0; q < N; q++) l0[q] /= P->m[q] * (1.0 + 0.5 * P->sig[q] * dt);
+        if (qbar)
+            for (int s = 0; s < nsrc; s++)
+                qbar[(long)s * nt + (k - 1)] = dt * dt * sample(&S[s], l0);
+        if (grad) {
+            const double *u2 = P->store + (long)k * N, *u1 = P->store + (long)(k - 1) * N;
+            const double *u0 = k >= 2 ? P->store + (long)(k - 2) * N : NULL;
+#pragma omp parallel for
+            for (long q = 0; q < N; q++) {
+                double a = 1.0 + 0.5 * P->sig[q] * dt, b = 1.0 - 0.5 * P->sig[q] * dt;
+                grad[q] -= l0[q] * (a * u2[q] - 2.0 * u1[q] + (u0 ? b * u0[q] : 0.0));
+            }
+        }
+        double *t = l2; l2 = l1; l1 = l0; l0 = t;
+    }
+    free(l0); free(l1); free(l2); free(Ll); free(S); free(R);
+    return OR_OK;
+}
+
+int or_ac_adjoint(or_prob *P, int nrec, const float *rec, const double *traces,
+                  int nsrc, const float *src, double *qbar)
+{
+    if (P->d.kind != 3) return OR_EINVAL;
+    return ac_adjoint_core(P, nrec, rec, traces, nsrc, src, qbar, NULL);
+}
+
+/* dJ/dm on the physical grid (fold of the computational gradient),
+ * J = 1/2 || F(m) q - d_obs ||^2; grad_comp (may be NULL) the unfolded one. */
+int or_ac_gradient(or_prob *P, int nsrc, const float *src, const float *wav,
+                   int nrec, const float *rec, const double *d_obs,
+                   double *grad_phys, double *misfit, double *grad_comp)
+{
+    if (P->d.kind != 3) return OR_EINVAL;
+    int nt = P->d.nt;
+    double *tr = dalloc((long)nrec * nt);
+    int rc = or_ac_forward(P, nsrc, src, wav, nrec, rec, tr, 1);
+    if (rc) { free(tr); return rc; }
+    double J = 0.0;
+    for (long i = 0; i < (long)nrec * nt; i++) {
+        tr[i] -= d_obs[i];
+        J += 0.5 * tr[i] * tr[i];
+    }
+    if (misfit) *misfit = J;
+    double *g = dalloc(P->N);
+    rc = ac_adjoint_core(P, nrec, rec, tr, nsrc, src, NULL, g);
+    if (!rc) {
+        if (grad_comp) memcpy(grad_comp, g, sizeof(double) * P->N);
+        if (grad_phys) fold(g, grad_phys, P);
+    }
+    free(g); free(tr);
+    free(P->store); P->store = NULL; P->stored = 0;
+    return rc;
+}
+
+/* (dJ/dm, dJ/dwavelet) for a given trace residual (autograd backward). */
+int or_ac_backward(or_prob *P, int nsrc, const float *src, const float *wav,
+                   int nrec, const float *rec, const double *resid,
+                   double *grad_phys, double *qbar)
+{
+    if (P->d.kind != 3) return OR_EINVAL;
+    int nt = P->d.nt;
+    double *tr = dalloc((long)nrec * nt);
+    int rc = or_ac_forward(P, nsrc, src, wav, nrec, rec, tr, 1);
+    free(tr);
+    if (rc) return rc;
+    double *g = dalloc(P->N);
+    rc = ac_adjoint_core(P, nrec, rec, resid, nsrc, src, qbar, g);
+    if (!rc && grad_phys) fold(g, grad_phys, P);
+    free(g);
+    free(P->store); P->store = NULL; P->stored = 0;
+    return rc;
+}
+
+/* nsteps source-free steps of a double state (u0, u1) = (u^{n-1}, u^n) in
+ * place: afterwards u1 holds the newest level and u0 the one before. */
+int or_ac_step_state_d(or_prob *P, double *u0, double *u1, int nsteps)
+{
+    if (P->d.kind != 3) return OR_EINVAL;
+    double *u2 = dalloc(P->N);
+    for (int i = 0; i < nsteps; i++) {
+        ac_step(P, u0, u1, u2);
+        memcpy(u0, u1, sizeof(double) * P->N);
+        memcpy(u1, u2, sizeof(double) * P->N);
+    }
+    free(u2);
+    return OR_OK;
+}
+
+/* one step evaluated at npts points idx[] (computational-grid linear
+ * indices) from a float32 state (u0, u1); model: the PHYSICAL float32 vp
+ * (edge replication by clamped indices); out[i] = u^{n+1} at idx[i]. */
+int or_ac_step_points(const or_desc *d, const float *vp, const float *u0, const float *u1,
+                      int npts, const long *idx, double *out)
+{
+    if (d->kind != 3) return OR_EINVAL;
+    const int NX = d->nx + 2 * d->nbl, NY = d->ny + 2 * d->nbl, NZ = d->nz + 2 * d->nbl, M = d->so / 2;
+    double w[MAXM + 1];
+    if (or_weights_d2(d->so, w)) return OR_EINVAL;
+    long np = (long)d->nx * d->ny * d->nz;
+    double vmax = 0.0;
+    for (long q = 0; q < np; q++)
+        if (1000.0 * (double)vp[q] > vmax) vmax = 1000.0 * (double)vp[q];
+    if (d->vdamp > 0) vmax = d->vdamp;
+    or_prob Pd; memset(&Pd, 0, sizeof(Pd)); Pd.d = *d;
+    const double dt = d->dt, h2 = d->h * d->h;
+#pragma omp parallel for
+    for (int i = 0; i < npts; i++) {
+        long q = idx[i];
+        int z = (int)(q % NZ), y = (int)((q / NZ) % NY), x = (int)(q / ((long)NZ * NY));
+        double L = 3.0 * w[0] * u1[q];
+        for (int k = 1; k <= M; k++) {
+            int c[6][3] = {{x + k, y, z}, {x - k, y, z}, {x, y + k, z}, {x, y - k, z}, {x, y, z + k}, {x, y, z - k}};
+            for (int j = 0; j < 6; j++) {
+                int a = c[j][0], b = c[j][1], e = c[j][2];
+                if (a < 0 || a >= NX || b < 0 || b >= NY || e < 0 || e >= NZ) continue;
+                L += w[k] * u1[((long)a * NY + b) * NZ + e];
+            }
+        }
+        L /= h2;
+        int pi = clampi(x - d->nbl, 0, d->nx - 1), pj = clampi(y - d->nbl, 0, d->ny - 1),
+            pk = clampi(z - d->nbl, 0, d->nz - 1);
+        double v = 1000.0 * (double)vp[((long)pi * d->ny + pj) * d->nz + pk];
+        double m = 1.0 / (v * v), sg = tti_sigma(&Pd, x, y, z, vmax);
+        double A = m * (1.0 + 0.5 * sg * dt), B = m * (1.0 - 0.5 * sg * dt);
+        out[i] = (dt * dt * L + 2.0 * m * u1[q] - B * u0[q]) / A;
+    }
     return OR_OK;
 }
 

@@ -24,6 +24,7 @@ import numpy as np
 
 TTI = 1
 ELASTIC = 2
+ACOUSTIC = 3
 
 DEG = math.pi / 180.0
 
@@ -113,7 +114,7 @@ class Problem:
     so: int
     nt: int
     dt: float
-    model: dict            # TTI: vp, eps, delta, theta, phi ; ELASTIC: vp, vs, rho
+    model: dict            # TTI: vp, eps, delta, theta, phi ; ELASTIC: vp, vs, rho ; ACOUSTIC: vp
     src: np.ndarray        # [nsrc, 3] float32
     wavelet: np.ndarray    # [nsrc, nt] float32
     rec: np.ndarray        # [nrec, 3] float32
@@ -127,8 +128,8 @@ class Problem:
                 * (self.nz + 2 * self.nbl))
 
     def model_list(self):
-        keys = ("vp", "eps", "delta", "theta", "phi") if self.kind == TTI \
-            else ("vp", "vs", "rho")
+        keys = {TTI: ("vp", "eps", "delta", "theta", "phi"), ELASTIC: ("vp", "vs", "rho"),
+                ACOUSTIC: ("vp",)}[self.kind]
         return [np.ascontiguousarray(self.model[k], dtype=np.float32) for k in keys]
 
 
@@ -146,6 +147,17 @@ def two_layer_tti(nx, ny, nz, h, z_interface, top, bottom) -> dict:
     return out
 
 
+def layered_vp(nx, ny, nz, seed, nlayers=10, vmin=1.5, vmax=4.5, noise_sigma=16.0,
+               noise_amp=0.25) -> np.ndarray:
+    """``nlayers`` flat layers increasing from vmin to vmax [km/s] with depth,
+    plus smooth noise, clipped to [vmin, vmax] (float64)."""
+    z = np.arange(nz) / max(nz - 1, 1)
+    layer = np.minimum((z * nlayers).astype(int), nlayers - 1)
+    vlayer = vmin + (vmax - vmin) * layer / max(nlayers - 1, 1)
+    noise = smooth_noise((nx, ny, nz), noise_sigma, seed) * 2.0 - 1.0
+    return np.clip(vlayer[None, None, :] + noise_amp * (vmax - vmin) * noise, vmin, vmax)
+
+
 def layered_tti(nx, ny, nz, seed, nlayers=10, vmin=1.5, vmax=4.5,
                 noise_sigma=16.0, noise_amp=0.25, smooth_sigma=4.0,
                 eps_max=0.3, theta_max_deg=40.0) -> dict:
@@ -157,11 +169,7 @@ def layered_tti(nx, ny, nz, seed, nlayers=10, vmin=1.5, vmax=4.5,
     eps >= delta); tilt = dip of the smoothed-velocity iso-surfaces clipped
     to theta_max; azimuth = direction of the lateral gradient in [0, 90 deg].
     """
-    z = np.arange(nz) / max(nz - 1, 1)
-    layer = np.minimum((z * nlayers).astype(int), nlayers - 1)
-    vlayer = vmin + (vmax - vmin) * layer / max(nlayers - 1, 1)
-    noise = smooth_noise((nx, ny, nz), noise_sigma, seed) * 2.0 - 1.0
-    vp = np.clip(vlayer[None, None, :] + noise_amp * (vmax - vmin) * noise, vmin, vmax)
+    vp = layered_vp(nx, ny, nz, seed, nlayers, vmin, vmax, noise_sigma, noise_amp)
     vs_ = vp.copy()
     for ax in range(3):
         vs_ = _gauss_axis(vs_, smooth_sigma, ax)
@@ -375,4 +383,70 @@ def tti_batch_shots(nshots=8, nt=150, seed=20045, size_range=(200, 600), nz=300,
         p0 = Problem(TTI, nx, ny, nz, nbl, h, so, nt, dt, start, src, wav, rec,
                      name=name.replace("window", "window-start"))
         shots.append((true, p0))
+    return shots
+
+
+# --------------------------------------------------------------------------
+# isotropic acoustic workloads
+# --------------------------------------------------------------------------
+def acoustic_layered(nx=800, ny=800, nz=400, h=12.5, nbl=40, so=12, nt=3000, f0=12.0,
+                     seed=20046, rec_dx=40.0, rec_n=250) -> Problem:
+    """Isotropic acoustic forward on the layered-plus-noise velocity of the
+    industry-scale TTI recipe (same grid, order and geometry)."""
+    vp = np.ascontiguousarray(layered_vp(nx, ny, nz, seed), dtype=np.float32)
+    dt = cfl_dt(h, float(vp.max()))
+    src = np.array([[(nx // 2) * h, (ny // 2) * h, 2 * h]], np.float32)
+    wav = ricker(f0, dt, nt)[None, :]
+    n = min(rec_n, int(((nx - 1) * h) // rec_dx) + 1)
+    m = min(rec_n, int(((ny - 1) * h) // rec_dx) + 1)
+    rec = carpet_receivers(0.0, 0.0, rec_dx, n, m, h)
+    return Problem(ACOUSTIC, nx, ny, nz, nbl, h, so, nt, dt, {"vp": vp}, src, wav, rec,
+                   name=f"acoustic-layered-{nx}x{ny}x{nz}-so{so}-nt{nt}")
+
+
+def acoustic_small(shape=(37, 29, 45), nbl=7, h=10.0, so=8, nt=70, seed=3):
+    """Small heterogeneous acoustic problem (parity tests): layered-plus-noise
+    velocity, two sources, a carpet of receivers."""
+    nx, ny, nz = shape
+    vp = np.ascontiguousarray(layered_vp(nx, ny, nz, seed, noise_sigma=3.0), dtype=np.float32)
+    dt = cfl_dt(h, float(vp.max()))
+    src = np.array([[nx * h * 0.45 + 1.3, ny * h * 0.55 - 2.1, 3.3 * h],
+                    [nx * h * 0.25, ny * h * 0.3 + 0.7, nz * h * 0.6]], np.float32)
+    wav = np.vstack([ricker(25.0, dt, nt), 0.6 * ricker(18.0, dt, nt)]).astype(np.float32)
+    rec = carpet_receivers(5.2, 7.1, 3.7 * h, 9, 7, 1.9 * h)
+    return Problem(ACOUSTIC, nx, ny, nz, nbl, h, so, nt, dt, {"vp": vp}, src, wav, rec,
+                   name=f"acoustic-small-{nx}x{ny}x{nz}-so{so}")
+
+
+def acoustic_rtm_shots(nshots=8, nt=150, seed=20047, size_range=(200, 600), nz=300, h=12.5,
+                       nbl=40, so=12, f0=12.0, global_cells=(1000, 1000, 500)):
+    """RTM over many shots: ``nshots`` acoustic shots on windows with
+    nx, ny ~ U[size_range], nz fixed, at random offsets in the undulating
+    10-layer model (velocity only) of ``global_cells`` cells at h; source at
+    the window centre, 25 m deep; receivers every 4 cells at depth h.  Each
+    entry is (true problem, migration problem, (ox, oy, 0)): the migration
+    velocity increases linearly with depth over the velocity range.  The
+    stacked image is the sum of the shots' dJ/dm at their offsets in the
+    global grid."""
+    rng = np.random.default_rng(seed)
+    gx, gy, gz = global_cells
+    model = UndulatingTTI(seed, extent=(gx * h, gy * h, gz * h))
+    dt = cfl_dt(h, model.vmax)
+    shots = []
+    for s in range(nshots):
+        nx, ny = (int(v) for v in rng.integers(size_range[0], size_range[1] + 1, 2))
+        ox = int(rng.integers(0, gx - nx + 1))
+        oy = int(rng.integers(0, gy - ny + 1))
+        vp = model.window(ox, oy, nx, ny, nz, h)["vp"]
+        src = np.array([[(nx // 2) * h, (ny // 2) * h, 25.0]], np.float32)
+        rec = carpet_receivers(0.0, 0.0, 4 * h, (nx - 1) // 4 + 1, (ny - 1) // 4 + 1, h)
+        wav = ricker(f0, dt, nt)[None, :]
+        name = f"acoustic-window-{nx}x{ny}x{nz}-at-{ox},{oy}-so{so}-nt{nt}"
+        true = Problem(ACOUSTIC, nx, ny, nz, nbl, h, so, nt, dt, {"vp": vp}, src, wav, rec, name=name)
+        z = (np.arange(nz) / max(nz - 1, 1)).astype(np.float32)
+        v0 = model.vmin + (model.vmax - model.vmin) * z
+        vmig = np.ascontiguousarray(np.broadcast_to(v0[None, None, :], (nx, ny, nz)), dtype=np.float32)
+        p0 = Problem(ACOUSTIC, nx, ny, nz, nbl, h, so, nt, dt, {"vp": vmig}, src, wav, rec,
+                     name=name.replace("window", "window-migration"))
+        shots.append((true, p0, (ox, oy, 0)))
     return shots
