@@ -57,7 +57,10 @@ enum {
                              or a call that needs a saved forward run      */
 };
 
-enum { PROP_TTI = 1, PROP_ELASTIC = 2 };
+/* PROP_ACOUSTIC: the isotropic acoustic equation of Sec. II-A, Eq. (acou),
+ * m u_tt - laplace(u) + damp u_t = q, laplace = sum over axes of the centred
+ * second derivative of the space order, damped like TTI. */
+enum { PROP_TTI = 1, PROP_ELASTIC = 2, PROP_ACOUSTIC = 3 };
 
 /* Storage of forward wavefields for the gradient (Sec. III: full storage in
  * memory, or checkpointing).  CKPT_* keep the full state every
@@ -66,15 +69,15 @@ enum { PROP_TTI = 1, PROP_ELASTIC = 2 };
 enum { SNAP_FULL_FP32 = 0, SNAP_CKPT_FP32 = 1, SNAP_CKPT_BF16 = 2, SNAP_CKPT_FP16 = 3 };
 
 typedef struct {
-    int kind;            /* PROP_TTI or PROP_ELASTIC                          */
+    int kind;            /* PROP_TTI, PROP_ELASTIC or PROP_ACOUSTIC           */
     int nx, ny, nz;      /* physical grid points (>= 1)                       */
     int nbl;             /* absorbing cells added on every face (>= 0)        */
     float h;             /* grid spacing [m] (> 0)                            */
     int space_order;     /* 4, 8, 12 or 16                                    */
     int nt;              /* time samples per trace (>= 2)                     */
     float dt;            /* time step [s]; <= 0 selects dt = 0.4 h / vmax     */
-    float vdamp;         /* TTI damping reference velocity [m/s]; <= 0: the
-                            model's max vp sqrt(1+2 eps)                      */
+    float vdamp;         /* TTI/acoustic damping reference velocity [m/s];
+                            <= 0: the model's max vp sqrt(1+2 eps) (max vp)  */
     int snap_mode;       /* SNAP_* for prop_gradient / prop_backward          */
     int ckpt_interval;   /* steps between checkpoints; 0 = ceil(sqrt(nt))     */
     int check_nan;       /* nonzero: stencil kernels flag NaN/Inf, reported
@@ -84,6 +87,7 @@ typedef struct {
 /* Create a propagator.  model points to the PHYSICAL-grid float32 arrays
  *   TTI:     vp [km/s], epsilon, delta, theta (tilt) [rad], phi (azimuth) [rad]
  *   ELASTIC: vp [km/s], vs [km/s], rho [g/cc]
+ *   ACOUSTIC: vp [km/s]
  * (Sec. III-A: 4 Thomsen/angle parameters + velocity; Sec. IV: Lame
  * parameters and density, lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2).
  * The arrays are copied; they may be freed after the call.
@@ -100,8 +104,10 @@ int prop_create(const prop_desc *desc, const float *const *model, void *cuda_str
  *   src_xyz  [nsrc][3]   source positions
  *   rec_xyz  [nrec][3]   receiver positions
  *   traces   [nrec][nt]  output: TTI records p; ELASTIC records
- *                        txx + tyy + tzz (trace of stress, Sec. IV-B).
- * TTI injects q into both p and r; ELASTIC injects dt q into txx, tyy, tzz
+ *                        txx + tyy + tzz (trace of stress, Sec. IV-B);
+ *                        ACOUSTIC records u.
+ * TTI injects q into both p and r; ACOUSTIC into u (both with dt^2 / A,
+ * A = m (1 + sig dt/2)); ELASTIC injects dt q into txx, tyy, tzz
  * (explosive source).  nsrc, nrec >= 1. */
 int prop_forward(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,
                  const float *rec_xyz, int nrec, float *traces);
@@ -114,8 +120,9 @@ int prop_adjoint(prop_t *p, const float *traces_in, const float *rec_xyz, int nr
 /* FWI gradient of J = 1/2 ||F(model) q - d_obs||^2 by the adjoint-state
  * method (zero-lag cross-correlation of forward and adjoint wavefields).
  *   d_obs  [nrec][nt]
- *   grad   TTI: [nx][ny][nz] dJ/dm, m = 1/vp^2 [s^2/m^2] on the physical grid
- *          (layer contributions folded back through the edge replication);
+ *   grad   TTI, ACOUSTIC: [nx][ny][nz] dJ/dm, m = 1/vp^2 [s^2/m^2] on the
+ *          physical grid (layer contributions folded back through the edge
+ *          replication);
  *          ELASTIC: [3][nx][ny][nz] dJ/d(lambda [Pa], mu [Pa], b = 1/rho [m^3/kg])
  *   misfit J (may be NULL).
  * Forward wavefields are kept according to desc.snap_mode. */
@@ -176,6 +183,17 @@ int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wa
                         const int *nrec, const float *const *d_obs, float *const *grad,
                         double *misfit, size_t budget_bytes);
 
+/* Image stacking over shots (reverse-time migration of many experiments,
+ * Sec. III-B): adds weight * image ([nx][ny][nz], the handle's physical
+ * grid, e.g. its dJ/dm; host or device) into stack ([sx][sy][sz] =
+ * stack_dims, DEVICE memory) with the window's first point at offset
+ * (ox, oy, oz), on the handle's stream; returns when done.  The caller
+ * serialises calls that target the same stack (a handle's calls are
+ * ordered on its stream).  PROP_EINVAL for NULL arguments, a host stack or
+ * a window that does not fit. */
+int prop_stack_image(prop_t *p, const float *image, float *stack, const int *stack_dims,
+                     const int *offset, float weight);
+
 /* Device bytes a prop_gradient call with nrec receivers would allocate on
  * top of what the handle holds (0 for p == NULL). */
 size_t prop_gradient_bytes(const prop_t *p, int nrec);
@@ -188,6 +206,7 @@ int prop_plan_waves(const size_t *bytes, int n, size_t budget, int *wave_of);
 
 /* Wavefield state access (computational grid, float32 [NX][NY][NZ] each):
  *   TTI:     fields[0..3] = p^n, r^n, p^{n-1}, r^{n-1}
+ *   ACOUSTIC: fields[0..1] = u^n, u^{n-1}
  *   ELASTIC: fields[0..8] = vx vy vz txx tyy tzz txy txz tyz
  * prop_step advances nsteps steps without sources or receivers (adjoint != 0:
  * transposed step, state holds the adjoint fields in the same order). */

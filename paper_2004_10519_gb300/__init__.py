@@ -1,4 +1,4 @@
-"""waveprop: TTI and elastic wave propagators on one GB300 (sm_103a).
+"""waveprop: TTI, elastic and isotropic acoustic wave propagators on one GB300 (sm_103a).
 
 Thin ctypes binding of ``libwaveprop.so`` (C ABI in ``include/waveprop.h``).
 Every step of the propagators runs in the library's CUDA kernels; this module
@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libwaveprop.so")
 
 PROP_OK, PROP_EINVAL, PROP_ENOMEM, PROP_ECUDA, PROP_EUNSTABLE, PROP_ETIMEOUT, PROP_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-PROP_TTI, PROP_ELASTIC = 1, 2
+PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC = 1, 2, 3
 SNAP_FULL_FP32, SNAP_CKPT_FP32, SNAP_CKPT_BF16, SNAP_CKPT_FP16 = 0, 1, 2, 3
 ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA",
              -4: "PROP_EUNSTABLE", -5: "PROP_ETIMEOUT", -6: "PROP_ESTATE"}
@@ -29,7 +29,7 @@ ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
                "prop_last_error", "prop_forward_noalloc", "prop_tile_planes",
                "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves",
-               "prop_gradient_aniso")
+               "prop_gradient_aniso", "prop_stack_image")
 
 
 class PropDesc(C.Structure):
@@ -79,6 +79,7 @@ def lib():
         L.prop_gradient_bytes.restype = C.c_size_t
         L.prop_gradient_bytes.argtypes = [vp, C.c_int]
         L.prop_plan_waves.argtypes = [C.POINTER(C.c_size_t), C.c_int, C.c_size_t, C.POINTER(C.c_int)]
+        L.prop_stack_image.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_float]
         L.prop_destroy.argtypes = [vp]
         L.prop_last_error.restype = C.c_char_p
         L.prop_last_error.argtypes = [vp]
@@ -140,9 +141,10 @@ def _stream_of(*xs):
 class Propagator:
     """Handle on one propagator (``prop_t``).
 
-    kind: PROP_TTI or PROP_ELASTIC; model: list of physical-grid float32
-    arrays (TTI: vp, eps, delta, theta, phi; elastic: vp, vs, rho) as numpy
-    arrays or torch tensors (host or device)."""
+    kind: PROP_TTI, PROP_ELASTIC or PROP_ACOUSTIC; model: list of
+    physical-grid float32 arrays (TTI: vp, eps, delta, theta, phi; elastic:
+    vp, vs, rho; acoustic: vp) as numpy arrays or torch tensors (host or
+    device)."""
 
     def __init__(self, kind, shape, nbl, h, space_order, nt, model, dt=0.0, vdamp=0.0,
                  snap_mode=SNAP_FULL_FP32, ckpt_interval=0, check_nan=0, stream=None):
@@ -172,7 +174,8 @@ class Propagator:
 
     @classmethod
     def from_problem(cls, prob, model=None, **kw):
-        keys = ("vp", "eps", "delta", "theta", "phi") if prob.kind == PROP_TTI else ("vp", "vs", "rho")
+        keys = {PROP_TTI: ("vp", "eps", "delta", "theta", "phi"), PROP_ELASTIC: ("vp", "vs", "rho"),
+                PROP_ACOUSTIC: ("vp",)}[prob.kind]
         ml = model if model is not None else [prob.model[k] for k in keys]
         kw.setdefault("dt", prob.dt)
         kw.setdefault("vdamp", getattr(prob, "vdamp", 0.0) or 0.0)
@@ -231,7 +234,7 @@ class Propagator:
 
     def _gshape(self):
         nx, ny, nz = self.shape
-        return (nx, ny, nz) if self.kind == PROP_TTI else (3, nx, ny, nz)
+        return (3, nx, ny, nz) if self.kind == PROP_ELASTIC else (nx, ny, nz)
 
     def gradient(self, wavelet, src, rec, d_obs, out=None):
         src_a, rec_a = _Arg(src), _Arg(rec)
@@ -261,6 +264,17 @@ class Propagator:
         self._check(lib().prop_gradient_aniso(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, d.ptr,
                                               o.ptr, C.byref(J)))
         return out, J.value
+
+    def stack_image(self, image, stack, offset, weight=1.0):
+        """Add ``weight * image`` (this handle's physical grid) into the device
+        array ``stack`` with the window's first point at ``offset``
+        (``prop_stack_image``)."""
+        im = _Arg(image, int(np.prod(self.shape)))
+        st = _Arg(stack, writable=True)
+        dims = (C.c_int * 3)(*[int(v) for v in stack.shape])
+        off = (C.c_int * 3)(*[int(v) for v in offset])
+        self._check(lib().prop_stack_image(self.h, im.ptr, st.ptr, dims, off, float(weight)))
+        return stack
 
     def backward(self, resid, grad_out=True, src_grad_out=True, nsrc=None):
         r = _Arg(resid)

@@ -1,4 +1,4 @@
-"""Differentiable TTI and elastic modelling for PyTorch.
+"""Differentiable TTI, elastic and isotropic acoustic modelling for PyTorch.
 
 ``TTIModelling.apply(m, wavelet, spec)`` maps squared slowness m = 1/vp^2
 [s^2/m^2] (physical grid) and the source wavelets to receiver traces.  Its
@@ -10,7 +10,9 @@ full FP32 storage, or checkpoints (FP32, BF16 or FP16 with one scale per
 field) with FP32 recomputation of each segment during the adjoint sweep.
 
 ``ElasticModelling.apply(lam, mu, b, wavelet, spec)`` does the same for the
-elastic system with respect to the Lame parameters and buoyancy.
+elastic system with respect to the Lame parameters and buoyancy, and
+``AcousticModelling.apply(m, wavelet, spec)`` for the isotropic acoustic
+equation of Sec. II-A (Eq. acou).
 """
 from __future__ import annotations
 
@@ -19,7 +21,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import (PROP_ELASTIC, PROP_TTI, SNAP_FULL_FP32, Propagator)
+from . import (PROP_ACOUSTIC, PROP_ELASTIC, PROP_TTI, SNAP_FULL_FP32, Propagator)
 
 
 @dataclass
@@ -54,6 +56,29 @@ class TTIModelling(torch.autograd.Function):
         model = [vp.contiguous(), spec.eps, spec.delta, spec.theta, spec.phi]
         prop = Propagator(PROP_TTI, spec.shape, spec.nbl, spec.h, spec.space_order, spec.nt,
                           model, dt=spec.dt, vdamp=spec.vdamp, snap_mode=spec.snap_mode,
+                          ckpt_interval=spec.ckpt_interval, stream=_stream(m))
+        traces = prop.forward(wavelet.detach().contiguous(), spec.src, spec.rec, save=True)
+        ctx.prop = prop
+        ctx.nsrc = spec.src.shape[0]
+        return traces
+
+    @staticmethod
+    def backward(ctx, gtr):
+        prop = ctx.prop
+        gm, gw = prop.backward(gtr.contiguous(), nsrc=ctx.nsrc)
+        prop.close()
+        ctx.prop = None
+        return gm, gw, None
+
+
+class AcousticModelling(torch.autograd.Function):
+    """m = 1/vp^2 [s^2/m^2] on the physical grid and the wavelets -> traces."""
+
+    @staticmethod
+    def forward(ctx, m, wavelet, spec: Spec):
+        vp = torch.rsqrt(m.detach().to(torch.float32)) / 1000.0          # km/s
+        prop = Propagator(PROP_ACOUSTIC, spec.shape, spec.nbl, spec.h, spec.space_order, spec.nt,
+                          [vp.contiguous()], dt=spec.dt, vdamp=spec.vdamp, snap_mode=spec.snap_mode,
                           ckpt_interval=spec.ckpt_interval, stream=_stream(m))
         traces = prop.forward(wavelet.detach().contiguous(), spec.src, spec.rec, save=True)
         ctx.prop = prop

@@ -32,6 +32,7 @@ struct GridDev {
 struct FDW {
     float c[WP_MAXM];        // centred   c_1..c_M
     float b[WP_MAXM];        // staggered b_1..b_M
+    float d2[WP_MAXM + 1];   // centred second derivative d2_0..d2_M (acoustic)
 };
 
 // Sparse-point tables (device).  Record: nrec x 8 (index, weight) pairs.
@@ -113,6 +114,10 @@ int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 int el_launch_fast(prop_s *P, float *const *S, float dt_sign);
 // TMA-fed passes (stencil_tma.cu): usable when NZ % 4 == 0
 bool tma_usable(const prop_s *P);
+// acoustic step (S[0] = u^n, S[1] = u^{n-1} <- u^{n+1}); grad != NULL:
+// transposed step with imaging grad -= dt^2 uf (L lam) / m
+int acu_launch_step(prop_s *P, float *const *S, const float *uf, float *grad);
+int acu_launch_tma(prop_s *P, float *const *S, const float *uf, float *grad);
 int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
 // TTI imaging of the coupling matrix (TMA passes): with the forward field
 // (up, ur) at level n and the adjoint field (lp, lr) at level n+1,
@@ -166,6 +171,8 @@ void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2);
 void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long n);
 double k_sumsq_host(prop_s *P, const float *a, long long n);
 void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr);
+// stack[off + (i, j, k)] += weight * img[i][j][k] over the handle's physical grid
+void k_stack(prop_s *P, const float *img, float *stack, const int *gdims, const int *off, float weight);
 // snapshot codec
 void k_snap_encode(prop_s *P, const float *in, long long n, uint16_t *out, float *scale_dev,
                    int bf16, float *scratch);

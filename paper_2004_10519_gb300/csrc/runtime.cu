@@ -107,6 +107,34 @@ bool fd_weights(int M, float *c, float *bst)
     return true;
 }
 
+// centred second derivative, closed form:
+//   d2_k = 2 (-1)^(k+1) (M!)^2 / (k^2 (M-k)! (M+k)!),  d2_0 = -2 sum_k d2_k
+static void d2_weights(int M, float *d2)
+{
+    double s = 0.0;
+    for (int k = 1; k <= M; k++) {
+        double r = 1.0;                       // (M!)^2 / ((M-k)! (M+k)!)
+        for (int j = 1; j <= k; j++) r *= (double)(M - k + j) / (double)(M + j);
+        const double v = (k % 2 ? 2.0 : -2.0) * r / ((double)k * k);
+        d2[k] = (float)v;
+        s += v;
+    }
+    d2[0] = (float)(-2.0 * s);
+    for (int k = M + 1; k <= WP_MAXM; k++) d2[k] = 0.f;
+}
+
+// max over kappa of |d2_0 + 2 sum_k d2_k cos(k kappa)| (1D symbol of h^2 D2)
+static double symbol2_max(const float *d2, int M)
+{
+    double mx = 0.0;
+    for (int i = 0; i <= 4096; i++) {
+        double kap = M_PI * i / 4096.0, s = d2[0];
+        for (int k = 1; k <= M; k++) s += 2.0 * d2[k] * cos(k * kap);
+        mx = std::max(mx, fabs(s));
+    }
+    return mx;
+}
+
 // max over kappa of |sum_k 2 w_k sin(s_k kappa)| (s_k = k or k - 1/2)
 double symbol_max(const float *w, int M, bool stag)
 {
@@ -133,7 +161,7 @@ std::vector<float> layer_tables(const GridDev &g, int kind)
     std::vector<float> t;
     for (int a = 0; a < 3; a++)
         for (int i = 0; i < NN[a]; i++) {
-            if (kind == PROP_TTI) {
+            if (kind != PROP_ELASTIC) {                  // TTI, acoustic: damping rate
                 const double d = g.nbl > 0 ? depth(i, PN[a]) / g.nbl : 0.0;
                 t.push_back((float)((double)g.sig0 * d * d));
             } else {
@@ -183,7 +211,8 @@ static int copy_out(prop_s *P, float *dst, const float *src_dev, size_t n)
     return PROP_OK;
 }
 
-static int nfields(const prop_s *P) { return P->d.kind == PROP_TTI ? 4 : 9; }
+// state fields: TTI (p, r) at two levels, acoustic u at two levels, elastic 9
+static int nfields(const prop_s *P) { return P->d.kind == PROP_TTI ? 4 : (P->d.kind == PROP_ACOUSTIC ? 2 : 9); }
 
 // ---------------------------------------------------------------------------
 // profiling
@@ -327,7 +356,7 @@ static int autotune_xchunk(prop_s *P)
     if (std::find(cand.begin(), cand.end(), heuristic) == cand.end()) cand.push_back(heuristic);
     float *s[9];
     for (int i = 0; i < 9; i++) s[i] = P->st[i];
-    WP_TRY(zero_fields(P, s, P->d.kind == PROP_TTI ? 4 : 9));
+    WP_TRY(zero_fields(P, s, nfields(P)));
     cudaEvent_t e0, e1;
     WP_CK(P, cudaEventCreate(&e0));
     WP_CK(P, cudaEventCreate(&e1));
@@ -350,7 +379,7 @@ static int autotune_xchunk(prop_s *P)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int i = 0; i < 9; i++) P->st[i] = s[i];
-    WP_TRY(zero_fields(P, s, P->d.kind == PROP_TTI ? 4 : 9));
+    WP_TRY(zero_fields(P, s, nfields(P)));
     P->xchunk = best;
     std::lock_guard<std::mutex> lk(g_tune_mtx);
     g_tune[key] = best;
@@ -367,7 +396,8 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
 {
     P->d = *d;
     const int so = d->space_order;
-    if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC) return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI or PROP_ELASTIC");
+    if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC && d->kind != PROP_ACOUSTIC)
+        return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI, PROP_ELASTIC or PROP_ACOUSTIC");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return wp_fail(P, PROP_EINVAL, "grid sizes must be >= 1");
     if (d->nbl < 0) return wp_fail(P, PROP_EINVAL, "nbl must be >= 0");
     if (!(d->h > 0.f) || !std::isfinite(d->h)) return wp_fail(P, PROP_EINVAL, "h must be > 0");
@@ -376,7 +406,7 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     if (d->snap_mode < 0 || d->snap_mode > 3) return wp_fail(P, PROP_EINVAL, "snap_mode out of range");
     if (d->ckpt_interval < 0) return wp_fail(P, PROP_EINVAL, "ckpt_interval must be >= 0");
     if (!model) return wp_fail(P, PROP_EINVAL, "model is NULL");
-    const int nf = d->kind == PROP_TTI ? 5 : 3;
+    const int nf = d->kind == PROP_TTI ? 5 : (d->kind == PROP_ACOUSTIC ? 1 : 3);
     for (int i = 0; i < nf; i++)
         if (!model[i]) return wp_fail(P, PROP_EINVAL, "model array is NULL");
     P->M = so / 2;
@@ -388,6 +418,7 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     if (g.N >= (1LL << 32)) return wp_fail(P, PROP_EINVAL, "computational grid above 2^32 - 1 points");
     g.h = d->h; g.ih = 1.f / d->h;
     if (!fd_weights(P->M, P->w.c, P->w.b)) return wp_fail(P, PROP_EINVAL, "FD weights");
+    d2_weights(P->M, P->w.d2);
 
     // model on the host for validation
     const size_t np = (size_t)d->nx * d->ny * d->nz;
@@ -407,6 +438,8 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
             if (e < dl) return wp_fail(P, PROP_EINVAL, "epsilon < delta somewhere (TTI stability needs eps >= delta)");
             if (1.0 + 2.0 * dl <= 0.0) return wp_fail(P, PROP_EINVAL, "1 + 2 delta must be > 0");
             vmax = std::max(vmax, 1000.0 * vp * sqrt(1.0 + 2.0 * e));
+        } else if (d->kind == PROP_ACOUSTIC) {
+            vmax = std::max(vmax, 1000.0 * vp);
         } else {
             const float vs = hm[1][q], rho = hm[2][q];
             if (!(vs >= 0.f) || !std::isfinite(vs)) return wp_fail(P, PROP_EINVAL, "vs must be finite and >= 0");
@@ -420,8 +453,10 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     g.dt = (float)dt;
     P->d.dt = g.dt;
     // CFL: vmax dt / h <= 2 / (sqrt(3) max|symbol|)
+    // (acoustic: vmax dt / h <= 2 / sqrt(3 max|symbol of h^2 D2|))
     const bool stag = d->kind == PROP_ELASTIC;
-    const double lim = 2.0 / (sqrt(3.0) * symbol_max(stag ? P->w.b : P->w.c, P->M, stag));
+    const double lim = d->kind == PROP_ACOUSTIC ? 2.0 / sqrt(3.0 * symbol2_max(P->w.d2, P->M))
+                                                : 2.0 / (sqrt(3.0) * symbol_max(stag ? P->w.b : P->w.c, P->M, stag));
     const double cour = vmax * dt / d->h;
     if (cour > lim) {
         char buf[200];
@@ -454,6 +489,8 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
         WP_MALLOC(P, P->nrm[0], N * sizeof(float), "symmetry axis");
         WP_MALLOC(P, P->nrm[1], N * sizeof(float), "symmetry axis");
         k_normals(P);
+    } else if (d->kind == PROP_ACOUSTIC) {
+        WP_TRY(upload(0, P->m, 1000.f, 1));
     } else {
         WP_TRY(upload(0, P->bu, 1.f, 0));    // vp  -> b      (k_lame)
         WP_TRY(upload(1, P->lam, 1.f, 0));   // vs  -> lambda
@@ -583,6 +620,9 @@ static int step_state(prop_s *P, float **s, bool adjoint)
         WP_TRY(tti_launch_step(P, s, adjoint, nullptr, nullptr, nullptr));
         std::swap(s[0], s[2]);
         std::swap(s[1], s[3]);
+    } else if (P->d.kind == PROP_ACOUSTIC) {          // the transposed step is the same map
+        WP_TRY(acu_launch_step(P, s, nullptr, nullptr));
+        std::swap(s[0], s[1]);
     } else {
         if (adjoint) WP_TRY(ensure_tmp(P, 9));
         WP_TRY(el_launch_step(P, s, adjoint));
@@ -647,7 +687,7 @@ static int ckpt_K(const prop_s *P)
 }
 
 // slots of wavefield storage
-static size_t snap_fields(const prop_s *P) { return P->d.kind == PROP_TTI ? 2 : 9; }
+static size_t snap_fields(const prop_s *P) { return P->d.kind == PROP_TTI ? 2 : (P->d.kind == PROP_ACOUSTIC ? 1 : 9); }
 
 static int alloc_saves(prop_s *P)
 {
@@ -658,8 +698,9 @@ static int alloc_saves(prop_s *P)
     const int cf = nfields(P);               // fields per checkpoint
     switch (P->d.snap_mode) {
     case SNAP_FULL_FP32: {
-        // TTI: u^k, k = 1..nt-1 (p, r); elastic: X^k, k = 0..nt-1 (9 fields)
-        const size_t slots = P->d.kind == PROP_TTI ? (size_t)(nt - 1) : (size_t)nt;
+        // TTI: u^k, k = 1..nt-1 (p, r); acoustic: u^k, k = 1..nt-1;
+        // elastic: X^k, k = 0..nt-1 (9 fields)
+        const size_t slots = P->d.kind != PROP_ELASTIC ? (size_t)(nt - 1) : (size_t)nt;
         P->snap_bytes = slots * snap_fields(P) * N * sizeof(float);
         WP_MALLOC(P, P->snap, P->snap_bytes, "full FP32 wavefield storage");
         break;
@@ -729,23 +770,29 @@ static void inject_src(prop_s *P, const SparseDev &S, const float *wav, int n, f
     const int nt = P->d.nt;
     if (P->d.kind == PROP_TTI)
         sp_inject(P, &S, wav, nt, n, P->g.dt * P->g.dt, 1, s[0], s[1], nullptr, nullptr, nullptr);
+    else if (P->d.kind == PROP_ACOUSTIC)
+        sp_inject(P, &S, wav, nt, n, P->g.dt * P->g.dt, 1, s[0], nullptr, nullptr, nullptr, nullptr);
     else
         sp_inject(P, &S, wav, nt, n, P->g.dt, 0, s[3], s[4], s[5], nullptr, nullptr);
 }
 static void record_rec(prop_s *P, const SparseDev &R, float *const *s, float *col)
 {
-    if (P->d.kind == PROP_TTI) sp_record(P, &R, s[0], nullptr, nullptr, 1.f, col);
+    if (P->d.kind != PROP_ELASTIC) sp_record(P, &R, s[0], nullptr, nullptr, 1.f, col);
     else sp_record(P, &R, s[3], s[4], s[5], 1.f, col);
 }
 
-// One forward step n of state s (record already done).  TTI pointer rotation
-// is applied so that s[0..1] hold the new level afterwards.
+// One forward step n of state s (record already done).  TTI/acoustic
+// pointer rotation is applied so that s[0] (TTI: s[0..1]) hold the new level
+// afterwards.
 static int fwd_step(prop_s *P, float **s, const SparseDev &S, const float *wav, int n)
 {
     if (P->d.kind == PROP_TTI) {
         WP_TRY(tti_launch_step(P, s, false, nullptr, nullptr, nullptr));
         std::swap(s[0], s[2]);
         std::swap(s[1], s[3]);
+    } else if (P->d.kind == PROP_ACOUSTIC) {
+        WP_TRY(acu_launch_step(P, s, nullptr, nullptr));
+        std::swap(s[0], s[1]);
     } else {
         WP_TRY(el_launch_step(P, s, false));
     }
@@ -758,11 +805,11 @@ static int fwd_step(prop_s *P, float **s, const SparseDev &S, const float *wav, 
 static int store_full(prop_s *P, float *const *s, int lvl)
 {
     const size_t N = (size_t)P->g.N;
-    if (P->d.kind == PROP_TTI) {
+    if (P->d.kind != PROP_ELASTIC) {
         if (lvl < 1 || lvl > P->d.nt - 1) return PROP_OK;
         float *d = snap_slot(P, lvl - 1);
-        WP_CK(P, cudaMemcpyAsync(d, s[0], N * 4, cudaMemcpyDeviceToDevice, P->stream));
-        WP_CK(P, cudaMemcpyAsync(d + N, s[1], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        for (size_t f = 0; f < snap_fields(P); f++)
+            WP_CK(P, cudaMemcpyAsync(d + f * N, s[f], N * 4, cudaMemcpyDeviceToDevice, P->stream));
     } else {
         if (lvl < 0 || lvl > P->d.nt - 1) return PROP_OK;
         float *d = snap_slot(P, lvl);
@@ -863,6 +910,8 @@ static void inject_resid(prop_s *P, const Geometry &G, const float *res, int k, 
     const int nt = P->d.nt;
     if (P->d.kind == PROP_TTI)   // also keeps zeta = C lam (tmp[6], tmp[7]) in step
         sp_inject(P, &G.R, res, nt, k, 1.f, 3, a[0], P->tmp[6], P->tmp[7], grad ? img_p : nullptr, grad);
+    else if (P->d.kind == PROP_ACOUSTIC)
+        sp_inject(P, &G.R, res, nt, k, 1.f, 1, a[0], nullptr, nullptr, grad ? img_p : nullptr, grad);
     else
         sp_inject(P, &G.R, res, nt, k, 1.f, 0, a[3], a[4], a[5], nullptr, nullptr);
 }
@@ -870,6 +919,7 @@ static void inject_resid(prop_s *P, const Geometry &G, const float *res, int k, 
 static void sample_src(prop_s *P, const Geometry &G, float *const *a, float *col)
 {
     if (P->d.kind == PROP_TTI) sp_record(P, &G.S, a[0], a[1], nullptr, P->g.dt * P->g.dt, col);
+    else if (P->d.kind == PROP_ACOUSTIC) sp_record(P, &G.S, a[0], nullptr, nullptr, P->g.dt * P->g.dt, col);
     else sp_record(P, &G.S, a[3], a[4], a[5], P->g.dt, col);
 }
 
@@ -940,6 +990,48 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
             WP_TRY(adj_iter(k, u, u + N));
             WP_TRY(aniso_iter(k, k - 1 > n0 ? seg_slot(P, k - n0 - 2) : seg_slot(P, K)));
         }
+    }
+    return PROP_OK;
+}
+
+// acoustic adjoint sweep.  grad != NULL: imaging with the forward wavefield
+// of the same level (lam^k pairs with u^k: -u^k (dt^2 L lam^{k+1} + R^T r^k) / m)
+static int ac_sweep(prop_s *P, const Geometry &G, const float *res, const float *wav,
+                    float *srcstage, float *grad)
+{
+    const int nt = P->d.nt;
+    WP_TRY(ensure_ast(P));
+    float *a[2] = {P->ast[0], P->ast[1]};
+    WP_TRY(zero_fields(P, a, 2));
+    if (srcstage) WP_CK(P, cudaMemsetAsync(srcstage, 0, sizeof(float) * (size_t)nt * G.S.n, P->stream));
+    auto adj_iter = [&](int k, const float *u) -> int {
+        WP_TRY(acu_launch_step(P, a, u, grad));   // a[1] <- lam^k
+        std::swap(a[0], a[1]);
+        inject_resid(P, G, res, k, a, u, grad);
+        if (srcstage) sample_src(P, G, a, srcstage + (size_t)(k - 1) * G.S.n);
+        prof_maybe_collect(P);
+        return PROP_OK;
+    };
+    if (!grad) {
+        for (int k = nt - 1; k >= 1; k--) WP_TRY(adj_iter(k, nullptr));
+        return PROP_OK;
+    }
+    if (P->d.snap_mode == SNAP_FULL_FP32) {
+        for (int k = nt - 1; k >= 1; k--) WP_TRY(adj_iter(k, snap_slot(P, k - 1)));
+        return PROP_OK;
+    }
+    const size_t N = (size_t)P->g.N;
+    const int K = ckpt_K(P), J = (nt - 1 + K - 1) / K;
+    for (int j = J - 1; j >= 0; j--) {
+        const int n0 = j * K, E = std::min((j + 1) * K, nt - 1);
+        // restore level n0 and recompute levels n0+1..E (slot i: level n0+1+i)
+        float *s[2] = {P->st[0], P->st[1]};
+        WP_TRY(load_checkpoint(P, j, s));
+        for (int n = n0; n < E; n++) {
+            WP_TRY(fwd_step(P, s, G.S, wav, n));
+            WP_CK(P, cudaMemcpyAsync(seg_slot(P, n - n0), s[0], N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        }
+        for (int k = E; k >= n0 + 1; k--) WP_TRY(adj_iter(k, seg_slot(P, k - n0 - 1)));
     }
     return PROP_OK;
 }
@@ -1030,6 +1122,7 @@ extern "C" int prop_adjoint(prop_t *P, const float *traces_in, const float *rec_
     WP_TRY(wp_malloc(P, &stage.p, sizeof(float) * (size_t)nt * nsrc, "source staging"));
     WP_TRY(wp_malloc(P, &out.p, sizeof(float) * (size_t)nt * nsrc, "source output"));
     if (P->d.kind == PROP_TTI) WP_TRY(tti_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
+    else if (P->d.kind == PROP_ACOUSTIC) WP_TRY(ac_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
     else WP_TRY(el_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
     sp_transpose(P, (const float *)stage.p, (float *)out.p, nsrc, nt);
     WP_TRY(copy_out(P, src_out, (const float *)out.p, (size_t)nt * nsrc));
@@ -1059,7 +1152,8 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
     // delta and the three dJ/dn components that become theta, phi); elastic
     // lambda, mu, b
     const bool aniso = P->d.kind == PROP_TTI && P->aniso;
-    const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : 3, nout = aniso ? 5 : ng;
+    const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : (P->d.kind == PROP_ACOUSTIC ? 1 : 3),
+              nout = aniso ? 5 : ng;
     const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
     float *g3[6] = {};
     if (grad) {
@@ -1070,6 +1164,8 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
     }
     if (P->d.kind == PROP_TTI)
         WP_TRY(tti_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3 : nullptr));
+    else if (P->d.kind == PROP_ACOUSTIC)
+        WP_TRY(ac_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3[0] : nullptr));
     else
         WP_TRY(el_sweep(P, G, res, (const float *)wbuf.p, (float *)stage.p, grad ? g3 : nullptr));
     if (src_grad) {
@@ -1108,6 +1204,24 @@ extern "C" int prop_gradient_aniso(prop_t *P, const float *wavelet, const float 
     return rc;
 }
 
+extern "C" int prop_stack_image(prop_t *P, const float *image, float *stack, const int *stack_dims,
+                                const int *offset, float weight)
+{
+    WP_TRY(check_handle(P));
+    if (!image || !stack || !stack_dims || !offset) return wp_fail(P, PROP_EINVAL, "NULL argument");
+    if (!is_dev(stack)) return wp_fail(P, PROP_EINVAL, "stack must be device memory");
+    const int n[3] = {P->g.px, P->g.py, P->g.pz};
+    for (int a = 0; a < 3; a++)
+        if (offset[a] < 0 || stack_dims[a] < 1 || offset[a] + n[a] > stack_dims[a])
+            return wp_fail(P, PROP_EINVAL, "window outside the stack");
+    DevBuf ibuf;
+    const float *img = nullptr;
+    WP_TRY(dev_in(P, image, (size_t)n[0] * n[1] * n[2], ibuf, &img));
+    k_stack(P, img, stack, stack_dims, offset, weight);
+    WP_CK(P, cudaGetLastError());
+    return finish(P);
+}
+
 // device bytes one prop_gradient call allocates on top of what the handle
 // already holds (wavefield storage or checkpoints + recompute segment,
 // adjoint state, scratch fields, gradient buffers, traces)
@@ -1118,7 +1232,7 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
     size_t b = 0;
     switch (P->d.snap_mode) {
     case SNAP_FULL_FP32:
-        b += (P->d.kind == PROP_TTI ? (size_t)(nt - 1) : (size_t)nt) * snap_fields(P) * N * 4;
+        b += (P->d.kind != PROP_ELASTIC ? (size_t)(nt - 1) : (size_t)nt) * snap_fields(P) * N * 4;
         break;
     case SNAP_CKPT_FP32: b += (size_t)J * cf * N * 4; break;
     default: b += (size_t)J * cf * N * 2 + 4 * ((size_t)J * cf + 1024); break;
@@ -1128,10 +1242,11 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
     for (int i = 0; i < cf; i++)
         if (!P->ast[i]) b += N * 4;
     const bool aniso = P->d.kind == PROP_TTI && P->aniso;
-    const int ntmp = P->d.kind == PROP_TTI ? (aniso ? 14 : 8) : 15;
+    const int ntmp = P->d.kind == PROP_TTI ? (aniso ? 14 : 8) : (P->d.kind == PROP_ACOUSTIC ? 0 : 15);
     for (int i = 0; i < ntmp; i++)
         if (!P->tmp[i]) b += N * 4;
-    const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : 3, nout = aniso ? 5 : ng;
+    const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : (P->d.kind == PROP_ACOUSTIC ? 1 : 3),
+              nout = aniso ? 5 : ng;
     b += (N * ng + np * nout) * 4;
     b += (size_t)4 * 4 * nrec * nt;    // traces, staging, observed data, residual
     return b + ((size_t)64 << 20);     // point tables, wavelet, allocator granularity

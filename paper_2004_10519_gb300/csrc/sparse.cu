@@ -184,6 +184,19 @@ __global__ void fold_axis_kernel(const float *__restrict__ in, float *__restrict
     out[q] = s;
 }
 
+// stack[ox + i][oy + j][oz + k] += weight * img[i][j][k]  (img [nx][ny][nz],
+// stack [gx][gy][gz]; the window lies inside the stack)
+__global__ void stack_kernel(const float *__restrict__ img, float *stack, int nx, int ny, int nz, int gy, int gz,
+                             int ox, int oy, int oz, float weight)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(q % nz), j = (int)((q / nz) % ny), i = (int)(q / ((long long)nz * ny));
+        stack[((long long)(ox + i) * gy + (oy + j)) * gz + (oz + k)] += weight * img[q];
+    }
+}
+
 __global__ void zeta_kernel(long long n, const float *__restrict__ eps, const float *__restrict__ del,
                             const float *__restrict__ lp, const float *__restrict__ lr,
                             float *__restrict__ zp, float *__restrict__ zr)
@@ -419,6 +432,14 @@ void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2)
     fold_axis_kernel<<<nblk(n2), NB, 0, P->stream>>>(s1, s2, g.NX, g.NY, g.pz, 1, g.py, g.nbl);
     fold_axis_kernel<<<nblk(n3), NB, 0, P->stream>>>(s2, phys, g.NX, g.py, g.pz, 0, g.px, g.nbl);
     P->kern_launches += 3;
+}
+
+void k_stack(prop_s *P, const float *img, float *stack, const int *gdims, const int *off, float weight)
+{
+    const long long n = (long long)P->g.px * P->g.py * P->g.pz;
+    stack_kernel<<<nblk(n), NB, 0, P->stream>>>(img, stack, P->g.px, P->g.py, P->g.pz, gdims[1], gdims[2], off[0],
+                                                off[1], off[2], weight);
+    P->kern_launches += 1;
 }
 
 void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr)

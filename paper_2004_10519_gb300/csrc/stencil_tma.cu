@@ -878,6 +878,128 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
 }
 
 // ---------------------------------------------------------------------------
+// Isotropic acoustic step (Sec. II-A, Eq. acou; u.laplace of the
+// wave-equation listing):  u^{n+1} = (dt^2 L u^n + 2 m u^n - B u^{n-1}) / A,
+// L the sum over axes of the centred second derivative, A, B = m (1 +- sig
+// dt / 2).  L is symmetric, so the transposed step is the same pass; GRAD
+// fuses the imaging g -= dt^2 u_f (L lam) / m with the forward field u_f.
+// u^{n+1} overwrites u^{n-1} (each point is read before it is written, and
+// only by its own thread).
+// stage: [u^n rect] [queue head u^n (x+M)] [m, u^{n-1} (plane x)] (+ [u_f, g])
+// ---------------------------------------------------------------------------
+template <int M, int GRAD>
+struct AL {
+    using B = BX<M>;
+    static constexpr int NI = 3 + (GRAD ? 2 : 0);
+    static constexpr int OU = 0, OI = B::RS, SZ = OI + NI * IS;
+    static constexpr int QH = 0, MM = 1, U0 = 2, UF = 3, GG = 4;
+    static constexpr uint32_t BYTES = 4u * (B::RR * B::RC + NI * IS);
+};
+
+struct AMaps {
+    CUtensorMap u, q, m, u0, uf, g;
+};
+
+template <int M, int GRAD>
+__global__ void __launch_bounds__(NTP, 2)
+acu_tma(GridDev g, FDW w, const float *__restrict__ u1, float *__restrict__ u0, float *__restrict__ grad,
+        const __grid_constant__ AMaps mp, int *flag, int check, int xc, int *err)
+{
+    using L = AL<M, GRAD>;
+    using B = BX<M>;
+    constexpr int Q = 2 * M + 1;
+    extern __shared__ __align__(128) float sm[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
+    const int tz = threadIdx.x, ty = threadIdx.y, lane = (ty * TZ2 + tz) & 31;
+    const bool lead = ty == 0 && tz == 0;
+    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z = z0 + 2 * tz, y = y0 + ty;
+    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
+    auto issue = [&](int x, int st) {
+        float *S = sm + st * L::SZ;
+        float *I = S + L::OI;
+        uint64_t *bar = &bars[st];
+        mbar_expect(bar, L::BYTES);
+        tma3(S + L::OU, &mp.u, z0 - B::MZ, y0 - M, x, bar);
+        tma3(I + L::QH * IS, &mp.q, z0, y0, x + M, bar);              // beyond NX: zeros
+        tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
+        tma3(I + L::U0 * IS, &mp.u0, z0, y0, x, bar);
+        if (GRAD) {
+            tma3(I + L::UF * IS, &mp.uf, z0, y0, x, bar);
+            tma3(I + L::GG * IS, &mp.g, z0, y0, x, bar);
+        }
+    };
+    Ring R(bars);
+    if (lead) R.init();
+    __syncthreads();
+    if (ty >= FY) {                                       // producer warp
+        if (lane == 0) R.produce(xa, nit, issue, err);
+        return;
+    }
+    const bool act = y < g.NY && z < g.NZ;
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    float2 qu[Q];
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        const int xq = xa - M + j;
+        qu[j] = act && xq >= 0 && xq < g.NX ? ldg2(u1, xq * pl + q0) : Z2;
+    }
+    const float *sx = g.tab, *sy = g.tab + g.NX, *sz = g.tab + g.NX + g.NY;
+    const float dt2 = g.dt * g.dt, hdt = 0.5f * g.dt, ih2 = g.ih * g.ih, c0 = 3.f * w.d2[0];
+    const float syv = act ? __ldg(sy + y) : 0.f;
+    const float syz0 = act ? syv + __ldg(sz + z) : 0.f, syz1 = act ? syv + __ldg(sz + z + 1) : 0.f;
+    const int cy = ty + M, cz = B::MZ + 2 * tz, ii = ty * FZ + 2 * tz;
+    const int ci = cy * B::RC + cz;
+    for (int x = xa; x < xb; x++) {
+        if (!__all_sync(0xffffffffu, R.wait_full())) {
+            if (lane == 0) atomicOr(err, 2);
+            return;
+        }
+        const float *S = sm + R.st * L::SZ;
+        const float *I = S + L::OI + ii;
+        qu[Q - 1] = lds2(I + L::QH * IS);
+        if (act) {
+            const float *su = S + L::OU;
+            float wz[2 * M + 2];
+            zwin<M>(su + cy * B::RC, cz, wz);
+            const float2 uc = qu[M];
+            float la = c0 * uc.x, lb = c0 * uc.y;
+#pragma unroll
+            for (int k = 1; k <= M; k++) {
+                const float c = w.d2[k];
+                const float2 yp = lds2(su + ci + k * B::RC), ym = lds2(su + ci - k * B::RC);
+                la += c * ((qu[M + k].x + qu[M - k].x) + (yp.x + ym.x) + (wz[M + k] + wz[M - k]));
+                lb += c * ((qu[M + k].y + qu[M - k].y) + (yp.y + ym.y) + (wz[M + k + 1] + wz[M - k + 1]));
+            }
+            const float lap[2] = {la * ih2, lb * ih2};
+            const float2 mm = lds2(I + L::MM * IS), p0 = lds2(I + L::U0 * IS);
+            const float sxv = __ldg(sx + x);
+            const float M2[2] = {mm.x, mm.y}, P0[2] = {p0.x, p0.y}, P1[2] = {uc.x, uc.y};
+            const float SYZ[2] = {syz0, syz1};
+            float un[2];
+#pragma unroll
+            for (int i = 0; i < 2; i++) {
+                const float sd = hdt * (sxv + SYZ[i]);
+                const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
+                un[i] = (dt2 * lap[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
+            }
+            const unsigned q = x * pl + q0;
+            st2(u0, q, un[0], un[1]);
+            if (GRAD) {
+                const float2 uf = lds2(I + L::UF * IS), gg = lds2(I + L::GG * IS);
+                st2(grad, q, gg.x - dt2 * uf.x * lap[0] / M2[0], gg.y - dt2 * uf.y * lap[1] / M2[1]);
+            }
+            if (check && !(isfinite(un[0]) && isfinite(un[1]))) atomicOr(flag, 1);
+        }
+#pragma unroll
+        for (int j = 0; j < Q - 1; j++) qu[j] = qu[j + 1];
+        R.release(lane);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host: tensor maps
 // ---------------------------------------------------------------------------
 typedef CUresult (*EncodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -1204,7 +1326,48 @@ int tti_launch_any(prop_s *P, float *const *S, bool adjoint, const float *up, co
     return grad ? tti_launch<M, 1, 1>(P, S, up, ur, grad) : tti_launch<M, 1, 0>(P, S, up, ur, grad);
 }
 
+// acoustic step: S[0] = u^n, S[1] = u^{n-1} (overwritten by u^{n+1});
+// grad != NULL: imaging with the forward field uf
+template <int M, int GRAD>
+int acu_launch(prop_s *P, float *const *S, const float *uf, float *grad)
+{
+    using B = BX<M>;
+    const GridDev &g = P->g;
+    const int xc = P->xchunk;
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    AMaps am;
+    bool ok = map_of(P, S[0], B::RC, B::RR, &am.u) && map_of(P, S[0], FZ, FY, &am.q) &&
+              map_of(P, P->m, FZ, FY, &am.m) && map_of(P, S[1], FZ, FY, &am.u0);
+    if (GRAD) ok = ok && map_of(P, uf, FZ, FY, &am.uf) && map_of(P, grad, FZ, FY, &am.g);
+    if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+    const size_t sb = NSTAGE * AL<M, GRAD>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(acu_tma<M, GRAD>, sb);
+    (void)attr;
+    acu_tma<M, GRAD><<<grd, blk, sb, P->stream>>>(g, P->w, S[0], S[1], grad, am, P->flag, P->d.check_nan, xc,
+                                                  P->flag);
+    P->kern_launches += 1;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 }  // namespace
+
+// acoustic step through the TMA-fed pass (see acu_launch)
+int acu_launch_tma(prop_s *P, float *const *S, const float *uf, float *grad)
+{
+    const int id = grad ? 7 : 6;
+    prof_begin(P, id);
+    int rc;
+    switch (P->M) {
+    case 2: rc = grad ? acu_launch<2, 1>(P, S, uf, grad) : acu_launch<2, 0>(P, S, uf, grad); break;
+    case 4: rc = grad ? acu_launch<4, 1>(P, S, uf, grad) : acu_launch<4, 0>(P, S, uf, grad); break;
+    case 6: rc = grad ? acu_launch<6, 1>(P, S, uf, grad) : acu_launch<6, 0>(P, S, uf, grad); break;
+    case 8: rc = grad ? acu_launch<8, 1>(P, S, uf, grad) : acu_launch<8, 0>(P, S, uf, grad); break;
+    default: return wp_fail(P, PROP_EINVAL, "unsupported space order");
+    }
+    prof_end(P, id);
+    return rc;
+}
 
 // TMA-fed passes need 16-byte row strides (NZ a multiple of 4), the
 // driver's tensor-map encoder and (TTI) the symmetry-axis arrays

@@ -1,6 +1,7 @@
 """The TMA-fed stencil passes (used when the computational NZ is a multiple
-of 4) and the pipelined passes (any NZ; forced with WAVEPROP_NO_TMA=1) compute
-the same discrete operators: their traces agree to FP32 rounding."""
+of 4) and the pipelined or direct passes (any NZ; forced with
+WAVEPROP_NO_TMA=1) compute the same discrete operators: their traces agree
+to FP32 rounding."""
 import numpy as np
 import pytest
 
@@ -19,6 +20,10 @@ def tti_problem(shape=(36, 30, 44), nbl=6, so=12, nt=60, h=10.0):
                          synth.ricker(22.0, dt, nt)[None], rec)
 
 
+def ac_problem(shape=(36, 30, 44), nbl=6, so=12, nt=60):
+    return synth.acoustic_small(shape=shape, nbl=nbl, so=so, nt=nt)
+
+
 def el_problem(shape=(34, 30, 44), nbl=6, so=8, nt=60, h=10.0):
     nx, ny, nz = shape
     m = synth.random_elastic(nx, ny, nz, 8, 4.0)
@@ -29,11 +34,11 @@ def el_problem(shape=(34, 30, 44), nbl=6, so=8, nt=60, h=10.0):
                          synth.ricker(20.0, dt, nt)[None], rec)
 
 
-@pytest.mark.parametrize("kind", ["tti", "elastic"])
+@pytest.mark.parametrize("kind", ["tti", "elastic", "acoustic"])
 def test_tma_and_pipelined_paths_agree(kind, monkeypatch):
     import paper_2004_10519_gb300 as wp
     wp.lib()
-    p = tti_problem() if kind == "tti" else el_problem()
+    p = {"tti": tti_problem, "elastic": el_problem, "acoustic": ac_problem}[kind]()
     assert (p.nz + 2 * p.nbl) % 4 == 0
     d = np.random.default_rng(3).standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
     out = {}
@@ -51,13 +56,13 @@ def test_tma_and_pipelined_paths_agree(kind, monkeypatch):
         assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b), (kind, i)
 
 
-@pytest.mark.parametrize("kind", ["tti", "elastic"])
+@pytest.mark.parametrize("kind", ["tti", "elastic", "acoustic"])
 def test_tile_planes_do_not_change_results(kind, monkeypatch):
     """The autotuned x-extent of the stencil tiles only moves CTA boundaries:
     traces are bitwise identical to the occupancy heuristic's."""
     import paper_2004_10519_gb300 as wp
     wp.lib()
-    p = tti_problem(nt=40) if kind == "tti" else el_problem(nt=40)
+    p = {"tti": tti_problem, "elastic": el_problem, "acoustic": ac_problem}[kind](nt=40)
     out, planes = {}, {}
     for tag, env in (("tuned", None), ("heuristic", "0")):
         if env:
