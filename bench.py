@@ -40,7 +40,8 @@ HBM_FALLBACK_GBS = 6800.0
 # array read and written once, each parameter array read once):
 #   elastic: 9 state reads + 9 writes + 3 parameters (b, lambda, mu) = 84 B
 #   TTI:     4 state reads + 2 writes + 5 parameters                  = 44 B
-ALG_BYTES = {"elastic": 84.0, "tti": 44.0}
+#   acoustic: 2 state reads + 1 write + m                             = 16 B
+ALG_BYTES = {"elastic": 84.0, "tti": 44.0, "acoustic": 16.0}
 # DRAM bytes per point of one elastic step (velocity + stress pass) measured
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 200^3 case of
 # the same kernels (profiles/elastic_tma_passes_200cube_so8.md), scaled to a
@@ -48,8 +49,8 @@ ALG_BYTES = {"elastic": 84.0, "tti": 44.0}
 TRAFFIC_B_PER_PT = {"elastic": 113.9}
 # algorithmic FP32 operations per point update, counted from the kernels'
 # arithmetic (FMA = 2): elastic so 8 (velocity + stress pass), TTI so 12
-# (rotation + update pass)
-FLOP_PER_PT = {"elastic": 263.0, "tti": 250.0}
+# (rotation + update pass), acoustic so 12 (7 per stencil radius + 15)
+FLOP_PER_PT = {"elastic": 263.0, "tti": 250.0, "acoustic": 57.0}
 
 
 def peaks():
@@ -236,6 +237,80 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
     return out
 
 
+def acoustic_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
+    """Isotropic acoustic so-12 step rate on the industry-scale grid
+    (880 x 880 x 480 computational points) from a seeded random state, and
+    the transposed step with imaging (the gradient's inner step); the model
+    is uniform random in [1.5, 4.5] km/s (content does not change the work)."""
+    rng = np.random.default_rng(8)
+    vp = rng.uniform(1.5, 4.5, (nx, ny, nz)).astype(np.float32)
+    dt = synth.cfl_dt(h, 4.5)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    prop = wp.Propagator(wp.PROP_ACOUSTIC, (nx, ny, nz), nbl, h, so, 10, [vp], dt=dt, stream=stream)
+    del vp
+    N = int(np.prod(prop.grid))
+    prop.set_state([torch.randn(prop.grid, device=dev) for _ in range(2)])
+    out = {}
+    prop.step(5)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    prop.step(steps)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prop.profile(True)
+    prop.step(10)
+    kms, kn = prop.kernel_stats(wp.K_AC_STEP)
+    prop.profile(False)
+    t = kms / max(kn, 1) / 1e3
+    out["acoustic_forward"] = {"gpts_per_s": N / (ms / 1e3) / 1e9, "ms_per_step": ms,
+                               "kernel_ms_per_step": t * 1e3,
+                               "alg_gbs": ALG_BYTES["acoustic"] * N / t / 1e9,
+                               "alg_tflops": FLOP_PER_PT["acoustic"] * N / t / 1e12}
+    prop.close()
+    out["grid"] = list(prop.grid)
+    out["space_order"] = so
+    out["hbm_peak_gbs"] = peaks()[0]
+    return out
+
+
+def rtm_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
+    """Reverse-time migration over many shots (acoustic so 12, FP32
+    checkpoints): per-shot images (dJ/dm against the true model's data, in
+    the migration velocity) from one prop_gradient_batch call, stacked on the
+    device into the global image at each window's offset."""
+    kw = dict(size_range=(60, 120), nz=80, global_cells=(300, 300, 100)) if small else {}
+    shots = synth.acoustic_rtm_shots(nshots, nt, **kw)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    to = lambda a: torch.from_numpy(a).to(dev)
+    props, wav, src, rec, obs = [], [], [], [], []
+    gx, gy, _ = kw.get("global_cells", (1000, 1000, 500))
+    nz = shots[0][1].nz
+    for true, p0, _ in shots:
+        pt = wp.Propagator.from_problem(true, stream=stream)
+        w, s_, r = to(true.wavelet), to(true.src), to(true.rec)
+        obs.append(pt.forward(w, s_, r))
+        pt.close()
+        props.append(wp.Propagator.from_problem(p0, snap_mode=wp.SNAP_CKPT_FP32, stream=stream))
+        wav.append(w); src.append(s_); rec.append(r)
+    stack = torch.zeros((gx, gy, nz), dtype=torch.float32, device=dev)
+    props[0].gradient(wav[0], src[0], rec[0], obs[0])        # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grads, _ = wp.gradient_batch(props, wav, src, rec, obs)
+    for p, g, (_, _, off) in zip(props, grads, shots):
+        p.stack_image(g, stack, off)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    npts = sum(int(np.prod(p.grid)) for p in props)
+    for p in props:
+        p.close()
+    return {"shots": nshots, "nt": nt, "storage": "fp32 checkpoints", "points_total": npts,
+            "seconds": sec, "shots_per_hour": 3600.0 * nshots / sec,
+            "stack_dims": list(stack.shape), "stack_l2": float(torch.linalg.norm(stack))}
+
+
 def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
     """TTI FWI gradient (so 12) shots/hour on the 400x400x300 + 40 workload
     for several wavefield-storage modes at equal nt."""
@@ -401,7 +476,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--extra", default="", help="comma list: tti, grad, elgrad, gradsmall, batch (secondary measurements)")
+    ap.add_argument("--extra", default="",
+                    help="comma list: tti, acoustic, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--batch-shots", type=int, default=8)
     ap.add_argument("--batch-nt", type=int, default=150)
@@ -421,6 +497,13 @@ def main():
                 out["tti"] = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
             else:
                 out["tti"] = tti_throughput(wp, torch, dev)
+        if "acoustic" in extras:
+            if args.small:
+                out["acoustic"] = acoustic_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
+            else:
+                out["acoustic"] = acoustic_throughput(wp, torch, dev)
+        if "rtm" in extras:
+            out["rtm"] = rtm_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt, small=args.small)
         if "grad" in extras:
             out["grad"] = gradient_shots_per_hour(
                 wp, torch, dev, args.grad_nt,

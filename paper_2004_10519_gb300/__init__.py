@@ -326,7 +326,7 @@ class Propagator:
 
 
 # kernel ids of Propagator.kernel_stats
-K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD, K_EL_ADJ_U = 0, 1, 2, 3, 4, 5
+K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD, K_EL_ADJ_U, K_AC_STEP, K_AC_IMG = 0, 1, 2, 3, 4, 5, 6, 7
 
 
 def fp32_peak():

@@ -59,6 +59,7 @@ struct prop_s {
     float vmax = 0.f;        // max model velocity used for the CFL rule
     // model (computational grid)
     float *m = nullptr, *eps = nullptr, *del = nullptr, *th = nullptr, *ph = nullptr;   // TTI
+    float *acw = nullptr;    // acoustic: dt^2 / m
     float *nrm[2] = {};      // TTI symmetry axis n_x, n_y (sign chosen so that n_z >= 0)
     float *bu = nullptr, *lam = nullptr, *mu = nullptr;                                 // elastic
     // state: TTI 4 fields (p_cur, r_cur, p_prev, r_prev); elastic 9 fields
@@ -171,6 +172,8 @@ void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2);
 void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long n);
 double k_sumsq_host(prop_s *P, const float *a, long long n);
 void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr);
+// out = s / a (pointwise, n values)
+void k_ratio(prop_s *P, const float *a, float s, float *out, long long n);
 // stack[off + (i, j, k)] += weight * img[i][j][k] over the handle's physical grid
 void k_stack(prop_s *P, const float *img, float *stack, const int *gdims, const int *off, float weight);
 // snapshot codec

@@ -286,7 +286,7 @@ static void free_snaps(prop_s *P)
 
 static void free_all(prop_s *P)
 {
-    float *arrs[] = {P->m, P->eps, P->del, P->th, P->ph, P->nrm[0], P->nrm[1], P->bu, P->lam, P->mu};
+    float *arrs[] = {P->m, P->eps, P->del, P->th, P->ph, P->nrm[0], P->nrm[1], P->bu, P->lam, P->mu, P->acw};
     for (float *a : arrs) cudaFree(a);
     for (auto &a : P->st) cudaFree(a);
     for (auto &a : P->ast) cudaFree(a);
@@ -491,6 +491,8 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
         k_normals(P);
     } else if (d->kind == PROP_ACOUSTIC) {
         WP_TRY(upload(0, P->m, 1000.f, 1));
+        WP_MALLOC(P, P->acw, N * sizeof(float), "model");
+        k_ratio(P, P->m, g.dt * g.dt, P->acw, (long long)N);
     } else {
         WP_TRY(upload(0, P->bu, 1.f, 0));    // vp  -> b      (k_lame)
         WP_TRY(upload(1, P->lam, 1.f, 0));   // vs  -> lambda

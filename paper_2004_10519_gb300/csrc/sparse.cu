@@ -209,6 +209,12 @@ __global__ void zeta_kernel(long long n, const float *__restrict__ eps, const fl
     zr[q] = s * p + r;
 }
 
+__global__ void ratio_kernel(const float *__restrict__ a, float s, float *out, long long n)
+{
+    long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q < n) out[q] = s / a[q];
+}
+
 __global__ void diff_kernel(const float *a, const float *b, float *out, long long n)
 {
     long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -432,6 +438,12 @@ void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2)
     fold_axis_kernel<<<nblk(n2), NB, 0, P->stream>>>(s1, s2, g.NX, g.NY, g.pz, 1, g.py, g.nbl);
     fold_axis_kernel<<<nblk(n3), NB, 0, P->stream>>>(s2, phys, g.NX, g.py, g.pz, 0, g.px, g.nbl);
     P->kern_launches += 3;
+}
+
+void k_ratio(prop_s *P, const float *a, float s, float *out, long long n)
+{
+    ratio_kernel<<<nblk(n), NB, 0, P->stream>>>(a, s, out, n);
+    P->kern_launches += 1;
 }
 
 void k_stack(prop_s *P, const float *img, float *stack, const int *gdims, const int *off, float weight)

@@ -879,54 +879,69 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
 
 // ---------------------------------------------------------------------------
 // Isotropic acoustic step (Sec. II-A, Eq. acou; u.laplace of the
-// wave-equation listing):  u^{n+1} = (dt^2 L u^n + 2 m u^n - B u^{n-1}) / A,
-// L the sum over axes of the centred second derivative, A, B = m (1 +- sig
-// dt / 2).  L is symmetric, so the transposed step is the same pass; GRAD
-// fuses the imaging g -= dt^2 u_f (L lam) / m with the forward field u_f.
-// u^{n+1} overwrites u^{n-1} (each point is read before it is written, and
-// only by its own thread).
-// stage: [u^n rect] [queue head u^n (x+M)] [m, u^{n-1} (plane x)] (+ [u_f, g])
+// wave-equation listing), with w = dt^2 / m:
+//   u^{n+1} = (w L u^n + 2 u^n - (1 - sd) u^{n-1}) / (1 + sd),  sd = sig dt / 2,
+// L the sum over axes of the centred second derivative (the damped leapfrog
+// A u^{n+1} = dt^2 L u^n + 2 m u^n - B u^{n-1} divided by m).  L is
+// symmetric, so the transposed step is the same pass; GRAD fuses the imaging
+// g -= w u_f (L lam) with the forward field u_f.  u^{n+1} overwrites u^{n-1}
+// (each point is read before it is written, and only by its own thread).
+// Tile 32 (z) x 32 (y): each consumer thread updates 2 z points on 2
+// consecutive rows, so its z windows and y taps serve both rows, with
+// paired FP32 arithmetic (__ffma2_rn and friends: per component the results
+// of the scalar operations).  The x loop is unrolled over the queue length,
+// so the x-derivative queues rotate by renaming instead of register moves.
+// stage: [u^n rect (y, z halo)] [queue head u^n (x+M)] [w, u^{n-1} (plane x)]
+//        (+ [u_f, g])
 // ---------------------------------------------------------------------------
+constexpr int AFY = 2 * FY;       // rows per CTA
+constexpr int AIS = FZ * AFY;     // interior box (floats)
+
 template <int M, int GRAD>
 struct AL {
-    using B = BX<M>;
+    static constexpr int MZ = (M + 3) & ~3;
+    static constexpr int RR = AFY + 2 * M, RC = FZ + 2 * MZ, RS = al32(RR * RC);
     static constexpr int NI = 3 + (GRAD ? 2 : 0);
-    static constexpr int OU = 0, OI = B::RS, SZ = OI + NI * IS;
-    static constexpr int QH = 0, MM = 1, U0 = 2, UF = 3, GG = 4;
-    static constexpr uint32_t BYTES = 4u * (B::RR * B::RC + NI * IS);
+    static constexpr int OU = 0, OI = RS, SZ = OI + NI * AIS;
+    static constexpr int QH = 0, WW = 1, U0 = 2, UF = 3, GG = 4;
+    static constexpr uint32_t BYTES = 4u * (RR * RC + NI * AIS);
 };
 
 struct AMaps {
-    CUtensorMap u, q, m, u0, uf, g;
+    CUtensorMap u, q, w, u0, uf, g;
 };
 
+WP_DEV float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+WP_DEV float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+WP_DEV float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+WP_DEV float2 f2s(float a) { return make_float2(a, a); }
+
 template <int M, int GRAD>
-__global__ void __launch_bounds__(NTP, 2)
+__global__ void __launch_bounds__(NTP, M <= 6 ? 2 : 1)
 acu_tma(GridDev g, FDW w, const float *__restrict__ u1, float *__restrict__ u0, float *__restrict__ grad,
         const __grid_constant__ AMaps mp, int *flag, int check, int xc, int *err)
 {
     using L = AL<M, GRAD>;
-    using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, lane = (ty * TZ2 + tz) & 31;
     const bool lead = ty == 0 && tz == 0;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + 2 * tz, y = y0 + ty;
+    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * AFY;
+    const int z = z0 + 2 * tz, ya = y0 + 2 * ty;          // rows ya, ya + 1
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
         float *I = S + L::OI;
         uint64_t *bar = &bars[st];
         mbar_expect(bar, L::BYTES);
-        tma3(S + L::OU, &mp.u, z0 - B::MZ, y0 - M, x, bar);
-        tma3(I + L::QH * IS, &mp.q, z0, y0, x + M, bar);              // beyond NX: zeros
-        tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
-        tma3(I + L::U0 * IS, &mp.u0, z0, y0, x, bar);
+        tma3(S + L::OU, &mp.u, z0 - L::MZ, y0 - M, x, bar);
+        tma3(I + L::QH * AIS, &mp.q, z0, y0, x + M, bar);             // beyond NX: zeros
+        tma3(I + L::WW * AIS, &mp.w, z0, y0, x, bar);
+        tma3(I + L::U0 * AIS, &mp.u0, z0, y0, x, bar);
         if (GRAD) {
-            tma3(I + L::UF * IS, &mp.uf, z0, y0, x, bar);
-            tma3(I + L::GG * IS, &mp.g, z0, y0, x, bar);
+            tma3(I + L::UF * AIS, &mp.uf, z0, y0, x, bar);
+            tma3(I + L::GG * AIS, &mp.g, z0, y0, x, bar);
         }
     };
     Ring R(bars);
@@ -936,66 +951,86 @@ acu_tma(GridDev g, FDW w, const float *__restrict__ u1, float *__restrict__ u0, 
         if (lane == 0) R.produce(xa, nit, issue, err);
         return;
     }
-    const bool act = y < g.NY && z < g.NZ;
+    const bool a0 = ya < g.NY && z < g.NZ, a1 = a0 && ya + 1 < g.NY;
     const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
-    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
+    const unsigned qa = a0 ? (unsigned)ya * g.NZ + z : 0u, qb = a1 ? qa + g.NZ : 0u;
     const float2 Z2 = make_float2(0.f, 0.f);
-    float2 qu[Q];
+    float2 qu0[Q], qu1[Q];
 #pragma unroll
     for (int j = 0; j < Q - 1; j++) {
         const int xq = xa - M + j;
-        qu[j] = act && xq >= 0 && xq < g.NX ? ldg2(u1, xq * pl + q0) : Z2;
+        const bool in = xq >= 0 && xq < g.NX;
+        qu0[j] = a0 && in ? ldg2(u1, xq * pl + qa) : Z2;
+        qu1[j] = a1 && in ? ldg2(u1, xq * pl + qb) : Z2;
     }
     const float *sx = g.tab, *sy = g.tab + g.NX, *sz = g.tab + g.NX + g.NY;
-    const float dt2 = g.dt * g.dt, hdt = 0.5f * g.dt, ih2 = g.ih * g.ih, c0 = 3.f * w.d2[0];
-    const float syv = act ? __ldg(sy + y) : 0.f;
-    const float syz0 = act ? syv + __ldg(sz + z) : 0.f, syz1 = act ? syv + __ldg(sz + z + 1) : 0.f;
-    const int cy = ty + M, cz = B::MZ + 2 * tz, ii = ty * FZ + 2 * tz;
-    const int ci = cy * B::RC + cz;
-    for (int x = xa; x < xb; x++) {
-        if (!__all_sync(0xffffffffu, R.wait_full())) {
-            if (lane == 0) atomicOr(err, 2);
-            return;
+    const float sz0 = a0 ? __ldg(sz + z) : 0.f, sz1 = a0 ? __ldg(sz + z + 1) : 0.f;
+    const float sy0 = a0 ? __ldg(sy + ya) : 0.f, sy1 = a1 ? __ldg(sy + ya + 1) : 0.f;
+    const float2 syz[2] = {make_float2(sy0 + sz0, sy0 + sz1), make_float2(sy1 + sz0, sy1 + sz1)};
+    const float hdt = 0.5f * g.dt;
+    const float2 c0v = f2s(3.f * w.d2[0]), ih2 = f2s(g.ih * g.ih), one = f2s(1.f), two = f2s(2.f),
+                 mone = f2s(-1.f);
+    const int cz = L::MZ + 2 * tz, ii = 2 * ty * FZ + 2 * tz, cr = 2 * ty;
+    const unsigned qr[2] = {qa, qb};
+    const bool ar[2] = {a0, a1};
+    for (int x0 = xa; x0 < xb; x0 += Q) {
+#pragma unroll
+        for (int s = 0; s < Q; s++) {
+            const int x = x0 + s;
+            if (x >= xb) break;
+            if (!__all_sync(0xffffffffu, R.wait_full())) {
+                if (lane == 0) atomicOr(err, 2);
+                return;
+            }
+            const float *S = sm + R.st * L::SZ;
+            const float *I = S + L::OI + ii;
+            qu0[(s + 2 * M) % Q] = lds2(I + L::QH * AIS);
+            qu1[(s + 2 * M) % Q] = lds2(I + L::QH * AIS + FZ);
+            if (a0) {
+                const float *su = S + L::OU;
+                float2 col[2 * M + 2];               // y taps of both rows: rect rows cr .. cr+2M+1
+#pragma unroll
+                for (int i = 0; i < 2 * M + 2; i++) col[i] = lds2(su + (cr + i) * L::RC + cz);
+                float2 lap[2];
+#pragma unroll
+                for (int r = 0; r < 2; r++) {
+                    const float2 *qu = r ? qu1 : qu0;
+                    float wz[2 * M + 2];
+                    zwin<M>(su + (cr + M + r) * L::RC, cz, wz);
+                    float2 acc = f2mul(c0v, col[M + r]);
+#pragma unroll
+                    for (int k = 1; k <= M; k++) {
+                        const float2 sxk = f2add(qu[(s + M + k) % Q], qu[(s + M - k) % Q]);
+                        const float2 syk = f2add(col[M + r + k], col[M + r - k]);
+                        const float2 szk = make_float2(wz[M + k] + wz[M - k], wz[M + k + 1] + wz[M - k + 1]);
+                        acc = f2fma(f2s(w.d2[k]), f2add(f2add(sxk, syk), szk), acc);
+                    }
+                    lap[r] = f2mul(acc, ih2);
+                }
+                const float2 sxv = f2s(__ldg(sx + x));
+#pragma unroll
+                for (int r = 0; r < 2; r++) {
+                    if (!ar[r]) continue;
+                    const float2 wv = lds2(I + L::WW * AIS + r * FZ), p0 = lds2(I + L::U0 * AIS + r * FZ);
+                    const float2 sd = f2mul(f2s(hdt), f2add(sxv, syz[r]));
+                    float2 num = f2mul(wv, lap[r]);
+                    num = f2fma(two, col[M + r], num);
+                    num = f2fma(f2add(sd, mone), p0, num);
+                    const float2 den = f2add(one, sd);
+                    const float2 un = make_float2(__fdividef(num.x, den.x), __fdividef(num.y, den.y));
+                    const unsigned q = x * pl + qr[r];
+                    st2(u0, q, un.x, un.y);
+                    if (GRAD) {
+                        const float2 uf = lds2(I + L::UF * AIS + r * FZ), gg = lds2(I + L::GG * AIS + r * FZ);
+                        const float2 t = f2fma(f2mul(mone, wv), uf, Z2);
+                        const float2 gn = f2fma(t, lap[r], gg);
+                        st2(grad, q, gn.x, gn.y);
+                    }
+                    if (check && !(isfinite(un.x) && isfinite(un.y))) atomicOr(flag, 1);
+                }
+            }
+            R.release(lane);
         }
-        const float *S = sm + R.st * L::SZ;
-        const float *I = S + L::OI + ii;
-        qu[Q - 1] = lds2(I + L::QH * IS);
-        if (act) {
-            const float *su = S + L::OU;
-            float wz[2 * M + 2];
-            zwin<M>(su + cy * B::RC, cz, wz);
-            const float2 uc = qu[M];
-            float la = c0 * uc.x, lb = c0 * uc.y;
-#pragma unroll
-            for (int k = 1; k <= M; k++) {
-                const float c = w.d2[k];
-                const float2 yp = lds2(su + ci + k * B::RC), ym = lds2(su + ci - k * B::RC);
-                la += c * ((qu[M + k].x + qu[M - k].x) + (yp.x + ym.x) + (wz[M + k] + wz[M - k]));
-                lb += c * ((qu[M + k].y + qu[M - k].y) + (yp.y + ym.y) + (wz[M + k + 1] + wz[M - k + 1]));
-            }
-            const float lap[2] = {la * ih2, lb * ih2};
-            const float2 mm = lds2(I + L::MM * IS), p0 = lds2(I + L::U0 * IS);
-            const float sxv = __ldg(sx + x);
-            const float M2[2] = {mm.x, mm.y}, P0[2] = {p0.x, p0.y}, P1[2] = {uc.x, uc.y};
-            const float SYZ[2] = {syz0, syz1};
-            float un[2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                const float sd = hdt * (sxv + SYZ[i]);
-                const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
-                un[i] = (dt2 * lap[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
-            }
-            const unsigned q = x * pl + q0;
-            st2(u0, q, un[0], un[1]);
-            if (GRAD) {
-                const float2 uf = lds2(I + L::UF * IS), gg = lds2(I + L::GG * IS);
-                st2(grad, q, gg.x - dt2 * uf.x * lap[0] / M2[0], gg.y - dt2 * uf.y * lap[1] / M2[1]);
-            }
-            if (check && !(isfinite(un[0]) && isfinite(un[1]))) atomicOr(flag, 1);
-        }
-#pragma unroll
-        for (int j = 0; j < Q - 1; j++) qu[j] = qu[j + 1];
-        R.release(lane);
     }
 }
 
@@ -1331,14 +1366,14 @@ int tti_launch_any(prop_s *P, float *const *S, bool adjoint, const float *up, co
 template <int M, int GRAD>
 int acu_launch(prop_s *P, float *const *S, const float *uf, float *grad)
 {
-    using B = BX<M>;
     const GridDev &g = P->g;
     const int xc = P->xchunk;
-    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + AFY - 1) / AFY, (g.NX + xc - 1) / xc);
+    using L = AL<M, GRAD>;
     AMaps am;
-    bool ok = map_of(P, S[0], B::RC, B::RR, &am.u) && map_of(P, S[0], FZ, FY, &am.q) &&
-              map_of(P, P->m, FZ, FY, &am.m) && map_of(P, S[1], FZ, FY, &am.u0);
-    if (GRAD) ok = ok && map_of(P, uf, FZ, FY, &am.uf) && map_of(P, grad, FZ, FY, &am.g);
+    bool ok = map_of(P, S[0], L::RC, L::RR, &am.u) && map_of(P, S[0], FZ, AFY, &am.q) &&
+              map_of(P, P->acw, FZ, AFY, &am.w) && map_of(P, S[1], FZ, AFY, &am.u0);
+    if (GRAD) ok = ok && map_of(P, uf, FZ, AFY, &am.uf) && map_of(P, grad, FZ, AFY, &am.g);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t sb = NSTAGE * AL<M, GRAD>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(acu_tma<M, GRAD>, sb);
