@@ -73,6 +73,9 @@ def lib():
             L.or_ac_step_state_d.argtypes = [P, dp, dp, C.c_int]
             L.or_ac_step_points.argtypes = [C.POINTER(_Desc), fp, fp, fp, C.c_int, lp, dp]
             L.or_weights_d2.argtypes = [C.c_int, dp]
+            L.or_el2_forward.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp]
+            L.or_el2_adjoint.argtypes = [P, C.c_int, fp, dp, C.c_int, fp, dp]
+            L.or_el2_step_state_d.argtypes = [P, dp, C.c_int, C.c_int]
             L.or_tti_gradient_aniso.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp, dp, dp, dp]
             L.or_tti_apply_L.argtypes = [P, dp, dp, dp, dp]
             L.or_tti_step_state.argtypes = [P, fp, fp, fp, fp, dp, dp, C.c_int]
@@ -203,8 +206,11 @@ class Problem:
     def forward(self, wavelet=None, src=None, rec=None, store=False):
         src, rec, wav = self._geom(src, rec, wavelet)
         tr = np.zeros((rec.shape[0], self.nt))
-        f = {1: lib().or_tti_forward, 2: lib().or_el_forward, 3: lib().or_ac_forward}[self.prob.kind]
-        rc = f(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0], _fp(rec), _dp(tr), int(store))
+        if self.prob.kind == 4:
+            rc = lib().or_el2_forward(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0], _fp(rec), _dp(tr))
+        else:
+            f = {1: lib().or_tti_forward, 2: lib().or_el_forward, 3: lib().or_ac_forward}[self.prob.kind]
+            rc = f(self.h, src.shape[0], _fp(src), _fp(wav), rec.shape[0], _fp(rec), _dp(tr), int(store))
         if rc:
             raise ValueError(f"oracle forward rc={rc}")
         return tr
@@ -213,7 +219,8 @@ class Problem:
         src, rec, _ = self._geom(src, rec, None)
         traces = _d(traces)
         q = np.zeros((src.shape[0], self.nt))
-        f = {1: lib().or_tti_adjoint, 2: lib().or_el_adjoint, 3: lib().or_ac_adjoint}[self.prob.kind]
+        f = {1: lib().or_tti_adjoint, 2: lib().or_el_adjoint, 3: lib().or_ac_adjoint,
+             4: lib().or_el2_adjoint}[self.prob.kind]
         rc = f(self.h, rec.shape[0], _fp(rec), _dp(traces), src.shape[0], _fp(src), _dp(q))
         if rc:
             raise ValueError(f"oracle adjoint rc={rc}")
@@ -293,6 +300,13 @@ class Problem:
         out = np.zeros((9, self.N))
         lib().or_el_step_state(self.h, _fp(s), _dp(out), int(adjoint), nsteps)
         return out.reshape((9,) + self.shape)
+
+    def el2_run_d(self, state, nsteps, adjoint=False):
+        """2D elastic: nsteps source-free (transposed) steps of a state
+        [9][NX][1][NZ] in the 3D slot order (VX, VZ, TXX, TZZ, TXZ used)."""
+        s = _d(state).reshape(9, -1).copy()
+        lib().or_el2_step_state_d(self.h, _dp(s), int(adjoint), nsteps)
+        return s.reshape((9,) + self.shape)
 
     def el_run_d(self, state, nsteps, adjoint=False):
         s = _d(state).reshape(9, -1).copy()

@@ -1,5 +1,6 @@
 /*
- * FP64 CPU oracle for the TTI, elastic and isotropic acoustic propagators.
+ * FP64 CPU oracle for the TTI, elastic (3D and 2D) and isotropic acoustic
+ * propagators.
  *
  * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
  * bench.py's cpu_baseline leg load this library.  It shares no code with the
@@ -36,7 +37,9 @@
  * assembled-matrix transposes and Taylor tests of the gradients; for the
  * acoustic propagator the second-derivative moment conditions, Green's
  * function convergence, undamped leapfrog energy conservation, the dot test,
- * the assembled step's symmetry and a Taylor test).
+ * the assembled step's symmetry and a Taylor test; for the 2D elastic system
+ * equality with a y-invariant state of the 3D system, the dot test and the
+ * mu = 0 limit).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -53,7 +56,8 @@
 /* descriptor (own definition; the CUDA library has its own)           */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    int kind;            /* 1 = TTI, 2 = elastic, 3 = isotropic acoustic */
+    int kind;            /* 1 = TTI, 2 = elastic, 3 = isotropic acoustic,
+                            4 = 2D elastic (x-z plane, ny = 1) */
     int nx, ny, nz;      /* PHYSICAL grid points */
     int nbl;             /* absorbing cells added on every face */
     int so;              /* space order (even) */
@@ -67,6 +71,7 @@ typedef struct {
 typedef struct {
     or_desc d;
     int NX, NY, NZ;      /* computational grid */
+    int nby;             /* absorbing cells on the y faces (0 in 2D) */
     long N;
     int M;
     double c[MAXM + 1];  /* centred weights c_1..c_M */
@@ -323,7 +328,7 @@ static void extend(const float *phys, double *comp, const or_prob *P, double sca
         for (int y = 0; y < P->NY; y++)
             for (int z = 0; z < P->NZ; z++) {
                 int i = clampi(x - d->nbl, 0, d->nx - 1);
-                int j = clampi(y - d->nbl, 0, d->ny - 1);
+                int j = clampi(y - P->nby, 0, d->ny - 1);
                 int k = clampi(z - d->nbl, 0, d->nz - 1);
                 comp[((long)x * P->NY + y) * P->NZ + z] =
                     scale * (double)phys[((long)i * d->ny + j) * d->nz + k];
@@ -339,7 +344,7 @@ static void fold(const double *comp, double *phys, const or_prob *P)
         for (int y = 0; y < P->NY; y++)
             for (int z = 0; z < P->NZ; z++) {
                 int i = clampi(x - d->nbl, 0, d->nx - 1);
-                int j = clampi(y - d->nbl, 0, d->ny - 1);
+                int j = clampi(y - P->nby, 0, d->ny - 1);
                 int k = clampi(z - d->nbl, 0, d->nz - 1);
                 phys[((long)i * d->ny + j) * d->nz + k] += comp[((long)x * P->NY + y) * P->NZ + z];
             }
@@ -377,7 +382,7 @@ static double cerjan(const or_prob *P, double sx, double sy, double sz)
     if (d->nbl <= 0) return 1.0;
     const double a = 0.015;
     double dx = a * layer_depth(sx, d->nbl, d->nx);
-    double dy = a * layer_depth(sy, d->nbl, d->ny);
+    double dy = a * layer_depth(sy, P->nby, d->ny);
     double dz = a * layer_depth(sz, d->nbl, d->nz);
     return exp(-dx * dx) * exp(-dy * dy) * exp(-dz * dz);
 }
@@ -410,11 +415,12 @@ or_prob *or_create(const or_desc *d, const float *const *model)
     if (!d || d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nbl < 0 || d->so < 2 ||
         d->so % 2 || d->so / 2 > MAXM || d->nt < 1 || !(d->h > 0) || !(d->dt > 0))
         return NULL;
-    if (d->kind != 1 && d->kind != 2 && d->kind != 3) return NULL;
+    if (d->kind < 1 || d->kind > 4 || (d->kind == 4 && d->ny != 1)) return NULL;
     or_prob *P = (or_prob *)calloc(1, sizeof(or_prob));
     P->d = *d;
     P->NX = d->nx + 2 * d->nbl;
-    P->NY = d->ny + 2 * d->nbl;
+    P->nby = d->kind == 4 ? 0 : d->nbl;
+    P->NY = d->ny + 2 * P->nby;
     P->NZ = d->nz + 2 * d->nbl;
     P->N = (long)P->NX * P->NY * P->NZ;
     P->M = d->so / 2;
@@ -507,7 +513,7 @@ static int trilinear(const or_prob *P, const float *xyz, long *idx, double *w)
     double s[3]; int i0[3]; double f[3];
     int n[3] = {P->NX, P->NY, P->NZ};
     for (int a = 0; a < 3; a++) {
-        s[a] = (double)xyz[a] / P->d.h + P->d.nbl;
+        s[a] = (double)xyz[a] / P->d.h + (a == 1 ? P->nby : P->d.nbl);
         if (!(s[a] >= 0.0) || s[a] > (double)(n[a] - 1)) return -1;
         i0[a] = (int)floor(s[a]);
         f[a] = s[a] - i0[a];
@@ -1734,6 +1740,191 @@ int or_el_step_state_d(or_prob *P, double *state, int adjoint, int nsteps)
     return OR_OK;
 }
 
+/* ------------------------------------------------------------------ */
+/* 2D elastic (x-z plane; Sec. IV-A system, 2D example of Sec. IV-B):  */
+/* velocities vx, vz and stresses txx, tzz, txz on the staggered grid   */
+/* of the 3D system with every y term dropped (ny = 1, no layer in y).  */
+/* The state uses the 3D slots VX, VZ, TXX, TZZ, TXZ; the others stay 0. */
+/* ------------------------------------------------------------------ */
+static void el2_div_tau(const or_prob *P, double *const *s, double *dvx, double *dvz)
+{
+    long N = P->N;
+    double *t = dalloc(N);
+    /* x: D+x txx + D-z txz ;  z: D-x txz + D+z tzz */
+    apply_axis(line_Dp, s[TXX], dvx, 0, P);
+    apply_axis(line_Dm, s[TXZ], t, 2, P); for (long q = 0; q < N; q++) dvx[q] += t[q];
+    apply_axis(line_Dm, s[TXZ], dvz, 0, P);
+    apply_axis(line_Dp, s[TZZ], t, 2, P); for (long q = 0; q < N; q++) dvz[q] += t[q];
+    free(t);
+}
+
+/* strain of v: exx = D-x vx, ezz = D-z vz, gxz = D+z vx + D+x vz */
+static void el2_strain(const or_prob *P, double *const *s, double *exx, double *ezz, double *gxz)
+{
+    long N = P->N;
+    double *t = dalloc(N);
+    apply_axis(line_Dm, s[VX], exx, 0, P);
+    apply_axis(line_Dm, s[VZ], ezz, 2, P);
+    apply_axis(line_Dp, s[VX], gxz, 2, P);
+    apply_axis(line_Dp, s[VZ], t, 0, P); for (long q = 0; q < N; q++) gxz[q] += t[q];
+    free(t);
+}
+
+/* 2D stiffness: sxx = lam (exx + ezz) + 2 mu exx, szz = lam (exx + ezz) + 2 mu ezz,
+ * sxz = mu_avg gxz (mu averaged over the 4 nodes around the x-z edge point) */
+static void el2_stiff(const or_prob *P, const double *exx, const double *ezz, const double *gxz,
+                      double *sxx, double *szz, double *sxz)
+{
+#pragma omp parallel for
+    for (int x = 0; x < P->NX; x++)
+        for (int z = 0; z < P->NZ; z++) {
+            long q = IDX(P, x, 0, z);
+            double tr = exx[q] + ezz[q];
+            sxx[q] = P->lam[q] * tr + 2.0 * P->mu[q] * exx[q];
+            szz[q] = P->lam[q] * tr + 2.0 * P->mu[q] * ezz[q];
+            sxz[q] = muavg(P, 0, 2, x, 0, z) * gxz[q];
+        }
+}
+
+/* one forward step in place: v <- g (v + dt b div tau); tau <- g (tau + dt C S(v)) */
+static void el2_step(const or_prob *P, double *const *s)
+{
+    long N = P->N; double dt = P->d.dt;
+    double *dvx = dalloc(N), *dvz = dalloc(N), *e[3], *sg[3];
+    for (int i = 0; i < 3; i++) { e[i] = dalloc(N); sg[i] = dalloc(N); }
+    el2_div_tau(P, s, dvx, dvz);
+#pragma omp parallel for
+    for (int x = 0; x < P->NX; x++)
+        for (int z = 0; z < P->NZ; z++) {
+            long q = IDX(P, x, 0, z);
+            s[VX][q] = gtaper(P, VX, x, 0, z) * (s[VX][q] + dt * bavg(P, 0, x, 0, z) * dvx[q]);
+            s[VZ][q] = gtaper(P, VZ, x, 0, z) * (s[VZ][q] + dt * bavg(P, 2, x, 0, z) * dvz[q]);
+        }
+    el2_strain(P, s, e[0], e[1], e[2]);
+    el2_stiff(P, e[0], e[1], e[2], sg[0], sg[1], sg[2]);
+    const int comp[3] = {TXX, TZZ, TXZ};
+#pragma omp parallel for
+    for (int x = 0; x < P->NX; x++)
+        for (int z = 0; z < P->NZ; z++) {
+            long q = IDX(P, x, 0, z);
+            for (int c = 0; c < 3; c++)
+                s[comp[c]][q] = gtaper(P, comp[c], x, 0, z) * (s[comp[c]][q] + dt * sg[c][q]);
+        }
+    free(dvx); free(dvz);
+    for (int i = 0; i < 3; i++) { free(e[i]); free(sg[i]); }
+}
+
+/* transpose of el2_step, in place (literal transposes, as el_step_T):
+ *   t = g tau' ; vbar = v' + dt S^T (C t) ; tau = t ; s = g vbar ; tau += dt Dtau^T (b s) ; v = s */
+static void el2_step_T(const or_prob *P, double *const *s)
+{
+    long N = P->N; double dt = P->d.dt;
+    const int comp[3] = {TXX, TZZ, TXZ};
+    double *t[3], *sg[3], *wx = dalloc(N), *wz = dalloc(N);
+    for (int i = 0; i < 3; i++) { t[i] = dalloc(N); sg[i] = dalloc(N); }
+#pragma omp parallel for
+    for (int x = 0; x < P->NX; x++)
+        for (int z = 0; z < P->NZ; z++) {
+            long q = IDX(P, x, 0, z);
+            for (int c = 0; c < 3; c++) t[c][q] = gtaper(P, comp[c], x, 0, z) * s[comp[c]][q];
+        }
+    el2_stiff(P, t[0], t[1], t[2], sg[0], sg[1], sg[2]);
+    /* S^T: exx = D-x vx, ezz = D-z vz, gxz = D+z vx + D+x vz */
+    apply_axisT(line_DmT_add, sg[0], s[VX], 0, P, dt);
+    apply_axisT(line_DmT_add, sg[1], s[VZ], 2, P, dt);
+    apply_axisT(line_DpT_add, sg[2], s[VX], 2, P, dt);
+    apply_axisT(line_DpT_add, sg[2], s[VZ], 0, P, dt);
+    for (int c = 0; c < 3; c++) memcpy(s[comp[c]], t[c], sizeof(double) * N);
+#pragma omp parallel for
+    for (int x = 0; x < P->NX; x++)
+        for (int z = 0; z < P->NZ; z++) {
+            long q = IDX(P, x, 0, z);
+            s[VX][q] *= gtaper(P, VX, x, 0, z);
+            s[VZ][q] *= gtaper(P, VZ, x, 0, z);
+            wx[q] = bavg(P, 0, x, 0, z) * s[VX][q];
+            wz[q] = bavg(P, 2, x, 0, z) * s[VZ][q];
+        }
+    /* Dtau^T: dvx = D+x txx + D-z txz, dvz = D-x txz + D+z tzz */
+    apply_axisT(line_DpT_add, wx, s[TXX], 0, P, dt);
+    apply_axisT(line_DmT_add, wx, s[TXZ], 2, P, dt);
+    apply_axisT(line_DmT_add, wz, s[TXZ], 0, P, dt);
+    apply_axisT(line_DpT_add, wz, s[TZZ], 2, P, dt);
+    free(wx); free(wz);
+    for (int i = 0; i < 3; i++) { free(t[i]); free(sg[i]); }
+}
+
+/* forward modelling: record txx + tzz (2D trace of stress) from X^n, step,
+ * inject dt q^n into txx and tzz (explosive source). traces [nrec][nt] */
+int or_el2_forward(or_prob *P, int nsrc, const float *src, const float *wav,
+                   int nrec, const float *rec, double *traces)
+{
+    if (P->d.kind != 4) return OR_EINVAL;
+    int e1, e2;
+    pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
+    if (e1 || e2) { free(S); free(R); return OR_EINVAL; }
+    long N = P->N; int nt = P->d.nt; double dt = P->d.dt;
+    double *s[9];
+    for (int c = 0; c < 9; c++) s[c] = dalloc(N);
+    for (int n = 0; n < nt; n++) {
+        for (int i = 0; i < nrec; i++)
+            traces[(long)i * nt + n] = sample(&R[i], s[TXX]) + sample(&R[i], s[TZZ]);
+        el2_step(P, s);
+        for (int j = 0; j < nsrc; j++)
+            for (int c = 0; c < S[j].n; c++) {
+                double v = dt * S[j].w[c] * (double)wav[(long)j * nt + n];
+                s[TXX][S[j].idx[c]] += v;
+                s[TZZ][S[j].idx[c]] += v;
+            }
+    }
+    for (int c = 0; c < 9; c++) free(s[c]);
+    free(S); free(R);
+    return OR_OK;
+}
+
+/* adjoint: Xbar^{nt} = 0; k = nt-1 .. 1: Xbar^k = M^T Xbar^{k+1} + R^T r^k,
+ * qbar^{k-1} = dt P (tbar_xx + tbar_zz)^k */
+int or_el2_adjoint(or_prob *P, int nrec, const float *rec, const double *traces,
+                   int nsrc, const float *src, double *qbar)
+{
+    if (P->d.kind != 4) return OR_EINVAL;
+    int e1, e2;
+    pt8 *S = make_points(P, src, nsrc, &e1), *R = make_points(P, rec, nrec, &e2);
+    if (e1 || e2) { free(S); free(R); return OR_EINVAL; }
+    long N = P->N; int nt = P->d.nt; double dt = P->d.dt;
+    double *s[9];
+    for (int c = 0; c < 9; c++) s[c] = dalloc(N);
+    memset(qbar, 0, sizeof(double) * (size_t)nsrc * nt);
+    for (int k = nt - 1; k >= 1; k--) {
+        el2_step_T(P, s);
+        for (int i = 0; i < nrec; i++)
+            for (int c = 0; c < R[i].n; c++) {
+                double v = R[i].w[c] * traces[(long)i * nt + k];
+                s[TXX][R[i].idx[c]] += v;
+                s[TZZ][R[i].idx[c]] += v;
+            }
+        for (int j = 0; j < nsrc; j++)
+            qbar[(long)j * nt + (k - 1)] = dt * (sample(&S[j], s[TXX]) + sample(&S[j], s[TZZ]));
+    }
+    for (int c = 0; c < 9; c++) free(s[c]);
+    free(S); free(R);
+    return OR_OK;
+}
+
+/* nsteps source-free steps (adjoint != 0: transposed steps) of a double
+ * state [9][N] in the 3D slot order (only VX, VZ, TXX, TZZ, TXZ are used) */
+int or_el2_step_state_d(or_prob *P, double *state, int adjoint, int nsteps)
+{
+    if (P->d.kind != 4) return OR_EINVAL;
+    long N = P->N;
+    double *s[9];
+    for (int c = 0; c < 9; c++) s[c] = state + (long)c * N;
+    for (int it = 0; it < nsteps; it++) {
+        if (!adjoint) el2_step(P, s);
+        else el2_step_T(P, s);
+    }
+    return OR_OK;
+}
+
 /* TTI in double precision, many steps, no sources (p0,p1,r0,r1 in/out) */
 int or_tti_step_state_d(or_prob *P, double *p0, double *p1, double *r0, double *r1, int nsteps)
 {
@@ -1832,6 +2023,7 @@ int or_el_step_points(const or_desc *d, const float *const *model, const float *
     for (int k = 1; k <= C.M; k++) C.b[k] = tmp[k - 1];
     C.vp = model[0]; C.vs = model[1]; C.rho = model[2]; C.st = state;
     or_prob Pd; memset(&Pd, 0, sizeof(Pd)); Pd.d = *d; Pd.NX = C.NX; Pd.NY = C.NY; Pd.NZ = C.NZ;
+    Pd.nby = d->nbl;
     C.P = &Pd;
 #pragma omp parallel for
     for (int i = 0; i < npts; i++) {

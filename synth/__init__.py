@@ -25,6 +25,7 @@ import numpy as np
 TTI = 1
 ELASTIC = 2
 ACOUSTIC = 3
+ELASTIC2D = 4      # x-z plane, ny = 1
 
 DEG = math.pi / 180.0
 
@@ -129,7 +130,7 @@ class Problem:
 
     def model_list(self):
         keys = {TTI: ("vp", "eps", "delta", "theta", "phi"), ELASTIC: ("vp", "vs", "rho"),
-                ACOUSTIC: ("vp",)}[self.kind]
+                ACOUSTIC: ("vp",), ELASTIC2D: ("vp", "vs", "rho")}[self.kind]
         return [np.ascontiguousarray(self.model[k], dtype=np.float32) for k in keys]
 
 
@@ -450,3 +451,51 @@ def acoustic_rtm_shots(nshots=8, nt=150, seed=20047, size_range=(200, 600), nz=3
                      name=name.replace("window", "window-migration"))
         shots.append((true, p0, (ox, oy, 0)))
     return shots
+
+
+# --------------------------------------------------------------------------
+# 2D elastic workloads (x-z plane, ny = 1)
+# --------------------------------------------------------------------------
+def marine_elastic_2d(nx=1701, nz=701, h=5.0, nbl=40, so=8, nt=2000, f0=15.0, seed=20048,
+                      water_depth=450.0, rec_dx=10.0) -> Problem:
+    """2D elastic marine model standing in for the elastic Marmousi-II of the
+    2D example: a water layer (vp 1.5 km/s, vs 0, rho 1.02 g/cc) over a
+    layered elastic subsurface (vp 1.6 -> 4.5 km/s with depth plus smooth
+    noise, vs = vp / 1.9, rho = 0.31 vp^0.25 (Gardner, vp in m/s));
+    explosive source 10 m deep at the centre; pressure receivers every
+    rec_dx at 5 m depth."""
+    z = np.arange(nz) * h
+    noise = smooth_noise((nx, 1, nz), 8.0, seed)[:, 0, :] * 2.0 - 1.0
+    frac = np.clip((z - water_depth) / max(z[-1] - water_depth, h), 0.0, 1.0)
+    vlayer = 1.6 + (4.5 - 1.6) * np.floor(frac * 12.0) / 11.0
+    vp = np.clip(vlayer[None, :] + 0.25 * noise, 1.6, 4.5)
+    water = (z < water_depth)[None, :]
+    vp = np.where(water, 1.5, vp)
+    vs = np.where(water, 0.0, vp / 1.9)
+    rho = np.where(water, 1.02, 0.31 * (vp * 1000.0) ** 0.25)
+    f32 = lambda a: np.ascontiguousarray(a[:, None, :], dtype=np.float32)
+    model = {"vp": f32(vp), "vs": f32(vs), "rho": f32(rho)}
+    dt = cfl_dt(h, float(vp.max()))
+    src = np.array([[(nx // 2) * h, 0.0, 10.0]], np.float32)
+    nrec = int(((nx - 1) * h) // rec_dx) + 1
+    rec = np.zeros((nrec, 3), np.float32)
+    rec[:, 0] = np.arange(nrec) * rec_dx
+    rec[:, 2] = 5.0
+    wav = ricker(f0, dt, nt)[None, :]
+    return Problem(ELASTIC2D, nx, 1, nz, nbl, h, so, nt, dt, model, src, wav, rec,
+                   name=f"elastic2d-marine-{nx}x{nz}-so{so}-nt{nt}")
+
+
+def elastic2d_small(shape=(45, 38), nbl=7, h=10.0, so=8, nt=70, seed=4):
+    """Small heterogeneous 2D elastic problem (parity tests): smooth random
+    vp, vs, rho; two sources; a line of receivers."""
+    nx, nz = shape
+    m3 = random_elastic(nx, 1, nz, seed, 3.0)
+    dt = cfl_dt(h, float(m3["vp"].max()))
+    src = np.array([[nx * h * 0.45 + 1.3, 0.0, 3.3 * h], [nx * h * 0.25, 0.0, nz * h * 0.6]], np.float32)
+    wav = np.vstack([ricker(25.0, dt, nt), 0.6 * ricker(18.0, dt, nt)]).astype(np.float32)
+    rec = np.zeros((11, 3), np.float32)
+    rec[:, 0] = 5.2 + (nx - 2) * h / 10.0 * np.arange(11)
+    rec[:, 2] = 1.9 * h
+    return Problem(ELASTIC2D, nx, 1, nz, nbl, h, so, nt, dt, m3, src, wav, rec,
+                   name=f"elastic2d-small-{nx}x{nz}-so{so}")
