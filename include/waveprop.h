@@ -59,8 +59,13 @@ enum {
 
 /* PROP_ACOUSTIC: the isotropic acoustic equation of Sec. II-A, Eq. (acou),
  * m u_tt - laplace(u) + damp u_t = q, laplace = sum over axes of the centred
- * second derivative of the space order, damped like TTI. */
-enum { PROP_TTI = 1, PROP_ELASTIC = 2, PROP_ACOUSTIC = 3 };
+ * second derivative of the space order, damped like TTI.
+ * PROP_ELASTIC2D: the elastic system in the x-z plane (ny = 1, no absorbing
+ * cells on the y faces; source and receiver y = 0), as in the 2D example of
+ * Sec. IV-B: fields vx, vz, txx, tzz, txz; explosive source into txx and tzz;
+ * receivers record txx + tzz.  Forward and adjoint modelling and state
+ * stepping (forward only); no gradient or saved forward run (PROP_EINVAL). */
+enum { PROP_TTI = 1, PROP_ELASTIC = 2, PROP_ACOUSTIC = 3, PROP_ELASTIC2D = 4 };
 
 /* Storage of forward wavefields for the gradient (Sec. III: full storage in
  * memory, or checkpointing).  CKPT_* keep the full state every
@@ -69,9 +74,11 @@ enum { PROP_TTI = 1, PROP_ELASTIC = 2, PROP_ACOUSTIC = 3 };
 enum { SNAP_FULL_FP32 = 0, SNAP_CKPT_FP32 = 1, SNAP_CKPT_BF16 = 2, SNAP_CKPT_FP16 = 3 };
 
 typedef struct {
-    int kind;            /* PROP_TTI, PROP_ELASTIC or PROP_ACOUSTIC           */
+    int kind;            /* PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC or
+                            PROP_ELASTIC2D                                    */
     int nx, ny, nz;      /* physical grid points (>= 1)                       */
-    int nbl;             /* absorbing cells added on every face (>= 0)        */
+    int nbl;             /* absorbing cells added on every face (>= 0; not on
+                            the y faces of PROP_ELASTIC2D)                    */
     float h;             /* grid spacing [m] (> 0)                            */
     int space_order;     /* 4, 8, 12 or 16                                    */
     int nt;              /* time samples per trace (>= 2)                     */
@@ -86,7 +93,7 @@ typedef struct {
 
 /* Create a propagator.  model points to the PHYSICAL-grid float32 arrays
  *   TTI:     vp [km/s], epsilon, delta, theta (tilt) [rad], phi (azimuth) [rad]
- *   ELASTIC: vp [km/s], vs [km/s], rho [g/cc]
+ *   ELASTIC, ELASTIC2D: vp [km/s], vs [km/s], rho [g/cc]
  *   ACOUSTIC: vp [km/s]
  * (Sec. III-A: 4 Thomsen/angle parameters + velocity; Sec. IV: Lame
  * parameters and density, lambda = rho (vp^2 - 2 vs^2), mu = rho vs^2).
@@ -207,6 +214,7 @@ int prop_plan_waves(const size_t *bytes, int n, size_t budget, int *wave_of);
 /* Wavefield state access (computational grid, float32 [NX][NY][NZ] each):
  *   TTI:     fields[0..3] = p^n, r^n, p^{n-1}, r^{n-1}
  *   ACOUSTIC: fields[0..1] = u^n, u^{n-1}
+ *   ELASTIC2D: fields[0..4] = vx vz txx tzz txz (prop_step: forward only)
  *   ELASTIC: fields[0..8] = vx vy vz txx tyy tzz txy txz tyz
  * prop_step advances nsteps steps without sources or receivers (adjoint != 0:
  * transposed step, state holds the adjoint fields in the same order). */

@@ -1,4 +1,4 @@
-"""waveprop: TTI, elastic and isotropic acoustic wave propagators on one GB300 (sm_103a).
+"""waveprop: TTI, elastic (3D and 2D) and isotropic acoustic wave propagators on one GB300 (sm_103a).
 
 Thin ctypes binding of ``libwaveprop.so`` (C ABI in ``include/waveprop.h``).
 Every step of the propagators runs in the library's CUDA kernels; this module
@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libwaveprop.so")
 
 PROP_OK, PROP_EINVAL, PROP_ENOMEM, PROP_ECUDA, PROP_EUNSTABLE, PROP_ETIMEOUT, PROP_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC = 1, 2, 3
+PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC, PROP_ELASTIC2D = 1, 2, 3, 4
 SNAP_FULL_FP32, SNAP_CKPT_FP32, SNAP_CKPT_BF16, SNAP_CKPT_FP16 = 0, 1, 2, 3
 ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA",
              -4: "PROP_EUNSTABLE", -5: "PROP_ETIMEOUT", -6: "PROP_ESTATE"}
@@ -141,10 +141,10 @@ def _stream_of(*xs):
 class Propagator:
     """Handle on one propagator (``prop_t``).
 
-    kind: PROP_TTI, PROP_ELASTIC or PROP_ACOUSTIC; model: list of
-    physical-grid float32 arrays (TTI: vp, eps, delta, theta, phi; elastic:
-    vp, vs, rho; acoustic: vp) as numpy arrays or torch tensors (host or
-    device)."""
+    kind: PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC or PROP_ELASTIC2D (x-z plane,
+    shape (nx, 1, nz)); model: list of physical-grid float32 arrays (TTI: vp,
+    eps, delta, theta, phi; elastic and 2D elastic: vp, vs, rho; acoustic:
+    vp) as numpy arrays or torch tensors (host or device)."""
 
     def __init__(self, kind, shape, nbl, h, space_order, nt, model, dt=0.0, vdamp=0.0,
                  snap_mode=SNAP_FULL_FP32, ckpt_interval=0, check_nan=0, stream=None):
@@ -175,7 +175,7 @@ class Propagator:
     @classmethod
     def from_problem(cls, prob, model=None, **kw):
         keys = {PROP_TTI: ("vp", "eps", "delta", "theta", "phi"), PROP_ELASTIC: ("vp", "vs", "rho"),
-                PROP_ACOUSTIC: ("vp",)}[prob.kind]
+                PROP_ACOUSTIC: ("vp",), PROP_ELASTIC2D: ("vp", "vs", "rho")}[prob.kind]
         ml = model if model is not None else [prob.model[k] for k in keys]
         kw.setdefault("dt", prob.dt)
         kw.setdefault("vdamp", getattr(prob, "vdamp", 0.0) or 0.0)

@@ -17,6 +17,7 @@
 struct GridDev {
     int NX, NY, NZ;          // computational grid
     int nbl, px, py, pz;     // absorbing width, physical grid
+    int nby;                 // absorbing width on the y faces (0 in 2D)
     long long N;             // NX*NY*NZ
     float h, ih, dt;         // spacing, 1/h, time step
     float sig0;              // TTI damping: sigma(d) = sig0 * (d/L)^2 per axis [1/s]
@@ -113,6 +114,9 @@ int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 // pipelined elastic step with time step dt_sign * dt (any NZ): forward (+1)
 // or the transposed step in (b_avg vbar, g C tbar) variables (-1)
 int el_launch_fast(prop_s *P, float *const *S, float dt_sign);
+// one 2D elastic step of S = (vx, vz, txx, tzz, txz); dt_sign = -1: the
+// transposed step in the adjoint-modelling variables
+int el2_launch(prop_s *P, float *const *S, float dt_sign);
 // TMA-fed passes (stencil_tma.cu): usable when NZ % 4 == 0
 bool tma_usable(const prop_s *P);
 // acoustic step (S[0] = u^n, S[1] = u^{n-1} <- u^{n+1}); grad != NULL:

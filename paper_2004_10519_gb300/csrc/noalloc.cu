@@ -159,7 +159,7 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     P->d = *d;
     P->M = so / 2;
     GridDev &g = P->g;
-    g.nbl = d->nbl; g.px = d->nx; g.py = d->ny; g.pz = d->nz;
+    g.nbl = d->nbl; g.nby = d->nbl; g.px = d->nx; g.py = d->ny; g.pz = d->nz;
     g.NX = d->nx + 2 * d->nbl; g.NY = d->ny + 2 * d->nbl; g.NZ = d->nz + 2 * d->nbl;
     g.N = (long long)g.NX * g.NY * g.NZ;
     g.h = d->h; g.ih = 1.f / d->h; g.cer = 0.015f;

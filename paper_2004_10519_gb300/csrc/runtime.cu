@@ -153,20 +153,21 @@ double symbol_max(const float *w, int M, bool stag)
 // node or at the half point of a staggered component).
 std::vector<float> layer_tables(const GridDev &g, int kind)
 {
-    auto depth = [&](double s, int n) {
-        const double lo = g.nbl, hi = g.nbl + n - 1;
+    auto depth = [&](double s, int a) {
+        const int nb = a == 1 ? g.nby : g.nbl, n = a == 0 ? g.px : (a == 1 ? g.py : g.pz);
+        const double lo = nb, hi = nb + n - 1;
         return s < lo ? lo - s : (s > hi ? s - hi : 0.0);
     };
-    const int NN[3] = {g.NX, g.NY, g.NZ}, PN[3] = {g.px, g.py, g.pz};
+    const int NN[3] = {g.NX, g.NY, g.NZ};
     std::vector<float> t;
     for (int a = 0; a < 3; a++)
         for (int i = 0; i < NN[a]; i++) {
-            if (kind != PROP_ELASTIC) {                  // TTI, acoustic: damping rate
-                const double d = g.nbl > 0 ? depth(i, PN[a]) / g.nbl : 0.0;
+            if (kind == PROP_TTI || kind == PROP_ACOUSTIC) {   // damping rate
+                const double d = g.nbl > 0 ? depth(i, a) / g.nbl : 0.0;
                 t.push_back((float)((double)g.sig0 * d * d));
             } else {
                 for (int hf = 0; hf < 2; hf++) {
-                    const double d = g.nbl > 0 ? (double)g.cer * depth(i + 0.5 * hf, PN[a]) : 0.0;
+                    const double d = g.nbl > 0 ? (double)g.cer * depth(i + 0.5 * hf, a) : 0.0;
                     t.push_back((float)exp(-d * d));
                 }
             }
@@ -211,8 +212,17 @@ static int copy_out(prop_s *P, float *dst, const float *src_dev, size_t n)
     return PROP_OK;
 }
 
-// state fields: TTI (p, r) at two levels, acoustic u at two levels, elastic 9
-static int nfields(const prop_s *P) { return P->d.kind == PROP_TTI ? 4 : (P->d.kind == PROP_ACOUSTIC ? 2 : 9); }
+// state fields: TTI (p, r) at two levels, acoustic u at two levels, elastic 9,
+// 2D elastic 5
+static int nfields(const prop_s *P)
+{
+    switch (P->d.kind) {
+    case PROP_TTI: return 4;
+    case PROP_ACOUSTIC: return 2;
+    case PROP_ELASTIC2D: return 5;
+    default: return 9;
+    }
+}
 
 // ---------------------------------------------------------------------------
 // profiling
@@ -328,7 +338,7 @@ static std::string tune_key(const prop_s *P)
 static int autotune_xchunk(prop_s *P)
 {
     const char *on = getenv("WAVEPROP_AUTOTUNE");
-    if (on && !strcmp(on, "0")) return PROP_OK;
+    if ((on && !strcmp(on, "0")) || P->d.kind == PROP_ELASTIC2D) return PROP_OK;   // 2D passes have no x chunks
     const char *path = getenv("WAVEPROP_AUTOTUNE_CACHE");
     const std::string key = tune_key(P);
     {
@@ -396,8 +406,9 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
 {
     P->d = *d;
     const int so = d->space_order;
-    if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC && d->kind != PROP_ACOUSTIC)
-        return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI, PROP_ELASTIC or PROP_ACOUSTIC");
+    if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC && d->kind != PROP_ACOUSTIC && d->kind != PROP_ELASTIC2D)
+        return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC or PROP_ELASTIC2D");
+    if (d->kind == PROP_ELASTIC2D && d->ny != 1) return wp_fail(P, PROP_EINVAL, "PROP_ELASTIC2D needs ny = 1");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return wp_fail(P, PROP_EINVAL, "grid sizes must be >= 1");
     if (d->nbl < 0) return wp_fail(P, PROP_EINVAL, "nbl must be >= 0");
     if (!(d->h > 0.f) || !std::isfinite(d->h)) return wp_fail(P, PROP_EINVAL, "h must be > 0");
@@ -412,8 +423,9 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     P->M = so / 2;
     GridDev &g = P->g;
     g.nbl = d->nbl;
+    g.nby = d->kind == PROP_ELASTIC2D ? 0 : d->nbl;
     g.px = d->nx; g.py = d->ny; g.pz = d->nz;
-    g.NX = d->nx + 2 * d->nbl; g.NY = d->ny + 2 * d->nbl; g.NZ = d->nz + 2 * d->nbl;
+    g.NX = d->nx + 2 * d->nbl; g.NY = d->ny + 2 * g.nby; g.NZ = d->nz + 2 * d->nbl;
     g.N = (long long)g.NX * g.NY * g.NZ;
     if (g.N >= (1LL << 32)) return wp_fail(P, PROP_EINVAL, "computational grid above 2^32 - 1 points");
     g.h = d->h; g.ih = 1.f / d->h;
@@ -453,10 +465,11 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     g.dt = (float)dt;
     P->d.dt = g.dt;
     // CFL: vmax dt / h <= 2 / (sqrt(3) max|symbol|)
-    // (acoustic: vmax dt / h <= 2 / sqrt(3 max|symbol of h^2 D2|))
-    const bool stag = d->kind == PROP_ELASTIC;
+    // (acoustic: vmax dt / h <= 2 / sqrt(3 max|symbol of h^2 D2|); 2D: sqrt(2))
+    const bool stag = d->kind == PROP_ELASTIC || d->kind == PROP_ELASTIC2D;
+    const double ndim = d->kind == PROP_ELASTIC2D ? 2.0 : 3.0;
     const double lim = d->kind == PROP_ACOUSTIC ? 2.0 / sqrt(3.0 * symbol2_max(P->w.d2, P->M))
-                                                : 2.0 / (sqrt(3.0) * symbol_max(stag ? P->w.b : P->w.c, P->M, stag));
+                                                : 2.0 / (sqrt(ndim) * symbol_max(stag ? P->w.b : P->w.c, P->M, stag));
     const double cour = vmax * dt / d->h;
     if (cour > lim) {
         char buf[200];
@@ -625,6 +638,9 @@ static int step_state(prop_s *P, float **s, bool adjoint)
     } else if (P->d.kind == PROP_ACOUSTIC) {          // the transposed step is the same map
         WP_TRY(acu_launch_step(P, s, nullptr, nullptr));
         std::swap(s[0], s[1]);
+    } else if (P->d.kind == PROP_ELASTIC2D) {
+        if (adjoint) return wp_fail(P, PROP_EINVAL, "transposed state steps are not available for PROP_ELASTIC2D");
+        WP_TRY(el2_launch(P, s, 1.f));
     } else {
         if (adjoint) WP_TRY(ensure_tmp(P, 9));
         WP_TRY(el_launch_step(P, s, adjoint));
@@ -689,7 +705,10 @@ static int ckpt_K(const prop_s *P)
 }
 
 // slots of wavefield storage
-static size_t snap_fields(const prop_s *P) { return P->d.kind == PROP_TTI ? 2 : (P->d.kind == PROP_ACOUSTIC ? 1 : 9); }
+static size_t snap_fields(const prop_s *P)
+{
+    return P->d.kind == PROP_TTI ? 2 : (P->d.kind == PROP_ACOUSTIC ? 1 : (P->d.kind == PROP_ELASTIC2D ? 5 : 9));
+}
 
 static int alloc_saves(prop_s *P)
 {
@@ -774,12 +793,15 @@ static void inject_src(prop_s *P, const SparseDev &S, const float *wav, int n, f
         sp_inject(P, &S, wav, nt, n, P->g.dt * P->g.dt, 1, s[0], s[1], nullptr, nullptr, nullptr);
     else if (P->d.kind == PROP_ACOUSTIC)
         sp_inject(P, &S, wav, nt, n, P->g.dt * P->g.dt, 1, s[0], nullptr, nullptr, nullptr, nullptr);
+    else if (P->d.kind == PROP_ELASTIC2D)
+        sp_inject(P, &S, wav, nt, n, P->g.dt, 0, s[2], s[3], nullptr, nullptr, nullptr);
     else
         sp_inject(P, &S, wav, nt, n, P->g.dt, 0, s[3], s[4], s[5], nullptr, nullptr);
 }
 static void record_rec(prop_s *P, const SparseDev &R, float *const *s, float *col)
 {
-    if (P->d.kind != PROP_ELASTIC) sp_record(P, &R, s[0], nullptr, nullptr, 1.f, col);
+    if (P->d.kind == PROP_TTI || P->d.kind == PROP_ACOUSTIC) sp_record(P, &R, s[0], nullptr, nullptr, 1.f, col);
+    else if (P->d.kind == PROP_ELASTIC2D) sp_record(P, &R, s[2], s[3], nullptr, 1.f, col);
     else sp_record(P, &R, s[3], s[4], s[5], 1.f, col);
 }
 
@@ -795,6 +817,8 @@ static int fwd_step(prop_s *P, float **s, const SparseDev &S, const float *wav, 
     } else if (P->d.kind == PROP_ACOUSTIC) {
         WP_TRY(acu_launch_step(P, s, nullptr, nullptr));
         std::swap(s[0], s[1]);
+    } else if (P->d.kind == PROP_ELASTIC2D) {
+        WP_TRY(el2_launch(P, s, 1.f));
     } else {
         WP_TRY(el_launch_step(P, s, false));
     }
@@ -859,6 +883,8 @@ static int forward_impl(prop_s *P, const float *wavelet, const float *src, int n
 {
     WP_TRY(check_handle(P));
     if (!wavelet || !traces) return wp_fail(P, PROP_EINVAL, "wavelet or traces is NULL");
+    if (save && P->d.kind == PROP_ELASTIC2D)
+        return wp_fail(P, PROP_EINVAL, "gradients and saved forward runs are not available for PROP_ELASTIC2D");
     Geometry G;
     WP_TRY(build_geometry(P, G, src, nsrc, rec, nrec));
     const int nt = P->d.nt;
@@ -1038,6 +1064,27 @@ static int ac_sweep(prop_s *P, const Geometry &G, const float *res, const float 
     return PROP_OK;
 }
 
+// 2D elastic adjoint modelling in the variables (b_avg vbar, g C tbar): the
+// forward passes with dt -> -dt; residuals enter as g (2 lambda + 2 mu) r on
+// xx and zz, the source side reads dt (u_xx + u_zz) / (g (2 lambda + 2 mu))
+static int el2_sweep(prop_s *P, const Geometry &G, const float *res, float *srcstage)
+{
+    const int nt = P->d.nt;
+    WP_TRY(ensure_ast(P));
+    float *a[5];
+    for (int i = 0; i < 5; i++) a[i] = P->ast[i];
+    WP_TRY(zero_fields(P, a, 5));
+    if (srcstage) WP_CK(P, cudaMemsetAsync(srcstage, 0, sizeof(float) * (size_t)nt * G.S.n, P->stream));
+    for (int k = nt - 1; k >= 1; k--) {
+        WP_TRY(el2_launch(P, a, -1.f));
+        sp_inject(P, &G.R, res, nt, k, 1.f, 4, a[2], a[3], nullptr, nullptr, nullptr);
+        if (srcstage)
+            sp_record_trace_s(P, &G.S, a[2], a[3], nullptr, P->g.dt, srcstage + (size_t)(k - 1) * G.S.n);
+        prof_maybe_collect(P);
+    }
+    return PROP_OK;
+}
+
 // elastic adjoint sweep; g3 != NULL: gradient (lambda, mu, b) on the computational grid
 static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float *wav,
                     float *srcstage, float *const *g3)
@@ -1125,6 +1172,7 @@ extern "C" int prop_adjoint(prop_t *P, const float *traces_in, const float *rec_
     WP_TRY(wp_malloc(P, &out.p, sizeof(float) * (size_t)nt * nsrc, "source output"));
     if (P->d.kind == PROP_TTI) WP_TRY(tti_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
     else if (P->d.kind == PROP_ACOUSTIC) WP_TRY(ac_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
+    else if (P->d.kind == PROP_ELASTIC2D) WP_TRY(el2_sweep(P, G, res, (float *)stage.p));
     else WP_TRY(el_sweep(P, G, res, nullptr, (float *)stage.p, nullptr));
     sp_transpose(P, (const float *)stage.p, (float *)out.p, nsrc, nt);
     WP_TRY(copy_out(P, src_out, (const float *)out.p, (size_t)nt * nsrc));

@@ -54,11 +54,12 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
         const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
         const float A = m[q] * (1.f + 0.5f * tti_sigma(g, x, y, z) * g.dt);
         coef = scale / A;
-    } else if (mode == 2) {
-        // residual into u = g C tbar: g (3 lambda + 2 mu) on each diagonal component
+    } else if (mode == 2 || mode == 4) {
+        // residual into u = g C tbar: g (3 lambda + 2 mu) on each diagonal
+        // component (mode 4, the x-z plane: g (2 lambda + 2 mu) on xx, zz)
         const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
         const float gn = g.tab[2 * x] * g.tab[2 * g.NX + 2 * y] * g.tab[2 * (g.NX + g.NY) + 2 * z];
-        coef = scale * (3.f * lam[q] + 2.f * mu[q]) * gn;
+        coef = scale * ((mode == 2 ? 3.f : 2.f) * lam[q] + 2.f * mu[q]) * gn;
     }
     const float v = coef * acc;
     f0[q] += v;
@@ -77,8 +78,9 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
 __global__ void record_s_kernel(GridDev g, int n, const long long *__restrict__ idx, const float *__restrict__ w,
                                 const float *__restrict__ f0, const float *__restrict__ f1,
                                 const float *__restrict__ f2, const float *__restrict__ lam,
-                                const float *__restrict__ mu, float scale, float *__restrict__ out)
+                                const float *__restrict__ mu, float nl, float scale, float *__restrict__ out)
 {
+    // nl = 3 (3D) or 2 (x-z plane, f2 == NULL): C of the unit diagonal is (nl lambda + 2 mu)
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float s = 0.f;
@@ -91,7 +93,7 @@ __global__ void record_s_kernel(GridDev g, int n, const long long *__restrict__ 
             const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY),
                       x = (int)(q / ((long long)g.NZ * g.NY));
             const float gn = g.tab[2 * x] * g.tab[2 * g.NX + 2 * y] * g.tab[2 * (g.NX + g.NY) + 2 * z];
-            s += wc * (f0[q] + f1[q] + f2[q]) / ((3.f * lam[q] + 2.f * mu[q]) * gn);
+            s += wc * (f0[q] + f1[q] + (f2 ? f2[q] : 0.f)) / ((nl * lam[q] + 2.f * mu[q]) * gn);
         }
     }
     out[i] = scale * s;
@@ -126,7 +128,7 @@ __global__ void extend_kernel(GridDev g, const float *__restrict__ phys, float *
     long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (q >= g.N) return;
     const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
-    const int i = clampi(x - g.nbl, 0, g.px - 1), j = clampi(y - g.nbl, 0, g.py - 1),
+    const int i = clampi(x - g.nbl, 0, g.px - 1), j = clampi(y - g.nby, 0, g.py - 1),
               k = clampi(z - g.nbl, 0, g.pz - 1);
     const float v = phys[((long long)i * g.py + j) * g.pz + k];
     if (mode == 0) comp[q] = scale * v;
@@ -314,7 +316,7 @@ int sp_build(prop_s *P, const float *xyz, int n, const int *trace_of_point, Spar
         double s[3], f[3];
         int i0[3];
         for (int a = 0; a < 3; a++) {
-            s[a] = (double)xyz[3 * i + a] / (double)g.h + (double)g.nbl;
+            s[a] = (double)xyz[3 * i + a] / (double)g.h + (double)(a == 1 ? g.nby : g.nbl);
             if (!(s[a] >= 0.0) || s[a] > (double)(dims[a] - 1))
                 return wp_fail(P, PROP_EINVAL, "sparse point " + std::to_string(i) + " outside the grid");
             i0[a] = (int)std::floor(s[a]);
@@ -398,7 +400,7 @@ void sp_record_trace_s(prop_s *P, const SparseDev *S, const float *f0, const flo
 {
     if (S->n <= 0) return;
     record_s_kernel<<<nblk(S->n), NB, 0, P->stream>>>(P->g, S->n, S->rec_idx, S->rec_w, f0, f1, f2, P->lam,
-                                                      P->mu, scale, out_col);
+                                                      P->mu, f2 ? 3.f : 2.f, scale, out_col);
     P->kern_launches++;
 }
 
@@ -435,7 +437,7 @@ void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2)
     const long long n1 = (long long)g.NX * g.NY * g.pz, n2 = (long long)g.NX * g.py * g.pz,
                     n3 = (long long)g.px * g.py * g.pz;
     fold_axis_kernel<<<nblk(n1), NB, 0, P->stream>>>(comp, s1, g.NX, g.NY, g.NZ, 2, g.pz, g.nbl);
-    fold_axis_kernel<<<nblk(n2), NB, 0, P->stream>>>(s1, s2, g.NX, g.NY, g.pz, 1, g.py, g.nbl);
+    fold_axis_kernel<<<nblk(n2), NB, 0, P->stream>>>(s1, s2, g.NX, g.NY, g.pz, 1, g.py, g.nby);
     fold_axis_kernel<<<nblk(n3), NB, 0, P->stream>>>(s2, phys, g.NX, g.py, g.pz, 0, g.px, g.nbl);
     P->kern_launches += 3;
 }
