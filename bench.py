@@ -275,6 +275,37 @@ def acoustic_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40
     return out
 
 
+def elastic2d_throughput(wp, torch, dev, small=False):
+    """2D elastic forward modelling (so 8) on the marine model standing in for
+    the elastic Marmousi-II of the 2D example: 1701 x 701 cells at 5 m +
+    40-cell layer (x, z), water 450 m deep, 15 Hz explosive source 10 m
+    deep, pressure receivers every 10 m at 5 m depth.  Whole-run time and
+    the step kernels' time (velocity + stress pass)."""
+    kw = dict(nx=401, nz=201, nt=400) if small else dict(nt=2000)
+    p = synth.marine_elastic_2d(**kw)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    prop = wp.Propagator.from_problem(p, stream=stream)
+    w, s_, r = to(p.wavelet), to(p.src), to(p.rec)
+    prop.forward(w, s_, r)                                  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    prop.forward(w, s_, r)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    prop.profile(True)
+    prop.forward(w, s_, r)
+    kms, kn = prop.kernel_stats(wp.K_EL_FWD)
+    prop.profile(False)
+    N = int(np.prod(prop.grid))
+    prop.close()
+    t_step = kms / max(kn, 1) / 1e3
+    # algorithmic bytes: 5 state reads + 5 writes + b, lambda, mu = 52 B/pt
+    return {"grid": list(prop.grid), "nt": p.nt, "seconds": sec,
+            "gpts_per_s": N * p.nt / sec / 1e9, "kernel_ms_per_step": t_step * 1e3,
+            "kernel_gpts_per_s": N / t_step / 1e9, "alg_gbs": 52.0 * N / t_step / 1e9}
+
+
 def rtm_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
     """Reverse-time migration over many shots (acoustic so 12, FP32
     checkpoints): per-shot images (dJ/dm against the true model's data, in
@@ -477,7 +508,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--extra", default="",
-                    help="comma list: tti, acoustic, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
+                    help="comma list: tti, acoustic, el2d, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--batch-shots", type=int, default=8)
     ap.add_argument("--batch-nt", type=int, default=150)
@@ -502,6 +533,8 @@ def main():
                 out["acoustic"] = acoustic_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
             else:
                 out["acoustic"] = acoustic_throughput(wp, torch, dev)
+        if "el2d" in extras:
+            out["el2d"] = elastic2d_throughput(wp, torch, dev, small=args.small)
         if "rtm" in extras:
             out["rtm"] = rtm_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt, small=args.small)
         if "grad" in extras:
