@@ -73,6 +73,7 @@ def lib():
             L.or_ac_step_state_d.argtypes = [P, dp, dp, C.c_int]
             L.or_ac_step_points.argtypes = [C.POINTER(_Desc), fp, fp, fp, C.c_int, lp, dp]
             L.or_weights_d2.argtypes = [C.c_int, dp]
+            L.or_tti_set_operator.argtypes = [P, C.c_int]
             L.or_el2_forward.argtypes = [P, C.c_int, fp, fp, C.c_int, fp, dp]
             L.or_el2_adjoint.argtypes = [P, C.c_int, fp, dp, C.c_int, fp, dp]
             L.or_el2_step_state_d.argtypes = [P, dp, C.c_int, C.c_int]
@@ -173,6 +174,8 @@ class Problem:
         self.h = lib().or_create(C.byref(self.desc), arr)
         if not self.h:
             raise ValueError("oracle: invalid problem")
+        if getattr(prob, "tti_op", 0):
+            lib().or_tti_set_operator(self.h, int(prob.tti_op))
         d = (C.c_int * 3)()
         lib().or_dims(self.h, d)
         self.shape = (d[0], d[1], d[2])

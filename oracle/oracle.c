@@ -79,6 +79,8 @@ typedef struct {
     double c2[MAXM + 1]; /* second-derivative weights c2_0..c2_M (acoustic) */
     /* TTI */
     double *m, *eps, *del, *th, *ph, *sig;   /* sig: damping rate [1/s] */
+    int tti_op;          /* TTI operator: 0 = composed centred first derivatives
+                            (Eq. rot), 1 = staggered pair on the diagonal terms */
     /* elastic */
     double *lam, *mu, *bu;                   /* Lame [Pa], buoyancy [m^3/kg] */
     /* forward wavefield store for gradients */
@@ -568,9 +570,14 @@ static void frame(double th, double ph, double *xb, double *yb, double *zb)
 /* H0 p = -(G_xbxb + G_ybyb) p,  Hz r = -G_zbzb r,  G_aa = D_a^T D_a with
  * D_a u = sum_i a_i D_i u (pointwise frame) and D_a^T w = sum_i D_i^T (a_i w).
  * Literal three-axis form with the transposes as scatter loops. */
+static void tti_apply_H_sp(const or_prob *P, const double *p, const double *r, double *H0p, double *Hzr);
 static void tti_apply_H(const or_prob *P, const double *p, const double *r,
                         double *H0p, double *Hzr)
 {
+    if (P->tti_op == 1) {
+        tti_apply_H_sp(P, p, r, H0p, Hzr);
+        return;
+    }
     long N = P->N;
     double *gp[3], *gr[3], *ax[3], *ay[3], *az[3];
     for (int i = 0; i < 3; i++) {
@@ -670,6 +677,73 @@ static void tti_frame_image(const or_prob *P, const double *zp, const double *zr
     }
     for (int i = 0; i < 3; i++) { free(Gz[i]); free(Gr[i]); free(gp[i]); free(gr[i]); }
 }
+
+/* Staggered-pair variant of the same operators.  With P0 = xb xb^T + yb yb^T
+ * and Pz = zb zb^T (pointwise), the centred form above is
+ *   H0 u = -sum_{i,j} D_i^T (P0_ij D_j u),  Hz u = -sum_{i,j} D_i^T (Pz_ij D_j u);
+ * here each diagonal term i = j uses the staggered pair instead,
+ *   -(D+_i)^T (P0_ii~ D+_i u),  P0_ii~ = (P0_ii(q) + P0_ii(q + e_i)) / 2 at the
+ * half point (the neighbour clamped at the last node), which has no
+ * checkerboard null vector; the cross terms i != j keep the centred D.
+ * Both forms are symmetric, so the adjoint machinery is unchanged. */
+static void tti_apply_H_sp(const or_prob *P, const double *p, const double *r, double *H0p, double *Hzr)
+{
+    long N = P->N;
+    double *gp[3], *gr[3], *sp[3], *sr[3], *d0[3], *dz[3], *c0[3], *cz[3];
+    for (int i = 0; i < 3; i++) {
+        gp[i] = dalloc(N); gr[i] = dalloc(N); sp[i] = dalloc(N); sr[i] = dalloc(N);
+        d0[i] = dalloc(N); dz[i] = dalloc(N); c0[i] = dalloc(N); cz[i] = dalloc(N);
+        apply_axis(line_D, p, gp[i], i, P);
+        apply_axis(line_D, r, gr[i], i, P);
+        apply_axis(line_Dp, p, sp[i], i, P);
+        apply_axis(line_Dp, r, sr[i], i, P);
+    }
+    /* diagonal entries of P0, Pz at the nodes; cross fluxes sum_{j != i} P_ij D_j u */
+#pragma omp parallel for
+    for (long q = 0; q < N; q++) {
+        double xb[3], yb[3], zb[3];
+        frame(P->th[q], P->ph[q], xb, yb, zb);
+        for (int i = 0; i < 3; i++) {
+            d0[i][q] = xb[i] * xb[i] + yb[i] * yb[i];
+            dz[i][q] = zb[i] * zb[i];
+            double a = 0.0, b = 0.0;
+            for (int j = 0; j < 3; j++) {
+                if (j == i) continue;
+                a += (xb[i] * xb[j] + yb[i] * yb[j]) * gp[j][q];
+                b += zb[i] * zb[j] * gr[j][q];
+            }
+            c0[i][q] = a;
+            cz[i][q] = b;
+        }
+    }
+    /* diagonal fluxes at the half points: averaged coefficient times D+ u */
+#pragma omp parallel for collapse(2)
+    for (int x = 0; x < P->NX; x++)
+        for (int y = 0; y < P->NY; y++)
+            for (int z = 0; z < P->NZ; z++) {
+                long q = IDX(P, x, y, z);
+                for (int i = 0; i < 3; i++) {
+                    long q1 = IDX(P, clampi(x + (i == 0), 0, P->NX - 1), clampi(y + (i == 1), 0, P->NY - 1),
+                                  clampi(z + (i == 2), 0, P->NZ - 1));
+                    sp[i][q] *= 0.5 * (d0[i][q] + d0[i][q1]);
+                    sr[i][q] *= 0.5 * (dz[i][q] + dz[i][q1]);
+                }
+            }
+    memset(H0p, 0, sizeof(double) * N);
+    memset(Hzr, 0, sizeof(double) * N);
+    for (int i = 0; i < 3; i++) {
+        apply_axisT(line_DT_add, c0[i], H0p, i, P, -1.0);
+        apply_axisT(line_DpT_add, sp[i], H0p, i, P, -1.0);
+        apply_axisT(line_DT_add, cz[i], Hzr, i, P, -1.0);
+        apply_axisT(line_DpT_add, sr[i], Hzr, i, P, -1.0);
+    }
+    for (int i = 0; i < 3; i++) {
+        free(gp[i]); free(gr[i]); free(sp[i]); free(sr[i]);
+        free(d0[i]); free(dz[i]); free(c0[i]); free(cz[i]);
+    }
+}
+
+void or_tti_set_operator(or_prob *P, int op) { P->tti_op = op; }
 
 /* exported for the plane-wave dispersion pin: L u = C [H0 p; Hz r] */
 void or_tti_apply_L(const or_prob *P, const double *p, const double *r, double *Lp, double *Lr)
@@ -912,7 +986,7 @@ int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *w
                           int nrec, const float *rec, const double *d_obs,
                           double *grad_phys, double *misfit, double *abs_phys)
 {
-    if (P->d.kind != 1) return OR_EINVAL;
+    if (P->d.kind != 1 || P->tti_op != 0) return OR_EINVAL;   /* frame derivatives: centred form */
     int nt = P->d.nt;
     double *tr = dalloc((long)nrec * nt);
     int rc = or_tti_forward(P, nsrc, src, wav, nrec, rec, tr, 1);

@@ -122,6 +122,7 @@ class Problem:
     name: str = ""
     extra: dict = field(default_factory=dict)
     vdamp: float = 0.0     # TTI damping reference velocity [m/s]; 0 = from model
+    tti_op: int = 0        # TTI operator: 0 composed centred, 1 staggered pair (diagonal terms)
 
     @property
     def ncomp(self):

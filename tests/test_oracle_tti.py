@@ -366,3 +366,148 @@ def test_gradient_azimuth_vanishes_for_vertical_axis():
     gt, gf = np.abs(g5[3]).max(), np.abs(g5[4]).max()
     assert gt > 0
     assert gf <= 1e-12 * gt, (gf, gt)
+
+
+# ---------------------------------------------------------------------------
+# staggered-pair variant of the rotated operators (diagonal terms D+^T D+)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("theta,phi", [(0.5, 0.3), (1.3, -0.7)])
+def test_plane_wave_dispersion_staggered_pair(theta, phi):
+    """The staggered-pair operator approximates the same pseudo-acoustic
+    dispersion relation with the same order in kh."""
+    f32 = lambda v: float(np.float32(v))
+    eps, delta, theta, phi = f32(0.25), f32(0.1), f32(theta), f32(phi)
+    n, h = 25, 10.0
+    x0 = (12 * h, 12 * h, 12 * h)
+    nvec = np.array([math.sin(theta) * math.cos(phi), math.sin(theta) * math.sin(phi), math.cos(theta)])
+    kdir = np.random.default_rng(4).standard_normal(3)
+    kdir /= np.linalg.norm(kdir)
+    fast, slow = pseudo_acoustic_v2(eps, delta, math.acos(abs(float(kdir @ nvec))))
+    for so in (4, 8):
+        p = homogeneous_tti(n, h, so, 2.0, eps, delta, theta, phi)
+        p.tti_op = 1
+        o = oracle.Problem(p)
+        e = []
+        for kh in (0.2, 0.1):
+            S = symbol(o, kdir * kh / h, x0)
+            ev = np.sort(np.linalg.eigvals(-S).real)[::-1] / (kh / h) ** 2
+            e.append(max(abs(ev[0] - fast), abs(ev[1] - slow)))
+        assert math.log(e[0] / e[1], 2) > so - 0.3, (so, e)
+
+
+def test_staggered_pair_removes_checkerboard_null_mode():
+    """u = (-1)^(x+y+z), eps = delta = 0: the composed centred operator
+    annihilates it in the interior; the staggered pair gives exactly
+    -3 s^2 / h^2 u with s = 2 sum_k b_k (-1)^(k+1) (each diagonal D+^T D+),
+    whatever the tilt and azimuth (the cross terms cancel, P0 + Pz = I)."""
+    n, h, so = 24, 10.0, 8
+    rng = np.random.default_rng(2)
+    p = homogeneous_tti(n, h, so, 2.0, 0.0, 0.0, 0.0, 0.0)
+    p.model["theta"] = rng.uniform(0, np.pi, (n, n, n)).astype(np.float32)
+    p.model["phi"] = rng.uniform(-np.pi, np.pi, (n, n, n)).astype(np.float32)
+    ii = np.indices((n, n, n)).sum(0)
+    u = np.where(ii % 2 == 0, 1.0, -1.0)
+    inner = (slice(so, n - so),) * 3
+    b = oracle.weights_staggered(so)
+    s = 2.0 * sum(b[k - 1] * (-1) ** (k + 1) for k in range(1, so // 2 + 1))
+    for op in (0, 1):
+        p.tti_op = op
+        Lp, _ = oracle.Problem(p).tti_apply_L(u, u)
+        if op == 0:
+            assert np.abs(Lp[inner]).max() <= 1e-9 * (s / h) ** 2
+        else:
+            np.testing.assert_allclose(Lp[inner], -3.0 * s * s / h ** 2 * u[inner], rtol=1e-10)
+
+
+def test_staggered_pair_collapse_to_isotropic():
+    """eps = delta = 0, any tilt/azimuth: the staggered-pair TTI oracle is an
+    isotropic leapfrog with the compact Laplacian sum_i D-_i D+_i (numpy)."""
+    n, h, so, nt = 18, 10.0, 8, 50
+    rng = np.random.default_rng(6)
+    vp = (1.5 + rng.random((n, n, n))).astype(np.float32)
+    zero = np.zeros((n, n, n), np.float32)
+    m = {"vp": vp, "eps": zero, "delta": zero,
+         "theta": rng.uniform(0, np.pi, (n, n, n)).astype(np.float32),
+         "phi": rng.uniform(-np.pi, np.pi, (n, n, n)).astype(np.float32)}
+    dt = synth.cfl_dt(h, 2.5)
+    wav = synth.ricker(20.0, dt, nt)[None]
+    src = np.array([[90.0, 80.0, 70.0]], np.float32)
+    rec = np.array([[30.0, 50.0, 150.0], [160.0, 20.0, 10.0]], np.float32)
+    p = synth.Problem(synth.TTI, n, n, n, 0, h, so, nt, dt, m, src, wav, rec)
+    p.tti_op = 1
+    tr = oracle.Problem(p).forward()
+    b = oracle.weights_staggered(so)
+    M = so // 2
+
+    def sh(u, ax, d):
+        out = np.zeros_like(u)
+        L = u.shape[ax]
+        src_sl, dst_sl = [slice(None)] * 3, [slice(None)] * 3
+        if d >= 0:
+            src_sl[ax], dst_sl[ax] = slice(d, L), slice(0, L - d)
+        else:
+            src_sl[ax], dst_sl[ax] = slice(0, L + d), slice(-d, L)
+        out[tuple(dst_sl)] = u[tuple(src_sl)]
+        return out                           # out[i] = u[i + d], zero outside
+
+    def lap(u):
+        acc = np.zeros_like(u)
+        for ax in range(3):
+            dp = sum(b[k - 1] * (sh(u, ax, k) - sh(u, ax, 1 - k)) for k in range(1, M + 1)) / h
+            acc += sum(b[k - 1] * (sh(dp, ax, k - 1) - sh(dp, ax, -k)) for k in range(1, M + 1)) / h
+        return acc
+
+    m2 = 1.0 / (vp.astype(np.float64) * 1000.0) ** 2
+    u0, u1 = np.zeros((n, n, n)), np.zeros((n, n, n))
+    ref = np.zeros((2, nt))
+    si = tuple(int(v / h) for v in src[0])
+    ri = [tuple(int(v / h) for v in r) for r in rec]
+    for it in range(nt):
+        for j, r in enumerate(ri):
+            ref[j, it] = u1[r]
+        u2 = 2 * u1 - u0 + dt * dt / m2 * lap(u1)
+        u2[si] += dt * dt / m2[si] * wav[0, it]
+        u0, u1 = u1, u2
+    np.testing.assert_allclose(tr, ref, atol=1e-10 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("so", [4, 8])
+def test_staggered_pair_dot_product(so):
+    p = _small_problem(so=so)
+    p.tti_op = 1
+    o = oracle.Problem(p)
+    rng = np.random.default_rng(11)
+    q = rng.standard_normal((2, p.nt)).astype(np.float32)
+    d = rng.standard_normal((p.rec.shape[0], p.nt))
+    a = np.sum(o.forward(wavelet=q) * d)
+    b = np.sum(q.astype(np.float64) * o.adjoint(d))
+    assert abs(a - b) <= 1e-12 * abs(a), (a, b)
+
+
+def test_staggered_pair_taylor_gradient():
+    p = _small_problem(so=4, nt=60)
+    p.tti_op = 1
+    p.vdamp = 2500.0 * math.sqrt(1.4)
+    keys = ("vp", "eps", "delta", "theta", "phi")
+    dobs = oracle.Problem(p).forward()
+    vp0 = synth.smooth_model(p.model, 2.0)["vp"].astype(np.float32)
+    base = dict(p.model)
+
+    def J_of(vp):
+        mm = dict(base)
+        mm["vp"] = vp.astype(np.float32)
+        return 0.5 * np.sum((oracle.Problem(p, model=[mm[k] for k in keys]).forward() - dobs) ** 2)
+
+    m0 = 1.0 / (1000.0 * vp0.astype(np.float64)) ** 2
+    J0 = J_of(vp0)
+    mm = dict(base)
+    mm["vp"] = vp0
+    g, J = oracle.Problem(p, model=[mm[k] for k in keys]).gradient(dobs)
+    assert abs(J - J0) <= 1e-12 * J0
+    d = 0.02 * m0 * synth.perturbation(m0.shape, 2, 23).astype(np.float64)
+    lin = float(np.sum(g * d))
+    e2 = []
+    for hh in (1.0, 0.5, 0.25, 0.125):
+        e2.append(abs(J_of(1.0 / (1000.0 * np.sqrt(m0 + hh * d))) - J0 - hh * lin))
+    slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
+    assert all(abs(s - 2.0) < 0.2 for s in slopes), (slopes, e2)
