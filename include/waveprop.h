@@ -89,6 +89,15 @@ typedef struct {
     int ckpt_interval;   /* steps between checkpoints; 0 = ceil(sqrt(nt))     */
     int check_nan;       /* nonzero: stencil kernels flag NaN/Inf, reported
                             as PROP_EUNSTABLE at the end of the call          */
+    int tti_operator;    /* TTI only: 0 = rotated operators of Sec. III-A with
+                            composed centred first derivatives; 1 = staggered
+                            pair on the diagonal terms: D-_i (P_ii~ D+_i u),
+                            P_ii~ the two-node average of the projector's
+                            diagonal (P0 = I - n n^T for H0, n n^T for Hz) at
+                            the half point, cross terms centred; no
+                            checkerboard null vector.  Must be 0 for the other
+                            kinds; 1 is not available to prop_gradient_aniso
+                            or prop_forward_noalloc (PROP_EINVAL).            */
 } prop_desc;
 
 /* Create a propagator.  model points to the PHYSICAL-grid float32 arrays

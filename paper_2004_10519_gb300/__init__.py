@@ -36,7 +36,7 @@ class PropDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("nbl", C.c_int), ("h", C.c_float), ("space_order", C.c_int), ("nt", C.c_int),
                 ("dt", C.c_float), ("vdamp", C.c_float), ("snap_mode", C.c_int),
-                ("ckpt_interval", C.c_int), ("check_nan", C.c_int)]
+                ("ckpt_interval", C.c_int), ("check_nan", C.c_int), ("tti_operator", C.c_int)]
 
 
 class PropError(RuntimeError):
@@ -147,11 +147,11 @@ class Propagator:
     vp) as numpy arrays or torch tensors (host or device)."""
 
     def __init__(self, kind, shape, nbl, h, space_order, nt, model, dt=0.0, vdamp=0.0,
-                 snap_mode=SNAP_FULL_FP32, ckpt_interval=0, check_nan=0, stream=None):
+                 snap_mode=SNAP_FULL_FP32, ckpt_interval=0, check_nan=0, stream=None, tti_operator=0):
         L = lib()
         nx, ny, nz = shape
         self.desc = PropDesc(kind, nx, ny, nz, nbl, float(h), space_order, nt, float(dt),
-                             float(vdamp), snap_mode, ckpt_interval, check_nan)
+                             float(vdamp), snap_mode, ckpt_interval, check_nan, tti_operator)
         args = [_Arg(m, nx * ny * nz) for m in model]
         arr = (C.c_void_p * len(args))(*[a.ptr for a in args])
         if stream is None:
@@ -179,6 +179,7 @@ class Propagator:
         ml = model if model is not None else [prob.model[k] for k in keys]
         kw.setdefault("dt", prob.dt)
         kw.setdefault("vdamp", getattr(prob, "vdamp", 0.0) or 0.0)
+        kw.setdefault("tti_operator", getattr(prob, "tti_op", 0) or 0)
         return cls(prob.kind, (prob.nx, prob.ny, prob.nz), prob.nbl, prob.h, prob.so, prob.nt, ml, **kw)
 
     def close(self):

@@ -147,6 +147,7 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     const int so = d->space_order;
     if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC) return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI or PROP_ELASTIC");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1 || d->nbl < 0) return wp_fail(P, PROP_EINVAL, "bad grid sizes");
+    if (d->tti_operator != 0) return wp_fail(P, PROP_EINVAL, "prop_forward_noalloc needs tti_operator = 0");
     if (!(d->h > 0.f) || !std::isfinite(d->h)) return wp_fail(P, PROP_EINVAL, "h must be > 0");
     if (so != 4 && so != 8 && so != 12 && so != 16) return wp_fail(P, PROP_EINVAL, "space_order must be 4, 8, 12 or 16");
     if (d->nt < 2) return wp_fail(P, PROP_EINVAL, "nt must be >= 2");

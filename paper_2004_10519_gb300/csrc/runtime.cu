@@ -338,7 +338,8 @@ static std::string tune_key(const prop_s *P)
 static int autotune_xchunk(prop_s *P)
 {
     const char *on = getenv("WAVEPROP_AUTOTUNE");
-    if ((on && !strcmp(on, "0")) || P->d.kind == PROP_ELASTIC2D) return PROP_OK;   // 2D passes have no x chunks
+    // the 2D and staggered-pair passes have no x chunks
+    if ((on && !strcmp(on, "0")) || P->d.kind == PROP_ELASTIC2D || P->d.tti_operator == 1) return PROP_OK;
     const char *path = getenv("WAVEPROP_AUTOTUNE_CACHE");
     const std::string key = tune_key(P);
     {
@@ -409,6 +410,8 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     if (d->kind != PROP_TTI && d->kind != PROP_ELASTIC && d->kind != PROP_ACOUSTIC && d->kind != PROP_ELASTIC2D)
         return wp_fail(P, PROP_EINVAL, "kind must be PROP_TTI, PROP_ELASTIC, PROP_ACOUSTIC or PROP_ELASTIC2D");
     if (d->kind == PROP_ELASTIC2D && d->ny != 1) return wp_fail(P, PROP_EINVAL, "PROP_ELASTIC2D needs ny = 1");
+    if (d->tti_operator != 0 && (d->kind != PROP_TTI || d->tti_operator != 1))
+        return wp_fail(P, PROP_EINVAL, "tti_operator must be 0, or 1 for PROP_TTI");
     if (d->nx < 1 || d->ny < 1 || d->nz < 1) return wp_fail(P, PROP_EINVAL, "grid sizes must be >= 1");
     if (d->nbl < 0) return wp_fail(P, PROP_EINVAL, "nbl must be >= 0");
     if (!(d->h > 0.f) || !std::isfinite(d->h)) return wp_fail(P, PROP_EINVAL, "h must be > 0");
@@ -523,7 +526,7 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
         P->xchunk = stencil_xchunk(g, sms);
     }
     for (int i = 0; i < nfields(P); i++) WP_MALLOC(P, P->st[i], N * sizeof(float), "state");
-    WP_TRY(ensure_tmp(P, d->kind == PROP_TTI ? 8 : 0));
+    WP_TRY(ensure_tmp(P, d->kind == PROP_TTI ? (d->tti_operator == 1 ? 14 : 8) : 0));
     WP_MALLOC(P, P->flag, sizeof(int), "flag");
     WP_CK(P, cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
     WP_TRY(autotune_xchunk(P));
@@ -1246,6 +1249,8 @@ extern "C" int prop_gradient_aniso(prop_t *P, const float *wavelet, const float 
 {
     WP_TRY(check_handle(P));
     if (P->d.kind != PROP_TTI) return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso is for TTI propagators");
+    if (P->d.tti_operator != 0)
+        return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso needs the centred operators (tti_operator = 0)");
     if (!tma_usable(P))
         return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso needs a computational nz that is a multiple of 4");
     P->aniso = true;
@@ -1292,7 +1297,8 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
     for (int i = 0; i < cf; i++)
         if (!P->ast[i]) b += N * 4;
     const bool aniso = P->d.kind == PROP_TTI && P->aniso;
-    const int ntmp = P->d.kind == PROP_TTI ? (aniso ? 14 : 8) : (P->d.kind == PROP_ACOUSTIC ? 0 : 15);
+    const int ntmp = P->d.kind == PROP_TTI ? (aniso || P->d.tti_operator == 1 ? 14 : 8)
+                                           : (P->d.kind == PROP_ACOUSTIC ? 0 : 15);
     for (int i = 0; i < ntmp; i++)
         if (!P->tmp[i]) b += N * 4;
     const int ng = P->d.kind == PROP_TTI ? (aniso ? 6 : 1) : (P->d.kind == PROP_ACOUSTIC ? 1 : 3),

@@ -239,3 +239,70 @@ def test_one_step_sampled_full_size(wp, adjoint):
     # to the largest sampled value
     err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
     assert err <= TOL, err
+
+
+# ---------------------------------------------------------------------------
+# staggered-pair operators (desc.tti_operator = 1)
+# ---------------------------------------------------------------------------
+def sp_problem(so, nt=70, shape=(37, 29, 45)):
+    p = ragged_tti(so, nt=nt, shape=shape)
+    p.tti_op = 1
+    return p
+
+
+@pytest.mark.parametrize("so", [8, 12])
+@pytest.mark.parametrize("shape", SHAPES)
+def test_staggered_pair_forward_adjoint_parity(wp, so, shape):
+    p = sp_problem(so, nt=60, shape=shape)
+    prop = wp.Propagator.from_problem(p)
+    o = oracle.Problem(p)
+    assert rel(prop.forward(p.wavelet, p.src, p.rec), o.forward()) <= TOL
+    rng = np.random.default_rng(4)
+    d = rng.standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    q = rng.standard_normal((2, p.nt)).astype(np.float32)
+    qa = prop.adjoint(d, p.src, p.rec)
+    assert rel(qa, o.adjoint(d)) <= TOL
+    Fq = prop.forward(q, p.src, p.rec).astype(np.float64)
+    a = float(np.sum(Fq * d))
+    b = float(np.sum(q.astype(np.float64) * qa))
+    # with forward and adjoint each within TOL (relative L2) of the exact
+    # transposes, Cauchy-Schwarz bounds the dot-test gap by
+    # TOL (|Fq| |d| + |q| |F^T d|) (random d makes <Fq, d> itself small)
+    bound = TOL * (np.linalg.norm(Fq) * np.linalg.norm(d) + np.linalg.norm(q) * np.linalg.norm(qa))
+    assert abs(a - b) <= bound, (a, b, bound)
+    # the centred operators give different traces on the same model
+    p0 = ragged_tti(so, nt=60, shape=shape)
+    assert rel(wp.Propagator.from_problem(p0).forward(p.wavelet, p.src, p.rec), o.forward()) > 10 * TOL
+
+
+def test_staggered_pair_gradient_parity(wp):
+    p, p0, d_obs = grad_problem(shape=(30, 26, 36))
+    p.tti_op = p0.tti_op = 1
+    d_obs = oracle.Problem(p).forward()
+    g_ref, J_ref = oracle.Problem(p0).gradient(d_obs)
+    d32 = d_obs.astype(np.float32)
+    res = {}
+    for mode in (wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32):
+        prop = wp.Propagator.from_problem(p0, snap_mode=mode, ckpt_interval=9)
+        res[mode] = prop.gradient(p0.wavelet, p0.src, p0.rec, d32)
+        prop.close()
+    g, J = res[wp.SNAP_FULL_FP32]
+    assert abs(J - J_ref) <= 1e-5 * J_ref
+    assert rel(g, g_ref) <= 1e-4
+    np.testing.assert_array_equal(res[wp.SNAP_CKPT_FP32][0], g)
+    prop = wp.Propagator.from_problem(p0)
+    with pytest.raises(wp.PropError) as e:
+        prop.gradient_aniso(p0.wavelet, p0.src, p0.rec, d32)
+    assert e.value.code == wp.PROP_EINVAL
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_staggered_pair_state_steps(wp, adjoint):
+    p = sp_problem(12)
+    prop = wp.Propagator.from_problem(p)
+    st = synth.random_state(4, prop.grid, 21)
+    prop.set_state(st)             # p^n, r^n, p^{n-1}, r^{n-1}
+    prop.step(1, adjoint=adjoint)
+    out = prop.get_state()
+    p2, r2 = oracle.Problem(p).tti_step(st[2], st[0], st[3], st[1], adjoint=adjoint)
+    assert rel(out[0], p2) <= TOL and rel(out[1], r2) <= TOL
