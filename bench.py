@@ -193,7 +193,7 @@ def aggregate(ms, units_per_rank, dist=None, device=None):
     return ms, units_per_rank * world / (ms / 1e3)
 
 
-def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
+def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12, tti_operator=0):
     """TTI so-12 forward and adjoint step rates on the industry-scale grid
     (880 x 880 x 480 computational points) from a seeded random state; the
     model is uniform random within the workload's ranges (content does not
@@ -205,7 +205,7 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
     vmax = 4.5 * np.sqrt(1.6)
     dt = synth.cfl_dt(h, vmax)
     prop = wp.Propagator(wp.PROP_TTI, (nx, ny, nz), nbl, h, so, 10, model, dt=dt,
-                         stream=torch.cuda.current_stream(dev).cuda_stream)
+                         stream=torch.cuda.current_stream(dev).cuda_stream, tti_operator=tti_operator)
     del model
     N = int(np.prod(prop.grid))
     st = [torch.randn(prop.grid, device=dev) for _ in range(4)]
@@ -508,7 +508,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--extra", default="",
-                    help="comma list: tti, acoustic, el2d, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
+                    help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--batch-shots", type=int, default=8)
     ap.add_argument("--batch-nt", type=int, default=150)
@@ -528,6 +528,11 @@ def main():
                 out["tti"] = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
             else:
                 out["tti"] = tti_throughput(wp, torch, dev)
+        if "ttisp" in extras:              # staggered-pair operators
+            if args.small:
+                out["ttisp"] = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200, tti_operator=1)
+            else:
+                out["ttisp"] = tti_throughput(wp, torch, dev, steps=20, tti_operator=1)
         if "acoustic" in extras:
             if args.small:
                 out["acoustic"] = acoustic_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
