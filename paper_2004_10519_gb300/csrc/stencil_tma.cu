@@ -122,6 +122,14 @@ WP_DEV float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p)
 WP_DEV float2 ldg2(const float *__restrict__ p, unsigned o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); }
 WP_DEV void st2(float *p, unsigned o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); }
 WP_DEV float2 dif2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// paired FP32 arithmetic (one instruction for both lanes; per component the
+// result of the scalar operation)
+WP_DEV float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+WP_DEV float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+WP_DEV float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+WP_DEV float2 f2s(float a) { return make_float2(a, a); }
+// a - b as fma(-1, b, a): the same rounding as the subtraction
+WP_DEV float2 f2sub(float2 a, float2 b) { return __ffma2_rn(make_float2(-1.f, -1.f), b, a); }
 
 constexpr int al32(int n) { return (n + 31) & ~31; }   // 128-byte aligned float offsets
 constexpr int IS = FZ * FY;                             // interior box (tile of one plane)
@@ -301,23 +309,24 @@ el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int
             zwin<M>(S + L::OXZ + ty * B::ZC, cz, wxz);
             zwin<M>(syz + cy * B::RC, cz, wyz);
             zwin<M>(S + L::OZZ + ty * B::ZC, cz, wzz);
-            float d0a = 0.f, d0b = 0.f, d1a = 0.f, d1b = 0.f, d2a = 0.f, d2b = 0.f;
+            float2 d0 = Z2, d1 = Z2, d2 = Z2;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
-                const float b = w.b[k - 1];
-                const float2 ax = dif2(qxx[M - 1 + k], qxx[M - k]);
-                const float2 ay = dif2(lds2(sxy + (cy + k - 1) * B::YC + c2), lds2(sxy + (cy - k) * B::YC + c2));
-                d0a += b * (ax.x + ay.x + (wxz[M + k - 1] - wxz[M - k]));
-                d0b += b * (ax.y + ay.y + (wxz[M + k] - wxz[M - k + 1]));
-                const float2 bx_ = dif2(qxy[M + k - 1], qxy[M - k]);
-                const float2 by_ = dif2(lds2(syy + (cy + k) * B::YC + c2), lds2(syy + (cy - k + 1) * B::YC + c2));
-                d1a += b * (bx_.x + by_.x + (wyz[M + k - 1] - wyz[M - k]));
-                d1b += b * (bx_.y + by_.y + (wyz[M + k] - wyz[M - k + 1]));
-                const float2 cx_ = dif2(qxz[M + k - 1], qxz[M - k]);
-                const float2 cy_ = dif2(lds2(syz + (cy + k - 1) * B::RC + cz), lds2(syz + (cy - k) * B::RC + cz));
-                d2a += b * (cx_.x + cy_.x + (wzz[M + k] - wzz[M - k + 1]));
-                d2b += b * (cx_.y + cy_.y + (wzz[M + k + 1] - wzz[M - k + 2]));
+                const float2 b = f2s(w.b[k - 1]);
+                const float2 ax = f2sub(qxx[M - 1 + k], qxx[M - k]);
+                const float2 ay = f2sub(lds2(sxy + (cy + k - 1) * B::YC + c2), lds2(sxy + (cy - k) * B::YC + c2));
+                const float2 az = make_float2(wxz[M + k - 1] - wxz[M - k], wxz[M + k] - wxz[M - k + 1]);
+                d0 = f2fma(b, f2add(f2add(ax, ay), az), d0);
+                const float2 bx_ = f2sub(qxy[M + k - 1], qxy[M - k]);
+                const float2 by_ = f2sub(lds2(syy + (cy + k) * B::YC + c2), lds2(syy + (cy - k + 1) * B::YC + c2));
+                const float2 bz_ = make_float2(wyz[M + k - 1] - wyz[M - k], wyz[M + k] - wyz[M - k + 1]);
+                d1 = f2fma(b, f2add(f2add(bx_, by_), bz_), d1);
+                const float2 cx_ = f2sub(qxz[M + k - 1], qxz[M - k]);
+                const float2 cy_ = f2sub(lds2(syz + (cy + k - 1) * B::RC + cz), lds2(syz + (cy - k) * B::RC + cz));
+                const float2 cz_ = make_float2(wzz[M + k] - wzz[M - k + 1], wzz[M + k + 1] - wzz[M - k + 2]);
+                d2 = f2fma(b, f2add(f2add(cx_, cy_), cz_), d2);
             }
+            const float d0a = d0.x, d0b = d0.y, d1a = d1.x, d1b = d1.y, d2a = d2.x, d2b = d2.y;
             const float2 v0 = lds2(S + L::OV + ii), v1 = lds2(S + L::OV + IS + ii), v2 = lds2(S + L::OV + 2 * IS + ii);
             const float2 bxn = lds2(S + L::OBX + ii);
             const float2 b0 = lds2(sb + ty * B::PC + c2);
@@ -467,30 +476,25 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
             zwin<M>(svx + cy * B::RC, cz, wvx);
             zwin<M>(svy + cy * B::RC, cz, wvy);
             zwin<M>(svz + cy * B::RC, cz, wvz);
-            float exa = 0.f, exb = 0.f, eya = 0.f, eyb = 0.f, eza = 0.f, ezb = 0.f;
-            float gxya = 0.f, gxyb = 0.f, gxza = 0.f, gxzb = 0.f, gyza = 0.f, gyzb = 0.f;
+            float2 ex = Z2, ey = Z2, ez = Z2, gxy = Z2, gxz = Z2, gyz = Z2;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
-                const float b = w.b[k - 1];
-                const float2 dx = dif2(qvx[M + k - 1], qvx[M - k]);
-                exa += b * dx.x;
-                exb += b * dx.y;
-                const float2 dy = dif2(lds2(svy + (cy + k - 1) * B::RC + cz), lds2(svy + (cy - k) * B::RC + cz));
-                eya += b * dy.x;
-                eyb += b * dy.y;
-                eza += b * (wvz[M + k - 1] - wvz[M - k]);
-                ezb += b * (wvz[M + k] - wvz[M - k + 1]);
-                const float2 xy = dif2(lds2(svx + (cy + k) * B::RC + cz), lds2(svx + (cy - k + 1) * B::RC + cz));
-                const float2 yx = dif2(qvy[M - 1 + k], qvy[M - k]);
-                gxya += b * (xy.x + yx.x);
-                gxyb += b * (xy.y + yx.y);
-                const float2 zx = dif2(qvz[M - 1 + k], qvz[M - k]);
-                gxza += b * ((wvx[M + k] - wvx[M - k + 1]) + zx.x);
-                gxzb += b * ((wvx[M + k + 1] - wvx[M - k + 2]) + zx.y);
-                const float2 zy = dif2(lds2(svz + (cy + k) * B::RC + cz), lds2(svz + (cy - k + 1) * B::RC + cz));
-                gyza += b * ((wvy[M + k] - wvy[M - k + 1]) + zy.x);
-                gyzb += b * ((wvy[M + k + 1] - wvy[M - k + 2]) + zy.y);
+                const float2 b = f2s(w.b[k - 1]);
+                ex = f2fma(b, f2sub(qvx[M + k - 1], qvx[M - k]), ex);
+                ey = f2fma(b, f2sub(lds2(svy + (cy + k - 1) * B::RC + cz), lds2(svy + (cy - k) * B::RC + cz)), ey);
+                ez = f2fma(b, make_float2(wvz[M + k - 1] - wvz[M - k], wvz[M + k] - wvz[M - k + 1]), ez);
+                const float2 xy = f2sub(lds2(svx + (cy + k) * B::RC + cz), lds2(svx + (cy - k + 1) * B::RC + cz));
+                const float2 yx = f2sub(qvy[M - 1 + k], qvy[M - k]);
+                gxy = f2fma(b, f2add(xy, yx), gxy);
+                const float2 zx = f2sub(qvz[M - 1 + k], qvz[M - k]);
+                const float2 xz = make_float2(wvx[M + k] - wvx[M - k + 1], wvx[M + k + 1] - wvx[M - k + 2]);
+                gxz = f2fma(b, f2add(xz, zx), gxz);
+                const float2 zy = f2sub(lds2(svz + (cy + k) * B::RC + cz), lds2(svz + (cy - k + 1) * B::RC + cz));
+                const float2 yz = make_float2(wvy[M + k] - wvy[M - k + 1], wvy[M + k + 1] - wvy[M - k + 2]);
+                gyz = f2fma(b, f2add(yz, zy), gyz);
             }
+            const float exa = ex.x, exb = ex.y, eya = ey.x, eyb = ey.y, eza = ez.x, ezb = ez.y;
+            const float gxya = gxy.x, gxyb = gxy.y, gxza = gxz.x, gxzb = gxz.y, gyza = gyz.x, gyzb = gyz.y;
             const float *T = S + L::OT + ii;
             const float2 t0 = lds2(T), t1 = lds2(T + IS), t2 = lds2(T + 2 * IS);
             const float2 t3 = lds2(T + 3 * IS), t4 = lds2(T + 4 * IS), t5 = lds2(T + 5 * IS);
@@ -910,11 +914,6 @@ struct AL {
 struct AMaps {
     CUtensorMap u, q, w, u0, uf, g;
 };
-
-WP_DEV float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
-WP_DEV float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-WP_DEV float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-WP_DEV float2 f2s(float a) { return make_float2(a, a); }
 
 template <int M, int GRAD>
 __global__ void __launch_bounds__(NTP, M <= 6 ? 2 : 1)
