@@ -455,13 +455,14 @@ def gradient_small(wp, torch, dev):
     return out
 
 
-def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
-    """Batched TTI gradients (so 12, BF16 checkpoints): shots on windows of
-    one large model with nx, ny ~ U[200, 600], nz = 300 (+ 40-cell layer);
-    shots/hour of one prop_gradient call after another against one
-    prop_gradient_batch call over the same shots (results compared bitwise)."""
+def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
+    """Batched gradients (TTI so 12 or elastic so 8, BF16 checkpoints): shots
+    on windows of one large model with nx, ny ~ U[200, 600], nz = 300 (+
+    40-cell layer); shots/hour of one prop_gradient call after another
+    against one prop_gradient_batch call over the same shots (results
+    compared bitwise)."""
     kw = dict(size_range=(60, 120), nz=80) if small else {}
-    shots = synth.tti_batch_shots(nshots, nt, **kw)
+    shots = (synth.tti_batch_shots if kind == "tti" else synth.elastic_batch_shots)(nshots, nt, **kw)
     stream = torch.cuda.current_stream(dev).cuda_stream
     to = lambda a: torch.from_numpy(a).to(dev)
     props, wav, src, rec, obs = [], [], [], [], []
@@ -491,7 +492,7 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
                           int(torch.cuda.mem_get_info(dev)[0] * 0.9))[1]
     for p in props:
         p.close()
-    return {"shots": nshots, "nt": nt, "storage": "bf16 checkpoints",
+    return {"kind": kind, "shots": nshots, "nt": nt, "storage": "bf16 checkpoints",
             "windows": [s[1].name for s in shots], "points_total": npts,
             "sequential": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq},
             "batched": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
@@ -510,6 +511,9 @@ def main():
     ap.add_argument("--extra", default="",
                     help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
+    ap.add_argument("--grad-modes", default="0,1,2,3",
+                    help="storage modes of the grad/elgrad extras (0 full FP32, 1 FP32, 2 BF16, 3 FP16 checkpoints)")
+    ap.add_argument("--batch-kind", default="tti", choices=["tti", "elastic"])
     ap.add_argument("--batch-shots", type=int, default=8)
     ap.add_argument("--batch-nt", type=int, default=150)
     args = ap.parse_args()
@@ -544,19 +548,15 @@ def main():
             out["rtm"] = rtm_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt, small=args.small)
         if "grad" in extras:
             out["grad"] = gradient_shots_per_hour(
-                wp, torch, dev, args.grad_nt,
-                [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
-                small=args.small)
+                wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small)
         if "elgrad" in extras:
             out["elgrad"] = elastic_gradient_shots_per_hour(
-                wp, torch, dev, args.grad_nt,
-                [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_CKPT_BF16, wp.SNAP_CKPT_FP16],
-                small=args.small)
+                wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small)
         if "gradsmall" in extras:
             out["gradsmall"] = gradient_small(wp, torch, dev)
         if "batch" in extras:
             out["batch"] = batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
-                                                small=args.small)
+                                                small=args.small, kind=args.batch_kind)
         print(json.dumps(out), flush=True)
         return
 

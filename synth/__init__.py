@@ -500,3 +500,42 @@ def elastic2d_small(shape=(45, 38), nbl=7, h=10.0, so=8, nt=70, seed=4):
     rec[:, 2] = 1.9 * h
     return Problem(ELASTIC2D, nx, 1, nz, nbl, h, so, nt, dt, m3, src, wav, rec,
                    name=f"elastic2d-small-{nx}x{nz}-so{so}")
+
+
+def elastic_batch_shots(nshots=32, nt=1500, seed=20049, size_range=(200, 600), nz=300, h=12.5,
+                        nbl=40, so=8, f0=12.0, global_cells=(1000, 1000, 500)):
+    """Batched elastic gradients: ``nshots`` explosive-source shots on windows
+    with nx, ny ~ U[size_range], nz fixed, at random offsets in the undulating
+    10-layer model (velocity of the TTI batch recipe), vs = vp / 1.73 and
+    Gardner density rho = 0.31 vp^0.25 (vp in m/s); source at the window
+    centre 25 m deep; receivers every 4 cells at depth h.  Each entry is
+    (true problem, starting problem): the starting vp (and vs, rho through
+    the same relations) increases linearly with depth."""
+    rng = np.random.default_rng(seed)
+    gx, gy, gz = global_cells
+    model = UndulatingTTI(seed, extent=(gx * h, gy * h, gz * h))
+    dt = cfl_dt(h, model.vmax)
+
+    def elastic(vp):
+        vp = np.ascontiguousarray(vp, dtype=np.float32)
+        return {"vp": vp, "vs": (vp / np.float32(1.73)).astype(np.float32),
+                "rho": (0.31 * (vp.astype(np.float64) * 1000.0) ** 0.25).astype(np.float32)}
+
+    shots = []
+    for s in range(nshots):
+        nx, ny = (int(v) for v in rng.integers(size_range[0], size_range[1] + 1, 2))
+        ox = int(rng.integers(0, gx - nx + 1))
+        oy = int(rng.integers(0, gy - ny + 1))
+        m = elastic(model.window(ox, oy, nx, ny, nz, h)["vp"])
+        src = np.array([[(nx // 2) * h, (ny // 2) * h, 25.0]], np.float32)
+        rec = carpet_receivers(0.0, 0.0, 4 * h, (nx - 1) // 4 + 1, (ny - 1) // 4 + 1, h)
+        wav = ricker(f0, dt, nt)[None, :]
+        name = f"elastic-window-{nx}x{ny}x{nz}-at-{ox},{oy}-so{so}-nt{nt}"
+        true = Problem(ELASTIC, nx, ny, nz, nbl, h, so, nt, dt, m, src, wav, rec, name=name)
+        z = (np.arange(nz) / max(nz - 1, 1)).astype(np.float32)
+        v0 = model.vmin + (model.vmax - model.vmin) * z
+        start = elastic(np.broadcast_to(v0[None, None, :], (nx, ny, nz)))
+        p0 = Problem(ELASTIC, nx, ny, nz, nbl, h, so, nt, dt, start, src, wav, rec,
+                     name=name.replace("window", "window-start"))
+        shots.append((true, p0))
+    return shots
