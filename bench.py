@@ -473,14 +473,19 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
         obs.append(pt.forward(w, s_, r))
         pt.close()
         props.append(wp.Propagator.from_problem(p0, snap_mode=wp.SNAP_CKPT_BF16, stream=stream))
+        props[-1].trim()                 # idle handles hold only their model
         wav.append(w); src.append(s_); rec.append(r)
         npts += int(np.prod(props[-1].grid))
     torch.cuda.synchronize()
     # warm-up (tensor maps, autotuned tiles, allocator) on the first shot
     props[0].gradient(wav[0], src[0], rec[0], obs[0])
     torch.cuda.synchronize()
+    props[0].trim()
     t0 = time.perf_counter()
-    seq = [p.gradient(wav[i], src[i], rec[i], obs[i]) for i, p in enumerate(props)]
+    seq = []
+    for i, p in enumerate(props):
+        seq.append(p.gradient(wav[i], src[i], rec[i], obs[i]))
+        p.trim()                         # as the batch does after each shot
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     t0 = time.perf_counter()

@@ -193,7 +193,9 @@ int prop_backward(prop_t *p, const float *resid, float *grad, float *src_grad);
  * must not use them from another thread during the call.  misfit [nshots]
  * may be NULL.  Returns PROP_OK, or the error of the first failing shot
  * (its message, prefixed "shot i: ", from prop_last_error(NULL); each
- * handle keeps its own message); the other shots still run. */
+ * handle keeps its own message); the other shots still run.  Each shot's
+ * work arrays are released after its gradient (prop_trim), so later waves
+ * can use that memory; its wavefield state then reads as zero. */
 int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
                         const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
                         const int *nrec, const float *const *d_obs, float *const *grad,
@@ -209,6 +211,14 @@ int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wa
  * a window that does not fit. */
 int prop_stack_image(prop_t *p, const float *image, float *stack, const int *stack_dims,
                      const int *offset, float weight);
+
+/* Release the handle's work arrays (wavefield state, adjoint state,
+ * scratch fields, saved forward run) and keep the model: the next call
+ * allocates what it needs again (the state restarts at zero).  A batch of
+ * many shots can thus hold all its handles at the size of their models;
+ * prop_gradient_batch trims each shot after its gradient.  Synchronises the
+ * handle's stream. */
+int prop_trim(prop_t *p);
 
 /* Device bytes a prop_gradient call with nrec receivers would allocate on
  * top of what the handle holds (0 for p == NULL). */

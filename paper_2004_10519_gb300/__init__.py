@@ -29,7 +29,7 @@ ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
                "prop_last_error", "prop_forward_noalloc", "prop_tile_planes",
                "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves",
-               "prop_gradient_aniso", "prop_stack_image")
+               "prop_gradient_aniso", "prop_stack_image", "prop_trim")
 
 
 class PropDesc(C.Structure):
@@ -80,6 +80,7 @@ def lib():
         L.prop_gradient_bytes.argtypes = [vp, C.c_int]
         L.prop_plan_waves.argtypes = [C.POINTER(C.c_size_t), C.c_int, C.c_size_t, C.POINTER(C.c_int)]
         L.prop_stack_image.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_float]
+        L.prop_trim.argtypes = [vp]
         L.prop_destroy.argtypes = [vp]
         L.prop_last_error.restype = C.c_char_p
         L.prop_last_error.argtypes = [vp]
@@ -265,6 +266,10 @@ class Propagator:
         self._check(lib().prop_gradient_aniso(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, d.ptr,
                                               o.ptr, C.byref(J)))
         return out, J.value
+
+    def trim(self):
+        """Release the work arrays and keep the model (``prop_trim``)."""
+        self._check(lib().prop_trim(self.h))
 
     def stack_image(self, image, stack, offset, weight=1.0):
         """Add ``weight * image`` (this handle's physical grid) into the device

@@ -277,6 +277,17 @@ static int ensure_tmp(prop_s *P, int count)
         if (!P->tmp[i]) WP_MALLOC(P, P->tmp[i], sizeof(float) * P->g.N, "scratch fields");
     return PROP_OK;
 }
+// state and scratch arrays of a call (prop_trim releases them between calls)
+static int ensure_work(prop_s *P)
+{
+    for (int i = 0; i < nfields(P); i++)
+        if (!P->st[i]) {
+            WP_MALLOC(P, P->st[i], sizeof(float) * P->g.N, "state");
+            WP_CK(P, cudaMemsetAsync(P->st[i], 0, sizeof(float) * P->g.N, P->stream));
+        }
+    if (P->d.kind == PROP_TTI) return ensure_tmp(P, P->d.tti_operator == 1 ? 14 : 8);
+    return PROP_OK;
+}
 static int ensure_ast(prop_s *P)
 {
     for (int i = 0; i < nfields(P); i++)
@@ -613,6 +624,7 @@ static int zero_fields(prop_s *P, float *const *f, int n)
 extern "C" int prop_set_state(prop_t *P, const float *const *fields)
 {
     WP_TRY(check_handle(P));
+    WP_TRY(ensure_work(P));
     if (!fields) return wp_fail(P, PROP_EINVAL, "fields is NULL");
     for (int i = 0; i < nfields(P); i++) {
         if (!fields[i]) return wp_fail(P, PROP_EINVAL, "field pointer is NULL");
@@ -624,6 +636,7 @@ extern "C" int prop_set_state(prop_t *P, const float *const *fields)
 extern "C" int prop_get_state(prop_t *P, float *const *fields)
 {
     WP_TRY(check_handle(P));
+    WP_TRY(ensure_work(P));
     if (!fields) return wp_fail(P, PROP_EINVAL, "fields is NULL");
     for (int i = 0; i < nfields(P); i++) {
         if (!fields[i]) return wp_fail(P, PROP_EINVAL, "field pointer is NULL");
@@ -655,6 +668,7 @@ static int step_state(prop_s *P, float **s, bool adjoint)
 extern "C" int prop_step(prop_t *P, int nsteps, int adjoint)
 {
     WP_TRY(check_handle(P));
+    WP_TRY(ensure_work(P));
     // TTI transposed steps differentiate zeta = C lam, which each step then
     // keeps up to date: form it once from the state
     if (adjoint && P->d.kind == PROP_TTI && nsteps > 0) k_tti_zeta(P, P->st[0], P->st[1], P->tmp[6], P->tmp[7]);
@@ -888,6 +902,7 @@ static int forward_impl(prop_s *P, const float *wavelet, const float *src, int n
     if (!wavelet || !traces) return wp_fail(P, PROP_EINVAL, "wavelet or traces is NULL");
     if (save && P->d.kind == PROP_ELASTIC2D)
         return wp_fail(P, PROP_EINVAL, "gradients and saved forward runs are not available for PROP_ELASTIC2D");
+    WP_TRY(ensure_work(P));
     Geometry G;
     WP_TRY(build_geometry(P, G, src, nsrc, rec, nrec));
     const int nt = P->d.nt;
@@ -1165,6 +1180,7 @@ extern "C" int prop_adjoint(prop_t *P, const float *traces_in, const float *rec_
 {
     WP_TRY(check_handle(P));
     if (!traces_in || !src_out) return wp_fail(P, PROP_EINVAL, "traces_in or src_out is NULL");
+    WP_TRY(ensure_work(P));
     Geometry G;
     WP_TRY(build_geometry(P, G, src_xyz, nsrc, rec_xyz, nrec));
     const int nt = P->d.nt;
@@ -1187,6 +1203,7 @@ static int backward_impl(prop_s *P, const float *resid, float *grad, float *src_
 {
     (void)misfit_unused;
     if (!P->saved) return wp_fail(P, PROP_ESTATE, "prop_backward needs a preceding prop_forward_saved");
+    WP_TRY(ensure_work(P));
     const int nt = P->d.nt, nsrc = P->saved_nsrc, nrec = P->saved_nrec;
     Geometry G;
     WP_TRY(sp_build(P, P->saved_src.data(), nsrc, nullptr, &G.S));
@@ -1277,6 +1294,19 @@ extern "C" int prop_stack_image(prop_t *P, const float *image, float *stack, con
     return finish(P);
 }
 
+extern "C" int prop_trim(prop_t *P)
+{
+    WP_TRY(check_handle(P));
+    WP_CK(P, cudaStreamSynchronize(P->stream));
+    free_snaps(P);
+    for (auto &a : P->st) { cudaFree(a); a = nullptr; }
+    for (auto &a : P->ast) { cudaFree(a); a = nullptr; }
+    for (auto &a : P->tmp) { cudaFree(a); a = nullptr; }
+    P->saved = false;
+    P->tmaps.clear();
+    return PROP_OK;
+}
+
 // device bytes one prop_gradient call allocates on top of what the handle
 // already holds (wavefield storage or checkpoints + recompute segment,
 // adjoint state, scratch fields, gradient buffers, traces)
@@ -1294,8 +1324,10 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
     }
     if (P->d.snap_mode != SNAP_FULL_FP32)
         b += ((size_t)K + 1) * snap_fields(P) * N * 4;
-    for (int i = 0; i < cf; i++)
+    for (int i = 0; i < cf; i++) {
         if (!P->ast[i]) b += N * 4;
+        if (!P->st[i]) b += N * 4;
+    }
     const bool aniso = P->d.kind == PROP_TTI && P->aniso;
     const int ntmp = P->d.kind == PROP_TTI ? (aniso || P->d.tti_operator == 1 ? 14 : 8)
                                            : (P->d.kind == PROP_ACOUSTIC ? 0 : 15);
@@ -1414,6 +1446,8 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
                 P->stream = s;
                 rc[i] = prop_gradient(P, wavelet[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i], d_obs[i],
                                       grad[i], &mis[i]);
+                cudaStreamSynchronize(s);
+                if (!rc[i]) rc[i] = prop_trim(P);     // the next waves get this shot's work arrays
                 cudaEventRecord(e1, s);
                 cudaStreamWaitEvent(own, e1, 0);
                 P->stream = own;

@@ -109,3 +109,21 @@ def test_batch_reports_failing_shot(wp, shots):
     assert "shot 1" in str(e.value)
     for pr in props:
         pr.close()
+
+
+@pytest.mark.parametrize("snap", [0, 2])
+def test_trim_releases_work_arrays_only(wp, shots, snap):
+    """prop_trim keeps the model: a trimmed handle gives bitwise the traces
+    and gradient of a fresh one, and its state restarts at zero."""
+    p0, d = shots[1]
+    prop = wp.Propagator.from_problem(p0, snap_mode=snap, ckpt_interval=7)
+    tr = prop.forward(p0.wavelet, p0.src, p0.rec)
+    g, J = prop.gradient(p0.wavelet, p0.src, p0.rec, d)
+    prop.trim()
+    assert all(np.all(f == 0) for f in prop.get_state())
+    prop.trim()
+    np.testing.assert_array_equal(prop.forward(p0.wavelet, p0.src, p0.rec), tr)
+    prop.trim()
+    g2, J2 = prop.gradient(p0.wavelet, p0.src, p0.rec, d)
+    np.testing.assert_array_equal(g2, g)
+    assert J2 == J
