@@ -721,10 +721,17 @@ static int ckpt_K(const prop_s *P)
     return std::max(1, std::min(K, P->d.nt));
 }
 
-// slots of wavefield storage
+// fields per stored forward level: TTI p, r; acoustic u; elastic on the
+// TMA-fed passes only the velocities (the imaging reads the strain of
+// v^{k+1} and the face products (v^{k+1}/g - v^k)/b_avg), else all 9
 static size_t snap_fields(const prop_s *P)
 {
-    return P->d.kind == PROP_TTI ? 2 : (P->d.kind == PROP_ACOUSTIC ? 1 : (P->d.kind == PROP_ELASTIC2D ? 5 : 9));
+    switch (P->d.kind) {
+    case PROP_TTI: return 2;
+    case PROP_ACOUSTIC: return 1;
+    case PROP_ELASTIC2D: return 5;
+    default: return tma_usable(P) ? 3 : 9;
+    }
 }
 
 static int alloc_saves(prop_s *P)
@@ -856,7 +863,7 @@ static int store_full(prop_s *P, float *const *s, int lvl)
     } else {
         if (lvl < 0 || lvl > P->d.nt - 1) return PROP_OK;
         float *d = snap_slot(P, lvl);
-        for (int f = 0; f < 9; f++)
+        for (size_t f = 0; f < snap_fields(P); f++)
             WP_CK(P, cudaMemcpyAsync(d + f * N, s[f], N * 4, cudaMemcpyDeviceToDevice, P->stream));
     }
     return PROP_OK;
@@ -1137,8 +1144,9 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
     // k = nt-1: transposed step of a zero state, then the last residual sample
     WP_TRY(el_launch_step(P, a, true));
     after(nt - 1);
+    const int sf = (int)snap_fields(P);
     auto xs = [&](float *base, const float **out) {
-        for (int f = 0; f < 9; f++) out[f] = base + f * N;
+        for (int f = 0; f < 9; f++) out[f] = f < sf ? base + f * N : nullptr;
     };
     if (P->d.snap_mode == SNAP_FULL_FP32) {
         for (int k = nt - 2; k >= 0; k--) {
@@ -1156,11 +1164,11 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
         float *s[9];
         for (int i = 0; i < 9; i++) s[i] = P->st[i];
         WP_TRY(load_checkpoint(P, j, s));
-        for (int f = 0; f < 9; f++)
+        for (int f = 0; f < sf; f++)
             WP_CK(P, cudaMemcpyAsync(seg_slot(P, 0) + f * N, s[f], N * 4, cudaMemcpyDeviceToDevice, P->stream));
         for (int n = n0; n < E; n++) {
             WP_TRY(fwd_step(P, s, G.S, wav, n));
-            for (int f = 0; f < 9; f++)
+            for (int f = 0; f < sf; f++)
                 WP_CK(P, cudaMemcpyAsync(seg_slot(P, n + 1 - n0) + f * N, s[f], N * 4,
                                          cudaMemcpyDeviceToDevice, P->stream));
         }
