@@ -81,6 +81,7 @@ def lib():
         L.prop_plan_waves.argtypes = [C.POINTER(C.c_size_t), C.c_int, C.c_size_t, C.POINTER(C.c_int)]
         L.prop_stack_image.argtypes = [vp, vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_float]
         L.prop_trim.argtypes = [vp]
+        L.prop_selftest_wait.argtypes = [vp, C.c_float]
         L.prop_destroy.argtypes = [vp]
         L.prop_last_error.restype = C.c_char_p
         L.prop_last_error.argtypes = [vp]
@@ -266,6 +267,12 @@ class Propagator:
         self._check(lib().prop_gradient_aniso(self.h, w.ptr, src_a.ptr, nsrc, rec_a.ptr, nrec, d.ptr,
                                               o.ptr, C.byref(J)))
         return out, J.value
+
+    def selftest_wait(self, seconds=0.2):
+        """Failure-path self-test (``prop_selftest_wait``, not in the public
+        header): a device wait that nothing completes; raises PropError
+        PROP_ETIMEOUT after ``seconds``."""
+        self._check(lib().prop_selftest_wait(self.h, float(seconds)))
 
     def trim(self):
         """Release the work arrays and keep the model (``prop_trim``)."""

@@ -126,6 +126,8 @@ bool tma_usable(const prop_s *P);
 // transposed step with imaging grad -= dt^2 uf (L lam) / m
 int acu_launch_step(prop_s *P, float *const *S, const float *uf, float *grad);
 int acu_launch_tma(prop_s *P, float *const *S, const float *uf, float *grad);
+// bounded-wait self-test: a wait that nothing completes, limit in seconds
+int wait_probe_launch(prop_s *P, double seconds);
 int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
 // TTI imaging of the coupling matrix (TMA passes): with the forward field
 // (up, ur) at level n and the adjoint field (lp, lr) at level n+1,

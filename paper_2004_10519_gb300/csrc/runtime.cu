@@ -705,6 +705,15 @@ extern "C" int prop_kernel_stats(const prop_t *P, int id, double *ms, long long 
     return PROP_OK;
 }
 extern "C" long long prop_last_launches(const prop_t *P) { return P ? P->kern_launches : 0; }
+// failure-path self-test: a device wait that nothing completes gives up after
+// `seconds` and the call returns PROP_ETIMEOUT (the handle then reports
+// PROP_ESTATE, as after any expired wait); the context stays usable
+extern "C" int prop_selftest_wait(prop_t *P, float seconds)
+{
+    WP_TRY(check_handle(P));
+    WP_TRY(wait_probe_launch(P, seconds));
+    return finish(P);
+}
 
 // ---------------------------------------------------------------------------
 // forward modelling with optional saving of forward wavefields

@@ -1384,7 +1384,38 @@ int acu_launch(prop_s *P, float *const *S, const float *uf, float *grad)
     return PROP_OK;
 }
 
+// Self-test of the bounded waits: one warp waits on an mbarrier that nothing
+// completes, with a limit of limit_ns on %globaltimer, then reports bit 2
+// (as a TMA pass whose copies never land) and returns.
+__global__ void wait_probe(uint64_t limit_ns, int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_init();
+    }
+    __syncwarp();
+    bool ok = false;
+    if (threadIdx.x == 0) {
+        const uint64_t t0 = gtimer();
+        while (!(ok = mbar_try(&bar, 0)) && gtimer() - t0 < limit_ns) {
+        }
+        if (!ok) atomicOr(err, 2);
+    }
+    __syncwarp();
+}
+
 }  // namespace
+
+// launch the wait self-test on the handle's stream (limit in seconds, <= 2)
+int wait_probe_launch(prop_s *P, double seconds)
+{
+    const double s = seconds < 0.0 ? 0.0 : (seconds > 2.0 ? 2.0 : seconds);
+    wait_probe<<<1, 32, 0, P->stream>>>((uint64_t)(s * 1e9), P->flag);
+    P->kern_launches += 1;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
 
 // acoustic step through the TMA-fed pass (see acu_launch)
 int acu_launch_tma(prop_s *P, float *const *S, const float *uf, float *grad)
