@@ -25,15 +25,25 @@ struct Tile2 {
     static constexpr int R = TXR + 2 * M, C = TZ + 2 * M;   // rows (x), columns (z) with halo
 };
 
-// stage f[x0 - hx .. x0 + TXR + hx) x [z0 - hz .. z0 + TZ + hz) into s (row pitch C)
-template <int C>
-WP_DEV void stage(float *s, const float *__restrict__ f, const GridDev &g, int x0, int z0, int hx, int hz)
+// stage f[x0 - HX .. x0 + TXR + HX) x [z0 - HZ .. z0 + TZ + HZ) into s (row
+// pitch TZ + 2 HZ); a fixed trip count lets every load of a thread be in
+// flight before its shared stores
+template <int HX, int HZ>
+WP_DEV void stage(float *s, const float *__restrict__ f, const GridDev &g, int x0, int z0)
 {
-    const int rows = TXR + 2 * hx, cols = TZ + 2 * hz;
-    for (int i = threadIdx.y * TZ + threadIdx.x; i < rows * cols; i += TZ * BXR) {
-        const int r = i / cols, c = i % cols;
-        const int x = x0 - hx + r, z = z0 - hz + c;
-        s[r * C + c] = (x >= 0 && x < g.NX && z >= 0 && z < g.NZ) ? __ldg(f + (long long)x * g.NZ + z) : 0.f;
+    constexpr int cols = TZ + 2 * HZ, n = (TXR + 2 * HX) * cols, NTH = TZ * BXR, IT = (n + NTH - 1) / NTH;
+    const int tid = threadIdx.y * TZ + threadIdx.x;
+    float v[IT];
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int i = tid + it * NTH, r = i / cols, c = i % cols;
+        const int x = x0 - HX + r, z = z0 - HZ + c;
+        v[it] = (i < n && x >= 0 && x < g.NX && z >= 0 && z < g.NZ) ? __ldg(f + (long long)x * g.NZ + z) : 0.f;
+    }
+#pragma unroll
+    for (int it = 0; it < IT; it++) {
+        const int i = tid + it * NTH;
+        if (i < n) s[i] = v[it];
     }
 }
 
@@ -46,9 +56,9 @@ el2_vpass(GridDev g, FDW w, float *vx, float *vz, const float *__restrict__ txx,
     using T = Tile2<M>;
     __shared__ float sxx[T::R * TZ], sxz[T::R * T::C], szz[TXR * T::C];
     const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TXR;
-    stage<TZ>(sxx, txx, g, x0, z0, M, 0);
-    stage<T::C>(sxz, txz, g, x0, z0, M, M);
-    stage<T::C>(szz, tzz, g, x0, z0, 0, M);
+    stage<M, 0>(sxx, txx, g, x0, z0);
+    stage<M, M>(sxz, txz, g, x0, z0);
+    stage<0, M>(szz, tzz, g, x0, z0);
     __syncthreads();
     const int tz = threadIdx.x, z = z0 + tz;
     if (z >= g.NZ) return;
@@ -89,8 +99,8 @@ el2_tpass(GridDev g, FDW w, const float *__restrict__ vx, const float *__restric
     using T = Tile2<M>;
     __shared__ float svx[T::R * T::C], svz[T::R * T::C];
     const int z0 = blockIdx.x * TZ, x0 = blockIdx.y * TXR;
-    stage<T::C>(svx, vx, g, x0, z0, M, M);
-    stage<T::C>(svz, vz, g, x0, z0, M, M);
+    stage<M, M>(svx, vx, g, x0, z0);
+    stage<M, M>(svz, vz, g, x0, z0);
     __syncthreads();
     const int tz = threadIdx.x, z = z0 + tz;
     if (z >= g.NZ) return;
