@@ -1,6 +1,7 @@
 /*
- * waveprop: 3D pseudo-acoustic TTI and isotropic elastic wave propagators,
- * their exact adjoints and FWI gradients, on one NVIDIA GB300 (sm_103a).
+ * waveprop: 3D pseudo-acoustic TTI, isotropic elastic (3D and the x-z
+ * plane) and isotropic acoustic wave propagators, their exact adjoints and
+ * FWI gradients, on one NVIDIA GB300 (sm_103a).
  *
  * Method: Louboutin et al., "Scaling through abstractions - high-performance
  * vectorial wave simulations for seismic inversion with Devito" (SC20).
@@ -15,7 +16,8 @@
  *   - adjoints ("propagators along with their adjoints", abstract) and the
  *     adjoint-state gradient (zero-lag cross-correlation of forward and
  *     adjoint wavefields), exactness required: Sec. III-A;
- *   - checkpointing of forward wavefields: Sec. III.
+ *   - checkpointing of forward wavefields: Sec. III;
+ *   - many independent shots (RTM/FWI over experiments): Sec. III-B.
  *
  * Conventions (every entry point):
  *   - Grids are indexed [x][y][z], z fastest, float32.  The PHYSICAL grid has
@@ -23,7 +25,9 @@
  *     every face (computational grid (nx+2nbl)(ny+2nbl)(nz+2nbl)) and fills
  *     the layer by edge replication of the model.
  *   - Coordinates are metres, origin at the first physical point, z = depth;
- *     every source/receiver must lie inside [0,(n-1)h] on each axis.
+ *     every source/receiver must lie inside the computational grid,
+ *     [-nbl h, (n-1+nbl) h] on each axis (PROP_EINVAL otherwise; y = 0 for
+ *     PROP_ELASTIC2D, which has no absorbing cells in y).
  *   - Buffers may be host or device pointers (detected per pointer with
  *     cudaPointerGetAttributes).  The caller owns every buffer passed in or
  *     out; the library owns the handle and all device memory it allocates,
