@@ -668,6 +668,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": prob.name, "grid": list(prop.grid), "space_order": prob.so,
+                           "physical_grid": [prob.nx, prob.ny, prob.nz],
+                           "physical_gpts_per_s": value * (prob.nx * prob.ny * prob.nz) / float(np.prod(prop.grid)),
                            "time_steps_per_bench_step": 2 * nt, "shots_per_gpu": 1,
                            "parallelism": f"replicas{world}",
                            "l2": "working set 2.2 GB >> L2 (no flush needed)"},
