@@ -125,3 +125,11 @@ def tti_spec_from_problem(prob, device, **kw) -> Spec:
                 t(prob.src), t(prob.rec), t(prob.model["eps"]), t(prob.model["delta"]),
                 t(prob.model["theta"]), t(prob.model["phi"]),
                 vdamp=getattr(prob, "vdamp", 0.0) or 0.0, **kw)
+
+
+def acoustic_spec_from_problem(prob, device, **kw) -> Spec:
+    """Spec of an acoustic ``synth.Problem`` (model given to
+    ``AcousticModelling.apply`` as m = 1/vp^2)."""
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(device)
+    return Spec((prob.nx, prob.ny, prob.nz), prob.nbl, prob.h, prob.so, prob.nt, prob.dt,
+                t(prob.src), t(prob.rec), vdamp=getattr(prob, "vdamp", 0.0) or 0.0, **kw)

@@ -88,3 +88,26 @@ def test_autograd_gradient_matches_oracle(env):
     gw = wav.grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gm - g_ref) / np.linalg.norm(g_ref) <= 1e-4
     assert np.linalg.norm(gw - q_ref) / np.linalg.norm(q_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("snap", ["full", "ckpt32"])
+def test_acoustic_autograd_matches_oracle(env, snap):
+    """AcousticModelling: dL/dm and dL/dwavelet for an arbitrary trace
+    cotangent against the oracle's backward; FP32 checkpoints bitwise equal
+    to full storage."""
+    torch, wp, ag = env
+    dev = torch.device("cuda", 0)
+    p = synth.acoustic_small(shape=(30, 26, 36), nbl=6, so=8, nt=70)
+    gtr = np.random.default_rng(3).standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    g_ref, q_ref = oracle.Problem(p).backward(gtr)
+    mode = {"full": wp.SNAP_FULL_FP32, "ckpt32": wp.SNAP_CKPT_FP32}[snap]
+    spec = ag.acoustic_spec_from_problem(p, dev, snap_mode=mode, ckpt_interval=9)
+    m = torch.from_numpy((1.0 / (p.model["vp"].astype(np.float64) * 1000) ** 2).astype(np.float32)).to(dev)
+    m.requires_grad_(True)
+    wav = torch.from_numpy(p.wavelet).to(dev).requires_grad_(True)
+    tr = ag.AcousticModelling.apply(m, wav, spec)
+    tr.backward(torch.from_numpy(gtr).to(dev))
+    gm = m.grad.cpu().numpy().astype(np.float64)
+    gw = wav.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gm - g_ref) / np.linalg.norm(g_ref) <= 1e-4
+    assert np.linalg.norm(gw - q_ref) / np.linalg.norm(q_ref) <= 1e-5
