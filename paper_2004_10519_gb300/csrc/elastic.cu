@@ -180,9 +180,9 @@ el_grad_lm_kernel(GridDev g, FDW w, Fields9 s, Fields9 xf1, float *__restrict__ 
     const float t0 = s.f[3][q], t1 = s.f[4][q], t2 = s.f[5][q];
     glam[q] += c * (t0 + t1 + t2) * (e[0] + e[1] + e[2]);
     gmu[q] += 2.f * c * (t0 * e[0] + t1 * e[1] + t2 * e[2]);
-    e0[q] = c * s.f[6][q] * e[3];
-    e1[q] = c * s.f[7][q] * e[4];
-    e2[q] = c * s.f[8][q] * e[5];
+    e0[q] += c * s.f[6][q] * e[3];
+    e1[q] += c * s.f[7][q] * e[4];
+    e2[q] += c * s.f[8][q] * e[5];
 }
 // face products fp_c = dt vbar^k_c (Dtau tau^k)_c (c = x, y, z), scattered 1/2
 template <int M>
@@ -194,9 +194,9 @@ el_grad_b_kernel(GridDev g, FDW w, Fields9 s, Fields9 xf0, float *__restrict__ f
     float d[3];
     div_tau<M>(g, w, xf0.f[3], xf0.f[4], xf0.f[5], xf0.f[6], xf0.f[7], xf0.f[8], x, y, z, d);
     const float c = g.dt * g.ih;
-    f0[q] = c * s.f[0][q] * d[0];
-    f1[q] = c * s.f[1][q] * d[1];
-    f2[q] = c * s.f[2][q] * d[2];
+    f0[q] += c * s.f[0][q] * d[0];
+    f1[q] += c * s.f[1][q] * d[1];
+    f2[q] += c * s.f[2][q] * d[2];
 }
 
 // Face products of the b-gradient without a stencil.  The forward velocity
@@ -213,7 +213,12 @@ el_face2_kernel(GridDev g, Fields9 s, Fields9 xf0, Fields9 xf1, const float *__r
     if (y >= g.NY || z >= g.NZ) return;
     const long long pl = (long long)g.NY * g.NZ, q = ((long long)x * g.NY + y) * g.NZ + z;
     auto ld = [](const float *p, long long o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); };
-    auto st = [](float *p, long long o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); };
+    // accumulate into the face-product sums (read before written, own points only)
+    auto st = [](float *p, long long o, float a, float b) {
+        float2 *d = reinterpret_cast<float2 *>(p + o);
+        const float2 v = *d;
+        *d = make_float2(v.x + a, v.y + b);
+    };
     const float2 b0 = ld(bu, q);
     const float2 bX = x + 1 < g.NX ? ld(bu, q + pl) : b0, bY = y + 1 < g.NY ? ld(bu, q + g.NZ) : b0;
     const float bz2 = z + 2 < g.NZ ? __ldg(bu + q + 2) : b0.y;
@@ -541,10 +546,8 @@ int launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const fl
     el_adj_v_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, sg, P->bu);
     el_grad_b_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, f0, pr[3], pr[4], pr[5]);
     el_adj_t_kernel<M><<<grd, blk, 0, P->stream>>>(g, P->w, s, sg);
-    el_grad_gather_kernel<<<grd, blk, 0, P->stream>>>(g, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5],
-                                                      gr[1], gr[2]);
     prof_end(P, 4);
-    P->kern_launches += 6;
+    P->kern_launches += 5;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
 }
@@ -570,15 +573,27 @@ int launch_adj_grad_tma(prop_s *P, float *const *S, const float *const *xk, cons
     WP_TRY(el_adj_grad_tma(P, S, P->tmp, P->tmp + 6, xk1, gr, pr));
     el_face2_kernel<<<dim3((g.NZ + 63) / 64, (g.NY + 7) / 8, g.NX), dim3(32, 8, 1), 0, P->stream>>>(
         g, s, f0, f1, P->bu, pr[3], pr[4], pr[5]);
-    el_grad_gather_kernel<<<grd, blk, 0, P->stream>>>(g, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5],
-                                                      gr[1], gr[2]);
     prof_end(P, 4);
-    P->kern_launches += 3;
+    P->kern_launches += 2;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
 }
 
 }  // namespace
+
+// the edge and face products are summed over the steps of a sweep in
+// tmp[9..14] (the averaging transposes are linear and the same every step)
+// and gathered onto the nodes once at the end
+int el_grad_gather(prop_s *P, float *const *g)
+{
+    const GridDev &gd = P->g;
+    dim3 blk(TZ, TY, 1), grd((gd.NZ + TZ - 1) / TZ, (gd.NY + TY - 1) / TY, gd.NX);
+    float *const *pr = P->tmp + 9;
+    el_grad_gather_kernel<<<grd, blk, 0, P->stream>>>(gd, pr[0], pr[1], pr[2], pr[3], pr[4], pr[5], g[1], g[2]);
+    P->kern_launches += 1;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
 
 int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1,
                        float *const *g)

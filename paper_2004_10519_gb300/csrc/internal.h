@@ -192,6 +192,9 @@ void k_snap_decode(prop_s *P, const uint16_t *in, long long n, const float *scal
                    int bf16, float *out);
 // elastic transposed step fused with the gradient of forward step k:
 // xk = X^k, xk1 = X^{k+1} (9 fields each), g = (g_lambda, g_mu, g_b) accumulated
+// gather the edge and face products summed in tmp[9..14] over a sweep onto
+// the nodes: g[1] (mu) and g[2] (b)
+int el_grad_gather(prop_s *P, float *const *g);
 int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1,
                        float *const *g);
 

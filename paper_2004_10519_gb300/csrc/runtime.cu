@@ -1151,6 +1151,7 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
         return PROP_OK;
     }
     // k = nt-1: transposed step of a zero state, then the last residual sample
+    WP_TRY(zero_fields(P, P->tmp + 9, 6));      // edge and face product sums
     WP_TRY(el_launch_step(P, a, true));
     after(nt - 1);
     const int sf = (int)snap_fields(P);
@@ -1165,7 +1166,7 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
             WP_TRY(el_launch_adj_grad(P, a, x0, x1, g3));
             after(k);
         }
-        return PROP_OK;
+        return el_grad_gather(P, g3);
     }
     const int K = ckpt_K(P), J = (nt - 1 + K - 1) / K;
     for (int j = J - 1; j >= 0; j--) {
@@ -1189,7 +1190,7 @@ static int el_sweep(prop_s *P, const Geometry &G, const float *res, const float 
             after(k);
         }
     }
-    return PROP_OK;
+    return el_grad_gather(P, g3);
 }
 
 extern "C" int prop_adjoint(prop_t *P, const float *traces_in, const float *rec_xyz, int nrec,

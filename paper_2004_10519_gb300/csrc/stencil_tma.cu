@@ -536,9 +536,13 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
                     gl.y + c * (t0.y + t1.y + t2.y) * (exb + eyb + ezb));
                 st2(o.f[1], q, gm.x + 2.f * c * (t0.x * exa + t1.x * eya + t2.x * eza),
                     gm.y + 2.f * c * (t0.y * exb + t1.y * eyb + t2.y * ezb));
-                st2(o.f[2], q, c * t3.x * gxya, c * t3.y * gxyb);
-                st2(o.f[3], q, c * t4.x * gxza, c * t4.y * gxzb);
-                st2(o.f[4], q, c * t5.x * gyza, c * t5.y * gyzb);
+                // edge products summed over the steps (gathered onto the nodes at the end)
+                const float2 p3 = *reinterpret_cast<const float2 *>(o.f[2] + q);
+                const float2 p4 = *reinterpret_cast<const float2 *>(o.f[3] + q);
+                const float2 p5 = *reinterpret_cast<const float2 *>(o.f[4] + q);
+                st2(o.f[2], q, p3.x + c * t3.x * gxya, p3.y + c * t3.y * gxyb);
+                st2(o.f[3], q, p4.x + c * t4.x * gxza, p4.y + c * t4.y * gxzb);
+                st2(o.f[4], q, p5.x + c * t5.x * gyza, p5.y + c * t5.y * gyzb);
             }
         }
 #pragma unroll
