@@ -240,7 +240,11 @@ int prop_plan_waves(const size_t *bytes, int n, size_t budget, int *wave_of);
  *   ELASTIC2D: fields[0..4] = vx vz txx tzz txz (prop_step: forward only)
  *   ELASTIC: fields[0..8] = vx vy vz txx tyy tzz txy txz tyz
  * prop_step advances nsteps steps without sources or receivers (adjoint != 0:
- * transposed step, state holds the adjoint fields in the same order). */
+ * transposed step, state holds the adjoint fields in the same order).  From
+ * nsteps >= 4 on, pairs of steps replay a CUDA graph captured once per handle,
+ * direction and state buffers (results bitwise those of direct launches);
+ * environment WAVEPROP_GRAPHS=0 launches every step directly, =1 makes a
+ * failed capture an error (PROP_EINVAL) instead of a silent direct run. */
 int prop_grid_dims(const prop_t *p, int *dims /* [3] = NX, NY, NZ */, int *nfields);
 int prop_set_state(prop_t *p, const float *const *fields);
 int prop_get_state(prop_t *p, float *const *fields);

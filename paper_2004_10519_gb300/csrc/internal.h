@@ -96,6 +96,13 @@ struct prop_s {
     // TMA descriptors of the stencil passes, keyed by (array, box width, box
     // height) (stencil_tma.cu)
     std::map<std::tuple<const void *, int, int>, CUtensorMap> tmaps;
+    // prop_step: two steps captured as a CUDA graph, replayed; valid for the
+    // state buffers, direction and tile size it was captured with
+    cudaGraphExec_t step_graph = nullptr;
+    cudaStream_t graph_stream = nullptr;
+    int graph_adj = -1, graph_xc = 0;
+    long long graph_launches = 0;   // kernels in one replay
+    float *graph_st[9] = {};
 };
 
 // ---------------------------------------------------------------------------

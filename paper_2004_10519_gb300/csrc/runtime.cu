@@ -316,6 +316,8 @@ static void free_all(prop_s *P)
     cudaFree(P->tab);
     free_snaps(P);
     for (auto e : P->prof_ev) cudaEventDestroy(e);
+    if (P->step_graph) cudaGraphExecDestroy(P->step_graph);
+    if (P->graph_stream) cudaStreamDestroy(P->graph_stream);
 }
 
 static int step_state(prop_s *P, float **s, bool adjoint);
@@ -665,6 +667,57 @@ static int step_state(prop_s *P, float **s, bool adjoint)
     return PROP_OK;
 }
 
+// capture two source-free steps of the current state buffers into a graph
+// (on a private stream; the launches of step_state are recorded, not run),
+// or reuse the one captured for the same buffers, direction and tiles
+static bool step_graph_ready(prop_s *P, bool adjoint)
+{
+    const int nf = nfields(P);
+    bool same = P->step_graph && P->graph_adj == (int)adjoint && P->graph_xc == P->xchunk;
+    for (int i = 0; same && i < nf; i++) same = P->graph_st[i] == P->st[i];
+    if (same) return true;
+    if (P->step_graph) {
+        cudaGraphExecDestroy(P->step_graph);
+        P->step_graph = nullptr;
+    }
+    if (!P->graph_stream && cudaStreamCreateWithFlags(&P->graph_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        P->graph_stream = nullptr;
+        return false;
+    }
+    if (adjoint && P->d.kind == PROP_ELASTIC && ensure_tmp(P, 9) != PROP_OK) return false;   // no allocation while capturing
+    cudaStream_t own = P->stream;
+    const bool was_broken = P->broken;
+    const std::string was_err = P->err;
+    float *s[9];
+    for (int i = 0; i < 9; i++) s[i] = P->st[i];
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(P->graph_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        P->stream = P->graph_stream;
+        const long long launches = P->kern_launches;
+        ok = step_state(P, s, adjoint) == PROP_OK && step_state(P, s, adjoint) == PROP_OK;
+        P->graph_launches = P->kern_launches - launches;
+        P->kern_launches = launches;
+        P->stream = own;
+        ok = (cudaStreamEndCapture(P->graph_stream, &graph) == cudaSuccess) && ok;
+    }
+    for (int i = 0; ok && i < nf; i++) ok = s[i] == P->st[i];    // a pair restores the buffers
+    if (ok) ok = cudaGraphInstantiate(&P->step_graph, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {                           // stay on direct launches; the handle is unaffected
+        cudaGetLastError();
+        P->step_graph = nullptr;
+        P->broken = was_broken;
+        P->err = was_err;
+        return false;
+    }
+    P->graph_adj = (int)adjoint;
+    P->graph_xc = P->xchunk;
+    for (int i = 0; i < 9; i++) P->graph_st[i] = P->st[i];
+    return true;
+}
+
 extern "C" int prop_step(prop_t *P, int nsteps, int adjoint)
 {
     WP_TRY(check_handle(P));
@@ -673,7 +726,22 @@ extern "C" int prop_step(prop_t *P, int nsteps, int adjoint)
     // keeps up to date: form it once from the state
     if (adjoint && P->d.kind == PROP_TTI && nsteps > 0) k_tti_zeta(P, P->st[0], P->st[1], P->tmp[6], P->tmp[7]);
     if (nsteps < 0) return wp_fail(P, PROP_EINVAL, "nsteps < 0");
-    for (int i = 0; i < nsteps; i++) WP_TRY(step_state(P, P->st, adjoint != 0));
+    int done = 0;
+    if (nsteps >= 4 && !P->prof) {
+        // pairs of steps replayed from a CUDA graph (a pair returns the
+        // rotating state buffers of TTI and acoustic to their places)
+        const char *env = getenv("WAVEPROP_GRAPHS");
+        const bool off = env && !strcmp(env, "0"), required = env && !strcmp(env, "1");
+        if (!off && !step_graph_ready(P, adjoint != 0) && required)
+            return wp_fail(P, PROP_EINVAL, "prop_step: step graph could not be captured");
+        if (!off && P->step_graph) {
+            for (; done + 2 <= nsteps; done += 2) {
+                WP_CK(P, cudaGraphLaunch(P->step_graph, P->stream));
+                P->kern_launches += P->graph_launches;
+            }
+        }
+    }
+    for (int i = done; i < nsteps; i++) WP_TRY(step_state(P, P->st, adjoint != 0));
     return finish(P);
 }
 
@@ -1322,6 +1390,10 @@ extern "C" int prop_trim(prop_t *P)
     for (auto &a : P->tmp) { cudaFree(a); a = nullptr; }
     P->saved = false;
     P->tmaps.clear();
+    if (P->step_graph) {
+        cudaGraphExecDestroy(P->step_graph);
+        P->step_graph = nullptr;
+    }
     return PROP_OK;
 }
 
