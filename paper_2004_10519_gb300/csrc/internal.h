@@ -119,6 +119,8 @@ int tti_launch_fast(prop_s *P, float *const *S, bool adjoint, const float *img_p
 // the same step with the staggered-pair operators (desc.tti_operator = 1)
 int tti_sp_launch(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
                   float *grad);
+int tti_sp_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
+                      float *grad);
 // elastic step in place on S (9 fields); adjoint: transposed step (tbar form)
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 // pipelined elastic step with time step dt_sign * dt (any NZ): forward (+1)

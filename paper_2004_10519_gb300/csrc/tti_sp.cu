@@ -302,11 +302,17 @@ int launch(prop_s *P, float *const *S, bool adjoint, const float *up, const floa
 }  // namespace
 
 // one TTI step with the staggered-pair operators (same contract as
-// tti_launch_step; uses tmp[0..5], tmp[8..13] and zeta in tmp[6], tmp[7])
+// tti_launch_step; uses tmp[0..5], tmp[8..13] and zeta in tmp[6], tmp[7]):
+// the TMA-fed passes of tti_sp_tma.cu where NZ allows, else these
 int tti_sp_launch(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r, float *grad)
 {
     prof_begin(P, adjoint ? 1 : 0);
     int rc;
+    if (tma_usable(P)) {
+        rc = tti_sp_launch_tma(P, S, adjoint, img_p, img_r, grad);
+        prof_end(P, adjoint ? 1 : 0);
+        return rc;
+    }
     switch (P->M) {
     case 2: rc = launch<2>(P, S, adjoint, img_p, img_r, grad); break;
     case 4: rc = launch<4>(P, S, adjoint, img_p, img_r, grad); break;

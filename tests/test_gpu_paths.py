@@ -34,11 +34,13 @@ def el_problem(shape=(34, 30, 44), nbl=6, so=8, nt=60, h=10.0):
                          synth.ricker(20.0, dt, nt)[None], rec)
 
 
-@pytest.mark.parametrize("kind", ["tti", "elastic", "acoustic"])
+@pytest.mark.parametrize("kind", ["tti", "tti_sp", "elastic", "acoustic"])
 def test_tma_and_pipelined_paths_agree(kind, monkeypatch):
     import paper_2004_10519_gb300 as wp
     wp.lib()
-    p = {"tti": tti_problem, "elastic": el_problem, "acoustic": ac_problem}[kind]()
+    p = {"tti": tti_problem, "tti_sp": tti_problem, "elastic": el_problem, "acoustic": ac_problem}[kind]()
+    if kind == "tti_sp":
+        p.tti_op = 1                      # staggered-pair operators
     assert (p.nz + 2 * p.nbl) % 4 == 0
     d = np.random.default_rng(3).standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
     out = {}
@@ -51,9 +53,13 @@ def test_tma_and_pipelined_paths_agree(kind, monkeypatch):
         out[tag] = (prop.forward(p.wavelet, p.src, p.rec).astype(np.float64),
                     prop.adjoint(d, p.src, p.rec).astype(np.float64))
         prop.close()
+    # each path is within 2e-6 of the FP64 oracle; the staggered-pair
+    # adjoint of random traces reaches that on both paths (rounding order of
+    # the twelve fluxes), so their difference may reach twice it
+    tol = 5e-6 if kind == "tti_sp" else 2e-6
     for i in range(2):
         a, b = out["tma"][i], out["pipelined"][i]
-        assert np.linalg.norm(a - b) <= 2e-6 * np.linalg.norm(b), (kind, i)
+        assert np.linalg.norm(a - b) <= tol * np.linalg.norm(b), (kind, i)
 
 
 @pytest.mark.parametrize("kind", ["tti", "elastic", "acoustic"])
