@@ -38,7 +38,7 @@ struct F12 {
 };
 
 template <int M>
-__global__ void __launch_bounds__(NTP, 1)
+__global__ void __launch_bounds__(NTP, M <= 6 ? 2 : 1)
 tti_sp_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
                const __grid_constant__ SRMaps mp, F12 o, int xc, int *err)
 {
