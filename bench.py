@@ -50,7 +50,7 @@ TRAFFIC_B_PER_PT = {"elastic": 113.9}
 # algorithmic FP32 operations per point update, counted from the kernels'
 # arithmetic (FMA = 2): elastic so 8 (velocity + stress pass), TTI so 12
 # (rotation + update pass), acoustic so 12 (7 per stencil radius + 15)
-FLOP_PER_PT = {"elastic": 263.0, "tti": 250.0, "acoustic": 57.0}
+FLOP_PER_PT = {"elastic": 263.0, "tti": 250.0, "tti_sp": 510.0, "acoustic": 57.0}
 
 
 def peaks():
@@ -228,7 +228,8 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
         out[key] = {"gpts_per_s": N / (ms / 1e3) / 1e9, "ms_per_step": ms,
                     "kernel_ms_per_step": kms / max(kn, 1),
                     "alg_gbs": ALG_BYTES["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e9,
-                    "alg_tflops": FLOP_PER_PT["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e12}
+                    "alg_tflops": FLOP_PER_PT["tti_sp" if tti_operator else "tti"] * N / (kms / max(kn, 1) / 1e3)
+                    / 1e12}
     prop.close()
     out["grid"] = list(prop.grid)
     out["space_order"] = so
