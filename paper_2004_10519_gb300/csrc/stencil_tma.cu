@@ -396,6 +396,7 @@ struct RL {
     using B = BX<M>;
     static constexpr int OP = 0, OR = B::RS, OQ = 2 * B::RS, ON = OQ + 2 * IS, SZ = ON + 2 * IS;
     static constexpr uint32_t BYTES = 4u * (2 * B::RR * B::RC + 4 * IS);
+    static constexpr int NS = 4;         // ring stages (two CTAs per SM still fit)
 };
 
 struct RMaps {
@@ -413,7 +414,7 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::NS * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, lane = (ty * TZ2 + tz) & 31;
     const bool lead = ty == 0 && tz == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
@@ -430,7 +431,7 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
         tma3(S + L::ON, &mp.nx, z0, y0, x, bar);
         tma3(S + L::ON + IS, &mp.ny, z0, y0, x, bar);
     };
-    Ring R(bars);
+    RingN<L::NS> R(bars);
     if (lead) R.init();
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
@@ -1002,7 +1003,7 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
         ok = ok && map_of(P, up, FZ, FY, &um.up) && map_of(P, ur, FZ, FY, &um.ur) &&
              map_of(P, grad, FZ, FY, &um.g);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-    const size_t s1 = NSTAGE * RL<M>::SZ * sizeof(float) + 64,
+    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64,
                  s2 = NSTAGE * UL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(tti_rot_tma<M>, s1) && set_smem(tti_upd_tma<M, ADJ, GRAD>, s2);
     (void)attr;
@@ -1095,7 +1096,7 @@ int tti_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp
               map_of(P, lp, FZ, FY, &um.pc) && map_of(P, lr, FZ, FY, &um.rc) &&
               map_of(P, P->del, FZ, FY, &um.d) && map_of(P, ge, FZ, FY, &um.up) && map_of(P, gd, FZ, FY, &um.ur);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-    const size_t s1 = NSTAGE * RL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * UL<M, 2, 0>::SZ * sizeof(float) + 64;
+    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * UL<M, 2, 0>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(tti_rot_tma<M>, s1) && set_smem(tti_upd_tma<M, 2, 0>, s2);
     (void)attr;
     tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[0], t[1], t[2], t[3], t[4], t[5], xc,

@@ -79,9 +79,10 @@ WP_DEV void mbar_arrive(uint64_t *bar)
 }
 // producer after an abort: wait (bounded) for the stages of iterations
 // [a, b] that may still be in flight, so no copy lands after the CTA exits
+template <int NS = NSTAGE>
 WP_DEV void drain(uint64_t *full, int a, int b)
 {
-    for (int j = a < 0 ? 0 : a; j <= b; j++) mbar_wait(&full[j % NSTAGE], (uint32_t)((j / NSTAGE) & 1));
+    for (int j = a < 0 ? 0 : a; j <= b; j++) mbar_wait(&full[j % NS], (uint32_t)((j / NS) & 1));
 }
 
 // 8-byte accesses (z even, NZ even: always aligned)
@@ -128,41 +129,42 @@ WP_DEV void zwin(const float *row, int cz, float (&w)[2 * M + 2])
 // Producer/consumer plane ring.  full[s] completes when the copies of a
 // stage have landed (one arrive with the byte count + the TMA bytes);
 // empty[s] when every consumer warp has finished reading it (one arrive per
-// warp).  A dedicated producer warp (its lane 0) keeps NSTAGE planes in
+// warp).  A dedicated producer warp (its lane 0) keeps NS planes in
 // flight: it refills a stage as soon as it is released, so consumers never
 // wait for each other.  All waits are bounded; a warp that gives up reports
 // bit 2 and leaves, and the producer drains its copies in flight first.
 constexpr int NWARP = NT2 / 32;
 
-struct Ring {
+template <int NS = NSTAGE>
+struct RingN {
     uint64_t *full, *empty;
     int st = 0;
     uint32_t ph = 0;
-    WP_DEV explicit Ring(uint64_t *bars) : full(bars), empty(bars + NSTAGE) {}
+    WP_DEV explicit RingN(uint64_t *bars) : full(bars), empty(bars + NS) {}
     WP_DEV void init()
     {
-        for (int i = 0; i < NSTAGE; i++) {
+        for (int i = 0; i < NS; i++) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], NWARP);
         }
         fence_init();
     }
-    // producer (lane 0 of the producer warp): plane xa + it into stage it % NSTAGE
+    // producer (lane 0 of the producer warp): plane xa + it into stage it % NS
     template <class F>
     WP_DEV void produce(int xa, int nit, F issue, int *err)
     {
         for (int it = 0; it < nit; it++) {
-            const int s = it % NSTAGE;
-            if (it >= NSTAGE && !mbar_wait(&empty[s], (uint32_t)(((it / NSTAGE) - 1) & 1))) {
+            const int s = it % NS;
+            if (it >= NS && !mbar_wait(&empty[s], (uint32_t)(((it / NS) - 1) & 1))) {
                 atomicOr(err, 2);
-                drain(full, it - NSTAGE, it - 1);
+                drain<NS>(full, it - NS, it - 1);
                 return;
             }
             issue(xa + it, s);
         }
         // stay until the last copies have landed (bounded), so none can
         // arrive after the CTA has exited even if the consumers gave up
-        drain(full, nit - NSTAGE, nit - 1);
+        drain<NS>(full, nit - NS, nit - 1);
     }
     WP_DEV bool wait_full() { return mbar_wait(&full[st], ph); }
     // end of iteration: this warp is done with the stage
@@ -170,12 +172,13 @@ struct Ring {
     {
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
-        if (++st == NSTAGE) {
+        if (++st == NS) {
             st = 0;
             ph ^= 1u;
         }
     }
 };
+using Ring = RingN<>;
 
 
 // ---------------------------------------------------------------------------
