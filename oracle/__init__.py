@@ -85,6 +85,8 @@ def lib():
             L.or_el_step_state_d.argtypes = [P, dp, C.c_int, C.c_int]
             L.or_tti_step_points.argtypes = [C.POINTER(_Desc), C.POINTER(fp), fp, fp, fp, fp,
                                              C.c_int, lp, dp, C.c_int]
+            L.or_tti_step_points_op.argtypes = [C.POINTER(_Desc), C.POINTER(fp), fp, fp, fp, fp,
+                                                C.c_int, lp, dp, C.c_int, C.c_int]
             L.or_el_step_points.argtypes = [C.POINTER(_Desc), C.POINTER(fp), C.POINTER(fp),
                                             C.c_int, lp, dp]
             L.or_weights_centred.argtypes = [C.c_int, dp]
@@ -341,15 +343,17 @@ class Problem:
 
 def tti_step_points(prob, state, idx, adjoint=False):
     """One TTI step evaluated only at linear indices ``idx`` (computational
-    grid).  state = (p0, p1, r0, r1) float32 computational-grid arrays."""
+    grid), with the problem's operator form (``prob.tti_op``: 0 centred, 1
+    staggered pair).  state = (p0, p1, r0, r1) float32 computational-grid
+    arrays."""
     d = desc_of(prob)
     ml = prob.model_list()
     arr = (C.POINTER(C.c_float) * 5)(*[_fp(a) for a in ml])
     st = [_f(s).reshape(-1) for s in state]
     idx = np.ascontiguousarray(idx, dtype=np.int64)
     out = np.zeros((idx.size, 2))
-    rc = lib().or_tti_step_points(C.byref(d), arr, *[_fp(s) for s in st], idx.size, _lp(idx),
-                                  _dp(out), int(adjoint))
+    rc = lib().or_tti_step_points_op(C.byref(d), arr, *[_fp(s) for s in st], idx.size, _lp(idx),
+                                     _dp(out), int(adjoint), int(getattr(prob, "tti_op", 0)))
     if rc:
         raise ValueError(rc)
     return out

@@ -1280,7 +1280,7 @@ int or_ac_step_points(const or_desc *d, const float *vp, const float *u0, const 
 /* float32 arrays with clamped indices (= edge-replication extension).  */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    const or_desc *d; int NX, NY, NZ, M; double c[MAXM + 1];
+    const or_desc *d; int NX, NY, NZ, M; double c[MAXM + 1], b[MAXM + 1];
     const float *vp, *eps, *del, *th, *ph; double vmax;
 } pt_ctx;
 
@@ -1360,21 +1360,99 @@ static double pt_G(const pt_ctx *C, const float *u, int a, int x, int y, int z,
     return acc / C->d->h;
 }
 
+/* Staggered-pair operators (the form of tti_apply_H_sp) at one point.  A
+ * field accessor gives the differentiated field at a node, zero outside the
+ * grid: mode 0 the array u itself; in the transposed step the pointwise
+ * combinations zeta = C lam with C from eps, delta at that node (mode 1:
+ * (1+2eps) u + sqrt(1+2delta) u2, mode 2: sqrt(1+2delta) u + u2). */
+typedef struct { const pt_ctx *C; const float *u, *u2; int mode; } pt_fld;
+
+static double fld_at(const pt_fld *F, int x, int y, int z)
+{
+    const pt_ctx *C = F->C;
+    if (!pt_in(C, x, y, z)) return 0.0;
+    double a = pt_f(C, F->u, x, y, z);
+    if (F->mode == 0) return a;
+    double ca = 1.0 + 2.0 * pt_model(C, C->eps, x, y, z), cs = sqrt(1.0 + 2.0 * pt_model(C, C->del, x, y, z));
+    double b = pt_f(C, F->u2, x, y, z);
+    return F->mode == 1 ? ca * a + cs * b : cs * a + b;
+}
+/* centred (D_ax f)(node) and staggered (D+_ax f)(node + 1/2) */
+static double fld_D(const pt_fld *F, int ax, int x, int y, int z, int staggered)
+{
+    const pt_ctx *C = F->C;
+    double acc = 0.0;
+    for (int k = 1; k <= C->M; k++) {
+        int kp = k, km = staggered ? k - 1 : k;
+        double fp = fld_at(F, x + (ax == 0) * kp, y + (ax == 1) * kp, z + (ax == 2) * kp);
+        double fm = fld_at(F, x - (ax == 0) * km, y - (ax == 1) * km, z - (ax == 2) * km);
+        acc += (staggered ? C->b[k] : C->c[k]) * (fp - fm);
+    }
+    return acc / C->d->h;
+}
+/* entry (i, j) of P0 = xb xb^T + yb yb^T (which = 0) or Pz = zb zb^T (1) at a node */
+static double sp_P(const pt_ctx *C, int which, int i, int j, int x, int y, int z)
+{
+    double xb[3], yb[3], zb[3];
+    frame(pt_model(C, C->th, x, y, z), pt_model(C, C->ph, x, y, z), xb, yb, zb);
+    return which ? zb[i] * zb[j] : xb[i] * xb[j] + yb[i] * yb[j];
+}
+/* cross flux sum_{j != i} P_ij D_j f at a node (0 outside) */
+static double sp_cross(const pt_fld *F, int which, int i, int x, int y, int z)
+{
+    if (!pt_in(F->C, x, y, z)) return 0.0;
+    double acc = 0.0;
+    for (int j = 0; j < 3; j++)
+        if (j != i) acc += sp_P(F->C, which, i, j, x, y, z) * fld_D(F, j, x, y, z, 0);
+    return acc;
+}
+/* diagonal flux at the half point node + e_i/2: the two-node average of
+ * P_ii (the neighbour clamped at the last node) times D+_i f (0 outside) */
+static double sp_diag(const pt_fld *F, int which, int i, int x, int y, int z)
+{
+    const pt_ctx *C = F->C;
+    if (!pt_in(C, x, y, z)) return 0.0;
+    int x1 = clampi(x + (i == 0), 0, C->NX - 1), y1 = clampi(y + (i == 1), 0, C->NY - 1),
+        z1 = clampi(z + (i == 2), 0, C->NZ - 1);
+    double pa = 0.5 * (sp_P(C, which, i, i, x, y, z) + sp_P(C, which, i, i, x1, y1, z1));
+    return pa * fld_D(F, i, x, y, z, 1);
+}
+/* H u = -sum_i [ D_i^T (cross flux) + (D+_i)^T (diagonal flux) ] at a node, with
+ * (D_i^T w)(x) = (1/h) sum_k c_k (w(x - k) - w(x + k)) and
+ * ((D+_i)^T s)(x) = (1/h) sum_k b_k (s(x - k) - s(x + k - 1)) */
+static double sp_H(const pt_fld *F, int which, int x, int y, int z)
+{
+    const pt_ctx *C = F->C;
+    double acc = 0.0;
+    for (int i = 0; i < 3; i++)
+        for (int k = 1; k <= C->M; k++) {
+            int ex = (i == 0), ey = (i == 1), ez = (i == 2);
+            acc += C->c[k] * (sp_cross(F, which, i, x - ex * k, y - ey * k, z - ez * k) -
+                              sp_cross(F, which, i, x + ex * k, y + ey * k, z + ez * k));
+            acc += C->b[k] * (sp_diag(F, which, i, x - ex * k, y - ey * k, z - ez * k) -
+                              sp_diag(F, which, i, x + ex * (k - 1), y + ey * (k - 1), z + ez * (k - 1)));
+        }
+    return -acc / C->d->h;
+}
+
 /* Values of one step (forward, or adjoint if adjoint != 0) at npts points
  * idx[] (computational-grid linear indices).  State arrays are float32 on
  * the computational grid: (p0, p1, r0, r1) = (u^{n-1}, u^n) for p and r
  * (adjoint: lam^{k+2}, lam^{k+1}).  Model arrays are the PHYSICAL float32
  * inputs. out[2*i] = p2, out[2*i+1] = r2. */
-int or_tti_step_points(const or_desc *d, const float *const *model,
-                       const float *p0, const float *p1, const float *r0, const float *r1,
-                       int npts, const long *idx, double *out, int adjoint)
+int or_tti_step_points_op(const or_desc *d, const float *const *model,
+                          const float *p0, const float *p1, const float *r0, const float *r1,
+                          int npts, const long *idx, double *out, int adjoint, int op)
 {
     pt_ctx C;
     C.d = d; C.NX = d->nx + 2 * d->nbl; C.NY = d->ny + 2 * d->nbl; C.NZ = d->nz + 2 * d->nbl;
     C.M = d->so / 2;
+    if (op != 0 && op != 1) return OR_EINVAL;
     double tmp[MAXM];
     if (or_weights_centred(d->so, tmp)) return OR_EINVAL;
     for (int k = 1; k <= C.M; k++) C.c[k] = tmp[k - 1];
+    if (or_weights_staggered(d->so, tmp)) return OR_EINVAL;
+    for (int k = 1; k <= C.M; k++) C.b[k] = tmp[k - 1];
     C.vp = model[0]; C.eps = model[1]; C.del = model[2]; C.th = model[3]; C.ph = model[4];
     long np = (long)d->nx * d->ny * d->nz;
     double vmax = 0.0;
@@ -1389,7 +1467,11 @@ int or_tti_step_points(const or_desc *d, const float *const *model,
         long q = idx[i];
         int z = (int)(q % C.NZ), y = (int)((q / C.NZ) % C.NY), x = (int)(q / ((long)C.NZ * C.NY));
         double H0, Hz;
-        if (!adjoint) {
+        if (op == 1) {                   /* staggered-pair operators */
+            pt_fld Fp = {&C, p1, r1, adjoint ? 1 : 0}, Fr = {&C, adjoint ? p1 : r1, r1, adjoint ? 2 : 0};
+            H0 = sp_H(&Fp, 0, x, y, z);
+            Hz = sp_H(&Fr, 1, x, y, z);
+        } else if (!adjoint) {
             H0 = -(pt_G(&C, p1, 0, x, y, z, NULL, 0, NULL) + pt_G(&C, p1, 1, x, y, z, NULL, 0, NULL));
             Hz = -pt_G(&C, r1, 2, x, y, z, NULL, 0, NULL);
         } else {
@@ -1414,6 +1496,13 @@ int or_tti_step_points(const or_desc *d, const float *const *model,
         out[2 * i + 1] = (dt * dt * Lr + 2.0 * m * R1 - B * R0) / A;
     }
     return OR_OK;
+}
+
+int or_tti_step_points(const or_desc *d, const float *const *model,
+                       const float *p0, const float *p1, const float *r0, const float *r1,
+                       int npts, const long *idx, double *out, int adjoint)
+{
+    return or_tti_step_points_op(d, model, p0, p1, r0, r1, npts, idx, out, adjoint, 0);
 }
 
 /* ------------------------------------------------------------------ */

@@ -213,17 +213,20 @@ def sample_points(shape, n, seed):
     return np.array([(x * NY + y) * NZ + z for x, y, z in pts], np.int64)
 
 
+@pytest.mark.parametrize("op", [0, 1])
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_one_step_sampled_full_size(wp, adjoint):
+def test_one_step_sampled_full_size(wp, adjoint, op):
     """Industry-scale TTI grid (800x800x400 + 40-cell layer = 880x880x480),
-    space order 12: one step from a seeded random state; the oracle evaluates
-    the step at sampled points (interior, faces, edges, corners)."""
+    space order 12, centred (op 0) and staggered-pair (op 1) operators: one
+    step from a seeded random state; the oracle evaluates the step at
+    sampled points (interior, faces, edges, corners)."""
     nx, ny, nz, nbl, h = 800, 800, 400, 40, 12.5
     model = random_tti_model((nx, ny, nz), 77)
     dt = synth.cfl_dt(h, float(np.max(model["vp"] * np.sqrt(1 + 2 * model["eps"]))))
     p = synth.Problem(synth.TTI, nx, ny, nz, nbl, h, 12, 10, dt, model,
                       np.zeros((1, 3), np.float32), np.zeros((1, 10), np.float32),
                       np.zeros((1, 3), np.float32))
+    p.tti_op = op
     prop = wp.Propagator.from_problem(p)
     shape = prop.grid
     rng = np.random.default_rng(5)
