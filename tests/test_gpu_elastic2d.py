@@ -87,3 +87,27 @@ def test_rejected_calls(wp):
     assert e.value.code == wp.PROP_EINVAL
     tr = prop.forward(p.wavelet, p.src, p.rec)          # the handle stays usable
     assert np.isfinite(tr).all()
+
+
+def test_state_steps_full_size(wp):
+    """The 2D marine workload's full grid (1701 x 701 @ 5 m + 40-cell layer
+    = 1781 x 781, so 8) in the launch configuration of its modelling run:
+    three steps from a seeded random state against the oracle's whole-grid
+    steps, every point of every field."""
+    p = synth.marine_elastic_2d(nt=10)
+    prop = wp.Propagator.from_problem(p)
+    rng = np.random.default_rng(31)
+    shape = prop.grid
+    rs = [rng.standard_normal(shape).astype(np.float32) for _ in range(2)]
+    rs += [(1e6 * rng.standard_normal(shape)).astype(np.float32) for _ in range(3)]
+    prop.set_state(rs)
+    prop.step(3)
+    got = prop.get_state()
+    prop.close()
+    o = oracle.Problem(p)
+    s = np.zeros((9,) + o.shape)
+    for c, a in zip(E2, rs):
+        s[c] = a
+    ref = o.el2_run_d(s, 3)
+    for i, c in enumerate(E2):
+        assert rel(got[i], ref[c]) <= TOL, i
