@@ -253,7 +253,7 @@ def sp_problem(so, nt=70, shape=(37, 29, 45)):
     return p
 
 
-@pytest.mark.parametrize("so", [8, 12])
+@pytest.mark.parametrize("so", [4, 8, 12, 16])
 @pytest.mark.parametrize("shape", SHAPES)
 def test_staggered_pair_forward_adjoint_parity(wp, so, shape):
     p = sp_problem(so, nt=60, shape=shape)
