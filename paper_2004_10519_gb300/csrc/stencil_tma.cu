@@ -465,27 +465,20 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
             float wp[2 * M + 2], wr[2 * M + 2];
             zwin<M>(sp + cy * B::RC, cz, wp);
             zwin<M>(sr + cy * B::RC, cz, wr);
-            float gp0a = 0.f, gp0b = 0.f, gp1a = 0.f, gp1b = 0.f, gp2a = 0.f, gp2b = 0.f;
-            float gr0a = 0.f, gr0b = 0.f, gr1a = 0.f, gr1b = 0.f, gr2a = 0.f, gr2b = 0.f;
+            // paired FP32: .x the first z point, .y the second
+            float2 gp0 = Z2, gp1 = Z2, gp2 = Z2, gr0 = Z2, gr1 = Z2, gr2 = Z2;
 #pragma unroll
             for (int k = 1; k <= M; k++) {
-                const float c = w.c[k - 1];
-                const float2 px_ = dif2(qp[M + k], qp[M - k]), rx_ = dif2(qr[M + k], qr[M - k]);
-                gp0a += c * px_.x;
-                gp0b += c * px_.y;
-                gr0a += c * rx_.x;
-                gr0b += c * rx_.y;
-                const float2 py_ = dif2(lds2(sp + ci + k * B::RC), lds2(sp + ci - k * B::RC));
-                const float2 ry_ = dif2(lds2(sr + ci + k * B::RC), lds2(sr + ci - k * B::RC));
-                gp1a += c * py_.x;
-                gp1b += c * py_.y;
-                gr1a += c * ry_.x;
-                gr1b += c * ry_.y;
-                gp2a += c * (wp[M + k] - wp[M - k]);
-                gp2b += c * (wp[M + k + 1] - wp[M - k + 1]);
-                gr2a += c * (wr[M + k] - wr[M - k]);
-                gr2b += c * (wr[M + k + 1] - wr[M - k + 1]);
+                const float2 c = f2s(w.c[k - 1]);
+                gp0 = f2fma(c, f2sub(qp[M + k], qp[M - k]), gp0);
+                gr0 = f2fma(c, f2sub(qr[M + k], qr[M - k]), gr0);
+                gp1 = f2fma(c, f2sub(lds2(sp + ci + k * B::RC), lds2(sp + ci - k * B::RC)), gp1);
+                gr1 = f2fma(c, f2sub(lds2(sr + ci + k * B::RC), lds2(sr + ci - k * B::RC)), gr1);
+                gp2 = f2fma(c, make_float2(wp[M + k] - wp[M - k], wp[M + k + 1] - wp[M - k + 1]), gp2);
+                gr2 = f2fma(c, make_float2(wr[M + k] - wr[M - k], wr[M + k + 1] - wr[M - k + 1]), gr2);
             }
+            const float gp0a = gp0.x, gp0b = gp0.y, gp1a = gp1.x, gp1b = gp1.y, gp2a = gp2.x, gp2b = gp2.y;
+            const float gr0a = gr0.x, gr0b = gr0.y, gr1a = gr1.x, gr1b = gr1.y, gr2a = gr2.x, gr2b = gr2.y;
             const float2 n0 = lds2(S + L::ON + ii), n1 = lds2(S + L::ON + IS + ii);
             const float ih = g.ih;
             const unsigned q = x * pl + q0;
