@@ -737,6 +737,7 @@ struct AL {
     static constexpr int OU = 0, OI = RS, SZ = OI + NI * AIS;
     static constexpr int QH = 0, WW = 1, U0 = 2, UF = 3, GG = 4;
     static constexpr uint32_t BYTES = 4u * (RR * RC + NI * AIS);
+    static constexpr int NS = GRAD ? 3 : 4;   // ring stages that still fit two CTAs per SM
 };
 
 struct AMaps {
@@ -751,7 +752,7 @@ acu_tma(GridDev g, FDW w, const float *__restrict__ u1, float *__restrict__ u0, 
     using L = AL<M, GRAD>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::NS * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, lane = (ty * TZ2 + tz) & 31;
     const bool lead = ty == 0 && tz == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * AFY;
@@ -771,7 +772,7 @@ acu_tma(GridDev g, FDW w, const float *__restrict__ u1, float *__restrict__ u0, 
             tma3(I + L::GG * AIS, &mp.g, z0, y0, x, bar);
         }
     };
-    Ring R(bars);
+    RingN<L::NS> R(bars);
     if (lead) R.init();
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
@@ -1146,7 +1147,7 @@ int acu_launch(prop_s *P, float *const *S, const float *uf, float *grad)
               map_of(P, P->acw, FZ, AFY, &am.w) && map_of(P, S[1], FZ, AFY, &am.u0);
     if (GRAD) ok = ok && map_of(P, uf, FZ, AFY, &am.uf) && map_of(P, grad, FZ, AFY, &am.g);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-    const size_t sb = NSTAGE * AL<M, GRAD>::SZ * sizeof(float) + 64;
+    const size_t sb = AL<M, GRAD>::NS * AL<M, GRAD>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(acu_tma<M, GRAD>, sb);
     (void)attr;
     acu_tma<M, GRAD><<<grd, blk, sb, P->stream>>>(g, P->w, S[0], S[1], grad, am, P->flag, P->d.check_nan, xc,
