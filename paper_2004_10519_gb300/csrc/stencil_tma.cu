@@ -4,14 +4,16 @@
 // its 256 threads updates two adjacent z points, so shared-memory taps and
 // global accesses are 8-byte (float2) and every y-tap row serves two
 // outputs.  For every plane the y/z-halo boxes of the differentiated fields
-// are fetched with cp.async.bulk.tensor into a 3-stage shared-memory ring;
-// out-of-grid elements arrive as zeros, which is the zero extension of the
+// are fetched with cp.async.bulk.tensor into a shared-memory ring of three
+// stages (four in the TTI rotation and acoustic forward passes); out-of-grid
+// elements arrive as zeros, which is the zero extension of the
 // finite-difference operators.  Every other per-plane input (the thread's
 // own values, parameters, the new head of each x-derivative queue M planes
-// ahead) comes through the same ring as an interior box, so all loads are
-// issued two planes ahead.  The ring is a producer/consumer pipeline on
-// mbarriers (see Ring): lane 0 of warp 0 refills a stage once every warp has
-// released it, and no CTA-wide barrier is taken per plane.
+// ahead) comes through the same ring as an interior box.  The ring is a
+// producer/consumer pipeline on mbarriers (RingN in tma.cuh): a dedicated
+// producer warp refills a stage as soon as every consumer warp has released
+// it, and no CTA-wide barrier is taken per plane (the acoustic pass uses a
+// 32 x 32 tile, two rows per thread).
 // z-derivatives read a window of M+1 float2 per field; x-derivatives use
 // per-thread float2 register queues.
 // Offsets are 32-bit (the runtime keeps N below 2^32).  Every mbarrier wait
