@@ -4,7 +4,9 @@
 // d^n from u^n, advance, inject q^n into the new level.  Adjoint loops run
 // the transposed steps backwards.  Gradients use the adjoint-state method
 // (Sec. III) with forward wavefields either kept in full or recomputed from
-// checkpoints (FP32, or BF16/FP16 with one scale per field).
+// checkpoints (FP32, or BF16/FP16 with one scale per field).  Source-free
+// state steps (prop_step) replay pairs of steps from a CUDA graph captured
+// once per handle, direction and state buffers.
 #include "internal.h"
 
 #include <algorithm>
