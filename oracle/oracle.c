@@ -678,6 +678,74 @@ static void tti_frame_image(const or_prob *P, const double *zp, const double *zr
     for (int i = 0; i < 3; i++) { free(Gz[i]); free(Gr[i]); free(gp[i]); free(gr[i]); }
 }
 
+/* Tilt/azimuth imaging of one step for the staggered-pair operators
+ * (tti_apply_H_sp).  Their bilinear forms differ from the centred ones only
+ * in the diagonal terms: with a = D zp, b = D p, c = D zr, d = D r (centred,
+ * at the nodes) and the half-point products S0_i(h) = (D+_i zp)(D+_i p)(h),
+ * Sz_i(h) = (D+_i zr)(D+_i r)(h) (half point h + 1/2 stored at h),
+ *   <zp, H0 p> = -a^T P0 b + sum_i P0_ii a_i b_i - sum_{i,h} P0~_ii(h) S0_i(h)
+ * and likewise for Hz with Pz.  P_ii(q) enters P~_ii at the half points
+ * q + 1/2 (weight 1/2; 1 at the last node, whose partner is clamped to
+ * itself) and q - 1/2 (weight 1/2, none at the first node), so the term at q
+ * collects T_i(q) = w+ S_i(q) + w- S_i(q - e_i).  The derivative with
+ * respect to an angle t is therefore the centred one (tti_frame_image) plus
+ *   sum_i dP0_ii/dt (a_i b_i - T0_i) + sum_i dPz_ii/dt (c_i d_i - Tz_i),
+ * dP0_ii/dt = 2 (xb_t,i xb_i + yb_t,i yb_i), dPz_ii/dt = 2 zb_t,i zb_i. */
+static void tti_frame_image_sp(const or_prob *P, const double *zp, const double *zr, const double *p,
+                               const double *r, double scale, double *gt, double *gf, double *at, double *af)
+{
+    tti_frame_image(P, zp, zr, p, r, scale, gt, gf, at, af);
+    long N = P->N;
+    double *a[3], *b[3], *c[3], *d[3], *S0[3], *Sz[3], *t1 = dalloc(N), *t2 = dalloc(N);
+    for (int i = 0; i < 3; i++) {
+        a[i] = dalloc(N); b[i] = dalloc(N); c[i] = dalloc(N); d[i] = dalloc(N);
+        S0[i] = dalloc(N); Sz[i] = dalloc(N);
+        apply_axis(line_D, zp, a[i], i, P);
+        apply_axis(line_D, p, b[i], i, P);
+        apply_axis(line_D, zr, c[i], i, P);
+        apply_axis(line_D, r, d[i], i, P);
+        apply_axis(line_Dp, zp, t1, i, P);
+        apply_axis(line_Dp, p, t2, i, P);
+        for (long q = 0; q < N; q++) S0[i][q] = t1[q] * t2[q];
+        apply_axis(line_Dp, zr, t1, i, P);
+        apply_axis(line_Dp, r, t2, i, P);
+        for (long q = 0; q < N; q++) Sz[i][q] = t1[q] * t2[q];
+    }
+#pragma omp parallel for collapse(2)
+    for (int x = 0; x < P->NX; x++)
+        for (int y = 0; y < P->NY; y++)
+            for (int z = 0; z < P->NZ; z++) {
+                long q = IDX(P, x, y, z);
+                const int pos[3] = {x, y, z}, len[3] = {P->NX, P->NY, P->NZ};
+                double xb[3], yb[3], zb[3], A[3], B[3], C3[3], U[3], V[3], W[3];
+                frame(P->th[q], P->ph[q], xb, yb, zb);
+                frame_dth(P->th[q], P->ph[q], A, B, C3);
+                frame_dph(P->th[q], P->ph[q], U, V, W);
+                double tt = 0.0, ff = 0.0, ta = 0.0, fa = 0.0;
+                for (int i = 0; i < 3; i++) {
+                    long qm = q - (i == 0 ? (long)P->NY * P->NZ : (i == 1 ? P->NZ : 1));
+                    double wp = pos[i] == len[i] - 1 ? 1.0 : 0.5, wm = pos[i] >= 1 ? 0.5 : 0.0;
+                    double T0 = wp * S0[i][q] + (wm > 0.0 ? wm * S0[i][qm] : 0.0);
+                    double Tz = wp * Sz[i][q] + (wm > 0.0 ? wm * Sz[i][qm] : 0.0);
+                    double e0 = a[i][q] * b[i][q] - T0, ez = c[i][q] * d[i][q] - Tz;
+                    double d0t = 2.0 * (A[i] * xb[i] + B[i] * yb[i]), dzt = 2.0 * C3[i] * zb[i];
+                    double d0f = 2.0 * (U[i] * xb[i] + V[i] * yb[i]), dzf = 2.0 * W[i] * zb[i];
+                    tt += d0t * e0 + dzt * ez;
+                    ff += d0f * e0 + dzf * ez;
+                    ta += fabs(d0t) * (fabs(a[i][q] * b[i][q]) + fabs(T0)) + fabs(dzt) * (fabs(c[i][q] * d[i][q]) + fabs(Tz));
+                    fa += fabs(d0f) * (fabs(a[i][q] * b[i][q]) + fabs(T0)) + fabs(dzf) * (fabs(c[i][q] * d[i][q]) + fabs(Tz));
+                }
+                gt[q] += scale * tt;
+                gf[q] += scale * ff;
+                if (at) {
+                    at[q] += fabs(scale) * ta;
+                    af[q] += fabs(scale) * fa;
+                }
+            }
+    for (int i = 0; i < 3; i++) { free(a[i]); free(b[i]); free(c[i]); free(d[i]); free(S0[i]); free(Sz[i]); }
+    free(t1); free(t2);
+}
+
 /* Staggered-pair variant of the same operators.  With P0 = xb xb^T + yb yb^T
  * and Pz = zb zb^T (pointwise), the centred form above is
  *   H0 u = -sum_{i,j} D_i^T (P0_ij D_j u),  Hz u = -sum_{i,j} D_i^T (Pz_ij D_j u);
@@ -931,7 +999,10 @@ static int tti_adjoint_core(or_prob *P, int nrec, const float *rec, const double
                 zp[q] = a * l0[q] + s * s0[q];
                 zr[q] = s * l0[q] + s0[q];
             }
-            tti_frame_image(P, zp, zr, up1, ur1, dt * dt, grad_t, grad_f, abs_tf, abs_tf ? abs_tf + N : NULL);
+            if (P->tti_op == 1)
+                tti_frame_image_sp(P, zp, zr, up1, ur1, dt * dt, grad_t, grad_f, abs_tf, abs_tf ? abs_tf + N : NULL);
+            else
+                tti_frame_image(P, zp, zr, up1, ur1, dt * dt, grad_t, grad_f, abs_tf, abs_tf ? abs_tf + N : NULL);
             free(zp); free(zr);
         }
         double *t;
@@ -986,7 +1057,7 @@ int or_tti_gradient_aniso(or_prob *P, int nsrc, const float *src, const float *w
                           int nrec, const float *rec, const double *d_obs,
                           double *grad_phys, double *misfit, double *abs_phys)
 {
-    if (P->d.kind != 1 || P->tti_op != 0) return OR_EINVAL;   /* frame derivatives: centred form */
+    if (P->d.kind != 1) return OR_EINVAL;
     int nt = P->d.nt;
     double *tr = dalloc((long)nrec * nt);
     int rc = or_tti_forward(P, nsrc, src, wav, nrec, rec, tr, 1);
