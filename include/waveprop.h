@@ -100,8 +100,8 @@ typedef struct {
                             diagonal (P0 = I - n n^T for H0, n n^T for Hz) at
                             the half point, cross terms centred; no
                             checkerboard null vector.  Must be 0 for the other
-                            kinds; 1 is not available to prop_gradient_aniso
-                            or prop_forward_noalloc (PROP_EINVAL).            */
+                            kinds; 1 is not available to
+                            prop_forward_noalloc (PROP_EINVAL).               */
 } prop_desc;
 
 /* Create a propagator.  model points to the PHYSICAL-grid float32 arrays
@@ -162,7 +162,11 @@ int prop_gradient(prop_t *p, const float *wavelet, const float *src_xyz, int nsr
  * h = D r^n (centred first derivatives at the point) and
  *   V = D zeta_p (n.g) + (n.D zeta_p) g - D zeta_r (n.h) - (n.D zeta_r) h,
  *   dJ/dtheta = sum_n dt^2 dn/dtheta . V,   dJ/dphi = sum_n dt^2 dn/dphi . V
- * (each folded onto the physical grid like dJ/dm).
+ * (each folded onto the physical grid like dJ/dm).  With tti_operator = 1
+ * the diagonal terms use half-point averages of P_ii, so V gains
+ *   2 n_i (T0_i - (D_i zeta_p) g_i) - 2 n_i (Tz_i - (D_i zeta_r) h_i),
+ * T_i the products (D+_i zeta)(D+_i u) of the half points beside the node
+ * (weights 1/2; 1 above the last node, none below the first).
  *   grad  [5][nx][ny][nz]: dJ/dm, dJ/deps, dJ/ddelta, dJ/dtheta, dJ/dphi.
  * Costs per step one more application of H to the stored forward field and
  * the first derivatives of zeta and of the forward field; needs 6 more

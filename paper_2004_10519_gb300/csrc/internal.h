@@ -68,7 +68,7 @@ struct prop_s {
     // scratch: TTI 6 intermediates (ex ey ez fx fy fz) + 2 (zeta p, r);
     // elastic adjoint: 6 (stress-like) + 3 (weighted velocity) + 6 gradient
     // products (edges xy xz yz, faces x y z)
-    float *tmp[16] = {};
+    float *tmp[20] = {};
     int *flag = nullptr;     // device: bit0 NaN/Inf seen
     float *tab = nullptr;    // per-axis absorbing-layer tables (GridDev::tab)
     int xchunk = 8;          // planes per CTA of the x-streaming stencil kernels
@@ -121,6 +121,12 @@ int tti_sp_launch(prop_s *P, float *const *S, bool adjoint, const float *img_p, 
                   float *grad);
 int tti_sp_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
                       float *grad);
+// eps, delta (and tilt/azimuth) imaging of one transposed staggered-pair step
+// (zeta = C lam in tmp[6], tmp[7]; uses tmp[0..5], tmp[8..19])
+int tti_sp_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
+                           float *ge, float *gd, float *const *gax);
+// centred first derivatives D p (out[0..2]) and D r (out[3..5]), TMA pass
+int tti_raw_derivs_tma(prop_s *P, const float *p, const float *r, float *const *out);
 // elastic step in place on S (9 fields); adjoint: transposed step (tbar form)
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 // pipelined elastic step with time step dt_sign * dt (any NZ): forward (+1)

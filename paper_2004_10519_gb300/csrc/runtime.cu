@@ -1066,7 +1066,7 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
     const int nt = P->d.nt;
     const size_t N = (size_t)P->g.N;
     WP_TRY(ensure_ast(P));
-    if (aniso) WP_TRY(ensure_tmp(P, 14));
+    if (aniso) WP_TRY(ensure_tmp(P, P->d.tti_operator == 1 ? 20 : 14));
     float *a[4] = {P->ast[0], P->ast[1], P->ast[2], P->ast[3]};
     WP_TRY(zero_fields(P, a, 4));
     WP_TRY(zero_fields(P, P->tmp + 6, 2));   // zeta = C lam of the zero state
@@ -1354,8 +1354,6 @@ extern "C" int prop_gradient_aniso(prop_t *P, const float *wavelet, const float 
 {
     WP_TRY(check_handle(P));
     if (P->d.kind != PROP_TTI) return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso is for TTI propagators");
-    if (P->d.tti_operator != 0)
-        return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso needs the centred operators (tti_operator = 0)");
     if (!tma_usable(P))
         return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso needs a computational nz that is a multiple of 4");
     P->aniso = true;
@@ -1421,7 +1419,7 @@ static size_t gradient_bytes(const prop_s *P, int nrec)
         if (!P->st[i]) b += N * 4;
     }
     const bool aniso = P->d.kind == PROP_TTI && P->aniso;
-    const int ntmp = P->d.kind == PROP_TTI ? (aniso || P->d.tti_operator == 1 ? 14 : 8)
+    const int ntmp = P->d.kind == PROP_TTI ? (aniso && P->d.tti_operator == 1 ? 20 : aniso || P->d.tti_operator == 1 ? 14 : 8)
                                            : (P->d.kind == PROP_ACOUSTIC ? 0 : 15);
     for (int i = 0; i < ntmp; i++)
         if (!P->tmp[i]) b += N * 4;

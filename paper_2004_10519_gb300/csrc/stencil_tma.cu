@@ -1180,6 +1180,30 @@ __global__ void wait_probe(uint64_t limit_ns, int *err)
     __syncwarp();
 }
 
+// centred first derivatives of (p, r) through the rotation pass in its raw
+// mode: out[0..2] = D p, out[3..5] = D r
+template <int M>
+int raw_derivs(prop_s *P, const float *p, const float *r, float *const *out)
+{
+    using B = BX<M>;
+    const GridDev &g = P->g;
+    const int xc = P->xchunk;
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    RMaps rm;
+    const bool ok = map_of(P, p, B::RC, B::RR, &rm.p) && map_of(P, r, B::RC, B::RR, &rm.r) &&
+                    map_of(P, p, FZ, FY, &rm.qp) && map_of(P, r, FZ, FY, &rm.qr) &&
+                    map_of(P, P->nrm[0], FZ, FY, &rm.nx) && map_of(P, P->nrm[1], FZ, FY, &rm.ny);
+    if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_rot_tma<M, true>, s1);
+    (void)attr;
+    tti_rot_tma<M, true><<<grd, blk, s1, P->stream>>>(g, P->w, p, r, rm, out[0], out[1], out[2], out[3], out[4],
+                                                      out[5], xc, P->flag);
+    P->kern_launches += 1;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 }  // namespace
 
 // launch the wait self-test on the handle's stream (limit in seconds, <= 2)
@@ -1238,6 +1262,7 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
 int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
                         float *ge, float *gd, float *const *gax)
 {
+    if (P->d.tti_operator == 1) return tti_sp_image_aniso_tma(P, up, ur, lp, lr, ge, gd, gax);
     switch (P->M) {
     case 2: return tti_image_aniso<2>(P, up, ur, lp, lr, ge, gd, gax);
     case 4: return tti_image_aniso<4>(P, up, ur, lp, lr, ge, gd, gax);
@@ -1282,4 +1307,17 @@ int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
     }
     prof_end(P, adjoint ? 1 : 0);
     return rc;
+}
+
+// centred first derivatives D p (out[0..2]) and D r (out[3..5]) through the
+// TMA rotation pass in its raw mode (NZ a multiple of 4)
+int tti_raw_derivs_tma(prop_s *P, const float *p, const float *r, float *const *out)
+{
+    switch (P->M) {
+    case 2: return raw_derivs<2>(P, p, r, out);
+    case 4: return raw_derivs<4>(P, p, r, out);
+    case 6: return raw_derivs<6>(P, p, r, out);
+    case 8: return raw_derivs<8>(P, p, r, out);
+    }
+    return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }

@@ -195,15 +195,18 @@ tti_sp_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__res
 // ---------------------------------------------------------------------------
 // pass 2.  stage: [c0_y, cz_y, s0_y, sz_y (y boxes)] [c0_z, cz_z, s0_z, sz_z
 // (z boxes)] [heads c0_x, cz_x (x+M), s0_x, sz_x (x+M-1)] [m, p^n, r^n,
-// p^{n-1}, r^{n-1}, eps, delta (plane x)] (+ [u_p, u_r, g] imaging)
+// p^{n-1}, r^{n-1}, eps, delta (plane x)] (+ [u_p, u_r, g] imaging).
+// ADJ = 2: no step; imaging of the coupling C with the forward field whose
+// fluxes were just formed: interiors [lam_p, lam_r, delta, g_eps, g_delta]
 // ---------------------------------------------------------------------------
-template <int M, int GRAD>
+template <int M, int ADJ, int GRAD>
 struct SUL {
     using B = BX<M>;
-    static constexpr int NI = 11 + (GRAD ? 3 : 0);
+    static constexpr bool IMG = ADJ == 2;
+    static constexpr int NI = IMG ? 9 : 11 + (GRAD ? 3 : 0);
     static constexpr int OY = 0, OZ = 4 * B::YS, OI = OZ + 4 * B::ZS, SZ = OI + NI * IS;
-    static constexpr int HC0 = 0, HCZ = 1, HS0 = 2, HSZ = 3, MM = 4, PC = 5, RC = 6, PP = 7, RP = 8, EP = 9,
-                         DE = 10, UP = 11, UR = 12, GG = 13;
+    static constexpr int HC0 = 0, HCZ = 1, HS0 = 2, HSZ = 3, MM = 4, PC = IMG ? 4 : 5, RC = PC + 1, PP = 7,
+                         RP = 8, EP = 9, DE = IMG ? 6 : 10, UP = IMG ? 7 : 11, UR = UP + 1, GG = 13;
     static constexpr uint32_t BYTES = 4u * (4 * B::YR * B::YC + 4 * B::ZR * B::ZC + NI * IS);
 };
 
@@ -267,7 +270,7 @@ tti_sp_upd_tma(GridDev g, FDW w, F12 o, const __grid_constant__ SUMaps mp, float
                float *__restrict__ rp, float *__restrict__ grad, float *__restrict__ zp, float *__restrict__ zr,
                int *flag, int check, int xc, int *err)
 {
-    using L = SUL<M, GRAD>;
+    using L = SUL<M, ADJ, GRAD>;
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
     extern __shared__ __align__(128) float sm[];
@@ -290,13 +293,18 @@ tti_sp_upd_tma(GridDev g, FDW w, F12 o, const __grid_constant__ SUMaps mp, float
         tma3(I + L::HCZ * IS, &mp.h[1], z0, y0, x + M, bar);
         tma3(I + L::HS0 * IS, &mp.h[2], z0, y0, x + M - 1, bar);
         tma3(I + L::HSZ * IS, &mp.h[3], z0, y0, x + M - 1, bar);
-        tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
         tma3(I + L::PC * IS, &mp.pc, z0, y0, x, bar);
         tma3(I + L::RC * IS, &mp.rc, z0, y0, x, bar);
+        tma3(I + L::DE * IS, &mp.d, z0, y0, x, bar);
+        if (L::IMG) {
+            tma3(I + L::UP * IS, &mp.up, z0, y0, x, bar);
+            tma3(I + L::UR * IS, &mp.ur, z0, y0, x, bar);
+            return;
+        }
+        tma3(I + L::MM * IS, &mp.m, z0, y0, x, bar);
         tma3(I + L::PP * IS, &mp.pp, z0, y0, x, bar);
         tma3(I + L::RP * IS, &mp.rp, z0, y0, x, bar);
         tma3(I + L::EP * IS, &mp.e, z0, y0, x, bar);
-        tma3(I + L::DE * IS, &mp.d, z0, y0, x, bar);
         if (GRAD) {
             tma3(I + L::UP * IS, &mp.up, z0, y0, x, bar);
             tma3(I + L::UR * IS, &mp.ur, z0, y0, x, bar);
@@ -350,40 +358,50 @@ tti_sp_upd_tma(GridDev g, FDW w, F12 o, const __grid_constant__ SUMaps mp, float
             const float2 h0v = f2add(a0[0], yz_part<M>(Y, Y + 2 * B::YS, Zb, Zb + 2 * B::ZS, iy, izr, cz, w));
             const float2 hzv = f2add(az[0], yz_part<M>(Y + B::YS, Y + 3 * B::YS, Zb + B::ZS, Zb + 3 * B::ZS, iy,
                                                        izr, cz, w));
-            const float2 mm = lds2(I + L::MM * IS), p1 = lds2(I + L::PC * IS), r1 = lds2(I + L::RC * IS);
-            const float2 p0 = lds2(I + L::PP * IS), r0 = lds2(I + L::RP * IS);
-            const float2 e_ = lds2(I + L::EP * IS), d_ = lds2(I + L::DE * IS);
-            const float sxv = __ldg(sx + x);
-            const float h0[2] = {h0v.x * g.ih, h0v.y * g.ih}, hz[2] = {hzv.x * g.ih, hzv.y * g.ih};
-            const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
-            const float P1[2] = {p1.x, p1.y}, R1[2] = {r1.x, r1.y}, P0[2] = {p0.x, p0.y}, R0[2] = {r0.x, r0.y};
-            const float SYZ[2] = {syz0, syz1};
-            float pn[2], rn[2], Lp[2], Lr[2], c1[2], cc[2];
-#pragma unroll
-            for (int i = 0; i < 2; i++) {
-                c1[i] = 1.f + 2.f * E2[i];
-                cc[i] = sqrtf(1.f + 2.f * D2[i]);
-                Lp[i] = ADJ ? h0[i] : c1[i] * h0[i] + cc[i] * hz[i];
-                Lr[i] = ADJ ? hz[i] : cc[i] * h0[i] + hz[i];
-                const float sd = hdt * (sxv + SYZ[i]);
-                const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
-                pn[i] = (dt2 * Lp[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
-                rn[i] = (dt2 * Lr[i] + 2.f * M2[i] * R1[i] - Bc * R0[i]) / A;
-            }
             const unsigned q = x * pl + q0;
-            st2(pp, q, pn[0], pn[1]);
-            st2(rp, q, rn[0], rn[1]);
-            if (ADJ) {
-                st2(zp, q, c1[0] * pn[0] + cc[0] * rn[0], c1[1] * pn[1] + cc[1] * rn[1]);
-                st2(zr, q, cc[0] * pn[0] + rn[0], cc[1] * pn[1] + rn[1]);
+            if constexpr (L::IMG) {
+                // g_eps += 2 dt^2 lam_p H0 p^n, g_delta += dt^2 (lam_p Hz r^n + lam_r H0 p^n) / sqrt(1 + 2 delta)
+                const float2 lp = lds2(I + L::PC * IS), lr = lds2(I + L::RC * IS), d_ = lds2(I + L::DE * IS);
+                const float2 ge = lds2(I + L::UP * IS), gd = lds2(I + L::UR * IS);
+                const float h0a = h0v.x * g.ih, h0b = h0v.y * g.ih, hza = hzv.x * g.ih, hzb = hzv.y * g.ih;
+                st2(grad, q, ge.x + 2.f * dt2 * lp.x * h0a, ge.y + 2.f * dt2 * lp.y * h0b);
+                st2(zp, q, gd.x + dt2 * (lp.x * hza + lr.x * h0a) / sqrtf(1.f + 2.f * d_.x),
+                    gd.y + dt2 * (lp.y * hzb + lr.y * h0b) / sqrtf(1.f + 2.f * d_.y));
+            } else {
+                const float2 mm = lds2(I + L::MM * IS), p1 = lds2(I + L::PC * IS), r1 = lds2(I + L::RC * IS);
+                const float2 p0 = lds2(I + L::PP * IS), r0 = lds2(I + L::RP * IS);
+                const float2 e_ = lds2(I + L::EP * IS), d_ = lds2(I + L::DE * IS);
+                const float sxv = __ldg(sx + x);
+                const float h0[2] = {h0v.x * g.ih, h0v.y * g.ih}, hz[2] = {hzv.x * g.ih, hzv.y * g.ih};
+                const float M2[2] = {mm.x, mm.y}, E2[2] = {e_.x, e_.y}, D2[2] = {d_.x, d_.y};
+                const float P1[2] = {p1.x, p1.y}, R1[2] = {r1.x, r1.y}, P0[2] = {p0.x, p0.y}, R0[2] = {r0.x, r0.y};
+                const float SYZ[2] = {syz0, syz1};
+                float pn[2], rn[2], Lp[2], Lr[2], c1[2], cc[2];
+#pragma unroll
+                for (int i = 0; i < 2; i++) {
+                    c1[i] = 1.f + 2.f * E2[i];
+                    cc[i] = sqrtf(1.f + 2.f * D2[i]);
+                    Lp[i] = ADJ ? h0[i] : c1[i] * h0[i] + cc[i] * hz[i];
+                    Lr[i] = ADJ ? hz[i] : cc[i] * h0[i] + hz[i];
+                    const float sd = hdt * (sxv + SYZ[i]);
+                    const float A = M2[i] * (1.f + sd), Bc = M2[i] * (1.f - sd);
+                    pn[i] = (dt2 * Lp[i] + 2.f * M2[i] * P1[i] - Bc * P0[i]) / A;
+                    rn[i] = (dt2 * Lr[i] + 2.f * M2[i] * R1[i] - Bc * R0[i]) / A;
+                }
+                st2(pp, q, pn[0], pn[1]);
+                st2(rp, q, rn[0], rn[1]);
+                if (ADJ) {
+                    st2(zp, q, c1[0] * pn[0] + cc[0] * rn[0], c1[1] * pn[1] + cc[1] * rn[1]);
+                    st2(zr, q, cc[0] * pn[0] + rn[0], cc[1] * pn[1] + rn[1]);
+                }
+                if (GRAD) {
+                    const float2 u = lds2(I + L::UP * IS), v = lds2(I + L::UR * IS), gg = lds2(I + L::GG * IS);
+                    st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
+                        gg.y - dt2 * (u.y * Lp[1] + v.y * Lr[1]) / M2[1]);
+                }
+                if (check && !(isfinite(pn[0]) && isfinite(rn[0]) && isfinite(pn[1]) && isfinite(rn[1])))
+                    atomicOr(flag, 1);
             }
-            if (GRAD) {
-                const float2 u = lds2(I + L::UP * IS), v = lds2(I + L::UR * IS), gg = lds2(I + L::GG * IS);
-                st2(grad, q, gg.x - dt2 * (u.x * Lp[0] + v.x * Lr[0]) / M2[0],
-                    gg.y - dt2 * (u.y * Lp[1] + v.y * Lr[1]) / M2[1]);
-            }
-            if (check && !(isfinite(pn[0]) && isfinite(rn[0]) && isfinite(pn[1]) && isfinite(rn[1])))
-                atomicOr(flag, 1);
         }
         shift_x<M>(a0);
         shift_x<M>(az);
@@ -423,7 +441,7 @@ int sp_launch(prop_s *P, float *const *S, const float *up, const float *ur, floa
     if (GRAD)
         ok = ok && map_of(P, up, FZ, FY, &um.up) && map_of(P, ur, FZ, FY, &um.ur) && map_of(P, grad, FZ, FY, &um.g);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-    const size_t s1 = NSTAGE * SRL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * SUL<M, GRAD>::SZ * sizeof(float) + 64;
+    const size_t s1 = NSTAGE * SRL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * SUL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(tti_sp_rot_tma<M>, s1) && set_smem(tti_sp_upd_tma<M, ADJ, GRAD>, s2);
     (void)attr;
     tti_sp_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, rp_, rr_, rm, o, xc, P->flag);
@@ -442,6 +460,156 @@ int sp_launch_any(prop_s *P, float *const *S, bool adjoint, const float *up, con
     return sp_launch<M, 1, 1>(P, S, up, ur, grad);
 }
 
+// ---------------------------------------------------------------------------
+// tilt/azimuth imaging of the staggered-pair operators.  Their bilinear forms
+// differ from the centred ones only in the diagonal terms: with a = D zeta_p,
+// b = D p, c = D zeta_r, d = D r (centred, at the nodes) and the half-point
+// products S0_i(h) = (D+_i zeta_p)(D+_i p)(h), Sz_i(h) = (D+_i zeta_r)(D+_i r)(h),
+// the step's term of dJ/dn at node q is the centred one plus
+//   2 n_i (T0_i - a_i b_i) - 2 n_i (Tz_i - c_i d_i),
+//   T_i(q) = w+ S_i(q) + w- S_i(q - e_i)
+// (n(q) enters the two-node averages of the half points q +- 1/2 with weight
+// 1/2; at the last node its partner is clamped to itself, weight 1; the
+// first node has no half point below it).
+// ---------------------------------------------------------------------------
+struct F6 {
+    float *f[6];
+};
+
+template <int M>
+__global__ void sp_half_products(GridDev g, FDW w, const float *__restrict__ zp, const float *__restrict__ zr,
+                                 const float *__restrict__ up, const float *__restrict__ ur, F6 out)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= g.N) return;
+    const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
+    const int pos[3] = {x, y, z}, len[3] = {g.NX, g.NY, g.NZ};
+    const long long str[3] = {(long long)g.NY * g.NZ, g.NZ, 1};
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
+#pragma unroll
+        for (int k = 1; k <= M; k++) {
+            // D+ f at q + 1/2: b_k (f(q + k) - f(q - k + 1)), zero outside
+            const bool ip = pos[i] + k < len[i], im = pos[i] - k + 1 >= 0;
+            const long long op = q + k * str[i], om = q - (k - 1) * str[i];
+            const float bk = w.b[k - 1];
+            a += bk * ((ip ? __ldg(zp + op) : 0.f) - (im ? __ldg(zp + om) : 0.f));
+            b += bk * ((ip ? __ldg(up + op) : 0.f) - (im ? __ldg(up + om) : 0.f));
+            c += bk * ((ip ? __ldg(zr + op) : 0.f) - (im ? __ldg(zr + om) : 0.f));
+            d += bk * ((ip ? __ldg(ur + op) : 0.f) - (im ? __ldg(ur + om) : 0.f));
+        }
+        const float ih2 = g.ih * g.ih;
+        out.f[i][q] = a * b * ih2;
+        out.f[3 + i][q] = c * d * ih2;
+    }
+}
+
+struct SPAxisIn {
+    const float *dz[6], *du[6], *s[6], *nx, *ny;
+    float *acc[3];
+};
+
+__global__ void tti_axis_image_sp(GridDev g, float sc, SPAxisIn a)
+{
+    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (q >= g.N) return;
+    const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
+    const int pos[3] = {x, y, z}, len[3] = {g.NX, g.NY, g.NZ};
+    const long long str[3] = {(long long)g.NY * g.NZ, g.NZ, 1};
+    const float n0 = a.nx[q], n1 = a.ny[q];
+    const float nv[3] = {n0, n1, sqrtf(fmaxf(0.f, 1.f - n0 * n0 - n1 * n1))};
+    float zp[3], zr[3], gp[3], gr[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        zp[c] = a.dz[c][q];
+        zr[c] = a.dz[3 + c][q];
+        gp[c] = a.du[c][q];
+        gr[c] = a.du[3 + c][q];
+    }
+    float ng = 0.f, nzp = 0.f, nh = 0.f, nzr = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        ng += nv[c] * gp[c];
+        nzp += nv[c] * zp[c];
+        nh += nv[c] * gr[c];
+        nzr += nv[c] * zr[c];
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+        const float wp = pos[c] == len[c] - 1 ? 1.f : 0.5f;
+        const bool below = pos[c] >= 1;
+        const float T0 = wp * a.s[c][q] + (below ? 0.5f * a.s[c][q - str[c]] : 0.f);
+        const float Tz = wp * a.s[3 + c][q] + (below ? 0.5f * a.s[3 + c][q - str[c]] : 0.f);
+        const float v = zp[c] * ng + nzp * gp[c] - zr[c] * nh - nzr * gr[c] +
+                        2.f * nv[c] * ((T0 - zp[c] * gp[c]) - (Tz - zr[c] * gr[c]));
+        a.acc[c][q] += sc * v;
+    }
+}
+
+// eps, delta (and, gax != NULL, tilt/azimuth) imaging of one transposed
+// staggered-pair step with the forward field (up, ur) at level n and the
+// adjoint field (lp, lr) at level n+1; zeta = C lam in tmp[6], tmp[7].
+// Uses tmp[0..5], tmp[8..19].
+template <int M>
+int sp_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr, float *ge,
+                   float *gd, float *const *gax)
+{
+    using B = BX<M>;
+    const GridDev &g = P->g;
+    const int xc = P->xchunk;
+    dim3 blk(TZ2, FY + 2, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    float *const *t = P->tmp;
+    F12 o;
+    for (int i = 0; i < 6; i++) o.f[i] = t[i];
+    for (int i = 0; i < 6; i++) o.f[6 + i] = t[8 + i];
+    SRMaps rm;
+    SUMaps um;
+    bool ok = map_of(P, up, B::RC, B::RR, &rm.p) && map_of(P, ur, B::RC, B::RR, &rm.r) &&
+              map_of(P, up, FZ, FY, &rm.qp) && map_of(P, ur, FZ, FY, &rm.qr) &&
+              map_of(P, P->nrm[0], B::PC, B::PR, &rm.nx1) && map_of(P, P->nrm[1], B::PC, B::PR, &rm.ny1) &&
+              map_of(P, P->nrm[0], FZ, FY, &rm.nxi);
+    const int fy[4] = {1, 4, 7, 10}, fz[4] = {2, 5, 8, 11}, fx[4] = {0, 3, 6, 9};
+    for (int f = 0; f < 4; f++)
+        ok = ok && map_of(P, o.f[fy[f]], B::YC, B::YR, &um.y[f]) && map_of(P, o.f[fz[f]], B::ZC, B::ZR, &um.z[f]) &&
+             map_of(P, o.f[fx[f]], FZ, FY, &um.h[f]);
+    ok = ok && map_of(P, lp, FZ, FY, &um.pc) && map_of(P, lr, FZ, FY, &um.rc) && map_of(P, P->del, FZ, FY, &um.d) &&
+         map_of(P, ge, FZ, FY, &um.up) && map_of(P, gd, FZ, FY, &um.ur);
+    if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
+    const size_t s1 = NSTAGE * SRL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * SUL<M, 2, 0>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_sp_rot_tma<M>, s1) && set_smem(tti_sp_upd_tma<M, 2, 0>, s2);
+    (void)attr;
+    tti_sp_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, o, xc, P->flag);
+    tti_sp_upd_tma<M, 2, 0><<<grd, blk, s2, P->stream>>>(g, P->w, o, um, nullptr, nullptr, ge, gd, nullptr, P->flag,
+                                                         0, xc, P->flag);
+    P->kern_launches += 2;
+    WP_CK(P, cudaGetLastError());
+    if (!gax) return PROP_OK;
+    // centred first derivatives of zeta and of the forward field, the
+    // staggered half-point products, then the pointwise term
+    float *dz[6] = {t[0], t[1], t[2], t[3], t[4], t[5]}, *du[6] = {t[8], t[9], t[10], t[11], t[12], t[13]};
+    WP_TRY(tti_raw_derivs_tma(P, t[6], t[7], dz));
+    WP_TRY(tti_raw_derivs_tma(P, up, ur, du));
+    const long long n = g.N;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    F6 sp;
+    for (int i = 0; i < 6; i++) sp.f[i] = t[14 + i];
+    sp_half_products<M><<<nb, 256, 0, P->stream>>>(g, P->w, t[6], t[7], up, ur, sp);
+    SPAxisIn ai;
+    for (int c = 0; c < 6; c++) {
+        ai.dz[c] = dz[c];
+        ai.du[c] = du[c];
+        ai.s[c] = t[14 + c];
+    }
+    ai.nx = P->nrm[0];
+    ai.ny = P->nrm[1];
+    for (int c = 0; c < 3; c++) ai.acc[c] = gax[c];
+    tti_axis_image_sp<<<nb, 256, 0, P->stream>>>(g, g.dt * g.dt, ai);
+    P->kern_launches += 2;
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 }  // namespace
 
 // one staggered-pair TTI step through the TMA-fed passes (same contract as
@@ -453,6 +621,20 @@ int tti_sp_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img
     case 4: return sp_launch_any<4>(P, S, adjoint, img_p, img_r, grad);
     case 6: return sp_launch_any<6>(P, S, adjoint, img_p, img_r, grad);
     case 8: return sp_launch_any<8>(P, S, adjoint, img_p, img_r, grad);
+    }
+    return wp_fail(P, PROP_EINVAL, "unsupported space order");
+}
+
+// eps, delta (and tilt/azimuth) imaging of one transposed staggered-pair
+// step (see sp_image_aniso; NZ a multiple of 4)
+int tti_sp_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr, float *ge,
+                           float *gd, float *const *gax)
+{
+    switch (P->M) {
+    case 2: return sp_image_aniso<2>(P, up, ur, lp, lr, ge, gd, gax);
+    case 4: return sp_image_aniso<4>(P, up, ur, lp, lr, ge, gd, gax);
+    case 6: return sp_image_aniso<6>(P, up, ur, lp, lr, ge, gd, gax);
+    case 8: return sp_image_aniso<8>(P, up, ur, lp, lr, ge, gd, gax);
     }
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
