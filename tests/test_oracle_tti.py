@@ -519,3 +519,49 @@ def test_staggered_pair_taylor_gradient():
         e2.append(abs(J_of(1.0 / (1000.0 * np.sqrt(m0 + hh * d))) - J0 - hh * lin))
     slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
     assert all(abs(s - 2.0) < 0.2 for s in slopes), (slopes, e2)
+
+
+@pytest.mark.parametrize("op", [0, 1])
+def test_energy_conservation_undamped(op):
+    """Undamped leapfrog m (u^{n+1} - 2u^n + u^{n-1}) = dt^2 C H u^n of the
+    TTI system (Sec. III-A; u = (p, r), H = diag(H0, Hz) symmetric in both
+    operator forms, C symmetric positive definite when eps > delta): with
+    M = m C^{-1} pointwise,
+      E^{n+1/2} = (u^{n+1} - u^n)^T M (u^{n+1} - u^n) - dt^2 (u^{n+1})^T H u^n
+    is exactly constant (take the step against u^{n+1} - u^{n-1}).  H u^n is
+    C^{-1} L u^n with the oracle's L = C H."""
+    n, h, so = 14, 10.0, 8
+    rng = np.random.default_rng(41)
+    shp = (n, n, n)
+    eps = rng.uniform(0.05, 0.3, shp)
+    m = {"vp": rng.uniform(1.5, 3.0, shp).astype(np.float32), "eps": eps.astype(np.float32),
+         "delta": (eps * rng.uniform(0.2, 0.6, shp)).astype(np.float32),
+         "theta": rng.uniform(0.0, 0.7, shp).astype(np.float32),
+         "phi": rng.uniform(-1.0, 1.0, shp).astype(np.float32)}
+    dt = synth.cfl_dt(h, float(np.max(m["vp"] * np.sqrt(1 + 2 * m["eps"]))))
+    z3 = np.zeros((1, 3), np.float32)
+    p = synth.Problem(synth.TTI, n, n, n, 0, h, so, 10, dt, m, z3, np.zeros((1, 10), np.float32), z3)
+    p.tti_op = op
+    o = oracle.Problem(p)
+    e = m["eps"].astype(np.float64)
+    dl = m["delta"].astype(np.float64)
+    a, s = 1 + 2 * e, np.sqrt(1 + 2 * dl)
+    det = a - s * s                                   # 2 (eps - delta) > 0
+    mm = 1.0 / (1000.0 * m["vp"].astype(np.float64)) ** 2
+    st = [x.astype(np.float64) for x in synth.random_state(4, o.shape, seed=17, sigma_cells=1.2)]
+    p0, p1, r0, r1 = st[0], st[1], st[2], st[3]
+
+    def energy(p0, p1, r0, r1):
+        dp, dr = p1 - p0, r1 - r0
+        kin = np.sum(mm * (dp * dp - 2 * s * dp * dr + a * dr * dr) / det)   # du^T m C^{-1} du
+        Lp, Lr = o.tti_apply_L(p0, r0)                                     # C H u^n
+        Hp, Hr = (Lp - s * Lr) / det, (a * Lr - s * Lp) / det
+        return kin - dt * dt * np.sum(p1 * Hp + r1 * Hr)
+
+    E = []
+    for _ in range(150):
+        E.append(energy(p0, p1, r0, r1))
+        p0, p1, r0, r1 = o.tti_run_d(p0, p1, r0, r1, 1)
+    E = np.array(E)
+    assert E[0] > 0
+    assert np.max(np.abs(E - E[0])) <= 1e-11 * abs(E[0]), (E.min(), E.max())
