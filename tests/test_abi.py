@@ -115,3 +115,43 @@ def test_batch_argument_checks_need_no_gpu(libpath):
     rc = L.prop_gradient_batch(handles, 2, arr, arr, ints, arr, ints, arr, arr, None, 0)
     assert rc == wp.PROP_EINVAL
     assert b"shot handle 0 is NULL" in L.prop_last_error(None)
+
+
+def test_create_rejects_bad_descriptors_without_gpu(libpath):
+    """prop_create validates the descriptor before any device call: each
+    bad field returns PROP_EINVAL with a message naming it, no handle."""
+    import paper_2004_10519_gb300 as wp
+    L = wp.lib()
+    dummy = (C.c_float * 1)()
+    models = (C.c_void_p * 5)(*[C.cast(dummy, C.c_void_p)] * 5)
+
+    def desc(**kw):
+        d = dict(kind=wp.PROP_TTI, nx=8, ny=8, nz=8, nbl=2, h=10.0, space_order=8, nt=10, dt=0.0, vdamp=0.0,
+                 snap_mode=0, ckpt_interval=0, check_nan=0, tti_operator=0)
+        d.update(kw)
+        return wp.PropDesc(**d)
+
+    cases = [(dict(kind=7), b"kind must be"),
+             (dict(kind=wp.PROP_ELASTIC2D, ny=3), b"ny = 1"),
+             (dict(tti_operator=2), b"tti_operator"),
+             (dict(kind=wp.PROP_ELASTIC, tti_operator=1), b"tti_operator"),
+             (dict(nx=0), b"grid sizes"),
+             (dict(nbl=-1), b"nbl"),
+             (dict(h=0.0), b"h must be"),
+             (dict(h=float("nan")), b"h must be"),
+             (dict(space_order=6), b"space_order"),
+             (dict(nt=1), b"nt must be"),
+             (dict(snap_mode=4), b"snap_mode"),
+             (dict(ckpt_interval=-2), b"ckpt_interval"),
+             (dict(nx=2048, ny=2048, nz=1024), b"2^32")]
+    for kw, msg in cases:
+        h = C.c_void_p()
+        rc = L.prop_create(C.byref(desc(**kw)), models, None, C.byref(h))
+        assert rc == wp.PROP_EINVAL, kw
+        assert h.value is None, kw
+        assert msg in L.prop_last_error(None), (kw, L.prop_last_error(None))
+    h = C.c_void_p()
+    assert L.prop_create(C.byref(desc()), None, None, C.byref(h)) == wp.PROP_EINVAL
+    assert b"model is NULL" in L.prop_last_error(None)
+    assert L.prop_create(None, models, None, C.byref(h)) == wp.PROP_EINVAL
+    assert L.prop_create(C.byref(desc()), models, None, None) == wp.PROP_EINVAL
