@@ -13,6 +13,10 @@
 // queues of partial sums (H0 and Hz at planes x .. x+2M) as each plane's
 // fluxes arrive, instead of holding four queues of inputs: half the queue
 // registers for the same multiply-adds.
+// Gradients w.r.t. eps and delta image the coupling with pass 2 in a mode
+// without the step; the tilt/azimuth term adds, to the centred form's, the
+// half-point products of the staggered diagonal terms (sp_half_products,
+// tti_axis_image_sp).
 #include "tma.cuh"
 
 namespace {
