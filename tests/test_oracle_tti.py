@@ -568,3 +568,48 @@ def test_energy_conservation_undamped(op):
     E = np.array(E)
     assert E[0] > 0
     assert np.max(np.abs(E - E[0])) <= 1e-11 * abs(E[0]), (E.min(), E.max())
+
+
+@pytest.mark.parametrize("which", ["theta", "phi"])
+def test_taylor_tilt_azimuth_staggered_pair_to_the_faces(which):
+    """The staggered-pair tilt/azimuth gradient with a perturbation that
+    reaches the physical faces, so the edge-replicated layer values change
+    up to the last computational node, where the half-point average's
+    partner is clamped (weight 1 instead of 1/2) and the first node has no
+    half point below it: the Taylor remainder stays second order."""
+    p = _small_problem(so=4, nt=60, nbl=0)           # the faces are the grid's ends
+    p.vdamp = 2500.0 * math.sqrt(1.4)
+    p.tti_op = 1
+    keys = ("vp", "eps", "delta", "theta", "phi")
+    dobs = oracle.Problem(p).forward()
+    base = dict(p.model)
+    base["theta"] = (base["theta"].astype(np.float64) + 0.15).astype(np.float32)
+    idx = {"theta": 3, "phi": 4}[which]
+
+    def J_of(field):
+        mm = dict(base)
+        mm[which] = field.astype(np.float32)
+        o = oracle.Problem(p, model=[mm[k] for k in keys])
+        return 0.5 * np.sum((o.forward() - dobs) ** 2), o
+
+    J0, o0 = J_of(base[which].astype(np.float64))
+    f0 = base[which].astype(np.float64)
+    g5, _ = o0.gradient_aniso(dobs)
+    # weight the faces: the perturbation is largest on the outermost cells
+    n = f0.shape[0]
+    edge = np.zeros(f0.shape)
+    for ax in range(3):
+        sl = [slice(None)] * 3
+        sl[ax] = slice(0, 1)
+        edge[tuple(sl)] = 1.0
+        sl[ax] = slice(n - 1, n)
+        edge[tuple(sl)] = 1.0
+    d = 0.3 * edge * synth.perturbation(f0.shape, 0, 19).astype(np.float64)
+    lin = float(np.sum(g5[idx] * d))
+    assert abs(lin) > 0
+    e2 = []
+    for hh in (0.5, 0.25, 0.125, 0.0625, 0.03125):
+        Jh, _ = J_of(f0 + hh * d)
+        e2.append(abs(Jh - J0 - hh * lin))
+    slopes = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(e2) - 1)]
+    assert all(abs(s - 2.0) < 0.15 for s in slopes), slopes
