@@ -39,6 +39,7 @@ struct FDW {
 // Sparse-point tables (device).  Record: nrec x 8 (index, weight) pairs.
 // Inject: unique grid cells with CSR lists of (trace, weight).
 struct SparseDev {
+    void *blk = nullptr;     // one device block holding the six tables below
     int n = 0;               // points
     long long *rec_idx = nullptr;
     float *rec_w = nullptr;  // [n*8]
@@ -69,7 +70,8 @@ struct prop_s {
     // elastic adjoint: 6 (stress-like) + 3 (weighted velocity) + 6 gradient
     // products (edges xy xz yz, faces x y z)
     float *tmp[20] = {};
-    int *flag = nullptr;     // device: bit0 NaN/Inf seen
+    int *flag = nullptr;     // device: bit0 NaN/Inf seen, bit1 a bounded wait expired
+    double *sumsq = nullptr; // device: partial sums of k_sumsq (kept between calls)
     float *tab = nullptr;    // per-axis absorbing-layer tables (GridDev::tab)
     int xchunk = 8;          // planes per CTA of the x-streaming stencil kernels
     // saved forward run for prop_backward
@@ -167,6 +169,17 @@ int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
 int el_step_adjoint_u(prop_s *P, float *const *S);
 
 // sparse ops (sparse.cu)
+// Host-side trilinear tables of n points (metres, origin at the first
+// physical point): per point 8 (index, weight) pairs, zero weights dropped
+// (rec_*), and the unique cells with CSR lists of (trace, weight) (cells, ptr,
+// trs, ws) for injection.  trace_of_point == NULL: trace i for point i.
+struct SpHost {
+    std::vector<long long> ridx, cells;
+    std::vector<float> rw, ws;
+    std::vector<int> ptr, trs;
+};
+int sp_host_tables(prop_s *P, const float *xyz_host, int n, const int *trace_of_point, SpHost &T);
+// device copy of the tables in one allocation (wp_malloc); sp_free releases it
 int sp_build(prop_s *P, const float *xyz_host, int n, const int *trace_of_point, SparseDev *S);
 void sp_free(SparseDev *S);
 // record: out[t*n + i] = scale * sum_c w * (f0 + f1 + f2)[idx]   (f1, f2 may be NULL)
@@ -194,7 +207,9 @@ void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode);
 // edge-replication extension); s1, s2: scratch of N floats each
 void k_fold(prop_s *P, const float *comp, float *phys, float *s1, float *s2);
 void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long n);
-double k_sumsq_host(prop_s *P, const float *a, long long n);
+// sum of squares of n device floats, summed in FP64 on the host; errors of
+// the allocation, launch or copy are returned (the handle keeps the buffer)
+int k_sumsq(prop_s *P, const float *a, long long n, double *out);
 void k_tti_zeta(prop_s *P, const float *lp, const float *lr, float *zp, float *zr);
 // out = s / a (pointwise, n values)
 void k_ratio(prop_s *P, const float *a, float s, float *out, long long n);
@@ -232,6 +247,12 @@ int stencil_xchunk(const GridDev &g, int sms);
 
 // error helpers
 int wp_fail(prop_s *P, int code, const std::string &msg);
+// every device allocation of the library (WAVEPROP_FAULT=alloc: fails)
+int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what);
+// status of the device error word read back after a call: bit 1 (a bounded
+// device wait expired) -> PROP_ETIMEOUT; bit 0 (NaN/Inf seen) ->
+// PROP_EUNSTABLE when check_nan is set; else PROP_OK
+int wp_flag_status(prop_s *P, int flag);
 int wp_cuda(prop_s *P, cudaError_t e, const char *what);
 #define WP_CK(P, call)                                          \
     do {                                                        \

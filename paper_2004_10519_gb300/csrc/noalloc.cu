@@ -13,13 +13,17 @@
 // The array belongs to this library's code on each GPU: it is reserved on a
 // device when that device loads the module holding it (with CUDA's default
 // lazy module loading, at the first call of this entry point there) and it
-// stays reserved until the process exits.  The first call on a device looks
-// up the array's device address (cudaGetSymbolAddress with that device
-// current) and caches it; that first call should come before any stream
-// capture is started on that device.  All calls share the array and it keeps
-// the contents of the last call: everything that must start at zero is
-// cleared on every call, and calls that overlap on the GPU (concurrent
-// streams, or threads calling at once) race on the same memory.
+// stays reserved until the process exits.  Each call looks up the array's
+// device address (cudaGetSymbolAddress with the device current) unless the
+// stream is being captured, in which case the address found by the last
+// uncaptured call on that device is used: make one call on a device before
+// any stream capture starts there.  A device reset (cudaDeviceReset) unloads
+// the module; the next uncaptured call finds the new address.  All calls
+// share the array and it keeps the contents of the last call: everything
+// that must start at zero is cleared on every call, and calls that overlap on
+// the GPU (concurrent streams, or threads calling at once) race on the same
+// memory.  A call that fails after queuing work waits for that work before
+// it returns, so a failed call never leaves kernels running on the array.
 #include "internal.h"
 
 #include <algorithm>
@@ -42,16 +46,33 @@ int scratch_address(prop_s *P, unsigned char **out)
     int dev = 0;
     WP_CK(P, cudaGetDevice(&dev));
     if (dev < 0 || dev >= 256) return wp_fail(P, PROP_EINVAL, "device ordinal out of range");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    WP_CK(P, cudaStreamIsCapturing(P->stream, &cap));
     std::lock_guard<std::mutex> lk(g_mtx);
-    if (!g_addr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return wp_cuda(P, e, "cudaGetSymbolAddress(no-alloc scratch)");
         g_addr[dev] = p;
+    } else if (!g_addr[dev]) {
+        return wp_fail(P, PROP_EINVAL, "first prop_forward_noalloc call on a device must not be captured");
     }
     *out = (unsigned char *)g_addr[dev];
     return PROP_OK;
 }
+
+// waits for the queued work of a failed call (its status is not reported)
+struct SyncOnExit {
+    cudaStream_t s;
+    bool armed = false;
+    ~SyncOnExit()
+    {
+        if (armed) {
+            cudaStreamSynchronize(s);
+            cudaGetLastError();
+        }
+    }
+};
 
 // sequential sub-allocation of the static array (base == nullptr: sizing pass)
 struct Carver {
@@ -66,58 +87,8 @@ struct Carver {
     }
 };
 
-// trilinear tables (same layout as the library's own sparse tables)
-struct HostTables {
-    std::vector<long long> ridx, cells;
-    std::vector<float> rw, ws;
-    std::vector<int> ptr, trs;
-};
-
-int host_tables(prop_s *P, const float *xyz, int n, HostTables &T)
-{
-    const GridDev &g = P->g;
-    T.ridx.assign((size_t)n * 8, 0);
-    T.rw.assign((size_t)n * 8, 0.f);
-    std::vector<std::tuple<long long, int, float>> ent;
-    const int dims[3] = {g.NX, g.NY, g.NZ};
-    for (int i = 0; i < n; i++) {
-        double s[3], f[3];
-        int i0[3];
-        for (int a = 0; a < 3; a++) {
-            s[a] = (double)xyz[3 * i + a] / (double)g.h + (double)g.nbl;
-            if (!(s[a] >= 0.0) || s[a] > (double)(dims[a] - 1))
-                return wp_fail(P, PROP_EINVAL, "sparse point " + std::to_string(i) + " outside the grid");
-            i0[a] = (int)std::floor(s[a]);
-            f[a] = s[a] - i0[a];
-        }
-        int c = 0;
-        for (int a = 0; a < 2; a++)
-            for (int b = 0; b < 2; b++)
-                for (int d = 0; d < 2; d++, c++) {
-                    const double wt = (a ? f[0] : 1 - f[0]) * (b ? f[1] : 1 - f[1]) * (d ? f[2] : 1 - f[2]);
-                    if (wt == 0.0) continue;
-                    const long long q = ((long long)(i0[0] + a) * g.NY + (i0[1] + b)) * g.NZ + (i0[2] + d);
-                    T.ridx[8 * (size_t)i + c] = q;
-                    T.rw[8 * (size_t)i + c] = (float)wt;
-                    ent.emplace_back(q, i, (float)wt);
-                }
-    }
-    std::stable_sort(ent.begin(), ent.end(),
-                     [](const auto &A, const auto &B) { return std::get<0>(A) < std::get<0>(B); });
-    for (size_t e = 0; e < ent.size(); e++) {
-        if (e == 0 || std::get<0>(ent[e]) != std::get<0>(ent[e - 1])) {
-            T.cells.push_back(std::get<0>(ent[e]));
-            T.ptr.push_back((int)e);
-        }
-        T.trs.push_back(std::get<1>(ent[e]));
-        T.ws.push_back(std::get<2>(ent[e]));
-    }
-    T.ptr.push_back((int)ent.size());
-    return PROP_OK;
-}
-
 // carve device space for one table set and (if placed) copy it in
-int place_tables(prop_s *P, Carver &C, const HostTables &T, int n, SparseDev &S)
+int place_tables(prop_s *P, Carver &C, const SpHost &T, int n, SparseDev &S)
 {
     S.n = n;
     S.ncell = (int)T.cells.size();
@@ -157,6 +128,26 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     const int nf = tti ? 5 : 3;
     for (int i = 0; i < nf; i++)
         if (!model[i]) return wp_fail(P, PROP_EINVAL, "model array is NULL");
+    // sizes checked before any product can overflow: each computational axis,
+    // then the point count (< 2^32, 32-bit offsets in the kernels), then one
+    // field's bytes and every field's bytes against the static array
+    const long long ax[3] = {(long long)d->nx + 2LL * d->nbl, (long long)d->ny + 2LL * d->nbl,
+                             (long long)d->nz + 2LL * d->nbl};
+    for (long long a : ax)
+        if (a > (long long)WP_NOALLOC_BYTES)
+            return wp_fail(P, PROP_EINVAL, "grid axis too long for prop_forward_noalloc");
+    const unsigned long long nxy = (unsigned long long)ax[0] * (unsigned long long)ax[1];
+    if (nxy >= (1ull << 32) || nxy * (unsigned long long)ax[2] >= (1ull << 32))
+        return wp_fail(P, PROP_EINVAL, "computational grid above 2^32 - 1 points");
+    const unsigned long long nfield = (tti ? 7 + 4 + 6 : 3 + 9);
+    const unsigned long long fbytes = nxy * (unsigned long long)ax[2] * sizeof(float);
+    if (fbytes > WP_NOALLOC_BYTES || fbytes * nfield > WP_NOALLOC_BYTES) {
+        char buf[200];
+        snprintf(buf, sizeof buf,
+                 "problem needs more than %.1f MiB of device scratch; prop_forward_noalloc holds %u MiB",
+                 fbytes * (double)nfield / 1048576.0, WP_NOALLOC_BYTES >> 20);
+        return wp_fail(P, PROP_EINVAL, buf);
+    }
     P->d = *d;
     P->M = so / 2;
     GridDev &g = P->g;
@@ -172,9 +163,9 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     std::vector<float> hs((size_t)nsrc * 3), hr((size_t)nrec * 3);
     WP_CK(P, cudaMemcpy(hs.data(), src, hs.size() * 4, cudaMemcpyDefault));
     WP_CK(P, cudaMemcpy(hr.data(), rec, hr.size() * 4, cudaMemcpyDefault));
-    HostTables TS, TR;
-    if (int rc = host_tables(P, hs.data(), nsrc, TS)) return rc;
-    if (int rc = host_tables(P, hr.data(), nrec, TR)) return rc;
+    SpHost TS, TR;
+    if (int rc = sp_host_tables(P, hs.data(), nsrc, nullptr, TS)) return rc;
+    if (int rc = sp_host_tables(P, hr.data(), nrec, nullptr, TR)) return rc;
     SparseDev S, R;
     float *phys, *wav, *stage, *out, *tabd, *fields[20] = {};
     int *flag;
@@ -241,6 +232,8 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     // ---- place everything in the static array -----------------------------
     unsigned char *base = nullptr;
     if (int rc = scratch_address(P, &base)) return rc;
+    SyncOnExit guard{P->stream};
+    guard.armed = true;               // from here on work may be queued
     Carver C{base};
     if (int rc = layout(C)) return rc;
     int k = 0;
@@ -293,13 +286,11 @@ int run(prop_s *P, const prop_desc *d, const float *const *model, const float *w
     sp_transpose(P, stage, out, nrec, nt);
     WP_CK(P, cudaMemcpyAsync(traces, out, (size_t)nrec * nt * sizeof(float), cudaMemcpyDefault, P->stream));
     WP_CK(P, cudaStreamSynchronize(P->stream));
+    guard.armed = false;
     WP_CK(P, cudaGetLastError());
-    if (d->check_nan) {
-        int f = 0;
-        WP_CK(P, cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
-        if (f) return wp_fail(P, PROP_EUNSTABLE, "NaN or Inf in the wavefield");
-    }
-    return PROP_OK;
+    int f = 0;
+    WP_CK(P, cudaMemcpy(&f, flag, sizeof(int), cudaMemcpyDeviceToHost));
+    return wp_flag_status(P, f);
 }
 
 }  // namespace

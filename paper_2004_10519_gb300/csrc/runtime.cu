@@ -38,9 +38,10 @@ int wp_cuda(prop_s *P, cudaError_t e, const char *what)
     return wp_fail(P, PROP_ECUDA, m);
 }
 
-// All device allocations of the library go through here.  WAVEPROP_FAULT=alloc
-// makes every allocation fail (host-side fault injection for tests).
-static int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what)
+// All device allocations of the library go through here (prop_forward_noalloc
+// makes none).  WAVEPROP_FAULT=alloc makes every allocation fail (host-side
+// fault injection for tests).
+int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what)
 {
     *p = nullptr;
     const char *f = getenv("WAVEPROP_FAULT");
@@ -315,6 +316,7 @@ static void free_all(prop_s *P)
     for (auto &a : P->ast) cudaFree(a);
     for (auto &a : P->tmp) cudaFree(a);
     cudaFree(P->flag);
+    cudaFree(P->sumsq);
     cudaFree(P->tab);
     free_snaps(P);
     for (auto e : P->prof_ev) cudaEventDestroy(e);
@@ -611,6 +613,11 @@ static int finish(prop_s *P)
     int f = 0;
     WP_CK(P, cudaMemcpy(&f, P->flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (f) WP_CK(P, cudaMemset(P->flag, 0, sizeof(int)));
+    return wp_flag_status(P, f);
+}
+
+int wp_flag_status(prop_s *P, int f)
+{
     if (f & 2) return wp_fail(P, PROP_ETIMEOUT, "a bounded device-side wait expired (TMA pipeline)");
     if (P->d.check_nan && (f & 1)) return wp_fail(P, PROP_EUNSTABLE, "NaN or Inf in the wavefield");
     return PROP_OK;
@@ -1468,7 +1475,12 @@ extern "C" int prop_gradient(prop_t *P, const float *wavelet, const float *src_x
     rc = dev_in(P, d_obs, (size_t)nrec * nt, obs, &dobs);
     if (rc) { free_snaps(P); return rc; }
     k_axpy_sq(P, (const float *)tr.p, dobs, (float *)tr.p, (long long)nrec * nt);
-    if (misfit) *misfit = 0.5 * k_sumsq_host(P, (const float *)tr.p, (long long)nrec * nt);
+    if (misfit) {
+        double ss = 0.0;
+        rc = k_sumsq(P, (const float *)tr.p, (long long)nrec * nt, &ss);
+        if (rc) { free_snaps(P); return rc; }
+        *misfit = 0.5 * ss;
+    }
     rc = backward_impl(P, (const float *)tr.p, grad, nullptr, nullptr);
     free_snaps(P);
     return rc;

@@ -304,11 +304,12 @@ __global__ void dequant_kernel(const uint16_t *__restrict__ in, long long n, con
 }  // namespace
 
 // ---------------------------------------------------------------------------
-int sp_build(prop_s *P, const float *xyz, int n, const int *trace_of_point, SparseDev *S)
+int sp_host_tables(prop_s *P, const float *xyz, int n, const int *trace_of_point, SpHost &T)
 {
     const GridDev &g = P->g;
-    std::vector<long long> ridx((size_t)n * 8, 0);
-    std::vector<float> rw((size_t)n * 8, 0.f);
+    T = SpHost{};
+    T.ridx.assign((size_t)n * 8, 0);
+    T.rw.assign((size_t)n * 8, 0.f);
     std::vector<std::tuple<long long, int, float>> ent;
     ent.reserve((size_t)n * 8);
     const int dims[3] = {g.NX, g.NY, g.NZ};
@@ -329,49 +330,64 @@ int sp_build(prop_s *P, const float *xyz, int n, const int *trace_of_point, Spar
                     const double wt = (a ? f[0] : 1 - f[0]) * (b ? f[1] : 1 - f[1]) * (d ? f[2] : 1 - f[2]);
                     if (wt == 0.0) continue;
                     const long long q = ((long long)(i0[0] + a) * g.NY + (i0[1] + b)) * g.NZ + (i0[2] + d);
-                    ridx[8 * (size_t)i + c] = q;
-                    rw[8 * (size_t)i + c] = (float)wt;
+                    T.ridx[8 * (size_t)i + c] = q;
+                    T.rw[8 * (size_t)i + c] = (float)wt;
                     ent.emplace_back(q, trace_of_point ? trace_of_point[i] : i, (float)wt);
                 }
     }
     std::stable_sort(ent.begin(), ent.end(),
                      [](const auto &A, const auto &B) { return std::get<0>(A) < std::get<0>(B); });
-    std::vector<long long> cells;
-    std::vector<int> ptr, trs;
-    std::vector<float> ws;
     for (size_t e = 0; e < ent.size(); e++) {
         if (e == 0 || std::get<0>(ent[e]) != std::get<0>(ent[e - 1])) {
-            cells.push_back(std::get<0>(ent[e]));
-            ptr.push_back((int)e);
+            T.cells.push_back(std::get<0>(ent[e]));
+            T.ptr.push_back((int)e);
         }
-        trs.push_back(std::get<1>(ent[e]));
-        ws.push_back(std::get<2>(ent[e]));
+        T.trs.push_back(std::get<1>(ent[e]));
+        T.ws.push_back(std::get<2>(ent[e]));
     }
-    ptr.push_back((int)ent.size());
+    T.ptr.push_back((int)ent.size());
+    return PROP_OK;
+}
+
+int sp_build(prop_s *P, const float *xyz, int n, const int *trace_of_point, SparseDev *S)
+{
+    SpHost T;
+    WP_TRY(sp_host_tables(P, xyz, n, trace_of_point, T));
+    // one block, each table 256-byte aligned
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t b_ri = T.ridx.size() * sizeof(long long), b_rw = T.rw.size() * sizeof(float),
+                 b_c = std::max<size_t>(1, T.cells.size()) * sizeof(long long), b_p = T.ptr.size() * sizeof(int),
+                 b_t = std::max<size_t>(1, T.trs.size()) * sizeof(int),
+                 b_w = std::max<size_t>(1, T.ws.size()) * sizeof(float);
+    const size_t total = up(b_ri) + up(b_rw) + up(b_c) + up(b_p) + up(b_t) + up(b_w);
+    sp_free(S);
+    WP_TRY(wp_malloc(P, &S->blk, total, "sparse-point tables"));
+    unsigned char *q = (unsigned char *)S->blk;
+    S->rec_idx = (long long *)q; q += up(b_ri);
+    S->rec_w = (float *)q; q += up(b_rw);
+    S->cell = (long long *)q; q += up(b_c);
+    S->cell_ptr = (int *)q; q += up(b_p);
+    S->ent_trace = (int *)q; q += up(b_t);
+    S->ent_w = (float *)q;
     S->n = n;
-    S->ncell = (int)cells.size();
-    WP_CK(P, cudaMalloc(&S->rec_idx, sizeof(long long) * ridx.size()));
-    WP_CK(P, cudaMalloc(&S->rec_w, sizeof(float) * rw.size()));
-    WP_CK(P, cudaMalloc(&S->cell, sizeof(long long) * std::max<size_t>(1, cells.size())));
-    WP_CK(P, cudaMalloc(&S->cell_ptr, sizeof(int) * ptr.size()));
-    WP_CK(P, cudaMalloc(&S->ent_trace, sizeof(int) * std::max<size_t>(1, trs.size())));
-    WP_CK(P, cudaMalloc(&S->ent_w, sizeof(float) * std::max<size_t>(1, ws.size())));
-    WP_CK(P, cudaMemcpyAsync(S->rec_idx, ridx.data(), sizeof(long long) * ridx.size(), cudaMemcpyHostToDevice, P->stream));
-    WP_CK(P, cudaMemcpyAsync(S->rec_w, rw.data(), sizeof(float) * rw.size(), cudaMemcpyHostToDevice, P->stream));
-    if (!cells.empty()) {
-        WP_CK(P, cudaMemcpyAsync(S->cell, cells.data(), sizeof(long long) * cells.size(), cudaMemcpyHostToDevice, P->stream));
-        WP_CK(P, cudaMemcpyAsync(S->ent_trace, trs.data(), sizeof(int) * trs.size(), cudaMemcpyHostToDevice, P->stream));
-        WP_CK(P, cudaMemcpyAsync(S->ent_w, ws.data(), sizeof(float) * ws.size(), cudaMemcpyHostToDevice, P->stream));
-    }
-    WP_CK(P, cudaMemcpyAsync(S->cell_ptr, ptr.data(), sizeof(int) * ptr.size(), cudaMemcpyHostToDevice, P->stream));
-    WP_CK(P, cudaStreamSynchronize(P->stream));   // host vectors go out of scope
+    S->ncell = (int)T.cells.size();
+    auto cp = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (bytes) WP_CK(P, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, P->stream));
+        return PROP_OK;
+    };
+    WP_TRY(cp(S->rec_idx, T.ridx.data(), b_ri));
+    WP_TRY(cp(S->rec_w, T.rw.data(), b_rw));
+    WP_TRY(cp(S->cell, T.cells.data(), T.cells.size() * sizeof(long long)));
+    WP_TRY(cp(S->cell_ptr, T.ptr.data(), b_p));
+    WP_TRY(cp(S->ent_trace, T.trs.data(), T.trs.size() * sizeof(int)));
+    WP_TRY(cp(S->ent_w, T.ws.data(), T.ws.size() * sizeof(float)));
+    WP_CK(P, cudaStreamSynchronize(P->stream));   // the host tables go out of scope
     return PROP_OK;
 }
 
 void sp_free(SparseDev *S)
 {
-    cudaFree(S->rec_idx); cudaFree(S->rec_w); cudaFree(S->cell); cudaFree(S->cell_ptr);
-    cudaFree(S->ent_trace); cudaFree(S->ent_w);
+    if (S->blk) cudaFree(S->blk);
     *S = SparseDev{};
 }
 
@@ -468,20 +484,21 @@ void k_axpy_sq(prop_s *P, const float *a, const float *b, float *out, long long 
     P->kern_launches++;
 }
 
-double k_sumsq_host(prop_s *P, const float *a, long long n)
+int k_sumsq(prop_s *P, const float *a, long long n, double *out)
 {
     const int nb = 1024;
-    double *part = nullptr;
-    if (cudaMalloc(&part, sizeof(double) * nb) != cudaSuccess) return NAN;
-    sumsq_partial<<<nb, NB, 0, P->stream>>>(a, n, part);
+    *out = 0.0;
+    if (!P->sumsq) WP_TRY(wp_malloc(P, (void **)&P->sumsq, sizeof(double) * nb, "misfit partial sums"));
+    sumsq_partial<<<nb, NB, 0, P->stream>>>(a, n, P->sumsq);
     P->kern_launches++;
+    WP_CK(P, cudaGetLastError());
     std::vector<double> h(nb);
-    cudaMemcpyAsync(h.data(), part, sizeof(double) * nb, cudaMemcpyDeviceToHost, P->stream);
-    cudaStreamSynchronize(P->stream);
-    cudaFree(part);
+    WP_CK(P, cudaMemcpyAsync(h.data(), P->sumsq, sizeof(double) * nb, cudaMemcpyDeviceToHost, P->stream));
+    WP_CK(P, cudaStreamSynchronize(P->stream));
     double s = 0.0;
     for (double v : h) s += v;
-    return s;
+    *out = s;
+    return PROP_OK;
 }
 
 void k_snap_encode(prop_s *P, const float *in, long long n, uint16_t *out, float *scale_dev,

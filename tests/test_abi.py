@@ -155,3 +155,31 @@ def test_create_rejects_bad_descriptors_without_gpu(libpath):
     assert b"model is NULL" in L.prop_last_error(None)
     assert L.prop_create(None, models, None, C.byref(h)) == wp.PROP_EINVAL
     assert L.prop_create(C.byref(desc()), models, None, None) == wp.PROP_EINVAL
+
+
+def test_noalloc_rejects_huge_grids_without_gpu(libpath):
+    """prop_forward_noalloc checks every size before it multiplies them or
+    touches the device: axes whose product would wrap, grids of 2^32 points
+    or more, and grids whose fields exceed the static array all return
+    PROP_EINVAL (no CUDA call is made, so this runs without a GPU)."""
+    import paper_2004_10519_gb300 as wp
+    L = wp.lib()
+    vp = C.c_void_p
+    L.prop_forward_noalloc.argtypes = [C.POINTER(wp.PropDesc), C.POINTER(vp), vp, vp, C.c_int,
+                                       vp, C.c_int, vp, vp]
+    buf = (C.c_float * 16)()
+    p = C.cast(buf, vp)
+    models = (vp * 5)(*[p] * 5)
+    big = 2 ** 31 - 100
+    cases = [((big, big, big, 40), b"grid axis too long"),
+             ((2 ** 20, 2 ** 20, 8, 0), b"2^32"),
+             ((65536, 65536, 2, 0), b"2^32"),
+             ((2048, 2048, 1024, 0), b"2^32"),
+             ((200, 200, 200, 10), b"MiB"),
+             ((1000, 1000, 10, 0), b"MiB")]
+    for kind in (wp.PROP_TTI, wp.PROP_ELASTIC):
+        for (nx, ny, nz, nbl), msg in cases:
+            d = wp.PropDesc(kind, nx, ny, nz, nbl, 10.0, 8, 10, 0.0, 0.0, 0, 0, 0, 0)
+            rc = L.prop_forward_noalloc(C.byref(d), models, p, p, 1, p, 1, p, None)
+            assert rc == wp.PROP_EINVAL, (kind, nx, ny, nz)
+            assert msg in L.prop_last_error(None), (kind, nx, L.prop_last_error(None))
