@@ -63,7 +63,10 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 200 ms) while the context is open.  Samples
+    are stamped on arrival; ``region()`` brackets a timed region, and the
+    summary covers only the samples inside the regions (all samples if none
+    was marked)."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -73,6 +76,7 @@ class Clocks:
         self.gpu = gpu
         self.proc = None
         self.lines = []
+        self.regions = []
 
     def __enter__(self):
         try:
@@ -88,7 +92,7 @@ class Clocks:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -98,10 +102,27 @@ class Clocks:
             except Exception:
                 self.proc.kill()
 
+    class _Region:
+        def __init__(self, clk):
+            self.clk = clk
+
+        def __enter__(self):
+            self.t0 = time.perf_counter()
+            return self
+
+        def __exit__(self, *a):
+            # the sample describing the last 200 ms arrives up to ~0.3 s later
+            self.clk.regions.append((self.t0, time.perf_counter() + 0.3))
+
+    def region(self):
+        return Clocks._Region(self)
+
     def summary(self):
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
+            if self.regions and not any(a <= t <= b for a, b in self.regions):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -117,6 +138,18 @@ class Clocks:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+_CLK = None
+
+
+def timed_region():
+    """Bracket a timed region of a secondary measurement for the clock record
+    (a no-op context when no sampler runs)."""
+    if _CLK is None:
+        import contextlib
+        return contextlib.nullcontext()
+    return _CLK.region()
 
 
 def elastic_workload(small=False):
@@ -216,20 +249,26 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
         prop.step(5, adjoint=adj)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        prop.step(steps, adjoint=adj)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / steps
-        prop.profile(True)
-        prop.step(10, adjoint=adj)
-        kms, kn = prop.kernel_stats(kid)
-        prop.profile(False)
+        with timed_region():
+            e0.record()
+            prop.step(steps, adjoint=adj)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            prop.profile(True)
+            prop.step(10, adjoint=adj)
+            kms, kn = prop.kernel_stats(kid)
+            prop.profile(False)
+        t = kms / max(kn, 1) / 1e3
+        hbm, src_peak = peaks()
+        ach = ALG_BYTES["tti"] * N / t / 1e9
         out[key] = {"gpts_per_s": N / (ms / 1e3) / 1e9, "ms_per_step": ms,
-                    "kernel_ms_per_step": kms / max(kn, 1),
-                    "alg_gbs": ALG_BYTES["tti"] * N / (kms / max(kn, 1) / 1e3) / 1e9,
-                    "alg_tflops": FLOP_PER_PT["tti_sp" if tti_operator else "tti"] * N / (kms / max(kn, 1) / 1e3)
-                    / 1e12}
+                    "kernel_ms_per_step": t * 1e3,
+                    "alg_gbs": ach,
+                    "alg_tflops": FLOP_PER_PT["tti_sp" if tti_operator else "tti"] * N / t / 1e12,
+                    "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                                 "frac": ach / hbm, "peak_source": src_peak,
+                                 "alg_bytes_per_pt": ALG_BYTES["tti"], "launch_ms": t * 1e3}}
     prop.close()
     out["grid"] = list(prop.grid)
     out["space_order"] = so
@@ -255,15 +294,16 @@ def acoustic_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40
     prop.step(5)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    prop.step(steps)
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    prop.profile(True)
-    prop.step(10)
-    kms, kn = prop.kernel_stats(wp.K_AC_STEP)
-    prop.profile(False)
+    with timed_region():
+        e0.record()
+        prop.step(steps)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        prop.profile(True)
+        prop.step(10)
+        kms, kn = prop.kernel_stats(wp.K_AC_STEP)
+        prop.profile(False)
     t = kms / max(kn, 1) / 1e3
     out["acoustic_forward"] = {"gpts_per_s": N / (ms / 1e3) / 1e9, "ms_per_step": ms,
                                "kernel_ms_per_step": t * 1e3,
@@ -290,14 +330,15 @@ def elastic2d_throughput(wp, torch, dev, small=False):
     w, s_, r = to(p.wavelet), to(p.src), to(p.rec)
     prop.forward(w, s_, r)                                  # warm-up
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    prop.forward(w, s_, r)
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
-    prop.profile(True)
-    prop.forward(w, s_, r)
-    kms, kn = prop.kernel_stats(wp.K_EL_FWD)
-    prop.profile(False)
+    with timed_region():
+        t0 = time.perf_counter()
+        prop.forward(w, s_, r)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        prop.profile(True)
+        prop.forward(w, s_, r)
+        kms, kn = prop.kernel_stats(wp.K_EL_FWD)
+        prop.profile(False)
     N = int(np.prod(prop.grid))
     prop.close()
     t_step = kms / max(kn, 1) / 1e3
@@ -329,12 +370,13 @@ def rtm_shots_per_hour(wp, torch, dev, nshots, nt, small=False):
     stack = torch.zeros((gx, gy, nz), dtype=torch.float32, device=dev)
     props[0].gradient(wav[0], src[0], rec[0], obs[0])        # warm-up
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    grads, _ = wp.gradient_batch(props, wav, src, rec, obs)
-    for p, g, (_, _, off) in zip(props, grads, shots):
-        p.stack_image(g, stack, off)
-    torch.cuda.synchronize()
-    sec = time.perf_counter() - t0
+    with timed_region():
+        t0 = time.perf_counter()
+        grads, _ = wp.gradient_batch(props, wav, src, rec, obs)
+        for p, g, (_, _, off) in zip(props, grads, shots):
+            p.stack_image(g, stack, off)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
     npts = sum(int(np.prod(p.grid)) for p in props)
     for p in props:
         p.close()
@@ -365,10 +407,11 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
         try:
             g, J = prop.gradient(wav, src, rec, d_obs)          # warm-up + result
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g, J = prop.gradient(wav, src, rec, d_obs)
-            torch.cuda.synchronize()
-            s = time.perf_counter() - t0
+            with timed_region():
+                t0 = time.perf_counter()
+                g, J = prop.gradient(wav, src, rec, d_obs)
+                torch.cuda.synchronize()
+                s = time.perf_counter() - t0
             gd = g.double()
             if ref is None:
                 ref = gd
@@ -383,10 +426,11 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
     try:
         prop.gradient_aniso(wav, src, rec, d_obs)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, J = prop.gradient_aniso(wav, src, rec, d_obs)
-        torch.cuda.synchronize()
-        s = time.perf_counter() - t0
+        with timed_region():
+            t0 = time.perf_counter()
+            _, J = prop.gradient_aniso(wav, src, rec, d_obs)
+            torch.cuda.synchronize()
+            s = time.perf_counter() - t0
         aniso = {"mode": str(modes[0]), "seconds": s, "shots_per_hour": 3600.0 / s, "misfit": J}
     except wp.PropError as e:
         aniso = {"error": str(e)}
@@ -416,10 +460,11 @@ def elastic_gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
         try:
             g, J = prop.gradient(wav, src, rec, d_obs)          # warm-up + result
             torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g, J = prop.gradient(wav, src, rec, d_obs)
-            torch.cuda.synchronize()
-            sec = time.perf_counter() - t0
+            with timed_region():
+                t0 = time.perf_counter()
+                g, J = prop.gradient(wav, src, rec, d_obs)
+                torch.cuda.synchronize()
+                sec = time.perf_counter() - t0
             gd = g.double()
             if ref is None:
                 ref = gd
@@ -448,9 +493,10 @@ def gradient_small(wp, torch, dev):
         w, s_, r = to(p.wavelet), to(p.src), to(p.rec)
         d = prop.forward(w, s_, r) * 1.1
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, J = prop.gradient(w, s_, r, d)
-        torch.cuda.synchronize()
+        with timed_region():
+            t0 = time.perf_counter()
+            _, J = prop.gradient(w, s_, r, d)
+            torch.cuda.synchronize()
         out[key] = {"grid": list(prop.grid), "nt": p.nt, "seconds": time.perf_counter() - t0, "misfit": J}
         prop.close()
     return out
@@ -482,17 +528,19 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
     props[0].gradient(wav[0], src[0], rec[0], obs[0])
     torch.cuda.synchronize()
     props[0].trim()
-    t0 = time.perf_counter()
-    seq = []
-    for i, p in enumerate(props):
-        seq.append(p.gradient(wav[i], src[i], rec[i], obs[i]))
-        p.trim()                         # as the batch does after each shot
-    torch.cuda.synchronize()
-    t_seq = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    grads, J = wp.gradient_batch(props, wav, src, rec, obs)
-    torch.cuda.synchronize()
-    t_bat = time.perf_counter() - t0
+    with timed_region():
+        t0 = time.perf_counter()
+        seq = []
+        for i, p in enumerate(props):
+            seq.append(p.gradient(wav[i], src[i], rec[i], obs[i]))
+            p.trim()                         # as the batch does after each shot
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+    with timed_region():
+        t0 = time.perf_counter()
+        grads, J = wp.gradient_batch(props, wav, src, rec, obs)
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t0
     same = all(bool(torch.equal(g, s[0])) for g, s in zip(grads, seq))
     waves = wp.plan_waves([p.gradient_bytes(r.shape[0]) for p, r in zip(props, rec)],
                           int(torch.cuda.mem_get_info(dev)[0] * 0.9))[1]
@@ -506,7 +554,52 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
             "bitwise_equal": same}
 
 
+def run_extras(wp, torch, dev, args, extras):
+    """Secondary measurements (``--extra``); each timed region is marked for
+    the clock record."""
+    out = {}
+
+    def _clocked(out, key, fn):
+        if _CLK is not None:
+            _CLK.regions = []
+        out[key] = fn()
+        if _CLK is not None and isinstance(out[key], dict):
+            out[key]["clocks"] = _CLK.summary()
+    if "tti" in extras:
+        if args.small:      # profiling case: 240x240x200 + 40 (320x320x280 points)
+            _clocked(out, "tti", lambda: tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200))
+        else:
+            _clocked(out, "tti", lambda: tti_throughput(wp, torch, dev))
+    if "ttisp" in extras:              # staggered-pair operators
+        if args.small:
+            _clocked(out, "ttisp", lambda: tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200, tti_operator=1))
+        else:
+            _clocked(out, "ttisp", lambda: tti_throughput(wp, torch, dev, steps=20, tti_operator=1))
+    if "acoustic" in extras:
+        if args.small:
+            _clocked(out, "acoustic", lambda: acoustic_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200))
+        else:
+            _clocked(out, "acoustic", lambda: acoustic_throughput(wp, torch, dev))
+    if "el2d" in extras:
+        _clocked(out, "el2d", lambda: elastic2d_throughput(wp, torch, dev, small=args.small))
+    if "rtm" in extras:
+        _clocked(out, "rtm", lambda: rtm_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt, small=args.small))
+    if "grad" in extras:
+        _clocked(out, "grad", lambda: gradient_shots_per_hour(
+            wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small))
+    if "elgrad" in extras:
+        _clocked(out, "elgrad", lambda: elastic_gradient_shots_per_hour(
+            wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small))
+    if "gradsmall" in extras:
+        _clocked(out, "gradsmall", lambda: gradient_small(wp, torch, dev))
+    if "batch" in extras:
+        _clocked(out, "batch", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
+                                            small=args.small, kind=args.batch_kind))
+    return out
+
+
 def main():
+    global _CLK
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -514,6 +607,8 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced grid (debug)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the TTI so-12 industry-scale step rates reported beside the headline")
     ap.add_argument("--extra", default="",
                     help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
@@ -532,41 +627,15 @@ def main():
     if extras:
         dev = torch.device("cuda", 0)
         torch.cuda.set_device(dev)
-        out = {}
-        if "tti" in extras:
-            if args.small:      # profiling case: 240x240x200 + 40 (320x320x280 points)
-                out["tti"] = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
-            else:
-                out["tti"] = tti_throughput(wp, torch, dev)
-        if "ttisp" in extras:              # staggered-pair operators
-            if args.small:
-                out["ttisp"] = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200, tti_operator=1)
-            else:
-                out["ttisp"] = tti_throughput(wp, torch, dev, steps=20, tti_operator=1)
-        if "acoustic" in extras:
-            if args.small:
-                out["acoustic"] = acoustic_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
-            else:
-                out["acoustic"] = acoustic_throughput(wp, torch, dev)
-        if "el2d" in extras:
-            out["el2d"] = elastic2d_throughput(wp, torch, dev, small=args.small)
-        if "rtm" in extras:
-            out["rtm"] = rtm_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt, small=args.small)
-        if "grad" in extras:
-            out["grad"] = gradient_shots_per_hour(
-                wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small)
-        if "elgrad" in extras:
-            out["elgrad"] = elastic_gradient_shots_per_hour(
-                wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small)
-        if "gradsmall" in extras:
-            out["gradsmall"] = gradient_small(wp, torch, dev)
-        if "batch" in extras:
-            out["batch"] = batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
-                                                small=args.small, kind=args.batch_kind)
+        with Clocks(0) as clk:
+            _CLK = clk
+            out = run_extras(wp, torch, dev, args, extras)
+            _CLK = None
+        out["clocks"] = clk.summary()
         print(json.dumps(out), flush=True)
         return
-
     world = int(os.environ.get("WORLD_SIZE", "1"))
+
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dist = None
@@ -658,9 +727,23 @@ def main():
     e2e = {"value": upd / e2e_s / 1e9, "unit": "Gpts/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h}
 
+    prop.close()
+    # secondary: TTI so 12 forward and adjoint steps at the industry-scale
+    # grid (800x800x400 + 40-cell layer = 880x880x480), one GPU only
+    secondary = None
+    if world == 1 and not args.no_secondary:
+        with Clocks(local) as clk2:
+            _CLK = clk2
+            if args.small:
+                tti = tti_throughput(wp, torch, dev, steps=10, nx=240, ny=240, nz=200)
+            else:
+                tti = tti_throughput(wp, torch, dev)
+            _CLK = None
+        tti["clocks"] = clk2.summary()
+        secondary = {"tti_so12_industry_grid": tti}
+
     cpu = None
     if rank == 0 and not args.no_cpu:
-        prop.close()
         cpu = cpu_baseline(prob)
     if rank == 0:
         line = {"metric": "elastic propagator grid-point updates per second",
@@ -676,6 +759,8 @@ def main():
                            "l2": "working set 2.2 GB >> L2 (no flush needed)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}
+        if secondary:
+            line["secondary"] = secondary
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
