@@ -502,6 +502,36 @@ def gradient_small(wp, torch, dev):
     return out
 
 
+def gradient_aniso_cost(wp, torch, dev, small=False):
+    """Cost of the TTI gradient w.r.t. (m, eps, delta, theta, phi) against
+    the m-only gradient, for the centred (0) and the staggered-pair (1)
+    operators: so 12, 240x240x200 + 40-cell layer (320x320x280 points), 60
+    steps, full FP32 storage (small: 80x80x60 + 20, 30 steps)."""
+    kw = dict(nx=80, ny=80, nz=60, nbl=20, nt=30) if small else dict(nx=240, ny=240, nz=200, nt=60)
+    p = synth.tti_layered(**kw)
+    to = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    w, s_, r = to(p.wavelet), to(p.src), to(p.rec)
+    out = {"grid": [p.nx + 2 * p.nbl, p.ny + 2 * p.nbl, p.nz + 2 * p.nbl], "nt": p.nt}
+    for op in (0, 1):
+        prop = wp.Propagator.from_problem(p, stream=stream, tti_operator=op)
+        d = prop.forward(w, s_, r) * 1.1
+        prop.gradient(w, s_, r, d)                      # warm-up
+        prop.gradient_aniso(w, s_, r, d)
+        torch.cuda.synchronize()
+        res = {}
+        for key, fn in (("m", prop.gradient), ("m_eps_delta_theta_phi", prop.gradient_aniso)):
+            with timed_region():
+                t0 = time.perf_counter()
+                fn(w, s_, r, d)
+                torch.cuda.synchronize()
+                res[key] = time.perf_counter() - t0
+        res["ratio"] = res["m_eps_delta_theta_phi"] / res["m"]
+        out[f"operator{op}"] = res
+        prop.close()
+    return out
+
+
 def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
     """Batched gradients (TTI so 12 or elastic so 8, BF16 checkpoints): shots
     on windows of one large model with nx, ny ~ U[200, 600], nz = 300 (+
@@ -590,6 +620,8 @@ def run_extras(wp, torch, dev, args, extras):
     if "elgrad" in extras:
         _clocked(out, "elgrad", lambda: elastic_gradient_shots_per_hour(
             wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small))
+    if "gradaniso" in extras:
+        _clocked(out, "gradaniso", lambda: gradient_aniso_cost(wp, torch, dev, small=args.small))
     if "gradsmall" in extras:
         _clocked(out, "gradsmall", lambda: gradient_small(wp, torch, dev))
     if "batch" in extras:
@@ -610,7 +642,8 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the TTI so-12 industry-scale step rates reported beside the headline")
     ap.add_argument("--extra", default="",
-                    help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, batch, rtm (secondary measurements)")
+                    help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, gradaniso, batch, rtm "
+                         "(secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--grad-modes", default="0,1,2,3",
                     help="storage modes of the grad/elgrad extras (0 full FP32, 1 FP32, 2 BF16, 3 FP16 checkpoints)")

@@ -43,13 +43,54 @@ struct F5 {
 };
 
 
+struct VMaps {
+    CUtensorMap xy, yy, xz, zz, yz, b, v[3], qxx, qxy, qxz, bi;
+};
+
+// Per consumer thread and tile (32 z x 16 y columns at (z0, y0)): position,
+// shared-memory offsets and the y/z Cerjan factors of its two z points.
+template <int M>
+struct ElCtx {
+    bool act;
+    unsigned q0;             // in-plane offset of the first point
+    int cy, cz, c2, ii;      // rows/columns in the halo boxes and the interior box
+    int yb1, zb2;            // +1 box row of y+1 and column of z+2 (clamped at the grid end)
+    float gzn0, gzh0, gzn1, gzh1, gyn, gyh;
+};
+template <int M>
+WP_DEV ElCtx<M> el_ctx(const GridDev &g, int z0, int y0, int tz, int ty)
+{
+    using B = BX<M>;
+    ElCtx<M> t;
+    const int z = z0 + 2 * tz, y = y0 + ty;
+    t.act = y < g.NY && z < g.NZ;
+    t.q0 = t.act ? (unsigned)y * g.NZ + z : 0u;
+    const float *tabz = g.tab + 2 * (g.NX + g.NY);
+    const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
+    t.gzn0 = __ldg(tabz + 2 * zc0);
+    t.gzh0 = __ldg(tabz + 2 * zc0 + 1);
+    t.gzn1 = __ldg(tabz + 2 * zc1);
+    t.gzh1 = __ldg(tabz + 2 * zc1 + 1);
+    t.gyn = __ldg(g.tab + 2 * g.NX + 2 * yc);
+    t.gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
+    t.cy = ty + M;
+    t.cz = B::MZ + 2 * tz;
+    t.c2 = 2 * tz;
+    t.ii = ty * FZ + t.c2;
+    t.yb1 = y + 1 < g.NY ? ty + 1 : ty;
+    t.zb2 = z + 2 < g.NZ ? t.c2 + 2 : t.c2 + 1;
+    return t;
+}
+
 // ---------------------------------------------------------------------------
-// elastic velocity pass.  ADJ = 1: the velocity half of the transposed step
-// in the tbar form, vbar <- g (vbar - dt Dtau(sigma)) with sigma = C g tbar
-// in s.f[3..8], and w = b_avg vbar written to o.f[0..2].
+// elastic velocity pass, one plane.  ADJ = 1: the velocity half of the
+// transposed step in the tbar form, vbar <- g (vbar - dt Dtau(sigma)) with
+// sigma = C g tbar in s.f[3..8], and w = b_avg vbar written to o.f[0..2].
 // stage: [xy (y box)] [yy (y box)] [xz (z box)] [zz (z box)] [yz (rect)]
 //        [b (+1 box)] [v_x v_y v_z (plane x)] [queue heads: xx (x+M),
 //        xy (x+M-1), xz (x+M-1)] [b (plane x+1, clamped)]
+// x-derivative queues: qxx[j] = t_xx(x - M + 1 + j), qxy[j] = t_xy(x - M + j),
+// qxz[j] = t_xz(x - M + j), j = 0 .. 2M-1 (the last entry from the stage).
 // ---------------------------------------------------------------------------
 template <int M>
 struct VL {
@@ -61,40 +102,129 @@ struct VL {
                                             B::PR * B::PC + 7 * IS);
 };
 
-struct VMaps {
-    CUtensorMap xy, yy, xz, zz, yz, b, v[3], qxx, qxy, qxz, bi;
-};
+template <int M>
+WP_DEV void v_issue(const VMaps &mp, float *S, uint64_t *bar, int z0, int y0, int x, int NX)
+{
+    using L = VL<M>;
+    using B = BX<M>;
+    mbar_expect(bar, L::BYTES);
+    tma3(S + L::OXY, &mp.xy, z0, y0 - M, x, bar);
+    tma3(S + L::OYY, &mp.yy, z0, y0 - M, x, bar);
+    tma3(S + L::OXZ, &mp.xz, z0 - B::MZ, y0, x, bar);
+    tma3(S + L::OZZ, &mp.zz, z0 - B::MZ, y0, x, bar);
+    tma3(S + L::OYZ, &mp.yz, z0 - B::MZ, y0 - M, x, bar);
+    tma3(S + L::OB, &mp.b, z0, y0, x, bar);
+    for (int i = 0; i < 3; i++) tma3(S + L::OV + i * IS, &mp.v[i], z0, y0, x, bar);
+    tma3(S + L::OQ, &mp.qxx, z0, y0, x + M, bar);                  // beyond NX: zeros
+    tma3(S + L::OQ + IS, &mp.qxy, z0, y0, x + M - 1, bar);
+    tma3(S + L::OQ + 2 * IS, &mp.qxz, z0, y0, x + M - 1, bar);
+    tma3(S + L::OBX, &mp.bi, z0, y0, min(x + 1, NX - 1), bar);
+}
+
+template <int M>
+WP_DEV void v_preload(const GridDev &g, const F9 &s, const ElCtx<M> &t, int xa, float2 (&qxx)[2 * M],
+                      float2 (&qxy)[2 * M], float2 (&qxz)[2 * M])
+{
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const float2 Z2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 2 * M - 1; j++) {
+        const int xq = xa - M + 1 + j, xr = xa - M + j;
+        qxx[j] = t.act && xq >= 0 && xq < g.NX ? ldg2(s.f[3], xq * pl + t.q0) : Z2;
+        qxy[j] = t.act && xr >= 0 && xr < g.NX ? ldg2(s.f[6], xr * pl + t.q0) : Z2;
+        qxz[j] = t.act && xr >= 0 && xr < g.NX ? ldg2(s.f[7], xr * pl + t.q0) : Z2;
+    }
+}
+
+template <int M, int ADJ>
+WP_DEV void v_plane(const GridDev &g, const FDW &w, const F9 &s, const F5 &o, const float *S, const ElCtx<M> &t,
+                    int x, float2 (&qxx)[2 * M], float2 (&qxy)[2 * M], float2 (&qxz)[2 * M])
+{
+    using L = VL<M>;
+    using B = BX<M>;
+    constexpr int Q = 2 * M;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    qxx[Q - 1] = lds2(S + L::OQ + t.ii);
+    qxy[Q - 1] = lds2(S + L::OQ + IS + t.ii);
+    qxz[Q - 1] = lds2(S + L::OQ + 2 * IS + t.ii);
+    if (t.act) {
+        const int cy = t.cy, cz = t.cz, c2 = t.c2, ii = t.ii;
+        const float c = g.dt * g.ih;
+        const float *sxy = S + L::OXY, *syy = S + L::OYY, *syz = S + L::OYZ, *sb = S + L::OB;
+        float wxz[2 * M + 2], wyz[2 * M + 2], wzz[2 * M + 2];
+        zwin<M>(S + L::OXZ + (cy - M) * B::ZC, cz, wxz);
+        zwin<M>(syz + cy * B::RC, cz, wyz);
+        zwin<M>(S + L::OZZ + (cy - M) * B::ZC, cz, wzz);
+        float2 d0 = Z2, d1 = Z2, d2 = Z2;
+#pragma unroll
+        for (int k = 1; k <= M; k++) {
+            const float2 b = f2s(w.b[k - 1]);
+            const float2 ax = f2sub(qxx[M - 1 + k], qxx[M - k]);
+            const float2 ay = f2sub(lds2(sxy + (cy + k - 1) * B::YC + c2), lds2(sxy + (cy - k) * B::YC + c2));
+            const float2 az = make_float2(wxz[M + k - 1] - wxz[M - k], wxz[M + k] - wxz[M - k + 1]);
+            d0 = f2fma(b, f2add(f2add(ax, ay), az), d0);
+            const float2 bx_ = f2sub(qxy[M + k - 1], qxy[M - k]);
+            const float2 by_ = f2sub(lds2(syy + (cy + k) * B::YC + c2), lds2(syy + (cy - k + 1) * B::YC + c2));
+            const float2 bz_ = make_float2(wyz[M + k - 1] - wyz[M - k], wyz[M + k] - wyz[M - k + 1]);
+            d1 = f2fma(b, f2add(f2add(bx_, by_), bz_), d1);
+            const float2 cx_ = f2sub(qxz[M + k - 1], qxz[M - k]);
+            const float2 cy_ = f2sub(lds2(syz + (cy + k - 1) * B::RC + cz), lds2(syz + (cy - k) * B::RC + cz));
+            const float2 cz_ = make_float2(wzz[M + k] - wzz[M - k + 1], wzz[M + k + 1] - wzz[M - k + 2]);
+            d2 = f2fma(b, f2add(f2add(cx_, cy_), cz_), d2);
+        }
+        const float d0a = d0.x, d0b = d0.y, d1a = d1.x, d1b = d1.y, d2a = d2.x, d2b = d2.y;
+        const float2 v0 = lds2(S + L::OV + ii), v1 = lds2(S + L::OV + IS + ii), v2 = lds2(S + L::OV + 2 * IS + ii);
+        const float2 bxn = lds2(S + L::OBX + ii);
+        const int ty = cy - M;
+        const float2 b0 = lds2(sb + ty * B::PC + c2);
+        const float2 bY = lds2(sb + t.yb1 * B::PC + c2);
+        const float bz2 = sb[ty * B::PC + t.zb2];
+        const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
+        const unsigned q = x * (unsigned)g.NY * (unsigned)g.NZ + t.q0;
+        // face averages of buoyancy and tapers at the three velocity points
+        const float bxa = 0.5f * (b0.x + bxn.x), bxb = 0.5f * (b0.y + bxn.y);
+        const float bya = 0.5f * (b0.x + bY.x), byb = 0.5f * (b0.y + bY.y);
+        const float bza = 0.5f * (b0.x + b0.y), bzb = 0.5f * (b0.y + bz2);
+        const float gx0 = gxh * t.gyn * t.gzn0, gx1 = gxh * t.gyn * t.gzn1;
+        const float gy0 = gxn * t.gyh * t.gzn0, gy1 = gxn * t.gyh * t.gzn1;
+        const float gz0 = gxn * t.gyn * t.gzh0, gz1 = gxn * t.gyn * t.gzh1;
+        if (!ADJ) {
+            st2(s.f[0], q, gx0 * (v0.x + c * bxa * d0a), gx1 * (v0.y + c * bxb * d0b));
+            st2(s.f[1], q, gy0 * (v1.x + c * bya * d1a), gy1 * (v1.y + c * byb * d1b));
+            st2(s.f[2], q, gz0 * (v2.x + c * bza * d2a), gz1 * (v2.y + c * bzb * d2b));
+        } else {
+            const float u0a = gx0 * (v0.x - c * d0a), u0b = gx1 * (v0.y - c * d0b);
+            const float u1a = gy0 * (v1.x - c * d1a), u1b = gy1 * (v1.y - c * d1b);
+            const float u2a = gz0 * (v2.x - c * d2a), u2b = gz1 * (v2.y - c * d2b);
+            st2(s.f[0], q, u0a, u0b);
+            st2(s.f[1], q, u1a, u1b);
+            st2(s.f[2], q, u2a, u2b);
+            st2(o.f[0], q, bxa * u0a, bxb * u0b);
+            st2(o.f[1], q, bya * u1a, byb * u1b);
+            st2(o.f[2], q, bza * u2a, bzb * u2b);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        qxx[j] = qxx[j + 1];
+        qxy[j] = qxy[j + 1];
+        qxz[j] = qxz[j + 1];
+    }
+}
 
 template <int M, int ADJ>
 __global__ void __launch_bounds__(NTP, M <= 4 ? 2 : 1)
 el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int xc, int *err)
 {
     using L = VL<M>;
-    using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
     const bool lead = warp == 0 && lane == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
-    auto issue = [&](int x, int st) {
-        float *S = sm + st * L::SZ;
-        uint64_t *bar = &bars[st];
-        mbar_expect(bar, L::BYTES);
-        tma3(S + L::OXY, &mp.xy, z0, y0 - M, x, bar);
-        tma3(S + L::OYY, &mp.yy, z0, y0 - M, x, bar);
-        tma3(S + L::OXZ, &mp.xz, z0 - B::MZ, y0, x, bar);
-        tma3(S + L::OZZ, &mp.zz, z0 - B::MZ, y0, x, bar);
-        tma3(S + L::OYZ, &mp.yz, z0 - B::MZ, y0 - M, x, bar);
-        tma3(S + L::OB, &mp.b, z0, y0, x, bar);
-        for (int i = 0; i < 3; i++) tma3(S + L::OV + i * IS, &mp.v[i], z0, y0, x, bar);
-        tma3(S + L::OQ, &mp.qxx, z0, y0, x + M, bar);                  // beyond NX: zeros
-        tma3(S + L::OQ + IS, &mp.qxy, z0, y0, x + M - 1, bar);
-        tma3(S + L::OQ + 2 * IS, &mp.qxz, z0, y0, x + M - 1, bar);
-        tma3(S + L::OBX, &mp.bi, z0, y0, min(x + 1, g.NX - 1), bar);
-    };
+    auto issue = [&](int x, int st) { v_issue<M>(mp, sm + st * L::SZ, &bars[st], z0, y0, x, g.NX); };
     Ring R(bars);
     if (lead) R.init();
     __syncthreads();
@@ -102,105 +232,22 @@ el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int
         if (lane == 0) R.produce(xa, nit, issue, err);
         return;
     }
-    const bool act = y < g.NY && z < g.NZ;
-    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
-    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
-    const float2 Z2 = make_float2(0.f, 0.f);
-    const float *txx = s.f[3], *txy = s.f[6], *txz = s.f[7];
+    const ElCtx<M> t = el_ctx<M>(g, z0, y0, tz, ty);
     float2 qxx[Q], qxy[Q], qxz[Q];
-#pragma unroll
-    for (int j = 0; j < Q - 1; j++) {
-        const int xq = xa - M + 1 + j, xr = xa - M + j;
-        qxx[j] = act && xq >= 0 && xq < g.NX ? ldg2(txx, xq * pl + q0) : Z2;
-        qxy[j] = act && xr >= 0 && xr < g.NX ? ldg2(txy, xr * pl + q0) : Z2;
-        qxz[j] = act && xr >= 0 && xr < g.NX ? ldg2(txz, xr * pl + q0) : Z2;
-    }
-    const float c = g.dt * g.ih;
-    const float *tabz = g.tab + 2 * (g.NX + g.NY);
-    const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
-    const float gzn0 = __ldg(tabz + 2 * zc0), gzh0 = __ldg(tabz + 2 * zc0 + 1);
-    const float gzn1 = __ldg(tabz + 2 * zc1), gzh1 = __ldg(tabz + 2 * zc1 + 1);
-    const float gyn = __ldg(g.tab + 2 * g.NX + 2 * yc), gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
-    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz, ii = ty * FZ + c2;
-    const int yb1 = y + 1 < g.NY ? ty + 1 : ty;           // +1 box row of b(y+1), clamped
-    const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;       // +1 box column of b(z+2), clamped
+    v_preload<M>(g, s, t, xa, qxx, qxy, qxz);
     for (int x = xa; x < xb; x++) {
         if (!__all_sync(0xffffffffu, R.wait_full())) {
             if (lane == 0) atomicOr(err, 2);
             return;
         }
-        const float *S = sm + R.st * L::SZ;
-        {
-            qxx[Q - 1] = lds2(S + L::OQ + ii);
-            qxy[Q - 1] = lds2(S + L::OQ + IS + ii);
-            qxz[Q - 1] = lds2(S + L::OQ + 2 * IS + ii);
-        }
-        if (act) {
-            const float *sxy = S + L::OXY, *syy = S + L::OYY, *syz = S + L::OYZ, *sb = S + L::OB;
-            float wxz[2 * M + 2], wyz[2 * M + 2], wzz[2 * M + 2];
-            zwin<M>(S + L::OXZ + ty * B::ZC, cz, wxz);
-            zwin<M>(syz + cy * B::RC, cz, wyz);
-            zwin<M>(S + L::OZZ + ty * B::ZC, cz, wzz);
-            float2 d0 = Z2, d1 = Z2, d2 = Z2;
-#pragma unroll
-            for (int k = 1; k <= M; k++) {
-                const float2 b = f2s(w.b[k - 1]);
-                const float2 ax = f2sub(qxx[M - 1 + k], qxx[M - k]);
-                const float2 ay = f2sub(lds2(sxy + (cy + k - 1) * B::YC + c2), lds2(sxy + (cy - k) * B::YC + c2));
-                const float2 az = make_float2(wxz[M + k - 1] - wxz[M - k], wxz[M + k] - wxz[M - k + 1]);
-                d0 = f2fma(b, f2add(f2add(ax, ay), az), d0);
-                const float2 bx_ = f2sub(qxy[M + k - 1], qxy[M - k]);
-                const float2 by_ = f2sub(lds2(syy + (cy + k) * B::YC + c2), lds2(syy + (cy - k + 1) * B::YC + c2));
-                const float2 bz_ = make_float2(wyz[M + k - 1] - wyz[M - k], wyz[M + k] - wyz[M - k + 1]);
-                d1 = f2fma(b, f2add(f2add(bx_, by_), bz_), d1);
-                const float2 cx_ = f2sub(qxz[M + k - 1], qxz[M - k]);
-                const float2 cy_ = f2sub(lds2(syz + (cy + k - 1) * B::RC + cz), lds2(syz + (cy - k) * B::RC + cz));
-                const float2 cz_ = make_float2(wzz[M + k] - wzz[M - k + 1], wzz[M + k + 1] - wzz[M - k + 2]);
-                d2 = f2fma(b, f2add(f2add(cx_, cy_), cz_), d2);
-            }
-            const float d0a = d0.x, d0b = d0.y, d1a = d1.x, d1b = d1.y, d2a = d2.x, d2b = d2.y;
-            const float2 v0 = lds2(S + L::OV + ii), v1 = lds2(S + L::OV + IS + ii), v2 = lds2(S + L::OV + 2 * IS + ii);
-            const float2 bxn = lds2(S + L::OBX + ii);
-            const float2 b0 = lds2(sb + ty * B::PC + c2);
-            const float2 bY = lds2(sb + yb1 * B::PC + c2);
-            const float bz2 = sb[ty * B::PC + zb2];
-            const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
-            const unsigned q = x * pl + q0;
-            // face averages of buoyancy and tapers at the three velocity points
-            const float bxa = 0.5f * (b0.x + bxn.x), bxb = 0.5f * (b0.y + bxn.y);
-            const float bya = 0.5f * (b0.x + bY.x), byb = 0.5f * (b0.y + bY.y);
-            const float bza = 0.5f * (b0.x + b0.y), bzb = 0.5f * (b0.y + bz2);
-            const float gx0 = gxh * gyn * gzn0, gx1 = gxh * gyn * gzn1;
-            const float gy0 = gxn * gyh * gzn0, gy1 = gxn * gyh * gzn1;
-            const float gz0 = gxn * gyn * gzh0, gz1 = gxn * gyn * gzh1;
-            if (!ADJ) {
-                st2(s.f[0], q, gx0 * (v0.x + c * bxa * d0a), gx1 * (v0.y + c * bxb * d0b));
-                st2(s.f[1], q, gy0 * (v1.x + c * bya * d1a), gy1 * (v1.y + c * byb * d1b));
-                st2(s.f[2], q, gz0 * (v2.x + c * bza * d2a), gz1 * (v2.y + c * bzb * d2b));
-            } else {
-                const float u0a = gx0 * (v0.x - c * d0a), u0b = gx1 * (v0.y - c * d0b);
-                const float u1a = gy0 * (v1.x - c * d1a), u1b = gy1 * (v1.y - c * d1b);
-                const float u2a = gz0 * (v2.x - c * d2a), u2b = gz1 * (v2.y - c * d2b);
-                st2(s.f[0], q, u0a, u0b);
-                st2(s.f[1], q, u1a, u1b);
-                st2(s.f[2], q, u2a, u2b);
-                st2(o.f[0], q, bxa * u0a, bxb * u0b);
-                st2(o.f[1], q, bya * u1a, byb * u1b);
-                st2(o.f[2], q, bza * u2a, bzb * u2b);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < Q - 1; j++) {
-            qxx[j] = qxx[j + 1];
-            qxy[j] = qxy[j + 1];
-            qxz[j] = qxz[j + 1];
-        }
+        v_plane<M, ADJ>(g, w, s, o, sm + R.st * L::SZ, t, x, qxx, qxy, qxz);
         R.release(lane);
     }
 }
 
 // ---------------------------------------------------------------------------
-// elastic stress pass: the strain S(v) of a velocity triple (s.f[0..2]) and
+// elastic stress pass, one plane: the strain S(v) of a velocity triple
+// (s.f[0..2]) and
 //   MODE 0  tau <- g (tau + dt C S(v))                     (forward step)
 //   MODE 1  tbar <- t - dt S(w), t = g tbar, w = b_avg vbar  (stress half of
 //           the transposed step in the tbar form; t read, tbar written in
@@ -211,6 +258,8 @@ el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int
 // stage: [vx rect] [vy rect] [vz rect] (+ [mu +1 box, planes x, x+1] MODE 0)
 //        [t_xx .. t_yz (plane x)] (+ [lambda] MODE 0) (+ [g_lambda, g_mu]
 //        MODE 2) [queue heads: vx (x+M-1), vy (x+M), vz (x+M)]
+// x-derivative queues: qvx[j] = v_x(x - M + j), qvy[j] = v_y(x - M + 1 + j),
+// qvz[j] = v_z(x - M + 1 + j).
 // ---------------------------------------------------------------------------
 template <int M, int MODE>
 struct TL {
@@ -228,40 +277,154 @@ struct TMaps {
 };
 
 template <int M, int MODE>
+WP_DEV void t_issue(const TMaps &mp, float *S, uint64_t *bar, int z0, int y0, int x, int NX)
+{
+    using L = TL<M, MODE>;
+    using B = BX<M>;
+    mbar_expect(bar, L::BYTES);
+    tma3(S + L::OVX, &mp.vx, z0 - B::MZ, y0 - M, x, bar);
+    tma3(S + L::OVY, &mp.vy, z0 - B::MZ, y0 - M, x, bar);
+    tma3(S + L::OVZ, &mp.vz, z0 - B::MZ, y0 - M, x, bar);
+    if (MODE == 0) {
+        tma3(S + L::OM0, &mp.mu, z0, y0, x, bar);
+        tma3(S + L::OM1, &mp.mu, z0, y0, min(x + 1, NX - 1), bar);
+        tma3(S + L::OL, &mp.lam, z0, y0, x, bar);
+    }
+    for (int i = 0; i < 6; i++) tma3(S + L::OT + i * IS, &mp.t[i], z0, y0, x, bar);
+    if (MODE == 2) {
+        tma3(S + L::OG, &mp.gl, z0, y0, x, bar);
+        tma3(S + L::OG + IS, &mp.gm, z0, y0, x, bar);
+    }
+    tma3(S + L::OQ, &mp.qvx, z0, y0, x + M - 1, bar);              // beyond NX: zeros
+    tma3(S + L::OQ + IS, &mp.qvy, z0, y0, x + M, bar);
+    tma3(S + L::OQ + 2 * IS, &mp.qvz, z0, y0, x + M, bar);
+}
+
+template <int M>
+WP_DEV void t_preload(const GridDev &g, const F9 &s, const ElCtx<M> &t, int xa, float2 (&qvx)[2 * M],
+                      float2 (&qvy)[2 * M], float2 (&qvz)[2 * M])
+{
+    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
+    const float2 Z2 = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 2 * M - 1; j++) {
+        const int xr = xa - M + j, xq = xa - M + 1 + j;
+        qvx[j] = t.act && xr >= 0 && xr < g.NX ? ldg2(s.f[0], xr * pl + t.q0) : Z2;
+        qvy[j] = t.act && xq >= 0 && xq < g.NX ? ldg2(s.f[1], xq * pl + t.q0) : Z2;
+        qvz[j] = t.act && xq >= 0 && xq < g.NX ? ldg2(s.f[2], xq * pl + t.q0) : Z2;
+    }
+}
+
+template <int M, int MODE>
+WP_DEV void t_plane(const GridDev &g, const FDW &w, const F9 &s, const F5 &o, const float *S, const ElCtx<M> &t,
+                    int x, float2 (&qvx)[2 * M], float2 (&qvy)[2 * M], float2 (&qvz)[2 * M])
+{
+    using L = TL<M, MODE>;
+    using B = BX<M>;
+    constexpr int Q = 2 * M;
+    const float2 Z2 = make_float2(0.f, 0.f);
+    qvx[Q - 1] = lds2(S + L::OQ + t.ii);
+    qvy[Q - 1] = lds2(S + L::OQ + IS + t.ii);
+    qvz[Q - 1] = lds2(S + L::OQ + 2 * IS + t.ii);
+    if (t.act) {
+        const int cy = t.cy, cz = t.cz, c2 = t.c2, ii = t.ii, ty = t.cy - M;
+        const float c = g.dt * g.ih;
+        const float *svx = S + L::OVX, *svy = S + L::OVY, *svz = S + L::OVZ;
+        float wvx[2 * M + 2], wvy[2 * M + 2], wvz[2 * M + 2];
+        zwin<M>(svx + cy * B::RC, cz, wvx);
+        zwin<M>(svy + cy * B::RC, cz, wvy);
+        zwin<M>(svz + cy * B::RC, cz, wvz);
+        float2 ex = Z2, ey = Z2, ez = Z2, gxy = Z2, gxz = Z2, gyz = Z2;
+#pragma unroll
+        for (int k = 1; k <= M; k++) {
+            const float2 b = f2s(w.b[k - 1]);
+            ex = f2fma(b, f2sub(qvx[M + k - 1], qvx[M - k]), ex);
+            ey = f2fma(b, f2sub(lds2(svy + (cy + k - 1) * B::RC + cz), lds2(svy + (cy - k) * B::RC + cz)), ey);
+            ez = f2fma(b, make_float2(wvz[M + k - 1] - wvz[M - k], wvz[M + k] - wvz[M - k + 1]), ez);
+            const float2 xy = f2sub(lds2(svx + (cy + k) * B::RC + cz), lds2(svx + (cy - k + 1) * B::RC + cz));
+            const float2 yx = f2sub(qvy[M - 1 + k], qvy[M - k]);
+            gxy = f2fma(b, f2add(xy, yx), gxy);
+            const float2 zx = f2sub(qvz[M - 1 + k], qvz[M - k]);
+            const float2 xz = make_float2(wvx[M + k] - wvx[M - k + 1], wvx[M + k + 1] - wvx[M - k + 2]);
+            gxz = f2fma(b, f2add(xz, zx), gxz);
+            const float2 zy = f2sub(lds2(svz + (cy + k) * B::RC + cz), lds2(svz + (cy - k + 1) * B::RC + cz));
+            const float2 yz = make_float2(wvy[M + k] - wvy[M - k + 1], wvy[M + k + 1] - wvy[M - k + 2]);
+            gyz = f2fma(b, f2add(yz, zy), gyz);
+        }
+        const float exa = ex.x, exb = ex.y, eya = ey.x, eyb = ey.y, eza = ez.x, ezb = ez.y;
+        const float gxya = gxy.x, gxyb = gxy.y, gxza = gxz.x, gxzb = gxz.y, gyza = gyz.x, gyzb = gyz.y;
+        const float *T = S + L::OT + ii;
+        const float2 t0 = lds2(T), t1 = lds2(T + IS), t2 = lds2(T + 2 * IS);
+        const float2 t3 = lds2(T + 3 * IS), t4 = lds2(T + 4 * IS), t5 = lds2(T + 5 * IS);
+        const unsigned q = x * (unsigned)g.NY * (unsigned)g.NZ + t.q0;
+        if (MODE == 0) {
+            const float *R0 = S + L::OM0, *R1 = S + L::OM1;
+            const float2 m0 = lds2(R0 + ty * B::PC + c2), my = lds2(R0 + t.yb1 * B::PC + c2);
+            const float2 mx = lds2(R1 + ty * B::PC + c2), mxy_ = lds2(R1 + t.yb1 * B::PC + c2);
+            const float m0z = R0[ty * B::PC + t.zb2], myz = R0[t.yb1 * B::PC + t.zb2], mxz = R1[ty * B::PC + t.zb2];
+            const float2 l = lds2(S + L::OL + ii);
+            const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
+            const float gyn = t.gyn, gyh = t.gyh, gzn0 = t.gzn0, gzn1 = t.gzn1, gzh0 = t.gzh0, gzh1 = t.gzh1;
+            const float gn0 = gxn * gyn * gzn0, gn1 = gxn * gyn * gzn1;
+            // averages of mu over the 4 nodes around each edge (the pair's
+            // second lane is the first point's z+1 neighbour)
+            const float mxya = 0.25f * (m0.x + mx.x + my.x + mxy_.x);
+            const float mxza = 0.25f * (m0.x + mx.x + m0.y + mx.y);
+            const float myza = 0.25f * (m0.x + my.x + m0.y + my.y);
+            const float mxyb = 0.25f * (m0.y + mx.y + my.y + mxy_.y);
+            const float mxzb = 0.25f * (m0.y + mx.y + m0z + mxz);
+            const float myzb = 0.25f * (m0.y + my.y + m0z + myz);
+            const float tra = exa + eya + eza, trb = exb + eyb + ezb;
+            const float m2a = 2.f * m0.x, m2b = 2.f * m0.y;
+            st2(s.f[3], q, gn0 * (t0.x + c * (l.x * tra + m2a * exa)), gn1 * (t0.y + c * (l.y * trb + m2b * exb)));
+            st2(s.f[4], q, gn0 * (t1.x + c * (l.x * tra + m2a * eya)), gn1 * (t1.y + c * (l.y * trb + m2b * eyb)));
+            st2(s.f[5], q, gn0 * (t2.x + c * (l.x * tra + m2a * eza)), gn1 * (t2.y + c * (l.y * trb + m2b * ezb)));
+            st2(s.f[6], q, gxh * gyh * gzn0 * (t3.x + c * mxya * gxya), gxh * gyh * gzn1 * (t3.y + c * mxyb * gxyb));
+            st2(s.f[7], q, gxh * gyn * gzh0 * (t4.x + c * mxza * gxza), gxh * gyn * gzh1 * (t4.y + c * mxzb * gxzb));
+            st2(s.f[8], q, gxn * gyh * gzh0 * (t5.x + c * myza * gyza), gxn * gyh * gzh1 * (t5.y + c * myzb * gyzb));
+        } else if (MODE == 1) {
+            st2(s.f[3], q, t0.x - c * exa, t0.y - c * exb);
+            st2(s.f[4], q, t1.x - c * eya, t1.y - c * eyb);
+            st2(s.f[5], q, t2.x - c * eza, t2.y - c * ezb);
+            st2(s.f[6], q, t3.x - c * gxya, t3.y - c * gxyb);
+            st2(s.f[7], q, t4.x - c * gxza, t4.y - c * gxzb);
+            st2(s.f[8], q, t5.x - c * gyza, t5.y - c * gyzb);
+        } else {
+            const float2 gl = lds2(S + L::OG + ii), gm = lds2(S + L::OG + IS + ii);
+            st2(o.f[0], q, gl.x + c * (t0.x + t1.x + t2.x) * (exa + eya + eza),
+                gl.y + c * (t0.y + t1.y + t2.y) * (exb + eyb + ezb));
+            st2(o.f[1], q, gm.x + 2.f * c * (t0.x * exa + t1.x * eya + t2.x * eza),
+                gm.y + 2.f * c * (t0.y * exb + t1.y * eyb + t2.y * ezb));
+            // edge products summed over the steps (gathered onto the nodes at the end)
+            const float2 p3 = *reinterpret_cast<const float2 *>(o.f[2] + q);
+            const float2 p4 = *reinterpret_cast<const float2 *>(o.f[3] + q);
+            const float2 p5 = *reinterpret_cast<const float2 *>(o.f[4] + q);
+            st2(o.f[2], q, p3.x + c * t3.x * gxya, p3.y + c * t3.y * gxyb);
+            st2(o.f[3], q, p4.x + c * t4.x * gxza, p4.y + c * t4.y * gxzb);
+            st2(o.f[4], q, p5.x + c * t5.x * gyza, p5.y + c * t5.y * gyzb);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < Q - 1; j++) {
+        qvx[j] = qvx[j + 1];
+        qvy[j] = qvy[j + 1];
+        qvz[j] = qvz[j + 1];
+    }
+}
+
+template <int M, int MODE>
 __global__ void __launch_bounds__(NTP, M <= 4 ? 2 : 1)
 el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int xc, int *err)
 {
     using L = TL<M, MODE>;
-    using B = BX<M>;
     constexpr int Q = 2 * M;
     extern __shared__ __align__(128) float sm[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
     const bool lead = warp == 0 && lane == 0;
     const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int z = z0 + 2 * tz, y = y0 + ty;
     const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
-    auto issue = [&](int x, int st) {
-        float *S = sm + st * L::SZ;
-        uint64_t *bar = &bars[st];
-        mbar_expect(bar, L::BYTES);
-        tma3(S + L::OVX, &mp.vx, z0 - B::MZ, y0 - M, x, bar);
-        tma3(S + L::OVY, &mp.vy, z0 - B::MZ, y0 - M, x, bar);
-        tma3(S + L::OVZ, &mp.vz, z0 - B::MZ, y0 - M, x, bar);
-        if (MODE == 0) {
-            tma3(S + L::OM0, &mp.mu, z0, y0, x, bar);
-            tma3(S + L::OM1, &mp.mu, z0, y0, min(x + 1, g.NX - 1), bar);
-            tma3(S + L::OL, &mp.lam, z0, y0, x, bar);
-        }
-        for (int i = 0; i < 6; i++) tma3(S + L::OT + i * IS, &mp.t[i], z0, y0, x, bar);
-        if (MODE == 2) {
-            tma3(S + L::OG, &mp.gl, z0, y0, x, bar);
-            tma3(S + L::OG + IS, &mp.gm, z0, y0, x, bar);
-        }
-        tma3(S + L::OQ, &mp.qvx, z0, y0, x + M - 1, bar);              // beyond NX: zeros
-        tma3(S + L::OQ + IS, &mp.qvy, z0, y0, x + M, bar);
-        tma3(S + L::OQ + 2 * IS, &mp.qvz, z0, y0, x + M, bar);
-    };
+    auto issue = [&](int x, int st) { t_issue<M, MODE>(mp, sm + st * L::SZ, &bars[st], z0, y0, x, g.NX); };
     Ring R(bars);
     if (lead) R.init();
     __syncthreads();
@@ -269,120 +432,15 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
         if (lane == 0) R.produce(xa, nit, issue, err);
         return;
     }
-    const bool act = y < g.NY && z < g.NZ;
-    const unsigned pl = (unsigned)g.NY * (unsigned)g.NZ;
-    const unsigned q0 = act ? (unsigned)y * g.NZ + z : 0u;
-    const float2 Z2 = make_float2(0.f, 0.f);
-    const float *vxp = s.f[0], *vyp = s.f[1], *vzp = s.f[2];
+    const ElCtx<M> t = el_ctx<M>(g, z0, y0, tz, ty);
     float2 qvx[Q], qvy[Q], qvz[Q];
-#pragma unroll
-    for (int j = 0; j < Q - 1; j++) {
-        const int xr = xa - M + j, xq = xa - M + 1 + j;
-        qvx[j] = act && xr >= 0 && xr < g.NX ? ldg2(vxp, xr * pl + q0) : Z2;
-        qvy[j] = act && xq >= 0 && xq < g.NX ? ldg2(vyp, xq * pl + q0) : Z2;
-        qvz[j] = act && xq >= 0 && xq < g.NX ? ldg2(vzp, xq * pl + q0) : Z2;
-    }
-    const float c = g.dt * g.ih;
-    const float *tabz = g.tab + 2 * (g.NX + g.NY);
-    const int zc0 = min(z, g.NZ - 1), zc1 = min(z + 1, g.NZ - 1), yc = min(y, g.NY - 1);
-    const float gzn0 = __ldg(tabz + 2 * zc0), gzh0 = __ldg(tabz + 2 * zc0 + 1);
-    const float gzn1 = __ldg(tabz + 2 * zc1), gzh1 = __ldg(tabz + 2 * zc1 + 1);
-    const float gyn = __ldg(g.tab + 2 * g.NX + 2 * yc), gyh = __ldg(g.tab + 2 * g.NX + 2 * yc + 1);
-    const int cy = ty + M, cz = B::MZ + 2 * tz, c2 = 2 * tz, ii = ty * FZ + c2;
-    const int yb1 = y + 1 < g.NY ? ty + 1 : ty;
-    const int zb2 = z + 2 < g.NZ ? c2 + 2 : c2 + 1;
+    t_preload<M>(g, s, t, xa, qvx, qvy, qvz);
     for (int x = xa; x < xb; x++) {
         if (!__all_sync(0xffffffffu, R.wait_full())) {
             if (lane == 0) atomicOr(err, 2);
             return;
         }
-        const float *S = sm + R.st * L::SZ;
-        {
-            qvx[Q - 1] = lds2(S + L::OQ + ii);
-            qvy[Q - 1] = lds2(S + L::OQ + IS + ii);
-            qvz[Q - 1] = lds2(S + L::OQ + 2 * IS + ii);
-        }
-        if (act) {
-            const float *svx = S + L::OVX, *svy = S + L::OVY, *svz = S + L::OVZ;
-            float wvx[2 * M + 2], wvy[2 * M + 2], wvz[2 * M + 2];
-            zwin<M>(svx + cy * B::RC, cz, wvx);
-            zwin<M>(svy + cy * B::RC, cz, wvy);
-            zwin<M>(svz + cy * B::RC, cz, wvz);
-            float2 ex = Z2, ey = Z2, ez = Z2, gxy = Z2, gxz = Z2, gyz = Z2;
-#pragma unroll
-            for (int k = 1; k <= M; k++) {
-                const float2 b = f2s(w.b[k - 1]);
-                ex = f2fma(b, f2sub(qvx[M + k - 1], qvx[M - k]), ex);
-                ey = f2fma(b, f2sub(lds2(svy + (cy + k - 1) * B::RC + cz), lds2(svy + (cy - k) * B::RC + cz)), ey);
-                ez = f2fma(b, make_float2(wvz[M + k - 1] - wvz[M - k], wvz[M + k] - wvz[M - k + 1]), ez);
-                const float2 xy = f2sub(lds2(svx + (cy + k) * B::RC + cz), lds2(svx + (cy - k + 1) * B::RC + cz));
-                const float2 yx = f2sub(qvy[M - 1 + k], qvy[M - k]);
-                gxy = f2fma(b, f2add(xy, yx), gxy);
-                const float2 zx = f2sub(qvz[M - 1 + k], qvz[M - k]);
-                const float2 xz = make_float2(wvx[M + k] - wvx[M - k + 1], wvx[M + k + 1] - wvx[M - k + 2]);
-                gxz = f2fma(b, f2add(xz, zx), gxz);
-                const float2 zy = f2sub(lds2(svz + (cy + k) * B::RC + cz), lds2(svz + (cy - k + 1) * B::RC + cz));
-                const float2 yz = make_float2(wvy[M + k] - wvy[M - k + 1], wvy[M + k + 1] - wvy[M - k + 2]);
-                gyz = f2fma(b, f2add(yz, zy), gyz);
-            }
-            const float exa = ex.x, exb = ex.y, eya = ey.x, eyb = ey.y, eza = ez.x, ezb = ez.y;
-            const float gxya = gxy.x, gxyb = gxy.y, gxza = gxz.x, gxzb = gxz.y, gyza = gyz.x, gyzb = gyz.y;
-            const float *T = S + L::OT + ii;
-            const float2 t0 = lds2(T), t1 = lds2(T + IS), t2 = lds2(T + 2 * IS);
-            const float2 t3 = lds2(T + 3 * IS), t4 = lds2(T + 4 * IS), t5 = lds2(T + 5 * IS);
-            const unsigned q = x * pl + q0;
-            if (MODE == 0) {
-                const float *R0 = S + L::OM0, *R1 = S + L::OM1;
-                const float2 m0 = lds2(R0 + ty * B::PC + c2), my = lds2(R0 + yb1 * B::PC + c2);
-                const float2 mx = lds2(R1 + ty * B::PC + c2), mxy_ = lds2(R1 + yb1 * B::PC + c2);
-                const float m0z = R0[ty * B::PC + zb2], myz = R0[yb1 * B::PC + zb2], mxz = R1[ty * B::PC + zb2];
-                const float2 l = lds2(S + L::OL + ii);
-                const float gxn = __ldg(g.tab + 2 * x), gxh = __ldg(g.tab + 2 * x + 1);
-                const float gn0 = gxn * gyn * gzn0, gn1 = gxn * gyn * gzn1;
-                // averages of mu over the 4 nodes around each edge (the pair's
-                // second lane is the first point's z+1 neighbour)
-                const float mxya = 0.25f * (m0.x + mx.x + my.x + mxy_.x);
-                const float mxza = 0.25f * (m0.x + mx.x + m0.y + mx.y);
-                const float myza = 0.25f * (m0.x + my.x + m0.y + my.y);
-                const float mxyb = 0.25f * (m0.y + mx.y + my.y + mxy_.y);
-                const float mxzb = 0.25f * (m0.y + mx.y + m0z + mxz);
-                const float myzb = 0.25f * (m0.y + my.y + m0z + myz);
-                const float tra = exa + eya + eza, trb = exb + eyb + ezb;
-                const float m2a = 2.f * m0.x, m2b = 2.f * m0.y;
-                st2(s.f[3], q, gn0 * (t0.x + c * (l.x * tra + m2a * exa)), gn1 * (t0.y + c * (l.y * trb + m2b * exb)));
-                st2(s.f[4], q, gn0 * (t1.x + c * (l.x * tra + m2a * eya)), gn1 * (t1.y + c * (l.y * trb + m2b * eyb)));
-                st2(s.f[5], q, gn0 * (t2.x + c * (l.x * tra + m2a * eza)), gn1 * (t2.y + c * (l.y * trb + m2b * ezb)));
-                st2(s.f[6], q, gxh * gyh * gzn0 * (t3.x + c * mxya * gxya), gxh * gyh * gzn1 * (t3.y + c * mxyb * gxyb));
-                st2(s.f[7], q, gxh * gyn * gzh0 * (t4.x + c * mxza * gxza), gxh * gyn * gzh1 * (t4.y + c * mxzb * gxzb));
-                st2(s.f[8], q, gxn * gyh * gzh0 * (t5.x + c * myza * gyza), gxn * gyh * gzh1 * (t5.y + c * myzb * gyzb));
-            } else if (MODE == 1) {
-                st2(s.f[3], q, t0.x - c * exa, t0.y - c * exb);
-                st2(s.f[4], q, t1.x - c * eya, t1.y - c * eyb);
-                st2(s.f[5], q, t2.x - c * eza, t2.y - c * ezb);
-                st2(s.f[6], q, t3.x - c * gxya, t3.y - c * gxyb);
-                st2(s.f[7], q, t4.x - c * gxza, t4.y - c * gxzb);
-                st2(s.f[8], q, t5.x - c * gyza, t5.y - c * gyzb);
-            } else {
-                const float2 gl = lds2(S + L::OG + ii), gm = lds2(S + L::OG + IS + ii);
-                st2(o.f[0], q, gl.x + c * (t0.x + t1.x + t2.x) * (exa + eya + eza),
-                    gl.y + c * (t0.y + t1.y + t2.y) * (exb + eyb + ezb));
-                st2(o.f[1], q, gm.x + 2.f * c * (t0.x * exa + t1.x * eya + t2.x * eza),
-                    gm.y + 2.f * c * (t0.y * exb + t1.y * eyb + t2.y * ezb));
-                // edge products summed over the steps (gathered onto the nodes at the end)
-                const float2 p3 = *reinterpret_cast<const float2 *>(o.f[2] + q);
-                const float2 p4 = *reinterpret_cast<const float2 *>(o.f[3] + q);
-                const float2 p5 = *reinterpret_cast<const float2 *>(o.f[4] + q);
-                st2(o.f[2], q, p3.x + c * t3.x * gxya, p3.y + c * t3.y * gxyb);
-                st2(o.f[3], q, p4.x + c * t4.x * gxza, p4.y + c * t4.y * gxzb);
-                st2(o.f[4], q, p5.x + c * t5.x * gyza, p5.y + c * t5.y * gyzb);
-            }
-        }
-#pragma unroll
-        for (int j = 0; j < Q - 1; j++) {
-            qvx[j] = qvx[j + 1];
-            qvy[j] = qvy[j + 1];
-            qvz[j] = qvz[j + 1];
-        }
+        t_plane<M, MODE>(g, w, s, o, sm + R.st * L::SZ, t, x, qvx, qvy, qvz);
         R.release(lane);
     }
 }

@@ -111,3 +111,94 @@ def test_acoustic_autograd_matches_oracle(env, snap):
     gw = wav.grad.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(gm - g_ref) / np.linalg.norm(g_ref) <= 1e-4
     assert np.linalg.norm(gw - q_ref) / np.linalg.norm(q_ref) <= 1e-5
+
+
+def _elastic_problem(nt=70):
+    p = synth.elastic_random(n=28, nbl=6, so=8, nt=nt, corr_len=60.0, rec_dx=30.0)
+    p.src[:, 2] = 4 * p.h                 # shallow source: signal at the surface receivers
+    return p
+
+
+def _lame(p, torch, dev):
+    """(lambda, mu, b) in SI units (Pa, Pa, m^3/kg) from the problem's vp, vs
+    [km/s] and rho [g/cc], in FP64, as float32 tensors."""
+    vp = p.model["vp"].astype(np.float64) * 1000.0
+    vs = p.model["vs"].astype(np.float64) * 1000.0
+    rho = p.model["rho"].astype(np.float64) * 1000.0
+    t = lambda a: torch.from_numpy(a.astype(np.float32)).to(dev)
+    return t(rho * (vp ** 2 - 2 * vs ** 2)), t(rho * vs ** 2), t(1.0 / rho)
+
+
+def _elastic_spec(ag, p, torch, dev, **kw):
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(dev)
+    return ag.Spec((p.nx, p.ny, p.nz), p.nbl, p.h, p.so, p.nt, p.dt, t(p.src), t(p.rec), **kw)
+
+
+@pytest.mark.parametrize("snap", ["full", "ckpt32"])
+def test_elastic_autograd_matches_oracle(env, snap):
+    """ElasticModelling: the wrapper converts (lambda, mu, b) to (vp, vs, rho)
+    and the library rebuilds lambda, mu; dL/d(lambda, mu, b) for an arbitrary
+    trace cotangent must equal the oracle's exact gradient (residual = the
+    cotangent) and dL/dwavelet the oracle's adjoint at the source."""
+    torch, wp, ag = env
+    dev = torch.device("cuda", 0)
+    p = _elastic_problem()
+    o = oracle.Problem(p)
+    gtr = np.random.default_rng(4).standard_normal((p.rec.shape[0], p.nt))
+    g_ref, _ = o.gradient(o.forward() - gtr)
+    q_ref = o.adjoint(gtr)
+    mode = {"full": wp.SNAP_FULL_FP32, "ckpt32": wp.SNAP_CKPT_FP32}[snap]
+    spec = _elastic_spec(ag, p, torch, dev, snap_mode=mode, ckpt_interval=9)
+    lam, mu, b = [x.requires_grad_(True) for x in _lame(p, torch, dev)]
+    wav = torch.from_numpy(p.wavelet).to(dev).requires_grad_(True)
+    tr = ag.ElasticModelling.apply(lam, mu, b, wav, spec)
+    tr.backward(torch.from_numpy(gtr.astype(np.float32)).to(dev))
+    for name, x, ref in (("lambda", lam, g_ref[0]), ("mu", mu, g_ref[1]), ("b", b, g_ref[2])):
+        g = x.grad.cpu().numpy().astype(np.float64)
+        e = np.linalg.norm(g - ref) / np.linalg.norm(ref)
+        assert e <= 1e-4, (name, e)
+    gw = wav.grad.cpu().numpy().astype(np.float64)
+    assert np.linalg.norm(gw - q_ref) / np.linalg.norm(q_ref) <= 1e-5
+
+
+def test_elastic_taylor_through_autograd(env):
+    """J(lambda, mu, b) = 0.5 ||F - d||^2 through autograd: first-order
+    remainder O(h), second-order remainder O(h^2).  Direction: the gradient
+    itself, zero within two cells of the faces, scaled to 1 % of each
+    parameter's mean (a joint random direction nearly cancels in <g, dm>
+    and leaves the first-order term below the second-order one)."""
+    torch, wp, ag = env
+    dev = torch.device("cuda", 0)
+    p = _elastic_problem(nt=80)
+    d_obs = torch.from_numpy(oracle.Problem(p).forward().astype(np.float32)).to(dev)
+    lam, mu, b = _lame(p, torch, dev)
+    sm = synth.smooth_model(p.model, 2.0, keys=("vp", "vs", "rho"))
+    p0 = synth.Problem(**{**p.__dict__, "model": sm})
+    lam0, mu0, b0 = [x.requires_grad_(True) for x in _lame(p0, torch, dev)]
+    spec = _elastic_spec(ag, p, torch, dev)
+    wav = torch.from_numpy(p.wavelet).to(dev)
+
+    def J(l, m_, bb):
+        tr = ag.ElasticModelling.apply(l, m_, bb, wav, spec)
+        return 0.5 * torch.sum((tr.double() - d_obs.double()) ** 2)
+
+    J0 = J(lam0, mu0, b0)
+    J0.backward()
+    shp = tuple(lam0.shape)
+    mask = torch.zeros(shp, dtype=torch.float64, device=dev)
+    mask[2:-2, 2:-2, 2:-2] = 1.0
+    dirs = []
+    for x in (lam0, mu0, b0):
+        g = x.grad.double() * mask
+        dirs.append(-g / g.abs().max() * 0.01 * x.detach().double().abs().mean())
+    lin = float(sum(torch.sum(x.grad.double() * d) for x, d in zip((lam0, mu0, b0), dirs)))
+    e1, e2 = [], []
+    with torch.no_grad():
+        for hh in (1.0, 0.5, 0.25, 0.125):
+            Jh = float(J(*[(x.detach().double() + hh * d).float() for x, d in zip((lam0, mu0, b0), dirs)]))
+            e1.append(abs(Jh - float(J0)))
+            e2.append(abs(Jh - float(J0) - hh * lin))
+    s1 = [math.log(e1[i] / e1[i + 1], 2) for i in range(3)]
+    s2 = [math.log(e2[i] / e2[i + 1], 2) for i in range(3)]
+    assert all(abs(s - 1.0) < 0.15 for s in s1), s1
+    assert all(s > 1.8 for s in s2[:2]), (s2, e2)

@@ -162,3 +162,40 @@ def test_one_step_sampled_full_size(wp):
         got = out[c].reshape(-1)[idx]
         err = np.max(np.abs(got - ref[:, c])) / np.max(np.abs(ref[:, c]))
         assert err <= TOL, (c, err)
+
+
+def test_full_size_whole_grid_multistep(wp):
+    """The elastic workload at its own size (256^3 + 20-cell layer = 296^3,
+    so 8, its smooth random model): all nine fields over the whole grid
+    after 200 source-free steps from a seeded smooth state, against 200
+    FP64 oracle steps.  Each field within 1e-5 of the oracle's norm."""
+    p = synth.elastic_random(n=256, nbl=20, so=8, nt=10)
+    prop = wp.Propagator.from_problem(p)
+    st = synth.random_state(9, prop.grid, 21, sigma_cells=3.0)
+    prop.set_state(st)
+    prop.step(200)
+    gpu = prop.get_state()
+    prop.close()
+    ref = oracle.Problem(p).el_run_d(np.stack(st), 200)
+    for f in range(9):
+        e = rel(gpu[f], ref[f])
+        assert e <= TOL, (f, e)
+
+
+def test_full_size_dot_product(wp):
+    """Adjoint test at the workload's own size and length: <F q, d> =
+    <q, F^T d> for a seeded random wavelet q and traces d (4096 surface
+    receivers, 1000 steps: the wave from the centre reaches the surface),
+    the FP32 products accumulated in FP64."""
+    p = synth.elastic_random(n=256, nbl=20, so=8, nt=1000)
+    prop = wp.Propagator.from_problem(p)
+    rng = np.random.default_rng(9)
+    q = rng.standard_normal(p.wavelet.shape).astype(np.float32)
+    d = rng.standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    Fq = prop.forward(q, p.src, p.rec).astype(np.float64)
+    Ftd = prop.adjoint(d, p.src, p.rec).astype(np.float64)
+    prop.close()
+    lhs = float(np.sum(Fq * d))
+    rhs = float(np.sum(q.astype(np.float64) * Ftd))
+    assert np.max(np.abs(Fq)) > 0
+    assert abs(lhs - rhs) <= 1e-5 * max(abs(lhs), abs(rhs)), (lhs, rhs)
