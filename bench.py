@@ -532,13 +532,15 @@ def gradient_aniso_cost(wp, torch, dev, small=False):
     return out
 
 
-def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
+def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti", windows=None):
     """Batched gradients (TTI so 12 or elastic so 8, BF16 checkpoints): shots
     on windows of one large model with nx, ny ~ U[200, 600], nz = 300 (+
     40-cell layer); shots/hour of one prop_gradient call after another
     against one prop_gradient_batch call over the same shots (results
     compared bitwise)."""
     kw = dict(size_range=(60, 120), nz=80) if small else {}
+    if windows:
+        kw.update(size_range=windows[:2], nz=windows[2])
     shots = (synth.tti_batch_shots if kind == "tti" else synth.elastic_batch_shots)(nshots, nt, **kw)
     stream = torch.cuda.current_stream(dev).cuda_stream
     to = lambda a: torch.from_numpy(a).to(dev)
@@ -571,6 +573,16 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
         grads, J = wp.gradient_batch(props, wav, src, rec, obs)
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t0
+    shared, alone = wp.batch_stats()
+    # the same waves with every shot on its own launches
+    os.environ["WAVEPROP_BATCH_LAUNCH"] = "0"
+    with timed_region():
+        t0 = time.perf_counter()
+        grads2, _ = wp.gradient_batch(props, wav, src, rec, obs)
+        torch.cuda.synchronize()
+        t_own = time.perf_counter() - t0
+    del os.environ["WAVEPROP_BATCH_LAUNCH"]
+    same_own = all(bool(torch.equal(g, s_)) for g, s_ in zip(grads, grads2))
     same = all(bool(torch.equal(g, s[0])) for g, s in zip(grads, seq))
     waves = wp.plan_waves([p.gradient_bytes(r.shape[0]) for p, r in zip(props, rec)],
                           int(torch.cuda.mem_get_info(dev)[0] * 0.9))[1]
@@ -580,8 +592,9 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti"):
             "windows": [s[1].name for s in shots], "points_total": npts,
             "sequential": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq},
             "batched": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
-                        "waves": waves},
-            "bitwise_equal": same}
+                        "waves": waves, "shared_launch_rounds": shared, "unshared_rounds": alone},
+            "batched_own_launches": {"seconds": t_own, "shots_per_hour": 3600.0 * nshots / t_own},
+            "bitwise_equal": same and same_own}
 
 
 def run_extras(wp, torch, dev, args, extras):
@@ -624,6 +637,9 @@ def run_extras(wp, torch, dev, args, extras):
         _clocked(out, "gradaniso", lambda: gradient_aniso_cost(wp, torch, dev, small=args.small))
     if "gradsmall" in extras:
         _clocked(out, "gradsmall", lambda: gradient_small(wp, torch, dev))
+    if "batchsmall" in extras:       # many small windows: 40-80 x 40-80 x 60 cells
+        _clocked(out, "batchsmall", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
+                                                                 kind="tti", windows=(40, 80, 60)))
     if "batch" in extras:
         _clocked(out, "batch", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
                                             small=args.small, kind=args.batch_kind))

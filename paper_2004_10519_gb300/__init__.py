@@ -88,6 +88,7 @@ def lib():
         L.prop_profile.argtypes = [vp, C.c_int]
         L.prop_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.prop_fp32_peak.argtypes = [C.POINTER(C.c_double)]
+        L.prop_batch_stats.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
         L.prop_last_launches.restype = C.c_longlong
         L.prop_last_launches.argtypes = [vp]
         _lib = L
@@ -386,3 +387,12 @@ def gradient_batch(props, wavelets, srcs, recs, d_obs, outs=None, budget_bytes=0
     if rc:
         raise PropError(rc, lib().prop_last_error(None).decode())
     return grads, [J[i] for i in range(n)]
+
+
+def batch_stats():
+    """Rounds of TTI steps of the last ``gradient_batch`` call that shared one
+    launch per pass across the shots of a wave, and rounds launched shot by
+    shot (measurement hook ``prop_batch_stats``, not in the public header)."""
+    a, b = C.c_longlong(), C.c_longlong()
+    lib().prop_batch_stats(C.byref(a), C.byref(b))
+    return a.value, b.value

@@ -105,6 +105,10 @@ struct prop_s {
     int graph_adj = -1, graph_xc = 0;
     long long graph_launches = 0;   // kernels in one replay
     float *graph_st[9] = {};
+    // batched shots: the TTI steps of this handle meet those of the other
+    // shots of its wave and share one launch per pass (prop_gradient_batch)
+    struct StepRendezvous *rdv = nullptr;
+    int rdv_idx = -1;
 };
 
 // ---------------------------------------------------------------------------
@@ -167,6 +171,28 @@ int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
 // transposed elastic step in the variables (b_avg vbar, g C tbar): the
 // forward step with dt -> -dt
 int el_step_adjoint_u(prop_s *P, float *const *S);
+
+// batched TTI steps (stencil_tma.cu): one rotation and one update launch for
+// the steps of several shots (TMA path, centred operators, same space order
+// and step kind).  A request is one shot's step as tti_launch_step takes it.
+struct TtiBatchReq {
+    prop_s *P;
+    float *S[4];
+    bool adjoint;
+    const float *up, *ur;
+    float *grad;
+};
+struct TtiBatch;             // device tables and host staging of a batch
+TtiBatch *tti_batch_new();
+void tti_batch_free(TtiBatch *b);
+// 0: launched on `stream`; 1: the requests cannot share a launch (the caller
+// launches them one by one); < 0: error (message in *err)
+int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t stream, std::string *err);
+// true if the handle's TTI steps can join a batched launch
+bool tti_batchable(const prop_s *P);
+// a TTI step of a shot taking part in a rendezvous (runtime.cu): waits for
+// the other shots of the wave and shares their launch
+int rdv_tti_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r, float *grad);
 
 // sparse ops (sparse.cu)
 // Host-side trilinear tables of n points (metres, origin at the first

@@ -14,7 +14,9 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <condition_variable>
 #include <memory>
+#include <thread>
 
 static thread_local std::string tl_err;
 
@@ -1492,6 +1494,130 @@ extern "C" int prop_gradient(prop_t *P, const float *wavelet, const float *src_x
 // ---------------------------------------------------------------------------
 #include <thread>
 
+// ---------------------------------------------------------------------------
+// Rendezvous of the TTI steps of one wave.  Every shot runs its own
+// prop_gradient on its own host thread and stream; the shots' sweeps issue
+// their steps in the same order (same nt, storage mode and checkpoint
+// interval), so the k-th step of each shot can share one launch per pass.
+// A step records an event on the shot's stream and waits for the other
+// participants; the last to arrive makes a shared stream wait on all the
+// events, launches the batched passes (tile table over all shots), records
+// `done`, and each shot's stream waits on `done` before its next work.
+// Shots leave the group when their gradient returns, so participants with
+// other step sequences never wait for each other; steps of different kinds
+// met in one round are launched one by one.
+// ---------------------------------------------------------------------------
+struct StepRendezvous {
+    std::mutex mu;
+    std::condition_variable cv;
+    int active = 0, arrived = 0;
+    unsigned long long gen = 0;
+    std::vector<TtiBatchReq> req;
+    std::vector<char> present;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> result;      // 0 launched, 1 launch alone, < 0 error
+    cudaStream_t cs = nullptr;
+    cudaEvent_t done[2] = {};
+    TtiBatch *tb = nullptr;
+    std::string err;
+    long long batched = 0, alone = 0;
+
+    ~StepRendezvous()
+    {
+        if (cs) cudaStreamSynchronize(cs);
+        tti_batch_free(tb);
+        for (auto e : ev)
+            if (e) cudaEventDestroy(e);
+        for (auto e : done)
+            if (e) cudaEventDestroy(e);
+        if (cs) cudaStreamDestroy(cs);
+    }
+    int init(int n)
+    {
+        req.resize(n);
+        present.assign(n, 0);
+        ev.assign(n, nullptr);
+        result.assign(n, 0);
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return PROP_ECUDA;
+        for (auto &e : ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PROP_ECUDA;
+        for (auto &e : done)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PROP_ECUDA;
+        tb = tti_batch_new();
+        return PROP_OK;
+    }
+    // with the lock held, by the last participant to arrive
+    void launch_all()
+    {
+        std::vector<TtiBatchReq> r;
+        std::vector<int> who;
+        for (size_t i = 0; i < req.size(); i++)
+            if (present[i]) {
+                r.push_back(req[i]);
+                who.push_back((int)i);
+                cudaStreamWaitEvent(cs, ev[i], 0);
+            }
+        int rc = tti_batch_step(tb, r.data(), (int)r.size(), cs, &err);
+        if (rc == PROP_OK && cudaEventRecord(done[gen & 1], cs) != cudaSuccess) {
+            err = "batched TTI step: event record failed";
+            rc = PROP_ECUDA;
+        }
+        if (rc == PROP_OK) batched++;
+        else if (rc == 1) alone++;
+        for (int i : who) {
+            result[i] = rc;
+            present[i] = 0;
+        }
+        arrived = 0;
+        gen++;
+        cv.notify_all();
+    }
+    void leave()
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        active--;
+        if (active > 0 && arrived == active) launch_all();
+    }
+};
+
+int rdv_tti_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r, float *grad)
+{
+    StepRendezvous *R = P->rdv;
+    const int i = P->rdv_idx;
+    int res;
+    cudaEvent_t d;
+    {
+        std::unique_lock<std::mutex> lk(R->mu);
+        WP_CK(P, cudaEventRecord(R->ev[i], P->stream));
+        R->req[i] = TtiBatchReq{P, {S[0], S[1], S[2], S[3]}, adjoint, img_p, img_r, grad};
+        R->present[i] = 1;
+        const unsigned long long my = R->gen;
+        if (++R->arrived == R->active) R->launch_all();
+        else R->cv.wait(lk, [&] { return R->gen != my; });
+        res = R->result[i];
+        d = R->done[my & 1];
+        if (res < 0) return wp_fail(P, res, R->err);
+    }
+    if (res == 1) {                 // could not share the launch: this shot alone
+        P->rdv = nullptr;
+        const int rc = tti_launch_step(P, S, adjoint, img_p, img_r, grad);
+        P->rdv = R;
+        return rc;
+    }
+    WP_CK(P, cudaStreamWaitEvent(P->stream, d, 0));
+    return PROP_OK;
+}
+
+// shared TTI step launches of the last prop_gradient_batch call: rounds
+// launched together, rounds whose steps had to be launched one by one
+static long long batch_stats[2] = {0, 0};
+extern "C" int prop_batch_stats(long long *shared, long long *alone)
+{
+    if (shared) *shared = batch_stats[0];
+    if (alone) *alone = batch_stats[1];
+    return PROP_OK;
+}
+
 extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
                                    const float *const *src_xyz, const int *nsrc,
                                    const float *const *rec_xyz, const int *nrec,
@@ -1521,12 +1647,42 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
     const int nw = prop_plan_waves(need.data(), nshots, budget_bytes, wave.data());
     std::vector<int> rc(nshots, PROP_OK);
     std::vector<double> mis(nshots, 0.0);
+    batch_stats[0] = batch_stats[1] = 0;
+    // shared launches for the TTI steps of a wave (WAVEPROP_BATCH_LAUNCH=0:
+    // every shot launches its own)
+    const char *bl = getenv("WAVEPROP_BATCH_LAUNCH");
+    const bool share = !(bl && !strcmp(bl, "0"));
     for (int w = 0; w < nw; w++) {
+        std::unique_ptr<StepRendezvous> rdv;
+        int nb = 0;
+        for (int i = 0; i < nshots; i++)
+            if (wave[i] == w && tti_batchable(shots[i]) && !shots[i]->broken) nb++;
+        if (share && nb >= 2) {
+            rdv.reset(new StepRendezvous());
+            if (rdv->init(nshots) != PROP_OK) rdv.reset();
+            else rdv->active = nb;
+        }
+        for (int i = 0; i < nshots; i++)
+            if (rdv && wave[i] == w && tti_batchable(shots[i]) && !shots[i]->broken) {
+                shots[i]->rdv = rdv.get();
+                shots[i]->rdv_idx = i;
+            }
         std::vector<std::thread> th;
         for (int i = 0; i < nshots; i++) {
             if (wave[i] != w) continue;
             th.emplace_back([&, i] {
                 prop_s *P = shots[i];
+                struct Leave {       // leave the rendezvous on every way out
+                    prop_s *P;
+                    ~Leave()
+                    {
+                        if (P->rdv) {
+                            P->rdv->leave();
+                            P->rdv = nullptr;
+                            P->rdv_idx = -1;
+                        }
+                    }
+                } leave_rdv{P};
                 if (cudaSetDevice(dev) != cudaSuccess) {
                     rc[i] = wp_fail(P, PROP_ECUDA, "cudaSetDevice failed");
                     return;
@@ -1548,6 +1704,11 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
                 P->stream = s;
                 rc[i] = prop_gradient(P, wavelet[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i], d_obs[i],
                                       grad[i], &mis[i]);
+                if (P->rdv) {                         // no more steps from this shot
+                    P->rdv->leave();
+                    P->rdv = nullptr;
+                    P->rdv_idx = -1;
+                }
                 cudaStreamSynchronize(s);
                 if (!rc[i]) rc[i] = prop_trim(P);     // the next waves get this shot's work arrays
                 cudaEventRecord(e1, s);
@@ -1560,6 +1721,10 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
             });
         }
         for (auto &t : th) t.join();
+        if (rdv) {
+            batch_stats[0] += rdv->batched;
+            batch_stats[1] += rdv->alone;
+        }
     }
     int first = PROP_OK;
     for (int i = 0; i < nshots; i++) {

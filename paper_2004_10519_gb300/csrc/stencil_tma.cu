@@ -33,6 +33,11 @@
 // with n_z >= 0; the operators are quadratic in n, so n and -n agree).
 #include "tma.cuh"
 
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
 namespace {
 
 struct F9 {
@@ -463,12 +468,13 @@ struct RMaps {
     CUtensorMap p, r, qp, qr, nx, ny;
 };
 
-template <int M, bool RAW = false>
-__global__ void __launch_bounds__(NTP, 2)
-tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
-            const __grid_constant__ RMaps mp, float *__restrict__ ex, float *__restrict__ ey,
-            float *__restrict__ ez, float *__restrict__ fx, float *__restrict__ fy, float *__restrict__ fz,
-            int xc, int *err)
+// one tile (bx, by: 32 z x 16 y columns; bz: x chunk of xc planes)
+template <int M, bool RAW>
+WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict__ p,
+                         const float *__restrict__ r, const RMaps &mp, float *__restrict__ ex,
+                         float *__restrict__ ey, float *__restrict__ ez, float *__restrict__ fx,
+                         float *__restrict__ fy, float *__restrict__ fz, int bx, int by, int bz, int xc,
+                         int *err)
 {
     using L = RL<M>;
     using B = BX<M>;
@@ -477,9 +483,9 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + L::NS * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, lane = (ty * TZ2 + tz) & 31;
     const bool lead = ty == 0 && tz == 0;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z0 = bx * FZ, y0 = by * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
+    const int xa = bz * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
         uint64_t *bar = &bars[st];
@@ -583,6 +589,16 @@ tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restri
     }
 }
 
+template <int M, bool RAW = false>
+__global__ void __launch_bounds__(NTP, 2)
+tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
+            const __grid_constant__ RMaps mp, float *__restrict__ ex, float *__restrict__ ey,
+            float *__restrict__ ez, float *__restrict__ fx, float *__restrict__ fy, float *__restrict__ fz,
+            int xc, int *err)
+{
+    tti_rot_body<M, RAW>(g, w, p, r, mp, ex, ey, ez, fx, fy, fz, blockIdx.x, blockIdx.y, blockIdx.z, xc, err);
+}
+
 // ---------------------------------------------------------------------------
 // TTI update pass.  ADJ = 1: the transposed step, which also writes
 // zeta = C lam of the new level (zp, zr) for the next rotation pass.
@@ -613,11 +629,10 @@ struct UMaps {
 };
 
 template <int M, int ADJ, int GRAD>
-__global__ void __launch_bounds__(NTP, 2)
-tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
-            const __grid_constant__ UMaps mp, float *__restrict__ pp, float *__restrict__ rp,
-            float *__restrict__ grad, float *__restrict__ zp, float *__restrict__ zr, int *flag, int check,
-            int xc, int *err)
+WP_DEV void tti_upd_body(const GridDev &g, const FDW &w, const float *__restrict__ ex,
+                         const float *__restrict__ fx, const UMaps &mp, float *__restrict__ pp,
+                         float *__restrict__ rp, float *__restrict__ grad, float *__restrict__ zp,
+                         float *__restrict__ zr, int *flag, int check, int bx, int by, int bz, int xc, int *err)
 {
     using L = UL<M, ADJ, GRAD>;
     using B = BX<M>;
@@ -626,9 +641,9 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
     const bool lead = warp == 0 && lane == 0;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
+    const int z0 = bx * FZ, y0 = by * FY;
     const int z = z0 + 2 * tz, y = y0 + ty;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
+    const int xa = bz * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) {
         float *S = sm + st * L::SZ;
         float *I = S + L::OI;
@@ -767,6 +782,56 @@ tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restr
         }
         R.release(lane);
     }
+}
+
+template <int M, int ADJ, int GRAD>
+__global__ void __launch_bounds__(NTP, 2)
+tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
+            const __grid_constant__ UMaps mp, float *__restrict__ pp, float *__restrict__ rp,
+            float *__restrict__ grad, float *__restrict__ zp, float *__restrict__ zr, int *flag, int check,
+            int xc, int *err)
+{
+    tti_upd_body<M, ADJ, GRAD>(g, w, ex, fx, mp, pp, rp, grad, zp, zr, flag, check, blockIdx.x, blockIdx.y,
+                               blockIdx.z, xc, err);
+}
+
+// ---------------------------------------------------------------------------
+// Batched shots (Sec. III-B: many independent experiments): one launch of
+// each pass serves every shot of a wave.  Each CTA takes its tile
+// (shot, z tile, y tile, x chunk) from a table and its shot's grid, arrays
+// and tensor maps from a per-shot entry in device memory (the maps are
+// encoded on the host before the launch and never change during it).
+// ---------------------------------------------------------------------------
+struct TtiShot {
+    RMaps rm;
+    UMaps um;
+    GridDev g;
+    const float *rp, *rr;    // rotation input: (p, r), or zeta = C lam
+    float *t[8];             // intermediates ex ey ez fx fy fz, zeta p, r
+    float *pn, *rn;          // new level (written over the oldest)
+    float *grad;
+    int *flag;
+    int check, xc;
+};
+
+template <int M>
+__global__ void __launch_bounds__(NTP, 2)
+tti_rot_batch(const TtiShot *__restrict__ shots, const int4 *__restrict__ tiles, FDW w)
+{
+    const int4 tl = tiles[blockIdx.x];
+    const TtiShot &S = shots[tl.x];
+    tti_rot_body<M, false>(S.g, w, S.rp, S.rr, S.rm, S.t[0], S.t[1], S.t[2], S.t[3], S.t[4], S.t[5], tl.y, tl.z,
+                           tl.w, S.xc, S.flag);
+}
+
+template <int M, int ADJ, int GRAD>
+__global__ void __launch_bounds__(NTP, 2)
+tti_upd_batch(const TtiShot *__restrict__ shots, const int4 *__restrict__ tiles, FDW w)
+{
+    const int4 tl = tiles[blockIdx.x];
+    const TtiShot &S = shots[tl.x];
+    tti_upd_body<M, ADJ, GRAD>(S.g, w, S.t[0], S.t[3], S.um, S.pn, S.rn, S.grad, S.t[6], S.t[7], S.flag, S.check,
+                               tl.y, tl.z, tl.w, S.xc, S.flag);
 }
 
 // ---------------------------------------------------------------------------
@@ -1365,6 +1430,205 @@ int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
     }
     prof_end(P, adjoint ? 1 : 0);
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// batched TTI steps: tables and launches
+// ---------------------------------------------------------------------------
+struct TtiBatch {
+    // tile table (shot, z tile, y tile, x chunk), rebuilt when the shots'
+    // shapes or x-extents change; shots with more tiles first, so the
+    // longest work starts first
+    std::vector<long long> sig;
+    std::vector<int4> htiles;
+    int4 *dtiles = nullptr;
+    size_t tiles_cap = 0;
+    // per-shot entries: device buffer, and pinned host staging in a ring of
+    // slots (a slot is refilled only after its copy has run)
+    TtiShot *dshots = nullptr;
+    size_t shots_cap = 0;
+    static constexpr int NSLOT = 8;
+    TtiShot *hshots[NSLOT] = {};
+    cudaEvent_t copied[NSLOT] = {};
+    size_t hcap = 0;
+    unsigned long long calls = 0;
+};
+
+TtiBatch *tti_batch_new() { return new TtiBatch(); }
+
+void tti_batch_free(TtiBatch *b)
+{
+    if (!b) return;
+    cudaFree(b->dtiles);
+    cudaFree(b->dshots);
+    for (int i = 0; i < TtiBatch::NSLOT; i++) {
+        if (b->copied[i]) {
+            cudaEventSynchronize(b->copied[i]);
+            cudaEventDestroy(b->copied[i]);
+        }
+        cudaFreeHost(b->hshots[i]);
+    }
+    delete b;
+}
+
+bool tti_batchable(const prop_s *P)
+{
+    return P->d.kind == PROP_TTI && P->d.tti_operator == 0 && tma_usable(P);
+}
+
+template <int M, int ADJ, int GRAD>
+int tti_batch_launch(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    using B = BX<M>;
+    // per-shot entries into the next staging slot
+    const int slot = (int)(b->calls++ % TtiBatch::NSLOT);
+    if (b->copied[slot] && cudaEventSynchronize(b->copied[slot]) != cudaSuccess) {
+        *err = "batched TTI step: staging wait failed";
+        return PROP_ECUDA;
+    }
+    TtiShot *H = b->hshots[slot];
+    for (int i = 0; i < n; i++) {
+        prop_s *P = req[i].P;
+        float *const *S = req[i].S;
+        float *const *t = P->tmp;
+        TtiShot &e = H[i];
+        const float *rp_ = ADJ ? t[6] : S[0], *rr_ = ADJ ? t[7] : S[1];
+        bool ok = map_of(P, rp_, B::RC, B::RR, &e.rm.p) && map_of(P, rr_, B::RC, B::RR, &e.rm.r) &&
+                  map_of(P, rp_, FZ, FY, &e.rm.qp) && map_of(P, rr_, FZ, FY, &e.rm.qr) &&
+                  map_of(P, P->nrm[0], FZ, FY, &e.rm.nx) && map_of(P, P->nrm[1], FZ, FY, &e.rm.ny) &&
+                  map_of(P, t[1], B::YC, B::YR, &e.um.ey) && map_of(P, t[4], B::YC, B::YR, &e.um.fy) &&
+                  map_of(P, t[2], B::ZC, B::ZR, &e.um.ez) && map_of(P, t[5], B::ZC, B::ZR, &e.um.fz) &&
+                  map_of(P, t[0], FZ, FY, &e.um.qe) && map_of(P, t[3], FZ, FY, &e.um.qf) &&
+                  map_of(P, P->m, FZ, FY, &e.um.m) && map_of(P, S[0], FZ, FY, &e.um.pc) &&
+                  map_of(P, S[1], FZ, FY, &e.um.rc) && map_of(P, S[2], FZ, FY, &e.um.pp) &&
+                  map_of(P, S[3], FZ, FY, &e.um.rp) && map_of(P, P->eps, FZ, FY, &e.um.e) &&
+                  map_of(P, P->del, FZ, FY, &e.um.d);
+        if (GRAD)
+            ok = ok && map_of(P, req[i].up, FZ, FY, &e.um.up) && map_of(P, req[i].ur, FZ, FY, &e.um.ur) &&
+                 map_of(P, req[i].grad, FZ, FY, &e.um.g);
+        if (!ok) {
+            *err = "cuTensorMapEncodeTiled failed";
+            return PROP_ECUDA;
+        }
+        e.g = P->g;
+        e.rp = rp_;
+        e.rr = rr_;
+        for (int k = 0; k < 8; k++) e.t[k] = t[k];
+        e.pn = S[2];
+        e.rn = S[3];
+        e.grad = req[i].grad;
+        e.flag = P->flag;
+        e.check = P->d.check_nan;
+        e.xc = P->xchunk;
+    }
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    if (int rc = ck(cudaMemcpyAsync(b->dshots, H, n * sizeof(TtiShot), cudaMemcpyHostToDevice, st),
+                    "batched TTI step: shot table copy"))
+        return rc;
+    if (int rc = ck(cudaEventRecord(b->copied[slot], st), "batched TTI step: event")) return rc;
+    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64,
+                 s2 = NSTAGE * UL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_rot_batch<M>, s1) && set_smem(tti_upd_batch<M, ADJ, GRAD>, s2);
+    (void)attr;
+    const unsigned nt = (unsigned)b->htiles.size();
+    const dim3 blk(TZ2, FY + 2, 1);
+    tti_rot_batch<M><<<nt, blk, s1, st>>>(b->dshots, b->dtiles, req[0].P->w);
+    tti_upd_batch<M, ADJ, GRAD><<<nt, blk, s2, st>>>(b->dshots, b->dtiles, req[0].P->w);
+    for (int i = 0; i < n; i++) req[i].P->kern_launches += 2;
+    return ck(cudaGetLastError(), "batched TTI step launch");
+}
+
+int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    if (n < 1) return PROP_OK;
+    const prop_s *P0 = req[0].P;
+    const bool grad = req[0].grad != nullptr;
+    for (int i = 0; i < n; i++) {
+        const prop_s *P = req[i].P;
+        if (!tti_batchable(P) || P->M != P0->M || req[i].adjoint != req[0].adjoint ||
+            (req[i].grad != nullptr) != grad || (grad && !req[0].adjoint) ||
+            memcmp(&P->w, &P0->w, sizeof(FDW)) != 0)
+            return 1;
+    }
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    // tile table (cached while the shapes and x-extents stay the same)
+    std::vector<long long> sig;
+    for (int i = 0; i < n; i++) {
+        const GridDev &g = req[i].P->g;
+        sig.insert(sig.end(), {(long long)g.NX, (long long)g.NY, (long long)g.NZ, (long long)req[i].P->xchunk});
+    }
+    if (sig != b->sig) {
+        std::vector<std::pair<long long, int>> order;
+        for (int i = 0; i < n; i++) order.emplace_back(-req[i].P->g.N, i);
+        std::stable_sort(order.begin(), order.end());
+        b->htiles.clear();
+        for (auto &o : order) {
+            const int i = o.second;
+            const GridDev &g = req[i].P->g;
+            const int xc = req[i].P->xchunk;
+            const int tz = (g.NZ + FZ - 1) / FZ, tyy = (g.NY + FY - 1) / FY, tx = (g.NX + xc - 1) / xc;
+            for (int c = 0; c < tx; c++)
+                for (int y = 0; y < tyy; y++)
+                    for (int z = 0; z < tz; z++) b->htiles.push_back(make_int4(i, z, y, c));
+        }
+        if (b->htiles.size() > b->tiles_cap) {
+            cudaFree(b->dtiles);
+            b->dtiles = nullptr;
+            b->tiles_cap = 0;
+            if (int rc = ck(cudaMalloc(&b->dtiles, b->htiles.size() * sizeof(int4)), "batched TTI tile table"))
+                return rc;
+            b->tiles_cap = b->htiles.size();
+        }
+        if (int rc = ck(cudaMemcpyAsync(b->dtiles, b->htiles.data(), b->htiles.size() * sizeof(int4),
+                                        cudaMemcpyHostToDevice, st),
+                        "batched TTI tile table copy"))
+            return rc;
+        if (int rc = ck(cudaStreamSynchronize(st), "batched TTI tile table copy")) return rc;
+        b->sig = sig;
+    }
+    if ((size_t)n > b->shots_cap) {
+        cudaFree(b->dshots);
+        b->dshots = nullptr;
+        b->shots_cap = 0;
+        if (int rc = ck(cudaMalloc(&b->dshots, n * sizeof(TtiShot)), "batched TTI shot table")) return rc;
+        b->shots_cap = n;
+    }
+    if ((size_t)n > b->hcap) {
+        for (int i = 0; i < TtiBatch::NSLOT; i++) {
+            if (b->copied[i]) cudaEventSynchronize(b->copied[i]);
+            cudaFreeHost(b->hshots[i]);
+            b->hshots[i] = nullptr;
+        }
+        b->hcap = 0;
+        for (int i = 0; i < TtiBatch::NSLOT; i++) {
+            if (int rc = ck(cudaMallocHost(&b->hshots[i], n * sizeof(TtiShot)), "batched TTI staging")) return rc;
+            if (!b->copied[i])
+                if (int rc = ck(cudaEventCreateWithFlags(&b->copied[i], cudaEventDisableTiming),
+                                "batched TTI staging event"))
+                    return rc;
+        }
+        b->hcap = n;
+    }
+    const bool adj = req[0].adjoint;
+    switch (P0->M) {
+    case 2: return adj ? (grad ? tti_batch_launch<2, 1, 1>(b, req, n, st, err) : tti_batch_launch<2, 1, 0>(b, req, n, st, err))
+                       : tti_batch_launch<2, 0, 0>(b, req, n, st, err);
+    case 4: return adj ? (grad ? tti_batch_launch<4, 1, 1>(b, req, n, st, err) : tti_batch_launch<4, 1, 0>(b, req, n, st, err))
+                       : tti_batch_launch<4, 0, 0>(b, req, n, st, err);
+    case 6: return adj ? (grad ? tti_batch_launch<6, 1, 1>(b, req, n, st, err) : tti_batch_launch<6, 1, 0>(b, req, n, st, err))
+                       : tti_batch_launch<6, 0, 0>(b, req, n, st, err);
+    case 8: return adj ? (grad ? tti_batch_launch<8, 1, 1>(b, req, n, st, err) : tti_batch_launch<8, 1, 0>(b, req, n, st, err))
+                       : tti_batch_launch<8, 0, 0>(b, req, n, st, err);
+    }
+    return 1;
 }
 
 // centred first derivatives D p (out[0..2]) and D r (out[3..5]) through the

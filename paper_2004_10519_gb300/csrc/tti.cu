@@ -25,6 +25,7 @@
 int tti_launch_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
                     float *grad)
 {
+    if (P->rdv && tti_batchable(P)) return rdv_tti_step(P, S, adjoint, img_p, img_r, grad);
     if (P->d.tti_operator == 1) return tti_sp_launch(P, S, adjoint, img_p, img_r, grad);
     return tma_usable(P) ? tti_launch_tma(P, S, adjoint, img_p, img_r, grad)
                          : tti_launch_fast(P, S, adjoint, img_p, img_r, grad);

@@ -190,15 +190,19 @@ def test_elastic_taylor_through_autograd(env):
     dirs = []
     for x in (lam0, mu0, b0):
         g = x.grad.double() * mask
-        dirs.append(-g / g.abs().max() * 0.01 * x.detach().double().abs().mean())
+        dirs.append(-g / g.abs().max() * 0.003 * x.detach().double().abs().mean())
     lin = float(sum(torch.sum(x.grad.double() * d) for x, d in zip((lam0, mu0, b0), dirs)))
     e1, e2 = [], []
+    hs = (1.0, 0.5, 0.25, 0.125, 0.0625)
     with torch.no_grad():
-        for hh in (1.0, 0.5, 0.25, 0.125):
+        for hh in hs:
             Jh = float(J(*[(x.detach().double() + hh * d).float() for x, d in zip((lam0, mu0, b0), dirs)]))
             e1.append(abs(Jh - float(J0)))
             e2.append(abs(Jh - float(J0) - hh * lin))
-    s1 = [math.log(e1[i] / e1[i + 1], 2) for i in range(3)]
-    s2 = [math.log(e2[i] / e2[i + 1], 2) for i in range(3)]
-    assert all(abs(s - 1.0) < 0.15 for s in s1), s1
-    assert all(s > 1.8 for s in s2[:2]), (s2, e2)
+    s1 = [math.log(e1[i] / e1[i + 1], 2) for i in range(len(hs) - 1)]
+    s2 = [math.log(e2[i] / e2[i + 1], 2) for i in range(len(hs) - 1)]
+    # along the gradient the second-order term is not small at h = 1: the
+    # first-order slope reaches 1 as h shrinks, the remainder falls as h^2
+    assert abs(s1[-1] - 1.0) < 0.1 and s1[-1] >= s1[0] - 0.05, s1
+    assert all(s > 1.8 for s in s2[:3]), (s2, e2)
+    assert e2[-1] < 0.1 * e1[-1], (e1, e2)

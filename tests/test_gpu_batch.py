@@ -77,6 +77,11 @@ def test_batch_equals_one_call_per_shot(wp, shots, budget):
     for i, (g, j) in enumerate(zip(grads, J)):
         np.testing.assert_array_equal(g, ref[i][0], err_msg=f"shot {i}")
         assert j == ref[i][1], i
+    shared, alone = wp.batch_stats()
+    if budget == 0:     # the three TTI shots share one launch per pass and step
+        assert shared > 0 and alone == 0, (shared, alone)
+    else:               # one shot per wave: nothing to share
+        assert shared == 0 and alone == 0, (shared, alone)
     # the handles stay usable after the batch
     p, d = shots[0]
     again = props[0].gradient(p.wavelet, p.src, p.rec, d)
@@ -127,3 +132,47 @@ def test_trim_releases_work_arrays_only(wp, shots, snap):
     g2, J2 = prop.gradient(p0.wavelet, p0.src, p0.rec, d)
     np.testing.assert_array_equal(g2, g)
     assert J2 == J
+
+
+def test_shared_launch_with_different_step_sequences(wp, shots):
+    """Shots whose sweeps differ (full storage against FP32 checkpoints: the
+    adjoint sweep of the second recomputes forward steps between its adjoint
+    steps) still meet at every step: rounds of one kind share a launch,
+    mixed rounds are launched shot by shot, and every gradient is bitwise
+    that of its own prop_gradient call."""
+    sel = [shots[0], shots[1], shots[2]]
+    modes = [wp.SNAP_FULL_FP32, wp.SNAP_CKPT_FP32, wp.SNAP_FULL_FP32]
+    ref = []
+    for (p, d), mode in zip(sel, modes):
+        prop = wp.Propagator.from_problem(p, snap_mode=mode, ckpt_interval=7)
+        ref.append(prop.gradient(p.wavelet, p.src, p.rec, d))
+        prop.close()
+    props = [wp.Propagator.from_problem(p, snap_mode=mode, ckpt_interval=7) for (p, _), mode in zip(sel, modes)]
+    grads, J = wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                                 [p.rec for p, _ in sel], [d for _, d in sel])
+    shared, alone = wp.batch_stats()
+    assert shared > 0 and alone > 0, (shared, alone)
+    for i, (g, j) in enumerate(zip(grads, J)):
+        np.testing.assert_array_equal(g, ref[i][0], err_msg=f"shot {i}")
+        assert j == ref[i][1], i
+    for pr in props:
+        pr.close()
+
+
+def test_shared_launch_switch(wp, shots, monkeypatch):
+    """WAVEPROP_BATCH_LAUNCH=0 keeps every shot on its own launches; the
+    gradients are the same bits either way."""
+    sel = shots[:3]
+    out = {}
+    for env in ("1", "0"):
+        monkeypatch.setenv("WAVEPROP_BATCH_LAUNCH", env)
+        props = [wp.Propagator.from_problem(p) for p, _ in sel]
+        out[env] = wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                                     [p.rec for p, _ in sel], [d for _, d in sel])
+        out[env + "stats"] = wp.batch_stats()
+        for pr in props:
+            pr.close()
+    assert out["1stats"][0] > 0 and out["0stats"] == (0, 0)
+    for a, b in zip(out["1"][0], out["0"][0]):
+        np.testing.assert_array_equal(a, b)
+    assert out["1"][1] == out["0"][1]
