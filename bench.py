@@ -597,6 +597,33 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti", wi
             "bitwise_equal": same and same_own}
 
 
+def oracle_tti_industry(steps=3, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
+    """The FP64 oracle on the industry-scale TTI grid (880 x 880 x 480, so
+    12): a few source-free steps from a seeded random state with a uniform
+    random model (content does not change the work), timed and reported per
+    step (the full 3000-step run is that time x 3000; the oracle holds about
+    25 arrays of 371.7 M doubles, 74 GB of host memory)."""
+    import oracle
+    rng = np.random.default_rng(7)
+    f = lambda lo, hi: rng.uniform(lo, hi, (nx, ny, nz)).astype(np.float32)
+    eps = f(0.0, 0.3)
+    model = {"vp": f(1.5, 4.5), "eps": eps, "delta": (eps * f(0.0, 0.5)).astype(np.float32),
+             "theta": f(0.0, 0.7), "phi": f(0.0, 1.57)}
+    dt = synth.cfl_dt(h, 4.5 * np.sqrt(1.6))
+    z = np.zeros((1, 3), np.float32)
+    p = synth.Problem(synth.TTI, nx, ny, nz, nbl, h, so, 10, dt, model, z, np.zeros((1, 10), np.float32), z)
+    o = oracle.Problem(p)
+    del model, eps
+    st = [rng.standard_normal(o.shape).astype(np.float64) for _ in range(4)]
+    t0 = time.perf_counter()
+    o.tti_run_d(*st, steps)
+    sec = time.perf_counter() - t0
+    N = o.N
+    return {"grid": list(o.shape), "space_order": so, "steps_timed": steps, "seconds_per_step": sec / steps,
+            "gpts_per_s": N * steps / sec / 1e9, "cores": os.cpu_count(),
+            "full_run_estimate_hours": sec / steps * 3000 / 3600.0}
+
+
 def run_extras(wp, torch, dev, args, extras):
     """Secondary measurements (``--extra``); each timed region is marked for
     the clock record."""
@@ -637,6 +664,8 @@ def run_extras(wp, torch, dev, args, extras):
         _clocked(out, "gradaniso", lambda: gradient_aniso_cost(wp, torch, dev, small=args.small))
     if "gradsmall" in extras:
         _clocked(out, "gradsmall", lambda: gradient_small(wp, torch, dev))
+    if "oracle3" in extras:           # CPU only: no clock record needed, but harmless
+        _clocked(out, "oracle3", lambda: oracle_tti_industry())
     if "batchsmall" in extras:       # many small windows: 40-80 x 40-80 x 60 cells
         _clocked(out, "batchsmall", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
                                                                  kind="tti", windows=(40, 80, 60)))
