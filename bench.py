@@ -614,7 +614,7 @@ def oracle_tti_industry(steps=3, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
     p = synth.Problem(synth.TTI, nx, ny, nz, nbl, h, so, 10, dt, model, z, np.zeros((1, 10), np.float32), z)
     o = oracle.Problem(p)
     del model, eps
-    st = [rng.standard_normal(o.shape).astype(np.float64) for _ in range(4)]
+    st = [rng.standard_normal(o.shape, dtype=np.float32) for _ in range(4)]
     t0 = time.perf_counter()
     o.tti_run_d(*st, steps)
     sec = time.perf_counter() - t0

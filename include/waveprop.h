@@ -171,8 +171,11 @@ int prop_gradient(prop_t *p, const float *wavelet, const float *src_xyz, int nsr
  * Costs per step one more application of H to the stored forward field and
  * the first derivatives of zeta and of the forward field; needs 6 more
  * scratch fields than prop_gradient.
- * PROP_EINVAL for an elastic handle or a computational nz (nz + 2 nbl) that
- * is not a multiple of 4 (the TMA-fed kernels it uses need 16-byte rows). */
+ * Any computational nz with the centred operators (TMA-fed passes when nz +
+ * 2 nbl is a multiple of 4, the pipelined passes otherwise).
+ * PROP_EINVAL for a non-TTI handle, or for tti_operator = 1 with a
+ * computational nz that is not a multiple of 4 (its half-point imaging runs
+ * on the TMA-fed passes, which need 16-byte rows). */
 int prop_gradient_aniso(prop_t *p, const float *wavelet, const float *src_xyz, int nsrc,
                         const float *rec_xyz, int nrec, const float *d_obs, float *grad,
                         double *misfit);

@@ -157,6 +157,13 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
 // (tilt/azimuth imaging; zeta = C lam must be in tmp[6], tmp[7]; uses tmp[0..13])
 int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
                         float *ge, float *gd, float *const *gax);
+// the same imaging on the pipelined passes (any NZ, centred operators);
+// forms zeta = C lam itself (tmp[6], tmp[7]); uses tmp[0..13]
+int tti_image_aniso_fast(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
+                         float *ge, float *gd, float *const *gax);
+// pointwise tilt/azimuth term: acc += dt^2 V from the raw derivatives dz of
+// zeta and du of the forward field (6 fields each)
+void tti_axis_image_launch(prop_s *P, const float *const *dz, const float *const *du, float *const *acc);
 // dJ/dn accumulators a[0..2] -> dJ/dtheta in a[0], dJ/dphi in a[1] (pointwise)
 void tti_axis_to_angles(prop_s *P, float *const *a);
 // TMA passes of a transposed elastic step with imaging: on entry S[3..8] hold

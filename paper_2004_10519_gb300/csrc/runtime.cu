@@ -1094,7 +1094,8 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
     // (level 0 is zero: no term for k = 1)
     auto aniso_iter = [&](int k, const float *u1) -> int {
         if (!aniso || k < 2) return PROP_OK;
-        return tti_image_aniso_tma(P, u1, u1 + N, a[0], a[1], g3[1], g3[2], g3 + 3);
+        if (tma_usable(P)) return tti_image_aniso_tma(P, u1, u1 + N, a[0], a[1], g3[1], g3[2], g3 + 3);
+        return tti_image_aniso_fast(P, u1, u1 + N, a[0], a[1], g3[1], g3[2], g3 + 3);
     };
     if (!grad) {
         for (int k = nt - 1; k >= 1; k--) WP_TRY(adj_iter(k, nullptr, nullptr));
@@ -1363,8 +1364,10 @@ extern "C" int prop_gradient_aniso(prop_t *P, const float *wavelet, const float 
 {
     WP_TRY(check_handle(P));
     if (P->d.kind != PROP_TTI) return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso is for TTI propagators");
-    if (!tma_usable(P))
-        return wp_fail(P, PROP_EINVAL, "prop_gradient_aniso needs a computational nz that is a multiple of 4");
+    if (!tma_usable(P) && P->d.tti_operator == 1)
+        return wp_fail(P, PROP_EINVAL,
+                       "prop_gradient_aniso with the staggered-pair operators needs a computational nz that is a "
+                       "multiple of 4");
     P->aniso = true;
     const int rc = prop_gradient(P, wavelet, src_xyz, nsrc, rec_xyz, nrec, d_obs, grad, misfit);
     P->aniso = false;

@@ -1395,6 +1395,23 @@ int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
 
+// the pointwise tilt/azimuth term for any pass family (dz: raw derivatives of
+// zeta = C lam, du: of the forward field; acc += dt^2 V)
+void tti_axis_image_launch(prop_s *P, const float *const *dz, const float *const *du, float *const *acc)
+{
+    AxisIn ai;
+    for (int c = 0; c < 6; c++) {
+        ai.dz[c] = dz[c];
+        ai.du[c] = du[c];
+    }
+    ai.nx = P->nrm[0];
+    ai.ny = P->nrm[1];
+    for (int c = 0; c < 3; c++) ai.acc[c] = acc[c];
+    const long long n = (long long)P->g.N;
+    tti_axis_image<<<(unsigned)((n + 255) / 256), 256, 0, P->stream>>>(n, P->g.dt * P->g.dt, ai);
+    P->kern_launches += 1;
+}
+
 // dJ/dn accumulators (computational grid) -> dJ/dtheta in a[0], dJ/dphi in a[1]
 void tti_axis_to_angles(prop_s *P, float *const *a)
 {

@@ -5,6 +5,10 @@
 //   pass 2: H0 p = sum_i D_i e_i, Hz r = sum_i D_i f_i, coupling C (forward
 //           only), damped leapfrog; adjoint: fused imaging
 //           grad -= sum_f u_f^k dt^2 (H zeta)_f / m.
+// Imaging of eps, delta, theta, phi (prop_gradient_aniso) on these passes:
+// pass 1 in its RAW mode writes D p, D r unprojected; pass 2 in mode
+// ADJ = 2 takes no step and accumulates the coupling terms with lam^{n+1}
+// (see tti_image_aniso_fast).
 // Each pass streams along x over a 32(z) x 16(y) tile.  The loads of plane
 // x+1 (queue heads, own interior values, an even share of the halo) are in
 // flight while plane x is computed from double-buffered shared planes.
@@ -35,7 +39,7 @@ WP_DEV void src_pair(const GridDev &g, const float *__restrict__ p, const float 
     }
 }
 
-template <int M, int ADJ>
+template <int M, int ADJ, bool RAW = false>
 __global__ void __launch_bounds__(NT, 2)
 tti_rot_p(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
           const float *__restrict__ eps, const float *__restrict__ del, const float *__restrict__ nxa,
@@ -104,6 +108,14 @@ tti_rot_p(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict
             const float n2 = sqrtf(fmaxf(0.f, 1.f - n0 * n0 - n1 * n1));
             gp0 *= g.ih; gp1 *= g.ih; gp2 *= g.ih;
             gr0 *= g.ih; gr1 *= g.ih; gr2 *= g.ih;
+            if constexpr (RAW) {
+                ex[q] = gp0;
+                ey[q] = gp1;
+                ez[q] = gp2;
+                fx[q] = gr0;
+                fy[q] = gr1;
+                fz[q] = gr2;
+            } else {
             const float wp = n0 * gp0 + n1 * gp1 + n2 * gp2;
             const float wr = n0 * gr0 + n1 * gr1 + n2 * gr2;
             ex[q] = gp0 - n0 * wp;
@@ -112,6 +124,7 @@ tti_rot_p(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict
             fx[q] = n0 * wr;
             fy[q] = n1 * wr;
             fz[q] = n2 * wr;
+            }
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -185,11 +198,9 @@ tti_upd_p(GridDev g, FDW w, const float *__restrict__ ex, const float *__restric
         const long long q = act ? gidx(g, x, y, z) : 0;
         float mm = 1.f, e_ = 0.f, d_ = 0.f, p1 = 0.f, r1 = 0.f, p0 = 0.f, r0 = 0.f;
         if (act) {
-            mm = __ldg(m + q);
-            if (!ADJ) {
-                e_ = __ldg(eps + q);
-                d_ = __ldg(del + q);
-            }
+            if (ADJ != 2) mm = __ldg(m + q);
+            if (ADJ != 1) d_ = __ldg(del + q);
+            if (ADJ == 0) e_ = __ldg(eps + q);
             p1 = __ldg(pc + q);
             r1 = __ldg(rc + q);
             p0 = pp[q];
@@ -209,6 +220,14 @@ tti_upd_p(GridDev g, FDW w, const float *__restrict__ ex, const float *__restric
             }
             h0 *= g.ih;
             hz *= g.ih;
+            if (ADJ == 2) {
+                // imaging of the coupling with lam^{n+1} = (p1, r1) and the
+                // forward field's H0 p^n, Hz r^n: g_eps (pp) += 2 dt^2
+                // lam_p H0 p^n, g_delta (rp) += dt^2 (lam_p Hz r^n + lam_r
+                // H0 p^n) / sqrt(1 + 2 delta)
+                pp[q] = p0 + 2.f * dt2 * p1 * h0;
+                rp[q] = r0 + dt2 * (p1 * hz + r1 * h0) / sqrtf(1.f + 2.f * d_);
+            } else {
             float Lp, Lr;
             if (!ADJ) {
                 const float a = 1.f + 2.f * e_, s = sqrtf(1.f + 2.f * d_);
@@ -226,6 +245,7 @@ tti_upd_p(GridDev g, FDW w, const float *__restrict__ ex, const float *__restric
             rp[q] = rn;
             if (ADJ && grad) grad[q] -= dt2 * (__ldg(up + q) * Lp + __ldg(ur + q) * Lr) / mm;
             if (check && !(isfinite(pn) && isfinite(rn))) atomicOr(flag, 1);
+            }
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -259,7 +279,58 @@ int launch(prop_s *P, float *const *S, const float *up, const float *ur, float *
     return PROP_OK;
 }
 
+// eps, delta (and theta, phi) imaging of one transposed step on the
+// pipelined passes: the rotation pass on the forward field (up, ur), the
+// update pass in its imaging mode with lam = (lp, lr); with gax, zeta = C lam
+// into tmp[6], tmp[7], raw derivatives of zeta (tmp[0..5]) and of the
+// forward field (tmp[8..13]) and the pointwise axis term
+template <int M>
+int image_aniso(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr, float *ge,
+                float *gd, float *const *gax)
+{
+    const GridDev &g = P->g;
+    const int xc = P->xchunk;
+    dim3 blk(FZ, FY, 1), grd((g.NZ + FZ - 1) / FZ, (g.NY + FY - 1) / FY, (g.NX + xc - 1) / xc);
+    float *const *t = P->tmp;
+    const size_t s1 = 2 * 2 * PG<M>::size(2) * sizeof(float);
+    const size_t s2 = 2 * (2 * PG<M>::size(0) + 2 * PG<M>::size(1)) * sizeof(float);
+    static const bool attr =
+        (cudaFuncSetAttribute(tti_rot_p<M, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1),
+         cudaFuncSetAttribute(tti_rot_p<M, 0, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s1),
+         cudaFuncSetAttribute(tti_upd_p<M, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s2), true);
+    (void)attr;
+    tti_rot_p<M, 0><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, P->eps, P->del, P->nrm[0], P->nrm[1], t[0], t[1],
+                                                 t[2], t[3], t[4], t[5], xc);
+    tti_upd_p<M, 2><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[1], t[2], t[3], t[4], t[5], P->m, P->eps, P->del,
+                                                 lp, lr, ge, gd, nullptr, nullptr, nullptr, P->flag, 0, xc);
+    P->kern_launches += 2;
+    if (gax) {
+        k_tti_zeta(P, lp, lr, t[6], t[7]);
+        tti_rot_p<M, 0, true><<<grd, blk, s1, P->stream>>>(g, P->w, t[6], t[7], P->eps, P->del, P->nrm[0],
+                                                           P->nrm[1], t[0], t[1], t[2], t[3], t[4], t[5], xc);
+        tti_rot_p<M, 0, true><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, P->eps, P->del, P->nrm[0], P->nrm[1],
+                                                           t[8], t[9], t[10], t[11], t[12], t[13], xc);
+        P->kern_launches += 2;
+        const float *dz[6] = {t[0], t[1], t[2], t[3], t[4], t[5]}, *du[6] = {t[8], t[9], t[10], t[11], t[12], t[13]};
+        tti_axis_image_launch(P, dz, du, gax);
+    }
+    WP_CK(P, cudaGetLastError());
+    return PROP_OK;
+}
+
 }  // namespace
+
+int tti_image_aniso_fast(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
+                         float *ge, float *gd, float *const *gax)
+{
+    switch (P->M) {
+    case 2: return image_aniso<2>(P, up, ur, lp, lr, ge, gd, gax);
+    case 4: return image_aniso<4>(P, up, ur, lp, lr, ge, gd, gax);
+    case 6: return image_aniso<6>(P, up, ur, lp, lr, ge, gd, gax);
+    case 8: return image_aniso<8>(P, up, ur, lp, lr, ge, gd, gax);
+    }
+    return wp_fail(P, PROP_EINVAL, "unsupported space order");
+}
 
 int tti_launch_fast(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
                     float *grad)
