@@ -43,10 +43,9 @@ HBM_FALLBACK_GBS = 6800.0
 #   acoustic: 2 state reads + 1 write + m                             = 16 B
 ALG_BYTES = {"elastic": 84.0, "tti": 44.0, "acoustic": 16.0}
 # DRAM bytes per point of one elastic step (velocity + stress pass) measured
-# by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the 200^3 case of
-# the same kernels (profiles/elastic_tma_passes_200cube_so8.md), scaled to a
-# full launch by the number of points
-TRAFFIC_B_PER_PT = {"elastic": 113.9}
+# by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the benchmark's own
+# 296^3 grid (profiles/elastic_bench_launch_list_296cube_so8.md)
+TRAFFIC_B_PER_PT = {"elastic": 118.1}
 # algorithmic FP32 operations per point update, counted from the kernels'
 # arithmetic (FMA = 2): elastic so 8 (velocity + stress pass), TTI so 12
 # (rotation + update pass), acoustic so 12 (7 per stencil radius + 15)
