@@ -623,6 +623,47 @@ def oracle_tti_industry(steps=3, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
             "full_run_estimate_hours": sec / steps * 3000 / 3600.0}
 
 
+def forward_batch_shots_per_hour(wp, torch, dev, nshots, nt, windows=None):
+    """TTI forward modelling (so 12) of many shots on windows of one large
+    model: one prop_forward after another against one prop_forward_batch
+    (lockstep, one launch per pass and step for every shot, two steps
+    replayed from a CUDA graph); traces compared bitwise."""
+    kw = {}
+    if windows:
+        kw.update(size_range=windows[:2], nz=windows[2])
+    shots = synth.tti_batch_shots(nshots, nt, **kw)
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    to = lambda a: torch.from_numpy(a).to(dev)
+    props, wav, src, rec = [], [], [], []
+    npts = 0
+    for true, _ in shots:
+        props.append(wp.Propagator.from_problem(true, stream=stream))
+        wav.append(to(true.wavelet)); src.append(to(true.src)); rec.append(to(true.rec))
+        npts += int(np.prod(props[-1].grid))
+    props[0].forward(wav[0], src[0], rec[0])                   # warm-up
+    wp.forward_batch(props[:2], wav[:2], src[:2], rec[:2])
+    torch.cuda.synchronize()
+    with timed_region():
+        t0 = time.perf_counter()
+        seq = [p.forward(w, s_, r) for p, w, s_, r in zip(props, wav, src, rec)]
+        torch.cuda.synchronize()
+        t_seq = time.perf_counter() - t0
+    with timed_region():
+        t0 = time.perf_counter()
+        bat = wp.forward_batch(props, wav, src, rec)
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t0
+    same = all(bool(torch.equal(a, b)) for a, b in zip(seq, bat))
+    for p in props:
+        p.close()
+    return {"shots": nshots, "nt": nt, "points_total": npts,
+            "one_call_per_shot": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq,
+                                  "gpts_per_s": npts * nt / t_seq / 1e9},
+            "forward_batch": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
+                              "gpts_per_s": npts * nt / t_bat / 1e9},
+            "bitwise_equal": same}
+
+
 def run_extras(wp, torch, dev, args, extras):
     """Secondary measurements (``--extra``); each timed region is marked for
     the clock record."""
@@ -665,6 +706,11 @@ def run_extras(wp, torch, dev, args, extras):
         _clocked(out, "gradsmall", lambda: gradient_small(wp, torch, dev))
     if "oracle3" in extras:           # CPU only: no clock record needed, but harmless
         _clocked(out, "oracle3", lambda: oracle_tti_industry())
+    if "fwdbatch" in extras:          # forward modelling, industry-size and small windows
+        _clocked(out, "fwdbatch", lambda: forward_batch_shots_per_hour(wp, torch, dev, args.batch_shots,
+                                                                       args.batch_nt))
+        _clocked(out, "fwdbatchsmall", lambda: forward_batch_shots_per_hour(wp, torch, dev, args.batch_shots,
+                                                                            args.batch_nt, windows=(40, 80, 60)))
     if "batchsmall" in extras:       # many small windows: 40-80 x 40-80 x 60 cells
         _clocked(out, "batchsmall", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
                                                                  kind="tti", windows=(40, 80, 60)))

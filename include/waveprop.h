@@ -191,6 +191,25 @@ int prop_forward_saved(prop_t *p, const float *wavelet, const float *src_xyz, in
                        const float *rec_xyz, int nrec, float *traces);
 int prop_backward(prop_t *p, const float *resid, float *grad, float *src_grad);
 
+/* Forward modelling of many independent shots in lockstep (Sec. III-B):
+ * shot i computes exactly prop_forward(shots[i], wavelet[i], src_xyz[i],
+ * nsrc[i], rec_xyz[i], nrec[i], traces[i]) -- bitwise the same traces.
+ * When every shot is TTI with the centred operators, the same space order
+ * and nt and a computational nz that is a multiple of 4, each time step is
+ * one launch of each pass over a table of all the shots' tiles (each shot
+ * keeping its own model window, grid and x-extent) beside the shots'
+ * injection and receiver sampling; two steps are captured once as a CUDA
+ * graph and replayed (WAVEPROP_GRAPHS=0: direct launches).  The work runs
+ * on a private stream ordered after the work already queued on each
+ * handle's stream; each handle's stream waits for the batch, and the call
+ * is synchronous.  Other shot sets (and WAVEPROP_BATCH_LAUNCH=0) run one
+ * prop_forward after another.  Arguments as prop_gradient_batch.  Returns
+ * PROP_OK or the first error, with the message "shot i: ..." from
+ * prop_last_error(NULL). */
+int prop_forward_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
+                       const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
+                       const int *nrec, float *const *traces);
+
 /* Gradients of many independent shots (the paper's embarrassingly parallel
  * loop over sources, Sec. III-B: each shot its own model window, geometry
  * and handle).  Shot i computes exactly prop_gradient(shots[i], wavelet[i],
@@ -206,7 +225,11 @@ int prop_backward(prop_t *p, const float *resid, float *grad, float *src_grad);
  * (its message, prefixed "shot i: ", from prop_last_error(NULL); each
  * handle keeps its own message); the other shots still run.  Each shot's
  * work arrays are released after its gradient (prop_trim), so later waves
- * can use that memory; its wavefield state then reads as zero. */
+ * can use that memory; its wavefield state then reads as zero.
+ * TTI shots of a wave (centred operators, computational nz a multiple of 4)
+ * share their step launches: the k-th step of every such shot runs as one
+ * launch of each pass over a table of all the shots' tiles (set
+ * WAVEPROP_BATCH_LAUNCH=0 to launch shot by shot). */
 int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
                         const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
                         const int *nrec, const float *const *d_obs, float *const *grad,

@@ -29,7 +29,7 @@ ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
                "prop_last_error", "prop_forward_noalloc", "prop_tile_planes",
                "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves",
-               "prop_gradient_aniso", "prop_stack_image", "prop_trim")
+               "prop_gradient_aniso", "prop_stack_image", "prop_trim", "prop_forward_batch")
 
 
 class PropDesc(C.Structure):
@@ -76,6 +76,8 @@ def lib():
         L.prop_gradient_batch.argtypes = [fpp, C.c_int, fpp, fpp, C.POINTER(C.c_int), fpp,
                                           C.POINTER(C.c_int), fpp, fpp, C.POINTER(C.c_double),
                                           C.c_size_t]
+        L.prop_forward_batch.argtypes = [fpp, C.c_int, fpp, fpp, C.POINTER(C.c_int), fpp,
+                                         C.POINTER(C.c_int), fpp]
         L.prop_gradient_bytes.restype = C.c_size_t
         L.prop_gradient_bytes.argtypes = [vp, C.c_int]
         L.prop_plan_waves.argtypes = [C.POINTER(C.c_size_t), C.c_int, C.c_size_t, C.POINTER(C.c_int)]
@@ -387,6 +389,30 @@ def gradient_batch(props, wavelets, srcs, recs, d_obs, outs=None, budget_bytes=0
     if rc:
         raise PropError(rc, lib().prop_last_error(None).decode())
     return grads, [J[i] for i in range(n)]
+
+
+def forward_batch(props, wavelets, srcs, recs, outs=None):
+    """Forward modelling of independent shots in lockstep
+    (``prop_forward_batch``); shot i uses ``props[i]`` and the i-th entry
+    of every list.  Returns the list of traces [nrec_i][nt]."""
+    n = len(props)
+    keep, W, S, R, T = [], [], [], [], []
+    ns, nr = (C.c_int * max(n, 1))(), (C.c_int * max(n, 1))()
+    trs = []
+    for i, p in enumerate(props):
+        sa, ra = _Arg(srcs[i]), _Arg(recs[i])
+        ns[i], nr[i] = _npts(sa), _npts(ra)
+        w = _Arg(wavelets[i], ns[i] * p.nt)
+        out = outs[i] if outs is not None else p._out(wavelets[i], (nr[i], p.nt))
+        o = _Arg(out, nr[i] * p.nt, writable=True)
+        trs.append(out)
+        keep += [sa, ra, w, o]
+        W.append(w.ptr); S.append(sa.ptr); R.append(ra.ptr); T.append(o.ptr)
+    arr = lambda xs: (C.c_void_p * max(n, 1))(*xs)
+    rc = lib().prop_forward_batch(arr([p.h for p in props]), n, arr(W), arr(S), ns, arr(R), nr, arr(T))
+    if rc:
+        raise PropError(rc, lib().prop_last_error(None).decode())
+    return trs
 
 
 def batch_stats():

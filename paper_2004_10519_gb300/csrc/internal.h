@@ -195,6 +195,11 @@ void tti_batch_free(TtiBatch *b);
 // 0: launched on `stream`; 1: the requests cannot share a launch (the caller
 // launches them one by one); < 0: error (message in *err)
 int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t stream, std::string *err);
+// forward-step configuration `slot` (0 or 1) of every request into a fixed
+// device table (1: not batchable); then launches of that table, which may be
+// captured into a CUDA graph (no host staging)
+int tti_batch_fix(TtiBatch *b, const TtiBatchReq *req, int n, int slot, cudaStream_t stream, std::string *err);
+int tti_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t stream);
 // true if the handle's TTI steps can join a batched launch
 bool tti_batchable(const prop_s *P);
 // a TTI step of a shot taking part in a rendezvous (runtime.cu): waits for
@@ -215,9 +220,13 @@ int sp_host_tables(prop_s *P, const float *xyz_host, int n, const int *trace_of_
 // device copy of the tables in one allocation (wp_malloc); sp_free releases it
 int sp_build(prop_s *P, const float *xyz_host, int n, const int *trace_of_point, SparseDev *S);
 void sp_free(SparseDev *S);
-// record: out[t*n + i] = scale * sum_c w * (f0 + f1 + f2)[idx]   (f1, f2 may be NULL)
+// record: out[t*n + i] = scale * sum_c w * (f0 + f1 + f2)[idx]   (f1, f2 may be NULL);
+// out_col is the column of step t, or with tdev the base of the [nt][n]
+// staging array and t read from device memory (graph replay)
 void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, const float *f2,
-               float scale, float *out_col);
+               float scale, float *out_col, const int *tdev = nullptr);
+// device time index += d (one thread; steps replayed from a CUDA graph)
+void k_tick(prop_s *P, int *tdev, int d);
 // inject: f[cell] += coef(cell) * sum_j w_j traces[trace_j*nt + t] into up to 3 fields;
 // mode 0: coef = scale; mode 1: coef = scale / A (TTI, A = m(1+sig dt/2));
 // mode 2: coef = scale (3 lambda + 2 mu) (elastic adjoint in s = C tbar);
@@ -225,8 +234,10 @@ void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, 
 // that into f1 = zeta_p, f2 = zeta_r (TTI transposed step, zeta = C lam);
 // grad_u != NULL: grad[cell] -= u[cell] * scale*sum / m  (TTI imaging of the
 // residual injection)
+// (tdev != NULL: t read from device memory)
 void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
-               int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad);
+               int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad,
+               const int *tdev = nullptr);
 // as sp_record but each field sum is divided by (3 lambda + 2 mu) at the cell
 // (trace of tbar from s = C tbar)
 void sp_record_trace_s(prop_s *P, const SparseDev *S, const float *f0, const float *f1,

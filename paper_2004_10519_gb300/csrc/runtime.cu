@@ -1611,6 +1611,204 @@ int rdv_tti_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, c
     return PROP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Forward modelling of many TTI shots in lockstep: per time step the
+// receivers of every shot are sampled, one tile-table launch of each pass
+// advances every shot, and the sources are injected.  The TTI state buffers
+// rotate with period 2, so two steps are captured once into a CUDA graph
+// (the sparse kernels read the time index from device memory and a
+// one-thread kernel advances it) and the graph is replayed nt/2 times.
+// ---------------------------------------------------------------------------
+static int forward_batch_one_by_one(prop_t *const *shots, int n, const float *const *wavelet,
+                                    const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
+                                    const int *nrec, float *const *traces)
+{
+    for (int i = 0; i < n; i++) {
+        const int rc = prop_forward(shots[i], wavelet[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i], traces[i]);
+        if (rc) {
+            tl_err = "shot " + std::to_string(i) + ": " + prop_last_error(shots[i]);
+            return rc;
+        }
+    }
+    return PROP_OK;
+}
+
+extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *const *wavelet,
+                                  const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
+                                  const int *nrec, float *const *traces)
+{
+    if (n < 0) return wp_fail(nullptr, PROP_EINVAL, "nshots < 0");
+    if (n == 0) return PROP_OK;
+    if (!shots || !wavelet || !src_xyz || !nsrc || !rec_xyz || !nrec || !traces)
+        return wp_fail(nullptr, PROP_EINVAL, "NULL array argument");
+    for (int i = 0; i < n; i++) {
+        if (!shots[i]) return wp_fail(nullptr, PROP_EINVAL, "shot handle " + std::to_string(i) + " is NULL");
+        for (int j = 0; j < i; j++)
+            if (shots[j] == shots[i])
+                return wp_fail(nullptr, PROP_EINVAL, "shot handle " + std::to_string(i) + " repeats an earlier one");
+        if (!wavelet[i] || !src_xyz[i] || !rec_xyz[i] || !traces[i] || nsrc[i] < 1 || nrec[i] < 1)
+            return wp_fail(nullptr, PROP_EINVAL, "shot " + std::to_string(i) + ": missing wavelet, geometry or output");
+    }
+    // lockstep needs TTI shots on the TMA-fed passes with one space order and nt
+    bool lock = true;
+    for (int i = 0; i < n && lock; i++)
+        lock = tti_batchable(shots[i]) && shots[i]->M == shots[0]->M && shots[i]->d.nt == shots[0]->d.nt &&
+               !shots[i]->broken;
+    const char *bl = getenv("WAVEPROP_BATCH_LAUNCH");
+    if (!lock || n < 2 || (bl && !strcmp(bl, "0")))
+        return forward_batch_one_by_one(shots, n, wavelet, src_xyz, nsrc, rec_xyz, nrec, traces);
+
+    prop_s *P0 = shots[0];
+    const int nt = P0->d.nt;
+    // every shot's work runs on one private stream (capturable, unlike the
+    // legacy default stream), after what each handle had queued on its own
+    // stream; each handle's stream waits for the batch at the end
+    struct OwnStream {
+        cudaStream_t s = nullptr;
+        ~OwnStream()
+        {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } bs;
+    WP_CK(P0, cudaStreamCreateWithFlags(&bs.s, cudaStreamNonBlocking));
+    const cudaStream_t st = bs.s;
+    std::vector<cudaStream_t> own(n);
+    struct Restore {
+        prop_t *const *sh;
+        std::vector<cudaStream_t> *own;
+        int n;
+        ~Restore()
+        {
+            for (int i = 0; i < n; i++) sh[i]->stream = (*own)[i];
+        }
+    } restore{shots, &own, 0};
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        WP_TRY(check_handle(P));
+        own[i] = P->stream;
+        if (P->stream != st) {
+            cudaEvent_t e;
+            WP_CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            cudaEventRecord(e, P->stream);
+            cudaStreamWaitEvent(st, e, 0);
+            cudaEventDestroy(e);
+        }
+        P->stream = st;
+        restore.n = i + 1;
+        WP_TRY(ensure_work(P));
+    }
+    std::vector<Geometry> G(n);
+    std::vector<DevBuf> wb(n), stage(n), tr(n);
+    std::vector<const float *> wav(n);
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        WP_TRY(build_geometry(P, G[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i]));
+        WP_TRY(dev_in(P, wavelet[i], (size_t)nsrc[i] * nt, wb[i], &wav[i]));
+        WP_TRY(wp_malloc(P, &stage[i].p, sizeof(float) * (size_t)nt * nrec[i], "trace staging"));
+        WP_TRY(wp_malloc(P, &tr[i].p, sizeof(float) * (size_t)nt * nrec[i], "traces"));
+        WP_TRY(zero_fields(P, P->st, 4));
+    }
+    DevBuf tbuf;
+    WP_TRY(wp_malloc(P0, &tbuf.p, sizeof(int), "time index"));
+    int *tdev = (int *)tbuf.p;
+    WP_CK(P0, cudaMemsetAsync(tdev, 0, sizeof(int), st));
+    // the two buffer arrangements of a step: (p, r, p_prev, r_prev) and the rotated one
+    std::unique_ptr<TtiBatch, void (*)(TtiBatch *)> tb(tti_batch_new(), tti_batch_free);
+    for (int c = 0; c < 2; c++) {
+        std::vector<TtiBatchReq> req(n);
+        for (int i = 0; i < n; i++) {
+            float *const *q = shots[i]->st;
+            req[i] = c == 0 ? TtiBatchReq{shots[i], {q[0], q[1], q[2], q[3]}, false, nullptr, nullptr, nullptr}
+                            : TtiBatchReq{shots[i], {q[2], q[3], q[0], q[1]}, false, nullptr, nullptr, nullptr};
+        }
+        std::string err;
+        const int rc = tti_batch_fix(tb.get(), req.data(), n, c, st, &err);
+        if (rc == 1) return forward_batch_one_by_one(shots, n, wavelet, src_xyz, nsrc, rec_xyz, nrec, traces);
+        if (rc) return wp_fail(P0, rc, err);
+    }
+    // one step in arrangement c: record d^n from u^n, advance every shot,
+    // inject q^n into the new level, t += 1
+    auto step = [&](int c) -> int {
+        for (int i = 0; i < n; i++) {
+            prop_s *P = shots[i];
+            float *const *q = P->st;
+            sp_record(P, &G[i].R, c == 0 ? q[0] : q[2], nullptr, nullptr, 1.f, (float *)stage[i].p, tdev);
+        }
+        if (tti_batch_launch_fixed(tb.get(), c, st) != PROP_OK)
+            return wp_fail(P0, PROP_ECUDA, "batched TTI step launch failed");
+        for (int i = 0; i < n; i++) {
+            prop_s *P = shots[i];
+            float *const *q = P->st;
+            float *pn = c == 0 ? q[2] : q[0], *rn = c == 0 ? q[3] : q[1];
+            sp_inject(P, &G[i].S, wav[i], nt, 0, P->g.dt * P->g.dt, 1, pn, rn, nullptr, nullptr, nullptr, tdev);
+            P->kern_launches += 1;      // the shared pass launches, counted once per shot
+        }
+        k_tick(P0, tdev, 1);
+        return PROP_OK;
+    };
+    const char *ge = getenv("WAVEPROP_GRAPHS");
+    const bool graphs = !(ge && !strcmp(ge, "0")) && nt >= 4;
+    int done = 0;
+    if (graphs) {
+        cudaGraph_t gr = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        WP_CK(P0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        const int r0 = step(0), r1 = r0 ? r0 : step(1);
+        const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+        if (r1 || ec != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            if (r1) return r1;
+            return wp_cuda(P0, ec, "capture of the batched steps");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ex, gr, 0);
+        cudaGraphDestroy(gr);
+        WP_CK(P0, ei);
+        for (; done + 2 <= nt; done += 2) {
+            const cudaError_t el = cudaGraphLaunch(ex, st);
+            if (el != cudaSuccess) {
+                cudaGraphExecDestroy(ex);
+                return wp_cuda(P0, el, "cudaGraphLaunch (batched steps)");
+            }
+        }
+        WP_CK(P0, cudaStreamSynchronize(st));
+        cudaGraphExecDestroy(ex);
+    }
+    for (; done < nt; done++) WP_TRY(step(done & 1));
+    // the final state in st[] order (odd nt leaves the rotated arrangement)
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        if (nt & 1) {
+            std::swap(P->st[0], P->st[2]);
+            std::swap(P->st[1], P->st[3]);
+        }
+        sp_transpose(P, (const float *)stage[i].p, (float *)tr[i].p, nrec[i], nt);
+        WP_TRY(copy_out(P, traces[i], (const float *)tr[i].p, (size_t)nt * nrec[i]));
+    }
+    int first = PROP_OK;
+    for (int i = 0; i < n; i++) {
+        const int rc = finish(shots[i]);
+        if (rc && !first) {
+            first = rc;
+            tl_err = "shot " + std::to_string(i) + ": " + prop_last_error(shots[i]);
+        }
+    }
+    // each handle's own stream continues after the batch
+    for (int i = 0; i < n; i++)
+        if (own[i] != st) {
+            cudaEvent_t e;
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+                cudaEventRecord(e, st);
+                cudaStreamWaitEvent(own[i], e, 0);
+                cudaEventDestroy(e);
+            }
+        }
+    return first;
+}
+
 // shared TTI step launches of the last prop_gradient_batch call: rounds
 // launched together, rounds whose steps had to be launched one by one
 static long long batch_stats[2] = {0, 0};

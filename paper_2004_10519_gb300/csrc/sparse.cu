@@ -14,12 +14,16 @@ constexpr int NB = 256;
 
 inline int nblk(long long n, int b = NB) { return (int)std::min<long long>((n + b - 1) / b, 1 << 30); }
 
+// tdev != NULL: the time index comes from device memory (steps replayed from
+// a CUDA graph) and `out` is the base of the [nt][n] staging array
 __global__ void record_kernel(int n, const long long *__restrict__ idx, const float *__restrict__ w,
                               const float *__restrict__ f0, const float *__restrict__ f1,
-                              const float *__restrict__ f2, float scale, float *__restrict__ out)
+                              const float *__restrict__ f2, float scale, float *__restrict__ out,
+                              const int *__restrict__ tdev)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (tdev) out += (long long)(*tdev) * n;
     float s = 0.f;
 #pragma unroll
     for (int c = 0; c < 8; c++) {
@@ -41,11 +45,12 @@ __global__ void inject_kernel(GridDev g, int ncell, const long long *__restrict_
                               int t, float scale, int mode, const float *__restrict__ m,
                               const float *__restrict__ lam, const float *__restrict__ mu,
                               float *f0, float *f1, float *f2, const float *__restrict__ gu,
-                              float *grad)
+                              float *grad, const int *__restrict__ tdev)
 {
     // lam, mu: the elastic Lame parameters; for TTI (mode 3) epsilon, delta
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= ncell) return;
+    if (tdev) t = *tdev;
     float acc = 0.f;
     for (int e = ptr[j]; e < ptr[j + 1]; e++) acc += w[e] * traces[(long long)tr[e] * nt + t];
     const long long q = cell[j];
@@ -392,22 +397,31 @@ void sp_free(SparseDev *S)
 }
 
 void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, const float *f2,
-               float scale, float *out_col)
+               float scale, float *out_col, const int *tdev)
 {
     if (S->n <= 0) return;
-    record_kernel<<<nblk(S->n), NB, 0, P->stream>>>(S->n, S->rec_idx, S->rec_w, f0, f1, f2, scale, out_col);
+    record_kernel<<<nblk(S->n), NB, 0, P->stream>>>(S->n, S->rec_idx, S->rec_w, f0, f1, f2, scale, out_col,
+                                                    tdev);
+    P->kern_launches++;
+}
+
+__global__ void tick_kernel(int *t, int d) { *t += d; }
+
+void k_tick(prop_s *P, int *tdev, int d)
+{
+    tick_kernel<<<1, 1, 0, P->stream>>>(tdev, d);
     P->kern_launches++;
 }
 
 void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
-               int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad)
+               int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad, const int *tdev)
 {
     if (S->ncell <= 0) return;
     inject_kernel<<<nblk(S->ncell), NB, 0, P->stream>>>(P->g, S->ncell, S->cell, S->cell_ptr,
                                                         S->ent_trace, S->ent_w, traces, nt, t, scale,
                                                         mode, P->m, mode == 3 ? P->eps : P->lam,
                                                         mode == 3 ? P->del : P->mu, f0, f1, f2,
-                                                        grad_u, grad);
+                                                        grad_u, grad, tdev);
     P->kern_launches++;
 }
 

@@ -1469,6 +1469,11 @@ struct TtiBatch {
     cudaEvent_t copied[NSLOT] = {};
     size_t hcap = 0;
     unsigned long long calls = 0;
+    // fixed tables of forward-step configurations (graph replay)
+    TtiShot *dfixed[2] = {};
+    size_t fixed_cap = 0;
+    int fixed_n = 0, fixed_M = 0;
+    FDW w{};
 };
 
 TtiBatch *tti_batch_new() { return new TtiBatch(); }
@@ -1478,6 +1483,8 @@ void tti_batch_free(TtiBatch *b)
     if (!b) return;
     cudaFree(b->dtiles);
     cudaFree(b->dshots);
+    cudaFree(b->dfixed[0]);
+    cudaFree(b->dfixed[1]);
     for (int i = 0; i < TtiBatch::NSLOT; i++) {
         if (b->copied[i]) {
             cudaEventSynchronize(b->copied[i]);
@@ -1493,17 +1500,11 @@ bool tti_batchable(const prop_s *P)
     return P->d.kind == PROP_TTI && P->d.tti_operator == 0 && tma_usable(P);
 }
 
+// per-shot entries of one step of every request into H[0..n)
 template <int M, int ADJ, int GRAD>
-int tti_batch_launch(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
+int tti_batch_fill(const TtiBatchReq *req, int n, TtiShot *H, std::string *err)
 {
     using B = BX<M>;
-    // per-shot entries into the next staging slot
-    const int slot = (int)(b->calls++ % TtiBatch::NSLOT);
-    if (b->copied[slot] && cudaEventSynchronize(b->copied[slot]) != cudaSuccess) {
-        *err = "batched TTI step: staging wait failed";
-        return PROP_ECUDA;
-    }
-    TtiShot *H = b->hshots[slot];
     for (int i = 0; i < n; i++) {
         prop_s *P = req[i].P;
         float *const *S = req[i].S;
@@ -1538,6 +1539,20 @@ int tti_batch_launch(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st
         e.check = P->d.check_nan;
         e.xc = P->xchunk;
     }
+    return PROP_OK;
+}
+
+template <int M, int ADJ, int GRAD>
+int tti_batch_launch(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    // per-shot entries into the next staging slot
+    const int slot = (int)(b->calls++ % TtiBatch::NSLOT);
+    if (b->copied[slot] && cudaEventSynchronize(b->copied[slot]) != cudaSuccess) {
+        *err = "batched TTI step: staging wait failed";
+        return PROP_ECUDA;
+    }
+    TtiShot *H = b->hshots[slot];
+    if (int rc = tti_batch_fill<M, ADJ, GRAD>(req, n, H, err)) return rc;
     auto ck = [&](cudaError_t c, const char *what) {
         if (c == cudaSuccess) return PROP_OK;
         *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
@@ -1559,6 +1574,115 @@ int tti_batch_launch(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st
     return ck(cudaGetLastError(), "batched TTI step launch");
 }
 
+// tile table over the shots (cached while their shapes and x-extents stay
+// the same); shots with more points first
+static int tti_batch_tiles(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    std::vector<long long> sig;
+    for (int i = 0; i < n; i++) {
+        const GridDev &g = req[i].P->g;
+        sig.insert(sig.end(), {(long long)g.NX, (long long)g.NY, (long long)g.NZ, (long long)req[i].P->xchunk});
+    }
+    if (sig == b->sig) return PROP_OK;
+    std::vector<std::pair<long long, int>> order;
+    for (int i = 0; i < n; i++) order.emplace_back(-req[i].P->g.N, i);
+    std::stable_sort(order.begin(), order.end());
+    b->htiles.clear();
+    for (auto &o : order) {
+        const int i = o.second;
+        const GridDev &g = req[i].P->g;
+        const int xc = req[i].P->xchunk;
+        const int tz = (g.NZ + FZ - 1) / FZ, tyy = (g.NY + FY - 1) / FY, tx = (g.NX + xc - 1) / xc;
+        for (int c = 0; c < tx; c++)
+            for (int y = 0; y < tyy; y++)
+                for (int z = 0; z < tz; z++) b->htiles.push_back(make_int4(i, z, y, c));
+    }
+    if (b->htiles.size() > b->tiles_cap) {
+        cudaFree(b->dtiles);
+        b->dtiles = nullptr;
+        b->tiles_cap = 0;
+        if (int rc = ck(cudaMalloc(&b->dtiles, b->htiles.size() * sizeof(int4)), "batched TTI tile table")) return rc;
+        b->tiles_cap = b->htiles.size();
+    }
+    if (int rc = ck(cudaMemcpyAsync(b->dtiles, b->htiles.data(), b->htiles.size() * sizeof(int4),
+                                    cudaMemcpyHostToDevice, st),
+                    "batched TTI tile table copy"))
+        return rc;
+    if (int rc = ck(cudaStreamSynchronize(st), "batched TTI tile table copy")) return rc;
+    b->sig = sig;
+    return PROP_OK;
+}
+
+// a forward-step configuration of every request into the fixed device table
+// `slot` (0 or 1), once, before a graph that launches it is captured
+int tti_batch_fix(TtiBatch *b, const TtiBatchReq *req, int n, int slot, cudaStream_t st, std::string *err)
+{
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    for (int i = 0; i < n; i++)
+        if (!tti_batchable(req[i].P) || req[i].P->M != req[0].P->M || req[i].adjoint) return 1;
+    if (int rc = tti_batch_tiles(b, req, n, st, err)) return rc;
+    if ((size_t)n > b->fixed_cap) {
+        for (auto &d : b->dfixed) {
+            cudaFree(d);
+            d = nullptr;
+        }
+        b->fixed_cap = 0;
+        for (auto &d : b->dfixed)
+            if (int rc = ck(cudaMalloc(&d, n * sizeof(TtiShot)), "batched TTI fixed table")) return rc;
+        b->fixed_cap = n;
+    }
+    std::vector<TtiShot> H(n);
+    int rc = 1;
+    switch (req[0].P->M) {
+    case 2: rc = tti_batch_fill<2, 0, 0>(req, n, H.data(), err); break;
+    case 4: rc = tti_batch_fill<4, 0, 0>(req, n, H.data(), err); break;
+    case 6: rc = tti_batch_fill<6, 0, 0>(req, n, H.data(), err); break;
+    case 8: rc = tti_batch_fill<8, 0, 0>(req, n, H.data(), err); break;
+    }
+    if (rc) return rc;
+    if (int r2 = ck(cudaMemcpy(b->dfixed[slot], H.data(), n * sizeof(TtiShot), cudaMemcpyHostToDevice),
+                    "batched TTI fixed table copy"))
+        return r2;
+    b->fixed_n = n;
+    b->fixed_M = req[0].P->M;
+    b->w = req[0].P->w;
+    return PROP_OK;
+}
+
+// forward step of every shot of fixed table `slot` (capturable: launches only)
+template <int M>
+static int tti_batch_run_fixed(TtiBatch *b, int slot, cudaStream_t st)
+{
+    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * UL<M, 0, 0>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_rot_batch<M>, s1) && set_smem(tti_upd_batch<M, 0, 0>, s2);
+    (void)attr;
+    const unsigned nt = (unsigned)b->htiles.size();
+    const dim3 blk(TZ2, FY + 2, 1);
+    tti_rot_batch<M><<<nt, blk, s1, st>>>(b->dfixed[slot], b->dtiles, b->w);
+    tti_upd_batch<M, 0, 0><<<nt, blk, s2, st>>>(b->dfixed[slot], b->dtiles, b->w);
+    return cudaGetLastError() == cudaSuccess ? PROP_OK : PROP_ECUDA;
+}
+
+int tti_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t st)
+{
+    switch (b->fixed_M) {
+    case 2: return tti_batch_run_fixed<2>(b, slot, st);
+    case 4: return tti_batch_run_fixed<4>(b, slot, st);
+    case 6: return tti_batch_run_fixed<6>(b, slot, st);
+    case 8: return tti_batch_run_fixed<8>(b, slot, st);
+    }
+    return PROP_EINVAL;
+}
+
 int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
 {
     if (n < 1) return PROP_OK;
@@ -1576,41 +1700,7 @@ int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, 
         *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
         return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
     };
-    // tile table (cached while the shapes and x-extents stay the same)
-    std::vector<long long> sig;
-    for (int i = 0; i < n; i++) {
-        const GridDev &g = req[i].P->g;
-        sig.insert(sig.end(), {(long long)g.NX, (long long)g.NY, (long long)g.NZ, (long long)req[i].P->xchunk});
-    }
-    if (sig != b->sig) {
-        std::vector<std::pair<long long, int>> order;
-        for (int i = 0; i < n; i++) order.emplace_back(-req[i].P->g.N, i);
-        std::stable_sort(order.begin(), order.end());
-        b->htiles.clear();
-        for (auto &o : order) {
-            const int i = o.second;
-            const GridDev &g = req[i].P->g;
-            const int xc = req[i].P->xchunk;
-            const int tz = (g.NZ + FZ - 1) / FZ, tyy = (g.NY + FY - 1) / FY, tx = (g.NX + xc - 1) / xc;
-            for (int c = 0; c < tx; c++)
-                for (int y = 0; y < tyy; y++)
-                    for (int z = 0; z < tz; z++) b->htiles.push_back(make_int4(i, z, y, c));
-        }
-        if (b->htiles.size() > b->tiles_cap) {
-            cudaFree(b->dtiles);
-            b->dtiles = nullptr;
-            b->tiles_cap = 0;
-            if (int rc = ck(cudaMalloc(&b->dtiles, b->htiles.size() * sizeof(int4)), "batched TTI tile table"))
-                return rc;
-            b->tiles_cap = b->htiles.size();
-        }
-        if (int rc = ck(cudaMemcpyAsync(b->dtiles, b->htiles.data(), b->htiles.size() * sizeof(int4),
-                                        cudaMemcpyHostToDevice, st),
-                        "batched TTI tile table copy"))
-            return rc;
-        if (int rc = ck(cudaStreamSynchronize(st), "batched TTI tile table copy")) return rc;
-        b->sig = sig;
-    }
+    if (int rc = tti_batch_tiles(b, req, n, st, err)) return rc;
     if ((size_t)n > b->shots_cap) {
         cudaFree(b->dshots);
         b->dshots = nullptr;
