@@ -240,6 +240,7 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
                          stream=torch.cuda.current_stream(dev).cuda_stream, tti_operator=tti_operator)
     del model
     N = int(np.prod(prop.grid))
+    tile = {"z": 32, "y": prop.tile_rows, "x": prop.tile_planes}
     st = [torch.randn(prop.grid, device=dev) for _ in range(4)]
     prop.set_state(st)
     del st
@@ -270,6 +271,7 @@ def tti_throughput(wp, torch, dev, steps=40, nx=800, ny=800, nz=400, nbl=40, h=1
                                  "alg_bytes_per_pt": ALG_BYTES["tti"], "launch_ms": t * 1e3}}
     prop.close()
     out["grid"] = list(prop.grid)
+    out["tile"] = tile
     out["space_order"] = so
     out["hbm_peak_gbs"] = peaks()[0]
     out["fp32_peak_tflops"] = wp.fp32_peak()
@@ -401,7 +403,12 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
     rec = torch.from_numpy(p0.rec).to(dev)
     res = {}
     ref = None
-    for mode in modes:
+    runs = [(str(m), m, None) for m in modes]
+    if 1 in modes:      # FP32 checkpoints without the full-storage tail
+        runs.append(("1_no_tail", 1, "0"))
+    for key, mode, tail in runs:
+        if tail is not None:
+            os.environ["WAVEPROP_CKPT_TAIL"] = tail
         prop = wp.Propagator.from_problem(p0, snap_mode=mode, stream=stream)
         try:
             g, J = prop.gradient(wav, src, rec, d_obs)          # warm-up + result
@@ -415,11 +422,13 @@ def gradient_shots_per_hour(wp, torch, dev, nt, modes, small=False):
             if ref is None:
                 ref = gd
             err = float(torch.linalg.norm(gd - ref) / torch.linalg.norm(ref))
-            res[str(mode)] = {"seconds": s, "shots_per_hour": 3600.0 / s, "misfit": J,
-                              "rel_l2_vs_first_mode": err}
+            res[key] = {"seconds": s, "shots_per_hour": 3600.0 / s, "misfit": J,
+                        "rel_l2_vs_first_mode": err}
         except wp.PropError as e:
-            res[str(mode)] = {"error": str(e)}
+            res[key] = {"error": str(e)}
         prop.close()
+        if tail is not None:
+            del os.environ["WAVEPROP_CKPT_TAIL"]
     # gradient w.r.t. (m, eps, delta, theta, phi), full FP32 storage
     prop = wp.Propagator.from_problem(p0, snap_mode=modes[0], stream=stream)
     try:
@@ -772,6 +781,7 @@ def main():
     # replicas: every rank models its own shot (independent problems)
     prop = wp.Propagator.from_problem(prob, stream=torch.cuda.current_stream(dev).cuda_stream)
     N = int(np.prod(prop.grid))
+    tile = {"z": 32, "y": prop.tile_rows, "x": prop.tile_planes}
     nt = prob.nt
     wav = torch.from_numpy(prob.wavelet).to(dev)
     src = torch.from_numpy(prob.src).to(dev)
@@ -878,7 +888,7 @@ def main():
                            "physical_grid": [prob.nx, prob.ny, prob.nz],
                            "physical_gpts_per_s": value * (prob.nx * prob.ny * prob.nz) / float(np.prod(prop.grid)),
                            "time_steps_per_bench_step": 2 * nt, "shots_per_gpu": 1,
-                           "parallelism": f"replicas{world}",
+                           "parallelism": f"replicas{world}", "tile": tile,
                            "l2": "working set 2.2 GB >> L2 (no flush needed)"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk.summary()}

@@ -288,14 +288,19 @@ float prop_dt(const prop_t *p);
  * handle's stream).  Used for roofline accounting. */
 int prop_kernel_time(const prop_t *p, double *ms, long long *launches);
 
-/* Planes along x that one CTA of the x-streaming stencil kernels updates.
- * prop_create picks it by timing a few steps of the zero state for a set of
- * candidates (the choice is cached per kind, space order, grid and kernel
- * variant for the process; environment WAVEPROP_AUTOTUNE_CACHE=<file> keeps
+/* Tile shape of the x-streaming stencil kernels: a CTA updates a tile of
+ * 32 (z) x prop_tile_rows (y) columns over prop_tile_planes planes of x.
+ * prop_create picks both by timing a few steps of the zero state for a set
+ * of candidates: heights 8, 16 and 32 rows for the elastic and centred TTI
+ * passes on the TMA path (16 for the others), x-extents from NX down to 8
+ * planes.  The choice is cached per kind, space order, grid and kernel
+ * family for the process; environment WAVEPROP_AUTOTUNE_CACHE=<file> keeps
  * the cache across processes, WAVEPROP_AUTOTUNE=0 skips the timing and keeps
- * an occupancy heuristic).  Results are bitwise independent of the choice.
- * Returns 0 for p == NULL. */
+ * an occupancy heuristic at 16 rows, WAVEPROP_TILE_Y=8|16|32 fixes the
+ * height.  Results are bitwise independent of the choice.  Both return 0
+ * for p == NULL. */
 int prop_tile_planes(const prop_t *p);
+int prop_tile_rows(const prop_t *p);
 
 /* Forward modelling that allocates no device memory.  The paper has no
  * counterpart: this exists for callers that cannot call cudaMalloc, e.g. an

@@ -27,7 +27,7 @@ ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA
 ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_forward_saved", "prop_backward", "prop_grid_dims", "prop_set_state",
                "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
-               "prop_last_error", "prop_forward_noalloc", "prop_tile_planes",
+               "prop_last_error", "prop_forward_noalloc", "prop_tile_planes", "prop_tile_rows",
                "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves",
                "prop_gradient_aniso", "prop_stack_image", "prop_trim", "prop_forward_batch")
 
@@ -73,6 +73,7 @@ def lib():
         L.prop_dt.argtypes = [vp]
         L.prop_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
         L.prop_tile_planes.argtypes = [vp]
+        L.prop_tile_rows.argtypes = [vp]
         L.prop_gradient_batch.argtypes = [fpp, C.c_int, fpp, fpp, C.POINTER(C.c_int), fpp,
                                           C.POINTER(C.c_int), fpp, fpp, C.POINTER(C.c_double),
                                           C.c_size_t]
@@ -210,6 +211,11 @@ class Propagator:
     def tile_planes(self):
         """x-planes per CTA chosen by the autotuner at creation."""
         return lib().prop_tile_planes(self.h)
+
+    @property
+    def tile_rows(self):
+        """y-rows per tile (8, 16 or 32) chosen by the autotuner at creation."""
+        return lib().prop_tile_rows(self.h)
 
     def _out(self, like, shape):
         if _is_torch(like):

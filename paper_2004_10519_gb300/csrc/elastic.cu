@@ -581,6 +581,37 @@ int launch_adj_grad_tma(prop_s *P, float *const *S, const float *const *xk, cons
 
 }  // namespace
 
+// the pointwise kernels before and after the three TMA passes of a
+// transposed step with imaging, on a given stream (batched shots: the
+// passes are shared, these run per shot)
+void el_adj_pre_launch(prop_s *P, float *const *S, cudaStream_t st)
+{
+    const GridDev &g = P->g;
+    dim3 blk(TZ, TY, 1), grd((g.NZ + TZ - 1) / TZ, (g.NY + TY - 1) / TY, g.NX);
+    Fields9 s, sg;
+    for (int i = 0; i < 9; i++) {
+        s.f[i] = S[i];
+        sg.f[i] = P->tmp[i];
+    }
+    el_adj_pre_kernel<<<grd, blk, 0, st>>>(g, s, sg, P->lam, P->mu);
+    P->kern_launches += 1;
+}
+
+void el_face2_launch(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1, cudaStream_t st)
+{
+    const GridDev &g = P->g;
+    Fields9 s, f0, f1;
+    for (int i = 0; i < 9; i++) {
+        s.f[i] = S[i];
+        f0.f[i] = const_cast<float *>(xk[i]);
+        f1.f[i] = const_cast<float *>(xk1[i]);
+    }
+    float *const *pr = P->tmp + 9;
+    el_face2_kernel<<<dim3((g.NZ + 63) / 64, (g.NY + 7) / 8, g.NX), dim3(32, 8, 1), 0, st>>>(
+        g, s, f0, f1, P->bu, pr[3], pr[4], pr[5]);
+    P->kern_launches += 1;
+}
+
 // the edge and face products are summed over the steps of a sweep in
 // tmp[9..14] (the averaging transposes are linear and the same every step)
 // and gathered onto the nodes once at the end
@@ -598,6 +629,15 @@ int el_grad_gather(prop_s *P, float *const *g)
 int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1,
                        float *const *g)
 {
+    if (P->rdv && el_batchable(P)) {
+        ElBatchReq r{P, {}, 1, 1.f, {}, {}, {g[0], g[1], g[2]}};
+        for (int i = 0; i < 9; i++) {
+            r.S[i] = S[i];
+            r.xk[i] = xk[i];
+            r.xk1[i] = xk1[i];
+        }
+        return rdv_el_step(P, r);
+    }
     if (tma_usable(P)) return launch_adj_grad_tma(P, S, xk, xk1, g);
     switch (P->M) {
     case 2: return launch_adj_grad<2>(P, S, xk, xk1, g);
@@ -610,11 +650,21 @@ int el_launch_adj_grad(prop_s *P, float *const *S, const float *const *xk, const
 
 int el_step_adjoint_u(prop_s *P, float *const *S)
 {
+    if (P->rdv && el_batchable(P)) {
+        ElBatchReq r{P, {}, 0, -1.f, {}, {}, {}};
+        for (int i = 0; i < 9; i++) r.S[i] = S[i];
+        return rdv_el_step(P, r);
+    }
     return tma_usable(P) ? el_launch_tma(P, S, -1.f) : el_launch_fast(P, S, -1.f);
 }
 
 int el_launch_step(prop_s *P, float *const *S, bool adjoint)
 {
+    if (!adjoint && P->rdv && el_batchable(P)) {
+        ElBatchReq r{P, {}, 0, 1.f, {}, {}, {}};
+        for (int i = 0; i < 9; i++) r.S[i] = S[i];
+        return rdv_el_step(P, r);
+    }
     switch (P->M) {
     case 2: return launch_step<2>(P, S, adjoint);
     case 4: return launch_step<4>(P, S, adjoint);

@@ -74,6 +74,7 @@ struct prop_s {
     double *sumsq = nullptr; // device: partial sums of k_sumsq (kept between calls)
     float *tab = nullptr;    // per-axis absorbing-layer tables (GridDev::tab)
     int xchunk = 8;          // planes per CTA of the x-streaming stencil kernels
+    int tile_y = 16;         // rows (y) per tile of the TMA-fed passes: 8, 16 or 32
     // saved forward run for prop_backward
     bool saved = false;
     bool aniso = false;      // TTI gradient also w.r.t. eps, delta (prop_gradient_aniso)
@@ -84,6 +85,11 @@ struct prop_s {
     uint16_t *snap16 = nullptr; size_t snap16_bytes = 0;  // BF16/FP16 checkpoints
     float *snap_scale = nullptr;                          // per checkpoint field scales
     float *seg = nullptr;   size_t seg_bytes = 0;         // recompute segment buffer
+    // FP32 checkpoints: the last tail_T levels kept in full (sized from the
+    // free device memory at the forward run; none inside batches)
+    float *tail = nullptr;  size_t tail_bytes = 0;
+    int tail_T = 0;
+    bool no_tail = false;
     // timing of stencil kernels in the last call
     double kern_ms = 0.0;
     long long kern_launches = 0;
@@ -102,7 +108,7 @@ struct prop_s {
     // state buffers, direction and tile size it was captured with
     cudaGraphExec_t step_graph = nullptr;
     cudaStream_t graph_stream = nullptr;
-    int graph_adj = -1, graph_xc = 0;
+    int graph_adj = -1, graph_xc = 0, graph_ty = 0;
     long long graph_launches = 0;   // kernels in one replay
     float *graph_st[9] = {};
     // batched shots: the TTI steps of this handle meet those of the other
@@ -131,8 +137,11 @@ int tti_sp_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img
 // (zeta = C lam in tmp[6], tmp[7]; uses tmp[0..5], tmp[8..19])
 int tti_sp_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
                            float *ge, float *gd, float *const *gax);
-// centred first derivatives D p (out[0..2]) and D r (out[3..5]), TMA pass
-int tti_raw_derivs_tma(prop_s *P, const float *p, const float *r, float *const *out);
+// centred first derivatives D p (dp[0..2]), D r (dr[0..2]) and the products
+// of the staggered derivatives at the half points, h_i = (D+_i p)(D+_i r),
+// in one TMA rotation pass
+int tti_raw_half_tma(prop_s *P, const float *p, const float *r, float *const *dp, float *const *dr,
+                     float *const *h);
 // elastic step in place on S (9 fields); adjoint: transposed step (tbar form)
 int el_launch_step(prop_s *P, float *const *S, bool adjoint);
 // pipelined elastic step with time step dt_sign * dt (any NZ): forward (+1)
@@ -150,6 +159,9 @@ int acu_launch_tma(prop_s *P, float *const *S, const float *uf, float *grad);
 // bounded-wait self-test: a wait that nothing completes, limit in seconds
 int wait_probe_launch(prop_s *P, double seconds);
 int el_launch_tma(prop_s *P, float *const *S, float dt_sign);
+// true if the handle's TMA passes can run at a tile height of ty rows (8, 16,
+// 32: elastic and centred TTI; 16 only for the other kinds)
+bool tile_height_fits(const prop_s *P, int ty);
 // TTI imaging of the coupling matrix (TMA passes): with the forward field
 // (up, ur) at level n and the adjoint field (lp, lr) at level n+1,
 // ge += 2 dt^2 lam_p H0 p^n, gd += dt^2 (lam_p Hz r^n + lam_r H0 p^n) / sqrt(1+2 delta)
@@ -202,6 +214,24 @@ int tti_batch_fix(TtiBatch *b, const TtiBatchReq *req, int n, int slot, cudaStre
 int tti_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t stream);
 // true if the handle's TTI steps can join a batched launch
 bool tti_batchable(const prop_s *P);
+// batched elastic steps: mode 0 a step with time step sign * dt (forward
+// modelling +1, adjoint modelling -1); mode 1 the transposed step with
+// imaging of el_launch_adj_grad (S, xk, xk1, g as there)
+struct ElBatchReq {
+    prop_s *P;
+    float *S[9];
+    int mode;
+    float sign;
+    const float *xk[9], *xk1[9];
+    float *g[3];
+};
+bool el_batchable(const prop_s *P);
+// 0 launched; 1 not batchable together (launch one by one); < 0 error
+int el_batch_step(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t stream, std::string *err);
+// per-shot pointwise kernels of the batched transposed elastic step (elastic.cu)
+void el_adj_pre_launch(prop_s *P, float *const *S, cudaStream_t st);
+void el_face2_launch(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1, cudaStream_t st);
+int rdv_el_step(prop_s *P, const ElBatchReq &r);
 // a TTI step of a shot taking part in a rendezvous (runtime.cu): waits for
 // the other shots of the wave and shares their launch
 int rdv_tti_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r, float *grad);

@@ -302,6 +302,7 @@ static int ensure_ast(prop_s *P)
 
 static void free_snaps(prop_s *P)
 {
+    cudaFree(P->tail); P->tail = nullptr; P->tail_bytes = 0; P->tail_T = 0;
     cudaFree(P->snap); P->snap = nullptr; P->snap_bytes = 0;
     cudaFree(P->snap16); P->snap16 = nullptr; P->snap16_bytes = 0;
     cudaFree(P->snap_scale); P->snap_scale = nullptr;
@@ -330,12 +331,19 @@ static int step_state(prop_s *P, float **s, bool adjoint);
 static int zero_fields(prop_s *P, float *const *f, int n);
 
 // ---------------------------------------------------------------------------
-// autotuner: x-extent of the stencil tiles (planes per CTA).  It sets the
-// number of CTAs (waves on the SMs) against the queue warm-up cost per chunk.
-// Candidates are timed on a few forward steps of the zero state; the choice
-// is cached per (kind, space order, grid, TMA path) for the process and, if
-// WAVEPROP_AUTOTUNE_CACHE names a file, across processes.  WAVEPROP_AUTOTUNE=0
-// keeps the occupancy heuristic.  Results do not depend on the choice.
+// autotuner: tile shape of the stencil passes, i.e. the tile height (rows of
+// y per CTA: 8, 16 or 32, each a separately compiled set of TMA passes;
+// elastic and centred TTI) and the x-extent (planes per CTA).  The height
+// trades the y halo each plane re-fetches (2M rows per tile) against the
+// number of CTAs and their size; the x-extent sets the number of CTAs
+// (waves on the SMs) against the queue warm-up cost per chunk.  Candidates
+// are timed on a few forward steps of the zero state; the choice is cached
+// per (kind, space order, grid, TMA path) for the process and, if
+// WAVEPROP_AUTOTUNE_CACHE names a file, across processes (lines "key xc ty").
+// WAVEPROP_AUTOTUNE=0 keeps the occupancy heuristic at 16 rows;
+// WAVEPROP_TILE_Y=8|16|32 fixes the height and tunes only the x-extent.
+// Results do not depend on the choice (a point's arithmetic is the same in
+// every tile).
 // ---------------------------------------------------------------------------
 #include <map>
 #include <mutex>
@@ -343,46 +351,69 @@ static int zero_fields(prop_s *P, float *const *f, int n);
 #include <fstream>
 
 static std::mutex g_tune_mtx;
-static std::map<std::string, int> g_tune;
+static std::map<std::string, std::pair<int, int>> g_tune;
 static bool g_tune_loaded = false;
 
-static std::string tune_key(const prop_s *P)
+static std::string tune_key(const prop_s *P, int forced_ty)
 {
     std::ostringstream k;
     k << P->d.kind << ':' << P->M << ':' << P->g.NX << 'x' << P->g.NY << 'x' << P->g.NZ << ':'
-      << (tma_usable(P) ? "tma" : "pipe");
+      << (tma_usable(P) ? "tma" : "pipe") << ":h" << forced_ty;
     return k.str();
 }
 
-static int autotune_xchunk(prop_s *P)
+// WAVEPROP_TILE_Y: a fixed tile height, or 0 (tuned)
+static int forced_tile_y()
+{
+    const char *v = getenv("WAVEPROP_TILE_Y");
+    if (!v) return 0;
+    const int t = atoi(v);
+    return t == 8 || t == 16 || t == 32 ? t : 0;
+}
+
+static int autotune_tiles(prop_s *P)
 {
     const char *on = getenv("WAVEPROP_AUTOTUNE");
+    const int fty = forced_tile_y();
+    const bool tma = tma_usable(P);
+    if (fty && tma && tile_height_fits(P, fty)) P->tile_y = fty;
     // the 2D and staggered-pair passes have no x chunks
     if ((on && !strcmp(on, "0")) || P->d.kind == PROP_ELASTIC2D || P->d.tti_operator == 1) return PROP_OK;
     const char *path = getenv("WAVEPROP_AUTOTUNE_CACHE");
-    const std::string key = tune_key(P);
+    const std::string key = tune_key(P, fty);
     {
         std::lock_guard<std::mutex> lk(g_tune_mtx);
         if (!g_tune_loaded && path) {
             std::ifstream f(path);
-            std::string k;
-            int v;
-            while (f >> k >> v) g_tune[k] = v;
+            std::string line;
+            while (std::getline(f, line)) {
+                std::istringstream ls(line);
+                std::string k;
+                int xc = 0, ty = 0;
+                if (ls >> k >> xc >> ty && xc > 0) g_tune[k] = {xc, ty};
+            }
         }
         g_tune_loaded = true;
         auto it = g_tune.find(key);
-        if (it != g_tune.end()) {
-            P->xchunk = it->second;
+        if (it != g_tune.end() && (!tma || tile_height_fits(P, it->second.second))) {
+            P->xchunk = it->second.first;
+            if (tma) P->tile_y = it->second.second;
             return PROP_OK;
         }
     }
+    std::vector<int> heights;
+    if (!tma) heights = {P->tile_y};
+    else if (fty) heights = {P->tile_y};
+    else
+        for (int ty : {16, 8, 32})
+            if (tile_height_fits(P, ty)) heights.push_back(ty);
     const int NX = P->g.NX;
     std::vector<int> cand;
     for (int c : {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48}) {
         const int xc = std::max(8, (NX + c - 1) / c);
         if (std::find(cand.begin(), cand.end(), xc) == cand.end()) cand.push_back(xc);
     }
-    const int heuristic = P->xchunk;
+    const int heuristic = P->xchunk, ty0 = P->tile_y;
     if (std::find(cand.begin(), cand.end(), heuristic) == cand.end()) cand.push_back(heuristic);
     float *s[9];
     for (int i = 0; i < 9; i++) s[i] = P->st[i];
@@ -390,37 +421,42 @@ static int autotune_xchunk(prop_s *P)
     cudaEvent_t e0, e1;
     WP_CK(P, cudaEventCreate(&e0));
     WP_CK(P, cudaEventCreate(&e1));
-    int best = heuristic;
+    int best = heuristic, best_ty = ty0;
     float best_ms = 1e30f;
-    for (int xc : cand) {
-        P->xchunk = xc;
-        WP_TRY(step_state(P, s, false));                   // warm-up (first launch of a variant)
-        WP_CK(P, cudaEventRecord(e0, P->stream));
-        for (int i = 0; i < 3; i++) WP_TRY(step_state(P, s, false));
-        WP_CK(P, cudaEventRecord(e1, P->stream));
-        WP_CK(P, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        WP_CK(P, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = xc;
+    for (int ty : heights)
+        for (int xc : cand) {
+            P->tile_y = ty;
+            P->xchunk = xc;
+            WP_TRY(step_state(P, s, false));                   // warm-up (first launch of a variant)
+            WP_CK(P, cudaEventRecord(e0, P->stream));
+            for (int i = 0; i < 3; i++) WP_TRY(step_state(P, s, false));
+            WP_CK(P, cudaEventRecord(e1, P->stream));
+            WP_CK(P, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            WP_CK(P, cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = xc;
+                best_ty = ty;
+            }
         }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     for (int i = 0; i < 9; i++) P->st[i] = s[i];
     WP_TRY(zero_fields(P, s, nfields(P)));
     P->xchunk = best;
+    P->tile_y = best_ty;
     std::lock_guard<std::mutex> lk(g_tune_mtx);
-    g_tune[key] = best;
+    g_tune[key] = {best, best_ty};
     if (path) {
         std::ofstream f(path, std::ios::app);
-        f << key << ' ' << best << '\n';
+        f << key << ' ' << best << ' ' << best_ty << '\n';
     }
     return PROP_OK;
 }
 
 extern "C" int prop_tile_planes(const prop_t *P) { return P ? P->xchunk : 0; }
+extern "C" int prop_tile_rows(const prop_t *P) { return P ? P->tile_y : 0; }
 
 static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
 {
@@ -548,7 +584,7 @@ static int create_impl(prop_s *P, const prop_desc *d, const float *const *model)
     WP_TRY(ensure_tmp(P, d->kind == PROP_TTI ? (d->tti_operator == 1 ? 14 : 8) : 0));
     WP_MALLOC(P, P->flag, sizeof(int), "flag");
     WP_CK(P, cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
-    WP_TRY(autotune_xchunk(P));
+    WP_TRY(autotune_tiles(P));
     WP_CK(P, cudaMemsetAsync(P->flag, 0, sizeof(int), P->stream));
     WP_CK(P, cudaStreamSynchronize(P->stream));
     WP_CK(P, cudaGetLastError());
@@ -684,7 +720,8 @@ static int step_state(prop_s *P, float **s, bool adjoint)
 static bool step_graph_ready(prop_s *P, bool adjoint)
 {
     const int nf = nfields(P);
-    bool same = P->step_graph && P->graph_adj == (int)adjoint && P->graph_xc == P->xchunk;
+    bool same = P->step_graph && P->graph_adj == (int)adjoint && P->graph_xc == P->xchunk &&
+                P->graph_ty == P->tile_y;
     for (int i = 0; same && i < nf; i++) same = P->graph_st[i] == P->st[i];
     if (same) return true;
     if (P->step_graph) {
@@ -725,6 +762,7 @@ static bool step_graph_ready(prop_s *P, bool adjoint)
     }
     P->graph_adj = (int)adjoint;
     P->graph_xc = P->xchunk;
+    P->graph_ty = P->tile_y;
     for (int i = 0; i < 9; i++) P->graph_st[i] = P->st[i];
     return true;
 }
@@ -802,11 +840,21 @@ struct Geometry {
     ~Geometry() { sp_free(&S); sp_free(&R); }
 };
 
+// levels 1 .. ckpt_span are recomputed from checkpoints; the levels above
+// it (FP32 checkpoints only) are kept in full in the tail buffer
+static int ckpt_span(const prop_s *P) { return P->d.nt - 1 - P->tail_T; }
+
 static int ckpt_K(const prop_s *P)
 {
+    const int span = std::max(1, ckpt_span(P));
     int K = P->d.ckpt_interval;
-    if (K <= 0) K = (int)ceil(sqrt((double)P->d.nt));
-    return std::max(1, std::min(K, P->d.nt));
+    if (K <= 0) K = (int)ceil(sqrt((double)span));
+    return std::max(1, std::min(K, span));
+}
+static int ckpt_J(const prop_s *P)
+{
+    const int K = ckpt_K(P), span = ckpt_span(P);
+    return span > 0 ? (span + K - 1) / K : 0;
 }
 
 // fields per stored forward level: TTI p, r; acoustic u; elastic on the
@@ -822,12 +870,45 @@ static size_t snap_fields(const prop_s *P)
     }
 }
 
+// tail of full FP32 levels for FP32 checkpoints (TTI, acoustic): as many
+// levels as fit in 80 % of the free device memory left after the
+// checkpoints and the segment buffer; WAVEPROP_CKPT_TAIL caps it (0: none)
+static int choose_tail(prop_s *P)
+{
+    P->tail_T = 0;
+    if (P->d.snap_mode != SNAP_CKPT_FP32 || P->no_tail || P->aniso ||
+        (P->d.kind != PROP_TTI && P->d.kind != PROP_ACOUSTIC))
+        return 0;
+    const char *e = getenv("WAVEPROP_CKPT_TAIL");
+    long cap = e ? atol(e) : (long)P->d.nt;
+    if (cap <= 0) return 0;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t N = (size_t)P->g.N, level = snap_fields(P) * N * sizeof(float);
+    const size_t ck = (size_t)nfields(P) * N * sizeof(float);
+    const int nt = P->d.nt;
+    int T = (int)std::min<long>(cap, nt - 1);
+    // shrink until tail + checkpoints + segment buffer fit the budget
+    const double budget = 0.8 * (double)fr - (double)(1ull << 30);
+    for (; T > 0; T = T * 15 / 16) {
+        P->tail_T = T;
+        const double need = (double)T * level + (double)ckpt_J(P) * ck + (double)(ckpt_K(P) + 1) * level;
+        if (need <= budget) break;
+    }
+    P->tail_T = std::max(0, T);
+    return P->tail_T;
+}
+
 static int alloc_saves(prop_s *P)
 {
     free_snaps(P);
+    choose_tail(P);
     const size_t N = (size_t)P->g.N;
     const int nt = P->d.nt, K = ckpt_K(P);
-    const int J = (nt - 1 + K - 1) / K;     // checkpoints / segments
+    const int J = ckpt_J(P);                 // checkpoints / segments
     const int cf = nfields(P);               // fields per checkpoint
     switch (P->d.snap_mode) {
     case SNAP_FULL_FP32: {
@@ -839,8 +920,12 @@ static int alloc_saves(prop_s *P)
         break;
     }
     case SNAP_CKPT_FP32:
-        P->snap_bytes = (size_t)J * cf * N * sizeof(float);
+        P->snap_bytes = (size_t)std::max(J, 1) * cf * N * sizeof(float);
         WP_MALLOC(P, P->snap, P->snap_bytes, "FP32 checkpoints");
+        if (P->tail_T > 0) {
+            P->tail_bytes = (size_t)P->tail_T * snap_fields(P) * N * sizeof(float);
+            WP_MALLOC(P, P->tail, P->tail_bytes, "full FP32 tail of the checkpointed run");
+        }
         break;
     default:
         P->snap16_bytes = (size_t)J * cf * N * sizeof(uint16_t);
@@ -870,8 +955,8 @@ static float *seg_slot(prop_s *P, size_t slot)
 static int save_checkpoint(prop_s *P, int j, float *const *s)
 {
     const size_t N = (size_t)P->g.N;
-    const int cf = nfields(P), K = ckpt_K(P);
-    const size_t nscale = (size_t)((P->d.nt - 1 + K - 1) / K) * cf;   // scales, then 1024 partials
+    const int cf = nfields(P);
+    const size_t nscale = (size_t)ckpt_J(P) * cf;   // scales, then 1024 partials
     for (int f = 0; f < cf; f++) {
         const size_t slot = (size_t)j * cf + f;
         if (P->d.snap_mode == SNAP_CKPT_FP32)
@@ -967,11 +1052,18 @@ static int run_forward(prop_s *P, const Geometry &G, const float *wav, float *st
     const bool full = save && P->d.snap_mode == SNAP_FULL_FP32;
     const bool ckpt = save && !full;
     if (full && P->d.kind == PROP_ELASTIC) WP_TRY(store_full(P, s, 0));
+    const int span = ckpt_span(P), L0 = nt - P->tail_T;   // tail: levels L0 .. nt-1
+    const size_t tl = snap_fields(P) * (size_t)P->g.N;
     for (int n = 0; n < nt; n++) {
         record_rec(P, G.R, s, stage + (size_t)n * G.R.n);
-        if (ckpt && n % K == 0 && n < nt - 1) WP_TRY(save_checkpoint(P, n / K, s));
+        if (ckpt && n % K == 0 && n < span) WP_TRY(save_checkpoint(P, n / K, s));
         WP_TRY(fwd_step(P, s, G.S, wav, n));
         if (full) WP_TRY(store_full(P, s, n + 1));
+        if (ckpt && P->tail_T > 0 && n + 1 >= L0 && n + 1 <= nt - 1) {
+            float *d = P->tail + (size_t)(n + 1 - L0) * tl;
+            for (size_t f = 0; f < snap_fields(P); f++)
+                WP_CK(P, cudaMemcpyAsync(d + f * P->g.N, s[f], P->g.N * 4, cudaMemcpyDeviceToDevice, P->stream));
+        }
     }
     // the final state, in st[] order, for prop_get_state (buffers permuted)
     for (int i = 0; i < nfields(P); i++) P->st[i] = s[i];
@@ -1109,10 +1201,16 @@ static int tti_sweep(prop_s *P, const Geometry &G, const float *res, const float
         }
         return PROP_OK;
     }
-    const int K = ckpt_K(P), J = (nt - 1 + K - 1) / K;
+    const int K = ckpt_K(P), J = ckpt_J(P), span = ckpt_span(P), L0 = nt - P->tail_T;
+    // the tail: levels kept in full (no eps/delta/axis imaging here: the tail
+    // is not used for prop_gradient_aniso)
+    for (int k = nt - 1; k >= L0; k--) {
+        const float *u = P->tail + (size_t)(k - L0) * 2 * N;
+        WP_TRY(adj_iter(k, u, u + N));
+    }
     float *s[4] = {P->st[0], P->st[1], P->st[2], P->st[3]};
     for (int j = J - 1; j >= 0; j--) {
-        const int n0 = j * K, E = std::min((j + 1) * K, nt - 1);
+        const int n0 = j * K, E = std::min((j + 1) * K, span);
         // restore level n0 and recompute levels n0+1..E
         float *f[4] = {P->st[0], P->st[1], P->st[2], P->st[3]};
         for (int i = 0; i < 4; i++) s[i] = f[i];
@@ -1163,9 +1261,10 @@ static int ac_sweep(prop_s *P, const Geometry &G, const float *res, const float 
         return PROP_OK;
     }
     const size_t N = (size_t)P->g.N;
-    const int K = ckpt_K(P), J = (nt - 1 + K - 1) / K;
+    const int K = ckpt_K(P), J = ckpt_J(P), span = ckpt_span(P), L0 = nt - P->tail_T;
+    for (int k = nt - 1; k >= L0; k--) WP_TRY(adj_iter(k, P->tail + (size_t)(k - L0) * N));
     for (int j = J - 1; j >= 0; j--) {
-        const int n0 = j * K, E = std::min((j + 1) * K, nt - 1);
+        const int n0 = j * K, E = std::min((j + 1) * K, span);
         // restore level n0 and recompute levels n0+1..E (slot i: level n0+1+i)
         float *s[2] = {P->st[0], P->st[1]};
         WP_TRY(load_checkpoint(P, j, s));
@@ -1415,7 +1514,11 @@ extern "C" int prop_trim(prop_t *P)
 static size_t gradient_bytes(const prop_s *P, int nrec)
 {
     const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
-    const int nt = P->d.nt, K = ckpt_K(P), J = (nt - 1 + K - 1) / K, cf = nfields(P);
+    const int nt = P->d.nt, cf = nfields(P);
+    int K = P->d.ckpt_interval;              // without a tail (batches keep none)
+    if (K <= 0) K = (int)ceil(sqrt((double)std::max(1, nt - 1)));
+    K = std::max(1, std::min(K, std::max(1, nt - 1)));
+    const int J = (nt - 1 + K - 1) / K;
     size_t b = 0;
     switch (P->d.snap_mode) {
     case SNAP_FULL_FP32:
@@ -1498,30 +1601,37 @@ extern "C" int prop_gradient(prop_t *P, const float *wavelet, const float *src_x
 #include <thread>
 
 // ---------------------------------------------------------------------------
-// Rendezvous of the TTI steps of one wave.  Every shot runs its own
+// Rendezvous of the steps of one wave.  Every shot runs its own
 // prop_gradient on its own host thread and stream; the shots' sweeps issue
 // their steps in the same order (same nt, storage mode and checkpoint
 // interval), so the k-th step of each shot can share one launch per pass.
 // A step records an event on the shot's stream and waits for the other
 // participants; the last to arrive makes a shared stream wait on all the
-// events, launches the batched passes (tile table over all shots), records
-// `done`, and each shot's stream waits on `done` before its next work.
-// Shots leave the group when their gradient returns, so participants with
-// other step sequences never wait for each other; steps of different kinds
-// met in one round are launched one by one.
+// events, launches the batched passes (tile table over all shots; TTI and
+// elastic shots of a round in one launch per kind), records `done`, and
+// each shot's stream waits on `done` before its next work.  Shots leave the
+// group when their gradient returns, so participants with other step
+// sequences never wait for each other; steps that cannot share a launch
+// (different step kinds of one propagator in a round) run one by one.
 // ---------------------------------------------------------------------------
+struct RdvReq {
+    int kind;                 // 1 TTI step, 2 elastic step
+    TtiBatchReq t;
+    ElBatchReq e;
+};
+
 struct StepRendezvous {
     std::mutex mu;
     std::condition_variable cv;
     int active = 0, arrived = 0;
     unsigned long long gen = 0;
-    std::vector<TtiBatchReq> req;
+    std::vector<RdvReq> req;
     std::vector<char> present;
     std::vector<cudaEvent_t> ev;
     std::vector<int> result;      // 0 launched, 1 launch alone, < 0 error
     cudaStream_t cs = nullptr;
     cudaEvent_t done[2] = {};
-    TtiBatch *tb = nullptr;
+    TtiBatch *tb = nullptr, *eb = nullptr;   // tables of the TTI and of the elastic shots
     std::string err;
     long long batched = 0, alone = 0;
 
@@ -1529,6 +1639,7 @@ struct StepRendezvous {
     {
         if (cs) cudaStreamSynchronize(cs);
         tti_batch_free(tb);
+        tti_batch_free(eb);
         for (auto e : ev)
             if (e) cudaEventDestroy(e);
         for (auto e : done)
@@ -1547,30 +1658,46 @@ struct StepRendezvous {
         for (auto &e : done)
             if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return PROP_ECUDA;
         tb = tti_batch_new();
+        eb = tti_batch_new();
         return PROP_OK;
     }
-    // with the lock held, by the last participant to arrive
+    // with the lock held, by the last participant to arrive: one shared
+    // launch per kind of step present in the round
     void launch_all()
     {
-        std::vector<TtiBatchReq> r;
-        std::vector<int> who;
+        std::vector<TtiBatchReq> rt;
+        std::vector<ElBatchReq> re;
+        std::vector<int> wt, we;
         for (size_t i = 0; i < req.size(); i++)
             if (present[i]) {
-                r.push_back(req[i]);
-                who.push_back((int)i);
                 cudaStreamWaitEvent(cs, ev[i], 0);
+                if (req[i].kind == 1) {
+                    rt.push_back(req[i].t);
+                    wt.push_back((int)i);
+                } else {
+                    re.push_back(req[i].e);
+                    we.push_back((int)i);
+                }
             }
-        int rc = tti_batch_step(tb, r.data(), (int)r.size(), cs, &err);
-        if (rc == PROP_OK && cudaEventRecord(done[gen & 1], cs) != cudaSuccess) {
-            err = "batched TTI step: event record failed";
-            rc = PROP_ECUDA;
+        bool any = false;
+        auto settle = [&](int rc, const std::vector<int> &who) {
+            if (who.empty()) return;
+            if (rc == PROP_OK) {
+                batched++;
+                any = true;
+            } else if (rc == 1) {
+                alone++;
+            }
+            for (int i : who) result[i] = rc;
+        };
+        settle(rt.empty() ? PROP_OK : tti_batch_step(tb, rt.data(), (int)rt.size(), cs, &err), wt);
+        settle(re.empty() ? PROP_OK : el_batch_step(eb, re.data(), (int)re.size(), cs, &err), we);
+        if (any && cudaEventRecord(done[gen & 1], cs) != cudaSuccess) {
+            err = "batched step: event record failed";
+            for (size_t i = 0; i < req.size(); i++)
+                if (present[i] && result[i] == PROP_OK) result[i] = PROP_ECUDA;
         }
-        if (rc == PROP_OK) batched++;
-        else if (rc == 1) alone++;
-        for (int i : who) {
-            result[i] = rc;
-            present[i] = 0;
-        }
+        for (size_t i = 0; i < req.size(); i++) present[i] = 0;
         arrived = 0;
         gen++;
         cv.notify_all();
@@ -1581,29 +1708,59 @@ struct StepRendezvous {
         active--;
         if (active > 0 && arrived == active) launch_all();
     }
+    // one shot's step: deposit, wait for the round, then order the shot's
+    // stream after the shared launch (0), or tell it to launch alone (1)
+    int meet(prop_s *P, const RdvReq &r, cudaEvent_t *d)
+    {
+        const int i = P->rdv_idx;
+        std::unique_lock<std::mutex> lk(mu);
+        const cudaError_t e = cudaEventRecord(ev[i], P->stream);
+        if (e != cudaSuccess) return wp_cuda(P, e, "cudaEventRecord (batched step)");
+        req[i] = r;
+        present[i] = 1;
+        const unsigned long long my = gen;
+        if (++arrived == active) launch_all();
+        else cv.wait(lk, [&] { return gen != my; });
+        *d = done[my & 1];
+        if (result[i] < 0) return wp_fail(P, result[i], err);
+        return result[i];
+    }
 };
 
 int rdv_tti_step(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r, float *grad)
 {
     StepRendezvous *R = P->rdv;
-    const int i = P->rdv_idx;
-    int res;
-    cudaEvent_t d;
-    {
-        std::unique_lock<std::mutex> lk(R->mu);
-        WP_CK(P, cudaEventRecord(R->ev[i], P->stream));
-        R->req[i] = TtiBatchReq{P, {S[0], S[1], S[2], S[3]}, adjoint, img_p, img_r, grad};
-        R->present[i] = 1;
-        const unsigned long long my = R->gen;
-        if (++R->arrived == R->active) R->launch_all();
-        else R->cv.wait(lk, [&] { return R->gen != my; });
-        res = R->result[i];
-        d = R->done[my & 1];
-        if (res < 0) return wp_fail(P, res, R->err);
-    }
+    RdvReq r{};
+    r.kind = 1;
+    r.t = TtiBatchReq{P, {S[0], S[1], S[2], S[3]}, adjoint, img_p, img_r, grad};
+    cudaEvent_t d = nullptr;
+    const int res = R->meet(P, r, &d);
+    if (res < 0) return res;
     if (res == 1) {                 // could not share the launch: this shot alone
         P->rdv = nullptr;
         const int rc = tti_launch_step(P, S, adjoint, img_p, img_r, grad);
+        P->rdv = R;
+        return rc;
+    }
+    WP_CK(P, cudaStreamWaitEvent(P->stream, d, 0));
+    return PROP_OK;
+}
+
+int rdv_el_step(prop_s *P, const ElBatchReq &e)
+{
+    StepRendezvous *R = P->rdv;
+    RdvReq r{};
+    r.kind = 2;
+    r.e = e;
+    cudaEvent_t d = nullptr;
+    const int res = R->meet(P, r, &d);
+    if (res < 0) return res;
+    if (res == 1) {
+        P->rdv = nullptr;
+        int rc;
+        if (e.mode == 1) rc = el_launch_adj_grad(P, e.S, e.xk, e.xk1, e.g);
+        else if (e.sign < 0.f) rc = el_step_adjoint_u(P, e.S);
+        else rc = el_launch_step(P, e.S, false);
         P->rdv = R;
         return rc;
     }
@@ -1857,14 +2014,14 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
         std::unique_ptr<StepRendezvous> rdv;
         int nb = 0;
         for (int i = 0; i < nshots; i++)
-            if (wave[i] == w && tti_batchable(shots[i]) && !shots[i]->broken) nb++;
+            if (wave[i] == w && (tti_batchable(shots[i]) || el_batchable(shots[i])) && !shots[i]->broken) nb++;
         if (share && nb >= 2) {
             rdv.reset(new StepRendezvous());
             if (rdv->init(nshots) != PROP_OK) rdv.reset();
             else rdv->active = nb;
         }
         for (int i = 0; i < nshots; i++)
-            if (rdv && wave[i] == w && tti_batchable(shots[i]) && !shots[i]->broken) {
+            if (rdv && wave[i] == w && (tti_batchable(shots[i]) || el_batchable(shots[i])) && !shots[i]->broken) {
                 shots[i]->rdv = rdv.get();
                 shots[i]->rdv_idx = i;
             }
@@ -1903,8 +2060,10 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
                 cudaEventRecord(e0, own);
                 cudaStreamWaitEvent(s, e0, 0);
                 P->stream = s;
+                P->no_tail = true;                    // concurrent shots share the free memory
                 rc[i] = prop_gradient(P, wavelet[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i], d_obs[i],
                                       grad[i], &mis[i]);
+                P->no_tail = false;
                 if (P->rdv) {                         // no more steps from this shot
                     P->rdv->leave();
                     P->rdv = nullptr;

@@ -1,9 +1,10 @@
 // Stencil passes fed by the Tensor Memory Accelerator (sm_103a).
 //
-// Each CTA owns a 32(z) x 16(y) tile of columns and streams along x; each of
-// its 256 threads updates two adjacent z points, so shared-memory taps and
-// global accesses are 8-byte (float2) and every y-tap row serves two
-// outputs.  For every plane the y/z-halo boxes of the differentiated fields
+// Each CTA owns a 32(z) x FY(y) tile of columns (FY = 8, 16 or 32 rows, one
+// compiled set of passes per height, see tma.cuh) and streams along x; each
+// of its 16 FY consumer threads updates two adjacent z points, so
+// shared-memory taps and global accesses are 8-byte (float2) and every y-tap
+// row serves two outputs.  For every plane the y/z-halo boxes of the differentiated fields
 // are fetched with cp.async.bulk.tensor into a shared-memory ring of three
 // stages (four in the TTI rotation and acoustic forward passes); out-of-grid
 // elements arrive as zeros, which is the zero extension of the
@@ -52,7 +53,7 @@ struct VMaps {
     CUtensorMap xy, yy, xz, zz, yz, b, v[3], qxx, qxy, qxz, bi;
 };
 
-// Per consumer thread and tile (32 z x 16 y columns at (z0, y0)): position,
+// Per consumer thread and tile (32 z x FY y columns at (z0, y0)): position,
 // shared-memory offsets and the y/z Cerjan factors of its two z points.
 template <int M>
 struct ElCtx {
@@ -217,9 +218,10 @@ WP_DEV void v_plane(const GridDev &g, const FDW &w, const F9 &s, const F5 &o, co
     }
 }
 
+// one tile (bx, by: z and y tile; bz: x chunk of xc planes)
 template <int M, int ADJ>
-__global__ void __launch_bounds__(NTP, M <= 4 ? 2 : 1)
-el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int xc, int *err)
+WP_DEV void el_vpass_body(const GridDev &g, const FDW &w, const F9 &s, const F5 &o, const VMaps &mp, int bx,
+                          int by, int bz, int xc, int *err)
 {
     using L = VL<M>;
     constexpr int Q = 2 * M;
@@ -227,8 +229,8 @@ el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
     const bool lead = warp == 0 && lane == 0;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
+    const int z0 = bx * FZ, y0 = by * FY;
+    const int xa = bz * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) { v_issue<M>(mp, sm + st * L::SZ, &bars[st], z0, y0, x, g.NX); };
     Ring R(bars);
     if (lead) R.init();
@@ -248,6 +250,13 @@ el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int
         v_plane<M, ADJ>(g, w, s, o, sm + R.st * L::SZ, t, x, qxx, qxy, qxz);
         R.release(lane);
     }
+}
+
+template <int M, int ADJ>
+__global__ void __launch_bounds__(NTP, occ(M <= 4 ? 2 : 1))
+el_vpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ VMaps mp, int xc, int *err)
+{
+    el_vpass_body<M, ADJ>(g, w, s, o, mp, blockIdx.x, blockIdx.y, blockIdx.z, xc, err);
 }
 
 // ---------------------------------------------------------------------------
@@ -418,8 +427,8 @@ WP_DEV void t_plane(const GridDev &g, const FDW &w, const F9 &s, const F5 &o, co
 }
 
 template <int M, int MODE>
-__global__ void __launch_bounds__(NTP, M <= 4 ? 2 : 1)
-el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int xc, int *err)
+WP_DEV void el_tpass_body(const GridDev &g, const FDW &w, const F9 &s, const F5 &o, const TMaps &mp, int bx,
+                          int by, int bz, int xc, int *err)
 {
     using L = TL<M, MODE>;
     constexpr int Q = 2 * M;
@@ -427,8 +436,8 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
     uint64_t *bars = reinterpret_cast<uint64_t *>(sm + NSTAGE * L::SZ);   // after the ring
     const int tz = threadIdx.x, ty = threadIdx.y, warp = (ty * TZ2 + tz) >> 5, lane = (ty * TZ2 + tz) & 31;
     const bool lead = warp == 0 && lane == 0;
-    const int z0 = blockIdx.x * FZ, y0 = blockIdx.y * FY;
-    const int xa = blockIdx.z * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
+    const int z0 = bx * FZ, y0 = by * FY;
+    const int xa = bz * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) { t_issue<M, MODE>(mp, sm + st * L::SZ, &bars[st], z0, y0, x, g.NX); };
     Ring R(bars);
     if (lead) R.init();
@@ -450,10 +459,51 @@ el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int
     }
 }
 
+template <int M, int MODE>
+__global__ void __launch_bounds__(NTP, occ(M <= 4 ? 2 : 1))
+el_tpass_tma(GridDev g, FDW w, F9 s, F5 o, const __grid_constant__ TMaps mp, int xc, int *err)
+{
+    el_tpass_body<M, MODE>(g, w, s, o, mp, blockIdx.x, blockIdx.y, blockIdx.z, xc, err);
+}
+
+// batched elastic passes: per-shot entries (grid with the step's dt,
+// fields, maps) and a tile table over all shots, as for TTI
+struct ElShot {
+    VMaps vm;
+    TMaps tm;
+    GridDev g;
+    F9 s;
+    F5 o;
+    int xc;
+    int *flag;
+};
+
+template <int M, int ADJ>
+__global__ void __launch_bounds__(NTP, occ(M <= 4 ? 2 : 1))
+el_vpass_batch(const ElShot *__restrict__ shots, const int4 *__restrict__ tiles, FDW w)
+{
+    const int4 tl = tiles[blockIdx.x];
+    const ElShot &S = shots[tl.x];
+    el_vpass_body<M, ADJ>(S.g, w, S.s, S.o, S.vm, tl.y, tl.z, tl.w, S.xc, S.flag);
+}
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(NTP, occ(M <= 4 ? 2 : 1))
+el_tpass_batch(const ElShot *__restrict__ shots, const int4 *__restrict__ tiles, FDW w)
+{
+    const int4 tl = tiles[blockIdx.x];
+    const ElShot &S = shots[tl.x];
+    el_tpass_body<M, MODE>(S.g, w, S.s, S.o, S.tm, tl.y, tl.z, tl.w, S.xc, S.flag);
+}
+
 // ---------------------------------------------------------------------------
 // TTI rotation pass on (p, r), or on zeta = C lam in the transposed step
-// (the update pass of the previous adjoint step writes zeta).  RAW: write
-// the unprojected first derivatives D p, D r (tilt/azimuth imaging).
+// (the update pass of the previous adjoint step writes zeta).  MODE 1: write
+// the unprojected first derivatives D p, D r (tilt/azimuth imaging).  MODE 2:
+// also the products of the staggered first derivatives at the half points,
+// h_i = (D+_i p)(D+_i r), D+_i f(q + 1/2) = sum_k b_k (f(q + k e_i) -
+// f(q - (k - 1) e_i)) / h, zero outside the grid (staggered-pair tilt/azimuth
+// imaging with p = zeta_p, r = u_p or p = zeta_r, r = u_r)
 // stage: [p rect] [r rect] [queue heads p, r (x+M)] [n_x, n_y (plane x)]
 // ---------------------------------------------------------------------------
 template <int M>
@@ -468,14 +518,19 @@ struct RMaps {
     CUtensorMap p, r, qp, qr, nx, ny;
 };
 
-// one tile (bx, by: 32 z x 16 y columns; bz: x chunk of xc planes)
-template <int M, bool RAW>
+// one tile (bx, by: 32 z x FY y columns; bz: x chunk of xc planes)
+struct F3 {
+    float *f[3];
+};
+
+template <int M, int MODE>
 WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict__ p,
                          const float *__restrict__ r, const RMaps &mp, float *__restrict__ ex,
                          float *__restrict__ ey, float *__restrict__ ez, float *__restrict__ fx,
-                         float *__restrict__ fy, float *__restrict__ fz, int bx, int by, int bz, int xc,
-                         int *err)
+                         float *__restrict__ fy, float *__restrict__ fz, const F3 &hh, int bx, int by, int bz,
+                         int xc, int *err)
 {
+    constexpr bool RAW = MODE != 0, HALF = MODE == 2;
     using L = RL<M>;
     using B = BX<M>;
     constexpr int Q = 2 * M + 1;
@@ -533,6 +588,7 @@ WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict
             zwin<M>(sr + cy * B::RC, cz, wr);
             // paired FP32: .x the first z point, .y the second
             float2 gp0 = Z2, gp1 = Z2, gp2 = Z2, gr0 = Z2, gr1 = Z2, gr2 = Z2;
+            float2 hp0 = Z2, hp1 = Z2, hp2 = Z2, hr0 = Z2, hr1 = Z2, hr2 = Z2;   // HALF: staggered sums
 #pragma unroll
             for (int k = 1; k <= M; k++) {
                 const float2 c = f2s(w.c[k - 1]);
@@ -542,6 +598,15 @@ WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict
                 gr1 = f2fma(c, f2sub(lds2(sr + ci + k * B::RC), lds2(sr + ci - k * B::RC)), gr1);
                 gp2 = f2fma(c, make_float2(wp[M + k] - wp[M - k], wp[M + k + 1] - wp[M - k + 1]), gp2);
                 gr2 = f2fma(c, make_float2(wr[M + k] - wr[M - k], wr[M + k + 1] - wr[M - k + 1]), gr2);
+                if constexpr (HALF) {
+                    const float2 b = f2s(w.b[k - 1]);
+                    hp0 = f2fma(b, f2sub(qp[M + k], qp[M - k + 1]), hp0);
+                    hr0 = f2fma(b, f2sub(qr[M + k], qr[M - k + 1]), hr0);
+                    hp1 = f2fma(b, f2sub(lds2(sp + ci + k * B::RC), lds2(sp + ci - (k - 1) * B::RC)), hp1);
+                    hr1 = f2fma(b, f2sub(lds2(sr + ci + k * B::RC), lds2(sr + ci - (k - 1) * B::RC)), hr1);
+                    hp2 = f2fma(b, make_float2(wp[M + k] - wp[M - k + 1], wp[M + k + 1] - wp[M - k + 2]), hp2);
+                    hr2 = f2fma(b, make_float2(wr[M + k] - wr[M - k + 1], wr[M + k + 1] - wr[M - k + 2]), hr2);
+                }
             }
             const float gp0a = gp0.x, gp0b = gp0.y, gp1a = gp1.x, gp1b = gp1.y, gp2a = gp2.x, gp2b = gp2.y;
             const float gr0a = gr0.x, gr0b = gr0.y, gr1a = gr1.x, gr1b = gr1.y, gr2a = gr2.x, gr2b = gr2.y;
@@ -579,6 +644,12 @@ WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict
             st2(fx, q, o[0][3], o[1][3]);
             st2(fy, q, o[0][4], o[1][4]);
             st2(fz, q, o[0][5], o[1][5]);
+            if constexpr (HALF) {
+                const float ih2 = ih * ih;
+                st2(hh.f[0], q, hp0.x * hr0.x * ih2, hp0.y * hr0.y * ih2);
+                st2(hh.f[1], q, hp1.x * hr1.x * ih2, hp1.y * hr1.y * ih2);
+                st2(hh.f[2], q, hp2.x * hr2.x * ih2, hp2.y * hr2.y * ih2);
+            }
         }
 #pragma unroll
         for (int j = 0; j < Q - 1; j++) {
@@ -589,14 +660,15 @@ WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict
     }
 }
 
-template <int M, bool RAW = false>
-__global__ void __launch_bounds__(NTP, 2)
+template <int M, int MODE = 0>
+__global__ void __launch_bounds__(NTP, occ(MODE == 2 && M > 6 ? 1 : 2))
 tti_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__restrict__ r,
             const __grid_constant__ RMaps mp, float *__restrict__ ex, float *__restrict__ ey,
             float *__restrict__ ez, float *__restrict__ fx, float *__restrict__ fy, float *__restrict__ fz,
-            int xc, int *err)
+            F3 hh, int xc, int *err)
 {
-    tti_rot_body<M, RAW>(g, w, p, r, mp, ex, ey, ez, fx, fy, fz, blockIdx.x, blockIdx.y, blockIdx.z, xc, err);
+    tti_rot_body<M, MODE>(g, w, p, r, mp, ex, ey, ez, fx, fy, fz, hh, blockIdx.x, blockIdx.y, blockIdx.z, xc,
+                          err);
 }
 
 // ---------------------------------------------------------------------------
@@ -705,10 +777,8 @@ WP_DEV void tti_upd_body(const GridDev &g, const FDW &w, const float *__restrict
         }
         const float *S = sm + R.st * L::SZ;
         const float *I = S + L::OI + ii;
-        {
-            qe[Q - 1] = lds2(I + L::QE * IS);
-            qf[Q - 1] = lds2(I + L::QF * IS);
-        }
+        qe[Q - 1] = lds2(I + L::QE * IS);
+        qf[Q - 1] = lds2(I + L::QF * IS);
         if (act) {
             const float *sey = S + L::OEY, *sfy = S + L::OFY;
             float we[2 * M + 2], wf[2 * M + 2];
@@ -785,7 +855,7 @@ WP_DEV void tti_upd_body(const GridDev &g, const FDW &w, const float *__restrict
 }
 
 template <int M, int ADJ, int GRAD>
-__global__ void __launch_bounds__(NTP, 2)
+__global__ void __launch_bounds__(NTP, occ(2))
 tti_upd_tma(GridDev g, FDW w, const float *__restrict__ ex, const float *__restrict__ fx,
             const __grid_constant__ UMaps mp, float *__restrict__ pp, float *__restrict__ rp,
             float *__restrict__ grad, float *__restrict__ zp, float *__restrict__ zr, int *flag, int check,
@@ -815,17 +885,17 @@ struct TtiShot {
 };
 
 template <int M>
-__global__ void __launch_bounds__(NTP, 2)
+__global__ void __launch_bounds__(NTP, occ(2))
 tti_rot_batch(const TtiShot *__restrict__ shots, const int4 *__restrict__ tiles, FDW w)
 {
     const int4 tl = tiles[blockIdx.x];
     const TtiShot &S = shots[tl.x];
-    tti_rot_body<M, false>(S.g, w, S.rp, S.rr, S.rm, S.t[0], S.t[1], S.t[2], S.t[3], S.t[4], S.t[5], tl.y, tl.z,
+    tti_rot_body<M, 0>(S.g, w, S.rp, S.rr, S.rm, S.t[0], S.t[1], S.t[2], S.t[3], S.t[4], S.t[5], F3{}, tl.y, tl.z,
                            tl.w, S.xc, S.flag);
 }
 
 template <int M, int ADJ, int GRAD>
-__global__ void __launch_bounds__(NTP, 2)
+__global__ void __launch_bounds__(NTP, occ(2))
 tti_upd_batch(const TtiShot *__restrict__ shots, const int4 *__restrict__ tiles, FDW w)
 {
     const int4 tl = tiles[blockIdx.x];
@@ -1126,8 +1196,8 @@ int tti_launch(prop_s *P, float *const *S, const float *up, const float *ur, flo
                  s2 = NSTAGE * UL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(tti_rot_tma<M>, s1) && set_smem(tti_upd_tma<M, ADJ, GRAD>, s2);
     (void)attr;
-    tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, rp_, rr_, rm, t[0], t[1], t[2], t[3], t[4], t[5], xc,
-                                               P->flag);
+    tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, rp_, rr_, rm, t[0], t[1], t[2], t[3], t[4], t[5], F3{},
+                                               xc, P->flag);
     tti_upd_tma<M, ADJ, GRAD><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, S[2], S[3], grad, t[6], t[7],
                                                           P->flag, P->d.check_nan, xc, P->flag);
     P->kern_launches += 2;
@@ -1218,8 +1288,8 @@ int tti_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp
     const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * UL<M, 2, 0>::SZ * sizeof(float) + 64;
     static const bool attr = set_smem(tti_rot_tma<M>, s1) && set_smem(tti_upd_tma<M, 2, 0>, s2);
     (void)attr;
-    tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[0], t[1], t[2], t[3], t[4], t[5], xc,
-                                               P->flag);
+    tti_rot_tma<M><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[0], t[1], t[2], t[3], t[4], t[5], F3{},
+                                               xc, P->flag);
     tti_upd_tma<M, 2, 0><<<grd, blk, s2, P->stream>>>(g, P->w, t[0], t[3], um, nullptr, nullptr, ge, gd, nullptr,
                                                      P->flag, 0, xc, P->flag);
     P->kern_launches += 2;
@@ -1229,12 +1299,12 @@ int tti_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp
              map_of(P, t[6], FZ, FY, &rz.qp) && map_of(P, t[7], FZ, FY, &rz.qr) && (rz.nx = rm.nx, true) &&
              (rz.ny = rm.ny, true);
         if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
-        static const bool attr_raw = set_smem(tti_rot_tma<M, true>, s1);
+        static const bool attr_raw = set_smem(tti_rot_tma<M, 1>, s1);
         (void)attr_raw;
-        tti_rot_tma<M, true><<<grd, blk, s1, P->stream>>>(g, P->w, t[6], t[7], rz, t[0], t[1], t[2], t[3], t[4],
-                                                          t[5], xc, P->flag);
-        tti_rot_tma<M, true><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[8], t[9], t[10], t[11], t[12],
-                                                          t[13], xc, P->flag);
+        tti_rot_tma<M, 1><<<grd, blk, s1, P->stream>>>(g, P->w, t[6], t[7], rz, t[0], t[1], t[2], t[3], t[4], t[5],
+                                                       F3{}, xc, P->flag);
+        tti_rot_tma<M, 1><<<grd, blk, s1, P->stream>>>(g, P->w, up, ur, rm, t[8], t[9], t[10], t[11], t[12], t[13],
+                                                       F3{}, xc, P->flag);
         AxisIn ai;
         for (int c = 0; c < 6; c++) {
             ai.dz[c] = t[c];
@@ -1303,10 +1373,11 @@ __global__ void wait_probe(uint64_t limit_ns, int *err)
     __syncwarp();
 }
 
-// centred first derivatives of (p, r) through the rotation pass in its raw
-// mode: out[0..2] = D p, out[3..5] = D r
+// centred first derivatives of (p, r) and the half-point products of their
+// staggered derivatives through the rotation pass in mode 2: dp[0..2] = D p,
+// dr[0..2] = D r, h[0..2] = (D+ p)(D+ r) per axis
 template <int M>
-int raw_derivs(prop_s *P, const float *p, const float *r, float *const *out)
+int raw_half(prop_s *P, const float *p, const float *r, float *const *dp, float *const *dr, float *const *h)
 {
     using B = BX<M>;
     const GridDev &g = P->g;
@@ -1318,10 +1389,10 @@ int raw_derivs(prop_s *P, const float *p, const float *r, float *const *out)
                     map_of(P, P->nrm[0], FZ, FY, &rm.nx) && map_of(P, P->nrm[1], FZ, FY, &rm.ny);
     if (!ok) return wp_fail(P, PROP_ECUDA, "cuTensorMapEncodeTiled failed");
     const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64;
-    static const bool attr = set_smem(tti_rot_tma<M, true>, s1);
+    static const bool attr = set_smem(tti_rot_tma<M, 2>, s1);
     (void)attr;
-    tti_rot_tma<M, true><<<grd, blk, s1, P->stream>>>(g, P->w, p, r, rm, out[0], out[1], out[2], out[3], out[4],
-                                                      out[5], xc, P->flag);
+    tti_rot_tma<M, 2><<<grd, blk, s1, P->stream>>>(g, P->w, p, r, rm, dp[0], dp[1], dp[2], dr[0], dr[1], dr[2],
+                                                   F3{{h[0], h[1], h[2]}}, xc, P->flag);
     P->kern_launches += 1;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
@@ -1329,6 +1400,19 @@ int raw_derivs(prop_s *P, const float *p, const float *r, float *const *out)
 
 }  // namespace
 
+// Entry points of one tile height carry its suffix (_y8, _y16, _y32); the
+// unit of the default height also holds the dispatchers by the handle's
+// tile_y and everything that exists once (batched launches, self-test,
+// acoustic pass, raw derivatives of the staggered-pair imaging).
+#if WP_TILE_Y == 8
+#define WP_TILE_FN(name) name##_y8
+#elif WP_TILE_Y == 32
+#define WP_TILE_FN(name) name##_y32
+#else
+#define WP_TILE_FN(name) name##_y16
+#endif
+
+#if WP_TILE_Y == 16
 // launch the wait self-test on the handle's stream (limit in seconds, <= 2)
 int wait_probe_launch(prop_s *P, double seconds)
 {
@@ -1364,9 +1448,11 @@ bool tma_usable(const prop_s *P)
            (P->d.kind != PROP_TTI || (P->nrm[0] && P->nrm[1]));
 }
 
+#endif  // WP_TILE_Y == 16
+
 // elastic step with time step dt_sign * dt (forward: +1; adjoint modelling
 // in (b_avg vbar, g C tbar) variables: -1)
-int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
+int WP_TILE_FN(el_launch_tma)(prop_s *P, float *const *S, float dt_sign)
 {
     prof_begin(P, dt_sign > 0 ? 2 : 5);
     int rc;
@@ -1381,11 +1467,11 @@ int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
     return rc;
 }
 
-// eps, delta (and theta, phi) imaging of one transposed TTI step (see tti_image_aniso)
-int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
-                        float *ge, float *gd, float *const *gax)
+// eps, delta (and theta, phi) imaging of one transposed TTI step (see
+// tti_image_aniso; centred operators)
+int WP_TILE_FN(tti_image_aniso_tma)(prop_s *P, const float *up, const float *ur, const float *lp,
+                                    const float *lr, float *ge, float *gd, float *const *gax)
 {
-    if (P->d.tti_operator == 1) return tti_sp_image_aniso_tma(P, up, ur, lp, lr, ge, gd, gax);
     switch (P->M) {
     case 2: return tti_image_aniso<2>(P, up, ur, lp, lr, ge, gd, gax);
     case 4: return tti_image_aniso<4>(P, up, ur, lp, lr, ge, gd, gax);
@@ -1395,6 +1481,7 @@ int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
 
+#if WP_TILE_Y == 16
 // the pointwise tilt/azimuth term for any pass family (dz: raw derivatives of
 // zeta = C lam, du: of the forward field; acc += dt^2 V)
 void tti_axis_image_launch(prop_s *P, const float *const *dz, const float *const *du, float *const *acc)
@@ -1420,9 +1507,11 @@ void tti_axis_to_angles(prop_s *P, float *const *a)
     P->kern_launches += 1;
 }
 
+#endif  // WP_TILE_Y == 16
+
 // the TMA passes of one transposed elastic step with imaging (see el_adj_grad)
-int el_adj_grad_tma(prop_s *P, float *const *S, float *const *sig, float *const *w, const float *const *v1,
-                    float *const *gr, float *const *ep)
+int WP_TILE_FN(el_adj_grad_tma)(prop_s *P, float *const *S, float *const *sig, float *const *w,
+                                const float *const *v1, float *const *gr, float *const *ep)
 {
     switch (P->M) {
     case 2: return el_adj_grad<2>(P, S, sig, w, v1, gr, ep);
@@ -1433,8 +1522,8 @@ int el_adj_grad_tma(prop_s *P, float *const *S, float *const *sig, float *const 
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
 
-int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
-                   float *grad)
+int WP_TILE_FN(tti_launch_tma)(prop_s *P, float *const *S, bool adjoint, const float *img_p,
+                               const float *img_r, float *grad)
 {
     prof_begin(P, adjoint ? 1 : 0);
     int rc;
@@ -1447,6 +1536,106 @@ int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p,
     }
     prof_end(P, adjoint ? 1 : 0);
     return rc;
+}
+
+// largest dynamic shared memory of the passes a handle of this kind and
+// order launches at this tile height
+namespace {
+template <int M>
+size_t smem_need(int kind)
+{
+    auto b = [](int floats) { return (size_t)floats * sizeof(float) + 64; };
+    if (kind == PROP_ELASTIC)
+        return std::max({b(NSTAGE * VL<M>::SZ), b(NSTAGE * TL<M, 0>::SZ), b(NSTAGE * TL<M, 1>::SZ),
+                         b(NSTAGE * TL<M, 2>::SZ)});
+    return std::max({b(RL<M>::NS * RL<M>::SZ), b(NSTAGE * UL<M, 0, 0>::SZ), b(NSTAGE * UL<M, 1, 0>::SZ),
+                     b(NSTAGE * UL<M, 1, 1>::SZ), b(NSTAGE * UL<M, 2, 0>::SZ)});
+}
+}  // namespace
+
+// true if the passes of the handle's kind and order fit one CTA's shared
+// memory at this tile height (elastic and centred TTI)
+bool WP_TILE_FN(tile_fits)(const prop_s *P)
+{
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return false;
+    size_t need = 0;
+    switch (P->M) {
+    case 2: need = smem_need<2>(P->d.kind); break;
+    case 4: need = smem_need<4>(P->d.kind); break;
+    case 6: need = smem_need<6>(P->d.kind); break;
+    case 8: need = smem_need<8>(P->d.kind); break;
+    default: return false;
+    }
+    return need <= (size_t)optin;
+}
+
+#if WP_TILE_Y == 16
+// the other tile heights, compiled in their own units
+#define WP_DECL_HEIGHT(sfx)                                                                                    \
+    bool tile_fits##sfx(const prop_s *P);                                                                     \
+    int el_launch_tma##sfx(prop_s *P, float *const *S, float dt_sign);                                        \
+    int tti_image_aniso_tma##sfx(prop_s *P, const float *up, const float *ur, const float *lp,                \
+                                 const float *lr, float *ge, float *gd, float *const *gax);                   \
+    int el_adj_grad_tma##sfx(prop_s *P, float *const *S, float *const *sig, float *const *w,                  \
+                             const float *const *v1, float *const *gr, float *const *ep);                     \
+    int tti_launch_tma##sfx(prop_s *P, float *const *S, bool adjoint, const float *img_p,                     \
+                            const float *img_r, float *grad);
+WP_DECL_HEIGHT(_y8)
+WP_DECL_HEIGHT(_y32)
+#undef WP_DECL_HEIGHT
+
+// dispatch on the handle's tile height (prop_s::tile_y, set by the autotuner)
+bool tile_height_fits(const prop_s *P, int ty)
+{
+    if (P->d.kind != PROP_ELASTIC && !(P->d.kind == PROP_TTI && P->d.tti_operator == 0)) return ty == 16;
+    // a 32-row CTA (17 warps) gets at most 96 registers per thread; the
+    // elastic passes above space order 8 need 144-168 and would spill
+    if (ty == 32 && P->d.kind == PROP_ELASTIC && P->M > 4) return false;
+    switch (ty) {
+    case 8: return tile_fits_y8(P);
+    case 16: return tile_fits_y16(P);
+    case 32: return tile_fits_y32(P);
+    }
+    return false;
+}
+int el_launch_tma(prop_s *P, float *const *S, float dt_sign)
+{
+    switch (P->tile_y) {
+    case 8: return el_launch_tma_y8(P, S, dt_sign);
+    case 32: return el_launch_tma_y32(P, S, dt_sign);
+    }
+    return el_launch_tma_y16(P, S, dt_sign);
+}
+int tti_image_aniso_tma(prop_s *P, const float *up, const float *ur, const float *lp, const float *lr,
+                        float *ge, float *gd, float *const *gax)
+{
+    if (P->d.tti_operator == 1) return tti_sp_image_aniso_tma(P, up, ur, lp, lr, ge, gd, gax);
+    switch (P->tile_y) {
+    case 8: return tti_image_aniso_tma_y8(P, up, ur, lp, lr, ge, gd, gax);
+    case 32: return tti_image_aniso_tma_y32(P, up, ur, lp, lr, ge, gd, gax);
+    }
+    return tti_image_aniso_tma_y16(P, up, ur, lp, lr, ge, gd, gax);
+}
+int el_adj_grad_tma(prop_s *P, float *const *S, float *const *sig, float *const *w, const float *const *v1,
+                    float *const *gr, float *const *ep)
+{
+    switch (P->tile_y) {
+    case 8: return el_adj_grad_tma_y8(P, S, sig, w, v1, gr, ep);
+    case 32: return el_adj_grad_tma_y32(P, S, sig, w, v1, gr, ep);
+    }
+    return el_adj_grad_tma_y16(P, S, sig, w, v1, gr, ep);
+}
+int tti_launch_tma(prop_s *P, float *const *S, bool adjoint, const float *img_p, const float *img_r,
+                   float *grad)
+{
+    switch (P->tile_y) {
+    case 8: return tti_launch_tma_y8(P, S, adjoint, img_p, img_r, grad);
+    case 32: return tti_launch_tma_y32(P, S, adjoint, img_p, img_r, grad);
+    }
+    return tti_launch_tma_y16(P, S, adjoint, img_p, img_r, grad);
 }
 
 // ---------------------------------------------------------------------------
@@ -1469,6 +1658,13 @@ struct TtiBatch {
     cudaEvent_t copied[NSLOT] = {};
     size_t hcap = 0;
     unsigned long long calls = 0;
+    // elastic entries (bytes: one table for a modelling step, three for a
+    // transposed step with imaging)
+    void *del = nullptr;
+    size_t del_cap = 0;
+    char *hel[NSLOT] = {};
+    size_t hel_cap = 0;
+    cudaEvent_t elcopied[NSLOT] = {};
     // fixed tables of forward-step configurations (graph replay)
     TtiShot *dfixed[2] = {};
     size_t fixed_cap = 0;
@@ -1485,6 +1681,14 @@ void tti_batch_free(TtiBatch *b)
     cudaFree(b->dshots);
     cudaFree(b->dfixed[0]);
     cudaFree(b->dfixed[1]);
+    cudaFree(b->del);
+    for (int i = 0; i < TtiBatch::NSLOT; i++) {
+        if (b->elcopied[i]) {
+            cudaEventSynchronize(b->elcopied[i]);
+            cudaEventDestroy(b->elcopied[i]);
+        }
+        cudaFreeHost(b->hel[i]);
+    }
     for (int i = 0; i < TtiBatch::NSLOT; i++) {
         if (b->copied[i]) {
             cudaEventSynchronize(b->copied[i]);
@@ -1576,8 +1780,16 @@ int tti_batch_launch(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st
 
 // tile table over the shots (cached while their shapes and x-extents stay
 // the same); shots with more points first
+static int batch_tiles(TtiBatch *b, const std::vector<prop_s *> &Ps, cudaStream_t st, std::string *err);
 static int tti_batch_tiles(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, std::string *err)
 {
+    std::vector<prop_s *> Ps(n);
+    for (int i = 0; i < n; i++) Ps[i] = req[i].P;
+    return batch_tiles(b, Ps, st, err);
+}
+static int batch_tiles(TtiBatch *b, const std::vector<prop_s *> &Ps, cudaStream_t st, std::string *err)
+{
+    const int n = (int)Ps.size();
     auto ck = [&](cudaError_t c, const char *what) {
         if (c == cudaSuccess) return PROP_OK;
         *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
@@ -1585,18 +1797,18 @@ static int tti_batch_tiles(TtiBatch *b, const TtiBatchReq *req, int n, cudaStrea
     };
     std::vector<long long> sig;
     for (int i = 0; i < n; i++) {
-        const GridDev &g = req[i].P->g;
-        sig.insert(sig.end(), {(long long)g.NX, (long long)g.NY, (long long)g.NZ, (long long)req[i].P->xchunk});
+        const GridDev &g = Ps[i]->g;
+        sig.insert(sig.end(), {(long long)g.NX, (long long)g.NY, (long long)g.NZ, (long long)Ps[i]->xchunk});
     }
     if (sig == b->sig) return PROP_OK;
     std::vector<std::pair<long long, int>> order;
-    for (int i = 0; i < n; i++) order.emplace_back(-req[i].P->g.N, i);
+    for (int i = 0; i < n; i++) order.emplace_back(-Ps[i]->g.N, i);
     std::stable_sort(order.begin(), order.end());
     b->htiles.clear();
     for (auto &o : order) {
         const int i = o.second;
-        const GridDev &g = req[i].P->g;
-        const int xc = req[i].P->xchunk;
+        const GridDev &g = Ps[i]->g;
+        const int xc = Ps[i]->xchunk;
         const int tz = (g.NZ + FZ - 1) / FZ, tyy = (g.NY + FY - 1) / FY, tx = (g.NX + xc - 1) / xc;
         for (int c = 0; c < tx; c++)
             for (int y = 0; y < tyy; y++)
@@ -1738,15 +1950,151 @@ int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, 
     return 1;
 }
 
-// centred first derivatives D p (out[0..2]) and D r (out[3..5]) through the
-// TMA rotation pass in its raw mode (NZ a multiple of 4)
-int tti_raw_derivs_tma(prop_s *P, const float *p, const float *r, float *const *out)
+bool el_batchable(const prop_s *P) { return P->d.kind == PROP_ELASTIC && tma_usable(P); }
+
+template <int M>
+static int el_batch_launch(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    const int mode = req[0].mode, per = mode == 0 ? 1 : 3;
+    const size_t bytes = (size_t)n * per * sizeof(ElShot);
+    if (bytes > b->del_cap) {
+        cudaFree(b->del);
+        b->del = nullptr;
+        b->del_cap = 0;
+        if (int rc = ck(cudaMalloc(&b->del, bytes), "batched elastic shot table")) return rc;
+        b->del_cap = bytes;
+    }
+    if (bytes > b->hel_cap) {
+        for (int i = 0; i < TtiBatch::NSLOT; i++) {
+            if (b->elcopied[i]) cudaEventSynchronize(b->elcopied[i]);
+            cudaFreeHost(b->hel[i]);
+            b->hel[i] = nullptr;
+        }
+        b->hel_cap = 0;
+        for (int i = 0; i < TtiBatch::NSLOT; i++) {
+            if (int rc = ck(cudaMallocHost(&b->hel[i], bytes), "batched elastic staging")) return rc;
+            if (!b->elcopied[i])
+                if (int rc = ck(cudaEventCreateWithFlags(&b->elcopied[i], cudaEventDisableTiming),
+                                "batched elastic staging event"))
+                    return rc;
+        }
+        b->hel_cap = bytes;
+    }
+    const int slot = (int)(b->calls++ % TtiBatch::NSLOT);
+    if (int rc = ck(cudaEventSynchronize(b->elcopied[slot]), "batched elastic staging wait")) return rc;
+    ElShot *H = reinterpret_cast<ElShot *>(b->hel[slot]);
+    for (int i = 0; i < n; i++) {
+        prop_s *P = req[i].P;
+        float *const *S = req[i].S;
+        bool ok = true;
+        if (mode == 0) {
+            ElShot &e = H[i];
+            e.g = P->g;
+            e.g.dt = req[i].sign * P->g.dt;
+            for (int k = 0; k < 9; k++) e.s.f[k] = S[k];
+            e.o = F5{};
+            ok = vmaps<M>(P, S, S + 3, &e.vm) && tmaps<M>(P, S, S + 3, &e.tm);
+            e.xc = P->xchunk;
+            e.flag = P->flag;
+        } else {
+            // the three passes of el_adj_grad: velocity (adjoint), stress
+            // (imaging with the forward v^{k+1}), stress (adjoint)
+            float *const *sig = P->tmp, *const *w = P->tmp + 6, *const *ep = P->tmp + 9;
+            const float *const *v1 = req[i].xk1;
+            ElShot &ev = H[i], &e2 = H[n + i], &e1 = H[2 * n + i];
+            for (ElShot *e : {&ev, &e2, &e1}) {
+                e->g = P->g;
+                e->xc = P->xchunk;
+                e->flag = P->flag;
+                e->o = F5{};
+            }
+            for (int k = 0; k < 3; k++) {
+                ev.s.f[k] = S[k];
+                e2.s.f[k] = const_cast<float *>(v1[k]);
+                e1.s.f[k] = w[k];
+                ev.o.f[k] = w[k];
+            }
+            for (int k = 0; k < 6; k++) {
+                ev.s.f[3 + k] = sig[k];
+                e2.s.f[3 + k] = S[3 + k];
+                e1.s.f[3 + k] = S[3 + k];
+            }
+            e2.o = F5{{req[i].g[0], req[i].g[1], ep[0], ep[1], ep[2]}};
+            ok = vmaps<M>(P, S, sig, &ev.vm) && tmaps<M>(P, v1, S + 3, &e2.tm) && tmaps<M>(P, w, S + 3, &e1.tm) &&
+                 map_of(P, req[i].g[0], FZ, FY, &e2.tm.gl) && map_of(P, req[i].g[1], FZ, FY, &e2.tm.gm);
+        }
+        if (!ok) {
+            *err = "cuTensorMapEncodeTiled failed";
+            return PROP_ECUDA;
+        }
+    }
+    if (int rc = ck(cudaMemcpyAsync(b->del, H, bytes, cudaMemcpyHostToDevice, st), "batched elastic table copy"))
+        return rc;
+    if (int rc = ck(cudaEventRecord(b->elcopied[slot], st), "batched elastic event")) return rc;
+    const unsigned nt = (unsigned)b->htiles.size();
+    const dim3 blk(TZ2, FY + 2, 1);
+    const ElShot *D = reinterpret_cast<const ElShot *>(b->del);
+    const FDW &w = req[0].P->w;
+    if (mode == 0) {
+        const size_t sv = NSTAGE * VL<M>::SZ * sizeof(float) + 64, stt = NSTAGE * TL<M, 0>::SZ * sizeof(float) + 64;
+        static const bool attr = set_smem(el_vpass_batch<M, 0>, sv) && set_smem(el_tpass_batch<M, 0>, stt);
+        (void)attr;
+        el_vpass_batch<M, 0><<<nt, blk, sv, st>>>(D, b->dtiles, w);
+        el_tpass_batch<M, 0><<<nt, blk, stt, st>>>(D, b->dtiles, w);
+    } else {
+        const size_t sv = NSTAGE * VL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * TL<M, 2>::SZ * sizeof(float) + 64,
+                     s1 = NSTAGE * TL<M, 1>::SZ * sizeof(float) + 64;
+        static const bool attr = set_smem(el_vpass_batch<M, 1>, sv) && set_smem(el_tpass_batch<M, 2>, s2) &&
+                                 set_smem(el_tpass_batch<M, 1>, s1);
+        (void)attr;
+        for (int i = 0; i < n; i++) el_adj_pre_launch(req[i].P, req[i].S, st);
+        el_vpass_batch<M, 1><<<nt, blk, sv, st>>>(D, b->dtiles, w);
+        el_tpass_batch<M, 2><<<nt, blk, s2, st>>>(D + n, b->dtiles, w);
+        el_tpass_batch<M, 1><<<nt, blk, s1, st>>>(D + 2 * n, b->dtiles, w);
+        for (int i = 0; i < n; i++) el_face2_launch(req[i].P, req[i].S, req[i].xk, req[i].xk1, st);
+    }
+    for (int i = 0; i < n; i++) req[i].P->kern_launches += mode == 0 ? 2 : 3;
+    return ck(cudaGetLastError(), "batched elastic step launch");
+}
+
+int el_batch_step(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    if (n < 1) return PROP_OK;
+    const prop_s *P0 = req[0].P;
+    for (int i = 0; i < n; i++) {
+        const prop_s *P = req[i].P;
+        if (!el_batchable(P) || P->M != P0->M || req[i].mode != req[0].mode || req[i].sign != req[0].sign)
+            return 1;
+    }
+    std::vector<prop_s *> Ps(n);
+    for (int i = 0; i < n; i++) Ps[i] = req[i].P;
+    if (int rc = batch_tiles(b, Ps, st, err)) return rc;
+    switch (P0->M) {
+    case 2: return el_batch_launch<2>(b, req, n, st, err);
+    case 4: return el_batch_launch<4>(b, req, n, st, err);
+    case 6: return el_batch_launch<6>(b, req, n, st, err);
+    case 8: return el_batch_launch<8>(b, req, n, st, err);
+    }
+    return 1;
+}
+
+// centred first derivatives D p, D r and the half-point products
+// (D+_i p)(D+_i r) through the TMA rotation pass (see raw_half; NZ a
+// multiple of 4)
+int tti_raw_half_tma(prop_s *P, const float *p, const float *r, float *const *dp, float *const *dr,
+                     float *const *h)
 {
     switch (P->M) {
-    case 2: return raw_derivs<2>(P, p, r, out);
-    case 4: return raw_derivs<4>(P, p, r, out);
-    case 6: return raw_derivs<6>(P, p, r, out);
-    case 8: return raw_derivs<8>(P, p, r, out);
+    case 2: return raw_half<2>(P, p, r, dp, dr, h);
+    case 4: return raw_half<4>(P, p, r, dp, dr, h);
+    case 6: return raw_half<6>(P, p, r, dp, dr, h);
+    case 8: return raw_half<8>(P, p, r, dp, dr, h);
     }
     return wp_fail(P, PROP_EINVAL, "unsupported space order");
 }
+#endif  // WP_TILE_Y == 16

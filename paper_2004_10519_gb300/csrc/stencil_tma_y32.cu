@@ -1,0 +1,6 @@
+// The TMA-fed stencil passes (elastic, centred TTI) at a tile height of 32
+// rows: the same source as stencil_tma.cu, compiled with WP_TILE_Y = 32.
+// Its entry points carry the suffix _y32; the autotuner picks the height per
+// grid.
+#define WP_TILE_Y 32
+#include "stencil_tma.cu"

@@ -1,8 +1,14 @@
 // TMA plane-ring machinery shared by the TMA-fed stencil passes: tile
-// geometry (32 z x 16 y columns, two z points per consumer thread, one
+// geometry (32 z x FY y columns, two z points per consumer thread, one
 // producer warp), mbarrier and cp.async.bulk.tensor helpers in inline PTX,
 // the bounded producer/consumer ring, and the host side that encodes
 // (and caches per handle) the 3D tensor maps.
+//
+// The tile height FY is a compile-time constant of the translation unit
+// (WP_TILE_Y: 8, 16 or 32 rows; 16 unless the unit defines it).  The
+// stencil passes are compiled once per height and the autotuner picks one
+// per grid; the arithmetic of a point does not depend on the tile, so every
+// height gives the same bits.
 #pragma once
 #include "tile.cuh"
 
@@ -10,14 +16,22 @@
 #include <cstdlib>
 #include <mutex>
 
+#ifndef WP_TILE_Y
+#define WP_TILE_Y 16
+#endif
+static_assert(WP_TILE_Y == 8 || WP_TILE_Y == 16 || WP_TILE_Y == 32, "tile height must be 8, 16 or 32");
+
 namespace {
 
-using tile::FY;
+constexpr int FY = WP_TILE_Y;
 using tile::FZ;
 
 constexpr int TZ2 = FZ / 2;        // threads along z, two points each
-constexpr int NT2 = TZ2 * FY;      // consumer threads per CTA (8 warps)
+constexpr int NT2 = TZ2 * FY;      // consumer threads per CTA (FY / 2 warps)
 constexpr int NTP = NT2 + 32;      // + one producer warp
+// resident CTAs per SM for the launch bounds: `base` at 16 rows, scaled
+// with the CTA size (a 32-row CTA has the threads of two 16-row ones)
+constexpr int occ(int base) { return FY == 8 ? 2 * base : (FY == 32 ? 1 : base); }
 // Elastic passes above space order 8 need more than 96 registers per thread
 // and more shared memory than two CTAs per SM allow: they run one CTA per SM.
 constexpr int NSTAGE = 3;

@@ -15,8 +15,9 @@
 // registers for the same multiply-adds.
 // Gradients w.r.t. eps and delta image the coupling with pass 2 in a mode
 // without the step; the tilt/azimuth term adds, to the centred form's, the
-// half-point products of the staggered diagonal terms (sp_half_products,
-// tti_axis_image_sp).
+// half-point products of the staggered diagonal terms (formed with the
+// centred derivatives in the TMA rotation pass's mode 2, tti_raw_half_tma,
+// then tti_axis_image_sp).
 #include "tma.cuh"
 
 namespace {
@@ -476,39 +477,6 @@ int sp_launch_any(prop_s *P, float *const *S, bool adjoint, const float *up, con
 // 1/2; at the last node its partner is clamped to itself, weight 1; the
 // first node has no half point below it).
 // ---------------------------------------------------------------------------
-struct F6 {
-    float *f[6];
-};
-
-template <int M>
-__global__ void sp_half_products(GridDev g, FDW w, const float *__restrict__ zp, const float *__restrict__ zr,
-                                 const float *__restrict__ up, const float *__restrict__ ur, F6 out)
-{
-    const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (q >= g.N) return;
-    const int z = (int)(q % g.NZ), y = (int)((q / g.NZ) % g.NY), x = (int)(q / ((long long)g.NZ * g.NY));
-    const int pos[3] = {x, y, z}, len[3] = {g.NX, g.NY, g.NZ};
-    const long long str[3] = {(long long)g.NY * g.NZ, g.NZ, 1};
-#pragma unroll
-    for (int i = 0; i < 3; i++) {
-        float a = 0.f, b = 0.f, c = 0.f, d = 0.f;
-#pragma unroll
-        for (int k = 1; k <= M; k++) {
-            // D+ f at q + 1/2: b_k (f(q + k) - f(q - k + 1)), zero outside
-            const bool ip = pos[i] + k < len[i], im = pos[i] - k + 1 >= 0;
-            const long long op = q + k * str[i], om = q - (k - 1) * str[i];
-            const float bk = w.b[k - 1];
-            a += bk * ((ip ? __ldg(zp + op) : 0.f) - (im ? __ldg(zp + om) : 0.f));
-            b += bk * ((ip ? __ldg(up + op) : 0.f) - (im ? __ldg(up + om) : 0.f));
-            c += bk * ((ip ? __ldg(zr + op) : 0.f) - (im ? __ldg(zr + om) : 0.f));
-            d += bk * ((ip ? __ldg(ur + op) : 0.f) - (im ? __ldg(ur + om) : 0.f));
-        }
-        const float ih2 = g.ih * g.ih;
-        out.f[i][q] = a * b * ih2;
-        out.f[3 + i][q] = c * d * ih2;
-    }
-}
-
 struct SPAxisIn {
     const float *dz[6], *du[6], *s[6], *nx, *ny;
     float *acc[3];
@@ -589,16 +557,14 @@ int sp_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp,
     P->kern_launches += 2;
     WP_CK(P, cudaGetLastError());
     if (!gax) return PROP_OK;
-    // centred first derivatives of zeta and of the forward field, the
-    // staggered half-point products, then the pointwise term
+    // centred first derivatives of zeta and of the forward field with the
+    // staggered half-point products, one rotation pass per pair (zeta_p, u_p)
+    // and (zeta_r, u_r), then the pointwise term
     float *dz[6] = {t[0], t[1], t[2], t[3], t[4], t[5]}, *du[6] = {t[8], t[9], t[10], t[11], t[12], t[13]};
-    WP_TRY(tti_raw_derivs_tma(P, t[6], t[7], dz));
-    WP_TRY(tti_raw_derivs_tma(P, up, ur, du));
+    WP_TRY(tti_raw_half_tma(P, t[6], up, dz, du, t + 14));
+    WP_TRY(tti_raw_half_tma(P, t[7], ur, dz + 3, du + 3, t + 17));
     const long long n = g.N;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    F6 sp;
-    for (int i = 0; i < 6; i++) sp.f[i] = t[14 + i];
-    sp_half_products<M><<<nb, 256, 0, P->stream>>>(g, P->w, t[6], t[7], up, ur, sp);
     SPAxisIn ai;
     for (int c = 0; c < 6; c++) {
         ai.dz[c] = dz[c];
@@ -609,7 +575,7 @@ int sp_image_aniso(prop_s *P, const float *up, const float *ur, const float *lp,
     ai.ny = P->nrm[1];
     for (int c = 0; c < 3; c++) ai.acc[c] = gax[c];
     tti_axis_image_sp<<<nb, 256, 0, P->stream>>>(g, g.dt * g.dt, ai);
-    P->kern_launches += 2;
+    P->kern_launches += 1;
     WP_CK(P, cudaGetLastError());
     return PROP_OK;
 }

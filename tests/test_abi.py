@@ -100,6 +100,7 @@ def test_wave_plan_first_fit_in_order(libpath):
     assert L.prop_plan_waves(None, -1, 10, None) == wp.PROP_EINVAL
     assert L.prop_gradient_bytes(None, 10) == 0
     assert L.prop_tile_planes(None) == 0
+    assert L.prop_tile_rows(None) == 0
 
 
 def test_batch_argument_checks_need_no_gpu(libpath):

@@ -220,3 +220,48 @@ def test_forward_batch_mixed_shots_fall_back(wp, shots):
         np.testing.assert_array_equal(t, r)
     for pr in props:
         pr.close()
+
+
+def elastic_window_shots(nt=50, h=10.0, nbl=4):
+    """Elastic shots on windows of different sizes cut from one random model
+    (computational nz 32: the TMA-fed passes), starting model halfway to
+    another random model."""
+    big = synth.random_elastic(40, 36, 24, 8, 3.0)
+    other = synth.random_elastic(40, 36, 24, 5, 3.0)
+    dt = synth.cfl_dt(h, float(big["vp"].max()))
+    out = []
+    for (ox, oy, nx, ny) in [(0, 0, 22, 20), (10, 6, 28, 26), (14, 12, 24, 22)]:
+        m = {k: np.ascontiguousarray(v[ox:ox + nx, oy:oy + ny]) for k, v in big.items()}
+        src = np.array([[nx * h / 2 + 0.4, ny * h / 2, 24 * h / 2 - 0.6]], np.float32)
+        rec = synth.carpet_receivers(3.3, 4.4, 3.3 * h, 6, 5, 0.0)
+        p = synth.Problem(synth.ELASTIC, nx, ny, 24, nbl, h, 8, nt, dt, m, src, synth.ricker(20.0, dt, nt)[None], rec)
+        d_obs = oracle.Problem(p).forward()
+        start = {k: (0.5 * (other[k][ox:ox + nx, oy:oy + ny] + m[k])).astype(np.float32) for k in m}
+        out.append((synth.Problem(**{**p.__dict__, "model": start}), d_obs.astype(np.float32)))
+    return out
+
+
+@pytest.mark.parametrize("snap", [0, 1])
+def test_elastic_batch_shares_launches(wp, snap):
+    """Elastic shots of one wave share their steps' launches (forward steps:
+    the velocity and stress passes over all shots; transposed steps with
+    imaging: the three passes, with the pointwise kernels per shot); the
+    gradients are bitwise those of one prop_gradient per shot, with full
+    storage and with FP32 checkpoints (recomputed forward steps)."""
+    sel = elastic_window_shots()
+    ref = []
+    for p, d in sel:
+        prop = wp.Propagator.from_problem(p, snap_mode=snap, ckpt_interval=7)
+        ref.append(prop.gradient(p.wavelet, p.src, p.rec, d))
+        prop.close()
+    props = [wp.Propagator.from_problem(p, snap_mode=snap, ckpt_interval=7) for p, _ in sel]
+    grads, J = wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                                 [p.rec for p, _ in sel], [d for _, d in sel])
+    shared, alone = wp.batch_stats()
+    assert shared > 0 and alone == 0, (shared, alone)
+    for i, (g, j) in enumerate(zip(grads, J)):
+        assert np.max(np.abs(ref[i][0])) > 0
+        np.testing.assert_array_equal(g, ref[i][0], err_msg=f"shot {i}")
+        assert j == ref[i][1], i
+    for pr in props:
+        pr.close()

@@ -81,3 +81,50 @@ def test_tile_planes_do_not_change_results(kind, monkeypatch):
         prop.close()
     assert planes["tuned"] >= 8 and planes["heuristic"] >= 8
     np.testing.assert_array_equal(out["tuned"], out["heuristic"])
+
+
+@pytest.mark.parametrize("kind", ["tti", "elastic"])
+def test_tile_heights_give_the_same_bits(kind, monkeypatch):
+    """The tile height of the TMA-fed passes (8, 16 or 32 rows of y, each a
+    separately compiled set of kernels that the autotuner chooses between)
+    only moves CTA boundaries: forward traces, adjoint source-side traces
+    and gradients (TTI also w.r.t. eps, delta, theta, phi) are bitwise the
+    same at every height, on a grid whose NY (42) is ragged for all three."""
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    p = {"tti": tti_problem, "elastic": el_problem}[kind](nt=40)
+    assert (p.ny + 2 * p.nbl) % 8 != 0
+    d = np.random.default_rng(5).standard_normal((p.rec.shape[0], p.nt)).astype(np.float32)
+    out = {}
+    for ty in (16, 8, 32):
+        monkeypatch.setenv("WAVEPROP_TILE_Y", str(ty))
+        prop = wp.Propagator.from_problem(p)
+        assert prop.tile_rows == ty
+        res = [prop.forward(p.wavelet, p.src, p.rec), prop.adjoint(d, p.src, p.rec)]
+        g, J = prop.gradient(p.wavelet, p.src, p.rec, d)
+        res += [g, np.array([J])]
+        if kind == "tti":
+            ga, Ja = prop.gradient_aniso(p.wavelet, p.src, p.rec, d)
+            res += [ga, np.array([Ja])]
+        prop.close()
+        out[ty] = res
+    for ty in (8, 32):
+        for a, b in zip(out[ty], out[16]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_autotuner_reports_a_tile_shape(monkeypatch):
+    """The autotuner's choice is one of the compiled heights and an x-extent
+    of at least 8 planes; WAVEPROP_AUTOTUNE=0 keeps 16 rows."""
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    p = el_problem(nt=10)
+    monkeypatch.delenv("WAVEPROP_TILE_Y", raising=False)
+    monkeypatch.delenv("WAVEPROP_AUTOTUNE", raising=False)
+    prop = wp.Propagator.from_problem(p)
+    assert prop.tile_rows in (8, 16, 32) and prop.tile_planes >= 8
+    prop.close()
+    monkeypatch.setenv("WAVEPROP_AUTOTUNE", "0")
+    prop = wp.Propagator.from_problem(p)
+    assert prop.tile_rows == 16
+    prop.close()

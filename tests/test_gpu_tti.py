@@ -314,3 +314,27 @@ def test_staggered_pair_state_steps(wp, adjoint):
     out = prop.get_state()
     p2, r2 = oracle.Problem(p).tti_step(st[2], st[0], st[3], st[1], adjoint=adjoint)
     assert rel(out[0], p2) <= TOL and rel(out[1], r2) <= TOL
+
+
+@pytest.mark.parametrize("kind", ["tti", "acoustic"])
+def test_checkpoint_tail_is_bitwise(wp, monkeypatch, kind):
+    """FP32 checkpoints keep the last levels of the run in full when device
+    memory allows (the adjoint sweep then recomputes only the checkpointed
+    part).  The gradient is bitwise that of full storage with no tail, a
+    partial tail (WAVEPROP_CKPT_TAIL caps it) and every level in the tail."""
+    if kind == "tti":
+        _, p0, d_obs = grad_problem(shape=(30, 26, 36))
+    else:
+        p0 = synth.acoustic_small(shape=(30, 26, 36), nbl=6, so=8, nt=70)
+        d_obs = 1.1 * oracle.Problem(p0).forward()
+    d32 = d_obs.astype(np.float32)
+    prop = wp.Propagator.from_problem(p0, snap_mode=wp.SNAP_FULL_FP32)
+    ref, J_ref = prop.gradient(p0.wavelet, p0.src, p0.rec, d32)
+    prop.close()
+    for cap in ("0", "7", "100000"):
+        monkeypatch.setenv("WAVEPROP_CKPT_TAIL", cap)
+        prop = wp.Propagator.from_problem(p0, snap_mode=wp.SNAP_CKPT_FP32, ckpt_interval=0)
+        g, J = prop.gradient(p0.wavelet, p0.src, p0.rec, d32)
+        prop.close()
+        np.testing.assert_array_equal(g, ref, err_msg=cap)
+        assert J == J_ref
