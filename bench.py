@@ -44,8 +44,9 @@ HBM_FALLBACK_GBS = 6800.0
 ALG_BYTES = {"elastic": 84.0, "tti": 44.0, "acoustic": 16.0}
 # DRAM bytes per point of one elastic step (velocity + stress pass) measured
 # by ncu (dram__bytes_read.sum + dram__bytes_write.sum) on the benchmark's own
-# 296^3 grid (profiles/elastic_bench_launch_list_296cube_so8.md)
-TRAFFIC_B_PER_PT = {"elastic": 118.1}
+# 296^3 grid at the autotuned 8-row tile (118.1 at 16 rows;
+# profiles/elastic_bench_launch_list_296cube_so8.md)
+TRAFFIC_B_PER_PT = {"elastic": 118.7}
 # algorithmic FP32 operations per point update, counted from the kernels'
 # arithmetic (FMA = 2): elastic so 8 (velocity + stress pass), TTI so 12
 # (rotation + update pass), acoustic so 12 (7 per stencil radius + 15)
@@ -722,7 +723,7 @@ def run_extras(wp, torch, dev, args, extras):
                                                                             args.batch_nt, windows=(40, 80, 60)))
     if "batchsmall" in extras:       # many small windows: 40-80 x 40-80 x 60 cells
         _clocked(out, "batchsmall", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
-                                                                 kind="tti", windows=(40, 80, 60)))
+                                                                 kind=args.batch_kind, windows=(40, 80, 60)))
     if "batch" in extras:
         _clocked(out, "batch", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
                                             small=args.small, kind=args.batch_kind))

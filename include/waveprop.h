@@ -54,7 +54,9 @@ enum {
     PROP_OK = 0,
     PROP_EINVAL = -1,     /* bad argument (message says which)             */
     PROP_ENOMEM = -2,     /* device allocation failed (nothing leaked)     */
-    PROP_ECUDA = -3,      /* CUDA runtime error; handle unusable           */
+    PROP_ECUDA = -3,      /* CUDA runtime error, or (WAVEPROP_CHECK=1
+                             build) a device bounds check failed; handle
+                             unusable                                      */
     PROP_EUNSTABLE = -4,  /* dt violates the CFL bound, or NaN/Inf seen    */
     PROP_ETIMEOUT = -5,   /* a bounded device-side wait gave up            */
     PROP_ESTATE = -6      /* handle unusable after an earlier error,

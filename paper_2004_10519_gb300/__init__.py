@@ -49,13 +49,19 @@ _lib = None
 
 
 def lib():
-    """Load libwaveprop.so (built by ``__graft_entry__.build()``)."""
+    """Load libwaveprop.so (built by ``__graft_entry__.build()``).  With
+    WAVEPROP_CHECK=1 in the environment, the bounds-checking build
+    libwaveprop_check.so instead (compiled on first use)."""
     global _lib
     if _lib is None:
-        if not os.path.exists(LIB_PATH):
-            raise RuntimeError(f"waveprop CUDA library not built ({LIB_PATH} missing); "
+        path = LIB_PATH
+        if os.environ.get("WAVEPROP_CHECK") == "1":
+            from . import _build
+            path = _build.build(check=True)
+        if not os.path.exists(path):
+            raise RuntimeError(f"waveprop CUDA library not built ({path} missing); "
                                "run __graft_entry__.build() -- there is no CPU fallback")
-        L = C.CDLL(LIB_PATH)
+        L = C.CDLL(path)
         vp = C.c_void_p
         fpp = C.POINTER(C.c_void_p)
         L.prop_create.argtypes = [C.POINTER(PropDesc), fpp, vp, C.POINTER(vp)]

@@ -656,6 +656,8 @@ static int finish(prop_s *P)
 
 int wp_flag_status(prop_s *P, int f)
 {
+    // bit 8: the bounds-checking build (WAVEPROP_CHECK=1) skipped an access
+    if (f & 8) return wp_fail(P, PROP_ECUDA, "device bounds check failed (an access was skipped)");
     if (f & 2) return wp_fail(P, PROP_ETIMEOUT, "a bounded device-side wait expired (TMA pipeline)");
     if (P->d.check_nan && (f & 1)) return wp_fail(P, PROP_EUNSTABLE, "NaN or Inf in the wavefield");
     return PROP_OK;

@@ -233,7 +233,10 @@ WP_DEV void el_vpass_body(const GridDev &g, const FDW &w, const F9 &s, const F5 
     const int xa = bz * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) { v_issue<M>(mp, sm + st * L::SZ, &bars[st], z0, y0, x, g.NX); };
     Ring R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);
@@ -440,7 +443,10 @@ WP_DEV void el_tpass_body(const GridDev &g, const FDW &w, const F9 &s, const F5 
     const int xa = bz * xc, xb = min(xa + xc, g.NX), nit = xb - xa;
     auto issue = [&](int x, int st) { t_issue<M, MODE>(mp, sm + st * L::SZ, &bars[st], z0, y0, x, g.NX); };
     Ring R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);
@@ -553,7 +559,10 @@ WP_DEV void tti_rot_body(const GridDev &g, const FDW &w, const float *__restrict
         tma3(S + L::ON + IS, &mp.ny, z0, y0, x, bar);
     };
     RingN<L::NS> R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);
@@ -746,7 +755,10 @@ WP_DEV void tti_upd_body(const GridDev &g, const FDW &w, const float *__restrict
         }
     };
     Ring R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);
@@ -968,7 +980,10 @@ acu_tma(GridDev g, FDW w, const float *__restrict__ u1, float *__restrict__ u0, 
         }
     };
     RingN<L::NS> R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);

@@ -54,8 +54,14 @@ WP_DEV void mbar_expect(uint64_t *bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(saddr(bar)), "r"(bytes)
                  : "memory");
 }
+#ifdef WP_CHECK
+WP_DEV bool ck_tma(const float *dst, int c0);
+#endif
 WP_DEV void tma3(float *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar)
 {
+#ifdef WP_CHECK
+    if (!ck_tma(dst, c0)) return;
+#endif
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
             saddr(dst)),
@@ -100,9 +106,64 @@ WP_DEV void drain(uint64_t *full, int a, int b)
 }
 
 // 8-byte accesses (z even, NZ even: always aligned)
-WP_DEV float2 lds2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
-WP_DEV float2 ldg2(const float *__restrict__ p, unsigned o) { return __ldg(reinterpret_cast<const float2 *>(p + o)); }
-WP_DEV void st2(float *p, unsigned o, float a, float b) { *reinterpret_cast<float2 *>(p + o) = make_float2(a, b); }
+// Bounds-checking build (WP_CHECK, selected at run time by WAVEPROP_CHECK=1):
+// every shared-memory read must lie in the CTA's dynamic shared memory, every
+// global float2 access of a field below the grid size and every TMA copy
+// start on a 16-byte boundary in x and in shared memory.  A failing access is
+// skipped (loads return zeros) and bit 8 of the handle's error word is set,
+// which the host reports as PROP_ECUDA; nothing traps, and a skipped copy
+// ends in the bounded wait of its stage (bit 2).  In the normal build the
+// checks compile to nothing.
+#ifdef WP_CHECK
+static __shared__ unsigned long long wp_ck_n;   // elements of a field
+static __shared__ int *wp_ck_err;
+extern __shared__ __align__(128) float wp_dsm[];
+WP_DEV void ck_begin(unsigned long long n, int *err)
+{
+    wp_ck_n = n;
+    wp_ck_err = err;
+}
+WP_DEV bool ck_fail()
+{
+    atomicOr(wp_ck_err, 8);
+    return false;
+}
+WP_DEV bool ck_smem(const void *p, unsigned bytes)
+{
+    unsigned dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    const uint32_t a = saddr(p), b = saddr(wp_dsm);
+    return (a >= b && a + bytes <= b + dyn && (a & (bytes - 1)) == 0) || ck_fail();
+}
+WP_DEV bool ck_field(unsigned o) { return (unsigned long long)o + 2 <= wp_ck_n || ck_fail(); }
+// x (innermost, z) coordinate of a copy: 16-byte multiple; destination
+// 16-byte aligned inside the dynamic shared memory
+WP_DEV bool ck_tma(const float *dst, int c0) { return ((c0 & 3) == 0 || ck_fail()) && ck_smem(dst, 16); }
+#else
+WP_DEV void ck_begin(unsigned long long, int *) {}
+#endif
+
+WP_DEV float2 lds2(const float *p)
+{
+#ifdef WP_CHECK
+    if (!ck_smem(p, 8)) return make_float2(0.f, 0.f);
+#endif
+    return *reinterpret_cast<const float2 *>(p);
+}
+WP_DEV float2 ldg2(const float *__restrict__ p, unsigned o)
+{
+#ifdef WP_CHECK
+    if (!ck_field(o)) return make_float2(0.f, 0.f);
+#endif
+    return __ldg(reinterpret_cast<const float2 *>(p + o));
+}
+WP_DEV void st2(float *p, unsigned o, float a, float b)
+{
+#ifdef WP_CHECK
+    if (!ck_field(o)) return;
+#endif
+    *reinterpret_cast<float2 *>(p + o) = make_float2(a, b);
+}
 WP_DEV float2 dif2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 // paired FP32 arithmetic (one instruction for both lanes; per component the
 // result of the scalar operation)

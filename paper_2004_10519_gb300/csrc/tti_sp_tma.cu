@@ -70,7 +70,10 @@ tti_sp_rot_tma(GridDev g, FDW w, const float *__restrict__ p, const float *__res
         tma3(S + L::OXN, &mp.nxi, z0, y0, min(x + 1, g.NX - 1), bar);
     };
     Ring R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);
@@ -317,7 +320,10 @@ tti_sp_upd_tma(GridDev g, FDW w, F12 o, const __grid_constant__ SUMaps mp, float
         }
     };
     Ring R(bars);
-    if (lead) R.init();
+    if (lead) {
+        R.init();
+        ck_begin(g.N, err);
+    }
     __syncthreads();
     if (ty >= FY) {                                       // producer warp
         if (lane == 0) R.produce(xa, nit, issue, err);
