@@ -39,7 +39,12 @@
  * function convergence, undamped leapfrog energy conservation, the dot test,
  * the assembled step's symmetry and a Taylor test; for the 2D elastic system
  * equality with a y-invariant state of the 3D system, the dot test and the
- * mu = 0 limit).
+ * mu = 0 limit; for the sparse points exact reproduction of trilinear
+ * functions by the injection/interpolation weights at random off-node
+ * fractions and the one-step injection-to-recording product of the weights;
+ * for the absorbing layers the first-arrival attenuation into the layer
+ * against the WKB prediction of the damping and Cerjan profiles; for TTI
+ * the spatial convergence order against the analytic 2D Green's function).
  */
 #include <math.h>
 #include <stdlib.h>
