@@ -158,10 +158,9 @@ def test_one_step_sampled_full_size(wp):
     prop.close()
     idx = sample_points(shape, 300, 8)
     ref = oracle.el_step_points(p, state, idx)
+    from test_gpu_tti import assert_pointwise
     for c in range(9):
-        got = out[c].reshape(-1)[idx]
-        err = np.max(np.abs(got - ref[:, c])) / np.max(np.abs(ref[:, c]))
-        assert err <= TOL, (c, err)
+        assert_pointwise(out[c].reshape(-1)[idx], ref[:, c], c)
 
 
 def test_full_size_whole_grid_multistep(wp):

@@ -210,6 +210,23 @@ def random_tti_model(shape, seed):
             "theta": f(0.0, 40 * synth.DEG), "phi": f(0.0, 90 * synth.DEG)}
 
 
+def assert_pointwise(got, ref, tag=""):
+    """Per-point bound of a sampled comparison: where the reference is at
+    least 1 % of its largest sampled magnitude, the relative error of every
+    point is at most TOL; everywhere the absolute error is at most 0.1 TOL
+    of that magnitude (FP32 rounding of the step's terms: measured on the
+    full-size grids at most 3.8e-6 relative where it applies, 1.7e-7 of the
+    magnitude in absolute terms)."""
+    got, ref = np.asarray(got, np.float64), np.asarray(ref, np.float64)
+    m = float(np.max(np.abs(ref)))
+    ae = np.abs(got - ref)
+    big = np.abs(ref) >= 0.01 * m
+    assert big.sum() >= ref.size // 2, tag
+    rel_pt = float(np.max(ae[big] / np.abs(ref[big])))
+    assert rel_pt <= TOL, (tag, rel_pt)
+    assert float(np.max(ae)) <= 0.1 * TOL * m, (tag, float(np.max(ae)) / m)
+
+
 def sample_points(shape, n, seed):
     """Sampled outputs: random interior points plus every corner / face / edge class."""
     NX, NY, NZ = shape
@@ -247,10 +264,8 @@ def test_one_step_sampled_full_size(wp, adjoint, op):
     idx = sample_points(shape, 400, 6)
     ref = oracle.tti_step_points(p, (state[2], state[0], state[3], state[1]), idx, adjoint=adjoint)
     got = np.stack([out[0].reshape(-1)[idx], out[1].reshape(-1)[idx]], axis=1)
-    # compare the increment over 2u^n - u^{n-1} scale: absolute error relative
-    # to the largest sampled value
-    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
-    assert err <= TOL, err
+    for c in range(2):
+        assert_pointwise(got[:, c], ref[:, c], ("p", "r")[c])
 
 
 # ---------------------------------------------------------------------------
