@@ -583,7 +583,17 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti", wi
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t0
     shared, alone = wp.batch_stats()
-    # the same waves with every shot on its own launches
+    # the same waves from one host thread per shot meeting at every step
+    # (shared launches without the lockstep driver), then with every shot on
+    # its own launches
+    os.environ["WAVEPROP_LOCKSTEP"] = "0"
+    with timed_region():
+        t0 = time.perf_counter()
+        grads3, _ = wp.gradient_batch(props, wav, src, rec, obs)
+        torch.cuda.synchronize()
+        t_rdv = time.perf_counter() - t0
+    shared_rdv, alone_rdv = wp.batch_stats()
+    del os.environ["WAVEPROP_LOCKSTEP"]
     os.environ["WAVEPROP_BATCH_LAUNCH"] = "0"
     with timed_region():
         t0 = time.perf_counter()
@@ -591,7 +601,8 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti", wi
         torch.cuda.synchronize()
         t_own = time.perf_counter() - t0
     del os.environ["WAVEPROP_BATCH_LAUNCH"]
-    same_own = all(bool(torch.equal(g, s_)) for g, s_ in zip(grads, grads2))
+    same_own = all(bool(torch.equal(g, s_)) and bool(torch.equal(g, s3))
+                   for g, s_, s3 in zip(grads, grads2, grads3))
     same = all(bool(torch.equal(g, s[0])) for g, s in zip(grads, seq))
     waves = wp.plan_waves([p.gradient_bytes(r.shape[0]) for p, r in zip(props, rec)],
                           int(torch.cuda.mem_get_info(dev)[0] * 0.9))[1]
@@ -601,7 +612,10 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti", wi
             "windows": [s[1].name for s in shots], "points_total": npts,
             "sequential": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq},
             "batched": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
-                        "waves": waves, "shared_launch_rounds": shared, "unshared_rounds": alone},
+                        "waves": waves, "shared_launch_rounds": shared, "unshared_rounds": alone,
+                        "driver": "lockstep (graph-replayed segments) where a wave qualifies"},
+            "batched_rendezvous": {"seconds": t_rdv, "shots_per_hour": 3600.0 * nshots / t_rdv,
+                                   "shared_launch_rounds": shared_rdv, "unshared_rounds": alone_rdv},
             "batched_own_launches": {"seconds": t_own, "shots_per_hour": 3600.0 * nshots / t_own},
             "bitwise_equal": same and same_own}
 

@@ -207,9 +207,10 @@ void tti_batch_free(TtiBatch *b);
 // 0: launched on `stream`; 1: the requests cannot share a launch (the caller
 // launches them one by one); < 0: error (message in *err)
 int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t stream, std::string *err);
-// forward-step configuration `slot` (0 or 1) of every request into a fixed
-// device table (1: not batchable); then launches of that table, which may be
-// captured into a CUDA graph (no host staging)
+// step configuration `slot` (any index >= 0; forward, transposed, or
+// transposed with imaging, as the requests say) of every request into a
+// fixed device table (1: not batchable); then launches of that table, which
+// may be captured into a CUDA graph (no host staging)
 int tti_batch_fix(TtiBatch *b, const TtiBatchReq *req, int n, int slot, cudaStream_t stream, std::string *err);
 int tti_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t stream);
 // true if the handle's TTI steps can join a batched launch
@@ -257,6 +258,7 @@ void sp_record(prop_s *P, const SparseDev *S, const float *f0, const float *f1, 
                float scale, float *out_col, const int *tdev = nullptr);
 // device time index += d (one thread; steps replayed from a CUDA graph)
 void k_tick(prop_s *P, int *tdev, int d);
+void k_set_int(prop_s *P, int *p, int v);
 // inject: f[cell] += coef(cell) * sum_j w_j traces[trace_j*nt + t] into up to 3 fields;
 // mode 0: coef = scale; mode 1: coef = scale / A (TTI, A = m(1+sig dt/2));
 // mode 2: coef = scale (3 lambda + 2 mu) (elastic adjoint in s = C tbar);

@@ -11,12 +11,14 @@
 
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <condition_variable>
 #include <memory>
 #include <thread>
+#include <functional>
 
 static thread_local std::string tl_err;
 
@@ -1987,13 +1989,374 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
 }
 
 // shared TTI step launches of the last prop_gradient_batch call: rounds
-// launched together, rounds whose steps had to be launched one by one
+// launched together (rendezvous rounds and lockstep steps), rounds whose
+// steps had to be launched one by one
 static long long batch_stats[2] = {0, 0};
 extern "C" int prop_batch_stats(long long *shared, long long *alone)
 {
     if (shared) *shared = batch_stats[0];
     if (alone) *alone = batch_stats[1];
     return PROP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Gradients of a wave of TTI shots in lockstep (same space order, nt and
+// checkpoint schedule, centred operators on the TMA-fed passes, checkpointed
+// storage): one host thread drives every shot through the same sweep.
+//   forward:  per step, the receivers of every shot are sampled, one
+//             tile-table launch of each pass advances every shot and the
+//             sources are injected; a checkpoint is saved at the start of
+//             each segment of K steps;
+//   adjoint:  per segment (last first), every shot's checkpoint is loaded,
+//             K steps are recomputed into the segment buffers, then K
+//             transposed steps with imaging run (one launch of each pass
+//             for every shot) with the residual injected after each.
+// The time index lives in device memory, the per-shot tables of every step
+// configuration (two forward arrangements; the transposed step for each
+// position in the segment and each arrangement of the adjoint state) are
+// fixed device tables, so the K steps of a forward segment and the 2K steps
+// of an adjoint segment are each captured once as a CUDA graph and replayed
+// for every full segment; checkpoint saves and loads, partial segments and
+// WAVEPROP_GRAPHS=0 launch directly.  Each shot's operations are those of its
+// own prop_gradient, in the same order, so the results are the same bits.
+// Returns 1 (nothing done) if the wave does not qualify.
+// ---------------------------------------------------------------------------
+
+static bool lockstep_ok(prop_t *const *sh, int n)
+{
+    if (n < 2) return false;
+    const prop_s *P0 = sh[0];
+    for (int i = 0; i < n; i++) {
+        const prop_s *P = sh[i];
+        if (!tti_batchable(P) || P->broken || P->aniso || P->M != P0->M || P->d.nt != P0->d.nt ||
+            P->d.snap_mode == SNAP_FULL_FP32 || P->d.snap_mode != P0->d.snap_mode ||
+            P->d.ckpt_interval != P0->d.ckpt_interval)
+            return false;
+    }
+    const char *e = getenv("WAVEPROP_LOCKSTEP");
+    return !(e && !strcmp(e, "0"));
+}
+
+static int gradient_lockstep(prop_t *const *shots, int n, const float *const *wavelet,
+                             const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
+                             const int *nrec, const float *const *d_obs, float *const *grad, double *mis)
+{
+    prop_s *P0 = shots[0];
+    const int nt = P0->d.nt;
+    struct OwnStream {
+        cudaStream_t s = nullptr;
+        ~OwnStream()
+        {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } bs;
+    WP_CK(P0, cudaStreamCreateWithFlags(&bs.s, cudaStreamNonBlocking));
+    const cudaStream_t st = bs.s;
+    // WAVEPROP_BATCH_VERBOSE=1: wall time of each phase on stderr (the
+    // stream is synchronised at the phase ends)
+    const char *vb = getenv("WAVEPROP_BATCH_VERBOSE");
+    const bool verbose = vb && !strcmp(vb, "1");
+    auto tnow = [] { return std::chrono::steady_clock::now(); };
+    auto tlast = tnow();
+    auto phase = [&](const char *name) {
+        if (!verbose) return;
+        cudaStreamSynchronize(st);
+        const auto t = tnow();
+        fprintf(stderr, "lockstep %d shots: %-10s %9.3f ms\n", n, name,
+                std::chrono::duration<double, std::milli>(t - tlast).count());
+        tlast = t;
+    };
+    std::vector<cudaStream_t> own(n);
+    struct Restore {            // streams and the tail switch of every shot
+        prop_t *const *sh;
+        std::vector<cudaStream_t> *own;
+        int n;
+        ~Restore()
+        {
+            for (int i = 0; i < n; i++) {
+                sh[i]->stream = (*own)[i];
+                sh[i]->no_tail = false;
+                free_snaps(sh[i]);
+            }
+        }
+    } restore{shots, &own, 0};
+    // a wave whose setup fails (a bad argument of one shot, or the memory of
+    // the whole wave) runs shot by shot instead, so that each call reports
+    // its own error
+    for (int i = 0; i < n; i++)
+        if (!d_obs[i] || !grad[i] || !wavelet[i] || !src_xyz[i] || !rec_xyz[i] || nsrc[i] < 1 || nrec[i] < 1)
+            return 1;
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        if (check_handle(P) != PROP_OK) return 1;
+        own[i] = P->stream;
+        cudaEvent_t e;
+        WP_CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaEventRecord(e, P->stream);
+        cudaStreamWaitEvent(st, e, 0);
+        cudaEventDestroy(e);
+        P->stream = st;
+        P->no_tail = true;
+        restore.n = i + 1;
+        if (ensure_work(P) != PROP_OK || ensure_ast(P) != PROP_OK) return 1;
+    }
+    // every allocation before the first capture
+    std::vector<Geometry> G(n);
+    std::vector<DevBuf> wb(n), ob(n), stage(n), tr(n), gb(n), gp(n);
+    std::vector<const float *> wav(n), obs(n);
+    auto setup = [&](int i) -> int {
+        prop_s *P = shots[i];
+        const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
+        WP_TRY(build_geometry(P, G[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i]));
+        WP_TRY(dev_in(P, wavelet[i], (size_t)nsrc[i] * nt, wb[i], &wav[i]));
+        WP_TRY(dev_in(P, d_obs[i], (size_t)nrec[i] * nt, ob[i], &obs[i]));
+        WP_TRY(wp_malloc(P, &stage[i].p, sizeof(float) * (size_t)nt * nrec[i], "trace staging"));
+        WP_TRY(wp_malloc(P, &tr[i].p, sizeof(float) * (size_t)nt * nrec[i], "traces"));
+        WP_TRY(wp_malloc(P, &gb[i].p, sizeof(float) * N, "gradient"));
+        WP_TRY(wp_malloc(P, &gp[i].p, sizeof(float) * np, "gradient (physical)"));
+        WP_CK(P, cudaMemsetAsync(gb[i].p, 0, sizeof(float) * N, st));
+        WP_TRY(alloc_saves(P));
+        WP_TRY(zero_fields(P, P->st, 4));
+        WP_TRY(zero_fields(P, P->ast, 4));
+        WP_TRY(zero_fields(P, P->tmp + 6, 2));     // zeta = C lam of the zero state
+        return PROP_OK;
+    };
+    phase("handles");
+    for (int i = 0; i < n; i++)
+        if (setup(i) != PROP_OK) {
+            cudaStreamSynchronize(st);
+            return 1;
+        }
+    phase("setup");
+    const int K = ckpt_K(P0), J = ckpt_J(P0), span = ckpt_span(P0);
+    for (int i = 1; i < n; i++)
+        if (ckpt_K(shots[i]) != K || ckpt_J(shots[i]) != J || ckpt_span(shots[i]) != span) return 1;
+    DevBuf tbuf;
+    WP_TRY(wp_malloc(P0, &tbuf.p, sizeof(int), "time index"));
+    int *tdev = (int *)tbuf.p;
+    // fixed tables: slots 0, 1 the forward arrangements of the state (the
+    // recomputation starts from the same arrangement in every segment);
+    // slot 2 + 2p + q the transposed step with imaging at segment position p
+    // (forward level n0 + p + 1 in segment buffer p) in adjoint arrangement q
+    std::unique_ptr<TtiBatch, void (*)(TtiBatch *)> tb(tti_batch_new(), tti_batch_free);
+    std::vector<TtiBatchReq> req(n);
+    std::string err;
+    for (int c = 0; c < 2; c++) {
+        for (int i = 0; i < n; i++) {
+            float *const *q = shots[i]->st;
+            req[i] = c == 0 ? TtiBatchReq{shots[i], {q[0], q[1], q[2], q[3]}, false, nullptr, nullptr, nullptr}
+                            : TtiBatchReq{shots[i], {q[2], q[3], q[0], q[1]}, false, nullptr, nullptr, nullptr};
+        }
+        const int rc = tti_batch_fix(tb.get(), req.data(), n, c, st, &err);
+        if (rc) return rc == 1 ? 1 : wp_fail(P0, rc, err);
+    }
+    for (int pos = 0; pos < K; pos++)
+        for (int qa = 0; qa < 2; qa++) {
+            for (int i = 0; i < n; i++) {
+                prop_s *P = shots[i];
+                float *const *a = P->ast;
+                const float *u = P->seg + (size_t)pos * 2 * (size_t)P->g.N;
+                req[i] = qa == 0 ? TtiBatchReq{P, {a[0], a[1], a[2], a[3]}, true, u, u + P->g.N, (float *)gb[i].p}
+                                 : TtiBatchReq{P, {a[2], a[3], a[0], a[1]}, true, u, u + P->g.N, (float *)gb[i].p};
+            }
+            const int rc = tti_batch_fix(tb.get(), req.data(), n, 2 + 2 * pos + qa, st, &err);
+            if (rc) return rc == 1 ? 1 : wp_fail(P0, rc, err);
+        }
+    phase("tables");
+    auto launch = [&](int slot) -> int {
+        if (tti_batch_launch_fixed(tb.get(), slot, st) != PROP_OK)
+            return wp_fail(P0, PROP_ECUDA, "batched TTI step launch failed");
+        for (int i = 0; i < n; i++) shots[i]->kern_launches += 1;
+        batch_stats[0]++;
+        return PROP_OK;
+    };
+    // The per-shot kernels of a step (receiver sampling, injection, segment
+    // copies) are small: shot i runs them on worker stream i % W, forked from
+    // and joined back into the shared stream, so that different shots' run
+    // side by side (parallel branches when captured).
+    constexpr int W = 8;
+    struct Workers {
+        cudaStream_t s[W] = {};
+        cudaEvent_t fork = nullptr, join[W] = {};
+        ~Workers()
+        {
+            for (auto x : s)
+                if (x) cudaStreamDestroy(x);
+            if (fork) cudaEventDestroy(fork);
+            for (auto e : join)
+                if (e) cudaEventDestroy(e);
+        }
+    } wk;
+    const int nwk = std::min(W, n);
+    WP_CK(P0, cudaEventCreateWithFlags(&wk.fork, cudaEventDisableTiming));
+    for (int w = 0; w < nwk; w++) {
+        WP_CK(P0, cudaStreamCreateWithFlags(&wk.s[w], cudaStreamNonBlocking));
+        WP_CK(P0, cudaEventCreateWithFlags(&wk.join[w], cudaEventDisableTiming));
+    }
+    auto per_shot = [&](const std::function<int(int)> &fn) -> int {
+        WP_CK(P0, cudaEventRecord(wk.fork, st));
+        for (int w = 0; w < nwk; w++) WP_CK(P0, cudaStreamWaitEvent(wk.s[w], wk.fork, 0));
+        int rc = PROP_OK;
+        for (int i = 0; i < n && !rc; i++) {
+            shots[i]->stream = wk.s[i % nwk];
+            rc = fn(i);
+            shots[i]->stream = st;
+        }
+        for (int w = 0; w < nwk; w++) {
+            WP_CK(P0, cudaEventRecord(wk.join[w], wk.s[w]));
+            WP_CK(P0, cudaStreamWaitEvent(st, wk.join[w], 0));
+        }
+        return rc;
+    };
+    // forward step in arrangement c: record d^t, step, inject q^t (and, in
+    // the recomputation, copy the new level into segment buffer pos), t += 1
+    auto fwd = [&](int c, bool record, int pos) -> int {
+        if (record)
+            WP_TRY(per_shot([&](int i) -> int {
+                float *const *q = shots[i]->st;
+                sp_record(shots[i], &G[i].R, c == 0 ? q[0] : q[2], nullptr, nullptr, 1.f, (float *)stage[i].p,
+                          tdev);
+                return PROP_OK;
+            }));
+        WP_TRY(launch(c));
+        WP_TRY(per_shot([&](int i) -> int {
+            prop_s *P = shots[i];
+            float *const *q = P->st;
+            float *pn = c == 0 ? q[2] : q[0], *rn = c == 0 ? q[3] : q[1];
+            sp_inject(P, &G[i].S, wav[i], nt, 0, P->g.dt * P->g.dt, 1, pn, rn, nullptr, nullptr, nullptr, tdev);
+            if (pos >= 0) {
+                const size_t N = (size_t)P->g.N;
+                float *d = P->seg + (size_t)pos * 2 * N;
+                WP_CK(P, cudaMemcpyAsync(d, pn, N * 4, cudaMemcpyDeviceToDevice, P->stream));
+                WP_CK(P, cudaMemcpyAsync(d + N, rn, N * 4, cudaMemcpyDeviceToDevice, P->stream));
+            }
+            return PROP_OK;
+        }));
+        k_tick(P0, tdev, 1);
+        return PROP_OK;
+    };
+    // recomputed forward step at segment position pos
+    auto recompute = [&](int pos) -> int { return fwd(pos & 1, false, pos); };
+    // transposed step k = t with imaging at position pos, adjoint
+    // arrangement qa; residual r^k into the new level; t -= 1
+    auto adj = [&](int pos, int qa) -> int {
+        WP_TRY(launch(2 + 2 * pos + qa));
+        WP_TRY(per_shot([&](int i) -> int {
+            prop_s *P = shots[i];
+            float *const *a = P->ast;
+            const float *u = P->seg + (size_t)pos * 2 * (size_t)P->g.N;
+            sp_inject(P, &G[i].R, (const float *)tr[i].p, nt, 0, 1.f, 3, qa == 0 ? a[2] : a[0], P->tmp[6],
+                      P->tmp[7], u, (float *)gb[i].p, tdev);
+            return PROP_OK;
+        }));
+        k_tick(P0, tdev, -1);
+        return PROP_OK;
+    };
+    const char *ge = getenv("WAVEPROP_GRAPHS");
+    const bool graphs = !(ge && !strcmp(ge, "0"));
+    struct Graphs {
+        cudaGraphExec_t g[4] = {};
+        ~Graphs()
+        {
+            for (auto e : g)
+                if (e) cudaGraphExecDestroy(e);
+        }
+    } gx;
+    // run body() directly, or from graph `id` (captured on first use)
+    auto run = [&](int id, const std::function<int()> &body) -> int {
+        if (!graphs) return body();
+        if (!gx.g[id]) {
+            cudaGraph_t gr = nullptr;
+            WP_CK(P0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int rb = body();
+            const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+            if (rb || ec != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                cudaGetLastError();
+                return rb ? rb : wp_cuda(P0, ec, "capture of the lockstep segment");
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&gx.g[id], gr, 0);
+            cudaGraphDestroy(gr);
+            WP_CK(P0, ei);
+        }
+        WP_CK(P0, cudaGraphLaunch(gx.g[id], st));
+        return PROP_OK;
+    };
+    // ---- forward sweep with checkpoints ----
+    k_set_int(P0, tdev, 0);
+    for (int j = 0; j < J; j++) {
+        const int n0 = j * K, n1 = j + 1 < J ? n0 + K : nt;     // steps n0 .. n1-1
+        const int c0 = n0 & 1;
+        WP_TRY(per_shot([&](int i) -> int {
+            float *const *q = shots[i]->st;
+            float *s4[4] = {q[0], q[1], q[2], q[3]};
+            if (c0) s4[0] = q[2], s4[1] = q[3], s4[2] = q[0], s4[3] = q[1];
+            return save_checkpoint(shots[i], j, s4);
+        }));
+        auto body = [&]() -> int {
+            for (int t = n0; t < n1; t++) WP_TRY(fwd(t & 1, true, -1));
+            return PROP_OK;
+        };
+        if (n1 - n0 == K) WP_TRY(run(c0, body));
+        else WP_TRY(body());
+    }
+    phase("forward");
+    // ---- residuals and misfits ----
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        const long long m = (long long)nrec[i] * nt;
+        sp_transpose(P, (const float *)stage[i].p, (float *)tr[i].p, nrec[i], nt);
+        k_axpy_sq(P, (const float *)tr[i].p, obs[i], (float *)tr[i].p, m);
+        double ss = 0.0;
+        WP_TRY(k_sumsq(P, (const float *)tr[i].p, m, &ss));
+        mis[i] = 0.5 * ss;
+    }
+    phase("misfit");
+    // ---- adjoint sweep over the segments, last first ----
+    int qa = 0;                    // arrangement of the adjoint state
+    for (int j = J - 1; j >= 0; j--) {
+        const int n0 = j * K, E = std::min(n0 + K, span), len = E - n0;
+        WP_TRY(per_shot([&](int i) -> int { return load_checkpoint(shots[i], j, shots[i]->st); }));
+        k_set_int(P0, tdev, n0);
+        const int q0 = qa;
+        auto body = [&]() -> int {
+            for (int pos = 0; pos < len; pos++) WP_TRY(recompute(pos));
+            for (int k = E, q = q0; k >= n0 + 1; k--, q ^= 1) WP_TRY(adj(k - n0 - 1, q));
+            return PROP_OK;
+        };
+        if (len == K) WP_TRY(run(2 + q0, body));
+        else WP_TRY(body());
+        qa = (qa + len) & 1;
+    }
+    phase("adjoint");
+    // ---- gradients on the physical grid ----
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        const size_t np = (size_t)P->g.px * P->g.py * P->g.pz;
+        k_fold(P, (const float *)gb[i].p, (float *)gp[i].p, P->tmp[0], P->tmp[1]);
+        WP_TRY(copy_out(P, grad[i], (const float *)gp[i].p, np));
+    }
+    int first = PROP_OK;
+    for (int i = 0; i < n; i++) {
+        const int rc = finish(shots[i]);
+        if (rc && !first) {
+            first = rc;
+            tl_err = "shot " + std::to_string(i) + ": " + prop_last_error(shots[i]);
+        }
+    }
+    phase("gradients");
+    for (int i = 0; i < n; i++) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(e, st);
+            cudaStreamWaitEvent(own[i], e, 0);
+            cudaEventDestroy(e);
+        }
+    }
+    return first;
 }
 
 extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
@@ -2030,7 +2393,50 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
     // every shot launches its own)
     const char *bl = getenv("WAVEPROP_BATCH_LAUNCH");
     const bool share = !(bl && !strcmp(bl, "0"));
+    const char *vb = getenv("WAVEPROP_BATCH_VERBOSE");
+    const bool verbose = vb && !strcmp(vb, "1");
     for (int w = 0; w < nw; w++) {
+        const auto tw = std::chrono::steady_clock::now();
+        struct WaveTime {
+            bool on;
+            int w;
+            std::chrono::steady_clock::time_point t0;
+            ~WaveTime()
+            {
+                if (on)
+                    fprintf(stderr, "wave %d: %9.3f ms\n", w,
+                            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+            }
+        } wt{verbose, w, tw};
+        // a wave of TTI shots with one sweep: lockstep, one host thread
+        std::vector<int> ids;
+        for (int i = 0; i < nshots; i++)
+            if (wave[i] == w) ids.push_back(i);
+        std::vector<prop_t *> ws;
+        for (int i : ids) ws.push_back(shots[i]);
+        if (share && lockstep_ok(ws.data(), (int)ws.size())) {
+            const int m = (int)ids.size();
+            std::vector<const float *> wv(m), sx(m), rx(m), dob(m);
+            std::vector<float *> gr(m);
+            std::vector<int> ns(m), nr(m);
+            std::vector<double> ms(m, 0.0);
+            for (int k = 0; k < m; k++) {
+                const int i = ids[k];
+                wv[k] = wavelet[i]; sx[k] = src_xyz[i]; rx[k] = rec_xyz[i]; dob[k] = d_obs[i];
+                gr[k] = grad[i]; ns[k] = nsrc[i]; nr[k] = nrec[i];
+            }
+            const int lr = gradient_lockstep(ws.data(), m, wv.data(), sx.data(), ns.data(), rx.data(), nr.data(),
+                                             dob.data(), gr.data(), ms.data());
+            if (lr != 1) {
+                for (int k = 0; k < m; k++) {
+                    const int i = ids[k];
+                    rc[i] = lr;
+                    mis[i] = ms[k];
+                    if (!lr) rc[i] = prop_trim(shots[i]);     // the next waves get the work arrays
+                }
+                continue;
+            }
+        }
         std::unique_ptr<StepRendezvous> rdv;
         int nb = 0;
         for (int i = 0; i < nshots; i++)

@@ -413,6 +413,14 @@ void k_tick(prop_s *P, int *tdev, int d)
     P->kern_launches++;
 }
 
+__global__ void set_int_kernel(int *p, int v) { *p = v; }
+
+void k_set_int(prop_s *P, int *p, int v)
+{
+    set_int_kernel<<<1, 1, 0, P->stream>>>(p, v);
+    P->kern_launches++;
+}
+
 void sp_inject(prop_s *P, const SparseDev *S, const float *traces, int nt, int t, float scale,
                int mode, float *f0, float *f1, float *f2, const float *grad_u, float *grad, const int *tdev)
 {

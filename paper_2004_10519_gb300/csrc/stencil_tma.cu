@@ -1680,8 +1680,11 @@ struct TtiBatch {
     char *hel[NSLOT] = {};
     size_t hel_cap = 0;
     cudaEvent_t elcopied[NSLOT] = {};
-    // fixed tables of forward-step configurations (graph replay)
-    TtiShot *dfixed[2] = {};
+    // fixed tables of step configurations, one per slot (graph replay); the
+    // mode of a slot: 0 forward step, 1 transposed step, 2 transposed step
+    // with imaging
+    std::vector<TtiShot *> dfixed;
+    std::vector<int> fixed_mode;
     size_t fixed_cap = 0;
     int fixed_n = 0, fixed_M = 0;
     FDW w{};
@@ -1694,8 +1697,7 @@ void tti_batch_free(TtiBatch *b)
     if (!b) return;
     cudaFree(b->dtiles);
     cudaFree(b->dshots);
-    cudaFree(b->dfixed[0]);
-    cudaFree(b->dfixed[1]);
+    for (auto d : b->dfixed) cudaFree(d);
     cudaFree(b->del);
     for (int i = 0; i < TtiBatch::NSLOT; i++) {
         if (b->elcopied[i]) {
@@ -1854,59 +1856,84 @@ int tti_batch_fix(TtiBatch *b, const TtiBatchReq *req, int n, int slot, cudaStre
         *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
         return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
     };
+    if (slot < 0) return PROP_EINVAL;
+    const int mode = req[0].adjoint ? (req[0].grad ? 2 : 1) : 0;
     for (int i = 0; i < n; i++)
-        if (!tti_batchable(req[i].P) || req[i].P->M != req[0].P->M || req[i].adjoint) return 1;
+        if (!tti_batchable(req[i].P) || req[i].P->M != req[0].P->M || req[i].adjoint != req[0].adjoint ||
+            (req[i].grad != nullptr) != (req[0].grad != nullptr))
+            return 1;
     if (int rc = tti_batch_tiles(b, req, n, st, err)) return rc;
-    if ((size_t)n > b->fixed_cap) {
+    if ((size_t)n > b->fixed_cap) {              // every slot holds n entries
         for (auto &d : b->dfixed) {
             cudaFree(d);
             d = nullptr;
         }
-        b->fixed_cap = 0;
-        for (auto &d : b->dfixed)
-            if (int rc = ck(cudaMalloc(&d, n * sizeof(TtiShot)), "batched TTI fixed table")) return rc;
         b->fixed_cap = n;
     }
+    if ((size_t)slot >= b->dfixed.size()) {
+        b->dfixed.resize(slot + 1, nullptr);
+        b->fixed_mode.resize(slot + 1, -1);
+    }
+    if (!b->dfixed[slot])
+        if (int rc = ck(cudaMalloc(&b->dfixed[slot], b->fixed_cap * sizeof(TtiShot)), "batched TTI fixed table"))
+            return rc;
     std::vector<TtiShot> H(n);
     int rc = 1;
+#define WP_FILL(MM)                                                                                            \
+    case MM:                                                                                                   \
+        rc = mode == 0 ? tti_batch_fill<MM, 0, 0>(req, n, H.data(), err)                                      \
+                       : (mode == 1 ? tti_batch_fill<MM, 1, 0>(req, n, H.data(), err)                         \
+                                    : tti_batch_fill<MM, 1, 1>(req, n, H.data(), err));                       \
+        break;
     switch (req[0].P->M) {
-    case 2: rc = tti_batch_fill<2, 0, 0>(req, n, H.data(), err); break;
-    case 4: rc = tti_batch_fill<4, 0, 0>(req, n, H.data(), err); break;
-    case 6: rc = tti_batch_fill<6, 0, 0>(req, n, H.data(), err); break;
-    case 8: rc = tti_batch_fill<8, 0, 0>(req, n, H.data(), err); break;
+        WP_FILL(2)
+        WP_FILL(4)
+        WP_FILL(6)
+        WP_FILL(8)
     }
+#undef WP_FILL
     if (rc) return rc;
     if (int r2 = ck(cudaMemcpy(b->dfixed[slot], H.data(), n * sizeof(TtiShot), cudaMemcpyHostToDevice),
                     "batched TTI fixed table copy"))
         return r2;
+    b->fixed_mode[slot] = mode;
     b->fixed_n = n;
     b->fixed_M = req[0].P->M;
     b->w = req[0].P->w;
     return PROP_OK;
 }
 
-// forward step of every shot of fixed table `slot` (capturable: launches only)
-template <int M>
+// the step of every shot of fixed table `slot` (capturable: launches only)
+template <int M, int ADJ, int GRAD>
 static int tti_batch_run_fixed(TtiBatch *b, int slot, cudaStream_t st)
 {
-    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * UL<M, 0, 0>::SZ * sizeof(float) + 64;
-    static const bool attr = set_smem(tti_rot_batch<M>, s1) && set_smem(tti_upd_batch<M, 0, 0>, s2);
+    const size_t s1 = RL<M>::NS * RL<M>::SZ * sizeof(float) + 64,
+                 s2 = NSTAGE * UL<M, ADJ, GRAD>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(tti_rot_batch<M>, s1) && set_smem(tti_upd_batch<M, ADJ, GRAD>, s2);
     (void)attr;
     const unsigned nt = (unsigned)b->htiles.size();
     const dim3 blk(TZ2, FY + 2, 1);
     tti_rot_batch<M><<<nt, blk, s1, st>>>(b->dfixed[slot], b->dtiles, b->w);
-    tti_upd_batch<M, 0, 0><<<nt, blk, s2, st>>>(b->dfixed[slot], b->dtiles, b->w);
+    tti_upd_batch<M, ADJ, GRAD><<<nt, blk, s2, st>>>(b->dfixed[slot], b->dtiles, b->w);
     return cudaGetLastError() == cudaSuccess ? PROP_OK : PROP_ECUDA;
 }
 
 int tti_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t st)
 {
+    if (slot < 0 || (size_t)slot >= b->dfixed.size() || !b->dfixed[slot]) return PROP_EINVAL;
+    const int mode = b->fixed_mode[slot];
+#define WP_RUN(MM)                                                                                             \
+    case MM:                                                                                                   \
+        return mode == 0 ? tti_batch_run_fixed<MM, 0, 0>(b, slot, st)                                         \
+                         : (mode == 1 ? tti_batch_run_fixed<MM, 1, 0>(b, slot, st)                            \
+                                      : tti_batch_run_fixed<MM, 1, 1>(b, slot, st));
     switch (b->fixed_M) {
-    case 2: return tti_batch_run_fixed<2>(b, slot, st);
-    case 4: return tti_batch_run_fixed<4>(b, slot, st);
-    case 6: return tti_batch_run_fixed<6>(b, slot, st);
-    case 8: return tti_batch_run_fixed<8>(b, slot, st);
+        WP_RUN(2)
+        WP_RUN(4)
+        WP_RUN(6)
+        WP_RUN(8)
     }
+#undef WP_RUN
     return PROP_EINVAL;
 }
 

@@ -265,3 +265,42 @@ def test_elastic_batch_shares_launches(wp, snap):
         assert j == ref[i][1], i
     for pr in props:
         pr.close()
+
+
+@pytest.mark.parametrize("snap,interval", [(1, 7), (2, 7), (2, 6), (3, 5)],
+                         ids=["fp32ckpt-K7", "bf16-K7", "bf16-K6", "fp16-K5"])
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_lockstep_gradient_batch_is_bitwise(wp, monkeypatch, snap, interval, graphs):
+    """A wave of TTI shots with checkpoints and one sweep runs in lockstep
+    from one host thread: per step one launch of each pass over all shots,
+    full segments replayed from CUDA graphs (two arrangements of the state
+    when K is odd; a partial first adjoint segment and, for K = 7, a
+    partial last forward segment launched directly).  Gradients and misfits
+    are bitwise those of one prop_gradient per shot and of the per-thread
+    batch (WAVEPROP_LOCKSTEP=0), with graphs on and off."""
+    monkeypatch.setenv("WAVEPROP_GRAPHS", graphs)
+    sel = window_shots(nt=60)
+    kw = dict(snap_mode=snap, ckpt_interval=interval)
+    ref = []
+    for p, d in sel:
+        prop = wp.Propagator.from_problem(p, **kw)
+        ref.append(prop.gradient(p.wavelet, p.src, p.rec, d))
+        prop.close()
+    out = {}
+    for lock in ("1", "0"):
+        monkeypatch.setenv("WAVEPROP_LOCKSTEP", lock)
+        props = [wp.Propagator.from_problem(p, **kw) for p, _ in sel]
+        out[lock] = wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                                      [p.rec for p, _ in sel], [d for _, d in sel])
+        out[lock + "stats"] = wp.batch_stats()
+        # the handles stay usable after the batch
+        p, d = sel[0]
+        np.testing.assert_array_equal(props[0].gradient(p.wavelet, p.src, p.rec, d)[0], ref[0][0])
+        for pr in props:
+            pr.close()
+    assert out["1stats"][0] > 0 and out["1stats"][1] == 0, out["1stats"]
+    for i in range(len(sel)):
+        assert np.max(np.abs(ref[i][0])) > 0
+        for lock in ("1", "0"):
+            np.testing.assert_array_equal(out[lock][0][i], ref[i][0], err_msg=f"shot {i} lockstep {lock}")
+            assert out[lock][1][i] == ref[i][1], (i, lock)

@@ -9,7 +9,8 @@ family on grids ragged in y and z: elastic and centred TTI at all three
 tile heights (forward, adjoint, gradient; TTI also the (m, eps, delta,
 theta, phi) gradient), the staggered-pair operators (forward and the
 five-parameter gradient), acoustic forward, batched gradients with shared
-launches (TTI and elastic) and lockstep forward modelling.  No check may
+launches (TTI and elastic), lockstep gradients and lockstep forward
+modelling.  No check may
 fire, and every result must be bitwise that of the normal build."""
 import os
 import subprocess
@@ -92,6 +93,15 @@ def run_cases(wp):
                 out[f"fwdbatch{i}"] = trs[i]
         for q in props:
             q.close()
+    # lockstep gradients (BF16 checkpoints: graph-replayed segments)
+    ps = [_tti(nx=26 + 4 * i, ny=22 + 2 * i, seed=i) for i in range(2)]
+    props = [wp.Propagator.from_problem(p, snap_mode=wp.SNAP_CKPT_BF16, ckpt_interval=7) for p in ps]
+    gs, Js = wp.gradient_batch(props, [p.wavelet for p in ps], [p.src for p in ps], [p.rec for p in ps],
+                               [_data(p, 5 + i) for i, p in enumerate(ps)])
+    for i in range(2):
+        out[f"lockstep{i}"], out[f"lockstep{i}_J"] = gs[i], np.array([Js[i]])
+    for q in props:
+        q.close()
     return out
 
 
