@@ -613,7 +613,8 @@ def batch_shots_per_hour(wp, torch, dev, nshots, nt, small=False, kind="tti", wi
             "sequential": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq},
             "batched": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
                         "waves": waves, "shared_launch_rounds": shared, "unshared_rounds": alone,
-                        "driver": "lockstep (graph-replayed segments) where a wave qualifies"},
+                        "driver": "lockstep with graph-replayed segments for qualifying waves of windows up to "
+                                  "16 M points, else one host thread per shot meeting at every step"},
             "batched_rendezvous": {"seconds": t_rdv, "shots_per_hour": 3600.0 * nshots / t_rdv,
                                    "shared_launch_rounds": shared_rdv, "unshared_rounds": alone_rdv},
             "batched_own_launches": {"seconds": t_own, "shots_per_hour": 3600.0 * nshots / t_own},

@@ -233,11 +233,12 @@ int prop_forward_batch(prop_t *const *shots, int nshots, const float *const *wav
  * launch of each pass over a table of all the shots' tiles (set
  * WAVEPROP_BATCH_LAUNCH=0 to launch shot by shot).  A wave whose shots are
  * all such TTI shots with checkpoints (FP32, BF16 or FP16), one space
- * order, nt and checkpoint interval runs in lockstep from the calling
+ * order, nt and checkpoint interval, on windows of at most 16 M
+ * computational points on average, runs in lockstep from the calling
  * thread: per step one launch of each pass for every shot, and each full
  * checkpoint segment (the forward steps between two checkpoints; the
  * recomputation and the transposed steps of a segment) replayed from a
- * CUDA graph (WAVEPROP_LOCKSTEP=0: one thread per shot instead;
+ * CUDA graph (WAVEPROP_LOCKSTEP=1: for any window size, =0: never;
  * WAVEPROP_GRAPHS=0: direct launches). */
 int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
                         const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
