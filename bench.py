@@ -511,6 +511,57 @@ def gradient_small(wp, torch, dev):
     return out
 
 
+def tile_heights(wp, torch, dev, small=False):
+    """Step time of the TMA-fed passes at each tile height (8, 16, 32 rows of
+    y; the x-extent tuned for each) and the autotuner's own choice, on the
+    benchmark grids and on a small window: elastic so 8 at 296^3 and
+    100^3, TTI so 12 at 880x880x480 and 100^3 (computational points),
+    random models and states (content does not change the work)."""
+    rng = np.random.default_rng(11)
+    cases = [("elastic", 256, 256, 256, 20, 8, 10.0), ("elastic", 60, 60, 60, 20, 8, 10.0),
+             ("tti", 800, 800, 400, 40, 12, 12.5), ("tti", 60, 60, 60, 20, 12, 12.5)]
+    if small:
+        cases = [c[:1] + (60, 60, 60) + c[4:] for c in cases]
+    stream = torch.cuda.current_stream(dev).cuda_stream
+    out = []
+    for kind, nx, ny, nz, nbl, so, h in cases:
+        f = lambda lo, hi: rng.uniform(lo, hi, (nx, ny, nz)).astype(np.float32)
+        if kind == "elastic":
+            vp = f(1.5, 4.5)
+            model, K, vmax = [vp, (vp / 1.73).astype(np.float32), f(1.0, 2.5)], wp.PROP_ELASTIC, 4.5
+        else:
+            eps = f(0.0, 0.3)
+            model = [f(1.5, 4.5), eps, (eps * f(0.0, 0.5)).astype(np.float32), f(0.0, 0.7), f(0.0, 1.57)]
+            K, vmax = wp.PROP_TTI, 4.5 * np.sqrt(1.6)
+        dt = synth.cfl_dt(h, vmax)
+        row = {"kind": kind, "so": so}
+        for ty in ("8", "16", "32", "auto"):
+            if ty == "auto":
+                os.environ.pop("WAVEPROP_TILE_Y", None)
+            else:
+                os.environ["WAVEPROP_TILE_Y"] = ty
+            prop = wp.Propagator(K, (nx, ny, nz), nbl, h, so, 10, model, dt=dt, stream=stream)
+            row["grid"] = list(prop.grid)
+            nf = 9 if kind == "elastic" else 4
+            prop.set_state([torch.randn(prop.grid, device=dev) for _ in range(nf)])
+            steps = 10 if nx > 100 else 200
+            prop.step(3)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with timed_region():
+                e0.record()
+                prop.step(steps)
+                e1.record()
+                torch.cuda.synchronize()
+            row[ty] = {"rows": prop.tile_rows, "planes": prop.tile_planes,
+                       "ms_per_step": e0.elapsed_time(e1) / steps}
+            prop.close()
+        os.environ.pop("WAVEPROP_TILE_Y", None)
+        del model
+        out.append(row)
+    return out
+
+
 def gradient_aniso_cost(wp, torch, dev, small=False):
     """Cost of the TTI gradient w.r.t. (m, eps, delta, theta, phi) against
     the m-only gradient, for the centred (0) and the staggered-pair (1)
@@ -725,6 +776,8 @@ def run_extras(wp, torch, dev, args, extras):
     if "elgrad" in extras:
         _clocked(out, "elgrad", lambda: elastic_gradient_shots_per_hour(
             wp, torch, dev, args.grad_nt, [int(v) for v in args.grad_modes.split(",")], small=args.small))
+    if "tiles" in extras:
+        _clocked(out, "tiles", lambda: tile_heights(wp, torch, dev, small=args.small))
     if "gradaniso" in extras:
         _clocked(out, "gradaniso", lambda: gradient_aniso_cost(wp, torch, dev, small=args.small))
     if "gradsmall" in extras:
@@ -757,7 +810,7 @@ def main():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the TTI so-12 industry-scale step rates reported beside the headline")
     ap.add_argument("--extra", default="",
-                    help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, gradaniso, batch, rtm "
+                    help="comma list: tti, ttisp, acoustic, el2d, grad, elgrad, gradsmall, gradaniso, tiles, batch, rtm "
                          "(secondary measurements)")
     ap.add_argument("--grad-nt", type=int, default=600)
     ap.add_argument("--grad-modes", default="0,1,2,3",
