@@ -699,15 +699,15 @@ def oracle_tti_industry(steps=3, nx=800, ny=800, nz=400, nbl=40, h=12.5, so=12):
             "full_run_estimate_hours": sec / steps * 3000 / 3600.0}
 
 
-def forward_batch_shots_per_hour(wp, torch, dev, nshots, nt, windows=None):
-    """TTI forward modelling (so 12) of many shots on windows of one large
-    model: one prop_forward after another against one prop_forward_batch
-    (lockstep, one launch per pass and step for every shot, two steps
-    replayed from a CUDA graph); traces compared bitwise."""
+def forward_batch_shots_per_hour(wp, torch, dev, nshots, nt, windows=None, kind="tti"):
+    """Forward modelling (TTI so 12 or elastic so 8) of many shots on
+    windows of one large model: one prop_forward after another against one
+    prop_forward_batch (lockstep, one launch per pass and step for every
+    shot, two steps replayed from a CUDA graph); traces compared bitwise."""
     kw = {}
     if windows:
         kw.update(size_range=windows[:2], nz=windows[2])
-    shots = synth.tti_batch_shots(nshots, nt, **kw)
+    shots = (synth.tti_batch_shots if kind == "tti" else synth.elastic_batch_shots)(nshots, nt, **kw)
     stream = torch.cuda.current_stream(dev).cuda_stream
     to = lambda a: torch.from_numpy(a).to(dev)
     props, wav, src, rec = [], [], [], []
@@ -729,14 +729,25 @@ def forward_batch_shots_per_hour(wp, torch, dev, nshots, nt, windows=None):
         bat = wp.forward_batch(props, wav, src, rec)
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t0
-    same = all(bool(torch.equal(a, b)) for a, b in zip(seq, bat))
+    # lockstep whatever the window size (the call above takes it only for
+    # windows up to 16 M points)
+    os.environ["WAVEPROP_LOCKSTEP"] = "1"
+    with timed_region():
+        t0 = time.perf_counter()
+        bat2 = wp.forward_batch(props, wav, src, rec)
+        torch.cuda.synchronize()
+        t_lock = time.perf_counter() - t0
+    del os.environ["WAVEPROP_LOCKSTEP"]
+    same = all(bool(torch.equal(a, b)) and bool(torch.equal(a, c)) for a, b, c in zip(seq, bat, bat2))
     for p in props:
         p.close()
-    return {"shots": nshots, "nt": nt, "points_total": npts,
+    return {"kind": kind, "shots": nshots, "nt": nt, "points_total": npts,
             "one_call_per_shot": {"seconds": t_seq, "shots_per_hour": 3600.0 * nshots / t_seq,
                                   "gpts_per_s": npts * nt / t_seq / 1e9},
             "forward_batch": {"seconds": t_bat, "shots_per_hour": 3600.0 * nshots / t_bat,
                               "gpts_per_s": npts * nt / t_bat / 1e9},
+            "forward_batch_lockstep_forced": {"seconds": t_lock, "shots_per_hour": 3600.0 * nshots / t_lock,
+                                              "gpts_per_s": npts * nt / t_lock / 1e9},
             "bitwise_equal": same}
 
 
@@ -786,9 +797,10 @@ def run_extras(wp, torch, dev, args, extras):
         _clocked(out, "oracle3", lambda: oracle_tti_industry())
     if "fwdbatch" in extras:          # forward modelling, industry-size and small windows
         _clocked(out, "fwdbatch", lambda: forward_batch_shots_per_hour(wp, torch, dev, args.batch_shots,
-                                                                       args.batch_nt))
+                                                                       args.batch_nt, kind=args.batch_kind))
         _clocked(out, "fwdbatchsmall", lambda: forward_batch_shots_per_hour(wp, torch, dev, args.batch_shots,
-                                                                            args.batch_nt, windows=(40, 80, 60)))
+                                                                            args.batch_nt, windows=(40, 80, 60),
+                                                                            kind=args.batch_kind))
     if "batchsmall" in extras:       # many small windows: 40-80 x 40-80 x 60 cells
         _clocked(out, "batchsmall", lambda: batch_shots_per_hour(wp, torch, dev, args.batch_shots, args.batch_nt,
                                                                  kind=args.batch_kind, windows=(40, 80, 60)))

@@ -196,8 +196,10 @@ int prop_backward(prop_t *p, const float *resid, float *grad, float *src_grad);
 /* Forward modelling of many independent shots in lockstep (Sec. III-B):
  * shot i computes exactly prop_forward(shots[i], wavelet[i], src_xyz[i],
  * nsrc[i], rec_xyz[i], nrec[i], traces[i]) -- bitwise the same traces.
- * When every shot is TTI with the centred operators, the same space order
- * and nt and a computational nz that is a multiple of 4, each time step is
+ * When every shot is TTI with the centred operators (or every shot is
+ * elastic), with the same space order and nt, a computational nz that is a
+ * multiple of 4 and windows of at most 16 M computational points on
+ * average (WAVEPROP_LOCKSTEP=1: any size, =0: never), each time step is
  * one launch of each pass over a table of all the shots' tiles (each shot
  * keeping its own model window, grid and x-extent) beside the shots'
  * injection and receiver sampling; two steps are captured once as a CUDA

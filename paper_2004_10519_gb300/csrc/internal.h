@@ -229,6 +229,10 @@ struct ElBatchReq {
 bool el_batchable(const prop_s *P);
 // 0 launched; 1 not batchable together (launch one by one); < 0 error
 int el_batch_step(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t stream, std::string *err);
+// fixed table `slot` of an elastic forward step of every request (mode 0,
+// sign +1; 1: not batchable), and launches of it that may be captured
+int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream_t stream, std::string *err);
+int el_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t stream);
 // per-shot pointwise kernels of the batched transposed elastic step (elastic.cu)
 void el_adj_pre_launch(prop_s *P, float *const *S, cudaStream_t st);
 void el_face2_launch(prop_s *P, float *const *S, const float *const *xk, const float *const *xk1, cudaStream_t st);

@@ -1791,12 +1791,13 @@ int rdv_el_step(prop_s *P, const ElBatchReq &e)
 }
 
 // ---------------------------------------------------------------------------
-// Forward modelling of many TTI shots in lockstep: per time step the
-// receivers of every shot are sampled, one tile-table launch of each pass
-// advances every shot, and the sources are injected.  The TTI state buffers
-// rotate with period 2, so two steps are captured once into a CUDA graph
-// (the sparse kernels read the time index from device memory and a
-// one-thread kernel advances it) and the graph is replayed nt/2 times.
+// Forward modelling of many TTI (or many elastic) shots in lockstep: per
+// time step the receivers of every shot are sampled, one tile-table launch
+// of each pass advances every shot, and the sources are injected.  The TTI
+// state buffers rotate with period 2 (the elastic state is updated in
+// place), so two steps are captured once into a CUDA graph (the sparse
+// kernels read the time index from device memory and a one-thread kernel
+// advances it) and the graph is replayed nt/2 times.
 // ---------------------------------------------------------------------------
 static int forward_batch_one_by_one(prop_t *const *shots, int n, const float *const *wavelet,
                                     const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
@@ -1828,11 +1829,22 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
         if (!wavelet[i] || !src_xyz[i] || !rec_xyz[i] || !traces[i] || nsrc[i] < 1 || nrec[i] < 1)
             return wp_fail(nullptr, PROP_EINVAL, "shot " + std::to_string(i) + ": missing wavelet, geometry or output");
     }
-    // lockstep needs TTI shots on the TMA-fed passes with one space order and nt
+    // lockstep needs TTI shots (or elastic shots) on the TMA-fed passes with
+    // one space order and nt
+    const bool el = el_batchable(shots[0]);
     bool lock = true;
     for (int i = 0; i < n && lock; i++)
-        lock = tti_batchable(shots[i]) && shots[i]->M == shots[0]->M && shots[i]->d.nt == shots[0]->d.nt &&
-               !shots[i]->broken;
+        lock = (el ? el_batchable(shots[i]) : tti_batchable(shots[i])) && shots[i]->M == shots[0]->M &&
+               shots[i]->d.nt == shots[0]->d.nt && !shots[i]->broken;
+    // as for gradients, lockstep pays on small windows: elastic, 32 shots of
+    // about 1 M points 168.5k against 153.0k shots/h; of 30-110 M points
+    // 7,269 against 7,976 (the windows fill the GPU one at a time).
+    // WAVEPROP_LOCKSTEP=1 forces it for any size, =0 disables it.
+    const char *ls = getenv("WAVEPROP_LOCKSTEP");
+    double pts = 0.0;
+    for (int i = 0; i < n; i++) pts += (double)shots[i]->g.N;
+    if (ls && !strcmp(ls, "0")) lock = false;
+    else if (!(ls && !strcmp(ls, "1")) && pts / n > 16.0e6) lock = false;
     const char *bl = getenv("WAVEPROP_BATCH_LAUNCH");
     if (!lock || n < 2 || (bl && !strcmp(bl, "0")))
         return forward_batch_one_by_one(shots, n, wavelet, src_xyz, nsrc, rec_xyz, nrec, traces);
@@ -1888,41 +1900,59 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
         WP_TRY(dev_in(P, wavelet[i], (size_t)nsrc[i] * nt, wb[i], &wav[i]));
         WP_TRY(wp_malloc(P, &stage[i].p, sizeof(float) * (size_t)nt * nrec[i], "trace staging"));
         WP_TRY(wp_malloc(P, &tr[i].p, sizeof(float) * (size_t)nt * nrec[i], "traces"));
-        WP_TRY(zero_fields(P, P->st, 4));
+        WP_TRY(zero_fields(P, P->st, nfields(P)));
     }
     DevBuf tbuf;
     WP_TRY(wp_malloc(P0, &tbuf.p, sizeof(int), "time index"));
     int *tdev = (int *)tbuf.p;
     WP_CK(P0, cudaMemsetAsync(tdev, 0, sizeof(int), st));
-    // the two buffer arrangements of a step: (p, r, p_prev, r_prev) and the rotated one
+    // TTI: the two buffer arrangements of a step, (p, r, p_prev, r_prev) and
+    // the rotated one; elastic: one (the state is updated in place)
     std::unique_ptr<TtiBatch, void (*)(TtiBatch *)> tb(tti_batch_new(), tti_batch_free);
-    for (int c = 0; c < 2; c++) {
-        std::vector<TtiBatchReq> req(n);
-        for (int i = 0; i < n; i++) {
-            float *const *q = shots[i]->st;
-            req[i] = c == 0 ? TtiBatchReq{shots[i], {q[0], q[1], q[2], q[3]}, false, nullptr, nullptr, nullptr}
-                            : TtiBatchReq{shots[i], {q[2], q[3], q[0], q[1]}, false, nullptr, nullptr, nullptr};
-        }
+    for (int c = 0; c < (el ? 1 : 2); c++) {
         std::string err;
-        const int rc = tti_batch_fix(tb.get(), req.data(), n, c, st, &err);
+        int rc;
+        if (el) {
+            std::vector<ElBatchReq> req(n);
+            for (int i = 0; i < n; i++) {
+                req[i] = ElBatchReq{shots[i], {}, 0, 1.f, {}, {}, {}};
+                for (int k = 0; k < 9; k++) req[i].S[k] = shots[i]->st[k];
+            }
+            rc = el_batch_fix(tb.get(), req.data(), n, 0, st, &err);
+        } else {
+            std::vector<TtiBatchReq> req(n);
+            for (int i = 0; i < n; i++) {
+                float *const *q = shots[i]->st;
+                req[i] = c == 0 ? TtiBatchReq{shots[i], {q[0], q[1], q[2], q[3]}, false, nullptr, nullptr, nullptr}
+                                : TtiBatchReq{shots[i], {q[2], q[3], q[0], q[1]}, false, nullptr, nullptr, nullptr};
+            }
+            rc = tti_batch_fix(tb.get(), req.data(), n, c, st, &err);
+        }
         if (rc == 1) return forward_batch_one_by_one(shots, n, wavelet, src_xyz, nsrc, rec_xyz, nrec, traces);
         if (rc) return wp_fail(P0, rc, err);
     }
     // one step in arrangement c: record d^n from u^n, advance every shot,
-    // inject q^n into the new level, t += 1
+    // inject q^n into the new level, t += 1 (elastic: receivers record the
+    // trace of the stress, the source enters tau_xx, tau_yy, tau_zz)
     auto step = [&](int c) -> int {
         for (int i = 0; i < n; i++) {
             prop_s *P = shots[i];
             float *const *q = P->st;
-            sp_record(P, &G[i].R, c == 0 ? q[0] : q[2], nullptr, nullptr, 1.f, (float *)stage[i].p, tdev);
+            if (el) sp_record(P, &G[i].R, q[3], q[4], q[5], 1.f, (float *)stage[i].p, tdev);
+            else sp_record(P, &G[i].R, c == 0 ? q[0] : q[2], nullptr, nullptr, 1.f, (float *)stage[i].p, tdev);
         }
-        if (tti_batch_launch_fixed(tb.get(), c, st) != PROP_OK)
-            return wp_fail(P0, PROP_ECUDA, "batched TTI step launch failed");
+        if ((el ? el_batch_launch_fixed(tb.get(), 0, st) : tti_batch_launch_fixed(tb.get(), c, st)) != PROP_OK)
+            return wp_fail(P0, PROP_ECUDA, "batched step launch failed");
         for (int i = 0; i < n; i++) {
             prop_s *P = shots[i];
             float *const *q = P->st;
-            float *pn = c == 0 ? q[2] : q[0], *rn = c == 0 ? q[3] : q[1];
-            sp_inject(P, &G[i].S, wav[i], nt, 0, P->g.dt * P->g.dt, 1, pn, rn, nullptr, nullptr, nullptr, tdev);
+            if (el) {
+                sp_inject(P, &G[i].S, wav[i], nt, 0, P->g.dt, 0, q[3], q[4], q[5], nullptr, nullptr, tdev);
+            } else {
+                float *pn = c == 0 ? q[2] : q[0], *rn = c == 0 ? q[3] : q[1];
+                sp_inject(P, &G[i].S, wav[i], nt, 0, P->g.dt * P->g.dt, 1, pn, rn, nullptr, nullptr, nullptr,
+                          tdev);
+            }
             P->kern_launches += 1;      // the shared pass launches, counted once per shot
         }
         k_tick(P0, tdev, 1);
@@ -1957,10 +1987,10 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
         cudaGraphExecDestroy(ex);
     }
     for (; done < nt; done++) WP_TRY(step(done & 1));
-    // the final state in st[] order (odd nt leaves the rotated arrangement)
+    // the final state in st[] order (TTI: odd nt leaves the rotated arrangement)
     for (int i = 0; i < n; i++) {
         prop_s *P = shots[i];
-        if (nt & 1) {
+        if ((nt & 1) && !el) {
             std::swap(P->st[0], P->st[2]);
             std::swap(P->st[1], P->st[3]);
         }

@@ -1687,6 +1687,9 @@ struct TtiBatch {
     std::vector<int> fixed_mode;
     size_t fixed_cap = 0;
     int fixed_n = 0, fixed_M = 0;
+    // fixed tables of elastic forward steps (graph replay)
+    std::vector<ElShot *> elfixed;
+    size_t elfixed_cap = 0;
     FDW w{};
 };
 
@@ -1698,6 +1701,7 @@ void tti_batch_free(TtiBatch *b)
     cudaFree(b->dtiles);
     cudaFree(b->dshots);
     for (auto d : b->dfixed) cudaFree(d);
+    for (auto d : b->elfixed) cudaFree(d);
     cudaFree(b->del);
     for (int i = 0; i < TtiBatch::NSLOT; i++) {
         if (b->elcopied[i]) {
@@ -2123,6 +2127,89 @@ int el_batch_step(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t st, st
     case 8: return el_batch_launch<8>(b, req, n, st, err);
     }
     return 1;
+}
+
+// fixed table `slot` of an elastic forward step (mode 0, sign +1) of every
+// request, for launches that may be captured into a CUDA graph
+int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream_t st, std::string *err)
+{
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    if (n < 1 || slot < 0) return PROP_EINVAL;
+    const prop_s *P0 = req[0].P;
+    for (int i = 0; i < n; i++)
+        if (!el_batchable(req[i].P) || req[i].P->M != P0->M || req[i].mode != 0 || req[i].sign != 1.f) return 1;
+    std::vector<prop_s *> Ps(n);
+    for (int i = 0; i < n; i++) Ps[i] = req[i].P;
+    if (int rc = batch_tiles(b, Ps, st, err)) return rc;
+    if ((size_t)n > b->elfixed_cap) {
+        for (auto &d : b->elfixed) {
+            cudaFree(d);
+            d = nullptr;
+        }
+        b->elfixed_cap = n;
+    }
+    if ((size_t)slot >= b->elfixed.size()) b->elfixed.resize(slot + 1, nullptr);
+    if (!b->elfixed[slot])
+        if (int rc = ck(cudaMalloc(&b->elfixed[slot], b->elfixed_cap * sizeof(ElShot)), "batched elastic fixed table"))
+            return rc;
+    std::vector<ElShot> H(n);
+    for (int i = 0; i < n; i++) {
+        prop_s *P = req[i].P;
+        float *const *S = req[i].S;
+        ElShot &e = H[i];
+        e.g = P->g;
+        for (int k = 0; k < 9; k++) e.s.f[k] = S[k];
+        e.o = F5{};
+        bool ok = false;
+        switch (P->M) {
+        case 2: ok = vmaps<2>(P, S, S + 3, &e.vm) && tmaps<2>(P, S, S + 3, &e.tm); break;
+        case 4: ok = vmaps<4>(P, S, S + 3, &e.vm) && tmaps<4>(P, S, S + 3, &e.tm); break;
+        case 6: ok = vmaps<6>(P, S, S + 3, &e.vm) && tmaps<6>(P, S, S + 3, &e.tm); break;
+        case 8: ok = vmaps<8>(P, S, S + 3, &e.vm) && tmaps<8>(P, S, S + 3, &e.tm); break;
+        }
+        if (!ok) {
+            *err = "cuTensorMapEncodeTiled failed";
+            return PROP_ECUDA;
+        }
+        e.xc = P->xchunk;
+        e.flag = P->flag;
+    }
+    if (int rc = ck(cudaMemcpy(b->elfixed[slot], H.data(), n * sizeof(ElShot), cudaMemcpyHostToDevice),
+                    "batched elastic fixed table copy"))
+        return rc;
+    b->fixed_M = P0->M;
+    b->w = P0->w;
+    return PROP_OK;
+}
+
+template <int M>
+static int el_batch_run_fixed(TtiBatch *b, int slot, cudaStream_t st)
+{
+    const size_t sv = NSTAGE * VL<M>::SZ * sizeof(float) + 64, stt = NSTAGE * TL<M, 0>::SZ * sizeof(float) + 64;
+    static const bool attr = set_smem(el_vpass_batch<M, 0>, sv) && set_smem(el_tpass_batch<M, 0>, stt);
+    (void)attr;
+    const unsigned nt = (unsigned)b->htiles.size();
+    const dim3 blk(TZ2, FY + 2, 1);
+    el_vpass_batch<M, 0><<<nt, blk, sv, st>>>(b->elfixed[slot], b->dtiles, b->w);
+    el_tpass_batch<M, 0><<<nt, blk, stt, st>>>(b->elfixed[slot], b->dtiles, b->w);
+    return cudaGetLastError() == cudaSuccess ? PROP_OK : PROP_ECUDA;
+}
+
+// the forward step of every shot of elastic fixed table `slot` (capturable)
+int el_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t st)
+{
+    if (slot < 0 || (size_t)slot >= b->elfixed.size() || !b->elfixed[slot]) return PROP_EINVAL;
+    switch (b->fixed_M) {
+    case 2: return el_batch_run_fixed<2>(b, slot, st);
+    case 4: return el_batch_run_fixed<4>(b, slot, st);
+    case 6: return el_batch_run_fixed<6>(b, slot, st);
+    case 8: return el_batch_run_fixed<8>(b, slot, st);
+    }
+    return PROP_EINVAL;
 }
 
 // centred first derivatives D p, D r and the half-point products

@@ -304,3 +304,29 @@ def test_lockstep_gradient_batch_is_bitwise(wp, monkeypatch, snap, interval, gra
         for lock in ("1", "0"):
             np.testing.assert_array_equal(out[lock][0][i], ref[i][0], err_msg=f"shot {i} lockstep {lock}")
             assert out[lock][1][i] == ref[i][1], (i, lock)
+
+
+@pytest.mark.parametrize("nt", [50, 51])
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_forward_batch_elastic_equals_one_call_per_shot(wp, monkeypatch, nt, graphs):
+    """prop_forward_batch with elastic shots: one launch of the velocity and
+    of the stress pass per step over all shots (the state updated in place),
+    steps replayed from a CUDA graph; traces and final states bitwise those
+    of one prop_forward per shot, for even and odd nt and with the graph off."""
+    monkeypatch.setenv("WAVEPROP_GRAPHS", graphs)
+    sel = elastic_window_shots(nt=nt)
+    ref, st_ref = [], []
+    for p, _ in sel:
+        prop = wp.Propagator.from_problem(p)
+        ref.append(prop.forward(p.wavelet, p.src, p.rec))
+        st_ref.append(prop.get_state())
+        prop.close()
+    props = [wp.Propagator.from_problem(p) for p, _ in sel]
+    trs = wp.forward_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel], [p.rec for p, _ in sel])
+    for i, (t, r) in enumerate(zip(trs, ref)):
+        assert np.max(np.abs(r)) > 0
+        np.testing.assert_array_equal(t, r, err_msg=f"shot {i}")
+        for a, b in zip(props[i].get_state(), st_ref[i]):
+            np.testing.assert_array_equal(a, b)
+    for pr in props:
+        pr.close()
