@@ -2296,14 +2296,16 @@ static int gradient_lockstep(prop_t *const *shots, int n, const float *const *wa
     };
     const char *ge = getenv("WAVEPROP_GRAPHS");
     const bool graphs = !(ge && !strcmp(ge, "0"));
-    struct Graphs {
+    struct Graphs {             // destroyed only after the stream's work (error paths too)
+        cudaStream_t st;
         cudaGraphExec_t g[4] = {};
         ~Graphs()
         {
+            cudaStreamSynchronize(st);
             for (auto e : g)
                 if (e) cudaGraphExecDestroy(e);
         }
-    } gx;
+    } gx{st};
     // run body() directly, or from graph `id` (captured on first use)
     auto run = [&](int id, const std::function<int()> &body) -> int {
         if (!graphs) return body();
