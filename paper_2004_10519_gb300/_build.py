@@ -31,7 +31,8 @@ def _newest(paths):
     return max((os.path.getmtime(p) for p in paths), default=0.0)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=(), check: bool = False) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), check: bool = False,
+          workers: int = 0) -> str:
     """Compile every csrc/*.cu and link the library.  check=True builds the
     bounds-checking variant (-DWP_CHECK) into libwaveprop_check.so."""
     lib_path, build_dir = (LIB_CHECK, BUILD_CHECK) if check else (LIB, BUILD)
@@ -57,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), check: boo
             print(r.stdout, r.stderr, flush=True)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=workers or min(8, os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = lib_path + f".tmp{os.getpid()}"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared"]
@@ -66,6 +67,15 @@ def build(force: bool = False, verbose: bool = False, extra_flags=(), check: boo
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, lib_path)
     return lib_path
+
+
+def build_all(force: bool = False) -> None:
+    """The library and its bounds-checking variant, compiled side by side."""
+    w = max(2, (os.cpu_count() or 4) // 2)
+    with cf.ThreadPoolExecutor(max_workers=2) as ex:
+        jobs = [ex.submit(build, force, False, (), c, w) for c in (False, True)]
+        for j in jobs:
+            j.result()
 
 
 if __name__ == "__main__":
