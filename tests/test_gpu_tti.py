@@ -353,3 +353,19 @@ def test_checkpoint_tail_is_bitwise(wp, monkeypatch, kind):
         prop.close()
         np.testing.assert_array_equal(g, ref, err_msg=cap)
         assert J == J_ref
+
+
+def test_industry_recipe_at_reduced_size(wp):
+    """The industry-scale TTI workload's recipe (layered-plus-noise model
+    with eps, delta, tilt and azimuth derived from it, so 12, 12.5 m, 40-cell
+    layer, 12 Hz source 25 m deep, surface carpet of receivers every 40 m) at
+    200 x 200 x 100 physical points (280 x 280 x 180 computational), 150
+    steps: traces against the FP64 oracle's whole run."""
+    p = synth.tti_layered(nx=200, ny=200, nz=100, nt=150)
+    assert p.rec.shape[0] > 1000
+    prop = wp.Propagator.from_problem(p)
+    tr = prop.forward(p.wavelet, p.src, p.rec)
+    prop.close()
+    ref = oracle.Problem(p).forward()
+    assert np.max(np.abs(ref)) > 0
+    assert rel(tr, ref) <= TOL, rel(tr, ref)
