@@ -234,7 +234,8 @@ int prop_forward_batch(prop_t *const *shots, int nshots, const float *const *wav
  * share their step launches: the k-th step of every such shot runs as one
  * launch of each pass over a table of all the shots' tiles (set
  * WAVEPROP_BATCH_LAUNCH=0 to launch shot by shot).  A wave whose shots are
- * all such TTI shots with checkpoints (FP32, BF16 or FP16), one space
+ * all such TTI shots, or all elastic shots on the TMA-fed passes, with
+ * checkpoints (FP32, BF16 or FP16), one space
  * order, nt and checkpoint interval, on windows of at most 16 M
  * computational points on average, runs in lockstep from the calling
  * thread: per step one launch of each pass for every shot, and each full

@@ -229,8 +229,10 @@ struct ElBatchReq {
 bool el_batchable(const prop_s *P);
 // 0 launched; 1 not batchable together (launch one by one); < 0 error
 int el_batch_step(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t stream, std::string *err);
-// fixed table `slot` of an elastic forward step of every request (mode 0,
-// sign +1; 1: not batchable), and launches of it that may be captured
+// fixed table `slot` of an elastic step of every request (mode 0 with sign
+// +1, or mode 1: the three passes of the transposed step with imaging,
+// without its pointwise kernels; 1: not batchable), and launches of it that
+// may be captured
 int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream_t stream, std::string *err);
 int el_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t stream);
 // per-shot pointwise kernels of the batched transposed elastic step (elastic.cu)

@@ -2056,9 +2056,11 @@ static bool lockstep_ok(prop_t *const *sh, int n)
 {
     if (n < 2) return false;
     const prop_s *P0 = sh[0];
+    const bool el = el_batchable(P0);
     for (int i = 0; i < n; i++) {
         const prop_s *P = sh[i];
-        if (!tti_batchable(P) || P->broken || P->aniso || P->M != P0->M || P->d.nt != P0->d.nt ||
+        if (!(el ? el_batchable(P) : tti_batchable(P)) || P->broken || P->aniso || P->M != P0->M ||
+            P->d.nt != P0->d.nt ||
             P->d.snap_mode == SNAP_FULL_FP32 || P->d.snap_mode != P0->d.snap_mode ||
             P->d.ckpt_interval != P0->d.ckpt_interval)
             return false;
@@ -2400,6 +2402,318 @@ static int gradient_lockstep(prop_t *const *shots, int n, const float *const *wa
     return first;
 }
 
+// ---------------------------------------------------------------------------
+// Gradients of a wave of elastic shots in lockstep (same space order, nt and
+// checkpoint schedule, TMA-fed passes, checkpointed storage): as for TTI,
+// one host thread; the state and the adjoint state are updated in place, so
+// one fixed table serves every forward step and one per segment position
+// the transposed step with imaging (its three passes; the pointwise kernels
+// before and after it run per shot).  Full segments (K recomputed steps and
+// K transposed steps) are captured once as a CUDA graph and replayed.
+// Each shot's operations are those of its own prop_gradient, in the same
+// order, so the results are the same bits.  Returns 1 (nothing done) if the
+// wave does not qualify.
+// ---------------------------------------------------------------------------
+static int el_gradient_lockstep(prop_t *const *shots, int n, const float *const *wavelet,
+                                const float *const *src_xyz, const int *nsrc, const float *const *rec_xyz,
+                                const int *nrec, const float *const *d_obs, float *const *grad, double *mis)
+{
+    prop_s *P0 = shots[0];
+    const int nt = P0->d.nt;
+    struct OwnStream {
+        cudaStream_t s = nullptr;
+        ~OwnStream()
+        {
+            if (s) {
+                cudaStreamSynchronize(s);
+                cudaStreamDestroy(s);
+            }
+        }
+    } bs;
+    WP_CK(P0, cudaStreamCreateWithFlags(&bs.s, cudaStreamNonBlocking));
+    const cudaStream_t st = bs.s;
+    std::vector<cudaStream_t> own(n);
+    struct Restore {
+        prop_t *const *sh;
+        std::vector<cudaStream_t> *own;
+        int n;
+        ~Restore()
+        {
+            for (int i = 0; i < n; i++) {
+                sh[i]->stream = (*own)[i];
+                free_snaps(sh[i]);
+            }
+        }
+    } restore{shots, &own, 0};
+    for (int i = 0; i < n; i++)
+        if (!d_obs[i] || !grad[i] || !wavelet[i] || !src_xyz[i] || !rec_xyz[i] || nsrc[i] < 1 || nrec[i] < 1)
+            return 1;
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        if (check_handle(P) != PROP_OK) return 1;
+        own[i] = P->stream;
+        cudaEvent_t e;
+        WP_CK(P, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaEventRecord(e, P->stream);
+        cudaStreamWaitEvent(st, e, 0);
+        cudaEventDestroy(e);
+        P->stream = st;
+        restore.n = i + 1;
+        if (ensure_work(P) != PROP_OK || ensure_ast(P) != PROP_OK || ensure_tmp(P, 15) != PROP_OK) return 1;
+    }
+    std::vector<Geometry> G(n);
+    std::vector<DevBuf> wb(n), ob(n), stage(n), tr(n), gb(n), gp(n);
+    std::vector<const float *> wav(n), obs(n);
+    auto setup = [&](int i) -> int {
+        prop_s *P = shots[i];
+        const size_t N = (size_t)P->g.N, np = (size_t)P->g.px * P->g.py * P->g.pz;
+        WP_TRY(build_geometry(P, G[i], src_xyz[i], nsrc[i], rec_xyz[i], nrec[i]));
+        WP_TRY(dev_in(P, wavelet[i], (size_t)nsrc[i] * nt, wb[i], &wav[i]));
+        WP_TRY(dev_in(P, d_obs[i], (size_t)nrec[i] * nt, ob[i], &obs[i]));
+        WP_TRY(wp_malloc(P, &stage[i].p, sizeof(float) * (size_t)nt * nrec[i], "trace staging"));
+        WP_TRY(wp_malloc(P, &tr[i].p, sizeof(float) * (size_t)nt * nrec[i], "traces"));
+        WP_TRY(wp_malloc(P, &gb[i].p, sizeof(float) * N * 3, "gradient"));
+        WP_TRY(wp_malloc(P, &gp[i].p, sizeof(float) * np * 3, "gradient (physical)"));
+        WP_CK(P, cudaMemsetAsync(gb[i].p, 0, sizeof(float) * N * 3, st));
+        WP_TRY(alloc_saves(P));
+        WP_TRY(zero_fields(P, P->st, 9));
+        WP_TRY(zero_fields(P, P->ast, 9));
+        WP_TRY(zero_fields(P, P->tmp + 9, 6));     // edge and face product sums
+        return PROP_OK;
+    };
+    for (int i = 0; i < n; i++)
+        if (setup(i) != PROP_OK) {
+            cudaStreamSynchronize(st);
+            return 1;
+        }
+    const int K = ckpt_K(P0), J = ckpt_J(P0), span = ckpt_span(P0);
+    if (span != nt - 1) return 1;
+    for (int i = 1; i < n; i++)
+        if (ckpt_K(shots[i]) != K || ckpt_J(shots[i]) != J || ckpt_span(shots[i]) != span) return 1;
+    const int sf = (int)snap_fields(P0);
+    DevBuf tbuf;
+    WP_TRY(wp_malloc(P0, &tbuf.p, sizeof(int), "time index"));
+    int *tdev = (int *)tbuf.p;
+    auto g3 = [&](int i, int c) { return (float *)gb[i].p + (size_t)c * shots[i]->g.N; };
+    auto xs = [&](int i, int slot, const float **out) {
+        prop_s *P = shots[i];
+        for (int f = 0; f < 9; f++) out[f] = f < sf ? seg_slot(P, slot) + (size_t)f * P->g.N : nullptr;
+    };
+    // fixed tables: slot 0 the forward step; slot 1 + p the transposed step
+    // with imaging at segment position p (forward levels p and p + 1)
+    std::unique_ptr<TtiBatch, void (*)(TtiBatch *)> tb(tti_batch_new(), tti_batch_free);
+    std::vector<ElBatchReq> req(n);
+    std::string err;
+    for (int i = 0; i < n; i++) {
+        req[i] = ElBatchReq{shots[i], {}, 0, 1.f, {}, {}, {}};
+        for (int k = 0; k < 9; k++) req[i].S[k] = shots[i]->st[k];
+    }
+    if (int rc = el_batch_fix(tb.get(), req.data(), n, 0, st, &err)) return rc == 1 ? 1 : wp_fail(P0, rc, err);
+    for (int pos = 0; pos < K; pos++) {
+        for (int i = 0; i < n; i++) {
+            req[i] = ElBatchReq{shots[i], {}, 1, 1.f, {}, {}, {g3(i, 0), g3(i, 1), g3(i, 2)}};
+            for (int k = 0; k < 9; k++) req[i].S[k] = shots[i]->ast[k];
+            xs(i, pos, req[i].xk);
+            xs(i, pos + 1, req[i].xk1);
+        }
+        if (int rc = el_batch_fix(tb.get(), req.data(), n, 1 + pos, st, &err))
+            return rc == 1 ? 1 : wp_fail(P0, rc, err);
+    }
+    auto launch = [&](int slot) -> int {
+        if (el_batch_launch_fixed(tb.get(), slot, st) != PROP_OK)
+            return wp_fail(P0, PROP_ECUDA, "batched elastic step launch failed");
+        for (int i = 0; i < n; i++) shots[i]->kern_launches += 1;
+        batch_stats[0]++;
+        return PROP_OK;
+    };
+    constexpr int W = 8;
+    struct Workers {
+        cudaStream_t s[W] = {};
+        cudaEvent_t fork = nullptr, join[W] = {};
+        ~Workers()
+        {
+            for (auto x : s)
+                if (x) cudaStreamDestroy(x);
+            if (fork) cudaEventDestroy(fork);
+            for (auto e : join)
+                if (e) cudaEventDestroy(e);
+        }
+    } wk;
+    const int nwk = std::min(W, n);
+    WP_CK(P0, cudaEventCreateWithFlags(&wk.fork, cudaEventDisableTiming));
+    for (int w = 0; w < nwk; w++) {
+        WP_CK(P0, cudaStreamCreateWithFlags(&wk.s[w], cudaStreamNonBlocking));
+        WP_CK(P0, cudaEventCreateWithFlags(&wk.join[w], cudaEventDisableTiming));
+    }
+    auto per_shot = [&](const std::function<int(int)> &fn) -> int {
+        WP_CK(P0, cudaEventRecord(wk.fork, st));
+        for (int w = 0; w < nwk; w++) WP_CK(P0, cudaStreamWaitEvent(wk.s[w], wk.fork, 0));
+        int rc = PROP_OK;
+        for (int i = 0; i < n && !rc; i++) {
+            shots[i]->stream = wk.s[i % nwk];
+            rc = fn(i);
+            shots[i]->stream = st;
+        }
+        for (int w = 0; w < nwk; w++) {
+            WP_CK(P0, cudaEventRecord(wk.join[w], wk.s[w]));
+            WP_CK(P0, cudaStreamWaitEvent(st, wk.join[w], 0));
+        }
+        return rc;
+    };
+    // forward step: record d^t (trace of the stress), step, inject q^t into
+    // the normal stresses (and, recomputing, keep the velocities in segment
+    // buffer pos + 1), t += 1
+    auto fwd = [&](bool record, int pos) -> int {
+        if (record)
+            WP_TRY(per_shot([&](int i) -> int {
+                float *const *q = shots[i]->st;
+                sp_record(shots[i], &G[i].R, q[3], q[4], q[5], 1.f, (float *)stage[i].p, tdev);
+                return PROP_OK;
+            }));
+        WP_TRY(launch(0));
+        WP_TRY(per_shot([&](int i) -> int {
+            prop_s *P = shots[i];
+            float *const *q = P->st;
+            sp_inject(P, &G[i].S, wav[i], nt, 0, P->g.dt, 0, q[3], q[4], q[5], nullptr, nullptr, tdev);
+            if (pos >= 0)
+                for (int f = 0; f < sf; f++)
+                    WP_CK(P, cudaMemcpyAsync(seg_slot(P, pos + 1) + (size_t)f * P->g.N, q[f], P->g.N * 4,
+                                             cudaMemcpyDeviceToDevice, P->stream));
+            return PROP_OK;
+        }));
+        k_tick(P0, tdev, 1);
+        return PROP_OK;
+    };
+    // transposed step k = t - 1 with imaging at position pos: t -= 1, the
+    // pointwise kernel before, the three passes, the face products, the
+    // residual r^k
+    auto adj = [&](int pos) -> int {
+        k_tick(P0, tdev, -1);
+        WP_TRY(per_shot([&](int i) -> int {
+            el_adj_pre_launch(shots[i], shots[i]->ast, shots[i]->stream);
+            return PROP_OK;
+        }));
+        WP_TRY(launch(1 + pos));
+        WP_TRY(per_shot([&](int i) -> int {
+            prop_s *P = shots[i];
+            const float *x0[9], *x1[9];
+            xs(i, pos, x0);
+            xs(i, pos + 1, x1);
+            el_face2_launch(P, P->ast, x0, x1, P->stream);
+            float *const *a = P->ast;
+            sp_inject(P, &G[i].R, (const float *)tr[i].p, nt, 0, 1.f, 0, a[3], a[4], a[5], nullptr, nullptr, tdev);
+            return PROP_OK;
+        }));
+        return PROP_OK;
+    };
+    const char *ge = getenv("WAVEPROP_GRAPHS");
+    const bool graphs = !(ge && !strcmp(ge, "0"));
+    struct Graphs {
+        cudaStream_t st;
+        cudaGraphExec_t g[2] = {};
+        ~Graphs()
+        {
+            cudaStreamSynchronize(st);
+            for (auto e : g)
+                if (e) cudaGraphExecDestroy(e);
+        }
+    } gx{st};
+    auto run = [&](int id, const std::function<int()> &body) -> int {
+        if (!graphs) return body();
+        if (!gx.g[id]) {
+            cudaGraph_t gr = nullptr;
+            WP_CK(P0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int rb = body();
+            const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+            if (rb || ec != cudaSuccess) {
+                if (gr) cudaGraphDestroy(gr);
+                cudaGetLastError();
+                return rb ? rb : wp_cuda(P0, ec, "capture of the lockstep segment");
+            }
+            const cudaError_t ei = cudaGraphInstantiate(&gx.g[id], gr, 0);
+            cudaGraphDestroy(gr);
+            WP_CK(P0, ei);
+        }
+        WP_CK(P0, cudaGraphLaunch(gx.g[id], st));
+        return PROP_OK;
+    };
+    // ---- forward sweep with checkpoints ----
+    k_set_int(P0, tdev, 0);
+    for (int j = 0; j < J; j++) {
+        const int n0 = j * K, n1 = j + 1 < J ? n0 + K : nt;
+        WP_TRY(per_shot([&](int i) -> int { return save_checkpoint(shots[i], j, shots[i]->st); }));
+        auto body = [&]() -> int {
+            for (int t = n0; t < n1; t++) WP_TRY(fwd(true, -1));
+            return PROP_OK;
+        };
+        if (n1 - n0 == K) WP_TRY(run(0, body));
+        else WP_TRY(body());
+    }
+    // ---- residuals and misfits ----
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        const long long m = (long long)nrec[i] * nt;
+        sp_transpose(P, (const float *)stage[i].p, (float *)tr[i].p, nrec[i], nt);
+        k_axpy_sq(P, (const float *)tr[i].p, obs[i], (float *)tr[i].p, m);
+        double ss = 0.0;
+        WP_TRY(k_sumsq(P, (const float *)tr[i].p, m, &ss));
+        mis[i] = 0.5 * ss;
+    }
+    // ---- adjoint sweep: k = nt - 1 (a transposed step of the zero state and
+    // the last residual sample), then the segments, last first ----
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        float *const *a = P->ast;
+        WP_TRY(el_launch_step(P, P->ast, true));
+        sp_inject(P, &G[i].R, (const float *)tr[i].p, nt, nt - 1, 1.f, 0, a[3], a[4], a[5], nullptr, nullptr);
+    }
+    for (int j = J - 1; j >= 0; j--) {
+        const int n0 = j * K, E = std::min(n0 + K, nt - 1), len = E - n0;
+        WP_TRY(per_shot([&](int i) -> int {
+            prop_s *P = shots[i];
+            WP_TRY(load_checkpoint(P, j, P->st));
+            for (int f = 0; f < sf; f++)
+                WP_CK(P, cudaMemcpyAsync(seg_slot(P, 0) + (size_t)f * P->g.N, P->st[f], P->g.N * 4,
+                                         cudaMemcpyDeviceToDevice, P->stream));
+            return PROP_OK;
+        }));
+        k_set_int(P0, tdev, n0);
+        auto body = [&]() -> int {
+            for (int pos = 0; pos < len; pos++) WP_TRY(fwd(false, pos));
+            for (int k = E - 1; k >= n0; k--) WP_TRY(adj(k - n0));
+            return PROP_OK;
+        };
+        if (len == K) WP_TRY(run(1, body));
+        else WP_TRY(body());
+    }
+    // ---- gradients on the physical grid ----
+    for (int i = 0; i < n; i++) {
+        prop_s *P = shots[i];
+        const size_t np = (size_t)P->g.px * P->g.py * P->g.pz;
+        float *gg[3] = {g3(i, 0), g3(i, 1), g3(i, 2)};
+        WP_TRY(el_grad_gather(P, gg));
+        for (int c = 0; c < 3; c++) k_fold(P, gg[c], (float *)gp[i].p + c * np, P->tmp[0], P->tmp[1]);
+        WP_TRY(copy_out(P, grad[i], (const float *)gp[i].p, np * 3));
+    }
+    int first = PROP_OK;
+    for (int i = 0; i < n; i++) {
+        const int rc = finish(shots[i]);
+        if (rc && !first) {
+            first = rc;
+            tl_err = "shot " + std::to_string(i) + ": " + prop_last_error(shots[i]);
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+            cudaEventRecord(e, st);
+            cudaStreamWaitEvent(own[i], e, 0);
+            cudaEventDestroy(e);
+        }
+    }
+    return first;
+}
+
 extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float *const *wavelet,
                                    const float *const *src_xyz, const int *nsrc,
                                    const float *const *rec_xyz, const int *nrec,
@@ -2466,8 +2780,8 @@ extern "C" int prop_gradient_batch(prop_t *const *shots, int nshots, const float
                 wv[k] = wavelet[i]; sx[k] = src_xyz[i]; rx[k] = rec_xyz[i]; dob[k] = d_obs[i];
                 gr[k] = grad[i]; ns[k] = nsrc[i]; nr[k] = nrec[i];
             }
-            const int lr = gradient_lockstep(ws.data(), m, wv.data(), sx.data(), ns.data(), rx.data(), nr.data(),
-                                             dob.data(), gr.data(), ms.data());
+            const int lr = (el_batchable(ws[0]) ? el_gradient_lockstep : gradient_lockstep)(
+                ws.data(), m, wv.data(), sx.data(), ns.data(), rx.data(), nr.data(), dob.data(), gr.data(), ms.data());
             if (lr != 1) {
                 for (int k = 0; k < m; k++) {
                     const int i = ids[k];

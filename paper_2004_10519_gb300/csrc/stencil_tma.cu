@@ -1687,8 +1687,10 @@ struct TtiBatch {
     std::vector<int> fixed_mode;
     size_t fixed_cap = 0;
     int fixed_n = 0, fixed_M = 0;
-    // fixed tables of elastic forward steps (graph replay)
+    // fixed tables of elastic steps (graph replay): per slot n entries (a
+    // forward step) or 3n (a transposed step with imaging)
     std::vector<ElShot *> elfixed;
+    std::vector<int> elfixed_mode;
     size_t elfixed_cap = 0;
     FDW w{};
 };
@@ -1998,42 +2000,14 @@ int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, 
 
 bool el_batchable(const prop_s *P) { return P->d.kind == PROP_ELASTIC && tma_usable(P); }
 
+// per-shot entries of one elastic step of every request: mode 0 one table
+// H[0..n); mode 1 the three tables of the transposed step with imaging,
+// H[0..n) velocity (adjoint), H[n..2n) stress (imaging), H[2n..3n) stress
+// (adjoint)
 template <int M>
-static int el_batch_launch(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t st, std::string *err)
+static int el_fill(const ElBatchReq *req, int n, ElShot *H, std::string *err)
 {
-    auto ck = [&](cudaError_t c, const char *what) {
-        if (c == cudaSuccess) return PROP_OK;
-        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
-        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
-    };
-    const int mode = req[0].mode, per = mode == 0 ? 1 : 3;
-    const size_t bytes = (size_t)n * per * sizeof(ElShot);
-    if (bytes > b->del_cap) {
-        cudaFree(b->del);
-        b->del = nullptr;
-        b->del_cap = 0;
-        if (int rc = ck(cudaMalloc(&b->del, bytes), "batched elastic shot table")) return rc;
-        b->del_cap = bytes;
-    }
-    if (bytes > b->hel_cap) {
-        for (int i = 0; i < TtiBatch::NSLOT; i++) {
-            if (b->elcopied[i]) cudaEventSynchronize(b->elcopied[i]);
-            cudaFreeHost(b->hel[i]);
-            b->hel[i] = nullptr;
-        }
-        b->hel_cap = 0;
-        for (int i = 0; i < TtiBatch::NSLOT; i++) {
-            if (int rc = ck(cudaMallocHost(&b->hel[i], bytes), "batched elastic staging")) return rc;
-            if (!b->elcopied[i])
-                if (int rc = ck(cudaEventCreateWithFlags(&b->elcopied[i], cudaEventDisableTiming),
-                                "batched elastic staging event"))
-                    return rc;
-        }
-        b->hel_cap = bytes;
-    }
-    const int slot = (int)(b->calls++ % TtiBatch::NSLOT);
-    if (int rc = ck(cudaEventSynchronize(b->elcopied[slot]), "batched elastic staging wait")) return rc;
-    ElShot *H = reinterpret_cast<ElShot *>(b->hel[slot]);
+    const int mode = req[0].mode;
     for (int i = 0; i < n; i++) {
         prop_s *P = req[i].P;
         float *const *S = req[i].S;
@@ -2079,6 +2053,46 @@ static int el_batch_launch(TtiBatch *b, const ElBatchReq *req, int n, cudaStream
             return PROP_ECUDA;
         }
     }
+    return PROP_OK;
+}
+
+template <int M>
+static int el_batch_launch(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t st, std::string *err)
+{
+    auto ck = [&](cudaError_t c, const char *what) {
+        if (c == cudaSuccess) return PROP_OK;
+        *err = std::string("CUDA error '") + cudaGetErrorString(c) + "' in " + what;
+        return c == cudaErrorMemoryAllocation ? PROP_ENOMEM : PROP_ECUDA;
+    };
+    const int mode = req[0].mode, per = mode == 0 ? 1 : 3;
+    const size_t bytes = (size_t)n * per * sizeof(ElShot);
+    if (bytes > b->del_cap) {
+        cudaFree(b->del);
+        b->del = nullptr;
+        b->del_cap = 0;
+        if (int rc = ck(cudaMalloc(&b->del, bytes), "batched elastic shot table")) return rc;
+        b->del_cap = bytes;
+    }
+    if (bytes > b->hel_cap) {
+        for (int i = 0; i < TtiBatch::NSLOT; i++) {
+            if (b->elcopied[i]) cudaEventSynchronize(b->elcopied[i]);
+            cudaFreeHost(b->hel[i]);
+            b->hel[i] = nullptr;
+        }
+        b->hel_cap = 0;
+        for (int i = 0; i < TtiBatch::NSLOT; i++) {
+            if (int rc = ck(cudaMallocHost(&b->hel[i], bytes), "batched elastic staging")) return rc;
+            if (!b->elcopied[i])
+                if (int rc = ck(cudaEventCreateWithFlags(&b->elcopied[i], cudaEventDisableTiming),
+                                "batched elastic staging event"))
+                    return rc;
+        }
+        b->hel_cap = bytes;
+    }
+    const int slot = (int)(b->calls++ % TtiBatch::NSLOT);
+    if (int rc = ck(cudaEventSynchronize(b->elcopied[slot]), "batched elastic staging wait")) return rc;
+    ElShot *H = reinterpret_cast<ElShot *>(b->hel[slot]);
+    if (int rc = el_fill<M>(req, n, H, err)) return rc;
     if (int rc = ck(cudaMemcpyAsync(b->del, H, bytes, cudaMemcpyHostToDevice, st), "batched elastic table copy"))
         return rc;
     if (int rc = ck(cudaEventRecord(b->elcopied[slot], st), "batched elastic event")) return rc;
@@ -2129,8 +2143,9 @@ int el_batch_step(TtiBatch *b, const ElBatchReq *req, int n, cudaStream_t st, st
     return 1;
 }
 
-// fixed table `slot` of an elastic forward step (mode 0, sign +1) of every
-// request, for launches that may be captured into a CUDA graph
+// fixed table `slot` of an elastic step of every request (mode 0 with sign
+// +1: a forward step; mode 1: the transposed step with imaging, three
+// tables), for launches that may be captured into a CUDA graph
 int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream_t st, std::string *err)
 {
     auto ck = [&](cudaError_t c, const char *what) {
@@ -2140,47 +2155,42 @@ int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream
     };
     if (n < 1 || slot < 0) return PROP_EINVAL;
     const prop_s *P0 = req[0].P;
+    const int mode = req[0].mode;
     for (int i = 0; i < n; i++)
-        if (!el_batchable(req[i].P) || req[i].P->M != P0->M || req[i].mode != 0 || req[i].sign != 1.f) return 1;
+        if (!el_batchable(req[i].P) || req[i].P->M != P0->M || req[i].mode != mode || (mode == 0 && req[i].sign != 1.f))
+            return 1;
     std::vector<prop_s *> Ps(n);
     for (int i = 0; i < n; i++) Ps[i] = req[i].P;
     if (int rc = batch_tiles(b, Ps, st, err)) return rc;
-    if ((size_t)n > b->elfixed_cap) {
+    if ((size_t)n > b->elfixed_cap) {             // every slot holds 3n entries
         for (auto &d : b->elfixed) {
             cudaFree(d);
             d = nullptr;
         }
         b->elfixed_cap = n;
     }
-    if ((size_t)slot >= b->elfixed.size()) b->elfixed.resize(slot + 1, nullptr);
-    if (!b->elfixed[slot])
-        if (int rc = ck(cudaMalloc(&b->elfixed[slot], b->elfixed_cap * sizeof(ElShot)), "batched elastic fixed table"))
-            return rc;
-    std::vector<ElShot> H(n);
-    for (int i = 0; i < n; i++) {
-        prop_s *P = req[i].P;
-        float *const *S = req[i].S;
-        ElShot &e = H[i];
-        e.g = P->g;
-        for (int k = 0; k < 9; k++) e.s.f[k] = S[k];
-        e.o = F5{};
-        bool ok = false;
-        switch (P->M) {
-        case 2: ok = vmaps<2>(P, S, S + 3, &e.vm) && tmaps<2>(P, S, S + 3, &e.tm); break;
-        case 4: ok = vmaps<4>(P, S, S + 3, &e.vm) && tmaps<4>(P, S, S + 3, &e.tm); break;
-        case 6: ok = vmaps<6>(P, S, S + 3, &e.vm) && tmaps<6>(P, S, S + 3, &e.tm); break;
-        case 8: ok = vmaps<8>(P, S, S + 3, &e.vm) && tmaps<8>(P, S, S + 3, &e.tm); break;
-        }
-        if (!ok) {
-            *err = "cuTensorMapEncodeTiled failed";
-            return PROP_ECUDA;
-        }
-        e.xc = P->xchunk;
-        e.flag = P->flag;
+    if ((size_t)slot >= b->elfixed.size()) {
+        b->elfixed.resize(slot + 1, nullptr);
+        b->elfixed_mode.resize(slot + 1, -1);
     }
-    if (int rc = ck(cudaMemcpy(b->elfixed[slot], H.data(), n * sizeof(ElShot), cudaMemcpyHostToDevice),
+    if (!b->elfixed[slot])
+        if (int rc = ck(cudaMalloc(&b->elfixed[slot], 3 * b->elfixed_cap * sizeof(ElShot)),
+                        "batched elastic fixed table"))
+            return rc;
+    std::vector<ElShot> H((mode == 0 ? 1 : 3) * n);
+    int rc = 1;
+    switch (P0->M) {
+    case 2: rc = el_fill<2>(req, n, H.data(), err); break;
+    case 4: rc = el_fill<4>(req, n, H.data(), err); break;
+    case 6: rc = el_fill<6>(req, n, H.data(), err); break;
+    case 8: rc = el_fill<8>(req, n, H.data(), err); break;
+    }
+    if (rc) return rc;
+    if (int r2 = ck(cudaMemcpy(b->elfixed[slot], H.data(), H.size() * sizeof(ElShot), cudaMemcpyHostToDevice),
                     "batched elastic fixed table copy"))
-        return rc;
+        return r2;
+    b->elfixed_mode[slot] = mode;
+    b->fixed_n = n;
     b->fixed_M = P0->M;
     b->w = P0->w;
     return PROP_OK;
@@ -2189,17 +2199,32 @@ int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream
 template <int M>
 static int el_batch_run_fixed(TtiBatch *b, int slot, cudaStream_t st)
 {
-    const size_t sv = NSTAGE * VL<M>::SZ * sizeof(float) + 64, stt = NSTAGE * TL<M, 0>::SZ * sizeof(float) + 64;
-    static const bool attr = set_smem(el_vpass_batch<M, 0>, sv) && set_smem(el_tpass_batch<M, 0>, stt);
-    (void)attr;
     const unsigned nt = (unsigned)b->htiles.size();
     const dim3 blk(TZ2, FY + 2, 1);
-    el_vpass_batch<M, 0><<<nt, blk, sv, st>>>(b->elfixed[slot], b->dtiles, b->w);
-    el_tpass_batch<M, 0><<<nt, blk, stt, st>>>(b->elfixed[slot], b->dtiles, b->w);
+    const ElShot *D = b->elfixed[slot];
+    const int n = b->fixed_n;
+    if (b->elfixed_mode[slot] == 0) {
+        const size_t sv = NSTAGE * VL<M>::SZ * sizeof(float) + 64, stt = NSTAGE * TL<M, 0>::SZ * sizeof(float) + 64;
+        static const bool attr = set_smem(el_vpass_batch<M, 0>, sv) && set_smem(el_tpass_batch<M, 0>, stt);
+        (void)attr;
+        el_vpass_batch<M, 0><<<nt, blk, sv, st>>>(D, b->dtiles, b->w);
+        el_tpass_batch<M, 0><<<nt, blk, stt, st>>>(D, b->dtiles, b->w);
+    } else {
+        // the three passes only: the pointwise kernels before and after are
+        // the caller's (per shot)
+        const size_t sv = NSTAGE * VL<M>::SZ * sizeof(float) + 64, s2 = NSTAGE * TL<M, 2>::SZ * sizeof(float) + 64,
+                     s1 = NSTAGE * TL<M, 1>::SZ * sizeof(float) + 64;
+        static const bool attr = set_smem(el_vpass_batch<M, 1>, sv) && set_smem(el_tpass_batch<M, 2>, s2) &&
+                                 set_smem(el_tpass_batch<M, 1>, s1);
+        (void)attr;
+        el_vpass_batch<M, 1><<<nt, blk, sv, st>>>(D, b->dtiles, b->w);
+        el_tpass_batch<M, 2><<<nt, blk, s2, st>>>(D + n, b->dtiles, b->w);
+        el_tpass_batch<M, 1><<<nt, blk, s1, st>>>(D + 2 * n, b->dtiles, b->w);
+    }
     return cudaGetLastError() == cudaSuccess ? PROP_OK : PROP_ECUDA;
 }
 
-// the forward step of every shot of elastic fixed table `slot` (capturable)
+// the step of every shot of elastic fixed table `slot` (capturable)
 int el_batch_launch_fixed(TtiBatch *b, int slot, cudaStream_t st)
 {
     if (slot < 0 || (size_t)slot >= b->elfixed.size() || !b->elfixed[slot]) return PROP_EINVAL;

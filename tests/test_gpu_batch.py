@@ -242,12 +242,14 @@ def elastic_window_shots(nt=50, h=10.0, nbl=4):
 
 
 @pytest.mark.parametrize("snap", [0, 1])
-def test_elastic_batch_shares_launches(wp, snap):
+def test_elastic_batch_shares_launches(wp, monkeypatch, snap):
     """Elastic shots of one wave share their steps' launches (forward steps:
     the velocity and stress passes over all shots; transposed steps with
     imaging: the three passes, with the pointwise kernels per shot); the
     gradients are bitwise those of one prop_gradient per shot, with full
-    storage and with FP32 checkpoints (recomputed forward steps)."""
+    storage and with FP32 checkpoints (recomputed forward steps), here with
+    one host thread per shot (WAVEPROP_LOCKSTEP=0)."""
+    monkeypatch.setenv("WAVEPROP_LOCKSTEP", "0")
     sel = elastic_window_shots()
     ref = []
     for p, d in sel:
@@ -330,3 +332,37 @@ def test_forward_batch_elastic_equals_one_call_per_shot(wp, monkeypatch, nt, gra
             np.testing.assert_array_equal(a, b)
     for pr in props:
         pr.close()
+
+
+@pytest.mark.parametrize("snap,interval", [(1, 7), (2, 6), (3, 5)], ids=["fp32ckpt-K7", "bf16-K6", "fp16-K5"])
+@pytest.mark.parametrize("graphs", ["1", "0"])
+def test_elastic_lockstep_gradient_batch_is_bitwise(wp, monkeypatch, snap, interval, graphs):
+    """A wave of elastic shots with checkpoints runs in lockstep from one
+    host thread (fixed tables of the forward step and of the transposed step
+    at every segment position; full segments replayed from a CUDA graph, the
+    partial first adjoint segment launched directly): gradients (lambda, mu,
+    b) and misfits bitwise those of one prop_gradient per shot and of the
+    per-thread batch, with graphs on and off."""
+    monkeypatch.setenv("WAVEPROP_GRAPHS", graphs)
+    sel = elastic_window_shots()
+    kw = dict(snap_mode=snap, ckpt_interval=interval)
+    ref = []
+    for p, d in sel:
+        prop = wp.Propagator.from_problem(p, **kw)
+        ref.append(prop.gradient(p.wavelet, p.src, p.rec, d))
+        prop.close()
+    out = {}
+    for lock in ("1", "0"):
+        monkeypatch.setenv("WAVEPROP_LOCKSTEP", lock)
+        props = [wp.Propagator.from_problem(p, **kw) for p, _ in sel]
+        out[lock] = wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                                      [p.rec for p, _ in sel], [d for _, d in sel])
+        out[lock + "stats"] = wp.batch_stats()
+        for pr in props:
+            pr.close()
+    assert out["1stats"][0] > 0 and out["1stats"][1] == 0, out["1stats"]
+    for i in range(len(sel)):
+        assert np.max(np.abs(ref[i][0])) > 0
+        for lock in ("1", "0"):
+            np.testing.assert_array_equal(out[lock][0][i], ref[i][0], err_msg=f"shot {i} lockstep {lock}")
+            assert out[lock][1][i] == ref[i][1], (i, lock)
