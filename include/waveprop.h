@@ -296,11 +296,6 @@ int prop_step(prop_t *p, int nsteps, int adjoint);
 /* Time step actually used (after the CFL rule), in seconds. */
 float prop_dt(const prop_t *p);
 
-/* Device time of the stencil kernels of the most recent call, summed over
- * launches [ms], and the number of those launches (CUDA events on the
- * handle's stream).  Used for roofline accounting. */
-int prop_kernel_time(const prop_t *p, double *ms, long long *launches);
-
 /* Tile shape of the x-streaming stencil kernels: a CTA updates a tile of
  * 32 (z) x prop_tile_rows (y) columns over prop_tile_planes planes of x.
  * prop_create picks both by timing a few steps of the zero state for a set

@@ -26,10 +26,13 @@ ERR_NAMES = {0: "PROP_OK", -1: "PROP_EINVAL", -2: "PROP_ENOMEM", -3: "PROP_ECUDA
 # exported symbols declared in include/waveprop.h
 ABI_SYMBOLS = ("prop_create", "prop_forward", "prop_adjoint", "prop_gradient",
                "prop_forward_saved", "prop_backward", "prop_grid_dims", "prop_set_state",
-               "prop_get_state", "prop_step", "prop_dt", "prop_kernel_time", "prop_destroy",
+               "prop_get_state", "prop_step", "prop_dt", "prop_destroy",
                "prop_last_error", "prop_forward_noalloc", "prop_tile_planes", "prop_tile_rows",
                "prop_gradient_batch", "prop_gradient_bytes", "prop_plan_waves",
                "prop_gradient_aniso", "prop_stack_image", "prop_trim", "prop_forward_batch")
+# measurement and self-test hooks declared in include/waveprop_diag.h
+DIAG_SYMBOLS = ("prop_profile", "prop_kernel_stats", "prop_kernel_time", "prop_last_launches",
+                "prop_batch_stats", "prop_fp32_peak", "prop_selftest_wait")
 
 
 class PropDesc(C.Structure):
@@ -284,9 +287,9 @@ class Propagator:
         return out, J.value
 
     def selftest_wait(self, seconds=0.2):
-        """Failure-path self-test (``prop_selftest_wait``, not in the public
-        header): a device wait that nothing completes; raises PropError
-        PROP_ETIMEOUT after ``seconds``."""
+        """Failure-path self-test (``prop_selftest_wait``,
+        include/waveprop_diag.h): a device wait that nothing completes;
+        raises PropError PROP_ETIMEOUT after ``seconds``."""
         self._check(lib().prop_selftest_wait(self.h, float(seconds)))
 
     def trim(self):
@@ -353,7 +356,7 @@ class Propagator:
         return lib().prop_gradient_bytes(self.h, int(nrec))
 
 
-# kernel ids of Propagator.kernel_stats
+# kernel groups of Propagator.kernel_stats (PROP_K_* of include/waveprop_diag.h)
 K_TTI_FWD, K_TTI_ADJ, K_EL_FWD, K_EL_ADJ, K_EL_ADJ_GRAD, K_EL_ADJ_U, K_AC_STEP, K_AC_IMG = 0, 1, 2, 3, 4, 5, 6, 7
 
 

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/waveprop.h"
+#include "../../include/waveprop_diag.h"
 
 #define WP_MAXM 8   // space order up to 16
 

@@ -827,7 +827,7 @@ extern "C" int prop_kernel_time(const prop_t *P, double *ms, long long *launches
     return PROP_OK;
 }
 
-// measurement hooks (declared in the Python binding, not in the public header)
+// measurement hooks (waveprop_diag.h)
 extern "C" int prop_profile(prop_t *P, int on)
 {
     if (!P) return wp_fail(nullptr, PROP_EINVAL, "NULL handle");
@@ -1964,6 +1964,8 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
     if (graphs) {
         cudaGraph_t gr = nullptr;
         cudaGraphExec_t ex = nullptr;
+        std::vector<long long> before(n);
+        for (int i = 0; i < n; i++) before[i] = shots[i]->kern_launches;
         WP_CK(P0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
         const int r0 = step(0), r1 = r0 ? r0 : step(1);
         const cudaError_t ec = cudaStreamEndCapture(st, &gr);
@@ -1985,6 +1987,9 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
         }
         WP_CK(P0, cudaStreamSynchronize(st));
         cudaGraphExecDestroy(ex);
+        // the capture counted the launches of one replay
+        for (int i = 0; i < n; i++)
+            shots[i]->kern_launches += (shots[i]->kern_launches - before[i]) * (done / 2 - 1);
     }
     for (; done < nt; done++) WP_TRY(step(done & 1));
     // the final state in st[] order (TTI: odd nt leaves the rotated arrangement)
@@ -2018,10 +2023,10 @@ extern "C" int prop_forward_batch(prop_t *const *shots, int n, const float *cons
     return first;
 }
 
-// shared TTI step launches of the last prop_gradient_batch call: rounds
-// launched together (rendezvous rounds and lockstep steps), rounds whose
-// steps had to be launched one by one
-static long long batch_stats[2] = {0, 0};
+// shared step launches of the calling thread's last prop_gradient_batch
+// call: rounds launched together (rendezvous rounds and lockstep steps),
+// rounds whose steps had to be launched one by one
+static thread_local long long batch_stats[2] = {0, 0};
 extern "C" int prop_batch_stats(long long *shared, long long *alone)
 {
     if (shared) *shared = batch_stats[0];
@@ -2308,10 +2313,13 @@ static int gradient_lockstep(prop_t *const *shots, int n, const float *const *wa
                 if (e) cudaGraphExecDestroy(e);
         }
     } gx{st};
+    std::vector<long long> held[4];     // launches each graph holds, per shot
     // run body() directly, or from graph `id` (captured on first use)
     auto run = [&](int id, const std::function<int()> &body) -> int {
         if (!graphs) return body();
         if (!gx.g[id]) {
+            std::vector<long long> before(n);
+            for (int i = 0; i < n; i++) before[i] = shots[i]->kern_launches;
             cudaGraph_t gr = nullptr;
             WP_CK(P0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             const int rb = body();
@@ -2324,6 +2332,10 @@ static int gradient_lockstep(prop_t *const *shots, int n, const float *const *wa
             const cudaError_t ei = cudaGraphInstantiate(&gx.g[id], gr, 0);
             cudaGraphDestroy(gr);
             WP_CK(P0, ei);
+            held[id].resize(n);
+            for (int i = 0; i < n; i++) held[id][i] = shots[i]->kern_launches - before[i];
+        } else {
+            for (int i = 0; i < n; i++) shots[i]->kern_launches += held[id][i];
         }
         WP_CK(P0, cudaGraphLaunch(gx.g[id], st));
         return PROP_OK;
@@ -2618,9 +2630,12 @@ static int el_gradient_lockstep(prop_t *const *shots, int n, const float *const 
                 if (e) cudaGraphExecDestroy(e);
         }
     } gx{st};
+    std::vector<long long> held[2];     // launches each graph holds, per shot
     auto run = [&](int id, const std::function<int()> &body) -> int {
         if (!graphs) return body();
         if (!gx.g[id]) {
+            std::vector<long long> before(n);
+            for (int i = 0; i < n; i++) before[i] = shots[i]->kern_launches;
             cudaGraph_t gr = nullptr;
             WP_CK(P0, cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
             const int rb = body();
@@ -2633,6 +2648,10 @@ static int el_gradient_lockstep(prop_t *const *shots, int n, const float *const 
             const cudaError_t ei = cudaGraphInstantiate(&gx.g[id], gr, 0);
             cudaGraphDestroy(gr);
             WP_CK(P0, ei);
+            held[id].resize(n);
+            for (int i = 0; i < n; i++) held[id][i] = shots[i]->kern_launches - before[i];
+        } else {
+            for (int i = 0; i < n; i++) shots[i]->kern_launches += held[id][i];
         }
         WP_CK(P0, cudaGraphLaunch(gx.g[id], st));
         return PROP_OK;

@@ -1,6 +1,7 @@
 """C ABI checks that need no GPU: the library builds/loads, exports every
-function declared in include/waveprop.h, and the binding's prop_desc layout
-matches the C compiler's."""
+function declared in include/waveprop.h and include/waveprop_diag.h (and no
+other prop_ symbol), and the binding's prop_desc layout matches the C
+compiler's."""
 import ctypes as C
 import os
 import re
@@ -11,12 +12,13 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "waveprop.h")
+DIAG_HEADER = os.path.join(ROOT, "include", "waveprop_diag.h")
 
 
-def _declared():
-    txt = open(HEADER).read()
+def _declared(path=HEADER):
+    txt = open(path).read()
     txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(prop_[a-z_]+)\s*\(", txt)))
+    return sorted(set(re.findall(r"\b(prop_[a-z0-9_]+)\s*\(", txt)))
 
 
 @pytest.fixture(scope="module")
@@ -36,16 +38,22 @@ def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True,
                          text=True, check=True).stdout
     exported = set(re.findall(r"\bT\s+(\w+)", out))
-    missing = [n for n in _declared() if n not in exported]
+    declared = _declared() + _declared(DIAG_HEADER)
+    missing = [n for n in declared if n not in exported]
     assert not missing, missing
-    # and the binding lists exactly the header's functions
+    # every exported prop_ function is declared in one of the two headers
+    undeclared = sorted(n for n in exported if n.startswith("prop_") and n not in declared)
+    assert not undeclared, undeclared
+    # and the binding lists exactly the headers' functions
     import paper_2004_10519_gb300 as wp
     assert sorted(wp.ABI_SYMBOLS) == _declared()
+    assert sorted(wp.DIAG_SYMBOLS) == _declared(DIAG_HEADER)
+    assert not set(_declared()) & set(_declared(DIAG_HEADER))
 
 
 def test_library_loads_without_gpu(libpath):
     L = C.CDLL(libpath)
-    for n in _declared():
+    for n in _declared() + _declared(DIAG_HEADER):
         assert hasattr(L, n)
     # calls that touch no device: NULL-safe destroy and error queries
     L.prop_destroy(None)
@@ -184,3 +192,38 @@ def test_noalloc_rejects_huge_grids_without_gpu(libpath):
             rc = L.prop_forward_noalloc(C.byref(d), models, p, p, 1, p, 1, p, None)
             assert rc == wp.PROP_EINVAL, (kind, nx, ny, nz)
             assert msg in L.prop_last_error(None), (kind, nx, L.prop_last_error(None))
+
+
+def test_diag_hooks_reject_null_without_gpu(libpath):
+    """The measurement hooks of include/waveprop_diag.h check their arguments
+    before touching a device."""
+    import threading
+    L = C.CDLL(libpath)
+    vp = C.c_void_p
+    L.prop_profile.argtypes = [vp, C.c_int]
+    L.prop_kernel_stats.argtypes = [vp, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.prop_kernel_time.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]
+    L.prop_last_launches.restype = C.c_longlong
+    L.prop_last_launches.argtypes = [vp]
+    L.prop_fp32_peak.argtypes = [C.POINTER(C.c_double)]
+    L.prop_selftest_wait.argtypes = [vp, C.c_float]
+    L.prop_batch_stats.argtypes = [C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)]
+    EINVAL = -1
+    assert L.prop_profile(None, 1) == EINVAL
+    assert L.prop_kernel_stats(None, 0, None, None) == EINVAL
+    assert L.prop_kernel_time(None, None, None) == EINVAL
+    assert L.prop_last_launches(None) == 0
+    assert L.prop_fp32_peak(None) == EINVAL
+    assert L.prop_selftest_wait(None, 0.1) == EINVAL
+    # the batch counters belong to the calling thread: zero in a new one
+    out = []
+
+    def reader():
+        a, b = C.c_longlong(-7), C.c_longlong(-7)
+        out.append((L.prop_batch_stats(C.byref(a), C.byref(b)), a.value, b.value))
+        out.append(L.prop_batch_stats(None, None))
+
+    t = threading.Thread(target=reader)
+    t.start()
+    t.join()
+    assert out == [(0, 0, 0), 0]
