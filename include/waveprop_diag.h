@@ -64,7 +64,8 @@ int prop_kernel_time(const prop_t *p, double *ms, long long *steps);
  * call (every kernel: stencil passes, injection, interpolation, pointwise,
  * encode/decode of snapshots; a replayed CUDA graph counts the launches it
  * holds, and a launch that advances several shots of a batch counts once
- * for each of them).  0 for p == NULL. */
+ * for each of them; prop_trim leaves the count as it is, so after a batch
+ * call it is the count of that call).  0 for p == NULL. */
 long long prop_last_launches(const prop_t *p);
 
 /* Steps of the most recent prop_gradient_batch call made by the calling

@@ -654,10 +654,16 @@ extern "C" int prop_grid_dims(const prop_t *P, int *dims, int *nf)
     return PROP_OK;
 }
 
-static int check_handle(prop_s *P)
+static int check_usable(prop_s *P)
 {
     if (!P) return wp_fail(nullptr, PROP_EINVAL, "NULL handle");
     if (P->broken) return wp_fail(P, PROP_ESTATE, "handle unusable after an earlier CUDA error: " + P->err);
+    return PROP_OK;
+}
+// start of a call that launches work: the launch count starts from zero
+static int check_handle(prop_s *P)
+{
+    WP_TRY(check_usable(P));
     P->kern_launches = 0;
     return PROP_OK;
 }
@@ -1515,7 +1521,7 @@ extern "C" int prop_stack_image(prop_t *P, const float *image, float *stack, con
 
 extern "C" int prop_trim(prop_t *P)
 {
-    WP_TRY(check_handle(P));
+    WP_TRY(check_usable(P));      // launches nothing: the launch count stays
     WP_CK(P, cudaStreamSynchronize(P->stream));
     free_snaps(P);
     for (auto &a : P->st) { cudaFree(a); a = nullptr; }

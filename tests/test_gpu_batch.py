@@ -366,3 +366,30 @@ def test_elastic_lockstep_gradient_batch_is_bitwise(wp, monkeypatch, snap, inter
         for lock in ("1", "0"):
             np.testing.assert_array_equal(out[lock][0][i], ref[i][0], err_msg=f"shot {i} lockstep {lock}")
             assert out[lock][1][i] == ref[i][1], (i, lock)
+
+
+@pytest.mark.parametrize("kind", ["tti", "elastic"])
+def test_replayed_graphs_count_their_launches(wp, monkeypatch, kind):
+    """prop_last_launches counts the launches a replayed CUDA graph holds:
+    after a lockstep gradient wave and a lockstep forward batch every shot
+    reports the same launch count with graphs as with direct launches."""
+    monkeypatch.setenv("WAVEPROP_LOCKSTEP", "1")
+    sel = window_shots(nt=60) if kind == "tti" else elastic_window_shots()
+    kw = dict(snap_mode=wp.SNAP_CKPT_BF16, ckpt_interval=6)
+    counts = {}
+    for graphs in ("1", "0"):
+        monkeypatch.setenv("WAVEPROP_GRAPHS", graphs)
+        props = [wp.Propagator.from_problem(p, **kw) for p, _ in sel]
+        wp.gradient_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel],
+                          [p.rec for p, _ in sel], [d for _, d in sel])
+        assert wp.batch_stats()[0] > 0
+        grad = [pr.last_launches() for pr in props]
+        wp.forward_batch(props, [p.wavelet for p, _ in sel], [p.src for p, _ in sel], [p.rec for p, _ in sel])
+        fwd = [pr.last_launches() for pr in props]
+        counts[graphs] = (grad, fwd)
+        for pr in props:
+            pr.close()
+    assert counts["1"] == counts["0"], counts
+    # at least one stencil launch per step and shot
+    nt = sel[0][0].nt
+    assert min(counts["0"][0]) >= 2 * nt and min(counts["0"][1]) >= nt, counts
