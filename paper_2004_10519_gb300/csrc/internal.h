@@ -330,9 +330,14 @@ int stencil_xchunk(const GridDev &g, int sms);
 
 // error helpers
 int wp_fail(prop_s *P, int code, const std::string &msg);
-// every device allocation of the library (WAVEPROP_FAULT=alloc: fails)
+// every device allocation of the library goes through wp_dev_alloc
+// (WAVEPROP_FAULT=alloc: every allocation fails): PROP_ENOMEM or PROP_ECUDA
+// with the message in *msg (may be NULL), *p = NULL on failure; wp_malloc
+// records the failure on the handle (P may be NULL)
+int wp_dev_alloc(void **p, size_t bytes, const char *what, std::string *msg);
 int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what);
-// status of the device error word read back after a call: bit 1 (a bounded
+// status of the device error word read back after a call: bit 3 (the
+// bounds-checking build skipped an access) -> PROP_ECUDA; bit 1 (a bounded
 // device wait expired) -> PROP_ETIMEOUT; bit 0 (NaN/Inf seen) ->
 // PROP_EUNSTABLE when check_nan is set; else PROP_OK
 int wp_flag_status(prop_s *P, int flag);

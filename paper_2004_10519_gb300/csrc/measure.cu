@@ -36,7 +36,7 @@ extern "C" int prop_fp32_peak(double *tflops)
         return PROP_ECUDA;
     const int blocks = sms * 8, threads = 256, iters = 1 << 15;
     float *out = nullptr;
-    if (cudaMalloc(&out, sizeof(float) * blocks) != cudaSuccess) return PROP_ENOMEM;
+    if (int rc = wp_malloc(nullptr, (void **)&out, sizeof(float) * blocks, "FP32 peak measurement")) return rc;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -45,21 +45,33 @@ int wp_cuda(prop_s *P, cudaError_t e, const char *what)
 // All device allocations of the library go through here (prop_forward_noalloc
 // makes none).  WAVEPROP_FAULT=alloc makes every allocation fail (host-side
 // fault injection for tests).
-int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what)
+int wp_dev_alloc(void **p, size_t bytes, const char *what, std::string *msg)
 {
     *p = nullptr;
     const char *f = getenv("WAVEPROP_FAULT");
-    if (f && !strcmp(f, "alloc"))
-        return wp_fail(P, PROP_ENOMEM, std::string("injected allocation failure: ") + what);
-    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        char buf[160];
-        snprintf(buf, sizeof buf, "cannot allocate %.3f GB for %s", bytes / 1e9, what);
-        return wp_fail(P, PROP_ENOMEM, buf);
+    if (f && !strcmp(f, "alloc")) {
+        if (msg) *msg = std::string("injected allocation failure: ") + what;
+        return PROP_ENOMEM;
     }
-    return PROP_OK;
+    const cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e == cudaSuccess) return PROP_OK;
+    *p = nullptr;
+    char buf[200];
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        snprintf(buf, sizeof buf, "cannot allocate %.3f GB for %s", bytes / 1e9, what);
+        if (msg) *msg = buf;
+        return PROP_ENOMEM;
+    }
+    snprintf(buf, sizeof buf, "CUDA error '%s' allocating %.3f GB for %s", cudaGetErrorString(e), bytes / 1e9, what);
+    if (msg) *msg = buf;
+    return PROP_ECUDA;
+}
+int wp_malloc(prop_s *P, void **p, size_t bytes, const char *what)
+{
+    std::string m;
+    const int rc = wp_dev_alloc(p, bytes, what, &m);
+    return rc ? wp_fail(P, rc, m) : PROP_OK;
 }
 #define WP_MALLOC(P, ptr, bytes, what)                                            \
     do {                                                                          \

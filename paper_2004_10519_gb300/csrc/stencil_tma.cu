@@ -1841,7 +1841,9 @@ static int batch_tiles(TtiBatch *b, const std::vector<prop_s *> &Ps, cudaStream_
         cudaFree(b->dtiles);
         b->dtiles = nullptr;
         b->tiles_cap = 0;
-        if (int rc = ck(cudaMalloc(&b->dtiles, b->htiles.size() * sizeof(int4)), "batched TTI tile table")) return rc;
+        if (int rc = wp_dev_alloc((void **)&b->dtiles, b->htiles.size() * sizeof(int4), "batched TTI tile table",
+                                  err))
+            return rc;
         b->tiles_cap = b->htiles.size();
     }
     if (int rc = ck(cudaMemcpyAsync(b->dtiles, b->htiles.data(), b->htiles.size() * sizeof(int4),
@@ -1881,7 +1883,8 @@ int tti_batch_fix(TtiBatch *b, const TtiBatchReq *req, int n, int slot, cudaStre
         b->fixed_mode.resize(slot + 1, -1);
     }
     if (!b->dfixed[slot])
-        if (int rc = ck(cudaMalloc(&b->dfixed[slot], b->fixed_cap * sizeof(TtiShot)), "batched TTI fixed table"))
+        if (int rc = wp_dev_alloc((void **)&b->dfixed[slot], b->fixed_cap * sizeof(TtiShot),
+                                  "batched TTI fixed table", err))
             return rc;
     std::vector<TtiShot> H(n);
     int rc = 1;
@@ -1965,7 +1968,7 @@ int tti_batch_step(TtiBatch *b, const TtiBatchReq *req, int n, cudaStream_t st, 
         cudaFree(b->dshots);
         b->dshots = nullptr;
         b->shots_cap = 0;
-        if (int rc = ck(cudaMalloc(&b->dshots, n * sizeof(TtiShot)), "batched TTI shot table")) return rc;
+        if (int rc = wp_dev_alloc((void **)&b->dshots, n * sizeof(TtiShot), "batched TTI shot table", err)) return rc;
         b->shots_cap = n;
     }
     if ((size_t)n > b->hcap) {
@@ -2070,7 +2073,7 @@ static int el_batch_launch(TtiBatch *b, const ElBatchReq *req, int n, cudaStream
         cudaFree(b->del);
         b->del = nullptr;
         b->del_cap = 0;
-        if (int rc = ck(cudaMalloc(&b->del, bytes), "batched elastic shot table")) return rc;
+        if (int rc = wp_dev_alloc((void **)&b->del, bytes, "batched elastic shot table", err)) return rc;
         b->del_cap = bytes;
     }
     if (bytes > b->hel_cap) {
@@ -2174,8 +2177,8 @@ int el_batch_fix(TtiBatch *b, const ElBatchReq *req, int n, int slot, cudaStream
         b->elfixed_mode.resize(slot + 1, -1);
     }
     if (!b->elfixed[slot])
-        if (int rc = ck(cudaMalloc(&b->elfixed[slot], 3 * b->elfixed_cap * sizeof(ElShot)),
-                        "batched elastic fixed table"))
+        if (int rc = wp_dev_alloc((void **)&b->elfixed[slot], 3 * b->elfixed_cap * sizeof(ElShot),
+                                  "batched elastic fixed table", err))
             return rc;
     std::vector<ElShot> H((mode == 0 ? 1 : 3) * n);
     int rc = 1;

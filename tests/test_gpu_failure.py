@@ -130,3 +130,59 @@ def test_nan_in_state_is_reported_when_checked(kind):
         tr = prop.forward(p.wavelet, p.src, p.rec)
         assert np.all(np.isfinite(tr)) and np.max(np.abs(tr)) > 0
         prop.close()
+
+
+@pytest.mark.parametrize("kind", ["tti", "elastic"])
+def test_injected_allocation_failure_in_batches(monkeypatch, kind):
+    """WAVEPROP_FAULT=alloc also fails the allocations of the batched calls
+    (per-shot work arrays and the batches' device tables): prop_gradient_batch
+    and prop_forward_batch, in lockstep and with one thread per shot, return
+    PROP_ENOMEM, the handles stay usable and give the reference results
+    afterwards, and device memory returns to its starting level."""
+    import paper_2004_10519_gb300 as wp
+    wp.lib()
+    if kind == "tti":
+        ps = [synth.tti_two_layer(n=24 + 4 * i, nbl=6, so=8, nt=40) for i in range(2)]
+    else:
+        ps = [synth.elastic_random(n=24 + 4 * i, nbl=6, so=8, nt=40, corr_len=60.0, rec_dx=40.0) for i in range(2)]
+        for p in ps:
+            p.rec = synth.line_receivers(10.0, 20.0, 8, 95.0, 5.0)
+    kw = dict(snap_mode=wp.SNAP_CKPT_BF16, ckpt_interval=6)
+    args = lambda: ([p.wavelet for p in ps], [p.src for p in ps], [p.rec for p in ps])
+
+    def run(lock):
+        monkeypatch.setenv("WAVEPROP_LOCKSTEP", lock)
+        props = [wp.Propagator.from_problem(p, **kw) for p in ps]
+        trs = wp.forward_batch(props, *args())
+        g, J = wp.gradient_batch(props, *args(), [0.5 * t for t in trs])
+        return props, trs, g
+
+    # warm-up: loads the modules of every kernel involved
+    for lock in ("1", "0"):
+        props, trs, g = run(lock)
+        for q in props:
+            q.close()
+    before = _free_bytes()
+    for lock in ("1", "0"):
+        monkeypatch.setenv("WAVEPROP_LOCKSTEP", lock)
+        props = [wp.Propagator.from_problem(p, **kw) for p in ps]
+        ref = wp.forward_batch(props, *args())
+        gref, _ = wp.gradient_batch(props, *args(), [0.5 * t for t in ref])
+        for q in props:
+            q.trim()
+        monkeypatch.setenv("WAVEPROP_FAULT", "alloc")
+        with pytest.raises(wp.PropError) as e:
+            wp.forward_batch(props, *args())
+        assert e.value.code == wp.PROP_ENOMEM, lock
+        with pytest.raises(wp.PropError) as e:
+            wp.gradient_batch(props, *args(), [0.5 * t for t in ref])
+        assert e.value.code == wp.PROP_ENOMEM, lock
+        monkeypatch.delenv("WAVEPROP_FAULT")
+        trs = wp.forward_batch(props, *args())
+        g, _ = wp.gradient_batch(props, *args(), [0.5 * t for t in ref])
+        for i in range(2):
+            np.testing.assert_array_equal(trs[i], ref[i])
+            np.testing.assert_array_equal(g[i], gref[i])
+        for q in props:
+            q.close()
+        assert _free_bytes() == before, lock
