@@ -284,7 +284,6 @@ void sp_record_trace_s(prop_s *P, const SparseDev *S, const float *f0, const flo
 void sp_transpose(prop_s *P, const float *in_tn, float *out_nt, int n, int nt);
 
 // misc kernels
-void k_fill(prop_s *P, float *a, long long n, float v);
 void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode);
 // fold a computational-grid array onto the physical grid (transpose of the
 // edge-replication extension); s1, s2: scratch of N floats each

@@ -119,13 +119,6 @@ __global__ void transpose_kernel(const float *__restrict__ in, float *__restrict
     }
 }
 
-__global__ void fill_kernel(float *a, long long n, float v)
-{
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        a[i] = v;
-}
-
 // mode 0: comp = scale*phys ; 1: comp = 1/(scale*phys)^2
 __global__ void extend_kernel(GridDev g, const float *__restrict__ phys, float *__restrict__ comp,
                               float scale, int mode)
@@ -447,11 +440,6 @@ void sp_transpose(prop_s *P, const float *in_tn, float *out_nt, int n, int nt)
     dim3 blk(32, 8), grd((n + 31) / 32, (nt + 31) / 32);
     transpose_kernel<<<grd, blk, 0, P->stream>>>(in_tn, out_nt, n, nt);
     P->kern_launches++;
-}
-
-void k_fill(prop_s *P, float *a, long long n, float v)
-{
-    fill_kernel<<<std::min(nblk(n), 152 * 16), NB, 0, P->stream>>>(a, n, v);
 }
 
 void k_extend(prop_s *P, const float *phys, float *comp, float scale, int mode)
