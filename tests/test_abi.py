@@ -227,3 +227,20 @@ def test_diag_hooks_reject_null_without_gpu(libpath):
     t.start()
     t.join()
     assert out == [(0, 0, 0), 0]
+
+
+def test_headers_compile_as_c_and_cxx():
+    """Both headers are self-contained C (and C++): a translation unit that
+    includes only waveprop_diag.h takes the address of every declared
+    function with the declared types."""
+    names = _declared() + _declared(DIAG_HEADER)
+    body = "".join(f"    p[{i}] = (void (*)(void)){n};\n" for i, n in enumerate(names))
+    prog = ('#include "waveprop_diag.h"\nint main(void){\n'
+            f"    void (*p[{len(names)}])(void);\n{body}"
+            "    return PROP_K_GROUPS == 8 && p[0] != 0 ? 0 : 1;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        for lang, cc, ext in (("c", "gcc", ".c"), ("c++", "g++", ".cpp")):
+            src = os.path.join(d, "t" + ext)
+            open(src, "w").write(prog)
+            subprocess.check_call([cc, "-std=c11" if lang == "c" else "-std=c++17", "-Wall", "-Werror",
+                                   "-fsyntax-only", "-I", os.path.dirname(HEADER), src])
