@@ -38,6 +38,9 @@
  *     after PROP_ECUDA or PROP_ETIMEOUT every later call returns PROP_ESTATE
  *     until prop_destroy.  prop_last_error gives the message.
  *   - One handle per host thread at a time.
+ *
+ * Measurement hooks (device time per kernel group, launch counts, the FP32
+ * peak) and the wait self-test are declared in waveprop_diag.h.
  */
 #ifndef WAVEPROP_H
 #define WAVEPROP_H
